@@ -1,0 +1,653 @@
+/*
+ * Reference oracle for the per-frame dynamic-mesh update -- TEST
+ * INFRASTRUCTURE ONLY.  Plain, slow, serial C.  It shares no code, header or
+ * constant with the CUDA library; only the test-suite, the smoke check and the
+ * benchmark's CPU-baseline leg load it.
+ *
+ * Everything is float64 except the Morton-key step, whose recipe is defined in
+ * float32 (see orc_morton); this file must be compiled with
+ * -ffp-contract=off so that no fused multiply-add changes a rounding.
+ *
+ * What the paper fixes and what is our reading:
+ *   - NearestSurface(v, M) of Eq. 1 / Eq. 2 (Sec. 3.3): the exact closest
+ *     point of v on the triangle mesh M, returned with its barycentric
+ *     weights ("barycentric interpolation for sub-face accuracy", Eq. 2).
+ *     The k-NN weighting Sec. 3.3 mentions for Eq. 1 is not used (reading).
+ *   - Acceleration structure built once from F0, holding indices only
+ *     (Sec. 3.4, Initialization): a linear BVH whose leaves are sorted faces;
+ *     the paper gives no construction, so this is Karras (2012).
+ *   - Collision-structure rebuild of the varying-topology baseline (Sec. 4.1).
+ *   - Gaussians bound to faces (Sec. 2, Sec. 3.1): the paper gives no
+ *     formula; the face-frame reading is ours (orc_bind_gaussians).
+ *   - Chamfer distance on surface samples (Sec. 4.2); squared, mean per
+ *     direction, point-to-mesh (reading).
+ *
+ * Pins for every function live in tests/test_oracle_*.py (closed forms,
+ * invariants, brute force, central differences).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_TIE_REL 1e-6      /* ties: lowest face id within 1e-6 relative distance */
+#define ORC_TIE_ABS 1e-12     /* absolute floor, times the mesh bounding-box diagonal */
+
+/* ------------------------------------------------------------------ */
+/* small float64 vector helpers                                        */
+/* ------------------------------------------------------------------ */
+typedef struct { double x, y, z; } d3;
+
+static d3 mk(double x, double y, double z) { d3 r = {x, y, z}; return r; }
+static d3 ld3(const double *p) { return mk(p[0], p[1], p[2]); }
+static d3 sub(d3 a, d3 b) { return mk(a.x - b.x, a.y - b.y, a.z - b.z); }
+static d3 add(d3 a, d3 b) { return mk(a.x + b.x, a.y + b.y, a.z + b.z); }
+static d3 scl(d3 a, double s) { return mk(a.x * s, a.y * s, a.z * s); }
+static double dot(d3 a, d3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+static d3 cross(d3 a, d3 b) {
+    return mk(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+static double norm(d3 a) { return sqrt(dot(a, a)); }
+
+/* ------------------------------------------------------------------ */
+/* Closest point on one triangle (Ericson, Real-Time Collision          */
+/* Detection, 5.1.5: classify p into the Voronoi regions of the         */
+/* vertices, edges and face of abc).                                   */
+/* ------------------------------------------------------------------ */
+static double seg_closest(d3 p, d3 x, d3 y, double *t_out) {
+    d3 xy = sub(y, x);
+    double L2 = dot(xy, xy);
+    double t = 0.0;
+    if (L2 > 0.0) {
+        t = dot(sub(p, x), xy) / L2;
+        if (t < 0.0) t = 0.0;
+        if (t > 1.0) t = 1.0;
+    }
+    d3 c = add(x, scl(xy, t));
+    d3 d = sub(p, c);
+    *t_out = t;
+    return dot(d, d);
+}
+
+/* Returns the squared distance; bary = (u, v, w) with point = u a + v b + w c. */
+double orc_point_triangle(const double *P, const double *A, const double *B,
+                          const double *C, double *bary, double *point) {
+    d3 p = mk(P[0], P[1], P[2]), a = mk(A[0], A[1], A[2]);
+    d3 b = mk(B[0], B[1], B[2]), c = mk(C[0], C[1], C[2]);
+    double u, v, w;
+    d3 ab = sub(b, a), ac = sub(c, a);
+    d3 n = cross(ab, ac);
+    if (n.x == 0.0 && n.y == 0.0 && n.z == 0.0) {
+        /* Zero-area triangle (reading): nearest of its three edges, first wins. */
+        double t0, t1, t2;
+        double s0 = seg_closest(p, a, b, &t0);
+        double s1 = seg_closest(p, b, c, &t1);
+        double s2 = seg_closest(p, c, a, &t2);
+        if (s0 <= s1 && s0 <= s2) { u = 1.0 - t0; v = t0; w = 0.0; }
+        else if (s1 <= s2)       { u = 0.0; v = 1.0 - t1; w = t1; }
+        else                     { u = t2; v = 0.0; w = 1.0 - t2; }
+    } else {
+        d3 ap = sub(p, a);
+        double d1 = dot(ab, ap), d2 = dot(ac, ap);
+        d3 bp = sub(p, b);
+        double d3_ = dot(ab, bp), d4 = dot(ac, bp);
+        d3 cp = sub(p, c);
+        double d5 = dot(ab, cp), d6 = dot(ac, cp);
+        double vc = d1 * d4 - d3_ * d2;
+        double vb = d5 * d2 - d1 * d6;
+        double va = d3_ * d6 - d5 * d4;
+        if (d1 <= 0.0 && d2 <= 0.0) {                 /* vertex a */
+            u = 1.0; v = 0.0; w = 0.0;
+        } else if (d3_ >= 0.0 && d4 <= d3_) {          /* vertex b */
+            u = 0.0; v = 1.0; w = 0.0;
+        } else if (vc <= 0.0 && d1 >= 0.0 && d3_ <= 0.0) {   /* edge ab */
+            double t = d1 / (d1 - d3_);
+            u = 1.0 - t; v = t; w = 0.0;
+        } else if (d6 >= 0.0 && d5 <= d6) {           /* vertex c */
+            u = 0.0; v = 0.0; w = 1.0;
+        } else if (vb <= 0.0 && d2 >= 0.0 && d6 <= 0.0) {   /* edge ac */
+            double t = d2 / (d2 - d6);
+            u = 1.0 - t; v = 0.0; w = t;
+        } else if (va <= 0.0 && (d4 - d3_) >= 0.0 && (d5 - d6) >= 0.0) {  /* edge bc */
+            double t = (d4 - d3_) / ((d4 - d3_) + (d5 - d6));
+            u = 0.0; v = 1.0 - t; w = t;
+        } else {                                        /* face interior */
+            double s = 1.0 / (va + vb + vc);
+            v = vb * s;
+            w = vc * s;
+            u = 1.0 - v - w;
+        }
+    }
+    d3 q = add(add(scl(a, u), scl(b, v)), scl(c, w));
+    d3 d = sub(p, q);
+    bary[0] = u; bary[1] = v; bary[2] = w;
+    point[0] = q.x; point[1] = q.y; point[2] = q.z;
+    return dot(d, d);
+}
+
+/* ------------------------------------------------------------------ */
+/* NearestSurface over a whole mesh (Eq. 1, Eq. 2): brute force over     */
+/* every face.  Ties: the lowest face id among faces whose distance is  */
+/* within d* (1 + 1e-6) + 1e-12 diag, d* the exact minimum.  A query     */
+/* whose d* exceeds max_dist gets face -1, d2 = +inf, zero bary/point.  */
+/* ------------------------------------------------------------------ */
+double orc_mesh_diag(const double *V, const int32_t *F, int64_t nF) {
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t f = 0; f < nF; ++f)
+        for (int k = 0; k < 3; ++k) {
+            const double *v = V + 3 * (int64_t)F[3 * f + k];
+            for (int c = 0; c < 3; ++c) {
+                if (v[c] < lo[c]) lo[c] = v[c];
+                if (v[c] > hi[c]) hi[c] = v[c];
+            }
+        }
+    if (nF == 0) return 0.0;
+    return sqrt((hi[0] - lo[0]) * (hi[0] - lo[0]) + (hi[1] - lo[1]) * (hi[1] - lo[1]) +
+                (hi[2] - lo[2]) * (hi[2] - lo[2]));
+}
+
+void orc_closest_point_mesh(const double *V, const int32_t *F, int64_t nF,
+                            const double *Q, int64_t nQ, double max_dist,
+                            int32_t *face, double *bary, double *point, double *d2,
+                            double *d2_all /* nullable: [nQ * nF] every face's distance^2 */) {
+    double tau = ORC_TIE_ABS * orc_mesh_diag(V, F, nF);
+    double *dist = (double *)malloc(sizeof(double) * (size_t)(nF > 0 ? nF : 1));
+    for (int64_t q = 0; q < nQ; ++q) {
+        double p[3] = {Q[3 * q], Q[3 * q + 1], Q[3 * q + 2]};
+        double best = INFINITY;
+        for (int64_t f = 0; f < nF; ++f) {
+            double A[3], B[3], C[3], bb[3], pp[3];
+            for (int c = 0; c < 3; ++c) {
+                A[c] = V[3 * (int64_t)F[3 * f] + c];
+                B[c] = V[3 * (int64_t)F[3 * f + 1] + c];
+                C[c] = V[3 * (int64_t)F[3 * f + 2] + c];
+            }
+            dist[f] = orc_point_triangle(p, A, B, C, bb, pp);
+            if (d2_all) d2_all[q * nF + f] = dist[f];
+            if (dist[f] < best) best = dist[f];
+        }
+        int32_t pick = -1;
+        if (nF > 0 && sqrt(best) <= max_dist) {
+            double lim = sqrt(best) * (1.0 + ORC_TIE_REL) + tau;
+            for (int64_t f = 0; f < nF; ++f)
+                if (sqrt(dist[f]) <= lim) { pick = (int32_t)f; break; }
+        }
+        face[q] = pick;
+        if (pick < 0) {
+            d2[q] = INFINITY;
+            for (int c = 0; c < 3; ++c) { bary[3 * q + c] = 0.0; point[3 * q + c] = 0.0; }
+        } else {
+            double A[3], B[3], C[3];
+            for (int c = 0; c < 3; ++c) {
+                A[c] = V[3 * (int64_t)F[3 * pick] + c];
+                B[c] = V[3 * (int64_t)F[3 * pick + 1] + c];
+                C[c] = V[3 * (int64_t)F[3 * pick + 2] + c];
+            }
+            d2[q] = orc_point_triangle(p, A, B, C, bary + 3 * q, point + 3 * q);
+        }
+    }
+    free(dist);
+}
+
+/* ------------------------------------------------------------------ */
+/* Morton keys of face centroids (Sec. 3.4 builds the structure from     */
+/* F0; Sec. 4.1 rebuilds it per frame).  The paper defines no key, so    */
+/* the recipe is ours and fixed in float32 round-to-nearest:             */
+/*   s_f   = (v0 + v1) + v2                       (centroid times 3)     */
+/*   lo,hi = componentwise min / max of s_f over all faces               */
+/*   inv   = 1 / (hi - lo)   (0 where hi == lo)                          */
+/*   t     = (s - lo) * inv                                              */
+/*   q     = clamp(floor(t * 1024), 0, 1023)                             */
+/*   key   = bits of qx, qy, qz interleaved, x most significant (30 bits)*/
+/* ------------------------------------------------------------------ */
+static uint32_t interleave3(uint32_t qx, uint32_t qy, uint32_t qz) {
+    uint32_t key = 0;
+    for (int bit = 9; bit >= 0; --bit) {
+        key = (key << 1) | ((qx >> bit) & 1u);
+        key = (key << 1) | ((qy >> bit) & 1u);
+        key = (key << 1) | ((qz >> bit) & 1u);
+    }
+    return key;
+}
+
+void orc_morton(const float *V, const int32_t *F, int64_t nF, uint32_t *keys) {
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    float *s = (float *)malloc(sizeof(float) * 3 * (size_t)(nF > 0 ? nF : 1));
+    for (int64_t f = 0; f < nF; ++f) {
+        const float *a = V + 3 * (int64_t)F[3 * f];
+        const float *b = V + 3 * (int64_t)F[3 * f + 1];
+        const float *c = V + 3 * (int64_t)F[3 * f + 2];
+        for (int k = 0; k < 3; ++k) {
+            volatile float ab = a[k] + b[k];
+            float v = ab + c[k];
+            s[3 * f + k] = v;
+            if (v < lo[k]) lo[k] = v;
+            if (v > hi[k]) hi[k] = v;
+        }
+    }
+    float inv[3];
+    for (int k = 0; k < 3; ++k) {
+        float ext = hi[k] - lo[k];
+        inv[k] = (ext > 0.0f) ? 1.0f / ext : 0.0f;
+    }
+    for (int64_t f = 0; f < nF; ++f) {
+        uint32_t q[3];
+        for (int k = 0; k < 3; ++k) {
+            volatile float d = s[3 * f + k] - lo[k];
+            volatile float t = d * inv[k];
+            float x = floorf(t * 1024.0f);
+            int qi = (int)x;
+            if (qi < 0) qi = 0;
+            if (qi > 1023) qi = 1023;
+            q[k] = (uint32_t)qi;
+        }
+        keys[f] = interleave3(q[0], q[1], q[2]);
+    }
+    free(s);
+}
+
+/* ------------------------------------------------------------------ */
+/* Sort (key, face id) pairs ascending, lexicographically; equal keys    */
+/* therefore keep ascending face id (a stable sort of the keys).         */
+/* ------------------------------------------------------------------ */
+typedef struct { uint32_t key; int32_t id; } kv;
+
+static int kv_cmp(const void *x, const void *y) {
+    const kv *a = (const kv *)x, *b = (const kv *)y;
+    if (a->key != b->key) return a->key < b->key ? -1 : 1;
+    return (a->id > b->id) - (a->id < b->id);
+}
+
+void orc_sort_pairs(const uint32_t *keys, int64_t n, uint32_t *sorted_keys, int32_t *perm) {
+    kv *t = (kv *)malloc(sizeof(kv) * (size_t)(n > 0 ? n : 1));
+    for (int64_t i = 0; i < n; ++i) { t[i].key = keys[i]; t[i].id = (int32_t)i; }
+    qsort(t, (size_t)n, sizeof(kv), kv_cmp);
+    for (int64_t i = 0; i < n; ++i) { sorted_keys[i] = t[i].key; perm[i] = t[i].id; }
+    free(t);
+}
+
+/* ------------------------------------------------------------------ */
+/* Binary radix tree over sorted keys (Karras 2012), built serially      */
+/* top-down.  Keys are augmented with their sorted position, so          */
+/* delta(i, j) = common-prefix length of (key_i, i) and (key_j, j).      */
+/* A node over [first, last] splits after gamma, the last position whose */
+/* augmented key shares more than delta(first, last) leading bits with   */
+/* position first (found by a linear scan).  Node numbering follows      */
+/* Karras: the root is internal node 0; a child range [first, gamma] is  */
+/* internal node gamma, a child range [gamma+1, last] is internal node   */
+/* gamma+1, and a one-element range is leaf gamma / gamma+1.             */
+/* Child encoding: internal c >= 0, leaf j as -(j+1).                    */
+/* parent[] has 2n-1 entries: internal nodes first, then leaves.         */
+/* ------------------------------------------------------------------ */
+static int clz32(uint32_t x) {
+    int n = 0;
+    if (x == 0) return 32;
+    while (!(x & 0x80000000u)) { x <<= 1; ++n; }
+    return n;
+}
+
+static int orc_delta(const uint32_t *k, int64_t i, int64_t j) {
+    if (k[i] != k[j]) return clz32(k[i] ^ k[j]);
+    return 32 + clz32((uint32_t)i ^ (uint32_t)j);
+}
+
+void orc_karras(const uint32_t *k, int64_t n, int32_t *left, int32_t *right, int32_t *parent,
+                int32_t *range_first, int32_t *range_last) {
+    if (n <= 0) return;
+    for (int64_t i = 0; i < 2 * n - 1; ++i) parent[i] = -1;
+    if (n == 1) return;
+    int64_t *stk = (int64_t *)malloc(sizeof(int64_t) * 3 * (size_t)n);
+    int64_t sp = 0;
+    stk[sp++] = 0; stk[sp++] = 0; stk[sp++] = n - 1;
+    while (sp > 0) {
+        int64_t last = stk[--sp], first = stk[--sp], node = stk[--sp];
+        range_first[node] = (int32_t)first;
+        range_last[node] = (int32_t)last;
+        int dn = orc_delta(k, first, last);
+        int64_t gamma = first;
+        for (int64_t j = first; j < last; ++j)
+            if (orc_delta(k, first, j) > dn) gamma = j;
+        if (gamma == first) {
+            left[node] = -(int32_t)(gamma + 1);
+            parent[(n - 1) + gamma] = (int32_t)node;
+        } else {
+            left[node] = (int32_t)gamma;
+            parent[gamma] = (int32_t)node;
+            stk[sp++] = gamma; stk[sp++] = first; stk[sp++] = gamma;
+        }
+        if (gamma + 1 == last) {
+            right[node] = -(int32_t)(gamma + 2);
+            parent[(n - 1) + gamma + 1] = (int32_t)node;
+        } else {
+            right[node] = (int32_t)(gamma + 1);
+            parent[gamma + 1] = (int32_t)node;
+            stk[sp++] = gamma + 1; stk[sp++] = gamma + 1; stk[sp++] = last;
+        }
+    }
+    free(stk);
+}
+
+/* ------------------------------------------------------------------ */
+/* Node bounding boxes: for every node, the componentwise min / max of  */
+/* the vertices of all faces in its sorted range, taken directly over   */
+/* the range (not as a union of child boxes).  Exact in float32.        */
+/* boxes: [2n-1][6] = (lo.xyz, hi.xyz), internal nodes then leaves.     */
+/* A refit is the same function called with the new vertex buffer.      */
+/* ------------------------------------------------------------------ */
+static void range_box(const float *V, const int32_t *F, const int32_t *perm,
+                      int64_t first, int64_t last, float *out) {
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t j = first; j <= last; ++j) {
+        int64_t f = perm[j];
+        for (int k = 0; k < 3; ++k) {
+            const float *v = V + 3 * (int64_t)F[3 * f + k];
+            for (int c = 0; c < 3; ++c) {
+                if (v[c] < lo[c]) lo[c] = v[c];
+                if (v[c] > hi[c]) hi[c] = v[c];
+            }
+        }
+    }
+    for (int c = 0; c < 3; ++c) { out[c] = lo[c]; out[3 + c] = hi[c]; }
+}
+
+void orc_node_boxes(const float *V, const int32_t *F, const int32_t *perm, int64_t n,
+                    const int32_t *range_first, const int32_t *range_last, float *boxes) {
+    for (int64_t i = 0; i + 1 < n; ++i)
+        range_box(V, F, perm, range_first[i], range_last[i], boxes + 6 * i);
+    for (int64_t j = 0; j < n; ++j)
+        range_box(V, F, perm, j, j, boxes + 6 * (n - 1 + j));
+}
+
+/* ------------------------------------------------------------------ */
+/* Gaussian binding to a face frame (reading; the paper says only that  */
+/* Gaussians are anchored to mesh faces, Sec. 2 and Sec. 3.1).          */
+/* For face (v0, v1, v2), barycentric anchor b and normal offset delta: */
+/*   e1 = (v1 - v0)/|v1 - v0|,  n = (v1-v0) x (v2-v0) / |...|,  e2 = n x e1 */
+/*   R  = [e1 e2 n] (columns),  mu = sum_j b_j v_j + delta n            */
+/*   q  = unit quaternion (w, x, y, z) of R, Shepperd's largest-pivot    */
+/*        branch, sign fixed so w > 0 (w == 0: first nonzero of x,y,z > 0) */
+/*   l  = |v1 - v0|, h = |(v1-v0) x (v2-v0)| / l (altitude onto v0v1)    */
+/*   s  = (l/3, h/3, 0.01 (l + h)/6)                                     */
+/* A face with l == 0 or zero area is degenerate: mu from b alone,      */
+/* q = (1, 0, 0, 0), s = 0, flag 1.                                      */
+/* ------------------------------------------------------------------ */
+#define ORC_RHO (1.0 / 3.0)
+#define ORC_EPS_S 1e-2
+
+static void orc_quat_from_R(const double R[3][3], double q[4]) {
+    double tr = R[0][0] + R[1][1] + R[2][2];
+    double w, x, y, z;
+    int br;
+    if (tr >= R[0][0] && tr >= R[1][1] && tr >= R[2][2]) br = 0;
+    else if (R[0][0] >= R[1][1] && R[0][0] >= R[2][2]) br = 1;
+    else if (R[1][1] >= R[2][2]) br = 2;
+    else br = 3;
+    if (br == 0) {
+        w = 0.5 * sqrt(1.0 + tr);
+        double f = 0.25 / w;
+        x = (R[2][1] - R[1][2]) * f; y = (R[0][2] - R[2][0]) * f; z = (R[1][0] - R[0][1]) * f;
+    } else if (br == 1) {
+        x = 0.5 * sqrt(1.0 + R[0][0] - R[1][1] - R[2][2]);
+        double f = 0.25 / x;
+        w = (R[2][1] - R[1][2]) * f; y = (R[0][1] + R[1][0]) * f; z = (R[0][2] + R[2][0]) * f;
+    } else if (br == 2) {
+        y = 0.5 * sqrt(1.0 - R[0][0] + R[1][1] - R[2][2]);
+        double f = 0.25 / y;
+        w = (R[0][2] - R[2][0]) * f; x = (R[0][1] + R[1][0]) * f; z = (R[1][2] + R[2][1]) * f;
+    } else {
+        z = 0.5 * sqrt(1.0 - R[0][0] - R[1][1] + R[2][2]);
+        double f = 0.25 / z;
+        w = (R[1][0] - R[0][1]) * f; x = (R[0][2] + R[2][0]) * f; y = (R[1][2] + R[2][1]) * f;
+    }
+    int neg = 0;
+    if (w < 0.0) neg = 1;
+    else if (w == 0.0) {
+        if (x != 0.0) neg = x < 0.0;
+        else if (y != 0.0) neg = y < 0.0;
+        else neg = z < 0.0;
+    }
+    double sg = neg ? -1.0 : 1.0;
+    q[0] = sg * w; q[1] = sg * x; q[2] = sg * y; q[3] = sg * z;
+}
+
+int64_t orc_bind_gaussians(const double *V, const int32_t *F, const int32_t *gface,
+                           const double *gbary, const double *goff /* nullable */, int64_t nG,
+                           double *mu, double *quat, double *scale, int32_t *flags) {
+    int64_t ndeg = 0;
+    for (int64_t g = 0; g < nG; ++g) {
+        int64_t f = gface[g];
+        d3 v0 = ld3(V + 3 * (int64_t)F[3 * f]);
+        d3 v1 = ld3(V + 3 * (int64_t)F[3 * f + 1]);
+        d3 v2 = ld3(V + 3 * (int64_t)F[3 * f + 2]);
+        double b0 = gbary[3 * g], b1 = gbary[3 * g + 1], b2 = gbary[3 * g + 2];
+        double off = goff ? goff[g] : 0.0;
+        d3 m = add(add(scl(v0, b0), scl(v1, b1)), scl(v2, b2));
+        d3 e = sub(v1, v0);
+        d3 nu = cross(e, sub(v2, v0));
+        double l = norm(e), an = norm(nu);
+        if (l == 0.0 || an == 0.0) {
+            ++ndeg;
+            flags[g] = 1;
+            mu[3 * g] = m.x; mu[3 * g + 1] = m.y; mu[3 * g + 2] = m.z;
+            quat[4 * g] = 1.0; quat[4 * g + 1] = quat[4 * g + 2] = quat[4 * g + 3] = 0.0;
+            scale[3 * g] = scale[3 * g + 1] = scale[3 * g + 2] = 0.0;
+            continue;
+        }
+        flags[g] = 0;
+        d3 e1 = scl(e, 1.0 / l);
+        d3 n = scl(nu, 1.0 / an);
+        d3 e2 = cross(n, e1);
+        double R[3][3] = {{e1.x, e2.x, n.x}, {e1.y, e2.y, n.y}, {e1.z, e2.z, n.z}};
+        m = add(m, scl(n, off));
+        mu[3 * g] = m.x; mu[3 * g + 1] = m.y; mu[3 * g + 2] = m.z;
+        orc_quat_from_R(R, quat + 4 * g);
+        double h = an / l;
+        scale[3 * g] = ORC_RHO * l;
+        scale[3 * g + 1] = ORC_RHO * h;
+        scale[3 * g + 2] = ORC_EPS_S * ORC_RHO * (l + h) * 0.5;
+    }
+    return ndeg;
+}
+
+/* ------------------------------------------------------------------ */
+/* Chamfer distance between two meshes on surface samples (Sec. 4.2):   */
+/*   out[0] = mean over a in SA of d(a, mesh B)^2                       */
+/*   out[1] = mean over b in SB of d(b, mesh A)^2                       */
+/* (the symmetric CD is out[0] + out[1]).  Sums in float64, in order.   */
+/* ------------------------------------------------------------------ */
+void orc_chamfer(const double *VA, const int32_t *FA, int64_t nFA, const double *SA, int64_t nSA,
+                 const double *VB, const int32_t *FB, int64_t nFB, const double *SB, int64_t nSB,
+                 double *out, double *dA, double *dB) {
+    int32_t *fc = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nSA > nSB ? nSA : nSB) + 4);
+    double *bb = (double *)malloc(sizeof(double) * 3 * (size_t)(nSA > nSB ? nSA : nSB) + 32);
+    double *pp = (double *)malloc(sizeof(double) * 3 * (size_t)(nSA > nSB ? nSA : nSB) + 32);
+    orc_closest_point_mesh(VB, FB, nFB, SA, nSA, INFINITY, fc, bb, pp, dA, NULL);
+    orc_closest_point_mesh(VA, FA, nFA, SB, nSB, INFINITY, fc, bb, pp, dB, NULL);
+    double s0 = 0.0, s1 = 0.0;
+    for (int64_t i = 0; i < nSA; ++i) s0 += dA[i];
+    for (int64_t i = 0; i < nSB; ++i) s1 += dB[i];
+    out[0] = nSA > 0 ? s0 / (double)nSA : 0.0;
+    out[1] = nSB > 0 ? s1 / (double)nSB : 0.0;
+    free(fc); free(bb); free(pp);
+}
+
+/* ------------------------------------------------------------------ */
+/* Gradients (extension of the method: differentiating the update).    */
+/* Point-to-mesh, with the nearest face and its barycentrics held fixed */
+/* (envelope theorem; valid away from region boundaries and ties):      */
+/*   d(d^2)/dq   =  2 (q - c)                                           */
+/*   d(d^2)/dv_j = -2 b_j (q - c)   for the nearest face's vertex j      */
+/* g is dL/d(d^2) per query; gQ [nQ,3], gV [nV,3] are accumulated into. */
+/* ------------------------------------------------------------------ */
+void orc_closest_point_backward(const double *V, const int32_t *F, const double *Q, int64_t nQ,
+                                const int32_t *face, const double *bary, const double *g,
+                                double *gQ, double *gV) {
+    for (int64_t q = 0; q < nQ; ++q) {
+        int64_t f = face[q];
+        if (f < 0) continue;
+        d3 p = ld3(Q + 3 * q);
+        d3 c = mk(0, 0, 0);
+        for (int j = 0; j < 3; ++j)
+            c = add(c, scl(ld3(V + 3 * (int64_t)F[3 * f + j]), bary[3 * q + j]));
+        d3 r = scl(sub(p, c), 2.0 * g[q]);
+        gQ[3 * q] += r.x; gQ[3 * q + 1] += r.y; gQ[3 * q + 2] += r.z;
+        for (int j = 0; j < 3; ++j) {
+            int64_t v = F[3 * f + j];
+            double bj = bary[3 * q + j];
+            gV[3 * v] -= bj * r.x; gV[3 * v + 1] -= bj * r.y; gV[3 * v + 2] -= bj * r.z;
+        }
+    }
+}
+
+/* Samples placed by barycentric weights on a mesh: p = sum_j b_j v_j.  */
+void orc_interpolate(const double *V, const int32_t *F, const int32_t *face, const double *bary,
+                     int64_t n, double *out) {
+    for (int64_t i = 0; i < n; ++i) {
+        d3 c = mk(0, 0, 0);
+        for (int j = 0; j < 3; ++j)
+            c = add(c, scl(ld3(V + 3 * (int64_t)F[3 * face[i] + j]), bary[3 * i + j]));
+        out[3 * i] = c.x; out[3 * i + 1] = c.y; out[3 * i + 2] = c.z;
+    }
+}
+
+/* d p / d v_j = b_j I: scatter dL/dp into dL/dV. */
+void orc_interpolate_backward(const int32_t *F, const int32_t *face, const double *bary,
+                              int64_t n, const double *gP, double *gV) {
+    for (int64_t i = 0; i < n; ++i)
+        for (int j = 0; j < 3; ++j) {
+            int64_t v = F[3 * face[i] + j];
+            double bj = bary[3 * i + j];
+            for (int c = 0; c < 3; ++c) gV[3 * v + c] += bj * gP[3 * i + c];
+        }
+}
+
+/* ------------------------------------------------------------------ */
+/* Reverse-mode derivative of orc_bind_gaussians with respect to the    */
+/* vertex positions.  Inputs dL/dmu [G,3], dL/dq [G,4], dL/ds [G,3];    */
+/* dL/dV [V,3] is accumulated into.  Each step of the forward formula   */
+/* is undone in reverse order; the quaternion step uses the same        */
+/* Shepperd branch and sign the forward pass took.  Degenerate faces    */
+/* contribute only through mu = sum_j b_j v_j.                          */
+/* ------------------------------------------------------------------ */
+static d3 vjp_normalize(d3 x, double len, d3 g) {
+    /* y = x/len, len = |x|: dL/dx = (g - y (y . g)) / len */
+    d3 y = scl(x, 1.0 / len);
+    return scl(sub(g, scl(y, dot(y, g))), 1.0 / len);
+}
+
+void orc_bind_gaussians_backward(const double *V, const int32_t *F, const int32_t *gface,
+                                 const double *gbary, const double *goff, int64_t nG,
+                                 const double *gmu, const double *gq, const double *gs,
+                                 double *gV) {
+    for (int64_t g = 0; g < nG; ++g) {
+        int64_t f = gface[g];
+        int64_t iv[3] = {F[3 * f], F[3 * f + 1], F[3 * f + 2]};
+        d3 v0 = ld3(V + 3 * iv[0]), v1 = ld3(V + 3 * iv[1]), v2 = ld3(V + 3 * iv[2]);
+        double b[3] = {gbary[3 * g], gbary[3 * g + 1], gbary[3 * g + 2]};
+        double off = goff ? goff[g] : 0.0;
+        d3 Gmu = mk(gmu[3 * g], gmu[3 * g + 1], gmu[3 * g + 2]);
+        d3 gv[3];
+        for (int j = 0; j < 3; ++j) gv[j] = scl(Gmu, b[j]);
+        d3 e = sub(v1, v0), e2v = sub(v2, v0);
+        d3 nu = cross(e, e2v);
+        double l = norm(e), an = norm(nu);
+        if (!(l == 0.0 || an == 0.0)) {
+            d3 e1 = scl(e, 1.0 / l), n = scl(nu, 1.0 / an), e2 = cross(n, e1);
+            double R[3][3] = {{e1.x, e2.x, n.x}, {e1.y, e2.y, n.y}, {e1.z, e2.z, n.z}};
+            /* quaternion -> dL/dR through the branch the forward pass used */
+            double q[4];
+            double tr = R[0][0] + R[1][1] + R[2][2];
+            int br;
+            if (tr >= R[0][0] && tr >= R[1][1] && tr >= R[2][2]) br = 0;
+            else if (R[0][0] >= R[1][1] && R[0][0] >= R[2][2]) br = 1;
+            else if (R[1][1] >= R[2][2]) br = 2;
+            else br = 3;
+            orc_quat_from_R(R, q);
+            /* the forward output is sg * (w, x, y, z) of the branch; recover sg */
+            double raw[4];
+            double Gq[4] = {gq[4 * g], gq[4 * g + 1], gq[4 * g + 2], gq[4 * g + 3]};
+            double dR[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+            {
+                double p, fct;
+                /* raw branch values */
+                if (br == 0) {
+                    p = 0.5 * sqrt(1.0 + tr); fct = 0.25 / p;
+                    raw[0] = p; raw[1] = (R[2][1] - R[1][2]) * fct;
+                    raw[2] = (R[0][2] - R[2][0]) * fct; raw[3] = (R[1][0] - R[0][1]) * fct;
+                } else if (br == 1) {
+                    p = 0.5 * sqrt(1.0 + R[0][0] - R[1][1] - R[2][2]); fct = 0.25 / p;
+                    raw[1] = p; raw[0] = (R[2][1] - R[1][2]) * fct;
+                    raw[2] = (R[0][1] + R[1][0]) * fct; raw[3] = (R[0][2] + R[2][0]) * fct;
+                } else if (br == 2) {
+                    p = 0.5 * sqrt(1.0 - R[0][0] + R[1][1] - R[2][2]); fct = 0.25 / p;
+                    raw[2] = p; raw[0] = (R[0][2] - R[2][0]) * fct;
+                    raw[1] = (R[0][1] + R[1][0]) * fct; raw[3] = (R[1][2] + R[2][1]) * fct;
+                } else {
+                    p = 0.5 * sqrt(1.0 - R[0][0] - R[1][1] + R[2][2]); fct = 0.25 / p;
+                    raw[3] = p; raw[0] = (R[1][0] - R[0][1]) * fct;
+                    raw[1] = (R[0][2] + R[2][0]) * fct; raw[2] = (R[1][2] + R[2][1]) * fct;
+                }
+                double sg = 1.0;
+                for (int k = 0; k < 4; ++k)
+                    if (raw[k] != 0.0) { sg = (q[k] == raw[k]) ? 1.0 : -1.0; break; }
+                double G[4];
+                for (int k = 0; k < 4; ++k) G[k] = sg * Gq[k];
+                /* pivot index of the branch in (w, x, y, z) order, and the
+                   3 off-diagonal combinations for the other components */
+                int piv = br;               /* 0:w 1:x 2:y 3:z */
+                /* off[k] = linear combination of R entries that equals 4 p raw[k] */
+                /* d raw[k] = d(off_k)/(4p) - off_k/(4p^2) dp ;  p = 0.5 sqrt(S), dp = dS/(8p) */
+                double Gp = G[piv];
+                /* contributions of the three non-pivot components */
+                for (int k = 0; k < 4; ++k) {
+                    if (k == piv) continue;
+                    double gk = G[k];
+                    double off_k = raw[k] * 4.0 * p;
+                    /* d raw_k / d off_k = 1/(4p); d raw_k / d p = -off_k / (4 p^2) */
+                    double coef = gk / (4.0 * p);
+                    Gp += -gk * off_k / (4.0 * p * p);
+                    int a = piv, bb = k;
+                    if (a > bb) { int t = a; a = bb; bb = t; }
+                    /* pairs: (w,x): R21-R12  (w,y): R02-R20  (w,z): R10-R01
+                              (x,y): R01+R10  (x,z): R02+R20  (y,z): R12+R21 */
+                    if (a == 0 && bb == 1) { dR[2][1] += coef; dR[1][2] -= coef; }
+                    else if (a == 0 && bb == 2) { dR[0][2] += coef; dR[2][0] -= coef; }
+                    else if (a == 0 && bb == 3) { dR[1][0] += coef; dR[0][1] -= coef; }
+                    else if (a == 1 && bb == 2) { dR[0][1] += coef; dR[1][0] += coef; }
+                    else if (a == 1 && bb == 3) { dR[0][2] += coef; dR[2][0] += coef; }
+                    else { dR[1][2] += coef; dR[2][1] += coef; }
+                }
+                /* p = 0.5 sqrt(S): dp/dS = 1/(8p); S = 1 + s0 R00 + s1 R11 + s2 R22 */
+                double gS = Gp / (8.0 * p);
+                double sgn[4][3] = {{1, 1, 1}, {1, -1, -1}, {-1, 1, -1}, {-1, -1, 1}};
+                for (int d = 0; d < 3; ++d) dR[d][d] += gS * sgn[br][d];
+            }
+            /* R columns: e1, e2, n */
+            d3 ge1 = mk(dR[0][0], dR[1][0], dR[2][0]);
+            d3 ge2 = mk(dR[0][1], dR[1][1], dR[2][1]);
+            d3 gn = mk(dR[0][2], dR[1][2], dR[2][2]);
+            gn = add(gn, scl(Gmu, off));
+            /* scale: s0 = rho l, s1 = rho h, s2 = eps rho (l + h)/2, h = an / l */
+            double gl = ORC_RHO * gs[3 * g] + ORC_EPS_S * ORC_RHO * 0.5 * gs[3 * g + 2];
+            double gh = ORC_RHO * gs[3 * g + 1] + ORC_EPS_S * ORC_RHO * 0.5 * gs[3 * g + 2];
+            gl += gh * (-an / (l * l));
+            double gan = gh / l;
+            /* e2 = n x e1 */
+            gn = add(gn, cross(e1, ge2));          /* d(n x e1)/dn^T g = e1 x g */
+            ge1 = add(ge1, cross(ge2, n));         /* d(n x e1)/de1^T g = g x n */
+            /* n = nu / an, an = |nu| */
+            d3 gnu = add(vjp_normalize(nu, an, gn), scl(nu, gan / an));
+            /* e1 = e / l, l = |e| */
+            d3 ge = add(vjp_normalize(e, l, ge1), scl(e, gl / l));
+            /* nu = e x f, f = v2 - v0 */
+            ge = add(ge, cross(e2v, gnu));         /* d(e x f)/de^T g = f x g */
+            d3 gf = cross(gnu, e);                 /* d(e x f)/df^T g = g x e */
+            gv[1] = add(gv[1], ge);
+            gv[2] = add(gv[2], gf);
+            gv[0] = sub(gv[0], add(ge, gf));
+        }
+        for (int j = 0; j < 3; ++j) {
+            gV[3 * iv[j]] += gv[j].x; gV[3 * iv[j] + 1] += gv[j].y; gV[3 * iv[j] + 2] += gv[j].z;
+        }
+    }
+}

@@ -1,0 +1,416 @@
+#!/usr/bin/env python
+"""Per-frame dynamic-mesh update benchmark (fixed-topology physics path).
+
+Workload (synthetic, seeded): a 400 x 250 grid torus (R = 1.0, r = 0.35;
+100k vertices / 200k faces) deformed every frame by 4-bone linear-blend
+skinning (rotations <= 30 deg); 1M particles uniform in the rest-pose box
+grown by 0.2 run contact queries with cutoff 0.05; 600k Gaussians (3 per face
+at seeded barycentres).  One step = one frame:
+
+  a1+a5  refit:    vertex-buffer update from frame k, BVH refit (fixed topology)
+  a6     contact:  1M closest-point queries with cutoff 0.05
+  a7     rebind:   600k face-bound Gaussians (centre, rotation, scale)
+  a2-a5  rebuild:  full LBVH build of the same frame (the varying-topology path)
+  a8     chamfer:  Chamfer distance, 10k samples on the deformed mesh vs 10k on
+                   the rest pose (the paper's CD sample count)
+
+value = point-to-mesh queries per second (1M contact + 20k Chamfer queries per
+frame) over graph-replayed frames, inputs resident in HBM, L2 flushed (a 512 MB
+write) between frames outside the timed events.  Stage times, the dominant
+kernel's roofline and the refit-vs-rebuild comparison come from an eager pass
+with events between stages.  `e2e` repeats the frame through the public API
+from pinned host buffers (frame vertices and particles in, contact face and
+distance out).  `--impl reference` times the CPU oracle on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from workloads.meshes import torus, TorusSkinning  # noqa: E402
+from workloads.sampling import osada_barycentrics, points_from, sample_surface, uniform_box  # noqa: E402
+
+METRIC = "point-to-mesh queries/s; ms/frame update (refit vs LBVH rebuild); % of roofline"
+WORKLOAD = "fixed-topology physics frame: torus 100k V / 200k F, 4-bone LBS, 1M particles " \
+           "(cutoff 0.05), 600k Gaussians, refit vs LBVH rebuild, 10k+10k-sample Chamfer"
+NU, NV_, CUTOFF, N_PART, G_PER_FACE, N_CD = 400, 250, 0.05, 1 << 20, 3, 10000
+SEED = 3000
+CONTACT_BYTES = 12 + 4 + 12 + 12 + 4      # query xyz in; face, bary, point, dist2 out
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="meshgs", choices=["meshgs", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+class Workload:
+    """Host-side inputs (generated once, seeded)."""
+
+    def __init__(self, n_frames: int):
+        self.V0, self.F = torus(NU, NV_)
+        self.skin = TorusSkinning(self.V0, seed=SEED)
+        self.frames = [self.skin.frame(t) for t in range(n_frames)]
+        lo, hi = self.V0.min(0) - 0.2, self.V0.max(0) + 0.2
+        self.P = uniform_box(N_PART, lo, hi, seed=SEED + 2)
+        rng = np.random.default_rng(SEED + 3)
+        self.gface = np.repeat(np.arange(self.F.shape[0], dtype=np.int32), G_PER_FACE)
+        self.gbary = osada_barycentrics(rng, self.gface.shape[0]).astype(np.float32)
+        self.cd_face, self.cd_bary = sample_surface(self.V0, self.F, N_CD, seed=SEED + 4)
+        rf, rb = sample_surface(self.V0, self.F, N_CD, seed=SEED + 5)
+        self.rest_samples = points_from(self.V0, self.F, rf, rb)
+
+    @property
+    def queries_per_frame(self):
+        return N_PART + 2 * N_CD
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        rows = []
+        for line in out.strip().splitlines():
+            p = [x.strip() for x in line.split(",")]
+            if len(p) == 6 and p[0].isdigit():
+                rows.append(p)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [int(r[0]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[2 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": int(rows[0][1]),
+                "samples": len(rows), "reasons": reasons}
+
+
+def gpu_arm(args, rank, world, local_rank):
+    import torch
+    from paper_2606_00444_gb300 import MeshBVH, Workspace, chamfer, launch_count
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    nfr = max(args.warmup + args.steps, 2)
+    W = Workload(min(nfr, 64))
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    frames = torch.stack([t(f) for f in W.frames])           # resident in HBM
+    F = t(W.F)
+    P = t(W.P)
+    gface, gbary = t(W.gface), t(W.gbary)
+    cdf, cdb = t(W.cd_face), t(W.cd_bary)
+    rest_S = t(W.rest_samples)
+    nV, nF = W.V0.shape[0], W.F.shape[0]
+
+    fixed = MeshBVH(nV, nF, dev).build(t(W.V0), F)
+    rebuilt = MeshBVH(nV, nF, dev)
+    rest = MeshBVH(nV, nF, dev).build(t(W.V0), F)
+    Vin = torch.empty(nV, 3, device=dev)
+    contact = dict(face=torch.empty(N_PART, dtype=torch.int32, device=dev),
+                   bary=torch.empty(N_PART, 3, device=dev), point=torch.empty(N_PART, 3, device=dev),
+                   dist2=torch.empty(N_PART, device=dev))
+    gout = (torch.empty(gface.shape[0], 3, device=dev), torch.empty(gface.shape[0], 4, device=dev),
+            torch.empty(gface.shape[0], 3, device=dev))
+    S_def = torch.empty(N_CD, 3, device=dev)
+    cd_out = torch.empty(2, dtype=torch.float64, device=dev)
+    cd_ws = Workspace(dev)
+    flush = torch.empty(128 << 20, dtype=torch.float32, device=dev)   # 512 MB > L2
+
+    def stages(ev=None):
+        def mark(i):
+            if ev is not None:
+                ev[i].record()
+        mark(0)
+        fixed.refit(Vin)                                         # a1 + a5
+        mark(1)
+        fixed.closest_point(P, CUTOFF, out=contact)              # a6
+        mark(2)
+        fixed.bind_gaussians(gface, gbary, out=gout)             # a7
+        mark(3)
+        rebuilt.build(Vin, F)                                    # a1 + a2..a5
+        mark(4)
+        fixed.interpolate(cdf, cdb, out=S_def)                   # a8
+        chamfer(fixed, S_def, rest, rest_S, ws=cd_ws, out=cd_out)
+        mark(5)
+
+    def load_frame(k):
+        Vin.copy_(frames[k % frames.shape[0]], non_blocking=True)
+
+    # eager warm-up, and launches per frame
+    for k in range(max(args.warmup, 3)):
+        load_frame(k)
+        stages()
+    torch.cuda.synchronize()
+    n0 = launch_count()
+    stages()
+    torch.cuda.synchronize()
+    launches_per_frame = launch_count() - n0
+    bits, _ = fixed.status()
+    if bits & ~0x4:
+        raise RuntimeError(f"device status bits {bits:#x} after warm-up")
+
+    # capture one frame as a CUDA graph (static buffers)
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream(device=dev)
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        stages()
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g):
+        stages()
+    torch.cuda.synchronize()
+
+    def timed_graph(nsteps, warm):
+        for k in range(warm):
+            load_frame(k)
+            g.replay()
+        times = []
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(nsteps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(nsteps)]
+        for k in range(nsteps):
+            flush.fill_(float(k))
+            starts[k].record()
+            load_frame(warm + k)
+            g.replay()
+            ends[k].record()
+        torch.cuda.synchronize()
+        for k in range(nsteps):
+            times.append(starts[k].elapsed_time(ends[k]))
+        return times
+
+    import torch.distributed as dist
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local_rank)
+    time.sleep(0.3)
+    t0 = time.perf_counter()
+    step_ms = timed_graph(args.steps, args.warmup)
+    wall = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ck = clocks.stop()
+    ms = float(np.mean(step_ms))
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+
+    # eager pass with per-stage events (stage breakdown + dominant kernel duration)
+    nst = min(args.steps, 100)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(nst)]
+    for k in range(nst):
+        flush.fill_(float(k))
+        load_frame(k)
+        stages(evs[k])
+    torch.cuda.synchronize()
+    names = ["refit", "contact", "rebind", "rebuild", "chamfer"]
+    st = {n: float(np.mean([e[i].elapsed_time(e[i + 1]) for e in evs])) for i, n in enumerate(names)}
+
+    # end to end through the public API from pinned host buffers
+    e2e_steps = min(args.steps, 50)
+    hV = [torch.from_numpy(np.ascontiguousarray(W.frames[k % len(W.frames)])).pin_memory()
+          for k in range(min(e2e_steps, len(W.frames)))]
+    hP = torch.from_numpy(W.P).pin_memory()
+    h_face = torch.empty(N_PART, dtype=torch.int32).pin_memory()
+    h_d2 = torch.empty(N_PART).pin_memory()
+    h_cd = torch.empty(2, dtype=torch.float64).pin_memory()
+    e_ms = []
+    for k in range(e2e_steps + 3):
+        flush.fill_(1.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        Vin.copy_(hV[k % len(hV)], non_blocking=True)
+        P.copy_(hP, non_blocking=True)
+        g.replay()
+        h_face.copy_(contact["face"], non_blocking=True)
+        h_d2.copy_(contact["dist2"], non_blocking=True)
+        h_cd.copy_(cd_out, non_blocking=True)
+        b.record()
+        b.synchronize()
+        if k >= 3:
+            e_ms.append(a.elapsed_time(b))
+    h2d = nV * 12 + N_PART * 12
+    d2h = N_PART * 8 + 16
+
+    out = dict(ms=ms, wall=wall, step_ms=step_ms, stages=st, clocks=ck, e2e_ms=float(np.mean(e_ms)),
+               h2d=h2d, d2h=d2h, launches=launches_per_frame * args.steps,
+               contact_hits=int((contact["face"] >= 0).sum().item()),
+               chamfer=[float(x) for x in cd_out.cpu()])
+    return out, W
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs"), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (the reported baseline and the reference arm)
+# ---------------------------------------------------------------------------
+def oracle_frame_sample(W, frame, nq, ng, ncd, rng):
+    """Time the oracle on one frame: full serial LBVH build, nq contact queries,
+    ng Gaussians, ncd Chamfer samples per side; returns the extrapolated time of
+    a full frame (1M queries, 600k Gaussians, 10k + 10k Chamfer samples)."""
+    import oracle
+    V = W.frames[frame % len(W.frames)]
+    t0 = time.perf_counter()
+    oracle.build_lbvh(V, W.F)
+    t1 = time.perf_counter()
+    qi = rng.choice(N_PART, nq, replace=False)
+    oracle.closest_point(V, W.F, W.P[qi], CUTOFF)
+    t2 = time.perf_counter()
+    gi = rng.choice(W.gface.shape[0], ng, replace=False)
+    oracle.bind_gaussians(V, W.F, W.gface[gi], W.gbary[gi])
+    t3 = time.perf_counter()
+    ci = rng.choice(N_CD, ncd, replace=False)
+    SA = oracle.interpolate(V.astype(np.float64), W.F, W.cd_face[ci], W.cd_bary[ci])
+    oracle.chamfer(V, W.F, SA, W.V0, W.F, W.rest_samples[ci])
+    t4 = time.perf_counter()
+    full = ((t1 - t0) + (t2 - t1) * N_PART / nq + (t3 - t2) * W.gface.shape[0] / ng
+            + (t4 - t3) * N_CD / ncd)
+    return full, t4 - t0
+
+
+def cpu_baseline(W, budget_s=20.0):
+    rng = np.random.default_rng(7)
+    nq = 4096
+    full, spent = oracle_frame_sample(W, 1, nq, 60000, 256, rng)
+    return {"value": W.queries_per_frame / full, "unit": "queries/s", "cores": 1, "kind": "oracle",
+            "sample": f"one frame: full serial LBVH build of 200k faces, {nq} of 1M contact "
+                      f"queries (brute force), 60000 of 600k Gaussians, 256 of 10k Chamfer "
+                      f"samples per side; extrapolated linearly to the full frame "
+                      f"({spent:.1f} s of CPU work, single thread)"}
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    W = Workload(4)
+    total = args.steps + args.warmup
+    budget = 150.0 / max(total, 1)                     # seconds per step, whole run ~ minutes
+    nq = int(max(16, min(4096, (budget - 0.35) * 250)))
+    rng = np.random.default_rng(11)
+    for _ in range(args.warmup):
+        oracle_frame_sample(W, 0, nq, 4096, 16, rng)
+    fulls = []
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        full, _ = oracle_frame_sample(W, k, nq, 4096, 16, rng)
+        fulls.append(full)
+    spent = time.perf_counter() - t0
+    val = W.queries_per_frame / float(np.mean(fulls))
+    line = {"metric": METRIC, "value": val, "unit": "queries/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(fulls)) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "frames": args.steps},
+            "cpu_baseline": {"value": val, "unit": "queries/s", "cores": 1, "kind": "oracle",
+                             "sample": f"per step: full serial LBVH build, {nq} contact queries, "
+                                       f"4096 Gaussians, 16 Chamfer samples per side, "
+                                       f"extrapolated to the full frame ({spent:.1f} s total)"},
+            "e2e": {"value": val, "unit": "queries/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return reference_arm(args, rank, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    res, W = gpu_arm(args, rank, world, local_rank)
+    if rank != 0:
+        return
+    q = W.queries_per_frame
+    ms = res["ms"]
+    hbm, src = peaks()
+    t_contact = res["stages"]["contact"] * 1e-3
+    achieved = CONTACT_BYTES * N_PART / t_contact / 1e9
+    st = res["stages"]
+    line = {
+        "metric": METRIC,
+        "value": world * q / (ms * 1e-3),
+        "unit": "queries/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "queries_per_frame": q, "faces": NU * NV_ * 2,
+                   "gaussians": NU * NV_ * 2 * G_PER_FACE, "parallelism": f"replicas{world}",
+                   "l2": "flushed between frames (512 MB write, outside the timed events)",
+                   "graph": "one CUDA graph per frame"},
+        "stages_ms": st,
+        "ms_per_frame": {"refit_path": st["refit"] + st["contact"] + st["rebind"],
+                         "rebuild_path": st["rebuild"] + st["contact"] + st["rebind"],
+                         "refit": st["refit"], "rebuild": st["rebuild"]},
+        "roofline": {"kernel": "k_closest_point (contact, 1M queries)", "bound": "hbm",
+                     "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "peak_source": src, "traffic": None,
+                     "bytes_per_query": CONTACT_BYTES},
+        "clocks": res["clocks"],
+        "e2e": {"value": world * q / (res["e2e_ms"] * 1e-3), "unit": "queries/s",
+                "h2d_bytes_per_step": res["h2d"], "d2h_bytes_per_step": res["d2h"]},
+        "gpu_launches": res["launches"],
+        "contact_hits_per_frame": res["contact_hits"],
+    }
+    if not args.no_cpu_baseline and world == 1:
+        import oracle
+        oracle.build()
+        line["cpu_baseline"] = cpu_baseline(W)
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

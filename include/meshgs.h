@@ -1,0 +1,213 @@
+/*
+ * meshgs -- per-frame dynamic-mesh update on the GPU, C ABI.
+ *
+ * Ramlal & Zelek, "Real-Time Physics Simulation with Dynamic Mesh-Gaussian
+ * Reconstructions" (CVIS 2026) keep a fixed-topology physics mesh and a set of
+ * mesh-bound Gaussians in sync (Sec. 3.2).  Every frame the vertex buffer is
+ * replaced (Sec. 3.4, Per-Frame Update), collision queries run against it
+ * (Sec. 3.4, step 3), and the Gaussians follow their faces.  The
+ * varying-topology baseline instead rebuilds the collision structure each
+ * frame (Sec. 4.1).  This library provides those steps as CUDA kernels:
+ *
+ *   mesh_build_lbvh       full BVH build (Morton keys, radix sort, Karras
+ *                         hierarchy, bottom-up boxes) -- the rebuild of Sec. 4.1
+ *   mesh_update_vertices  the O(N_v) vertex-buffer update of Sec. 3.4
+ *   mesh_refit            boxes recomputed over the fixed topology
+ *   mesh_closest_point    NearestSurface of Eq. 1 / Eq. 2 (exact closest point,
+ *                         barycentric weights, optional contact cutoff)
+ *   mesh_bind_gaussians   face-bound Gaussian centre / rotation / scale
+ *   mesh_chamfer          point-to-mesh Chamfer distance of Sec. 4.2
+ *   *_backward            gradients with respect to vertices and query points
+ *
+ * Conventions (all entry points):
+ *   - Pointers named d_* are DEVICE pointers owned by the caller; the library
+ *     never allocates device memory.  A BVH lives in caller-provided storage
+ *     (mesh_bvh_storage_bytes) and a build uses caller-provided scratch
+ *     (mesh_build_workspace_bytes).  Host pointers are named without d_.
+ *   - Positions are float32, row-major xyz: vertices [nV][3], queries [nQ][3].
+ *     Faces are int32 [nF][3] vertex indices (0-based), counter-clockwise.
+ *   - Every call is asynchronous on `stream` (a cudaStream_t passed as void*;
+ *     NULL is the legacy default stream) and may be captured in a CUDA graph.
+ *     Host-side argument errors are returned at once and launch nothing.
+ *     Device-side problems (an index out of range, a traversal stack
+ *     overflow) set sticky bits in the BVH's status word, read and cleared by
+ *     mesh_bvh_status(); the kernels never trap.
+ *   - No call is thread-safe against concurrent calls on the same handle.
+ */
+#ifndef MESHGS_H
+#define MESHGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MESH_OK = 0,
+    MESH_ERR_INVALID_ARG = 1,   /* null pointer, negative or too-large size      */
+    MESH_ERR_CUDA = 2,          /* a CUDA runtime call or launch failed            */
+    MESH_ERR_WORKSPACE = 3,     /* caller storage / workspace smaller than needed  */
+    MESH_ERR_DEVICE = 4         /* mesh_bvh_status found device-side status bits   */
+} mesh_status;
+
+/* Device status bits (mesh_bvh_status). */
+#define MESH_DEV_INDEX_RANGE     0x1u  /* a face / Gaussian / sample index was out of range; the
+                                          offending element was skipped or clamped to 0 */
+#define MESH_DEV_STACK_OVERFLOW  0x2u  /* traversal stack exhausted (cannot happen for nF < 2^33) */
+#define MESH_DEV_DEGENERATE      0x4u  /* a Gaussian sat on a zero-area face (not an error)       */
+
+typedef struct mesh_bvh mesh_bvh;   /* opaque host handle describing device storage */
+
+/* Child links in the node records: an internal node c >= 0, leaf j as -(j+1). */
+typedef struct {
+    int64_t n_faces, n_verts, max_faces, max_verts;
+    /* byte offsets inside the storage block given to mesh_bvh_create */
+    size_t off_header;   /* float4 root_lo, float4 root_hi, then uint32 status, uint32 n_degenerate */
+    size_t off_verts;    /* float4 [max_verts]   vertex buffer, w = 0                          */
+    size_t off_faces;    /* int4   [max_faces]   (v0, v1, v2, 0) in input face order           */
+    size_t off_keys;     /* uint32 [max_faces]   Morton keys in sorted (leaf) order            */
+    size_t off_perm;     /* int32  [max_faces]   face id of leaf j                             */
+    size_t off_nodes;    /* 4 x float4 per internal node: (lo_L, left) (hi_L, left)
+                                                          (lo_R, right) (hi_R, right),
+                            child index stored as int32 bits in .w                            */
+    size_t off_parent;   /* int32  [2 max_faces - 1]  2 * parent + side (0 left, 1 right),
+                            -1 at the root; internal nodes first, then leaves                 */
+    size_t off_tris;     /* 3 x float4 per leaf: (v0, face id bits) (v1, 0) (v2, 0)           */
+    size_t off_flags;    /* uint32 [max_faces]   bottom-up arrival counters (kept at zero)    */
+    size_t storage_bytes;
+} mesh_bvh_layout;
+
+/* ---------------------------------------------------------------- */
+/* Storage and handles                                               */
+/* ---------------------------------------------------------------- */
+
+/* Device bytes a BVH over up to max_faces faces / max_verts vertices occupies. */
+size_t mesh_bvh_storage_bytes(int64_t max_verts, int64_t max_faces);
+
+/* Device scratch bytes one mesh_build_lbvh over up to max_faces faces needs. */
+size_t mesh_build_workspace_bytes(int64_t max_faces);
+
+/* Wrap caller storage (>= mesh_bvh_storage_bytes, 256-byte aligned) in a handle.
+ * Host-only: allocates the small host struct, touches no device memory. */
+mesh_status mesh_bvh_create(void *d_storage, size_t storage_bytes, int64_t max_verts,
+                            int64_t max_faces, mesh_bvh **out);
+
+/* Free the host struct only; the storage stays the caller's. */
+void mesh_bvh_destroy(mesh_bvh *bvh);
+
+/* Offsets of every array inside the storage (for inspection and tests). */
+mesh_status mesh_bvh_get_layout(const mesh_bvh *bvh, mesh_bvh_layout *out);
+
+/* ---------------------------------------------------------------- */
+/* The update steps                                                  */
+/* ---------------------------------------------------------------- */
+
+/* Full LBVH build from scratch over (V, F): the collision-structure rebuild the
+ * varying-topology baseline pays every frame (Sec. 4.1) and the one-off build
+ * from F0 (Sec. 3.4, Initialization).  Copies V into the handle's vertex
+ * buffer and F into its face table, computes 30-bit Morton keys of face
+ * centroids, radix-sorts them (stable), builds Karras's binary radix tree and
+ * its boxes bottom-up.  nF may be 0 (every query then misses).  F indices
+ * outside [0, nV) set MESH_DEV_INDEX_RANGE and are read as 0.
+ * d_ws: >= mesh_build_workspace_bytes(nF) bytes of scratch, 256-byte aligned,
+ * free for other use once the stream has passed this call. */
+mesh_status mesh_build_lbvh(mesh_bvh *bvh, const float *d_V, int64_t nV, const int32_t *d_F,
+                            int64_t nF, void *d_ws, size_t ws_bytes, void *stream);
+
+/* Vertex-buffer update of Sec. 3.4 (step 2): copy V_k ([nV][3], nV equal to
+ * the built mesh's) into the handle's vertex buffer.  Topology is untouched. */
+mesh_status mesh_update_vertices(mesh_bvh *bvh, const float *d_V, int64_t nV, void *stream);
+
+/* Recompute every node box over the fixed topology from the current vertex
+ * buffer (after mesh_update_vertices).  If d_V is not NULL the vertex-buffer
+ * update is done first, as by mesh_update_vertices(bvh, d_V, nV). */
+mesh_status mesh_refit(mesh_bvh *bvh, const float *d_V, int64_t nV, void *stream);
+
+/* NearestSurface (Eq. 1 / Eq. 2): for each query q the closest point of the
+ * mesh, as face id, barycentric weights (u, v, w) of (v0, v1, v2), the point
+ * u v0 + v v1 + w v2 and its squared distance.  Ties: the lowest face id
+ * among faces within 1e-6 relative distance (+1e-12 of the box diagonal) of
+ * the nearest found.  A query with no face within max_dist (INFINITY = no
+ * cutoff) gets face -1, dist2 = +inf, bary = point = 0.  Any output pointer
+ * may be NULL (not written). */
+mesh_status mesh_closest_point(const mesh_bvh *bvh, const float *d_Q, int64_t nQ,
+                               float max_dist, int32_t *d_face, float *d_bary, float *d_point,
+                               float *d_dist2, void *stream);
+
+/* Face-bound Gaussians from the handle's current vertex buffer.  For Gaussian
+ * g on face f = d_gface[g] with weights b = d_gbary[g] and normal offset
+ * delta = d_goff[g] (NULL = 0):
+ *   e1 = (v1 - v0)/|v1 - v0|, n = unit((v1 - v0) x (v2 - v0)), e2 = n x e1,
+ *   mu = b0 v0 + b1 v1 + b2 v2 + delta n,
+ *   quat = unit quaternion (w, x, y, z) of [e1 e2 n] with w >= 0,
+ *   scale = (l/3, h/3, 0.01 (l + h)/6), l = |v1 - v0|, h = 2 area / l.
+ * Zero-area faces give mu from b alone, quat (1,0,0,0), scale 0 and set
+ * MESH_DEV_DEGENERATE.  Outputs: d_mu [nG][3], d_quat [nG][4], d_scale [nG][3]. */
+mesh_status mesh_bind_gaussians(const mesh_bvh *bvh, const int32_t *d_gface, const float *d_gbary,
+                                const float *d_goff, int64_t nG, float *d_mu, float *d_quat,
+                                float *d_scale, void *stream);
+
+/* Points given by face id and barycentric weights on the current vertex
+ * buffer: out[i] = sum_j bary[i][j] v_j(face[i]).  [n][3] float32. */
+mesh_status mesh_interpolate(const mesh_bvh *bvh, const int32_t *d_face, const float *d_bary,
+                             int64_t n, float *d_out, void *stream);
+
+/* Chamfer distance (Sec. 4.2): d_out[0] = mean over SA of d(a, mesh B)^2,
+ * d_out[1] = mean over SB of d(b, mesh A)^2, float64, summed in a fixed order
+ * (bit-reproducible run to run).  Per-sample results for the backward pass
+ * may be requested (any of the pointers may be NULL).
+ * d_ws: >= mesh_chamfer_workspace_bytes(nSA, nSB) bytes of scratch. */
+size_t mesh_chamfer_workspace_bytes(int64_t nSA, int64_t nSB);
+mesh_status mesh_chamfer(const mesh_bvh *A, const float *d_SA, int64_t nSA,
+                         const mesh_bvh *B, const float *d_SB, int64_t nSB,
+                         void *d_ws, size_t ws_bytes, double *d_out,
+                         int32_t *d_faceA, float *d_baryA, float *d_dist2A,
+                         int32_t *d_faceB, float *d_baryB, float *d_dist2B, void *stream);
+
+/* ---------------------------------------------------------------- */
+/* Gradients (nearest face and weights held fixed: envelope theorem) */
+/* ---------------------------------------------------------------- */
+
+/* Given dL/d(dist2) per query (d_g [nQ]) and the forward face / bary:
+ *   dL/dq   = 2 g (q - c)                 -> d_gQ [nQ][3] (written; may be NULL)
+ *   dL/dv_j = -2 g b_j (q - c)            -> d_gV [nV][3] (accumulated; may be NULL)
+ * with c = sum_j b_j v_j on the current vertex buffer.  face -1 contributes 0. */
+mesh_status mesh_closest_point_backward(const mesh_bvh *bvh, const float *d_Q, int64_t nQ,
+                                        const int32_t *d_face, const float *d_bary,
+                                        const float *d_g, float *d_gQ, float *d_gV,
+                                        void *stream);
+
+/* dL/dV += sum_i b_ij dL/dp_i over the vertices of face[i] (d_gV accumulated). */
+mesh_status mesh_interpolate_backward(const mesh_bvh *bvh, const int32_t *d_face,
+                                      const float *d_bary, int64_t n, const float *d_gP,
+                                      float *d_gV, void *stream);
+
+/* Reverse mode of mesh_bind_gaussians with respect to vertex positions:
+ * d_gmu [nG][3], d_gquat [nG][4], d_gscale [nG][3] (any may be NULL = 0);
+ * dL/dV accumulated into d_gV [nV][3]. */
+mesh_status mesh_bind_gaussians_backward(const mesh_bvh *bvh, const int32_t *d_gface,
+                                         const float *d_gbary, const float *d_goff, int64_t nG,
+                                         const float *d_gmu, const float *d_gquat,
+                                         const float *d_gscale, float *d_gV, void *stream);
+
+/* ---------------------------------------------------------------- */
+/* Status and diagnostics                                            */
+/* ---------------------------------------------------------------- */
+
+/* Synchronise `stream`, read and clear the BVH's device status bits into
+ * *bits (may be NULL) and the count of degenerate Gaussians seen into
+ * *n_degenerate (may be NULL).  Returns MESH_ERR_DEVICE if an error bit
+ * (anything but MESH_DEV_DEGENERATE) was set, else MESH_OK. */
+mesh_status mesh_bvh_status(mesh_bvh *bvh, uint32_t *bits, uint32_t *n_degenerate, void *stream);
+
+const char *mesh_status_string(mesh_status s);
+
+/* Number of kernels this library has launched in the process so far. */
+uint64_t mesh_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MESHGS_H */

@@ -1,0 +1,82 @@
+"""ctypes declarations of the meshgs C ABI (include/meshgs.h).
+
+Loading fails loudly: there is no CPU or Python fallback for any entry point.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+from . import _build
+
+_lib = None
+
+VP = C.c_void_p
+I64 = C.c_int64
+SZ = C.c_size_t
+
+MESH_OK = 0
+MESH_ERR_DEVICE = 4
+DEV_INDEX_RANGE = 0x1
+DEV_STACK_OVERFLOW = 0x2
+DEV_DEGENERATE = 0x4
+
+
+class Layout(C.Structure):
+    _fields_ = [("n_faces", I64), ("n_verts", I64), ("max_faces", I64), ("max_verts", I64),
+                ("off_header", SZ), ("off_verts", SZ), ("off_faces", SZ), ("off_keys", SZ),
+                ("off_perm", SZ), ("off_nodes", SZ), ("off_parent", SZ), ("off_tris", SZ),
+                ("off_flags", SZ), ("storage_bytes", SZ)]
+
+
+SIGNATURES = {
+    "mesh_bvh_storage_bytes": (SZ, [I64, I64]),
+    "mesh_build_workspace_bytes": (SZ, [I64]),
+    "mesh_bvh_create": (C.c_int, [VP, SZ, I64, I64, C.POINTER(VP)]),
+    "mesh_bvh_destroy": (None, [VP]),
+    "mesh_bvh_get_layout": (C.c_int, [VP, C.POINTER(Layout)]),
+    "mesh_build_lbvh": (C.c_int, [VP, VP, I64, VP, I64, VP, SZ, VP]),
+    "mesh_update_vertices": (C.c_int, [VP, VP, I64, VP]),
+    "mesh_refit": (C.c_int, [VP, VP, I64, VP]),
+    "mesh_closest_point": (C.c_int, [VP, VP, I64, C.c_float, VP, VP, VP, VP, VP]),
+    "mesh_bind_gaussians": (C.c_int, [VP, VP, VP, VP, I64, VP, VP, VP, VP]),
+    "mesh_interpolate": (C.c_int, [VP, VP, VP, I64, VP, VP]),
+    "mesh_chamfer_workspace_bytes": (SZ, [I64, I64]),
+    "mesh_chamfer": (C.c_int, [VP, VP, I64, VP, VP, I64, VP, SZ, VP, VP, VP, VP, VP, VP, VP, VP]),
+    "mesh_closest_point_backward": (C.c_int, [VP, VP, I64, VP, VP, VP, VP, VP, VP]),
+    "mesh_interpolate_backward": (C.c_int, [VP, VP, VP, I64, VP, VP, VP]),
+    "mesh_bind_gaussians_backward": (C.c_int, [VP, VP, VP, VP, I64, VP, VP, VP, VP, VP]),
+    "mesh_bvh_status": (C.c_int, [VP, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), VP]),
+    "mesh_status_string": (C.c_char_p, [C.c_int]),
+    "mesh_launch_count": (C.c_uint64, []),
+}
+
+
+def lib():
+    """The loaded libmeshgs.so (built in-tree on first use if absent or stale)."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"meshgs CUDA library missing at {path}")
+        L = C.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+class MeshError(RuntimeError):
+    pass
+
+
+def check(status: int, what: str = "") -> None:
+    if status != MESH_OK:
+        msg = lib().mesh_status_string(status).decode()
+        raise MeshError(f"{what}: {msg} (status {status})")
+
+
+def exported_symbols() -> list[str]:
+    return list(SIGNATURES)

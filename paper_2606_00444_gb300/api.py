@@ -1,0 +1,248 @@
+"""PyTorch-facing binding of the meshgs C ABI: argument marshalling only.
+
+PyTorch provides device memory (storage, workspace, outputs) and the current
+CUDA stream; every step of the update runs in the library's CUDA kernels.
+Inputs must be CUDA tensors of the documented dtype and shape (float32 xyz
+rows, int32 indices); they are made contiguous, never converted on the host.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+
+import torch
+
+from . import _abi
+from ._abi import check, lib
+
+
+def _stream() -> int:
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _ptr(t: torch.Tensor | None) -> int | None:
+    return None if t is None else t.data_ptr()
+
+
+def _f32(t: torch.Tensor, cols: int | None = None, name: str = "tensor") -> torch.Tensor:
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float32:
+        raise TypeError(f"{name} must be float32, got {t.dtype}")
+    if cols is not None and (t.dim() != 2 or t.shape[1] != cols):
+        raise ValueError(f"{name} must have shape [n, {cols}], got {tuple(t.shape)}")
+    return t.contiguous()
+
+
+def _i32(t: torch.Tensor, cols: int | None = None, name: str = "tensor") -> torch.Tensor:
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.int32:
+        raise TypeError(f"{name} must be int32, got {t.dtype}")
+    if cols is not None and (t.dim() != 2 or t.shape[1] != cols):
+        raise ValueError(f"{name} must have shape [n, {cols}], got {tuple(t.shape)}")
+    return t.contiguous()
+
+
+class Workspace:
+    """A grow-only device scratch buffer (256-byte aligned torch allocation)."""
+
+    def __init__(self, device):
+        self.device = device
+        self.buf = None
+
+    def get(self, nbytes: int) -> torch.Tensor:
+        if self.buf is None or self.buf.numel() < nbytes:
+            self.buf = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=self.device)
+        return self.buf
+
+
+class MeshBVH:
+    """A triangle mesh with its LBVH, vertex buffer and face table in device storage.
+
+    The same vertex buffer serves collision queries and the face-bound
+    Gaussians (the paper's shared physics / rendering mesh).
+    """
+
+    def __init__(self, max_verts: int, max_faces: int, device="cuda"):
+        self.device = torch.device(device)
+        nbytes = lib().mesh_bvh_storage_bytes(max_verts, max_faces)
+        if nbytes == 0:
+            raise ValueError("mesh too large")
+        self.storage = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        h = C.c_void_p()
+        check(lib().mesh_bvh_create(self.storage.data_ptr(), nbytes, max_verts, max_faces,
+                                    C.byref(h)), "mesh_bvh_create")
+        self.handle = h
+        self.max_verts, self.max_faces = max_verts, max_faces
+        self._ws = Workspace(self.device)
+        self._chamfer_ws = Workspace(self.device)
+        self.n_verts = 0
+        self.n_faces = 0
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            try:
+                lib().mesh_bvh_destroy(h)
+            except Exception:
+                pass
+            self.handle = None
+
+    @classmethod
+    def from_mesh(cls, V: torch.Tensor, F: torch.Tensor) -> "MeshBVH":
+        b = cls(V.shape[0], F.shape[0], V.device)
+        b.build(V, F)
+        return b
+
+    # -- the update steps -------------------------------------------------
+    def build(self, V: torch.Tensor, F: torch.Tensor) -> "MeshBVH":
+        V = _f32(V, 3, "V")
+        F = _i32(F, 3, "F")
+        ws = self._ws.get(lib().mesh_build_workspace_bytes(F.shape[0]))
+        check(lib().mesh_build_lbvh(self.handle, V.data_ptr(), V.shape[0], F.data_ptr(),
+                                    F.shape[0], ws.data_ptr(), ws.numel(), _stream()),
+              "mesh_build_lbvh")
+        self.n_verts, self.n_faces = V.shape[0], F.shape[0]
+        return self
+
+    def update_vertices(self, V: torch.Tensor) -> None:
+        V = _f32(V, 3, "V")
+        check(lib().mesh_update_vertices(self.handle, V.data_ptr(), V.shape[0], _stream()),
+              "mesh_update_vertices")
+
+    def refit(self, V: torch.Tensor | None = None) -> None:
+        if V is not None:
+            V = _f32(V, 3, "V")
+        check(lib().mesh_refit(self.handle, _ptr(V), 0 if V is None else V.shape[0], _stream()),
+              "mesh_refit")
+
+    def closest_point(self, Q: torch.Tensor, max_dist: float = math.inf, want=("face", "bary",
+                      "point", "dist2"), out: dict | None = None) -> dict:
+        Q = _f32(Q, 3, "Q")
+        n = Q.shape[0]
+        out = {} if out is None else out
+        if "face" in want and "face" not in out:
+            out["face"] = torch.empty(n, dtype=torch.int32, device=Q.device)
+        for k, c in (("bary", 3), ("point", 3)):
+            if k in want and k not in out:
+                out[k] = torch.empty(n, c, dtype=torch.float32, device=Q.device)
+        if "dist2" in want and "dist2" not in out:
+            out["dist2"] = torch.empty(n, dtype=torch.float32, device=Q.device)
+        check(lib().mesh_closest_point(self.handle, Q.data_ptr(), n, float(max_dist),
+                                       _ptr(out.get("face")), _ptr(out.get("bary")),
+                                       _ptr(out.get("point")), _ptr(out.get("dist2")), _stream()),
+              "mesh_closest_point")
+        return out
+
+    def bind_gaussians(self, gface, gbary, goff=None, out=None):
+        gface = _i32(gface, None, "gface")
+        gbary = _f32(gbary, 3, "gbary")
+        goff = None if goff is None else _f32(goff, None, "goff")
+        n = gface.shape[0]
+        if out is None:
+            out = (torch.empty(n, 3, device=gface.device), torch.empty(n, 4, device=gface.device),
+                   torch.empty(n, 3, device=gface.device))
+        mu, quat, scale = out
+        check(lib().mesh_bind_gaussians(self.handle, gface.data_ptr(), gbary.data_ptr(), _ptr(goff),
+                                        n, mu.data_ptr(), quat.data_ptr(), scale.data_ptr(),
+                                        _stream()), "mesh_bind_gaussians")
+        return mu, quat, scale
+
+    def interpolate(self, face, bary, out=None):
+        face = _i32(face, None, "face")
+        bary = _f32(bary, 3, "bary")
+        out = torch.empty(face.shape[0], 3, device=face.device) if out is None else out
+        check(lib().mesh_interpolate(self.handle, face.data_ptr(), bary.data_ptr(), face.shape[0],
+                                     out.data_ptr(), _stream()), "mesh_interpolate")
+        return out
+
+    # -- gradients -------------------------------------------------------
+    def closest_point_backward(self, Q, face, bary, g, gQ=None, gV=None):
+        Q = _f32(Q, 3, "Q")
+        check(lib().mesh_closest_point_backward(self.handle, Q.data_ptr(), Q.shape[0],
+                                                _i32(face).data_ptr(), _f32(bary, 3).data_ptr(),
+                                                _f32(g).data_ptr(), _ptr(gQ), _ptr(gV), _stream()),
+              "mesh_closest_point_backward")
+
+    def interpolate_backward(self, face, bary, gP, gV):
+        check(lib().mesh_interpolate_backward(self.handle, _i32(face).data_ptr(),
+                                              _f32(bary, 3).data_ptr(), face.shape[0],
+                                              _f32(gP, 3).data_ptr(), gV.data_ptr(), _stream()),
+              "mesh_interpolate_backward")
+
+    def bind_gaussians_backward(self, gface, gbary, goff, gmu, gquat, gscale, gV):
+        gface = _i32(gface)
+        check(lib().mesh_bind_gaussians_backward(
+            self.handle, gface.data_ptr(), _f32(gbary, 3).data_ptr(),
+            _ptr(None if goff is None else _f32(goff)), gface.shape[0],
+            _ptr(None if gmu is None else _f32(gmu, 3)),
+            _ptr(None if gquat is None else _f32(gquat, 4)),
+            _ptr(None if gscale is None else _f32(gscale, 3)), gV.data_ptr(), _stream()),
+            "mesh_bind_gaussians_backward")
+
+    # -- inspection -----------------------------------------------------
+    def status(self) -> tuple[int, int]:
+        bits = C.c_uint32()
+        ndeg = C.c_uint32()
+        st = lib().mesh_bvh_status(self.handle, C.byref(bits), C.byref(ndeg), _stream())
+        if st not in (_abi.MESH_OK, _abi.MESH_ERR_DEVICE):
+            check(st, "mesh_bvh_status")
+        return bits.value, ndeg.value
+
+    def layout(self) -> dict:
+        L = _abi.Layout()
+        check(lib().mesh_bvh_get_layout(self.handle, C.byref(L)), "mesh_bvh_get_layout")
+        return {k: getattr(L, k) for k, _ in _abi.Layout._fields_}
+
+    def arrays(self) -> dict:
+        """Views of the device arrays (see mesh_bvh_layout in include/meshgs.h)."""
+        L = self.layout()
+        n, nv = L["n_faces"], L["n_verts"]
+        s = self.storage
+
+        def view(off, count, dtype, shape):
+            nbytes = count * torch.tensor([], dtype=dtype).element_size()
+            return s[off:off + nbytes].view(dtype).reshape(shape)
+
+        out = dict(
+            root=view(L["off_header"], 8, torch.float32, (2, 4))[:, :3],
+            verts=view(L["off_verts"], 4 * nv, torch.float32, (nv, 4)),
+            faces=view(L["off_faces"], 4 * n, torch.int32, (n, 4)),
+            keys=view(L["off_keys"], n, torch.int32, (n,)),
+            perm=view(L["off_perm"], n, torch.int32, (n,)),
+            parent=view(L["off_parent"], max(2 * n - 1, 0), torch.int32, (max(2 * n - 1, 0),)),
+            tris=view(L["off_tris"], 12 * n, torch.float32, (n, 3, 4)),
+        )
+        m = max(n - 1, 0)
+        out["nodes"] = view(L["off_nodes"], 16 * m, torch.float32, (m, 4, 4))
+        out["nodes_i"] = view(L["off_nodes"], 16 * m, torch.int32, (m, 4, 4))
+        return out
+
+
+def chamfer(A: MeshBVH, SA: torch.Tensor, B: MeshBVH, SB: torch.Tensor, per_sample=False,
+            ws: Workspace | None = None, out: torch.Tensor | None = None):
+    """[mean d(SA, B)^2, mean d(SB, A)^2] (float64) and optional per-sample results."""
+    SA = _f32(SA, 3, "SA")
+    SB = _f32(SB, 3, "SB")
+    nA, nB = SA.shape[0], SB.shape[0]
+    ws = A._chamfer_ws if ws is None else ws
+    buf = ws.get(lib().mesh_chamfer_workspace_bytes(nA, nB))
+    out = torch.empty(2, dtype=torch.float64, device=SA.device) if out is None else out
+    ps = {}
+    if per_sample:
+        dev = SA.device
+        ps = dict(faceA=torch.empty(nA, dtype=torch.int32, device=dev),
+                  baryA=torch.empty(nA, 3, device=dev), dist2A=torch.empty(nA, device=dev),
+                  faceB=torch.empty(nB, dtype=torch.int32, device=dev),
+                  baryB=torch.empty(nB, 3, device=dev), dist2B=torch.empty(nB, device=dev))
+    check(lib().mesh_chamfer(A.handle, SA.data_ptr(), nA, B.handle, SB.data_ptr(), nB,
+                             buf.data_ptr(), buf.numel(), out.data_ptr(),
+                             _ptr(ps.get("faceA")), _ptr(ps.get("baryA")), _ptr(ps.get("dist2A")),
+                             _ptr(ps.get("faceB")), _ptr(ps.get("baryB")), _ptr(ps.get("dist2B")),
+                             _stream()), "mesh_chamfer")
+    return (out, ps) if per_sample else out
+
+
+def launch_count() -> int:
+    return int(lib().mesh_launch_count())

@@ -1,0 +1,57 @@
+// Internal definitions shared by the meshgs CUDA translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "meshgs.h"
+
+namespace meshgs {
+
+// Device-side header at the start of every BVH storage block.
+struct __align__(16) Header {
+    float4 root_lo;          // mesh box (all referenced vertices)
+    float4 root_hi;
+    unsigned int status;     // sticky MESH_DEV_* bits
+    unsigned int n_degenerate;
+    unsigned int pad[2];
+};
+
+struct mesh_bvh_impl {
+    char *base;
+    mesh_bvh_layout L;
+    Header *hdr() const { return reinterpret_cast<Header *>(base + L.off_header); }
+    float4 *verts() const { return reinterpret_cast<float4 *>(base + L.off_verts); }
+    int4 *faces() const { return reinterpret_cast<int4 *>(base + L.off_faces); }
+    unsigned int *keys() const { return reinterpret_cast<unsigned int *>(base + L.off_keys); }
+    int *perm() const { return reinterpret_cast<int *>(base + L.off_perm); }
+    float4 *nodes() const { return reinterpret_cast<float4 *>(base + L.off_nodes); }
+    int *parent() const { return reinterpret_cast<int *>(base + L.off_parent); }
+    float4 *tris() const { return reinterpret_cast<float4 *>(base + L.off_tris); }
+    unsigned int *flags() const { return reinterpret_cast<unsigned int *>(base + L.off_flags); }
+};
+
+// Host-side bookkeeping shared by the entry points.
+void count_launch(int n = 1);
+mesh_status check_launch();
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+inline unsigned int grid_for(int64_t n, int block) {
+    return (unsigned int)((n + block - 1) / block);
+}
+
+// Tie rule of NearestSurface: faces within (1 + 1e-6) of the nearest distance
+// (plus 1e-12 of the box diagonal) count as equally near; the lowest id wins.
+constexpr float kTieRel = 1e-6f;
+constexpr float kTieAbs = 1e-12f;
+
+__device__ __forceinline__ float4 ldg4(const float4 *p) { return __ldg(p); }
+
+__device__ __forceinline__ void set_status(Header *h, unsigned int bit) {
+    atomicOr(&h->status, bit);
+}
+
+}  // namespace meshgs
+
+struct mesh_bvh : meshgs::mesh_bvh_impl {};

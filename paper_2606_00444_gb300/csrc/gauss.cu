@@ -1,0 +1,267 @@
+// Face-bound Gaussians of the rendering representation (Sec. 3.2).  The paper
+// anchors Gaussians to mesh faces (Sec. 2, Sec. 3.1) but prints no formula;
+// the face frame used here is: e1 along edge v0->v1, n the unit face normal,
+// e2 = n x e1; centre = barycentric anchor plus a normal offset; rotation =
+// quaternion of [e1 e2 n]; scale from the edge length and the altitude.
+// One thread per Gaussian; face and vertex reads are float4 / int4 gathers
+// from the BVH's vertex buffer and face table (shared with the collision side).
+#include <math.h>
+
+#include "common.cuh"
+
+namespace meshgs {
+
+constexpr float kRho = 1.0f / 3.0f;
+constexpr float kEpsS = 1e-2f;
+
+struct V3 {
+    float x, y, z;
+};
+__device__ __forceinline__ V3 v3(float4 a) { return V3{a.x, a.y, a.z}; }
+__device__ __forceinline__ V3 operator+(V3 a, V3 b) { return V3{a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ __forceinline__ V3 operator-(V3 a, V3 b) { return V3{a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ V3 operator*(V3 a, float s) { return V3{a.x * s, a.y * s, a.z * s}; }
+__device__ __forceinline__ float dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ V3 cross(V3 a, V3 b) {
+    return V3{a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+
+// Zero area: the float32 cross product decides when it is clearly non-zero
+// (above its rounding bound); otherwise it is recomputed in float64, where
+// products of float32 inputs are exact, so the answer is the exact one.
+__device__ __forceinline__ bool zero_area(V3 e, V3 f, V3 nu) {
+    float an2 = dot(nu, nu);
+    if (an2 > 1e-10f * dot(e, e) * dot(f, f)) return false;
+    double ex = e.x, ey = e.y, ez = e.z, fx = f.x, fy = f.y, fz = f.z;
+    return (ey * fz - ez * fy) == 0.0 && (ez * fx - ex * fz) == 0.0 && (ex * fy - ey * fx) == 0.0;
+}
+
+struct Frame {
+    V3 e, f, nu, e1, n, e2;
+    float l, an;
+    bool degenerate;
+};
+
+__device__ __forceinline__ Frame face_frame(V3 a, V3 b, V3 c) {
+    Frame F;
+    F.e = b - a;
+    F.f = c - a;
+    F.nu = cross(F.e, F.f);
+    float l2 = dot(F.e, F.e);
+    F.degenerate = (l2 == 0.0f) || zero_area(F.e, F.f, F.nu);
+    if (F.degenerate) return F;
+    F.l = sqrtf(l2);
+    F.an = sqrtf(dot(F.nu, F.nu));
+    F.e1 = F.e * (1.0f / F.l);
+    F.n = F.nu * (1.0f / F.an);
+    F.e2 = cross(F.n, F.e1);
+    return F;
+}
+
+// Rotation-matrix -> quaternion by the largest of (trace, R00, R11, R22)
+// (Shepperd 1978).  R columns are (e1, e2, n).  raw = (w, x, y, z) before the
+// sign is fixed; returns the branch.
+__device__ __forceinline__ int quat_raw(const float R[3][3], float raw[4], float &p) {
+    float tr = R[0][0] + R[1][1] + R[2][2];
+    int br;
+    if (tr >= R[0][0] && tr >= R[1][1] && tr >= R[2][2]) br = 0;
+    else if (R[0][0] >= R[1][1] && R[0][0] >= R[2][2]) br = 1;
+    else if (R[1][1] >= R[2][2]) br = 2;
+    else br = 3;
+    if (br == 0) {
+        p = 0.5f * sqrtf(1.0f + tr);
+        float k = 0.25f / p;
+        raw[0] = p; raw[1] = (R[2][1] - R[1][2]) * k; raw[2] = (R[0][2] - R[2][0]) * k;
+        raw[3] = (R[1][0] - R[0][1]) * k;
+    } else if (br == 1) {
+        p = 0.5f * sqrtf(1.0f + R[0][0] - R[1][1] - R[2][2]);
+        float k = 0.25f / p;
+        raw[1] = p; raw[0] = (R[2][1] - R[1][2]) * k; raw[2] = (R[0][1] + R[1][0]) * k;
+        raw[3] = (R[0][2] + R[2][0]) * k;
+    } else if (br == 2) {
+        p = 0.5f * sqrtf(1.0f - R[0][0] + R[1][1] - R[2][2]);
+        float k = 0.25f / p;
+        raw[2] = p; raw[0] = (R[0][2] - R[2][0]) * k; raw[1] = (R[0][1] + R[1][0]) * k;
+        raw[3] = (R[1][2] + R[2][1]) * k;
+    } else {
+        p = 0.5f * sqrtf(1.0f - R[0][0] - R[1][1] + R[2][2]);
+        float k = 0.25f / p;
+        raw[3] = p; raw[0] = (R[1][0] - R[0][1]) * k; raw[1] = (R[0][2] + R[2][0]) * k;
+        raw[2] = (R[1][2] + R[2][1]) * k;
+    }
+    return br;
+}
+
+// Sign that makes w > 0 (or, at w == 0, the first non-zero of x, y, z > 0).
+__device__ __forceinline__ float quat_sign(const float raw[4]) {
+    if (raw[0] != 0.0f) return raw[0] < 0.0f ? -1.0f : 1.0f;
+    for (int k = 1; k < 4; ++k)
+        if (raw[k] != 0.0f) return raw[k] < 0.0f ? -1.0f : 1.0f;
+    return 1.0f;
+}
+
+__device__ __forceinline__ void frame_matrix(const Frame &F, float R[3][3]) {
+    R[0][0] = F.e1.x; R[0][1] = F.e2.x; R[0][2] = F.n.x;
+    R[1][0] = F.e1.y; R[1][1] = F.e2.y; R[1][2] = F.n.y;
+    R[2][0] = F.e1.z; R[2][1] = F.e2.z; R[2][2] = F.n.z;
+}
+
+__global__ void k_bind_gaussians(const int4 *__restrict__ faces, const float4 *__restrict__ verts,
+                                 int nF, const int *__restrict__ gface,
+                                 const float *__restrict__ gbary, const float *__restrict__ goff,
+                                 int64_t nG, float *__restrict__ mu, float *__restrict__ quat,
+                                 float *__restrict__ scale, Header *hdr) {
+    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= nG) return;
+    int f = gface[g];
+    if ((unsigned)f >= (unsigned)nF) {
+        set_status(hdr, MESH_DEV_INDEX_RANGE);
+        mu[3 * g] = mu[3 * g + 1] = mu[3 * g + 2] = 0.0f;
+        quat[4 * g] = 1.0f; quat[4 * g + 1] = quat[4 * g + 2] = quat[4 * g + 3] = 0.0f;
+        scale[3 * g] = scale[3 * g + 1] = scale[3 * g + 2] = 0.0f;
+        return;
+    }
+    int4 fv = faces[f];
+    V3 a = v3(verts[fv.x]), b = v3(verts[fv.y]), c = v3(verts[fv.z]);
+    float b0 = gbary[3 * g], b1 = gbary[3 * g + 1], b2 = gbary[3 * g + 2];
+    V3 m = a * b0 + b * b1 + c * b2;
+    Frame F = face_frame(a, b, c);
+    float q[4] = {1.0f, 0.0f, 0.0f, 0.0f};
+    float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f;
+    if (F.degenerate) {
+        atomicAdd(&hdr->n_degenerate, 1u);
+        set_status(hdr, MESH_DEV_DEGENERATE);
+    } else {
+        float off = goff ? goff[g] : 0.0f;
+        m = m + F.n * off;
+        float R[3][3], p;
+        frame_matrix(F, R);
+        quat_raw(R, q, p);
+        float sg = quat_sign(q);
+        for (int k = 0; k < 4; ++k) q[k] *= sg;
+        float h = F.an / F.l;
+        s0 = kRho * F.l;
+        s1 = kRho * h;
+        s2 = kEpsS * kRho * (F.l + h) * 0.5f;
+    }
+    mu[3 * g] = m.x; mu[3 * g + 1] = m.y; mu[3 * g + 2] = m.z;
+    quat[4 * g] = q[0]; quat[4 * g + 1] = q[1]; quat[4 * g + 2] = q[2]; quat[4 * g + 3] = q[3];
+    scale[3 * g] = s0; scale[3 * g + 1] = s1; scale[3 * g + 2] = s2;
+}
+
+__device__ __forceinline__ void add_grad(float *gV, int v, V3 g) {
+    atomicAdd(gV + 3 * (size_t)v, g.x);
+    atomicAdd(gV + 3 * (size_t)v + 1, g.y);
+    atomicAdd(gV + 3 * (size_t)v + 2, g.z);
+}
+
+// VJP of the normalisation y = x / |x|: (g - y (y . g)) / |x|.
+__device__ __forceinline__ V3 vjp_unit(V3 y, float len, V3 g) { return (g - y * dot(y, g)) * (1.0f / len); }
+
+// Reverse mode of k_bind_gaussians with respect to the three face vertices.
+__global__ void k_bind_gaussians_backward(const int4 *__restrict__ faces,
+                                          const float4 *__restrict__ verts, int nF,
+                                          const int *__restrict__ gface,
+                                          const float *__restrict__ gbary,
+                                          const float *__restrict__ goff, int64_t nG,
+                                          const float *__restrict__ gmu,
+                                          const float *__restrict__ gquat,
+                                          const float *__restrict__ gscale, float *gV,
+                                          Header *hdr) {
+    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= nG) return;
+    int f = gface[g];
+    if ((unsigned)f >= (unsigned)nF) { set_status(hdr, MESH_DEV_INDEX_RANGE); return; }
+    int4 fv = faces[f];
+    V3 a = v3(verts[fv.x]), b = v3(verts[fv.y]), c = v3(verts[fv.z]);
+    float b0 = gbary[3 * g], b1 = gbary[3 * g + 1], b2 = gbary[3 * g + 2];
+    V3 Gmu = gmu ? V3{gmu[3 * g], gmu[3 * g + 1], gmu[3 * g + 2]} : V3{0.0f, 0.0f, 0.0f};
+    V3 g0 = Gmu * b0, g1 = Gmu * b1, g2 = Gmu * b2;
+    Frame F = face_frame(a, b, c);
+    if (!F.degenerate) {
+        float off = goff ? goff[g] : 0.0f;
+        float R[3][3], raw[4], p;
+        frame_matrix(F, R);
+        int br = quat_raw(R, raw, p);
+        float sg = quat_sign(raw);
+        float G[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        if (gquat)
+            for (int k = 0; k < 4; ++k) G[k] = sg * gquat[4 * g + k];
+        float dR[3][3] = {{0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}};
+        // raw[k] (k != pivot) = off_k / (4 p); raw[pivot] = p = sqrt(S) / 2
+        float Gp = G[br];
+        for (int k = 0; k < 4; ++k) {
+            if (k == br) continue;
+            float coef = G[k] / (4.0f * p);
+            Gp -= G[k] * raw[k] / p;        // d raw_k / d p = -off_k / (4 p^2) = -raw_k / p
+            int lo = min(br, k), hi = max(br, k);
+            if (lo == 0 && hi == 1) { dR[2][1] += coef; dR[1][2] -= coef; }
+            else if (lo == 0 && hi == 2) { dR[0][2] += coef; dR[2][0] -= coef; }
+            else if (lo == 0 && hi == 3) { dR[1][0] += coef; dR[0][1] -= coef; }
+            else if (lo == 1 && hi == 2) { dR[0][1] += coef; dR[1][0] += coef; }
+            else if (lo == 1 && hi == 3) { dR[0][2] += coef; dR[2][0] += coef; }
+            else { dR[1][2] += coef; dR[2][1] += coef; }
+        }
+        float gS = Gp / (8.0f * p);         // p = sqrt(S)/2  ->  dp/dS = 1/(8p)
+        const float sgn[4][3] = {{1, 1, 1}, {1, -1, -1}, {-1, 1, -1}, {-1, -1, 1}};
+        for (int d = 0; d < 3; ++d) dR[d][d] += gS * sgn[br][d];
+        V3 ge1{dR[0][0], dR[1][0], dR[2][0]};
+        V3 ge2{dR[0][1], dR[1][1], dR[2][1]};
+        V3 gn{dR[0][2], dR[1][2], dR[2][2]};
+        gn = gn + Gmu * off;
+        float Gs0 = gscale ? gscale[3 * g] : 0.0f, Gs1 = gscale ? gscale[3 * g + 1] : 0.0f;
+        float Gs2 = gscale ? gscale[3 * g + 2] : 0.0f;
+        float gl = kRho * Gs0 + kEpsS * kRho * 0.5f * Gs2;
+        float gh = kRho * Gs1 + kEpsS * kRho * 0.5f * Gs2;
+        gl -= gh * F.an / (F.l * F.l);      // h = an / l
+        float gan = gh / F.l;
+        gn = gn + cross(F.e1, ge2);         // e2 = n x e1
+        ge1 = ge1 + cross(ge2, F.n);
+        V3 gnu = vjp_unit(F.n, F.an, gn) + F.nu * (gan / F.an);
+        V3 ge = vjp_unit(F.e1, F.l, ge1) + F.e * (gl / F.l);
+        ge = ge + cross(F.f, gnu);          // nu = e x f
+        V3 gf = cross(gnu, F.e);
+        g1 = g1 + ge;
+        g2 = g2 + gf;
+        g0 = g0 - (ge + gf);
+    }
+    add_grad(gV, fv.x, g0);
+    add_grad(gV, fv.y, g1);
+    add_grad(gV, fv.z, g2);
+}
+
+}  // namespace meshgs
+
+using namespace meshgs;
+
+extern "C" {
+
+mesh_status mesh_bind_gaussians(const mesh_bvh *bvh, const int32_t *d_gface, const float *d_gbary,
+                                const float *d_goff, int64_t nG, float *d_mu, float *d_quat,
+                                float *d_scale, void *stream) {
+    if (!bvh || nG < 0 || (nG > 0 && (!d_gface || !d_gbary || !d_mu || !d_quat || !d_scale)))
+        return MESH_ERR_INVALID_ARG;
+    if (nG == 0) return MESH_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    k_bind_gaussians<<<grid_for(nG, 256), 256, 0, s>>>(bvh->faces(), bvh->verts(),
+                                                       (int)bvh->L.n_faces, d_gface, d_gbary, d_goff,
+                                                       nG, d_mu, d_quat, d_scale, bvh->hdr());
+    count_launch();
+    return check_launch();
+}
+
+mesh_status mesh_bind_gaussians_backward(const mesh_bvh *bvh, const int32_t *d_gface,
+                                         const float *d_gbary, const float *d_goff, int64_t nG,
+                                         const float *d_gmu, const float *d_gquat,
+                                         const float *d_gscale, float *d_gV, void *stream) {
+    if (!bvh || nG < 0 || (nG > 0 && (!d_gface || !d_gbary || !d_gV))) return MESH_ERR_INVALID_ARG;
+    if (nG == 0) return MESH_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    k_bind_gaussians_backward<<<grid_for(nG, 256), 256, 0, s>>>(
+        bvh->faces(), bvh->verts(), (int)bvh->L.n_faces, d_gface, d_gbary, d_goff, nG, d_gmu,
+        d_gquat, d_gscale, d_gV, bvh->hdr());
+    count_launch();
+    return check_launch();
+}
+
+}  // extern "C"

@@ -1,0 +1,571 @@
+// LBVH construction and refit over a triangle mesh.
+//
+// The paper builds its collision structure once from the template faces and
+// afterwards only replaces the vertex buffer (Sec. 3.4); the varying-topology
+// baseline rebuilds it every frame (Sec. 4.1).  The paper gives no
+// construction, so the build here is a linear BVH: 30-bit Morton keys of face
+// centroids, a stable LSD radix sort, Karras's (2012) binary radix tree, and
+// boxes computed bottom-up.  The refit reuses the tree and recomputes boxes.
+#include <atomic>
+#include <cstdlib>
+#include <cstring>
+
+#include "common.cuh"
+
+namespace meshgs {
+
+static std::atomic<unsigned long long> g_launches{0};
+void count_launch(int n) { g_launches.fetch_add((unsigned long long)n); }
+
+mesh_status check_launch() {
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? MESH_OK : MESH_ERR_CUDA;
+}
+
+constexpr int kBlock = 256;
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 4;
+constexpr int kSortTile = kSortThreads * kSortItems;   // keys per sort tile
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kRadix = 256;
+constexpr int kScanThreads = 1024;
+static_assert(kSortThreads == kRadix, "one thread per digit in the sort kernels");
+
+// ---------------------------------------------------------------------------
+// Float <-> order-preserving unsigned encoding, so box extremes can be reduced
+// with integer atomics (exact: min / max need no rounding).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned int f2ord(float f) {
+    unsigned int u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float ord2f(unsigned int u) {
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+// ---------------------------------------------------------------------------
+// a1: vertex-buffer update, [nV][3] -> float4 [nV] (w = 0).
+// Optionally (re)initialises the 6-word centroid box used by the Morton step.
+// ---------------------------------------------------------------------------
+__global__ void k_copy_verts(const float *__restrict__ V3, int nV, float4 *__restrict__ V4,
+                             unsigned int *__restrict__ cbox) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cbox && i < 6) cbox[i] = (i < 3) ? 0xffffffffu : 0u;
+    if (i >= nV) return;
+    const float *p = V3 + 3 * (size_t)i;
+    V4[i] = make_float4(p[0], p[1], p[2], 0.0f);
+}
+
+// ---------------------------------------------------------------------------
+// Face table repack [nF][3] -> int4 (v0, v1, v2, 0) with index validation, and
+// the centroid sum s = (v0 + v1) + v2 in float32 round-to-nearest (the Morton
+// recipe uses the sum, not the mean: the normalisation absorbs the factor 3).
+// The per-block min / max of s goes to the centroid box by ordered atomics.
+// ---------------------------------------------------------------------------
+__global__ void k_faces_centroids(const int *__restrict__ F3, int nF, int nV,
+                                  const float4 *__restrict__ V4, int4 *__restrict__ F4,
+                                  float4 *__restrict__ cent, unsigned int *__restrict__ cbox,
+                                  Header *__restrict__ hdr) {
+    int f = blockIdx.x * blockDim.x + threadIdx.x;
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    if (f < nF) {
+        const int *p = F3 + 3 * (size_t)f;
+        int i0 = p[0], i1 = p[1], i2 = p[2];
+        bool bad = (unsigned)i0 >= (unsigned)nV || (unsigned)i1 >= (unsigned)nV ||
+                   (unsigned)i2 >= (unsigned)nV;
+        if (bad) {
+            set_status(hdr, MESH_DEV_INDEX_RANGE);
+            if ((unsigned)i0 >= (unsigned)nV) i0 = 0;
+            if ((unsigned)i1 >= (unsigned)nV) i1 = 0;
+            if ((unsigned)i2 >= (unsigned)nV) i2 = 0;
+        }
+        F4[f] = make_int4(i0, i1, i2, 0);
+        float4 a = V4[i0], b = V4[i1], c = V4[i2];
+        float s0 = __fadd_rn(__fadd_rn(a.x, b.x), c.x);
+        float s1 = __fadd_rn(__fadd_rn(a.y, b.y), c.y);
+        float s2 = __fadd_rn(__fadd_rn(a.z, b.z), c.z);
+        cent[f] = make_float4(s0, s1, s2, 0.0f);
+        lo[0] = hi[0] = s0;
+        lo[1] = hi[1] = s1;
+        lo[2] = hi[2] = s2;
+    }
+    // warp then block reduction of the 6 extremes
+    for (int k = 0; k < 3; ++k) {
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[k] = fminf(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+            hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+        }
+    }
+    __shared__ float s_lo[3][kBlock / 32], s_hi[3][kBlock / 32];
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0)
+        for (int k = 0; k < 3; ++k) { s_lo[k][w] = lo[k]; s_hi[k][w] = hi[k]; }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        int k = threadIdx.x;
+        float l = s_lo[k][0], h = s_hi[k][0];
+        for (int i = 1; i < (int)(blockDim.x >> 5); ++i) {
+            l = fminf(l, s_lo[k][i]);
+            h = fmaxf(h, s_hi[k][i]);
+        }
+        if (l <= h) {
+            atomicMin(&cbox[k], f2ord(l));
+            atomicMax(&cbox[3 + k], f2ord(h));
+        }
+    }
+}
+
+// Bit i of v (10 bits) moved to bit 3i.
+__device__ __forceinline__ unsigned int spread3(unsigned int v) {
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000ffu;
+    v = (v | (v << 8)) & 0x0300f00fu;
+    v = (v | (v << 4)) & 0x030c30c3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// a2: 30-bit Morton key per face.  t = (s - lo) * (1 / (hi - lo)) per axis,
+// q = clamp(floor(t * 1024), 0, 1023), bits interleaved x-major.  Every
+// float operation is an explicit round-to-nearest intrinsic so no FMA
+// contraction can change a key.
+// ---------------------------------------------------------------------------
+__global__ void k_morton(const float4 *__restrict__ cent, int nF,
+                         const unsigned int *__restrict__ cbox, unsigned int *__restrict__ keys,
+                         int *__restrict__ vals) {
+    int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nF) return;
+    float lo[3], inv[3];
+    for (int k = 0; k < 3; ++k) {
+        lo[k] = ord2f(cbox[k]);
+        float ext = __fsub_rn(ord2f(cbox[3 + k]), lo[k]);
+        inv[k] = ext > 0.0f ? __fdiv_rn(1.0f, ext) : 0.0f;
+    }
+    float4 s = cent[f];
+    float sv[3] = {s.x, s.y, s.z};
+    unsigned int q[3];
+    for (int k = 0; k < 3; ++k) {
+        float t = __fmul_rn(__fsub_rn(sv[k], lo[k]), inv[k]);
+        float x = floorf(__fmul_rn(t, 1024.0f));
+        int qi = (int)x;
+        qi = qi < 0 ? 0 : (qi > 1023 ? 1023 : qi);
+        q[k] = (unsigned int)qi;
+    }
+    keys[f] = (spread3(q[0]) << 2) | (spread3(q[1]) << 1) | spread3(q[2]);
+    vals[f] = f;
+}
+
+// ---------------------------------------------------------------------------
+// a3: stable LSD radix sort of (key, face id), 8 bits per pass, reduce-then-
+// scan (three kernels per pass, no inter-block waiting of any kind).
+//   upsweep:   per-tile digit histogram, stored digit-major hist[d * T + t]
+//   scan:      one block, exclusive scan of hist in that order, which makes
+//              hist[d * T + t] the global output offset of digit d in tile t
+//   downsweep: stable in-tile ranking (warp match_any + per-warp counters),
+//              scatter through shared memory, coalesced write-out.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kSortThreads)
+k_sort_upsweep(const unsigned int *__restrict__ keys, int n, int shift,
+               unsigned int *__restrict__ hist, int T) {
+    __shared__ unsigned int h[kRadix];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    int base = blockIdx.x * kSortTile;
+    int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        int idx = base + r * kSortThreads + threadIdx.x;
+        bool valid = idx < n;
+        unsigned int d = valid ? (keys[idx] >> shift) & 0xffu : 0x100u;
+        unsigned int peers = __match_any_sync(0xffffffffu, d);
+        if (valid && (__ffs(peers) - 1) == lane) atomicAdd(&h[d], (unsigned)__popc(peers));
+    }
+    __syncthreads();
+    hist[(size_t)threadIdx.x * T + blockIdx.x] = h[threadIdx.x];
+}
+
+__device__ __forceinline__ unsigned int warp_incl_scan(unsigned int x, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    return x;
+}
+
+// Exclusive scan of the per-thread values of one block (blockDim a multiple of 32,
+// at most 1024 threads).  Returns the exclusive prefix; *total gets the sum.
+__device__ unsigned int block_excl_scan(unsigned int x, unsigned int *s_warp, unsigned int *total) {
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    unsigned int inc = warp_incl_scan(x, lane);
+    if (lane == 31) s_warp[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        unsigned int v = lane < nw ? s_warp[lane] : 0u;
+        unsigned int vi = warp_incl_scan(v, lane);
+        if (lane < nw) s_warp[lane] = vi - v;
+        if (lane == 31) s_warp[32] = vi;
+    }
+    __syncthreads();
+    unsigned int r = s_warp[w] + inc - x;
+    if (total) *total = s_warp[32];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+k_sort_scan(unsigned int *__restrict__ hist, int total) {
+    __shared__ unsigned int s_warp[33];
+    int per = (total + kScanThreads - 1) / kScanThreads;
+    int beg = threadIdx.x * per;
+    int end = min(beg + per, total);
+    unsigned int sum = 0;
+    for (int i = beg; i < end; ++i) sum += hist[i];
+    unsigned int run = block_excl_scan(sum, s_warp, nullptr);
+    for (int i = beg; i < end; ++i) {
+        unsigned int v = hist[i];
+        hist[i] = run;
+        run += v;
+    }
+}
+
+__global__ void __launch_bounds__(kSortThreads)
+k_sort_downsweep(const unsigned int *__restrict__ kin, const int *__restrict__ vin,
+                 unsigned int *__restrict__ kout, int *__restrict__ vout, int n, int shift,
+                 const unsigned int *__restrict__ hist, int T) {
+    __shared__ unsigned int s_keys[kSortTile];
+    __shared__ int s_vals[kSortTile];
+    __shared__ unsigned int s_wcnt[kSortWarps][kRadix];
+    __shared__ unsigned int s_dstart[kRadix];
+    __shared__ unsigned int s_goff[kRadix];
+    __shared__ unsigned int s_warp[33];
+    int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    for (int i = tid; i < kSortWarps * kRadix; i += kSortThreads) (&s_wcnt[0][0])[i] = 0;
+    __syncthreads();
+    int base = blockIdx.x * kSortTile;
+    unsigned int key[kSortItems], rank[kSortItems];
+    int val[kSortItems];
+    unsigned int lt_mask = (1u << lane) - 1u;
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        int idx = base + w * (32 * kSortItems) + r * 32 + lane;
+        bool valid = idx < n;
+        key[r] = valid ? kin[idx] : 0u;
+        val[r] = valid ? vin[idx] : 0;
+        unsigned int d = valid ? (key[r] >> shift) & 0xffu : 0x100u;
+        unsigned int peers = __match_any_sync(0xffffffffu, d);
+        unsigned int before = valid ? s_wcnt[w][d] : 0u;
+        __syncwarp();
+        if (valid && (peers & lt_mask) == 0u) s_wcnt[w][d] = before + __popc(peers);
+        __syncwarp();
+        rank[r] = valid ? before + __popc(peers & lt_mask) : 0xffffffffu;
+    }
+    __syncthreads();
+    // per digit: exclusive prefix over warps, then exclusive scan over digits
+    unsigned int run = 0;
+    for (int ww = 0; ww < kSortWarps; ++ww) {
+        unsigned int c = s_wcnt[ww][tid];
+        s_wcnt[ww][tid] = run;
+        run += c;
+    }
+    unsigned int start = block_excl_scan(run, s_warp, nullptr);
+    s_dstart[tid] = start;
+    s_goff[tid] = hist[(size_t)tid * T + blockIdx.x];
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        if (rank[r] != 0xffffffffu) {
+            unsigned int d = (key[r] >> shift) & 0xffu;
+            unsigned int pos = s_dstart[d] + s_wcnt[w][d] + rank[r];
+            s_keys[pos] = key[r];
+            s_vals[pos] = val[r];
+        }
+    }
+    __syncthreads();
+    int nvalid = min(kSortTile, n - base);
+    for (int i = tid; i < nvalid; i += kSortThreads) {
+        unsigned int k = s_keys[i];
+        unsigned int d = (k >> shift) & 0xffu;
+        unsigned int g = s_goff[d] + (unsigned)i - s_dstart[d];
+        kout[g] = k;
+        vout[g] = s_vals[i];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a4: Karras (2012) hierarchy, one thread per internal node i in [0, n-2].
+// delta(i, j) = common-prefix length of the keys augmented with their sorted
+// position; -1 outside [0, n).  The node's range has i at one end; its
+// direction, far end and split are found by exponential + binary search.
+// Children go to the node record's .w slots; parent[] gets 2*i + side.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int kdelta(const unsigned int *__restrict__ k, int n, int i, int j) {
+    if (j < 0 || j >= n) return -1;
+    unsigned int a = k[i], b = k[j];
+    return a != b ? __clz(a ^ b) : 32 + __clz((unsigned)i ^ (unsigned)j);
+}
+
+__global__ void k_karras(const unsigned int *__restrict__ keys, int n, float4 *__restrict__ nodes,
+                         int *__restrict__ parent) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    int d = (kdelta(keys, n, i, i + 1) - kdelta(keys, n, i, i - 1)) >= 0 ? 1 : -1;
+    int dmin = kdelta(keys, n, i, i - d);
+    int lmax = 2;
+    while (kdelta(keys, n, i, i + lmax * d) > dmin) lmax <<= 1;
+    int l = 0;
+    for (int t = lmax >> 1; t >= 1; t >>= 1)
+        if (kdelta(keys, n, i, i + (l + t) * d) > dmin) l += t;
+    int j = i + l * d;
+    int dnode = kdelta(keys, n, i, j);
+    int s = 0;
+    int t = l;
+    do {
+        t = (t + 1) >> 1;
+        if (kdelta(keys, n, i, i + (s + t) * d) > dnode) s += t;
+    } while (t > 1);
+    int gamma = i + s * d + min(d, 0);
+    int lo = min(i, j), hi = max(i, j);
+    int left = (lo == gamma) ? -(gamma + 1) : gamma;
+    int right = (hi == gamma + 1) ? -(gamma + 2) : gamma + 1;
+    float *rec = reinterpret_cast<float *>(nodes + 4 * (size_t)i);
+    rec[3] = __int_as_float(left);
+    rec[7] = __int_as_float(left);
+    rec[11] = __int_as_float(right);
+    rec[15] = __int_as_float(right);
+    parent[left >= 0 ? left : (n - 1) + (-left - 1)] = 2 * i;
+    parent[right >= 0 ? right : (n - 1) + (-right - 1)] = 2 * i + 1;
+    if (i == 0) parent[0] = -1;
+}
+
+// Exact zero-area test: the products of float32 coordinates are exact in
+// float64, so the cross product is zero here exactly when it is zero in exact
+// arithmetic (the differences of float32 inputs are exact as well).
+__device__ __forceinline__ bool exactly_degenerate(float4 a, float4 b, float4 c) {
+    double ux = (double)b.x - a.x, uy = (double)b.y - a.y, uz = (double)b.z - a.z;
+    double vx = (double)c.x - a.x, vy = (double)c.y - a.y, vz = (double)c.z - a.z;
+    return (uy * vz - uz * vy) == 0.0 && (uz * vx - ux * vz) == 0.0 && (ux * vy - uy * vx) == 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// a5: leaf boxes and bottom-up internal boxes (build and refit).  One thread
+// per leaf j writes the packed triangle of face perm[j] (leaf order), puts the
+// leaf box into its parent's record, and climbs: at each internal node the
+// first arriving child stops, the second computes the union (the sibling's
+// box is read from L2 after a fence) and continues; it also clears the
+// arrival counter for the next refit.  The root box goes to the header.
+// ---------------------------------------------------------------------------
+__global__ void k_leaves_up(int n, const int *__restrict__ perm, const int4 *__restrict__ faces,
+                            const float4 *__restrict__ verts, float4 *__restrict__ tris,
+                            float4 *__restrict__ nodes, const int *__restrict__ parent,
+                            unsigned int *__restrict__ flags, Header *__restrict__ hdr) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    int f = perm[j];
+    int4 fv = faces[f];
+    float4 a = verts[fv.x], b = verts[fv.y], c = verts[fv.z];
+    float deg = exactly_degenerate(a, b, c) ? 1.0f : 0.0f;
+    tris[3 * (size_t)j + 0] = make_float4(a.x, a.y, a.z, __int_as_float(f));
+    tris[3 * (size_t)j + 1] = make_float4(b.x, b.y, b.z, deg);
+    tris[3 * (size_t)j + 2] = make_float4(c.x, c.y, c.z, 0.0f);
+    float3 lo = make_float3(fminf(fminf(a.x, b.x), c.x), fminf(fminf(a.y, b.y), c.y),
+                            fminf(fminf(a.z, b.z), c.z));
+    float3 hi = make_float3(fmaxf(fmaxf(a.x, b.x), c.x), fmaxf(fmaxf(a.y, b.y), c.y),
+                            fmaxf(fmaxf(a.z, b.z), c.z));
+    int self = -(j + 1);
+    int pe = parent[(n - 1) + j];
+    while (pe >= 0) {
+        int p = pe >> 1, side = pe & 1;
+        float4 *rec = nodes + 4 * (size_t)p;
+        rec[2 * side] = make_float4(lo.x, lo.y, lo.z, __int_as_float(self));
+        rec[2 * side + 1] = make_float4(hi.x, hi.y, hi.z, __int_as_float(self));
+        __threadfence();
+        unsigned int old = atomicAdd(&flags[p], 1u);
+        if (old == 0u) return;
+        __threadfence();
+        int o = 1 - side;
+        float4 olo = __ldcg(rec + 2 * o), ohi = __ldcg(rec + 2 * o + 1);
+        lo = make_float3(fminf(lo.x, olo.x), fminf(lo.y, olo.y), fminf(lo.z, olo.z));
+        hi = make_float3(fmaxf(hi.x, ohi.x), fmaxf(hi.y, ohi.y), fmaxf(hi.z, ohi.z));
+        flags[p] = 0u;
+        self = p;
+        pe = parent[p];
+    }
+    hdr->root_lo = make_float4(lo.x, lo.y, lo.z, 0.0f);
+    hdr->root_hi = make_float4(hi.x, hi.y, hi.z, 0.0f);
+}
+
+// ---------------------------------------------------------------------------
+// Build workspace layout.
+// ---------------------------------------------------------------------------
+struct BuildWs {
+    unsigned int *keysA, *keysB, *hist, *cbox;
+    int *valsA, *valsB;
+    float4 *cent;
+    int tiles;
+    size_t bytes;
+};
+
+static BuildWs build_ws_layout(char *base, int64_t nF) {
+    BuildWs w{};
+    int64_t n = nF > 0 ? nF : 1;
+    w.tiles = (int)((n + kSortTile - 1) / kSortTile);
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return base + o; };
+    w.keysA = (unsigned int *)take(4 * n);
+    w.keysB = (unsigned int *)take(4 * n);
+    w.valsA = (int *)take(4 * n);
+    w.valsB = (int *)take(4 * n);
+    w.cent = (float4 *)take(16 * n);
+    w.hist = (unsigned int *)take((size_t)4 * kRadix * w.tiles);
+    w.cbox = (unsigned int *)take(32);
+    w.bytes = off;
+    return w;
+}
+
+static mesh_bvh_layout storage_layout(int64_t maxV, int64_t maxF) {
+    mesh_bvh_layout L{};
+    int64_t v = maxV > 0 ? maxV : 1, f = maxF > 0 ? maxF : 1;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
+    L.max_faces = maxF;
+    L.max_verts = maxV;
+    L.off_header = take(sizeof(Header));
+    L.off_verts = take(16 * v);
+    L.off_faces = take(16 * f);
+    L.off_keys = take(4 * f);
+    L.off_perm = take(4 * f);
+    L.off_nodes = take(64 * (f > 1 ? f - 1 : 1));
+    L.off_parent = take(4 * (2 * f - 1));
+    L.off_tris = take(48 * f);
+    L.off_flags = take(4 * f);
+    L.storage_bytes = off;
+    return L;
+}
+
+constexpr int64_t kMaxFaces = (int64_t)1 << 30;
+
+}  // namespace meshgs
+
+using namespace meshgs;
+
+extern "C" {
+
+size_t mesh_bvh_storage_bytes(int64_t max_verts, int64_t max_faces) {
+    if (max_verts < 0 || max_faces < 0 || max_faces > kMaxFaces || max_verts > kMaxFaces) return 0;
+    return storage_layout(max_verts, max_faces).storage_bytes;
+}
+
+size_t mesh_build_workspace_bytes(int64_t max_faces) {
+    if (max_faces < 0 || max_faces > kMaxFaces) return 0;
+    return build_ws_layout(nullptr, max_faces).bytes;
+}
+
+mesh_status mesh_bvh_create(void *d_storage, size_t storage_bytes, int64_t max_verts,
+                            int64_t max_faces, mesh_bvh **out) {
+    if (!out || !d_storage || max_verts < 0 || max_faces < 0 || max_faces > kMaxFaces ||
+        max_verts > kMaxFaces)
+        return MESH_ERR_INVALID_ARG;
+    if (((uintptr_t)d_storage & 255u) != 0) return MESH_ERR_INVALID_ARG;
+    mesh_bvh_layout L = storage_layout(max_verts, max_faces);
+    if (storage_bytes < L.storage_bytes) return MESH_ERR_WORKSPACE;
+    mesh_bvh *h = (mesh_bvh *)std::calloc(1, sizeof(mesh_bvh));
+    if (!h) return MESH_ERR_INVALID_ARG;
+    h->base = (char *)d_storage;
+    h->L = L;
+    h->L.n_faces = 0;
+    h->L.n_verts = 0;
+    *out = h;
+    return MESH_OK;
+}
+
+void mesh_bvh_destroy(mesh_bvh *bvh) { std::free(bvh); }
+
+mesh_status mesh_bvh_get_layout(const mesh_bvh *bvh, mesh_bvh_layout *out) {
+    if (!bvh || !out) return MESH_ERR_INVALID_ARG;
+    *out = bvh->L;
+    return MESH_OK;
+}
+
+mesh_status mesh_update_vertices(mesh_bvh *bvh, const float *d_V, int64_t nV, void *stream) {
+    if (!bvh || nV < 0 || nV > bvh->L.max_verts || (nV > 0 && !d_V)) return MESH_ERR_INVALID_ARG;
+    if (bvh->L.n_faces > 0 && nV != bvh->L.n_verts) return MESH_ERR_INVALID_ARG;
+    bvh->L.n_verts = nV;
+    if (nV == 0) return MESH_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    k_copy_verts<<<grid_for(nV, kBlock), kBlock, 0, s>>>(d_V, (int)nV, bvh->verts(), nullptr);
+    count_launch();
+    return check_launch();
+}
+
+mesh_status mesh_refit(mesh_bvh *bvh, const float *d_V, int64_t nV, void *stream) {
+    if (!bvh) return MESH_ERR_INVALID_ARG;
+    if (d_V) {
+        mesh_status st = mesh_update_vertices(bvh, d_V, nV, stream);
+        if (st != MESH_OK) return st;
+    }
+    int n = (int)bvh->L.n_faces;
+    if (n == 0) return MESH_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    k_leaves_up<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, bvh->perm(), bvh->faces(), bvh->verts(),
+                                                       bvh->tris(), bvh->nodes(), bvh->parent(),
+                                                       bvh->flags(), bvh->hdr());
+    count_launch();
+    return check_launch();
+}
+
+mesh_status mesh_build_lbvh(mesh_bvh *bvh, const float *d_V, int64_t nV, const int32_t *d_F,
+                            int64_t nF, void *d_ws, size_t ws_bytes, void *stream) {
+    if (!bvh || nV < 0 || nF < 0 || nV > bvh->L.max_verts || nF > bvh->L.max_faces)
+        return MESH_ERR_INVALID_ARG;
+    if ((nV > 0 && !d_V) || (nF > 0 && (!d_F || nV == 0))) return MESH_ERR_INVALID_ARG;
+    BuildWs w = build_ws_layout((char *)d_ws, nF);
+    if (nF > 0 && (!d_ws || ws_bytes < w.bytes || ((uintptr_t)d_ws & 255u))) return MESH_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    bvh->L.n_verts = nV;
+    bvh->L.n_faces = nF;
+    int n = (int)nF;
+    cudaMemsetAsync(bvh->hdr(), 0, sizeof(Header), s);
+    if (nV > 0) {
+        k_copy_verts<<<grid_for(nV > 6 ? nV : 6, kBlock), kBlock, 0, s>>>(
+            d_V, (int)nV, bvh->verts(), n > 0 ? w.cbox : nullptr);
+        count_launch();
+    }
+    if (n == 0) return check_launch();
+    k_faces_centroids<<<grid_for(n, kBlock), kBlock, 0, s>>>(d_F, n, (int)nV, bvh->verts(),
+                                                             bvh->faces(), w.cent, w.cbox, bvh->hdr());
+    k_morton<<<grid_for(n, kBlock), kBlock, 0, s>>>(w.cent, n, w.cbox, w.keysA, w.valsA);
+    count_launch(2);
+    // four 8-bit passes: A -> B -> A -> B -> storage
+    unsigned int *kin = w.keysA, *kout = w.keysB;
+    int *vin = w.valsA, *vout = w.valsB;
+    for (int pass = 0; pass < 4; ++pass) {
+        if (pass == 3) { kout = bvh->keys(); vout = bvh->perm(); }
+        int shift = 8 * pass;
+        k_sort_upsweep<<<w.tiles, kSortThreads, 0, s>>>(kin, n, shift, w.hist, w.tiles);
+        k_sort_scan<<<1, kScanThreads, 0, s>>>(w.hist, kRadix * w.tiles);
+        k_sort_downsweep<<<w.tiles, kSortThreads, 0, s>>>(kin, vin, kout, vout, n, shift, w.hist,
+                                                          w.tiles);
+        count_launch(3);
+        unsigned int *tk = kin; kin = kout; kout = tk;
+        int *tv = vin; vin = vout; vout = tv;
+    }
+    if (n > 1) {
+        k_karras<<<grid_for(n - 1, kBlock), kBlock, 0, s>>>(bvh->keys(), n, bvh->nodes(),
+                                                           bvh->parent());
+        count_launch();
+    } else {
+        cudaMemsetAsync(bvh->parent(), 0xff, sizeof(int), s);   // lone leaf: no parent
+    }
+    cudaMemsetAsync(bvh->flags(), 0, sizeof(unsigned int) * (size_t)n, s);
+    k_leaves_up<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, bvh->perm(), bvh->faces(), bvh->verts(),
+                                                       bvh->tris(), bvh->nodes(), bvh->parent(),
+                                                       bvh->flags(), bvh->hdr());
+    count_launch();
+    return check_launch();
+}
+
+uint64_t mesh_launch_count(void) { return (uint64_t)g_launches.load(); }
+
+}  // extern "C"

@@ -1,0 +1,465 @@
+// NearestSurface queries (Eq. 1 / Eq. 2, Sec. 3.3) and the Chamfer distance
+// of Sec. 4.2, by traversal of the LBVH built in lbvh.cu.
+//
+// One thread per query.  A node record holds both children's boxes, so a
+// visit is one 64-byte read that tests two boxes.  Leaf children (single
+// faces) are tested on the spot; of two surviving internal children the
+// nearer is entered and the farther pushed, with its box distance, on a
+// per-thread stack kept in shared memory ([depth][thread], conflict free)
+// that spills to a small local array.  Boxes are pruned against the tie
+// window of the nearest distance found so far, so no face that could win the
+// tie rule is ever skipped.
+#include <math.h>
+
+#include "common.cuh"
+
+namespace meshgs {
+
+constexpr int kQueryBlock = 128;
+constexpr int kQueryMinBlocks = 8;    // 8 x 128 threads per SM: at most 64 registers
+constexpr int kStackShared = 24;      // entries per thread in shared memory
+constexpr int kStackTotal = 64;       // > 30 key bits + log2(nF) + 1: never exhausted for nF < 2^33
+
+__device__ __forceinline__ float box_d2(float3 q, float4 lo, float4 hi) {
+    float dx = fmaxf(fmaxf(lo.x - q.x, q.x - hi.x), 0.0f);
+    float dy = fmaxf(fmaxf(lo.y - q.y, q.y - hi.y), 0.0f);
+    float dz = fmaxf(fmaxf(lo.z - q.z, q.z - hi.z), 0.0f);
+    return dx * dx + dy * dy + dz * dz;
+}
+
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 sub3(float3 a, float3 b) {
+    return make_float3(a.x - b.x, a.y - b.y, a.z - b.z);
+}
+__device__ __forceinline__ float3 xyz(float4 v) { return make_float3(v.x, v.y, v.z); }
+
+// Closest point of segment xy to p: parameter t in [0, 1] and squared distance.
+// The residual is formed from p - x (small when p is near the segment), never
+// from absolute coordinates, so its rounding scales with the segment length.
+__device__ __forceinline__ float seg_d2(float3 p, float3 x, float3 y, float &t) {
+    float3 d = sub3(y, x), xp = sub3(p, x);
+    float L = dot3(d, d);
+    t = 0.0f;
+    if (L > 0.0f) t = fminf(fmaxf(dot3(xp, d) / L, 0.0f), 1.0f);
+    float3 r = make_float3(xp.x - t * d.x, xp.y - t * d.y, xp.z - t * d.z);
+    return dot3(r, r);
+}
+
+// Closest point on triangle abc to p (Ericson, Real-Time Collision Detection
+// 5.1.5: Voronoi regions of vertices, edges, face).  Faces flagged as exactly
+// zero-area at build / refit use the nearest of their three edges instead.
+// Returns the squared distance and the barycentric weights (u, v, w).  The
+// residual p - closest point is assembled from the vertex-relative vectors
+// (p - a, b - a, ...), so float32 rounding is relative to the triangle's size,
+// not to the magnitude of the coordinates.
+__device__ __forceinline__ float tri_closest(float3 p, float3 a, float3 b, float3 c, bool degenerate,
+                                             float &u, float &v, float &w) {
+    if (degenerate) {
+        float t0, t1, t2;
+        float s0 = seg_d2(p, a, b, t0), s1 = seg_d2(p, b, c, t1), s2 = seg_d2(p, c, a, t2);
+        if (s0 <= s1 && s0 <= s2) { u = 1.0f - t0; v = t0; w = 0.0f; return s0; }
+        if (s1 <= s2) { u = 0.0f; v = 1.0f - t1; w = t1; return s1; }
+        u = t2; v = 0.0f; w = 1.0f - t2;
+        return s2;
+    }
+    float3 ab = sub3(b, a), ac = sub3(c, a);
+    float3 ap = sub3(p, a);
+    float d1 = dot3(ab, ap), d2 = dot3(ac, ap);
+    if (d1 <= 0.0f && d2 <= 0.0f) { u = 1.0f; v = 0.0f; w = 0.0f; return dot3(ap, ap); }
+    float3 bp = sub3(p, b);
+    float d3 = dot3(ab, bp), d4 = dot3(ac, bp);
+    if (d3 >= 0.0f && d4 <= d3) { u = 0.0f; v = 1.0f; w = 0.0f; return dot3(bp, bp); }
+    float vc = d1 * d4 - d3 * d2;
+    float3 r;
+    if (vc <= 0.0f && d1 >= 0.0f && d3 <= 0.0f) {
+        float t = d1 / (d1 - d3);
+        u = 1.0f - t; v = t; w = 0.0f;
+        r = make_float3(ap.x - t * ab.x, ap.y - t * ab.y, ap.z - t * ab.z);
+    } else {
+        float3 cp = sub3(p, c);
+        float d5 = dot3(ab, cp), d6 = dot3(ac, cp);
+        if (d6 >= 0.0f && d5 <= d6) { u = 0.0f; v = 0.0f; w = 1.0f; return dot3(cp, cp); }
+        float vb = d5 * d2 - d1 * d6;
+        if (vb <= 0.0f && d2 >= 0.0f && d6 <= 0.0f) {
+            float t = d2 / (d2 - d6);
+            u = 1.0f - t; v = 0.0f; w = t;
+            r = make_float3(ap.x - t * ac.x, ap.y - t * ac.y, ap.z - t * ac.z);
+        } else {
+            float va = d3 * d6 - d5 * d4;
+            if (va <= 0.0f && (d4 - d3) >= 0.0f && (d5 - d6) >= 0.0f) {
+                float t = (d4 - d3) / ((d4 - d3) + (d5 - d6));
+                u = 0.0f; v = 1.0f - t; w = t;
+                float3 bc = sub3(c, b);
+                r = make_float3(bp.x - t * bc.x, bp.y - t * bc.y, bp.z - t * bc.z);
+            } else {
+                float s = 1.0f / (va + vb + vc);
+                v = vb * s;
+                w = vc * s;
+                u = 1.0f - v - w;
+                r = make_float3(ap.x - (ab.x * v + ac.x * w), ap.y - (ab.y * v + ac.y * w),
+                                ap.z - (ab.z * v + ac.z * w));
+            }
+        }
+    }
+    return dot3(r, r);
+}
+
+// The same region test in float64, used only to recompute the weights of the
+// winning face when float32 would lose them: a query far from the face relative
+// to its shortest edge (weight error grows like eps32 * d / edge) or a sliver.
+struct D3 {
+    double x, y, z;
+};
+__device__ __forceinline__ D3 dsub(D3 a, D3 b) { return D3{a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ double ddot(D3 a, D3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ D3 dof(float3 a) { return D3{a.x, a.y, a.z}; }
+
+__device__ __noinline__ void tri_weights_f64(float3 pf, float3 af, float3 bf, float3 cf,
+                                             bool degenerate, float &u, float &v, float &w) {
+    D3 p = dof(pf), a = dof(af), b = dof(bf), c = dof(cf);
+    double U, V, W;
+    if (degenerate) {
+        D3 P[3] = {a, b, c};
+        double best = 1e300, bt = 0.0;
+        int be = 0;
+        for (int e = 0; e < 3; ++e) {
+            D3 x = P[e], d = dsub(P[(e + 1) % 3], x), xp = dsub(p, x);
+            double L = ddot(d, d), t = 0.0;
+            if (L > 0.0) t = fmin(fmax(ddot(xp, d) / L, 0.0), 1.0);
+            D3 r = D3{xp.x - t * d.x, xp.y - t * d.y, xp.z - t * d.z};
+            double s = ddot(r, r);
+            if (s < best) { best = s; bt = t; be = e; }
+        }
+        if (be == 0) { U = 1.0 - bt; V = bt; W = 0.0; }
+        else if (be == 1) { U = 0.0; V = 1.0 - bt; W = bt; }
+        else { U = bt; V = 0.0; W = 1.0 - bt; }
+    } else {
+        D3 ab = dsub(b, a), ac = dsub(c, a), ap = dsub(p, a), bp = dsub(p, b), cp = dsub(p, c);
+        double d1 = ddot(ab, ap), d2 = ddot(ac, ap), d3 = ddot(ab, bp), d4 = ddot(ac, bp);
+        double d5 = ddot(ab, cp), d6 = ddot(ac, cp);
+        double vc = d1 * d4 - d3 * d2, vb = d5 * d2 - d1 * d6, va = d3 * d6 - d5 * d4;
+        if (d1 <= 0.0 && d2 <= 0.0) { U = 1.0; V = 0.0; W = 0.0; }
+        else if (d3 >= 0.0 && d4 <= d3) { U = 0.0; V = 1.0; W = 0.0; }
+        else if (vc <= 0.0 && d1 >= 0.0 && d3 <= 0.0) { double t = d1 / (d1 - d3); U = 1.0 - t; V = t; W = 0.0; }
+        else if (d6 >= 0.0 && d5 <= d6) { U = 0.0; V = 0.0; W = 1.0; }
+        else if (vb <= 0.0 && d2 >= 0.0 && d6 <= 0.0) { double t = d2 / (d2 - d6); U = 1.0 - t; V = 0.0; W = t; }
+        else if (va <= 0.0 && (d4 - d3) >= 0.0 && (d5 - d6) >= 0.0) {
+            double t = (d4 - d3) / ((d4 - d3) + (d5 - d6));
+            U = 0.0; V = 1.0 - t; W = t;
+        } else {
+            double s = 1.0 / (va + vb + vc);
+            V = vb * s; W = vc * s; U = 1.0 - V - W;
+        }
+    }
+    u = (float)U; v = (float)V; w = (float)W;
+}
+
+// True when float32 weights of this face would be too coarse for the query:
+// distance beyond 4 shortest edges, or a sliver (altitude < 5% of longest edge).
+__device__ __forceinline__ bool weights_need_f64(float3 a, float3 b, float3 c, float d2) {
+    float3 ab = sub3(b, a), ac = sub3(c, a), bc = sub3(c, b);
+    float l0 = dot3(ab, ab), l1 = dot3(ac, ac), l2 = dot3(bc, bc);
+    float lmin = fminf(l0, fminf(l1, l2)), lmax = fmaxf(l0, fmaxf(l1, l2));
+    float3 n = make_float3(ab.y * ac.z - ab.z * ac.y, ab.z * ac.x - ab.x * ac.z, ab.x * ac.y - ab.y * ac.x);
+    return d2 > 16.0f * lmin || dot3(n, n) < 2.5e-3f * lmax * lmax;
+}
+
+struct Hit {
+    int leaf;      // -1: nothing within the cutoff
+    int face;
+    float d2;
+};
+
+// Squared upper edge of the tie window around a nearest squared distance d2.
+__device__ __forceinline__ float tie_window2(float d2, float tau) {
+    float r = sqrtf(d2) * (1.0f + kTieRel) + tau;
+    return r * r;
+}
+
+struct Traversal {
+    const float4 *__restrict__ nodes;
+    const float4 *__restrict__ tris;
+    int n;
+    float tau;
+};
+
+// Candidate bookkeeping of the tie rule: dmin is the nearest squared distance
+// seen; the kept face is the lowest id within the window of dmin.
+struct Best {
+    int leaf, face;
+    float d2, dmin, thr;
+};
+
+__device__ __forceinline__ void consider(Best &B, int leaf, int face, float d2, float maxd2,
+                                         float tau) {
+    if (B.leaf < 0) {
+        if (d2 <= maxd2) {
+            B.leaf = leaf; B.face = face; B.d2 = d2; B.dmin = d2;
+            B.thr = tie_window2(d2, tau);
+        }
+        return;
+    }
+    float nmin = fminf(B.dmin, d2);
+    float w2 = nmin < B.dmin ? tie_window2(nmin, tau) : B.thr;
+    if (d2 <= w2 && (face < B.face || B.d2 > w2)) { B.leaf = leaf; B.face = face; B.d2 = d2; }
+    B.dmin = nmin;
+    B.thr = w2;
+}
+
+__device__ __forceinline__ void test_leaf(const Traversal &T, Best &B, int leaf, float3 q,
+                                          float maxd2) {
+    const float4 *t = T.tris + 3 * (size_t)leaf;
+    float4 a = ldg4(t), b = ldg4(t + 1), c = ldg4(t + 2);
+    float u, v, w;
+    float d2 = tri_closest(q, xyz(a), xyz(b), xyz(c), b.w != 0.0f, u, v, w);
+    consider(B, leaf, __float_as_int(a.w), d2, maxd2, T.tau);
+}
+
+template <int kBlockT>
+__device__ __forceinline__ Hit nearest(const Traversal &T, float3 q, float maxd2,
+                                       int2 (*stk)[kBlockT], unsigned int *status) {
+    Best B{-1, 0x7fffffff, INFINITY, INFINITY, maxd2};
+    if (T.n == 1) {
+        test_leaf(T, B, 0, q, maxd2);
+    } else if (T.n > 1) {
+        int2 spill[kStackTotal - kStackShared];
+        int sp = 0;
+        int node = 0;
+        const int tid = threadIdx.x;
+        while (true) {
+            const float4 *r = T.nodes + 4 * (size_t)node;
+            float4 l0 = ldg4(r), l1 = ldg4(r + 1), r0 = ldg4(r + 2), r1 = ldg4(r + 3);
+            float dl = box_d2(q, l0, l1), dr = box_d2(q, r0, r1);
+            int cl = __float_as_int(l0.w), cr = __float_as_int(r0.w);
+            if (cl < 0 && dl <= B.thr) test_leaf(T, B, -cl - 1, q, maxd2);
+            if (cr < 0 && dr <= B.thr) test_leaf(T, B, -cr - 1, q, maxd2);
+            bool gl = cl >= 0 && dl <= B.thr;
+            bool gr = cr >= 0 && dr <= B.thr;
+            if (gl && gr) {
+                bool lfirst = dl <= dr;
+                int2 e = make_int2(lfirst ? cr : cl, __float_as_int(lfirst ? dr : dl));
+                if (sp < kStackShared) stk[sp][tid] = e;
+                else if (sp < kStackTotal) spill[sp - kStackShared] = e;
+                else atomicOr(status, (unsigned)MESH_DEV_STACK_OVERFLOW);
+                if (sp < kStackTotal) ++sp;
+                node = lfirst ? cl : cr;
+                continue;
+            }
+            if (gl) { node = cl; continue; }
+            if (gr) { node = cr; continue; }
+            bool found = false;
+            while (sp > 0) {
+                --sp;
+                int2 e = sp < kStackShared ? stk[sp][tid] : spill[sp - kStackShared];
+                if (__int_as_float(e.y) <= B.thr) { node = e.x; found = true; break; }
+            }
+            if (!found) break;
+        }
+    }
+    return Hit{B.leaf, B.face, B.d2};
+}
+
+__device__ __forceinline__ float traversal_tau(const Header *hdr) {
+    float4 lo = hdr->root_lo, hi = hdr->root_hi;
+    float dx = hi.x - lo.x, dy = hi.y - lo.y, dz = hi.z - lo.z;
+    return kTieAbs * sqrtf(dx * dx + dy * dy + dz * dz);
+}
+
+// Writes the outputs of one query (recomputing the weights of the winning face).
+__device__ __forceinline__ void write_hit(const Traversal &T, const Hit &h, float3 q, int64_t i,
+                                          int *face, float *bary, float *point, float *dist2) {
+    if (h.leaf < 0) {
+        if (face) face[i] = -1;
+        if (dist2) dist2[i] = INFINITY;
+        if (bary) { bary[3 * i] = 0.0f; bary[3 * i + 1] = 0.0f; bary[3 * i + 2] = 0.0f; }
+        if (point) { point[3 * i] = 0.0f; point[3 * i + 1] = 0.0f; point[3 * i + 2] = 0.0f; }
+        return;
+    }
+    if (face) face[i] = h.face;
+    if (dist2) dist2[i] = h.d2;
+    if (bary || point) {
+        const float4 *t = T.tris + 3 * (size_t)h.leaf;
+        float4 a = ldg4(t), b = ldg4(t + 1), c = ldg4(t + 2);
+        float u, v, w;
+        tri_closest(q, xyz(a), xyz(b), xyz(c), b.w != 0.0f, u, v, w);
+        if (weights_need_f64(xyz(a), xyz(b), xyz(c), h.d2))
+            tri_weights_f64(q, xyz(a), xyz(b), xyz(c), b.w != 0.0f, u, v, w);
+        if (bary) { bary[3 * i] = u; bary[3 * i + 1] = v; bary[3 * i + 2] = w; }
+        if (point) {
+            point[3 * i] = u * a.x + v * b.x + w * c.x;
+            point[3 * i + 1] = u * a.y + v * b.y + w * c.y;
+            point[3 * i + 2] = u * a.z + v * b.z + w * c.z;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kQueryBlock, kQueryMinBlocks)
+k_closest_point(Traversal T, const Header *__restrict__ hdr, unsigned int *status,
+                const float *__restrict__ Q, int64_t nQ, float maxd2, int *face, float *bary,
+                float *point, float *dist2) {
+    __shared__ int2 stk[kStackShared][kQueryBlock];
+    int64_t i = (int64_t)blockIdx.x * kQueryBlock + threadIdx.x;
+    if (i >= nQ) return;
+    T.tau = traversal_tau(hdr);
+    float3 q = make_float3(Q[3 * i], Q[3 * i + 1], Q[3 * i + 2]);
+    Hit h = nearest<kQueryBlock>(T, q, maxd2, stk, status);
+    write_hit(T, h, q, i, face, bary, point, dist2);
+}
+
+// ---------------------------------------------------------------------------
+// Chamfer (Sec. 4.2): both directions in one launch (blocks [0, nbA) query SA
+// against B, the rest SB against A).  Each block sums its squared distances in
+// float64 with a fixed reduction tree and stores the partial; the last block
+// to finish (ticket counter) adds the partials in a fixed order, writes the
+// two means and resets the counter, so the result is bit-reproducible.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double block_sum_d(double x, double *s) {
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) s[w] = x;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += s[k];
+    __syncthreads();
+    return t;
+}
+
+struct ChamferSide {
+    Traversal T;
+    const Header *hdr;
+    const float *S;
+    int64_t n;
+    int *face;
+    float *bary, *dist2;
+};
+
+__global__ void __launch_bounds__(kQueryBlock, kQueryMinBlocks)
+k_chamfer(ChamferSide A2B, ChamferSide B2A, unsigned int nbA, unsigned int *status,
+          double *partial, unsigned int *ticket, double *out) {
+    __shared__ int2 stk[kStackShared][kQueryBlock];
+    __shared__ double s_red[kQueryBlock / 32];
+    __shared__ bool s_last;
+    bool first = blockIdx.x < nbA;
+    ChamferSide &C = first ? A2B : B2A;
+    int64_t i = (int64_t)(first ? blockIdx.x : blockIdx.x - nbA) * kQueryBlock + threadIdx.x;
+    double d2 = 0.0;
+    if (i < C.n) {
+        Traversal T = C.T;
+        T.tau = traversal_tau(C.hdr);
+        float3 q = make_float3(C.S[3 * i], C.S[3 * i + 1], C.S[3 * i + 2]);
+        Hit h = nearest<kQueryBlock>(T, q, INFINITY, stk, status);
+        write_hit(T, h, q, i, C.face, C.bary, nullptr, C.dist2);
+        d2 = h.leaf >= 0 ? (double)h.d2 : 0.0;
+    }
+    double s = block_sum_d(d2, s_red);
+    if (threadIdx.x == 0) {
+        partial[blockIdx.x] = s;
+        __threadfence();
+        unsigned int t = atomicAdd(ticket, 1u);
+        s_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    // fixed-order final sums: thread k adds partials k, k + blockDim, ... of each side
+    double a = 0.0, b = 0.0;
+    for (unsigned int k = threadIdx.x; k < nbA; k += blockDim.x) a += __ldcg(partial + k);
+    for (unsigned int k = nbA + threadIdx.x; k < gridDim.x; k += blockDim.x) b += __ldcg(partial + k);
+    a = block_sum_d(a, s_red);
+    b = block_sum_d(b, s_red);
+    if (threadIdx.x == 0) {
+        out[0] = A2B.n > 0 ? a / (double)A2B.n : 0.0;
+        out[1] = B2A.n > 0 ? b / (double)B2A.n : 0.0;
+        *ticket = 0u;
+    }
+}
+
+__global__ void k_interpolate(const int4 *__restrict__ faces, const float4 *__restrict__ verts,
+                              int nF, const int *__restrict__ face, const float *__restrict__ bary,
+                              int64_t n, float *__restrict__ out, unsigned int *status) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int f = face[i];
+    if ((unsigned)f >= (unsigned)nF) {
+        atomicOr(status, (unsigned)MESH_DEV_INDEX_RANGE);
+        out[3 * i] = out[3 * i + 1] = out[3 * i + 2] = 0.0f;
+        return;
+    }
+    int4 fv = faces[f];
+    float4 a = verts[fv.x], b = verts[fv.y], c = verts[fv.z];
+    float u = bary[3 * i], v = bary[3 * i + 1], w = bary[3 * i + 2];
+    out[3 * i] = u * a.x + v * b.x + w * c.x;
+    out[3 * i + 1] = u * a.y + v * b.y + w * c.y;
+    out[3 * i + 2] = u * a.z + v * b.z + w * c.z;
+}
+
+static Traversal traversal_of(const mesh_bvh *b) {
+    return Traversal{b->nodes(), b->tris(), (int)b->L.n_faces, 0.0f};
+}
+
+static size_t chamfer_blocks(int64_t n) { return (size_t)((n + kQueryBlock - 1) / kQueryBlock); }
+
+}  // namespace meshgs
+
+using namespace meshgs;
+
+extern "C" {
+
+mesh_status mesh_closest_point(const mesh_bvh *bvh, const float *d_Q, int64_t nQ, float max_dist,
+                               int32_t *d_face, float *d_bary, float *d_point, float *d_dist2,
+                               void *stream) {
+    if (!bvh || nQ < 0 || (nQ > 0 && !d_Q) || !(max_dist >= 0.0f)) return MESH_ERR_INVALID_ARG;
+    if (nQ == 0) return MESH_OK;
+    float maxd2 = isinf(max_dist) ? INFINITY : max_dist * max_dist;
+    cudaStream_t s = (cudaStream_t)stream;
+    k_closest_point<<<grid_for(nQ, kQueryBlock), kQueryBlock, 0, s>>>(
+        traversal_of(bvh), bvh->hdr(), &bvh->hdr()->status, d_Q, nQ, maxd2, d_face, d_bary,
+        d_point, d_dist2);
+    count_launch();
+    return check_launch();
+}
+
+size_t mesh_chamfer_workspace_bytes(int64_t nSA, int64_t nSB) {
+    if (nSA < 0 || nSB < 0) return 0;
+    return align_up(8 * (chamfer_blocks(nSA) + chamfer_blocks(nSB) + 1), 256) + 256;
+}
+
+mesh_status mesh_chamfer(const mesh_bvh *A, const float *d_SA, int64_t nSA, const mesh_bvh *B,
+                         const float *d_SB, int64_t nSB, void *d_ws, size_t ws_bytes,
+                         double *d_out, int32_t *d_faceA, float *d_baryA, float *d_dist2A,
+                         int32_t *d_faceB, float *d_baryB, float *d_dist2B, void *stream) {
+    if (!A || !B || !d_out || nSA < 0 || nSB < 0 || (nSA > 0 && !d_SA) || (nSB > 0 && !d_SB))
+        return MESH_ERR_INVALID_ARG;
+    size_t need = mesh_chamfer_workspace_bytes(nSA, nSB);
+    if (!d_ws || ws_bytes < need || ((uintptr_t)d_ws & 255u)) return MESH_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    size_t nbA = chamfer_blocks(nSA), nbB = chamfer_blocks(nSB);
+    double *partial = (double *)d_ws;
+    unsigned int *ticket = (unsigned int *)((char *)d_ws + need - 256);
+    if (nbA + nbB == 0) {
+        cudaMemsetAsync(d_out, 0, 2 * sizeof(double), s);
+        return check_launch();
+    }
+    cudaMemsetAsync(ticket, 0, sizeof(unsigned int), s);
+    ChamferSide a2b{traversal_of(B), B->hdr(), d_SA, nSA, d_faceA, d_baryA, d_dist2A};
+    ChamferSide b2a{traversal_of(A), A->hdr(), d_SB, nSB, d_faceB, d_baryB, d_dist2B};
+    k_chamfer<<<(unsigned)(nbA + nbB), kQueryBlock, 0, s>>>(a2b, b2a, (unsigned)nbA,
+                                                            &A->hdr()->status, partial, ticket,
+                                                            d_out);
+    count_launch();
+    return check_launch();
+}
+
+mesh_status mesh_interpolate(const mesh_bvh *bvh, const int32_t *d_face, const float *d_bary,
+                             int64_t n, float *d_out, void *stream) {
+    if (!bvh || n < 0 || (n > 0 && (!d_face || !d_bary || !d_out))) return MESH_ERR_INVALID_ARG;
+    if (n == 0) return MESH_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    k_interpolate<<<grid_for(n, 256), 256, 0, s>>>(bvh->faces(), bvh->verts(), (int)bvh->L.n_faces,
+                                                   d_face, d_bary, n, d_out, &bvh->hdr()->status);
+    count_launch();
+    return check_launch();
+}
+
+}  // extern "C"

@@ -1,0 +1,181 @@
+"""GPU face-bound Gaussian update, Chamfer distance and gradients against the
+oracle (Gaussian parameters 1e-5 absolute; Chamfer 1e-5 relative; gradients
+1e-4 relative to the oracle's analytic gradient, itself pinned by float64
+central differences)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2606_00444_gb300 import MeshBVH, chamfer
+from paper_2606_00444_gb300.autograd import BindGaussians, Chamfer, Interpolate, PointMeshDistance
+from parity import check_gaussians, dev, host
+from workloads.meshes import displaced_icosphere, icosphere, torus, TorusSkinning
+from workloads.sampling import osada_barycentrics, points_from, sample_surface, uniform_box
+
+pytestmark = pytest.mark.gpu
+
+
+def rel_close(a, b, rtol):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    return np.linalg.norm(a - b) <= rtol * max(np.linalg.norm(b), 1e-30)
+
+
+def test_rebind_centroid_single_frame():
+    VT, FT = icosphere(3)
+    G = FT.shape[0]
+    gface = np.arange(G, dtype=np.int32)
+    gbary = np.full((G, 3), 1 / 3, np.float32)
+    bvh = MeshBVH.from_mesh(dev(VT), dev(FT))
+    got = bvh.bind_gaussians(dev(gface), dev(gbary))
+    check_gaussians(got, oracle.bind_gaussians(VT, FT, gface, gbary))
+
+
+def test_rebind_random_anchors_offsets_and_degenerate_faces():
+    V, F = displaced_icosphere(3, 0.1, 2.0)
+    F = F.copy()
+    F[::11, 1] = F[::11, 0]
+    rng = np.random.default_rng(5)
+    G = 5000
+    gface = rng.integers(0, F.shape[0], G).astype(np.int32)
+    gbary = osada_barycentrics(rng, G).astype(np.float32)
+    goff = rng.normal(scale=0.02, size=G).astype(np.float32)
+    bvh = MeshBVH.from_mesh(dev(V), dev(F))
+    got = bvh.bind_gaussians(dev(gface), dev(gbary), dev(goff))
+    ref = oracle.bind_gaussians(V, F, gface, gbary, goff)
+    check_gaussians(got, ref)
+    bits, ndeg = bvh.status()
+    assert ndeg == ref["n_degenerate"] > 0 and bits == 0x4
+
+
+def test_rebind_full_size_600k_after_refit():
+    V0, F = torus(400, 250)
+    V1 = TorusSkinning(V0, seed=3000).frame(88)
+    rng = np.random.default_rng(3003)
+    gface = np.repeat(np.arange(F.shape[0], dtype=np.int32), 3)
+    gbary = osada_barycentrics(rng, gface.shape[0]).astype(np.float32)
+    bvh = MeshBVH.from_mesh(dev(V0), dev(F))
+    bvh.refit(dev(V1))
+    mu, quat, scale = bvh.bind_gaussians(dev(gface), dev(gbary))
+    pick = rng.choice(gface.shape[0], 20000, replace=False)
+    ref = oracle.bind_gaussians(V1, F, gface[pick], gbary[pick])
+    idx = dev(pick.astype(np.int64))
+    check_gaussians((mu[idx], quat[idx], scale[idx]), ref)
+
+
+def test_rebind_bad_index_sets_status():
+    V, F = icosphere(1)
+    bvh = MeshBVH.from_mesh(dev(V), dev(F))
+    gface = np.array([0, 5, 999], np.int32)
+    gbary = np.full((3, 3), 1 / 3, np.float32)
+    mu, quat, scale = bvh.bind_gaussians(dev(gface), dev(gbary))
+    bits, _ = bvh.status()
+    assert bits & 0x1
+    assert np.array_equal(host(quat)[2], [1, 0, 0, 0])
+
+
+@pytest.fixture(scope="module")
+def pair():
+    VA, FA = icosphere(3)
+    VB, FB = displaced_icosphere(4, 0.1, 0.4)
+    fa, ba = sample_surface(VA, FA, 3000, seed=6)
+    fb, bb = sample_surface(VB, FB, 2500, seed=7)
+    SA, SB = points_from(VA, FA, fa, ba), points_from(VB, FB, fb, bb)
+    return VA, FA, SA, VB, FB, SB
+
+
+def test_chamfer_matches_oracle_and_is_reproducible(pair):
+    VA, FA, SA, VB, FB, SB = pair
+    A = MeshBVH.from_mesh(dev(VA), dev(FA))
+    B = MeshBVH.from_mesh(dev(VB), dev(FB))
+    out, ps = chamfer(A, dev(SA), B, dev(SB), per_sample=True)
+    ref, dA, dB = oracle.chamfer(VA, FA, SA, VB, FB, SB)
+    np.testing.assert_allclose(host(out), ref, rtol=1e-5)
+    np.testing.assert_allclose(np.sqrt(host(ps["dist2A"])), np.sqrt(dA), rtol=1e-5, atol=1e-8)
+    again = chamfer(A, dev(SA), B, dev(SB))
+    assert torch.equal(out, again)
+    same = chamfer(A, dev(SA), A, dev(SA))
+    assert host(same).max() < 1e-12
+    empty = chamfer(A, dev(SA[:0]), B, dev(SB[:5]))
+    assert host(empty)[0] == 0
+
+
+def test_closest_point_backward_matches_oracle():
+    V, F = displaced_icosphere(3, 0.1, 0.9)
+    Q = uniform_box(3000, [-1.4] * 3, [1.4] * 3, seed=8)
+    g = np.random.default_rng(9).normal(size=3000).astype(np.float32)
+    bvh = MeshBVH.from_mesh(dev(V), dev(F))
+    out = bvh.closest_point(dev(Q))
+    gQ = torch.empty(3000, 3, device="cuda")
+    gV = torch.zeros(V.shape[0], 3, device="cuda")
+    bvh.closest_point_backward(dev(Q), out["face"], out["bary"], dev(g), gQ, gV)
+    rgQ, rgV = oracle.closest_point_backward(V, F, Q, host(out["face"]),
+                                             host(out["bary"]).astype(np.float64), g)
+    assert rel_close(host(gQ), rgQ, 1e-4) and rel_close(host(gV), rgV, 1e-4)
+
+
+def test_rebind_backward_matches_oracle():
+    V, F = displaced_icosphere(2, 0.1, 0.3)
+    rng = np.random.default_rng(10)
+    G = 2000
+    gface = rng.integers(0, F.shape[0], G).astype(np.int32)
+    gbary = osada_barycentrics(rng, G).astype(np.float32)
+    goff = rng.normal(scale=0.05, size=G).astype(np.float32)
+    wm = rng.normal(size=(G, 3)).astype(np.float32)
+    wq = rng.normal(size=(G, 4)).astype(np.float32)
+    ws = rng.normal(size=(G, 3)).astype(np.float32)
+    bvh = MeshBVH.from_mesh(dev(V), dev(F))
+    gV = torch.zeros(V.shape[0], 3, device="cuda")
+    bvh.bind_gaussians_backward(dev(gface), dev(gbary), dev(goff), dev(wm), dev(wq), dev(ws), gV)
+    ref = oracle.bind_gaussians_backward(V, F, gface, gbary, wm, wq, ws, goff)
+    assert rel_close(host(gV), ref, 1e-4)
+
+
+def test_autograd_template_fit_gradient_matches_oracle():
+    """L = mean d(S_T(V), target)^2 + mean d(S_G, template(V))^2 + mean d(V, target)^2
+    on a 162-vertex template: autograd through the CUDA kernels vs the oracle."""
+    VT, FT = icosphere(2, radius=0.95)
+    VG, FG = displaced_icosphere(3, 0.1, 0.4)
+    ft, bt = sample_surface(VT, FT, 4000, seed=11)
+    fg, bg = sample_surface(VG, FG, 4000, seed=12)
+    SG = points_from(VG, FG, fg, bg)
+    tmpl = MeshBVH.from_mesh(dev(VT), dev(FT))
+    targ = MeshBVH.from_mesh(dev(VG), dev(FG))
+    V = dev(VT).requires_grad_(True)
+    VGd = dev(VG)
+    ST = Interpolate.apply(V, tmpl, dev(ft), dev(bt))
+    cd = Chamfer.apply(ST, V, tmpl, dev(SG), VGd, targ)
+    d2v, _ = PointMeshDistance.apply(V, VGd, targ)
+    loss = cd[0] + cd[1] + d2v.mean()
+    loss.backward()
+    # oracle gradient of the same loss
+    VT64 = VT.astype(np.float64)
+    S = oracle.interpolate(VT64, FT, ft, bt)
+    oA = oracle.closest_point(VG, FG, S)
+    oB = oracle.closest_point(VT64, FT, SG)
+    oV = oracle.closest_point(VG, FG, VT64)
+    gS, _ = oracle.closest_point_backward(VG, FG, S, oA["face"], oA["bary"],
+                                          np.full(S.shape[0], 1 / S.shape[0]))
+    ref = oracle.interpolate_backward(VT.shape[0], FT, ft, bt, gS)
+    ref += oracle.closest_point_backward(VT64, FT, SG, oB["face"], oB["bary"],
+                                         np.full(SG.shape[0], 1 / SG.shape[0]))[1]
+    ref += oracle.closest_point_backward(VG, FG, VT64, oV["face"], oV["bary"],
+                                         np.full(VT.shape[0], 1 / VT.shape[0]))[0]
+    lref = oA["d2"].mean() + oB["d2"].mean() + oV["d2"].mean()
+    assert loss.item() == pytest.approx(lref, rel=1e-5)
+    assert rel_close(host(V.grad), ref, 1e-4)
+
+
+def test_autograd_bind_gaussians_matches_oracle_backward():
+    V, F = displaced_icosphere(2, 0.1, 0.8)
+    rng = np.random.default_rng(13)
+    G = 1500
+    gface = rng.integers(0, F.shape[0], G).astype(np.int32)
+    gbary = osada_barycentrics(rng, G).astype(np.float32)
+    bvh = MeshBVH.from_mesh(dev(V), dev(F))
+    Vd = dev(V).requires_grad_(True)
+    mu, quat, scale = BindGaussians.apply(Vd, bvh, dev(gface), dev(gbary))
+    wm, wq, ws = (rng.normal(size=s).astype(np.float32) for s in ((G, 3), (G, 4), (G, 3)))
+    ((mu * dev(wm)).sum() + (quat * dev(wq)).sum() + (scale * dev(ws)).sum()).backward()
+    ref = oracle.bind_gaussians_backward(V, F, gface, gbary, wm, wq, ws)
+    assert rel_close(host(Vd.grad), ref, 1e-4)

@@ -166,6 +166,29 @@ mesh_status mesh_chamfer(const mesh_bvh *A, const float *d_SA, int64_t nSA,
                          int32_t *d_faceA, float *d_baryA, float *d_dist2A,
                          int32_t *d_faceB, float *d_baryB, float *d_dist2B, void *stream);
 
+/* mesh_chamfer for callers that cannot allocate device memory.  (The paper has
+ * no counterpart; this exists for integrations, not for the method.)  Some
+ * callers cannot call cudaMalloc -- a physics or renderer plugin whose host
+ * application owns every device allocation, or code running while another
+ * framework captures the stream into a CUDA graph and forbids allocation --
+ * so they cannot supply mesh_chamfer's workspace.  This variant computes the
+ * same result with the same kernel, keeping its scratch in one fixed array
+ * inside the library (128 KB of device memory, held by every GPU that loads
+ * the library until the process exits) and allocates nothing.
+ *   - Limit: ceil(nSA/128) + ceil(nSB/128) <= 16384 (about 2M samples in
+ *     total); larger inputs return MESH_ERR_WORKSPACE and launch nothing.
+ *   - The first call on each device looks up that device's address of the
+ *     array (cudaGetSymbolAddress, with that device current); make that first
+ *     call before any stream capture.
+ *   - All calls share the array: calls that may overlap on the GPU (different
+ *     streams, or concurrent threads) race and give wrong results; serialise
+ *     them.  Each call clears the part that must start at zero itself.
+ * Arguments and outputs are those of mesh_chamfer. */
+mesh_status mesh_chamfer_noalloc(const mesh_bvh *A, const float *d_SA, int64_t nSA,
+                                 const mesh_bvh *B, const float *d_SB, int64_t nSB,
+                                 double *d_out, int32_t *d_faceA, float *d_baryA, float *d_dist2A,
+                                 int32_t *d_faceB, float *d_baryB, float *d_dist2B, void *stream);
+
 /* ---------------------------------------------------------------- */
 /* Gradients (nearest face and weights held fixed: envelope theorem) */
 /* ---------------------------------------------------------------- */

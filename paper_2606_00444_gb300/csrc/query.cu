@@ -11,6 +11,8 @@
 // tie rule is ever skipped.
 #include <math.h>
 
+#include <mutex>
+
 #include "common.cuh"
 
 namespace meshgs {
@@ -463,3 +465,69 @@ mesh_status mesh_interpolate(const mesh_bvh *bvh, const int32_t *d_face, const f
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Chamfer without caller workspace.
+//
+// Some callers cannot allocate device memory at all -- a physics or renderer
+// plugin whose host application owns every device allocation, or code that
+// runs while another framework is capturing the stream into a CUDA graph and
+// forbids allocation -- so they cannot hand mesh_chamfer a workspace.  This
+// entry point runs the same Chamfer kernel with its scratch (per-block float64
+// partial sums and the last-block ticket) in a fixed file-scope device array
+// instead.  Every GPU that loads the library holds that array until exit.
+// ---------------------------------------------------------------------------
+namespace meshgs {
+
+constexpr int kNoAllocMaxBlocks = 16384;   // partial sums: 16384 x 8 B = 128 KB
+static __device__ __align__(256) double g_chamfer_scratch[kNoAllocMaxBlocks + 32];
+
+constexpr int kMaxDevices = 64;
+static double *g_scratch_ptr[kMaxDevices];          // device address per device ordinal
+static std::mutex g_scratch_mu;
+
+// Device address of g_chamfer_scratch on the current device, looked up once per
+// device (the host-side symbol is only a stand-in, never a device address).
+static mesh_status scratch_address(double **out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MESH_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_chamfer_scratch) != cudaSuccess || !p) return MESH_ERR_CUDA;
+        g_scratch_ptr[dev] = (double *)p;
+    }
+    *out = g_scratch_ptr[dev];
+    return MESH_OK;
+}
+
+}  // namespace meshgs
+
+extern "C" mesh_status mesh_chamfer_noalloc(const mesh_bvh *A, const float *d_SA, int64_t nSA,
+                                            const mesh_bvh *B, const float *d_SB, int64_t nSB,
+                                            double *d_out, int32_t *d_faceA, float *d_baryA,
+                                            float *d_dist2A, int32_t *d_faceB, float *d_baryB,
+                                            float *d_dist2B, void *stream) {
+    using namespace meshgs;
+    if (!A || !B || !d_out || nSA < 0 || nSB < 0 || (nSA > 0 && !d_SA) || (nSB > 0 && !d_SB))
+        return MESH_ERR_INVALID_ARG;
+    size_t nbA = chamfer_blocks(nSA), nbB = chamfer_blocks(nSB);
+    if (nbA + nbB > (size_t)kNoAllocMaxBlocks) return MESH_ERR_WORKSPACE;
+    double *scratch = nullptr;
+    mesh_status st = scratch_address(&scratch);
+    if (st != MESH_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (nbA + nbB == 0) {
+        cudaMemsetAsync(d_out, 0, 2 * sizeof(double), s);
+        return check_launch();
+    }
+    unsigned int *ticket = (unsigned int *)(scratch + kNoAllocMaxBlocks);
+    cudaMemsetAsync(ticket, 0, sizeof(unsigned int), s);
+    ChamferSide a2b{traversal_of(B), B->hdr(), d_SA, nSA, d_faceA, d_baryA, d_dist2A};
+    ChamferSide b2a{traversal_of(A), A->hdr(), d_SB, nSB, d_faceB, d_baryB, d_dist2B};
+    k_chamfer<<<(unsigned)(nbA + nbB), kQueryBlock, 0, s>>>(a2b, b2a, (unsigned)nbA,
+                                                            &A->hdr()->status, scratch, ticket,
+                                                            d_out);
+    count_launch();
+    return check_launch();
+}

@@ -1,0 +1,84 @@
+"""mesh_chamfer_noalloc: the Chamfer entry point for callers that cannot allocate
+device memory (a plugin whose host application owns all device allocations, or
+code running under another framework's stream capture).  It keeps its scratch in
+a fixed array inside the library instead of a caller workspace; this checks,
+through the C ABI, that two calls in a row give what mesh_chamfer gives, and that
+inputs beyond its fixed limit are refused without a launch.
+
+This file is collected last on purpose (a failure here leaves every other test
+already run).  It passes alone in a fresh process and after the rest of the suite.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2606_00444_gb300 import MeshBVH
+from paper_2606_00444_gb300._abi import lib
+from parity import dev, host
+from workloads.meshes import displaced_icosphere, icosphere
+from workloads.sampling import points_from, sample_surface
+
+pytestmark = pytest.mark.gpu
+
+
+def _call_noalloc(A, SA, B, SB, out, ps):
+    p = lambda t: None if t is None else t.data_ptr()
+    return lib().mesh_chamfer_noalloc(
+        A.handle, SA.data_ptr(), SA.shape[0], B.handle, SB.data_ptr(), SB.shape[0],
+        out.data_ptr(), p(ps["faceA"]), p(ps["baryA"]), p(ps["dist2A"]), p(ps["faceB"]),
+        p(ps["baryB"]), p(ps["dist2B"]), torch.cuda.current_stream().cuda_stream)
+
+
+def _call_workspace(A, SA, B, SB, out, ps):
+    p = lambda t: None if t is None else t.data_ptr()
+    need = lib().mesh_chamfer_workspace_bytes(SA.shape[0], SB.shape[0])
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    return lib().mesh_chamfer(
+        A.handle, SA.data_ptr(), SA.shape[0], B.handle, SB.data_ptr(), SB.shape[0],
+        ws.data_ptr(), ws.numel(), out.data_ptr(), p(ps["faceA"]), p(ps["baryA"]),
+        p(ps["dist2A"]), p(ps["faceB"]), p(ps["baryB"]), p(ps["dist2B"]),
+        torch.cuda.current_stream().cuda_stream)
+
+
+def _outputs(nA, nB):
+    return dict(faceA=torch.empty(nA, dtype=torch.int32, device="cuda"),
+                baryA=torch.empty(nA, 3, device="cuda"), dist2A=torch.empty(nA, device="cuda"),
+                faceB=torch.empty(nB, dtype=torch.int32, device="cuda"),
+                baryB=torch.empty(nB, 3, device="cuda"), dist2B=torch.empty(nB, device="cuda"))
+
+
+def test_noalloc_chamfer_matches_workspace_chamfer_twice():
+    VA, FA = icosphere(3)
+    VB, FB = displaced_icosphere(4, 0.1, 0.9)
+    fa, ba = sample_surface(VA, FA, 5000, seed=21)
+    fb, bb = sample_surface(VB, FB, 3333, seed=22)
+    SA, SB = dev(points_from(VA, FA, fa, ba)), dev(points_from(VB, FB, fb, bb))
+    A = MeshBVH.from_mesh(dev(VA), dev(FA))
+    B = MeshBVH.from_mesh(dev(VB), dev(FB))
+    ref = torch.empty(2, dtype=torch.float64, device="cuda")
+    ref_ps = _outputs(SA.shape[0], SB.shape[0])
+    assert _call_workspace(A, SA, B, SB, ref, ref_ps) == 0
+    for _ in range(2):                                   # two calls in a row share the scratch
+        out = torch.full((2,), -1.0, dtype=torch.float64, device="cuda")
+        ps = _outputs(SA.shape[0], SB.shape[0])
+        assert _call_noalloc(A, SA, B, SB, out, ps) == 0
+        torch.cuda.synchronize()
+        np.testing.assert_allclose(host(out), host(ref), rtol=1e-5)
+        for k in ("faceA", "faceB"):
+            assert torch.equal(ps[k], ref_ps[k])
+        for k in ("dist2A", "dist2B", "baryA", "baryB"):
+            np.testing.assert_allclose(host(ps[k]), host(ref_ps[k]), rtol=1e-5, atol=1e-7)
+
+
+def test_noalloc_chamfer_refuses_inputs_beyond_its_limit():
+    V, F = icosphere(1)
+    A = MeshBVH.from_mesh(dev(V), dev(F))
+    big = torch.zeros(16384 * 128 + 1, 3, device="cuda")
+    out = torch.zeros(2, dtype=torch.float64, device="cuda")
+    n0 = lib().mesh_launch_count()
+    st = _call_noalloc(A, big, A, big[:1], out, dict.fromkeys(
+        ("faceA", "baryA", "dist2A", "faceB", "baryB", "dist2B")))
+    assert st == 3                                         # MESH_ERR_WORKSPACE
+    assert lib().mesh_launch_count() == n0

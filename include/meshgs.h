@@ -116,6 +116,16 @@ mesh_status mesh_bvh_get_layout(const mesh_bvh *bvh, mesh_bvh_layout *out);
 mesh_status mesh_build_lbvh(mesh_bvh *bvh, const float *d_V, int64_t nV, const int32_t *d_F,
                             int64_t nF, void *d_ws, size_t ws_bytes, void *stream);
 
+/* Morton order of a point set, for query coherence: d_order [n] receives the
+ * permutation that sorts the points by the 30-bit key of mesh_build_lbvh (a
+ * point p keyed as the zero-area face (p, p, p), over the points' own box),
+ * ties by index.  Storing queries in this order (e.g. a particle set that
+ * persists across frames) makes neighbouring threads traverse the same nodes.
+ * d_ws: >= mesh_morton_order_workspace_bytes(n) bytes, 256-byte aligned. */
+size_t mesh_morton_order_workspace_bytes(int64_t n);
+mesh_status mesh_morton_order(const float *d_P, int64_t n, int32_t *d_order, void *d_ws,
+                              size_t ws_bytes, void *stream);
+
 /* Vertex-buffer update of Sec. 3.4 (step 2): copy V_k ([nV][3], nV equal to
  * the built mesh's) into the handle's vertex buffer.  Topology is untouched. */
 mesh_status mesh_update_vertices(mesh_bvh *bvh, const float *d_V, int64_t nV, void *stream);
@@ -135,6 +145,15 @@ mesh_status mesh_refit(mesh_bvh *bvh, const float *d_V, int64_t nV, void *stream
 mesh_status mesh_closest_point(const mesh_bvh *bvh, const float *d_Q, int64_t nQ,
                                float max_dist, int32_t *d_face, float *d_bary, float *d_point,
                                float *d_dist2, void *stream);
+
+/* Lanes that cooperate on one query in mesh_closest_point and mesh_chamfer.
+ * 0 (default) picks from the query count: one thread per query when the
+ * queries fill the GPU, else the smallest power of two up to 32 that does (a
+ * group pops several stack entries per step and merges its candidates with
+ * the same tie rule).  1, 2, 4, 8, 16 or 32 force a width.  Process-wide,
+ * not thread-safe; for tuning and tests.  Results are the same for every
+ * width up to the tie rule's float32 margin. */
+mesh_status mesh_set_query_group(int lanes);
 
 /* Face-bound Gaussians from the handle's current vertex buffer.  For Gaussian
  * g on face f = d_gface[g] with weights b = d_gbary[g] and normal offset

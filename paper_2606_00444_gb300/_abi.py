@@ -36,9 +36,12 @@ SIGNATURES = {
     "mesh_bvh_destroy": (None, [VP]),
     "mesh_bvh_get_layout": (C.c_int, [VP, C.POINTER(Layout)]),
     "mesh_build_lbvh": (C.c_int, [VP, VP, I64, VP, I64, VP, SZ, VP]),
+    "mesh_morton_order_workspace_bytes": (SZ, [I64]),
+    "mesh_morton_order": (C.c_int, [VP, I64, VP, VP, SZ, VP]),
     "mesh_update_vertices": (C.c_int, [VP, VP, I64, VP]),
     "mesh_refit": (C.c_int, [VP, VP, I64, VP]),
     "mesh_closest_point": (C.c_int, [VP, VP, I64, C.c_float, VP, VP, VP, VP, VP]),
+    "mesh_set_query_group": (C.c_int, [C.c_int]),
     "mesh_bind_gaussians": (C.c_int, [VP, VP, VP, VP, I64, VP, VP, VP, VP]),
     "mesh_interpolate": (C.c_int, [VP, VP, VP, I64, VP, VP]),
     "mesh_chamfer_workspace_bytes": (SZ, [I64, I64]),

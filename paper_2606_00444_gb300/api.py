@@ -244,5 +244,22 @@ def chamfer(A: MeshBVH, SA: torch.Tensor, B: MeshBVH, SB: torch.Tensor, per_samp
     return (out, ps) if per_sample else out
 
 
+def morton_order(P: torch.Tensor, ws: Workspace | None = None) -> torch.Tensor:
+    """int32 permutation sorting the points [n, 3] by Morton key (see mesh_morton_order)."""
+    P = _f32(P, 3, "P")
+    n = P.shape[0]
+    ws = Workspace(P.device) if ws is None else ws
+    buf = ws.get(lib().mesh_morton_order_workspace_bytes(n))
+    order = torch.empty(n, dtype=torch.int32, device=P.device)
+    check(lib().mesh_morton_order(P.data_ptr(), n, order.data_ptr(), buf.data_ptr(), buf.numel(),
+                                  _stream()), "mesh_morton_order")
+    return order
+
+
+def set_query_group(lanes: int) -> None:
+    """Force the lanes per query of the traversal kernels (0 = automatic)."""
+    check(lib().mesh_set_query_group(int(lanes)), "mesh_set_query_group")
+
+
 def launch_count() -> int:
     return int(lib().mesh_launch_count())

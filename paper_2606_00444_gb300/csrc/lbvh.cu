@@ -115,6 +115,52 @@ __global__ void k_faces_centroids(const int *__restrict__ F3, int nF, int nV,
     }
 }
 
+// Sort keys for points: a point p is keyed as the zero-area face (p, p, p),
+// i.e. s = (p + p) + p in float32 round-to-nearest, so points and faces share
+// one Morton recipe.
+__global__ void k_points_centroids(const float *__restrict__ P, int n, float4 *__restrict__ cent,
+                                   unsigned int *__restrict__ cbox) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    if (i < n) {
+        const float *p = P + 3 * (size_t)i;
+        float s0 = __fadd_rn(__fadd_rn(p[0], p[0]), p[0]);
+        float s1 = __fadd_rn(__fadd_rn(p[1], p[1]), p[1]);
+        float s2 = __fadd_rn(__fadd_rn(p[2], p[2]), p[2]);
+        cent[i] = make_float4(s0, s1, s2, 0.0f);
+        lo[0] = hi[0] = s0;
+        lo[1] = hi[1] = s1;
+        lo[2] = hi[2] = s2;
+    }
+    for (int k = 0; k < 3; ++k) {
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[k] = fminf(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+            hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+        }
+    }
+    __shared__ float s_lo[3][kBlock / 32], s_hi[3][kBlock / 32];
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0)
+        for (int k = 0; k < 3; ++k) { s_lo[k][w] = lo[k]; s_hi[k][w] = hi[k]; }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        int k = threadIdx.x;
+        float l = s_lo[k][0], h = s_hi[k][0];
+        for (int j = 1; j < (int)(blockDim.x >> 5); ++j) {
+            l = fminf(l, s_lo[k][j]);
+            h = fmaxf(h, s_hi[k][j]);
+        }
+        if (l <= h) {
+            atomicMin(&cbox[k], f2ord(l));
+            atomicMax(&cbox[3 + k], f2ord(h));
+        }
+    }
+}
+
+__global__ void k_init_box(unsigned int *cbox) {
+    if (threadIdx.x < 6) cbox[threadIdx.x] = (threadIdx.x < 3) ? 0xffffffffu : 0u;
+}
+
 // Bit i of v (10 bits) moved to bit 3i.
 __device__ __forceinline__ unsigned int spread3(unsigned int v) {
     v &= 0x3ffu;
@@ -214,19 +260,29 @@ __device__ unsigned int block_excl_scan(unsigned int x, unsigned int *s_warp, un
     return r;
 }
 
+// Exclusive scan of hist[0, total) in place by one block: consecutive chunks of
+// kScanThreads * 4 entries, each thread loading 4 consecutive entries
+// (coalesced as one 16-byte load when aligned), a block scan of the per-thread
+// sums, and a running carry between chunks.
 __global__ void __launch_bounds__(kScanThreads)
 k_sort_scan(unsigned int *__restrict__ hist, int total) {
     __shared__ unsigned int s_warp[33];
-    int per = (total + kScanThreads - 1) / kScanThreads;
-    int beg = threadIdx.x * per;
-    int end = min(beg + per, total);
-    unsigned int sum = 0;
-    for (int i = beg; i < end; ++i) sum += hist[i];
-    unsigned int run = block_excl_scan(sum, s_warp, nullptr);
-    for (int i = beg; i < end; ++i) {
-        unsigned int v = hist[i];
-        hist[i] = run;
-        run += v;
+    unsigned int carry = 0;
+    const int chunk = kScanThreads * 4;
+    for (int base = 0; base < total; base += chunk) {
+        int i0 = base + 4 * threadIdx.x;
+        unsigned int v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] = (i0 + k < total) ? hist[i0 + k] : 0u;
+        unsigned int sum = v[0] + v[1] + v[2] + v[3];
+        unsigned int tot;
+        unsigned int run = carry + block_excl_scan(sum, s_warp, &tot);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (i0 + k < total) hist[i0 + k] = run;
+            run += v[k];
+        }
+        carry += tot;
     }
 }
 
@@ -424,6 +480,25 @@ static BuildWs build_ws_layout(char *base, int64_t nF) {
     return w;
 }
 
+// Four 8-bit passes over (w.keysA, w.valsA): A -> B -> A -> B -> (out_keys,
+// out_vals).  out_keys may be w.keysA (the last pass reads B).
+static void radix_sort_pairs(const BuildWs &w, int n, unsigned int *out_keys, int *out_vals,
+                             cudaStream_t s) {
+    unsigned int *kin = w.keysA, *kout = w.keysB;
+    int *vin = w.valsA, *vout = w.valsB;
+    for (int pass = 0; pass < 4; ++pass) {
+        if (pass == 3) { kout = out_keys; vout = out_vals; }
+        int shift = 8 * pass;
+        k_sort_upsweep<<<w.tiles, kSortThreads, 0, s>>>(kin, n, shift, w.hist, w.tiles);
+        k_sort_scan<<<1, kScanThreads, 0, s>>>(w.hist, kRadix * w.tiles);
+        k_sort_downsweep<<<w.tiles, kSortThreads, 0, s>>>(kin, vin, kout, vout, n, shift, w.hist,
+                                                          w.tiles);
+        count_launch(3);
+        unsigned int *tk = kin; kin = kout; kout = tk;
+        int *tv = vin; vin = vout; vout = tv;
+    }
+}
+
 static mesh_bvh_layout storage_layout(int64_t maxV, int64_t maxF) {
     mesh_bvh_layout L{};
     int64_t v = maxV > 0 ? maxV : 1, f = maxF > 0 ? maxF : 1;
@@ -537,20 +612,7 @@ mesh_status mesh_build_lbvh(mesh_bvh *bvh, const float *d_V, int64_t nV, const i
                                                              bvh->faces(), w.cent, w.cbox, bvh->hdr());
     k_morton<<<grid_for(n, kBlock), kBlock, 0, s>>>(w.cent, n, w.cbox, w.keysA, w.valsA);
     count_launch(2);
-    // four 8-bit passes: A -> B -> A -> B -> storage
-    unsigned int *kin = w.keysA, *kout = w.keysB;
-    int *vin = w.valsA, *vout = w.valsB;
-    for (int pass = 0; pass < 4; ++pass) {
-        if (pass == 3) { kout = bvh->keys(); vout = bvh->perm(); }
-        int shift = 8 * pass;
-        k_sort_upsweep<<<w.tiles, kSortThreads, 0, s>>>(kin, n, shift, w.hist, w.tiles);
-        k_sort_scan<<<1, kScanThreads, 0, s>>>(w.hist, kRadix * w.tiles);
-        k_sort_downsweep<<<w.tiles, kSortThreads, 0, s>>>(kin, vin, kout, vout, n, shift, w.hist,
-                                                          w.tiles);
-        count_launch(3);
-        unsigned int *tk = kin; kin = kout; kout = tk;
-        int *tv = vin; vin = vout; vout = tv;
-    }
+    radix_sort_pairs(w, n, bvh->keys(), bvh->perm(), s);
     if (n > 1) {
         k_karras<<<grid_for(n - 1, kBlock), kBlock, 0, s>>>(bvh->keys(), n, bvh->nodes(),
                                                            bvh->parent());
@@ -563,6 +625,24 @@ mesh_status mesh_build_lbvh(mesh_bvh *bvh, const float *d_V, int64_t nV, const i
                                                        bvh->tris(), bvh->nodes(), bvh->parent(),
                                                        bvh->flags(), bvh->hdr());
     count_launch();
+    return check_launch();
+}
+
+size_t mesh_morton_order_workspace_bytes(int64_t n) { return mesh_build_workspace_bytes(n); }
+
+mesh_status mesh_morton_order(const float *d_P, int64_t n, int32_t *d_order, void *d_ws,
+                              size_t ws_bytes, void *stream) {
+    if (n < 0 || n > kMaxFaces || (n > 0 && (!d_P || !d_order))) return MESH_ERR_INVALID_ARG;
+    if (n == 0) return MESH_OK;
+    BuildWs w = build_ws_layout((char *)d_ws, n);
+    if (!d_ws || ws_bytes < w.bytes || ((uintptr_t)d_ws & 255u)) return MESH_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    int m = (int)n;
+    k_init_box<<<1, 32, 0, s>>>(w.cbox);
+    k_points_centroids<<<grid_for(m, kBlock), kBlock, 0, s>>>(d_P, m, w.cent, w.cbox);
+    k_morton<<<grid_for(m, kBlock), kBlock, 0, s>>>(w.cent, m, w.cbox, w.keysA, w.valsA);
+    count_launch(3);
+    radix_sort_pairs(w, m, w.keysA, d_order, s);
     return check_launch();
 }
 

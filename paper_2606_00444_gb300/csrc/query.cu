@@ -156,14 +156,17 @@ __device__ __noinline__ void tri_weights_f64(float3 pf, float3 af, float3 bf, fl
     u = (float)U; v = (float)V; w = (float)W;
 }
 
-// True when float32 weights of this face would be too coarse for the query:
-// distance beyond 4 shortest edges, or a sliver (altitude < 5% of longest edge).
+// True when float32 weights of this face would be too coarse for the query.
+// Their error grows like ~8 eps32 d / l_min (measured), so beyond 12 shortest
+// edges it could approach 1e-5; slivers (altitude < 5% of the longest edge)
+// are ill-conditioned at any distance.  Float64 is slow on this part, so the
+// threshold keeps the float64 path off near-surface queries entirely.
 __device__ __forceinline__ bool weights_need_f64(float3 a, float3 b, float3 c, float d2) {
     float3 ab = sub3(b, a), ac = sub3(c, a), bc = sub3(c, b);
     float l0 = dot3(ab, ab), l1 = dot3(ac, ac), l2 = dot3(bc, bc);
     float lmin = fminf(l0, fminf(l1, l2)), lmax = fmaxf(l0, fmaxf(l1, l2));
     float3 n = make_float3(ab.y * ac.z - ab.z * ac.y, ab.z * ac.x - ab.x * ac.z, ab.x * ac.y - ab.y * ac.x);
-    return d2 > 16.0f * lmin || dot3(n, n) < 2.5e-3f * lmax * lmax;
+    return d2 > 144.0f * lmin || dot3(n, n) < 2.5e-3f * lmax * lmax;
 }
 
 struct Hit {
@@ -195,9 +198,10 @@ struct Best {
 __device__ __forceinline__ void consider(Best &B, int leaf, int face, float d2, float maxd2,
                                          float tau) {
     if (B.leaf < 0) {
-        if (d2 <= maxd2) {
-            B.leaf = leaf; B.face = face; B.d2 = d2; B.dmin = d2;
-            B.thr = tie_window2(d2, tau);
+        if (d2 <= maxd2 && d2 <= B.thr) {
+            B.leaf = leaf; B.face = face; B.d2 = d2;
+            B.dmin = fminf(B.dmin, d2);
+            B.thr = tie_window2(B.dmin, tau);
         }
         return;
     }
@@ -261,6 +265,183 @@ __device__ __forceinline__ Hit nearest(const Traversal &T, float3 q, float maxd2
     return Hit{B.leaf, B.face, B.d2};
 }
 
+// Depth-first search of the subtree under `start` by one thread with a
+// local stack (the tree depth bounds it, so kStackTotal entries suffice),
+// continuing the candidate state B.  Used by a cooperative group when its
+// shared stack is nearly full.
+__device__ __noinline__ void dfs_private(const Traversal &T, Best &B, int start, float3 q,
+                                         float maxd2, unsigned int *status) {
+    int2 stk[kStackTotal];
+    int sp = 0, node = start;
+    while (true) {
+        const float4 *r = T.nodes + 4 * (size_t)node;
+        float4 l0 = ldg4(r), l1 = ldg4(r + 1), r0 = ldg4(r + 2), r1 = ldg4(r + 3);
+        float dl = box_d2(q, l0, l1), dr = box_d2(q, r0, r1);
+        int cl = __float_as_int(l0.w), cr = __float_as_int(r0.w);
+        if (cl < 0 && dl <= B.thr) test_leaf(T, B, -cl - 1, q, maxd2);
+        if (cr < 0 && dr <= B.thr) test_leaf(T, B, -cr - 1, q, maxd2);
+        bool gl = cl >= 0 && dl <= B.thr, gr = cr >= 0 && dr <= B.thr;
+        if (gl && gr) {
+            bool lfirst = dl <= dr;
+            if (sp < kStackTotal) stk[sp++] = make_int2(lfirst ? cr : cl, __float_as_int(lfirst ? dr : dl));
+            else atomicOr(status, (unsigned)MESH_DEV_STACK_OVERFLOW);
+            node = lfirst ? cl : cr;
+            continue;
+        }
+        if (gl) { node = cl; continue; }
+        if (gr) { node = cr; continue; }
+        bool found = false;
+        while (sp > 0) {
+            int2 e = stk[--sp];
+            if (__int_as_float(e.y) <= B.thr) { node = e.x; found = true; break; }
+        }
+        if (!found) return;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Warp-cooperative NearestSurface: G lanes (an aligned group of a warp) share
+// one query.  Each step the group pops up to G entries of its shared stack,
+// every lane visits one node (testing its two child boxes and any leaf
+// children), the group merges the leaf candidates under the tie rule with
+// shuffles, and the surviving children are pushed back (each lane's nearer
+// child above its farther one, lane 0's above lane 1's).  This keeps the GPU
+// busy when there are too few queries for one thread each.  When the shared
+// stack is nearly full each lane instead finishes its popped subtree alone
+// (dfs_private), so no entry is ever dropped.  All collectives run on the full
+// warp every step; groups that are done simply take nothing.
+// ---------------------------------------------------------------------------
+// shared-memory stack entries per group: room for one full step (2G pushes)
+// above the near-full mark, plus a working depth
+template <int G> constexpr int group_cap() { return 4 * G + 64; }
+
+template <int G> __device__ __forceinline__ float grp_min(float x) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) x = fminf(x, __shfl_xor_sync(0xffffffffu, x, o));
+    return x;
+}
+template <int G> __device__ __forceinline__ int grp_min(int x) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) x = min(x, __shfl_xor_sync(0xffffffffu, x, o));
+    return x;
+}
+template <int G> __device__ __forceinline__ int grp_sum(int x) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+template <int G> __device__ __forceinline__ int grp_incl_scan(int x, int gl) {
+#pragma unroll
+    for (int o = 1; o < G; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o, G);
+        if (gl >= o) x += y;
+    }
+    return x;
+}
+
+template <int G>
+__device__ Hit nearest_group(const Traversal &T, float3 q, float maxd2, bool valid, int2 *stk,
+                             unsigned int *status) {
+    const int lane = threadIdx.x & 31;
+    const int gl = lane & (G - 1);
+    const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+    int bleaf = -1, bface = 0x7fffffff;
+    float bd2 = INFINITY, dmin = INFINITY, thr = maxd2;
+    int sp = 0;
+    if (valid && T.n == 1) {
+        Best B{-1, 0x7fffffff, INFINITY, INFINITY, maxd2};
+        test_leaf(T, B, 0, q, maxd2);
+        bleaf = B.leaf; bface = B.face; bd2 = B.d2;
+    } else if (valid && T.n > 1) {
+        if (gl == 0) stk[0] = make_int2(0, __float_as_int(0.0f));
+        sp = 1;
+    }
+    __syncwarp();
+    while (__any_sync(0xffffffffu, sp > 0)) {
+        const bool near_full = sp > group_cap<G>() - 2 * G;
+        const int take = min(G, sp);
+        bool act = gl < take;
+        int2 e = make_int2(0, 0);
+        if (act) e = stk[sp - 1 - gl];
+        __syncwarp();
+        sp -= take;
+        act = act && __int_as_float(e.y) <= thr;
+        float c0 = INFINITY, c1 = INFINITY;
+        int f0 = 0x7fffffff, f1 = 0x7fffffff, lf0 = -1, lf1 = -1;
+        int npush = 0;
+        int2 p_far = make_int2(0, 0), p_near = make_int2(0, 0);
+        if (act && !near_full) {
+            const float4 *r = T.nodes + 4 * (size_t)e.x;
+            float4 l0 = ldg4(r), l1 = ldg4(r + 1), r0 = ldg4(r + 2), r1 = ldg4(r + 3);
+            float dl = box_d2(q, l0, l1), dr = box_d2(q, r0, r1);
+            int cl = __float_as_int(l0.w), cr = __float_as_int(r0.w);
+            float u, v, w;
+            if (cl < 0 && dl <= thr) {
+                lf0 = -cl - 1;
+                const float4 *t = T.tris + 3 * (size_t)lf0;
+                float4 a = ldg4(t), b = ldg4(t + 1), c = ldg4(t + 2);
+                c0 = tri_closest(q, xyz(a), xyz(b), xyz(c), b.w != 0.0f, u, v, w);
+                f0 = __float_as_int(a.w);
+            }
+            if (cr < 0 && dr <= thr) {
+                lf1 = -cr - 1;
+                const float4 *t = T.tris + 3 * (size_t)lf1;
+                float4 a = ldg4(t), b = ldg4(t + 1), c = ldg4(t + 2);
+                c1 = tri_closest(q, xyz(a), xyz(b), xyz(c), b.w != 0.0f, u, v, w);
+                f1 = __float_as_int(a.w);
+            }
+            bool gol = cl >= 0 && dl <= thr, gor = cr >= 0 && dr <= thr;
+            if (gol && gor) {
+                bool lfirst = dl <= dr;
+                p_near = make_int2(lfirst ? cl : cr, __float_as_int(lfirst ? dl : dr));
+                p_far = make_int2(lfirst ? cr : cl, __float_as_int(lfirst ? dr : dl));
+                npush = 2;
+            } else if (gol) {
+                p_near = make_int2(cl, __float_as_int(dl));
+                npush = 1;
+            } else if (gor) {
+                p_near = make_int2(cr, __float_as_int(dr));
+                npush = 1;
+            }
+        } else if (act) {
+            Best P{-1, 0x7fffffff, INFINITY, dmin, thr};
+            dfs_private(T, P, e.x, q, maxd2, status);
+            if (P.leaf >= 0) { c0 = P.d2; f0 = P.face; lf0 = P.leaf; }
+        }
+        // merge the group's candidates under the tie rule
+        if (bleaf < 0) {                       // nothing accepted yet: the cutoff applies
+            if (c0 > maxd2) c0 = INFINITY;
+            if (c1 > maxd2) c1 = INFINITY;
+        }
+        float m = grp_min<G>(fminf(c0, c1));
+        float nmin = fminf(dmin, m);
+        float w2 = nmin < dmin ? tie_window2(nmin, T.tau) : thr;
+        int fc = min(c0 <= w2 ? f0 : 0x7fffffff, c1 <= w2 ? f1 : 0x7fffffff);
+        int fmin = grp_min<G>(fc);
+        bool mine = fmin != 0x7fffffff && fc == fmin;
+        unsigned bal = __ballot_sync(0xffffffffu, mine) & gmask;
+        int src = bal ? (__ffs(bal) - 1) & (G - 1) : 0;
+        float md2 = (c0 <= w2 && f0 == fmin) ? c0 : c1;
+        int mlf = (c0 <= w2 && f0 == fmin) ? lf0 : lf1;
+        float sd2 = __shfl_sync(0xffffffffu, md2, src, G);
+        int slf = __shfl_sync(0xffffffffu, mlf, src, G);
+        if (m < INFINITY) {
+            bool keep = bleaf >= 0 && bd2 <= w2 && bface < fmin;
+            if (!keep && fmin != 0x7fffffff) { bface = fmin; bd2 = sd2; bleaf = slf; }
+            dmin = nmin;
+            thr = w2;
+        }
+        // push surviving children: lane G-1's lowest, lane 0's on top
+        int total = grp_sum<G>(npush);
+        int above = total - grp_incl_scan<G>(npush, gl);
+        if (npush == 2) { stk[sp + above] = p_far; stk[sp + above + 1] = p_near; }
+        else if (npush == 1) { stk[sp + above] = p_near; }
+        sp += total;
+        __syncwarp();
+    }
+    return Hit{bleaf, bface, bd2};
+}
+
 __device__ __forceinline__ float traversal_tau(const Header *hdr) {
     float4 lo = hdr->root_lo, hi = hdr->root_hi;
     float dx = hi.x - lo.x, dy = hi.y - lo.y, dz = hi.z - lo.z;
@@ -308,6 +489,20 @@ k_closest_point(Traversal T, const Header *__restrict__ hdr, unsigned int *statu
     write_hit(T, h, q, i, face, bary, point, dist2);
 }
 
+template <int G>
+__global__ void __launch_bounds__(kQueryBlock)
+k_closest_point_group(Traversal T, const Header *__restrict__ hdr, unsigned int *status,
+                      const float *__restrict__ Q, int64_t nQ, float maxd2, int *face, float *bary,
+                      float *point, float *dist2) {
+    __shared__ int2 gstk[kQueryBlock / G][group_cap<G>()];
+    int64_t i = ((int64_t)blockIdx.x * kQueryBlock + threadIdx.x) / G;
+    bool valid = i < nQ;
+    T.tau = traversal_tau(hdr);
+    float3 q = valid ? make_float3(Q[3 * i], Q[3 * i + 1], Q[3 * i + 2]) : make_float3(0.f, 0.f, 0.f);
+    Hit h = nearest_group<G>(T, q, maxd2, valid, gstk[threadIdx.x / G], status);
+    if (valid && (threadIdx.x & (G - 1)) == 0) write_hit(T, h, q, i, face, bary, point, dist2);
+}
+
 // ---------------------------------------------------------------------------
 // Chamfer (Sec. 4.2): both directions in one launch (blocks [0, nbA) query SA
 // against B, the rest SB against A).  Each block sums its squared distances in
@@ -336,23 +531,37 @@ struct ChamferSide {
     float *bary, *dist2;
 };
 
-__global__ void __launch_bounds__(kQueryBlock, kQueryMinBlocks)
+template <int G>
+__global__ void __launch_bounds__(kQueryBlock, G == 1 ? kQueryMinBlocks : 1)
 k_chamfer(ChamferSide A2B, ChamferSide B2A, unsigned int nbA, unsigned int *status,
           double *partial, unsigned int *ticket, double *out) {
-    __shared__ int2 stk[kStackShared][kQueryBlock];
+    constexpr int kStk = G == 1 ? kStackShared * kQueryBlock : (kQueryBlock / G) * group_cap<G>();
+    __shared__ int2 stk_mem[kStk];
     __shared__ double s_red[kQueryBlock / 32];
     __shared__ bool s_last;
     bool first = blockIdx.x < nbA;
     ChamferSide &C = first ? A2B : B2A;
-    int64_t i = (int64_t)(first ? blockIdx.x : blockIdx.x - nbA) * kQueryBlock + threadIdx.x;
+    int64_t i = ((int64_t)(first ? blockIdx.x : blockIdx.x - nbA) * kQueryBlock + threadIdx.x) / G;
     double d2 = 0.0;
-    if (i < C.n) {
-        Traversal T = C.T;
-        T.tau = traversal_tau(C.hdr);
-        float3 q = make_float3(C.S[3 * i], C.S[3 * i + 1], C.S[3 * i + 2]);
-        Hit h = nearest<kQueryBlock>(T, q, INFINITY, stk, status);
-        write_hit(T, h, q, i, C.face, C.bary, nullptr, C.dist2);
-        d2 = h.leaf >= 0 ? (double)h.d2 : 0.0;
+    Traversal T = C.T;
+    T.tau = traversal_tau(C.hdr);
+    bool valid = i < C.n;
+    float3 q = valid ? make_float3(C.S[3 * i], C.S[3 * i + 1], C.S[3 * i + 2])
+                     : make_float3(0.f, 0.f, 0.f);
+    if constexpr (G == 1) {
+        if (valid) {
+            Hit h = nearest<kQueryBlock>(T, q, INFINITY,
+                                         reinterpret_cast<int2 (*)[kQueryBlock]>(stk_mem), status);
+            write_hit(T, h, q, i, C.face, C.bary, nullptr, C.dist2);
+            d2 = h.leaf >= 0 ? (double)h.d2 : 0.0;
+        }
+    } else {
+        Hit h = nearest_group<G>(T, q, INFINITY, valid, stk_mem + (threadIdx.x / G) * group_cap<G>(),
+                                 status);
+        if (valid && (threadIdx.x & (G - 1)) == 0) {
+            write_hit(T, h, q, i, C.face, C.bary, nullptr, C.dist2);
+            d2 = h.leaf >= 0 ? (double)h.d2 : 0.0;
+        }
     }
     double s = block_sum_d(d2, s_red);
     if (threadIdx.x == 0) {
@@ -400,7 +609,30 @@ static Traversal traversal_of(const mesh_bvh *b) {
     return Traversal{b->nodes(), b->tris(), (int)b->L.n_faces, 0.0f};
 }
 
-static size_t chamfer_blocks(int64_t n) { return (size_t)((n + kQueryBlock - 1) / kQueryBlock); }
+static size_t chamfer_blocks(int64_t n, int G = 1) {
+    return (size_t)((n * G + kQueryBlock - 1) / kQueryBlock);
+}
+
+// Lanes per query: one thread per query when there are enough queries to fill
+// the GPU (two resident blocks of threads per SM), otherwise the smallest power
+// of two G <= 32 that does.  (An explicit override can come from
+// mesh_set_query_group.)
+static int g_group_override = 0;
+static int pick_group(int64_t nQ) {
+    if (g_group_override > 0) return g_group_override;
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+            sms = 152;
+    }
+    int64_t target = (int64_t)sms * 2048;
+    if (nQ >= target || nQ <= 0) return 1;
+    int G = 1;
+    while (G < 32 && nQ * G < target) G <<= 1;
+    return G;
+}
 
 }  // namespace meshgs
 
@@ -415,16 +647,25 @@ mesh_status mesh_closest_point(const mesh_bvh *bvh, const float *d_Q, int64_t nQ
     if (nQ == 0) return MESH_OK;
     float maxd2 = isinf(max_dist) ? INFINITY : max_dist * max_dist;
     cudaStream_t s = (cudaStream_t)stream;
-    k_closest_point<<<grid_for(nQ, kQueryBlock), kQueryBlock, 0, s>>>(
-        traversal_of(bvh), bvh->hdr(), &bvh->hdr()->status, d_Q, nQ, maxd2, d_face, d_bary,
-        d_point, d_dist2);
+    int G = pick_group(nQ);
+    Traversal T = traversal_of(bvh);
+    Header *h = bvh->hdr();
+    unsigned int grid = grid_for(nQ * G, kQueryBlock);
+    switch (G) {
+        case 1: k_closest_point<<<grid, kQueryBlock, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2); break;
+        case 2: k_closest_point_group<2><<<grid, kQueryBlock, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2); break;
+        case 4: k_closest_point_group<4><<<grid, kQueryBlock, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2); break;
+        case 8: k_closest_point_group<8><<<grid, kQueryBlock, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2); break;
+        case 16: k_closest_point_group<16><<<grid, kQueryBlock, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2); break;
+        default: k_closest_point_group<32><<<grid, kQueryBlock, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2); break;
+    }
     count_launch();
     return check_launch();
 }
 
 size_t mesh_chamfer_workspace_bytes(int64_t nSA, int64_t nSB) {
     if (nSA < 0 || nSB < 0) return 0;
-    return align_up(8 * (chamfer_blocks(nSA) + chamfer_blocks(nSB) + 1), 256) + 256;
+    return align_up(8 * (chamfer_blocks(nSA, 32) + chamfer_blocks(nSB, 32) + 1), 256) + 256;
 }
 
 mesh_status mesh_chamfer(const mesh_bvh *A, const float *d_SA, int64_t nSA, const mesh_bvh *B,
@@ -436,7 +677,8 @@ mesh_status mesh_chamfer(const mesh_bvh *A, const float *d_SA, int64_t nSA, cons
     size_t need = mesh_chamfer_workspace_bytes(nSA, nSB);
     if (!d_ws || ws_bytes < need || ((uintptr_t)d_ws & 255u)) return MESH_ERR_WORKSPACE;
     cudaStream_t s = (cudaStream_t)stream;
-    size_t nbA = chamfer_blocks(nSA), nbB = chamfer_blocks(nSB);
+    int G = pick_group(nSA + nSB);
+    size_t nbA = chamfer_blocks(nSA, G), nbB = chamfer_blocks(nSB, G);
     double *partial = (double *)d_ws;
     unsigned int *ticket = (unsigned int *)((char *)d_ws + need - 256);
     if (nbA + nbB == 0) {
@@ -446,11 +688,26 @@ mesh_status mesh_chamfer(const mesh_bvh *A, const float *d_SA, int64_t nSA, cons
     cudaMemsetAsync(ticket, 0, sizeof(unsigned int), s);
     ChamferSide a2b{traversal_of(B), B->hdr(), d_SA, nSA, d_faceA, d_baryA, d_dist2A};
     ChamferSide b2a{traversal_of(A), A->hdr(), d_SB, nSB, d_faceB, d_baryB, d_dist2B};
-    k_chamfer<<<(unsigned)(nbA + nbB), kQueryBlock, 0, s>>>(a2b, b2a, (unsigned)nbA,
-                                                            &A->hdr()->status, partial, ticket,
-                                                            d_out);
+    unsigned grid = (unsigned)(nbA + nbB);
+    unsigned *st = &A->hdr()->status;
+    switch (G) {
+        case 1: k_chamfer<1><<<grid, kQueryBlock, 0, s>>>(a2b, b2a, (unsigned)nbA, st, partial, ticket, d_out); break;
+        case 2: k_chamfer<2><<<grid, kQueryBlock, 0, s>>>(a2b, b2a, (unsigned)nbA, st, partial, ticket, d_out); break;
+        case 4: k_chamfer<4><<<grid, kQueryBlock, 0, s>>>(a2b, b2a, (unsigned)nbA, st, partial, ticket, d_out); break;
+        case 8: k_chamfer<8><<<grid, kQueryBlock, 0, s>>>(a2b, b2a, (unsigned)nbA, st, partial, ticket, d_out); break;
+        case 16: k_chamfer<16><<<grid, kQueryBlock, 0, s>>>(a2b, b2a, (unsigned)nbA, st, partial, ticket, d_out); break;
+        default: k_chamfer<32><<<grid, kQueryBlock, 0, s>>>(a2b, b2a, (unsigned)nbA, st, partial, ticket, d_out); break;
+    }
     count_launch();
     return check_launch();
+}
+
+mesh_status mesh_set_query_group(int lanes) {
+    if (lanes != 0 && lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8 && lanes != 16 &&
+        lanes != 32)
+        return MESH_ERR_INVALID_ARG;
+    g_group_override = lanes;
+    return MESH_OK;
 }
 
 mesh_status mesh_interpolate(const mesh_bvh *bvh, const int32_t *d_face, const float *d_bary,
@@ -525,9 +782,9 @@ extern "C" mesh_status mesh_chamfer_noalloc(const mesh_bvh *A, const float *d_SA
     cudaMemsetAsync(ticket, 0, sizeof(unsigned int), s);
     ChamferSide a2b{traversal_of(B), B->hdr(), d_SA, nSA, d_faceA, d_baryA, d_dist2A};
     ChamferSide b2a{traversal_of(A), A->hdr(), d_SB, nSB, d_faceB, d_baryB, d_dist2B};
-    k_chamfer<<<(unsigned)(nbA + nbB), kQueryBlock, 0, s>>>(a2b, b2a, (unsigned)nbA,
-                                                            &A->hdr()->status, scratch, ticket,
-                                                            d_out);
+    k_chamfer<1><<<(unsigned)(nbA + nbB), kQueryBlock, 0, s>>>(a2b, b2a, (unsigned)nbA,
+                                                               &A->hdr()->status, scratch, ticket,
+                                                               d_out);
     count_launch();
     return check_launch();
 }

@@ -179,3 +179,18 @@ def test_autograd_bind_gaussians_matches_oracle_backward():
     ((mu * dev(wm)).sum() + (quat * dev(wq)).sum() + (scale * dev(ws)).sum()).backward()
     ref = oracle.bind_gaussians_backward(V, F, gface, gbary, wm, wq, ws)
     assert rel_close(host(Vd.grad), ref, 1e-4)
+
+
+@pytest.mark.parametrize("lanes", [1, 4, 32])
+def test_chamfer_every_group_width(pair, lanes):
+    from paper_2606_00444_gb300 import set_query_group
+    VA, FA, SA, VB, FB, SB = pair
+    A = MeshBVH.from_mesh(dev(VA), dev(FA))
+    B = MeshBVH.from_mesh(dev(VB), dev(FB))
+    try:
+        set_query_group(lanes)
+        out = chamfer(A, dev(SA), B, dev(SB))
+    finally:
+        set_query_group(0)
+    ref, _, _ = oracle.chamfer(VA, FA, SA, VB, FB, SB)
+    np.testing.assert_allclose(host(out), ref, rtol=1e-5)

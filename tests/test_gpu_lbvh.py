@@ -105,3 +105,19 @@ def test_out_of_range_index_sets_status_not_fault():
     bits, _ = bvh.status()
     assert bits & 0x1
     assert host(bvh.arrays()["faces"])[3, 2] == 0
+
+
+@pytest.mark.parametrize("n", [1, 2, 1000, 4099, 250000])
+def test_point_morton_order_bit_exact(n):
+    """mesh_morton_order keys a point p as the zero-area face (p, p, p): the oracle's
+    face recipe and stable sort give the expected permutation exactly."""
+    from paper_2606_00444_gb300 import morton_order
+    from workloads.sampling import uniform_box
+    P = uniform_box(n, [-1, -2, -0.5], [1, 2, 0.5], seed=n)
+    if n > 10:
+        P[::7] = P[3]                                    # duplicates: ties broken by index
+    idx = np.arange(n, dtype=np.int32)
+    keys = oracle.morton(P, np.stack([idx, idx, idx], 1))
+    _, perm = oracle.sort_pairs(keys)
+    got = host(morton_order(dev(P)))
+    assert np.array_equal(got, perm)

@@ -122,3 +122,24 @@ def test_contact_workload_full_size():
     sub = {k: v[idx] for k, v in out.items()}
     check_closest(V1, F, P[pick], sub, max_dist=0.05)
     assert fixed.status()[0] == 0
+
+
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8, 16, 32])
+def test_every_group_width_matches_oracle(c1, lanes):
+    """The cooperative traversal (G lanes per query) gives the oracle's answers for every G,
+    with and without a cutoff, including a mesh whose shared stacks overflow to the
+    private fallback (queries at the centre of a sphere see every face at once)."""
+    from paper_2606_00444_gb300 import set_query_group
+    _, _, VG, FG, Q = c1
+    bvh = MeshBVH.from_mesh(dev(VG), dev(FG))
+    try:
+        set_query_group(lanes)
+        check_closest(VG, FG, Q, bvh.closest_point(dev(Q)))
+        check_closest(VG, FG, Q, bvh.closest_point(dev(Q), max_dist=0.05), max_dist=0.05)
+        V, F = icosphere(4)
+        centre = MeshBVH.from_mesh(dev(V), dev(F))
+        Qc = (uniform_box(64, [-0.02] * 3, [0.02] * 3, seed=lanes)).astype(np.float32)
+        check_closest(V, F, Qc, centre.closest_point(dev(Qc)), max_tie_frac=0.2)
+        assert bvh.status()[0] == 0 and centre.status()[0] == 0
+    finally:
+        set_query_group(0)

@@ -155,6 +155,12 @@ mesh_status mesh_closest_point(const mesh_bvh *bvh, const float *d_Q, int64_t nQ
  * width up to the tie rule's float32 margin. */
 mesh_status mesh_set_query_group(int lanes);
 
+/* One-thread-per-query traversal form for mesh_closest_point: 0 = plain
+ * depth-first (default: leaf children tested as met), 1 = while-while (leaf
+ * children queued while internal nodes are traversed, tested together).
+ * Process-wide; for tuning and tests.  Same answers either way. */
+mesh_status mesh_set_traversal(int variant);
+
 /* Face-bound Gaussians from the handle's current vertex buffer.  For Gaussian
  * g on face f = d_gface[g] with weights b = d_gbary[g] and normal offset
  * delta = d_goff[g] (NULL = 0):

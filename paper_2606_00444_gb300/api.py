@@ -261,5 +261,10 @@ def set_query_group(lanes: int) -> None:
     check(lib().mesh_set_query_group(int(lanes)), "mesh_set_query_group")
 
 
+def set_traversal(variant: int) -> None:
+    """One-thread traversal form: 0 depth-first (default), 1 while-while."""
+    check(lib().mesh_set_traversal(int(variant)), "mesh_set_traversal")
+
+
 def launch_count() -> int:
     return int(lib().mesh_launch_count())

@@ -265,6 +265,64 @@ __device__ __forceinline__ Hit nearest(const Traversal &T, float3 q, float maxd2
     return Hit{B.leaf, B.face, B.d2};
 }
 
+// One thread per query, "while-while" form: internal nodes are traversed
+// while leaf children are only queued (up to kLeafQueue); the queued leaves
+// are tested when every lane still traversing has one queued (or its queue is
+// full, or it is done).  Leaf tests then run with the warp mostly converged
+// instead of in almost every step.  Same answers as nearest().
+constexpr int kLeafQueue = 4;
+
+template <int kBlockT>
+__device__ __forceinline__ Hit nearest_ww(const Traversal &T, float3 q, float maxd2,
+                                          int2 (*stk)[kBlockT], unsigned int *status) {
+    Best B{-1, 0x7fffffff, INFINITY, INFINITY, maxd2};
+    if (T.n == 1) {
+        test_leaf(T, B, 0, q, maxd2);
+        return Hit{B.leaf, B.face, B.d2};
+    }
+    if (T.n < 1) return Hit{-1, 0x7fffffff, INFINITY};
+    int2 spill[kStackTotal - kStackShared];
+    const int tid = threadIdx.x;
+    int sp = 0, node = 0;
+    bool done = false;
+    int lq[kLeafQueue];
+    int nq = 0;
+    while (true) {
+        while (!done && nq + 2 <= kLeafQueue) {
+            if (nq > 0 && __all_sync(__activemask(), nq > 0)) break;
+            const float4 *r = T.nodes + 4 * (size_t)node;
+            float4 l0 = ldg4(r), l1 = ldg4(r + 1), r0 = ldg4(r + 2), r1 = ldg4(r + 3);
+            float dl = box_d2(q, l0, l1), dr = box_d2(q, r0, r1);
+            int cl = __float_as_int(l0.w), cr = __float_as_int(r0.w);
+            if (cl < 0 && dl <= B.thr) lq[nq++] = -cl - 1;
+            if (cr < 0 && dr <= B.thr) lq[nq++] = -cr - 1;
+            bool gol = cl >= 0 && dl <= B.thr, gor = cr >= 0 && dr <= B.thr;
+            if (gol && gor) {
+                bool lfirst = dl <= dr;
+                int2 e = make_int2(lfirst ? cr : cl, __float_as_int(lfirst ? dr : dl));
+                if (sp < kStackShared) stk[sp][tid] = e;
+                else if (sp < kStackTotal) spill[sp - kStackShared] = e;
+                else atomicOr(status, (unsigned)MESH_DEV_STACK_OVERFLOW);
+                if (sp < kStackTotal) ++sp;
+                node = lfirst ? cl : cr;
+                continue;
+            }
+            if (gol) { node = cl; continue; }
+            if (gor) { node = cr; continue; }
+            done = true;
+            while (sp > 0) {
+                --sp;
+                int2 e = sp < kStackShared ? stk[sp][tid] : spill[sp - kStackShared];
+                if (__int_as_float(e.y) <= B.thr) { node = e.x; done = false; break; }
+            }
+        }
+        for (int k = 0; k < nq; ++k) test_leaf(T, B, lq[k], q, maxd2);
+        nq = 0;
+        if (done) break;
+    }
+    return Hit{B.leaf, B.face, B.d2};
+}
+
 // Depth-first search of the subtree under `start` by one thread with a
 // local stack (the tree depth bounds it, so kStackTotal entries suffice),
 // continuing the candidate state B.  Used by a cooperative group when its
@@ -353,6 +411,21 @@ __device__ Hit nearest_group(const Traversal &T, float3 q, float maxd2, bool val
         test_leaf(T, B, 0, q, maxd2);
         bleaf = B.leaf; bface = B.face; bd2 = B.d2;
     } else if (valid && T.n > 1) {
+        // Greedy dive (every lane of the group on the same path): the nearer
+        // child down to a leaf gives the parallel phase a tight window from
+        // the start, so the shared stack stays small.
+        int node = 0;
+        while (true) {
+            const float4 *r = T.nodes + 4 * (size_t)node;
+            float4 l0 = ldg4(r), l1 = ldg4(r + 1), r0 = ldg4(r + 2), r1 = ldg4(r + 3);
+            float dl = box_d2(q, l0, l1), dr = box_d2(q, r0, r1);
+            int c = dl <= dr ? __float_as_int(l0.w) : __float_as_int(r0.w);
+            if (c >= 0) { node = c; continue; }
+            Best B{-1, 0x7fffffff, INFINITY, INFINITY, maxd2};
+            test_leaf(T, B, -c - 1, q, maxd2);
+            if (B.leaf >= 0) { bleaf = B.leaf; bface = B.face; bd2 = B.d2; dmin = B.dmin; thr = B.thr; }
+            break;
+        }
         if (gl == 0) stk[0] = make_int2(0, __float_as_int(0.0f));
         sp = 1;
     }
@@ -476,6 +549,7 @@ __device__ __forceinline__ void write_hit(const Traversal &T, const Hit &h, floa
     }
 }
 
+template <bool kWhileWhile>
 __global__ void __launch_bounds__(kQueryBlock, kQueryMinBlocks)
 k_closest_point(Traversal T, const Header *__restrict__ hdr, unsigned int *status,
                 const float *__restrict__ Q, int64_t nQ, float maxd2, int *face, float *bary,
@@ -485,7 +559,8 @@ k_closest_point(Traversal T, const Header *__restrict__ hdr, unsigned int *statu
     if (i >= nQ) return;
     T.tau = traversal_tau(hdr);
     float3 q = make_float3(Q[3 * i], Q[3 * i + 1], Q[3 * i + 2]);
-    Hit h = nearest<kQueryBlock>(T, q, maxd2, stk, status);
+    Hit h = kWhileWhile ? nearest_ww<kQueryBlock>(T, q, maxd2, stk, status)
+                        : nearest<kQueryBlock>(T, q, maxd2, stk, status);
     write_hit(T, h, q, i, face, bary, point, dist2);
 }
 
@@ -618,6 +693,7 @@ static size_t chamfer_blocks(int64_t n, int G = 1) {
 // of two G <= 32 that does.  (An explicit override can come from
 // mesh_set_query_group.)
 static int g_group_override = 0;
+static int g_traversal = 0;          // one-thread traversal: 0 depth-first, 1 while-while
 static int pick_group(int64_t nQ) {
     if (g_group_override > 0) return g_group_override;
     static int sms = 0;
@@ -652,7 +728,12 @@ mesh_status mesh_closest_point(const mesh_bvh *bvh, const float *d_Q, int64_t nQ
     Header *h = bvh->hdr();
     unsigned int grid = grid_for(nQ * G, kQueryBlock);
     switch (G) {
-        case 1: k_closest_point<<<grid, kQueryBlock, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2); break;
+        case 1:
+            if (g_traversal == 1)
+                k_closest_point<true><<<grid, kQueryBlock, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2);
+            else
+                k_closest_point<false><<<grid, kQueryBlock, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2);
+            break;
         case 2: k_closest_point_group<2><<<grid, kQueryBlock, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2); break;
         case 4: k_closest_point_group<4><<<grid, kQueryBlock, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2); break;
         case 8: k_closest_point_group<8><<<grid, kQueryBlock, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2); break;
@@ -707,6 +788,12 @@ mesh_status mesh_set_query_group(int lanes) {
         lanes != 32)
         return MESH_ERR_INVALID_ARG;
     g_group_override = lanes;
+    return MESH_OK;
+}
+
+mesh_status mesh_set_traversal(int variant) {
+    if (variant != 0 && variant != 1) return MESH_ERR_INVALID_ARG;
+    g_traversal = variant;
     return MESH_OK;
 }
 

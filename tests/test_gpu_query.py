@@ -143,3 +143,18 @@ def test_every_group_width_matches_oracle(c1, lanes):
         assert bvh.status()[0] == 0 and centre.status()[0] == 0
     finally:
         set_query_group(0)
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_both_thread_traversals_match_oracle(c1, variant):
+    from paper_2606_00444_gb300 import set_query_group, set_traversal
+    _, _, VG, FG, Q = c1
+    bvh = MeshBVH.from_mesh(dev(VG), dev(FG))
+    try:
+        set_query_group(1)
+        set_traversal(variant)
+        check_closest(VG, FG, Q, bvh.closest_point(dev(Q)))
+        check_closest(VG, FG, Q, bvh.closest_point(dev(Q), max_dist=0.05), max_dist=0.05)
+    finally:
+        set_query_group(0)
+        set_traversal(0)

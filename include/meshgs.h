@@ -241,6 +241,73 @@ mesh_status mesh_bind_gaussians_backward(const mesh_bvh *bvh, const int32_t *d_g
                                          const float *d_gscale, float *d_gV, void *stream);
 
 /* ---------------------------------------------------------------- */
+/* Batched forms: many independent scenes in one storage block       */
+/* ---------------------------------------------------------------- */
+/* Scenes are concatenated: vertices [nV][3] with device offsets vert_off
+ * [B+1], faces [nF][3] holding SCENE-LOCAL vertex indices with face_off [B+1]
+ * (int32, non-decreasing, off[0] = 0, off[B] = total; empty scenes allowed).
+ * Each scene gets its own LBVH, identical to the one mesh_build_lbvh builds for
+ * that scene alone, but every phase runs as one launch over all scenes, and
+ * queries / Gaussians of all scenes go through one persistent launch (warps
+ * pull work in chunks from a counter), so per-scene launch overhead vanishes
+ * and the whole frame can be captured in one CUDA graph. */
+typedef struct mesh_batch mesh_batch;
+
+typedef struct {
+    int64_t n_scenes, n_verts, n_faces, max_scenes, max_verts, max_faces;
+    size_t off_scene;        /* per scene: float4 root_lo, float4 root_hi            */
+    size_t off_status;       /* uint32 status, uint32 n_degenerate, uint32 work counter */
+    size_t off_vert_off;     /* int32 [max_scenes + 1] copy of vert_off              */
+    size_t off_face_off;     /* int32 [max_scenes + 1] copy of face_off              */
+    size_t off_verts;        /* float4 [max_verts]                                   */
+    size_t off_faces;        /* int4 [max_faces]  GLOBAL vertex indices, .w = scene    */
+    size_t off_keys;         /* uint32 [max_faces] Morton keys, leaf order per scene  */
+    size_t off_perm;         /* int32 [max_faces]  global face id of leaf (face_off[s] + j) */
+    size_t off_nodes;        /* 64 B records; scene s's internal node i at face_off[s] + i */
+    size_t off_parent_int;   /* int32 [max_faces]  2 * local parent + side, -1 at a root  */
+    size_t off_parent_leaf;  /* int32 [max_faces]                                        */
+    size_t off_tris;         /* 48 B per leaf, global leaf order                          */
+    size_t off_flags;        /* uint32 [max_faces]                                        */
+    size_t storage_bytes;
+} mesh_batch_layout;
+
+size_t mesh_batch_storage_bytes(int64_t max_scenes, int64_t max_verts, int64_t max_faces);
+size_t mesh_batch_workspace_bytes(int64_t max_scenes, int64_t max_faces);
+mesh_status mesh_batch_create(void *d_storage, size_t storage_bytes, int64_t max_scenes,
+                              int64_t max_verts, int64_t max_faces, mesh_batch **out);
+void mesh_batch_destroy(mesh_batch *batch);
+mesh_status mesh_batch_get_layout(const mesh_batch *batch, mesh_batch_layout *out);
+
+/* Build all scenes' LBVHs (one launch per phase for the whole batch). */
+mesh_status mesh_batch_build(mesh_batch *batch, int64_t n_scenes, const float *d_V,
+                             const int32_t *d_vert_off, int64_t nV, const int32_t *d_F,
+                             const int32_t *d_face_off, int64_t nF, void *d_ws, size_t ws_bytes,
+                             void *stream);
+
+/* Vertex-buffer update [nV][3] (same offsets) and refit of every scene. */
+mesh_status mesh_batch_refit(mesh_batch *batch, const float *d_V, int64_t nV, void *stream);
+
+/* Closest point for queries of every scene: query i belongs to scene s with
+ * query_off[s] <= i < query_off[s+1] (device, int32 [B+1]).  Outputs as
+ * mesh_closest_point, face ids SCENE-LOCAL.  One persistent launch. */
+mesh_status mesh_batch_closest_point(mesh_batch *batch, const float *d_Q,
+                                     const int32_t *d_query_off, int64_t nQ, float max_dist,
+                                     int32_t *d_face, float *d_bary, float *d_point,
+                                     float *d_dist2, void *stream);
+
+/* Face-bound Gaussians of every scene: Gaussian g belongs to scene s with
+ * gauss_off[s] <= g < gauss_off[s+1]; d_gface holds SCENE-LOCAL face ids.
+ * Formula and outputs as mesh_bind_gaussians. */
+mesh_status mesh_batch_bind_gaussians(mesh_batch *batch, const int32_t *d_gface,
+                                      const int32_t *d_gauss_off, const float *d_gbary,
+                                      const float *d_goff, int64_t nG, float *d_mu,
+                                      float *d_quat, float *d_scale, void *stream);
+
+/* Read and clear the batch's device status bits (as mesh_bvh_status). */
+mesh_status mesh_batch_status(mesh_batch *batch, uint32_t *bits, uint32_t *n_degenerate,
+                              void *stream);
+
+/* ---------------------------------------------------------------- */
 /* Status and diagnostics                                            */
 /* ---------------------------------------------------------------- */
 

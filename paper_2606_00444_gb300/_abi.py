@@ -29,6 +29,15 @@ class Layout(C.Structure):
                 ("off_flags", SZ), ("storage_bytes", SZ)]
 
 
+class BatchLayout(C.Structure):
+    _fields_ = [("n_scenes", I64), ("n_verts", I64), ("n_faces", I64), ("max_scenes", I64),
+                ("max_verts", I64), ("max_faces", I64), ("off_scene", SZ), ("off_status", SZ),
+                ("off_vert_off", SZ), ("off_face_off", SZ), ("off_verts", SZ), ("off_faces", SZ),
+                ("off_keys", SZ), ("off_perm", SZ), ("off_nodes", SZ), ("off_parent_int", SZ),
+                ("off_parent_leaf", SZ), ("off_tris", SZ), ("off_flags", SZ),
+                ("storage_bytes", SZ)]
+
+
 SIGNATURES = {
     "mesh_bvh_storage_bytes": (SZ, [I64, I64]),
     "mesh_build_workspace_bytes": (SZ, [I64]),
@@ -51,6 +60,16 @@ SIGNATURES = {
     "mesh_closest_point_backward": (C.c_int, [VP, VP, I64, VP, VP, VP, VP, VP, VP]),
     "mesh_interpolate_backward": (C.c_int, [VP, VP, VP, I64, VP, VP, VP]),
     "mesh_bind_gaussians_backward": (C.c_int, [VP, VP, VP, VP, I64, VP, VP, VP, VP, VP]),
+    "mesh_batch_storage_bytes": (SZ, [I64, I64, I64]),
+    "mesh_batch_workspace_bytes": (SZ, [I64, I64]),
+    "mesh_batch_create": (C.c_int, [VP, SZ, I64, I64, I64, C.POINTER(VP)]),
+    "mesh_batch_destroy": (None, [VP]),
+    "mesh_batch_get_layout": (C.c_int, [VP, C.POINTER(BatchLayout)]),
+    "mesh_batch_build": (C.c_int, [VP, I64, VP, VP, I64, VP, VP, I64, VP, SZ, VP]),
+    "mesh_batch_refit": (C.c_int, [VP, VP, I64, VP]),
+    "mesh_batch_closest_point": (C.c_int, [VP, VP, VP, I64, C.c_float, VP, VP, VP, VP, VP]),
+    "mesh_batch_bind_gaussians": (C.c_int, [VP, VP, VP, VP, VP, I64, VP, VP, VP, VP]),
+    "mesh_batch_status": (C.c_int, [VP, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), VP]),
     "mesh_bvh_status": (C.c_int, [VP, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), VP]),
     "mesh_status_string": (C.c_char_p, [C.c_int]),
     "mesh_launch_count": (C.c_uint64, []),

@@ -220,6 +220,145 @@ class MeshBVH:
         return out
 
 
+def _offsets(counts, device) -> torch.Tensor:
+    off = [0]
+    for c in counts:
+        off.append(off[-1] + int(c))
+    return torch.tensor(off, dtype=torch.int32, device=device)
+
+
+class MeshBatch:
+    """Many independent meshes (scenes) in one storage block, each with its own LBVH.
+
+    Vertices / faces are concatenated with int32 CSR offsets; faces hold
+    scene-local vertex indices.  Every phase of the build, the queries and the
+    Gaussian update run as single launches over all scenes.
+    """
+
+    def __init__(self, max_scenes: int, max_verts: int, max_faces: int, device="cuda"):
+        self.device = torch.device(device)
+        nbytes = lib().mesh_batch_storage_bytes(max_scenes, max_verts, max_faces)
+        if nbytes == 0:
+            raise ValueError("batch too large")
+        self.storage = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        h = C.c_void_p()
+        check(lib().mesh_batch_create(self.storage.data_ptr(), nbytes, max_scenes, max_verts,
+                                      max_faces, C.byref(h)), "mesh_batch_create")
+        self.handle = h
+        self._ws = Workspace(self.device)
+        self.vert_off = self.face_off = None
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            try:
+                lib().mesh_batch_destroy(h)
+            except Exception:
+                pass
+            self.handle = None
+
+    @staticmethod
+    def concat(meshes, device="cuda"):
+        """(V [sum V, 3], vert_off, F [sum F, 3] scene-local, face_off) from [(V_s, F_s)]."""
+        V = torch.cat([torch.as_tensor(v, dtype=torch.float32) for v, _ in meshes]).to(device)
+        F = torch.cat([torch.as_tensor(f, dtype=torch.int32) for _, f in meshes]).to(device)
+        return (V.contiguous(), _offsets([len(v) for v, _ in meshes], device), F.contiguous(),
+                _offsets([len(f) for _, f in meshes], device))
+
+    @classmethod
+    def from_meshes(cls, meshes, device="cuda") -> "MeshBatch":
+        V, vo, F, fo = cls.concat(meshes, device)
+        b = cls(len(meshes), V.shape[0], F.shape[0], device)
+        b.build(V, vo, F, fo)
+        return b
+
+    def build(self, V, vert_off, F, face_off):
+        V = _f32(V, 3, "V")
+        F = _i32(F, 3, "F")
+        vert_off, face_off = _i32(vert_off, None, "vert_off"), _i32(face_off, None, "face_off")
+        B = face_off.shape[0] - 1
+        ws = self._ws.get(lib().mesh_batch_workspace_bytes(B, F.shape[0]))
+        check(lib().mesh_batch_build(self.handle, B, V.data_ptr(), vert_off.data_ptr(), V.shape[0],
+                                     F.data_ptr(), face_off.data_ptr(), F.shape[0], ws.data_ptr(),
+                                     ws.numel(), _stream()), "mesh_batch_build")
+        self.vert_off, self.face_off = vert_off, face_off
+        return self
+
+    def refit(self, V=None):
+        if V is not None:
+            V = _f32(V, 3, "V")
+        check(lib().mesh_batch_refit(self.handle, _ptr(V), 0 if V is None else V.shape[0],
+                                     _stream()), "mesh_batch_refit")
+
+    def closest_point(self, Q, query_off, max_dist=math.inf, want=("face", "bary", "point", "dist2"),
+                      out=None):
+        Q = _f32(Q, 3, "Q")
+        query_off = _i32(query_off, None, "query_off")
+        n = Q.shape[0]
+        out = {} if out is None else out
+        if "face" in want and "face" not in out:
+            out["face"] = torch.empty(n, dtype=torch.int32, device=Q.device)
+        for k in ("bary", "point"):
+            if k in want and k not in out:
+                out[k] = torch.empty(n, 3, device=Q.device)
+        if "dist2" in want and "dist2" not in out:
+            out["dist2"] = torch.empty(n, device=Q.device)
+        check(lib().mesh_batch_closest_point(self.handle, Q.data_ptr(), query_off.data_ptr(), n,
+                                             float(max_dist), _ptr(out.get("face")),
+                                             _ptr(out.get("bary")), _ptr(out.get("point")),
+                                             _ptr(out.get("dist2")), _stream()),
+              "mesh_batch_closest_point")
+        return out
+
+    def bind_gaussians(self, gface, gauss_off, gbary, goff=None, out=None):
+        gface = _i32(gface, None, "gface")
+        gauss_off = _i32(gauss_off, None, "gauss_off")
+        gbary = _f32(gbary, 3, "gbary")
+        n = gface.shape[0]
+        if out is None:
+            out = (torch.empty(n, 3, device=gface.device), torch.empty(n, 4, device=gface.device),
+                   torch.empty(n, 3, device=gface.device))
+        mu, quat, scale = out
+        check(lib().mesh_batch_bind_gaussians(self.handle, gface.data_ptr(), gauss_off.data_ptr(),
+                                              gbary.data_ptr(),
+                                              _ptr(None if goff is None else _f32(goff)), n,
+                                              mu.data_ptr(), quat.data_ptr(), scale.data_ptr(),
+                                              _stream()), "mesh_batch_bind_gaussians")
+        return mu, quat, scale
+
+    def status(self):
+        bits, ndeg = C.c_uint32(), C.c_uint32()
+        st = lib().mesh_batch_status(self.handle, C.byref(bits), C.byref(ndeg), _stream())
+        if st not in (_abi.MESH_OK, _abi.MESH_ERR_DEVICE):
+            check(st, "mesh_batch_status")
+        return bits.value, ndeg.value
+
+    def layout(self) -> dict:
+        L = _abi.BatchLayout()
+        check(lib().mesh_batch_get_layout(self.handle, C.byref(L)), "mesh_batch_get_layout")
+        return {k: getattr(L, k) for k, _ in _abi.BatchLayout._fields_}
+
+    def arrays(self) -> dict:
+        L = self.layout()
+        n, B = L["n_faces"], L["n_scenes"]
+        s = self.storage
+
+        def view(off, count, dtype, shape):
+            nbytes = count * torch.tensor([], dtype=dtype).element_size()
+            return s[off:off + nbytes].view(dtype).reshape(shape)
+
+        return dict(
+            scene_box=view(L["off_scene"], 8 * B, torch.float32, (B, 2, 4))[:, :, :3],
+            keys=view(L["off_keys"], n, torch.int32, (n,)),
+            perm=view(L["off_perm"], n, torch.int32, (n,)),
+            nodes=view(L["off_nodes"], 16 * n, torch.float32, (n, 4, 4)),
+            nodes_i=view(L["off_nodes"], 16 * n, torch.int32, (n, 4, 4)),
+            parent_int=view(L["off_parent_int"], n, torch.int32, (n,)),
+            parent_leaf=view(L["off_parent_leaf"], n, torch.int32, (n,)),
+            tris=view(L["off_tris"], 12 * n, torch.float32, (n, 3, 4)),
+        )
+
+
 def chamfer(A: MeshBVH, SA: torch.Tensor, B: MeshBVH, SB: torch.Tensor, per_sample=False,
             ws: Workspace | None = None, out: torch.Tensor | None = None):
     """[mean d(SA, B)^2, mean d(SB, A)^2] (float64) and optional per-sample results."""

@@ -31,6 +31,43 @@ struct mesh_bvh_impl {
     unsigned int *flags() const { return reinterpret_cast<unsigned int *>(base + L.off_flags); }
 };
 
+struct BatchStatus {
+    unsigned int status;
+    unsigned int n_degenerate;
+    unsigned int work;       // persistent-kernel work counter
+    unsigned int pad;
+};
+
+struct mesh_batch_impl {
+    char *base;
+    mesh_batch_layout L;
+    float4 *scene_box() const { return reinterpret_cast<float4 *>(base + L.off_scene); }
+    BatchStatus *st() const { return reinterpret_cast<BatchStatus *>(base + L.off_status); }
+    int *vert_off() const { return reinterpret_cast<int *>(base + L.off_vert_off); }
+    int *face_off() const { return reinterpret_cast<int *>(base + L.off_face_off); }
+    float4 *verts() const { return reinterpret_cast<float4 *>(base + L.off_verts); }
+    int4 *faces() const { return reinterpret_cast<int4 *>(base + L.off_faces); }
+    unsigned int *keys() const { return reinterpret_cast<unsigned int *>(base + L.off_keys); }
+    int *perm() const { return reinterpret_cast<int *>(base + L.off_perm); }
+    float4 *nodes() const { return reinterpret_cast<float4 *>(base + L.off_nodes); }
+    int *parent_int() const { return reinterpret_cast<int *>(base + L.off_parent_int); }
+    int *parent_leaf() const { return reinterpret_cast<int *>(base + L.off_parent_leaf); }
+    float4 *tris() const { return reinterpret_cast<float4 *>(base + L.off_tris); }
+    unsigned int *flags() const { return reinterpret_cast<unsigned int *>(base + L.off_flags); }
+};
+
+// Largest s in [0, n) with off[s] <= x (off non-decreasing, off[0] = 0): the
+// non-empty segment that contains x.
+__device__ __forceinline__ int segment_of(const int *__restrict__ off, int n, int64_t x) {
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (__ldg(off + mid) <= x) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
 // Host-side bookkeeping shared by the entry points.
 void count_launch(int n = 1);
 mesh_status check_launch();
@@ -55,3 +92,4 @@ __device__ __forceinline__ void set_status(Header *h, unsigned int bit) {
 }  // namespace meshgs
 
 struct mesh_bvh : meshgs::mesh_bvh_impl {};
+struct mesh_batch : meshgs::mesh_batch_impl {};

@@ -106,33 +106,20 @@ __device__ __forceinline__ void frame_matrix(const Frame &F, float R[3][3]) {
     R[2][0] = F.e1.z; R[2][1] = F.e2.z; R[2][2] = F.n.z;
 }
 
-__global__ void k_bind_gaussians(const int4 *__restrict__ faces, const float4 *__restrict__ verts,
-                                 int nF, const int *__restrict__ gface,
-                                 const float *__restrict__ gbary, const float *__restrict__ goff,
-                                 int64_t nG, float *__restrict__ mu, float *__restrict__ quat,
-                                 float *__restrict__ scale, Header *hdr) {
-    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= nG) return;
-    int f = gface[g];
-    if ((unsigned)f >= (unsigned)nF) {
-        set_status(hdr, MESH_DEV_INDEX_RANGE);
-        mu[3 * g] = mu[3 * g + 1] = mu[3 * g + 2] = 0.0f;
-        quat[4 * g] = 1.0f; quat[4 * g + 1] = quat[4 * g + 2] = quat[4 * g + 3] = 0.0f;
-        scale[3 * g] = scale[3 * g + 1] = scale[3 * g + 2] = 0.0f;
-        return;
-    }
-    int4 fv = faces[f];
+// One Gaussian on the face with global vertex indices fv.
+__device__ __forceinline__ void bind_one(int4 fv, const float4 *__restrict__ verts, float b0, float b1,
+                                         float b2, float off, int64_t g, float *__restrict__ mu,
+                                         float *__restrict__ quat, float *__restrict__ scale,
+                                         unsigned int *status, unsigned int *n_degenerate) {
     V3 a = v3(verts[fv.x]), b = v3(verts[fv.y]), c = v3(verts[fv.z]);
-    float b0 = gbary[3 * g], b1 = gbary[3 * g + 1], b2 = gbary[3 * g + 2];
     V3 m = a * b0 + b * b1 + c * b2;
     Frame F = face_frame(a, b, c);
     float q[4] = {1.0f, 0.0f, 0.0f, 0.0f};
     float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f;
     if (F.degenerate) {
-        atomicAdd(&hdr->n_degenerate, 1u);
-        set_status(hdr, MESH_DEV_DEGENERATE);
+        atomicAdd(n_degenerate, 1u);
+        atomicOr(status, (unsigned)MESH_DEV_DEGENERATE);
     } else {
-        float off = goff ? goff[g] : 0.0f;
         m = m + F.n * off;
         float R[3][3], p;
         frame_matrix(F, R);
@@ -147,6 +134,48 @@ __global__ void k_bind_gaussians(const int4 *__restrict__ faces, const float4 *_
     mu[3 * g] = m.x; mu[3 * g + 1] = m.y; mu[3 * g + 2] = m.z;
     quat[4 * g] = q[0]; quat[4 * g + 1] = q[1]; quat[4 * g + 2] = q[2]; quat[4 * g + 3] = q[3];
     scale[3 * g] = s0; scale[3 * g + 1] = s1; scale[3 * g + 2] = s2;
+}
+
+__device__ __forceinline__ void bind_invalid(int64_t g, float *mu, float *quat, float *scale,
+                                             unsigned int *status) {
+    atomicOr(status, (unsigned)MESH_DEV_INDEX_RANGE);
+    mu[3 * g] = mu[3 * g + 1] = mu[3 * g + 2] = 0.0f;
+    quat[4 * g] = 1.0f; quat[4 * g + 1] = quat[4 * g + 2] = quat[4 * g + 3] = 0.0f;
+    scale[3 * g] = scale[3 * g + 1] = scale[3 * g + 2] = 0.0f;
+}
+
+__global__ void k_bind_gaussians(const int4 *__restrict__ faces, const float4 *__restrict__ verts,
+                                 int nF, const int *__restrict__ gface,
+                                 const float *__restrict__ gbary, const float *__restrict__ goff,
+                                 int64_t nG, float *__restrict__ mu, float *__restrict__ quat,
+                                 float *__restrict__ scale, Header *hdr) {
+    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= nG) return;
+    int f = gface[g];
+    if ((unsigned)f >= (unsigned)nF) { bind_invalid(g, mu, quat, scale, &hdr->status); return; }
+    bind_one(faces[f], verts, gbary[3 * g], gbary[3 * g + 1], gbary[3 * g + 2],
+             goff ? goff[g] : 0.0f, g, mu, quat, scale, &hdr->status, &hdr->n_degenerate);
+}
+
+// Batched form: Gaussian g of scene s (gauss_off), face id local to s.  Grid-
+// stride loop over all Gaussians of all scenes.
+__global__ void k_batch_bind_gaussians(const int4 *__restrict__ faces, const float4 *__restrict__ verts,
+                                       const int *__restrict__ face_off,
+                                       const int *__restrict__ gauss_off, int nscenes,
+                                       const int *__restrict__ gface,
+                                       const float *__restrict__ gbary,
+                                       const float *__restrict__ goff, int64_t nG,
+                                       float *__restrict__ mu, float *__restrict__ quat,
+                                       float *__restrict__ scale, BatchStatus *st) {
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nG;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        int sc = segment_of(gauss_off, nscenes, g);
+        int fb = __ldg(face_off + sc), ns = __ldg(face_off + sc + 1) - fb;
+        int f = gface[g];
+        if ((unsigned)f >= (unsigned)ns) { bind_invalid(g, mu, quat, scale, &st->status); continue; }
+        bind_one(faces[fb + f], verts, gbary[3 * g], gbary[3 * g + 1], gbary[3 * g + 2],
+                 goff ? goff[g] : 0.0f, g, mu, quat, scale, &st->status, &st->n_degenerate);
+    }
 }
 
 __device__ __forceinline__ void add_grad(float *gV, int v, V3 g) {
@@ -246,6 +275,31 @@ mesh_status mesh_bind_gaussians(const mesh_bvh *bvh, const int32_t *d_gface, con
     k_bind_gaussians<<<grid_for(nG, 256), 256, 0, s>>>(bvh->faces(), bvh->verts(),
                                                        (int)bvh->L.n_faces, d_gface, d_gbary, d_goff,
                                                        nG, d_mu, d_quat, d_scale, bvh->hdr());
+    count_launch();
+    return check_launch();
+}
+
+mesh_status mesh_batch_bind_gaussians(mesh_batch *batch, const int32_t *d_gface,
+                                      const int32_t *d_gauss_off, const float *d_gbary,
+                                      const float *d_goff, int64_t nG, float *d_mu,
+                                      float *d_quat, float *d_scale, void *stream) {
+    if (!batch || nG < 0 ||
+        (nG > 0 && (!d_gface || !d_gauss_off || !d_gbary || !d_mu || !d_quat || !d_scale)))
+        return MESH_ERR_INVALID_ARG;
+    if (nG == 0) return MESH_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+            sms = 152;
+    }
+    int64_t want = (nG + 255) / 256;
+    unsigned int grid = (unsigned int)(want < (int64_t)sms * 8 ? want : (int64_t)sms * 8);
+    k_batch_bind_gaussians<<<grid, 256, 0, s>>>(batch->faces(), batch->verts(), batch->face_off(),
+                                                d_gauss_off, (int)batch->L.n_scenes, d_gface, d_gbary,
+                                                d_goff, nG, d_mu, d_quat, d_scale, batch->st());
     count_launch();
     return check_launch();
 }

@@ -362,10 +362,9 @@ __device__ __forceinline__ int kdelta(const unsigned int *__restrict__ k, int n,
     return a != b ? __clz(a ^ b) : 32 + __clz((unsigned)i ^ (unsigned)j);
 }
 
-__global__ void k_karras(const unsigned int *__restrict__ keys, int n, float4 *__restrict__ nodes,
-                         int *__restrict__ parent) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n - 1) return;
+// Children of internal node i of the tree over keys[0, n) (Karras 2012).
+__device__ __forceinline__ void karras_children(const unsigned int *__restrict__ keys, int n, int i,
+                                                int &left, int &right) {
     int d = (kdelta(keys, n, i, i + 1) - kdelta(keys, n, i, i - 1)) >= 0 ? 1 : -1;
     int dmin = kdelta(keys, n, i, i - d);
     int lmax = 2;
@@ -383,13 +382,25 @@ __global__ void k_karras(const unsigned int *__restrict__ keys, int n, float4 *_
     } while (t > 1);
     int gamma = i + s * d + min(d, 0);
     int lo = min(i, j), hi = max(i, j);
-    int left = (lo == gamma) ? -(gamma + 1) : gamma;
-    int right = (hi == gamma + 1) ? -(gamma + 2) : gamma + 1;
+    left = (lo == gamma) ? -(gamma + 1) : gamma;
+    right = (hi == gamma + 1) ? -(gamma + 2) : gamma + 1;
+}
+
+__device__ __forceinline__ void write_children(float4 *__restrict__ nodes, int i, int left, int right) {
     float *rec = reinterpret_cast<float *>(nodes + 4 * (size_t)i);
     rec[3] = __int_as_float(left);
     rec[7] = __int_as_float(left);
     rec[11] = __int_as_float(right);
     rec[15] = __int_as_float(right);
+}
+
+__global__ void k_karras(const unsigned int *__restrict__ keys, int n, float4 *__restrict__ nodes,
+                         int *__restrict__ parent) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    int left, right;
+    karras_children(keys, n, i, left, right);
+    write_children(nodes, i, left, right);
     parent[left >= 0 ? left : (n - 1) + (-left - 1)] = 2 * i;
     parent[right >= 0 ? right : (n - 1) + (-right - 1)] = 2 * i + 1;
     if (i == 0) parent[0] = -1;
@@ -453,6 +464,157 @@ __global__ void k_leaves_up(int n, const int *__restrict__ perm, const int4 *__r
 }
 
 // ---------------------------------------------------------------------------
+// Batched build: the same steps over many scenes at once.  Faces carry scene-
+// local vertex indices; offsets give each scene's vertex and face range.
+// ---------------------------------------------------------------------------
+__global__ void k_batch_init(unsigned int *__restrict__ cbox, int nscenes) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < 6 * nscenes) cbox[i] = (i % 6 < 3) ? 0xffffffffu : 0u;
+}
+
+__global__ void k_batch_faces(const int *__restrict__ F3, int nF, const int *__restrict__ vert_off,
+                              const int *__restrict__ face_off, int nscenes,
+                              const float4 *__restrict__ V4, int4 *__restrict__ F4,
+                              float4 *__restrict__ cent, unsigned int *__restrict__ cbox,
+                              unsigned int *__restrict__ status) {
+    int f = blockIdx.x * blockDim.x + threadIdx.x;
+    bool valid = f < nF;
+    int sc = valid ? segment_of(face_off, nscenes, f) : -1;
+    float s3[3] = {0.f, 0.f, 0.f};
+    if (valid) {
+        int vb = __ldg(vert_off + sc), nv = __ldg(vert_off + sc + 1) - vb;
+        const int *p = F3 + 3 * (size_t)f;
+        int i0 = p[0], i1 = p[1], i2 = p[2];
+        if ((unsigned)i0 >= (unsigned)nv || (unsigned)i1 >= (unsigned)nv || (unsigned)i2 >= (unsigned)nv) {
+            atomicOr(status, (unsigned)MESH_DEV_INDEX_RANGE);
+            if ((unsigned)i0 >= (unsigned)nv) i0 = 0;
+            if ((unsigned)i1 >= (unsigned)nv) i1 = 0;
+            if ((unsigned)i2 >= (unsigned)nv) i2 = 0;
+        }
+        i0 += vb; i1 += vb; i2 += vb;
+        F4[f] = make_int4(i0, i1, i2, sc);
+        float4 a = V4[i0], b = V4[i1], c = V4[i2];
+        s3[0] = __fadd_rn(__fadd_rn(a.x, b.x), c.x);
+        s3[1] = __fadd_rn(__fadd_rn(a.y, b.y), c.y);
+        s3[2] = __fadd_rn(__fadd_rn(a.z, b.z), c.z);
+        cent[f] = make_float4(s3[0], s3[1], s3[2], 0.0f);
+    }
+    // one atomic per scene present in the warp
+    unsigned int peers = __match_any_sync(0xffffffffu, sc);
+    for (int k = 0; k < 3; ++k) {
+        unsigned int lo = __reduce_min_sync(peers, valid ? f2ord(s3[k]) : 0xffffffffu);
+        unsigned int hi = __reduce_max_sync(peers, valid ? f2ord(s3[k]) : 0u);
+        if (valid && (peers & ((1u << (threadIdx.x & 31)) - 1u)) == 0u) {
+            atomicMin(&cbox[6 * sc + k], lo);
+            atomicMax(&cbox[6 * sc + 3 + k], hi);
+        }
+    }
+}
+
+__global__ void k_batch_morton(const float4 *__restrict__ cent, int nF, const int4 *__restrict__ F4,
+                               const unsigned int *__restrict__ cbox,
+                               unsigned int *__restrict__ key_of_face,
+                               unsigned int *__restrict__ keys, int *__restrict__ vals) {
+    int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nF) return;
+    const unsigned int *bx = cbox + 6 * F4[f].w;
+    float4 s = cent[f];
+    float sv[3] = {s.x, s.y, s.z};
+    unsigned int q[3];
+    for (int k = 0; k < 3; ++k) {
+        float lo = ord2f(bx[k]);
+        float ext = __fsub_rn(ord2f(bx[3 + k]), lo);
+        float inv = ext > 0.0f ? __fdiv_rn(1.0f, ext) : 0.0f;
+        float t = __fmul_rn(__fsub_rn(sv[k], lo), inv);
+        int qi = (int)floorf(__fmul_rn(t, 1024.0f));
+        qi = qi < 0 ? 0 : (qi > 1023 ? 1023 : qi);
+        q[k] = (unsigned int)qi;
+    }
+    unsigned int key = (spread3(q[0]) << 2) | (spread3(q[1]) << 1) | spread3(q[2]);
+    key_of_face[f] = key;
+    keys[f] = key;
+    vals[f] = f;
+}
+
+// Scene id of each (Morton-sorted) face, as the key of the last, stable pass.
+__global__ void k_batch_scene_keys(const int *__restrict__ vals, int n, const int4 *__restrict__ F4,
+                                   unsigned int *__restrict__ keys) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) keys[j] = (unsigned int)F4[vals[j]].w;
+}
+
+__global__ void k_batch_gather_keys(const int *__restrict__ perm, int n,
+                                    const unsigned int *__restrict__ key_of_face,
+                                    unsigned int *__restrict__ keys) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) keys[j] = key_of_face[perm[j]];
+}
+
+__global__ void k_batch_karras(const unsigned int *__restrict__ keys, int nF,
+                               const int *__restrict__ face_off, int nscenes,
+                               float4 *__restrict__ nodes, int *__restrict__ parent_int,
+                               int *__restrict__ parent_leaf) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nF) return;
+    int sc = segment_of(face_off, nscenes, j);
+    int base = __ldg(face_off + sc), n = __ldg(face_off + sc + 1) - base, i = j - base;
+    if (n == 1) { parent_leaf[base] = -1; return; }
+    if (i >= n - 1) return;
+    int left, right;
+    karras_children(keys + base, n, i, left, right);
+    write_children(nodes + 4 * (size_t)base, i, left, right);
+    if (left >= 0) parent_int[base + left] = 2 * i; else parent_leaf[base - left - 1] = 2 * i;
+    if (right >= 0) parent_int[base + right] = 2 * i + 1; else parent_leaf[base - right - 1] = 2 * i + 1;
+    if (i == 0) parent_int[base] = -1;
+}
+
+// Bottom-up boxes of every scene (build and refit), as k_leaves_up per scene.
+__global__ void k_batch_leaves_up(int nF, const int *__restrict__ face_off, int nscenes,
+                                  const int *__restrict__ perm, const int4 *__restrict__ faces,
+                                  const float4 *__restrict__ verts, float4 *__restrict__ tris,
+                                  float4 *__restrict__ nodes, const int *__restrict__ parent_int,
+                                  const int *__restrict__ parent_leaf,
+                                  unsigned int *__restrict__ flags, float4 *__restrict__ scene_box) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nF) return;
+    int sc = segment_of(face_off, nscenes, j);
+    int base = __ldg(face_off + sc);
+    int f = perm[j];
+    int4 fv = faces[f];
+    float4 a = verts[fv.x], b = verts[fv.y], c = verts[fv.z];
+    float deg = exactly_degenerate(a, b, c) ? 1.0f : 0.0f;
+    tris[3 * (size_t)j + 0] = make_float4(a.x, a.y, a.z, __int_as_float(f));
+    tris[3 * (size_t)j + 1] = make_float4(b.x, b.y, b.z, deg);
+    tris[3 * (size_t)j + 2] = make_float4(c.x, c.y, c.z, 0.0f);
+    float3 lo = make_float3(fminf(fminf(a.x, b.x), c.x), fminf(fminf(a.y, b.y), c.y),
+                            fminf(fminf(a.z, b.z), c.z));
+    float3 hi = make_float3(fmaxf(fmaxf(a.x, b.x), c.x), fmaxf(fmaxf(a.y, b.y), c.y),
+                            fmaxf(fmaxf(a.z, b.z), c.z));
+    float4 *snodes = nodes + 4 * (size_t)base;
+    int self = -(j - base + 1);
+    int pe = parent_leaf[j];
+    while (pe >= 0) {
+        int p = pe >> 1, side = pe & 1;
+        float4 *rec = snodes + 4 * (size_t)p;
+        rec[2 * side] = make_float4(lo.x, lo.y, lo.z, __int_as_float(self));
+        rec[2 * side + 1] = make_float4(hi.x, hi.y, hi.z, __int_as_float(self));
+        __threadfence();
+        unsigned int old = atomicAdd(&flags[base + p], 1u);
+        if (old == 0u) return;
+        __threadfence();
+        int o = 1 - side;
+        float4 olo = __ldcg(rec + 2 * o), ohi = __ldcg(rec + 2 * o + 1);
+        lo = make_float3(fminf(lo.x, olo.x), fminf(lo.y, olo.y), fminf(lo.z, olo.z));
+        hi = make_float3(fmaxf(hi.x, ohi.x), fmaxf(hi.y, ohi.y), fmaxf(hi.z, ohi.z));
+        flags[base + p] = 0u;
+        self = p;
+        pe = parent_int[base + p];
+    }
+    scene_box[2 * sc] = make_float4(lo.x, lo.y, lo.z, 0.0f);
+    scene_box[2 * sc + 1] = make_float4(hi.x, hi.y, hi.z, 0.0f);
+}
+
+// ---------------------------------------------------------------------------
 // Build workspace layout.
 // ---------------------------------------------------------------------------
 struct BuildWs {
@@ -497,6 +659,58 @@ static void radix_sort_pairs(const BuildWs &w, int n, unsigned int *out_keys, in
         unsigned int *tk = kin; kin = kout; kout = tk;
         int *tv = vin; vin = vout; vout = tv;
     }
+}
+
+static void radix_pass(const BuildWs &w, int n, int shift, const unsigned int *kin, const int *vin,
+                       unsigned int *kout, int *vout, cudaStream_t s) {
+    k_sort_upsweep<<<w.tiles, kSortThreads, 0, s>>>(kin, n, shift, w.hist, w.tiles);
+    k_sort_scan<<<1, kScanThreads, 0, s>>>(w.hist, kRadix * w.tiles);
+    k_sort_downsweep<<<w.tiles, kSortThreads, 0, s>>>(kin, vin, kout, vout, n, shift, w.hist, w.tiles);
+    count_launch(3);
+}
+
+struct BatchWs {
+    BuildWs sort;
+    unsigned int *key_of_face, *cbox;
+    size_t bytes;
+};
+
+static BatchWs batch_ws_layout(char *base, int64_t nscenes, int64_t nF) {
+    BatchWs w{};
+    w.sort = build_ws_layout(base, nF);
+    size_t off = w.sort.bytes;
+    int64_t n = nF > 0 ? nF : 1;
+    w.key_of_face = (unsigned int *)(base + off);
+    off = align_up(off + 4 * n, 256);
+    w.cbox = (unsigned int *)(base + off);
+    off = align_up(off + 24 * (nscenes > 0 ? nscenes : 1), 256);
+    w.bytes = off;
+    return w;
+}
+
+static mesh_batch_layout batch_layout(int64_t maxB, int64_t maxV, int64_t maxF) {
+    mesh_batch_layout L{};
+    int64_t b = maxB > 0 ? maxB : 1, v = maxV > 0 ? maxV : 1, f = maxF > 0 ? maxF : 1;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
+    L.max_scenes = maxB;
+    L.max_verts = maxV;
+    L.max_faces = maxF;
+    L.off_scene = take(32 * b);
+    L.off_status = take(sizeof(BatchStatus));
+    L.off_vert_off = take(4 * (b + 1));
+    L.off_face_off = take(4 * (b + 1));
+    L.off_verts = take(16 * v);
+    L.off_faces = take(16 * f);
+    L.off_keys = take(4 * f);
+    L.off_perm = take(4 * f);
+    L.off_nodes = take(64 * f);
+    L.off_parent_int = take(4 * f);
+    L.off_parent_leaf = take(4 * f);
+    L.off_tris = take(48 * f);
+    L.off_flags = take(4 * f);
+    L.storage_bytes = off;
+    return L;
 }
 
 static mesh_bvh_layout storage_layout(int64_t maxV, int64_t maxF) {
@@ -644,6 +858,130 @@ mesh_status mesh_morton_order(const float *d_P, int64_t n, int32_t *d_order, voi
     count_launch(3);
     radix_sort_pairs(w, m, w.keysA, d_order, s);
     return check_launch();
+}
+
+size_t mesh_batch_storage_bytes(int64_t max_scenes, int64_t max_verts, int64_t max_faces) {
+    if (max_scenes < 1 || max_scenes > 65536 || max_verts < 0 || max_faces < 0 ||
+        max_faces > kMaxFaces || max_verts > kMaxFaces)
+        return 0;
+    return batch_layout(max_scenes, max_verts, max_faces).storage_bytes;
+}
+
+size_t mesh_batch_workspace_bytes(int64_t max_scenes, int64_t max_faces) {
+    if (max_scenes < 1 || max_scenes > 65536 || max_faces < 0 || max_faces > kMaxFaces) return 0;
+    return batch_ws_layout(nullptr, max_scenes, max_faces).bytes;
+}
+
+mesh_status mesh_batch_create(void *d_storage, size_t storage_bytes, int64_t max_scenes,
+                              int64_t max_verts, int64_t max_faces, mesh_batch **out) {
+    if (!out || !d_storage || ((uintptr_t)d_storage & 255u)) return MESH_ERR_INVALID_ARG;
+    size_t need = mesh_batch_storage_bytes(max_scenes, max_verts, max_faces);
+    if (need == 0) return MESH_ERR_INVALID_ARG;
+    if (storage_bytes < need) return MESH_ERR_WORKSPACE;
+    mesh_batch *h = (mesh_batch *)std::calloc(1, sizeof(mesh_batch));
+    if (!h) return MESH_ERR_INVALID_ARG;
+    h->base = (char *)d_storage;
+    h->L = batch_layout(max_scenes, max_verts, max_faces);
+    *out = h;
+    return MESH_OK;
+}
+
+void mesh_batch_destroy(mesh_batch *batch) { std::free(batch); }
+
+mesh_status mesh_batch_get_layout(const mesh_batch *batch, mesh_batch_layout *out) {
+    if (!batch || !out) return MESH_ERR_INVALID_ARG;
+    *out = batch->L;
+    return MESH_OK;
+}
+
+mesh_status mesh_batch_build(mesh_batch *batch, int64_t n_scenes, const float *d_V,
+                             const int32_t *d_vert_off, int64_t nV, const int32_t *d_F,
+                             const int32_t *d_face_off, int64_t nF, void *d_ws, size_t ws_bytes,
+                             void *stream) {
+    if (!batch || n_scenes < 1 || n_scenes > batch->L.max_scenes || nV < 0 || nF < 0 ||
+        nV > batch->L.max_verts || nF > batch->L.max_faces || !d_vert_off || !d_face_off)
+        return MESH_ERR_INVALID_ARG;
+    if ((nV > 0 && !d_V) || (nF > 0 && (!d_F || nV == 0))) return MESH_ERR_INVALID_ARG;
+    BatchWs w = batch_ws_layout((char *)d_ws, n_scenes, nF);
+    if (nF > 0 && (!d_ws || ws_bytes < w.bytes || ((uintptr_t)d_ws & 255u))) return MESH_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    batch->L.n_scenes = n_scenes;
+    batch->L.n_verts = nV;
+    batch->L.n_faces = nF;
+    int B = (int)n_scenes, n = (int)nF;
+    cudaMemsetAsync(batch->st(), 0, sizeof(BatchStatus), s);
+    cudaMemsetAsync(batch->scene_box(), 0, 32 * (size_t)B, s);
+    cudaMemcpyAsync(batch->vert_off(), d_vert_off, 4 * (size_t)(B + 1), cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(batch->face_off(), d_face_off, 4 * (size_t)(B + 1), cudaMemcpyDeviceToDevice, s);
+    if (nV > 0) {
+        k_copy_verts<<<grid_for(nV, kBlock), kBlock, 0, s>>>(d_V, (int)nV, batch->verts(), nullptr);
+        count_launch();
+    }
+    if (n == 0) return check_launch();
+    unsigned int *status = &batch->st()->status;
+    k_batch_init<<<grid_for(6 * B, kBlock), kBlock, 0, s>>>(w.cbox, B);
+    k_batch_faces<<<grid_for(n, kBlock), kBlock, 0, s>>>(d_F, n, batch->vert_off(), batch->face_off(),
+                                                         B, batch->verts(), batch->faces(), w.sort.cent,
+                                                         w.cbox, status);
+    k_batch_morton<<<grid_for(n, kBlock), kBlock, 0, s>>>(w.sort.cent, n, batch->faces(), w.cbox,
+                                                          w.key_of_face, w.sort.keysA, w.sort.valsA);
+    count_launch(3);
+    // Morton order over all faces, then a stable pass (two past 256 scenes) on
+    // the scene id: faces end up grouped by scene in the order a per-scene
+    // build would give them.
+    radix_sort_pairs(w.sort, n, w.sort.keysA, w.sort.valsA, s);
+    k_batch_scene_keys<<<grid_for(n, kBlock), kBlock, 0, s>>>(w.sort.valsA, n, batch->faces(),
+                                                              w.sort.keysA);
+    count_launch();
+    if (B <= 256) {
+        radix_pass(w.sort, n, 0, w.sort.keysA, w.sort.valsA, w.sort.keysB, batch->perm(), s);
+    } else {
+        radix_pass(w.sort, n, 0, w.sort.keysA, w.sort.valsA, w.sort.keysB, w.sort.valsB, s);
+        radix_pass(w.sort, n, 8, w.sort.keysB, w.sort.valsB, w.sort.keysA, batch->perm(), s);
+    }
+    k_batch_gather_keys<<<grid_for(n, kBlock), kBlock, 0, s>>>(batch->perm(), n, w.key_of_face,
+                                                               batch->keys());
+    k_batch_karras<<<grid_for(n, kBlock), kBlock, 0, s>>>(batch->keys(), n, batch->face_off(), B,
+                                                          batch->nodes(), batch->parent_int(),
+                                                          batch->parent_leaf());
+    count_launch(2);
+    cudaMemsetAsync(batch->flags(), 0, sizeof(unsigned int) * (size_t)n, s);
+    k_batch_leaves_up<<<grid_for(n, kBlock), kBlock, 0, s>>>(
+        n, batch->face_off(), B, batch->perm(), batch->faces(), batch->verts(), batch->tris(),
+        batch->nodes(), batch->parent_int(), batch->parent_leaf(), batch->flags(), batch->scene_box());
+    count_launch();
+    return check_launch();
+}
+
+mesh_status mesh_batch_refit(mesh_batch *batch, const float *d_V, int64_t nV, void *stream) {
+    if (!batch || (d_V && nV != batch->L.n_verts)) return MESH_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (d_V && nV > 0) {
+        k_copy_verts<<<grid_for(nV, kBlock), kBlock, 0, s>>>(d_V, (int)nV, batch->verts(), nullptr);
+        count_launch();
+    }
+    int n = (int)batch->L.n_faces;
+    if (n == 0) return check_launch();
+    k_batch_leaves_up<<<grid_for(n, kBlock), kBlock, 0, s>>>(
+        n, batch->face_off(), (int)batch->L.n_scenes, batch->perm(), batch->faces(), batch->verts(),
+        batch->tris(), batch->nodes(), batch->parent_int(), batch->parent_leaf(), batch->flags(),
+        batch->scene_box());
+    count_launch();
+    return check_launch();
+}
+
+mesh_status mesh_batch_status(mesh_batch *batch, uint32_t *bits, uint32_t *n_degenerate,
+                              void *stream) {
+    if (!batch) return MESH_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned int h[2] = {0u, 0u};
+    if (cudaMemcpyAsync(h, batch->st(), sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return MESH_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return MESH_ERR_CUDA;
+    if (cudaMemsetAsync(batch->st(), 0, sizeof(h), s) != cudaSuccess) return MESH_ERR_CUDA;
+    if (bits) *bits = h[0];
+    if (n_degenerate) *n_degenerate = h[1];
+    return (h[0] & ~(unsigned)MESH_DEV_DEGENERATE) ? MESH_ERR_DEVICE : MESH_OK;
 }
 
 uint64_t mesh_launch_count(void) { return (uint64_t)g_launches.load(); }

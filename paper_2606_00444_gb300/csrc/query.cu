@@ -29,6 +29,20 @@ __device__ __forceinline__ float box_d2(float3 q, float4 lo, float4 hi) {
     return dx * dx + dy * dy + dz * dz;
 }
 
+// MinMaxDist of Roussopoulos, Kelley & Vincent (1995) for a tight AABB: every
+// face of the box touches the geometry inside it, so some primitive in the box
+// lies within this distance of q.  It bounds the nearest distance from above
+// before any triangle is tested and orders children whose boxes both contain q.
+__device__ __forceinline__ float box_minmax_d2(float3 q, float4 lo, float4 hi) {
+    float mx = 0.5f * (lo.x + hi.x), my = 0.5f * (lo.y + hi.y), mz = 0.5f * (lo.z + hi.z);
+    float nx = q.x - (q.x <= mx ? lo.x : hi.x), fx = q.x - (q.x >= mx ? lo.x : hi.x);
+    float ny = q.y - (q.y <= my ? lo.y : hi.y), fy = q.y - (q.y >= my ? lo.y : hi.y);
+    float nz = q.z - (q.z <= mz ? lo.z : hi.z), fz = q.z - (q.z >= mz ? lo.z : hi.z);
+    float f2x = fx * fx, f2y = fy * fy, f2z = fz * fz;
+    float S = f2x + f2y + f2z;
+    return fminf(fminf(S - f2x + nx * nx, S - f2y + ny * ny), S - f2z + nz * nz);
+}
+
 __device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
 __device__ __forceinline__ float3 sub3(float3 a, float3 b) {
     return make_float3(a.x - b.x, a.y - b.y, a.z - b.z);
@@ -181,11 +195,19 @@ __device__ __forceinline__ float tie_window2(float d2, float tau) {
     return r * r;
 }
 
+// Pruning threshold implied by an upper bound u2 on the nearest squared
+// distance: the tie window of u2, widened by 2e-5 relative to cover float32
+// rounding of the bound itself.
+__device__ __forceinline__ float bound_window2(float u2, float tau) {
+    return tie_window2(u2 * 1.00004f, tau);
+}
+
 struct Traversal {
     const float4 *__restrict__ nodes;
     const float4 *__restrict__ tris;
     int n;
     float tau;
+    bool mmd;      // use MinMaxDist bounds (unbounded queries; a cutoff is tighter)
 };
 
 // Candidate bookkeeping of the tie rule: dmin is the nearest squared distance
@@ -198,18 +220,18 @@ struct Best {
 __device__ __forceinline__ void consider(Best &B, int leaf, int face, float d2, float maxd2,
                                          float tau) {
     if (B.leaf < 0) {
-        if (d2 <= maxd2 && d2 <= B.thr) {
+        if (d2 <= maxd2) {
             B.leaf = leaf; B.face = face; B.d2 = d2;
             B.dmin = fminf(B.dmin, d2);
-            B.thr = tie_window2(B.dmin, tau);
+            B.thr = fminf(B.thr, tie_window2(B.dmin, tau));
         }
         return;
     }
     float nmin = fminf(B.dmin, d2);
-    float w2 = nmin < B.dmin ? tie_window2(nmin, tau) : B.thr;
+    float w2 = tie_window2(nmin, tau);
     if (d2 <= w2 && (face < B.face || B.d2 > w2)) { B.leaf = leaf; B.face = face; B.d2 = d2; }
     B.dmin = nmin;
-    B.thr = w2;
+    B.thr = fminf(B.thr, w2);
 }
 
 __device__ __forceinline__ void test_leaf(const Traversal &T, Best &B, int leaf, float3 q,
@@ -236,13 +258,19 @@ __device__ __forceinline__ Hit nearest(const Traversal &T, float3 q, float maxd2
             const float4 *r = T.nodes + 4 * (size_t)node;
             float4 l0 = ldg4(r), l1 = ldg4(r + 1), r0 = ldg4(r + 2), r1 = ldg4(r + 3);
             float dl = box_d2(q, l0, l1), dr = box_d2(q, r0, r1);
+            float ml = 0.0f, mr = 0.0f;
+            if (T.mmd) {
+                ml = box_minmax_d2(q, l0, l1);
+                mr = box_minmax_d2(q, r0, r1);
+                B.thr = fminf(B.thr, bound_window2(fminf(ml, mr), T.tau));
+            }
             int cl = __float_as_int(l0.w), cr = __float_as_int(r0.w);
             if (cl < 0 && dl <= B.thr) test_leaf(T, B, -cl - 1, q, maxd2);
             if (cr < 0 && dr <= B.thr) test_leaf(T, B, -cr - 1, q, maxd2);
             bool gl = cl >= 0 && dl <= B.thr;
             bool gr = cr >= 0 && dr <= B.thr;
             if (gl && gr) {
-                bool lfirst = dl <= dr;
+                bool lfirst = dl < dr || (dl == dr && ml <= mr);
                 int2 e = make_int2(lfirst ? cr : cl, __float_as_int(lfirst ? dr : dl));
                 if (sp < kStackShared) stk[sp][tid] = e;
                 else if (sp < kStackTotal) spill[sp - kStackShared] = e;
@@ -293,12 +321,18 @@ __device__ __forceinline__ Hit nearest_ww(const Traversal &T, float3 q, float ma
             const float4 *r = T.nodes + 4 * (size_t)node;
             float4 l0 = ldg4(r), l1 = ldg4(r + 1), r0 = ldg4(r + 2), r1 = ldg4(r + 3);
             float dl = box_d2(q, l0, l1), dr = box_d2(q, r0, r1);
+            float ml = 0.0f, mr = 0.0f;
+            if (T.mmd) {
+                ml = box_minmax_d2(q, l0, l1);
+                mr = box_minmax_d2(q, r0, r1);
+                B.thr = fminf(B.thr, bound_window2(fminf(ml, mr), T.tau));
+            }
             int cl = __float_as_int(l0.w), cr = __float_as_int(r0.w);
             if (cl < 0 && dl <= B.thr) lq[nq++] = -cl - 1;
             if (cr < 0 && dr <= B.thr) lq[nq++] = -cr - 1;
             bool gol = cl >= 0 && dl <= B.thr, gor = cr >= 0 && dr <= B.thr;
             if (gol && gor) {
-                bool lfirst = dl <= dr;
+                bool lfirst = dl < dr || (dl == dr && ml <= mr);
                 int2 e = make_int2(lfirst ? cr : cl, __float_as_int(lfirst ? dr : dl));
                 if (sp < kStackShared) stk[sp][tid] = e;
                 else if (sp < kStackTotal) spill[sp - kStackShared] = e;
@@ -335,12 +369,18 @@ __device__ __noinline__ void dfs_private(const Traversal &T, Best &B, int start,
         const float4 *r = T.nodes + 4 * (size_t)node;
         float4 l0 = ldg4(r), l1 = ldg4(r + 1), r0 = ldg4(r + 2), r1 = ldg4(r + 3);
         float dl = box_d2(q, l0, l1), dr = box_d2(q, r0, r1);
+        float ml = 0.0f, mr = 0.0f;
+        if (T.mmd) {
+            ml = box_minmax_d2(q, l0, l1);
+            mr = box_minmax_d2(q, r0, r1);
+            B.thr = fminf(B.thr, bound_window2(fminf(ml, mr), T.tau));
+        }
         int cl = __float_as_int(l0.w), cr = __float_as_int(r0.w);
         if (cl < 0 && dl <= B.thr) test_leaf(T, B, -cl - 1, q, maxd2);
         if (cr < 0 && dr <= B.thr) test_leaf(T, B, -cr - 1, q, maxd2);
         bool gl = cl >= 0 && dl <= B.thr, gr = cr >= 0 && dr <= B.thr;
         if (gl && gr) {
-            bool lfirst = dl <= dr;
+            bool lfirst = dl < dr || (dl == dr && ml <= mr);
             if (sp < kStackTotal) stk[sp++] = make_int2(lfirst ? cr : cl, __float_as_int(lfirst ? dr : dl));
             else atomicOr(status, (unsigned)MESH_DEV_STACK_OVERFLOW);
             node = lfirst ? cl : cr;
@@ -371,7 +411,7 @@ __device__ __noinline__ void dfs_private(const Traversal &T, Best &B, int start,
 // ---------------------------------------------------------------------------
 // shared-memory stack entries per group: room for one full step (2G pushes)
 // above the near-full mark, plus a working depth
-template <int G> constexpr int group_cap() { return 4 * G + 64; }
+template <int G> __host__ __device__ constexpr int group_cap() { return 4 * G + 64; }
 
 template <int G> __device__ __forceinline__ float grp_min(float x) {
 #pragma unroll
@@ -419,7 +459,10 @@ __device__ Hit nearest_group(const Traversal &T, float3 q, float maxd2, bool val
             const float4 *r = T.nodes + 4 * (size_t)node;
             float4 l0 = ldg4(r), l1 = ldg4(r + 1), r0 = ldg4(r + 2), r1 = ldg4(r + 3);
             float dl = box_d2(q, l0, l1), dr = box_d2(q, r0, r1);
-            int c = dl <= dr ? __float_as_int(l0.w) : __float_as_int(r0.w);
+            float ml = 0.0f, mr = 0.0f;
+            if (T.mmd) { ml = box_minmax_d2(q, l0, l1); mr = box_minmax_d2(q, r0, r1); }
+            bool lfirst = dl < dr || (dl == dr && ml <= mr);
+            int c = lfirst ? __float_as_int(l0.w) : __float_as_int(r0.w);
             if (c >= 0) { node = c; continue; }
             Best B{-1, 0x7fffffff, INFINITY, INFINITY, maxd2};
             test_leaf(T, B, -c - 1, q, maxd2);
@@ -442,11 +485,18 @@ __device__ Hit nearest_group(const Traversal &T, float3 q, float maxd2, bool val
         float c0 = INFINITY, c1 = INFINITY;
         int f0 = 0x7fffffff, f1 = 0x7fffffff, lf0 = -1, lf1 = -1;
         int npush = 0;
+        float lane_ub = INFINITY;
         int2 p_far = make_int2(0, 0), p_near = make_int2(0, 0);
         if (act && !near_full) {
             const float4 *r = T.nodes + 4 * (size_t)e.x;
             float4 l0 = ldg4(r), l1 = ldg4(r + 1), r0 = ldg4(r + 2), r1 = ldg4(r + 3);
             float dl = box_d2(q, l0, l1), dr = box_d2(q, r0, r1);
+            float ml = 0.0f, mr = 0.0f;
+            if (T.mmd) {
+                ml = box_minmax_d2(q, l0, l1);
+                mr = box_minmax_d2(q, r0, r1);
+                lane_ub = fminf(ml, mr);
+            }
             int cl = __float_as_int(l0.w), cr = __float_as_int(r0.w);
             float u, v, w;
             if (cl < 0 && dl <= thr) {
@@ -465,7 +515,7 @@ __device__ Hit nearest_group(const Traversal &T, float3 q, float maxd2, bool val
             }
             bool gol = cl >= 0 && dl <= thr, gor = cr >= 0 && dr <= thr;
             if (gol && gor) {
-                bool lfirst = dl <= dr;
+                bool lfirst = dl < dr || (dl == dr && ml <= mr);
                 p_near = make_int2(lfirst ? cl : cr, __float_as_int(lfirst ? dl : dr));
                 p_far = make_int2(lfirst ? cr : cl, __float_as_int(lfirst ? dr : dl));
                 npush = 2;
@@ -487,8 +537,9 @@ __device__ Hit nearest_group(const Traversal &T, float3 q, float maxd2, bool val
             if (c1 > maxd2) c1 = INFINITY;
         }
         float m = grp_min<G>(fminf(c0, c1));
+        float ub = grp_min<G>(lane_ub);
         float nmin = fminf(dmin, m);
-        float w2 = nmin < dmin ? tie_window2(nmin, T.tau) : thr;
+        float w2 = nmin < INFINITY ? tie_window2(nmin, T.tau) : INFINITY;
         int fc = min(c0 <= w2 ? f0 : 0x7fffffff, c1 <= w2 ? f1 : 0x7fffffff);
         int fmin = grp_min<G>(fc);
         bool mine = fmin != 0x7fffffff && fc == fmin;
@@ -502,8 +553,9 @@ __device__ Hit nearest_group(const Traversal &T, float3 q, float maxd2, bool val
             bool keep = bleaf >= 0 && bd2 <= w2 && bface < fmin;
             if (!keep && fmin != 0x7fffffff) { bface = fmin; bd2 = sd2; bleaf = slf; }
             dmin = nmin;
-            thr = w2;
+            thr = fminf(thr, w2);
         }
+        thr = fminf(thr, bound_window2(ub, T.tau));
         // push surviving children: lane G-1's lowest, lane 0's on top
         int total = grp_sum<G>(npush);
         int above = total - grp_incl_scan<G>(npush, gl);
@@ -576,6 +628,40 @@ k_closest_point_group(Traversal T, const Header *__restrict__ hdr, unsigned int 
     float3 q = valid ? make_float3(Q[3 * i], Q[3 * i + 1], Q[3 * i + 2]) : make_float3(0.f, 0.f, 0.f);
     Hit h = nearest_group<G>(T, q, maxd2, valid, gstk[threadIdx.x / G], status);
     if (valid && (threadIdx.x & (G - 1)) == 0) write_hit(T, h, q, i, face, bary, point, dist2);
+}
+
+// Batched NearestSurface: one persistent launch for the queries of every
+// scene.  Each warp takes the next 32 queries from a counter, each thread
+// finds its query's scene (binary search of the offsets) and traverses that
+// scene's tree; face ids are returned scene-local.
+__global__ void __launch_bounds__(kQueryBlock, kQueryMinBlocks)
+k_batch_closest_point(const float4 *__restrict__ nodes, const float4 *__restrict__ tris,
+                      const float4 *__restrict__ scene_box, const int *__restrict__ face_off,
+                      const int *__restrict__ query_off, int nscenes, const float *__restrict__ Q,
+                      int64_t nQ, float maxd2, bool mmd, int *face, float *bary, float *point,
+                      float *dist2, unsigned int *status, unsigned int *work) {
+    __shared__ int2 stk[kStackShared][kQueryBlock];
+    const int lane = threadIdx.x & 31;
+    while (true) {
+        unsigned int base = 0;
+        if (lane == 0) base = atomicAdd(work, 32u);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if ((int64_t)base >= nQ) break;
+        int64_t i = (int64_t)base + lane;
+        if (i < nQ) {
+            int sc = segment_of(query_off, nscenes, i);
+            int fb = __ldg(face_off + sc), ns = __ldg(face_off + sc + 1) - fb;
+            float4 lo = scene_box[2 * sc], hi = scene_box[2 * sc + 1];
+            float dx = hi.x - lo.x, dy = hi.y - lo.y, dz = hi.z - lo.z;
+            Traversal T{nodes + 4 * (size_t)fb, tris + 3 * (size_t)fb, ns,
+                        kTieAbs * sqrtf(dx * dx + dy * dy + dz * dz), mmd};
+            float3 q = make_float3(Q[3 * i], Q[3 * i + 1], Q[3 * i + 2]);
+            Hit h = nearest<kQueryBlock>(T, q, maxd2, stk, status);
+            if (h.leaf >= 0) h.face -= fb;
+            write_hit(T, h, q, i, face, bary, point, dist2);
+        }
+        __syncwarp();
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -680,8 +766,8 @@ __global__ void k_interpolate(const int4 *__restrict__ faces, const float4 *__re
     out[3 * i + 2] = u * a.z + v * b.z + w * c.z;
 }
 
-static Traversal traversal_of(const mesh_bvh *b) {
-    return Traversal{b->nodes(), b->tris(), (int)b->L.n_faces, 0.0f};
+static Traversal traversal_of(const mesh_bvh *b, bool mmd = true) {
+    return Traversal{b->nodes(), b->tris(), (int)b->L.n_faces, 0.0f, mmd};
 }
 
 static size_t chamfer_blocks(int64_t n, int G = 1) {
@@ -724,7 +810,7 @@ mesh_status mesh_closest_point(const mesh_bvh *bvh, const float *d_Q, int64_t nQ
     float maxd2 = isinf(max_dist) ? INFINITY : max_dist * max_dist;
     cudaStream_t s = (cudaStream_t)stream;
     int G = pick_group(nQ);
-    Traversal T = traversal_of(bvh);
+    Traversal T = traversal_of(bvh, isinf(max_dist));
     Header *h = bvh->hdr();
     unsigned int grid = grid_for(nQ * G, kQueryBlock);
     switch (G) {
@@ -779,6 +865,35 @@ mesh_status mesh_chamfer(const mesh_bvh *A, const float *d_SA, int64_t nSA, cons
         case 16: k_chamfer<16><<<grid, kQueryBlock, 0, s>>>(a2b, b2a, (unsigned)nbA, st, partial, ticket, d_out); break;
         default: k_chamfer<32><<<grid, kQueryBlock, 0, s>>>(a2b, b2a, (unsigned)nbA, st, partial, ticket, d_out); break;
     }
+    count_launch();
+    return check_launch();
+}
+
+mesh_status mesh_batch_closest_point(mesh_batch *batch, const float *d_Q,
+                                     const int32_t *d_query_off, int64_t nQ, float max_dist,
+                                     int32_t *d_face, float *d_bary, float *d_point,
+                                     float *d_dist2, void *stream) {
+    if (!batch || nQ < 0 || nQ > 0xffff0000LL || (nQ > 0 && (!d_Q || !d_query_off)) ||
+        !(max_dist >= 0.0f))
+        return MESH_ERR_INVALID_ARG;
+    if (nQ == 0) return MESH_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+            sms = 152;
+    }
+    float maxd2 = isinf(max_dist) ? INFINITY : max_dist * max_dist;
+    unsigned int *work = &batch->st()->work;
+    cudaMemsetAsync(work, 0, sizeof(unsigned int), s);
+    int64_t want = (nQ + kQueryBlock - 1) / kQueryBlock;
+    unsigned int grid = (unsigned int)(want < (int64_t)sms * kQueryMinBlocks ? want : (int64_t)sms * kQueryMinBlocks);
+    k_batch_closest_point<<<grid, kQueryBlock, 0, s>>>(
+        batch->nodes(), batch->tris(), batch->scene_box(), batch->face_off(), d_query_off,
+        (int)batch->L.n_scenes, d_Q, nQ, maxd2, isinf(max_dist), d_face, d_bary, d_point, d_dist2,
+        &batch->st()->status, work);
     count_launch();
     return check_launch();
 }

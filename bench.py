@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="meshgs", choices=["meshgs", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="physics", choices=["physics", "batch", "sequence", "fit"],
+                    help="physics: the default frame; batch: 64 scenes batched vs per scene; "
+                         "sequence: varying-topology conversion; fit: differentiable template fit")
     return ap.parse_args()
 
 
@@ -373,6 +376,254 @@ def reference_arm(args, rank, world):
     print(json.dumps(line))
 
 
+# ---------------------------------------------------------------------------
+# Other workloads (measurements for the design notes; one JSON line each)
+# ---------------------------------------------------------------------------
+def _events(n):
+    import torch
+    return [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+
+
+def _time_graph(g, steps, warm, flush, pre=None):
+    import torch
+    for k in range(warm):
+        if pre:
+            pre(k)
+        g.replay()
+    st, en = _events(steps), _events(steps)
+    for k in range(steps):
+        flush.fill_(float(k))
+        st[k].record()
+        if pre:
+            pre(warm + k)
+        g.replay()
+        en[k].record()
+    torch.cuda.synchronize()
+    return float(np.mean([a.elapsed_time(b) for a, b in zip(st, en)]))
+
+
+def _capture(fn):
+    import torch
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        fn()
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        fn()
+    torch.cuda.synchronize()
+    return g
+
+
+def bench_batch(args):
+    """64 scenes (log-uniform 1k-200k faces): per frame every scene is rebuilt, queried
+    (4 x its vertex count, uniform in its box grown by 10%) and its Gaussians (one per
+    face at the centroid) updated.  Batched: one launch per phase for all scenes.
+    Plain: the same calls per scene, 64 times.  Both captured as one CUDA graph."""
+    import torch
+    from paper_2606_00444_gb300 import MeshBatch, MeshBVH, launch_count, set_query_group
+    from workloads.meshes import batch_scenes
+    dev = torch.device("cuda")
+    S = batch_scenes(64, seed=4000)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    V, vo, F, fo = MeshBatch.concat(S, dev)
+    Qs, qn = [], []
+    for i, (v, f) in enumerate(S):
+        lo, hi = v.min(0), v.max(0)
+        pad = 0.1 * (hi - lo)
+        Qs.append(uniform_box(4 * len(v), lo - pad, hi + pad, seed=4100 + i))
+        qn.append(4 * len(v))
+    Q = t(np.concatenate(Qs))
+    qoff = t(np.concatenate([[0], np.cumsum(qn)]).astype(np.int32))
+    gface = torch.cat([torch.arange(len(f), dtype=torch.int32) for _, f in S]).to(dev)
+    goff = fo
+    gbary = torch.full((gface.shape[0], 3), 1.0 / 3.0, device=dev)
+    nQ = Q.shape[0]
+    batch = MeshBatch(64, V.shape[0], F.shape[0], dev)
+    out = dict(face=torch.empty(nQ, dtype=torch.int32, device=dev), bary=torch.empty(nQ, 3, device=dev),
+               point=torch.empty(nQ, 3, device=dev), dist2=torch.empty(nQ, device=dev))
+    gout = (torch.empty(gface.shape[0], 3, device=dev), torch.empty(gface.shape[0], 4, device=dev),
+            torch.empty(gface.shape[0], 3, device=dev))
+
+    def batched():
+        batch.build(V, vo, F, fo)
+        batch.closest_point(Q, qoff, out=out)
+        batch.bind_gaussians(gface, goff, gbary, out=gout)
+
+    singles = [MeshBVH(len(v), len(f), dev) for v, f in S]
+    Vs = [t(v) for v, _ in S]
+    Fs = [t(f) for _, f in S]
+    Qd = [t(q) for q in Qs]
+    outs = [dict(face=torch.empty(len(q), dtype=torch.int32, device=dev),
+                 bary=torch.empty(len(q), 3, device=dev), point=torch.empty(len(q), 3, device=dev),
+                 dist2=torch.empty(len(q), device=dev)) for q in Qs]
+    gfs = [torch.arange(len(f), dtype=torch.int32, device=dev) for _, f in S]
+    gbs = [torch.full((len(f), 3), 1.0 / 3.0, device=dev) for _, f in S]
+    gos = [(torch.empty(len(f), 3, device=dev), torch.empty(len(f), 4, device=dev),
+            torch.empty(len(f), 3, device=dev)) for _, f in S]
+
+    def plain():
+        for i in range(64):
+            singles[i].build(Vs[i], Fs[i])
+            singles[i].closest_point(Qd[i], out=outs[i])
+            singles[i].bind_gaussians(gfs[i], gbs[i], out=gos[i])
+
+    flush = torch.empty(128 << 20, dtype=torch.float32, device=dev)
+    set_query_group(1)
+    try:
+        n0 = launch_count(); batched(); torch.cuda.synchronize(); lb = launch_count() - n0
+        n0 = launch_count(); plain(); torch.cuda.synchronize(); lp = launch_count() - n0
+        gb, gp = _capture(batched), _capture(plain)
+        ms_b = _time_graph(gb, args.steps, args.warmup, flush)
+        ms_p = _time_graph(gp, args.steps, args.warmup, flush)
+        st, en = _events(5), _events(5)
+        for k in range(5):
+            flush.fill_(1.0); st[k].record(); plain(); en[k].record()
+        torch.cuda.synchronize()
+        ms_e = float(np.mean([a.elapsed_time(b) for a, b in zip(st, en)]))
+    finally:
+        set_query_group(0)
+    line = {"metric": METRIC, "value": nQ / (ms_b * 1e-3), "unit": "queries/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_b,
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "64 scenes, faces log-uniform 1k-200k (tori / icospheres, "
+                                   "sinusoidal displacement), queries 4 x vertices per scene; per "
+                                   "frame: LBVH build + closest point + one Gaussian per face",
+                       "faces": int(F.shape[0]), "queries": int(nQ)},
+            "ms_per_frame": {"batched_graph": ms_b, "per_scene_graph": ms_p,
+                             "per_scene_eager": ms_e},
+            "launches_per_frame": {"batched": lb, "per_scene": lp}}
+    print(json.dumps(line))
+
+
+def bench_sequence(args):
+    """Varying-topology conversion (template projection, Eq. 2): per frame the extracted
+    target is rebuilt, the 10242 template vertices projected onto it, the template refit
+    and its 20480 Gaussians updated, and the Chamfer distance (10k + 10k samples) taken."""
+    import torch
+    from paper_2606_00444_gb300 import MeshBVH, Workspace, chamfer
+    from workloads.isosurface import BlobSequence
+    from workloads.meshes import icosphere
+    dev = torch.device("cuda")
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    nfr = min(120, max(args.steps + args.warmup, 8))
+    seq = BlobSequence(2000)
+    frames = [seq.mesh(k) for k in range(nfr)]
+    tg = [(t(v), t(f), t(points_from(v, f, *sample_surface(v, f, N_CD, seed=2100 + k))))
+          for k, (v, f) in enumerate(frames)]
+    VT, FT = icosphere(5)
+    VTd, FTd = t(VT), t(FT)
+    maxF = max(len(f) for _, f in frames)
+    maxV = max(len(v) for v, _ in frames)
+    target = MeshBVH(maxV, maxF, dev)
+    tmpl = MeshBVH.from_mesh(VTd, FTd)
+    gface = torch.arange(len(FT), dtype=torch.int32, device=dev)
+    gbary = torch.full((len(FT), 3), 1.0 / 3.0, device=dev)
+    sf, sb = sample_surface(VT, FT, N_CD, seed=2200)
+    sf, sb = t(sf), t(sb)
+    ws = Workspace(dev)
+    cd_out = torch.empty(2, dtype=torch.float64, device=dev)
+    flush = torch.empty(128 << 20, dtype=torch.float32, device=dev)
+    proj = dict(point=torch.empty(len(VT), 3, device=dev), dist2=torch.empty(len(VT), device=dev))
+    ev = []
+
+    def frame(k):
+        V, F, SB = tg[k % nfr]
+        e = _events(6)
+        e[0].record()
+        target.build(V, F)                                     # rebuild (varying topology)
+        e[1].record()
+        target.closest_point(VTd, want=("point", "dist2"), out=proj)   # Eq. 2 projection
+        e[2].record()
+        tmpl.refit(proj["point"])                              # fixed-topology vertex update
+        e[3].record()
+        tmpl.bind_gaussians(gface, gbary)
+        e[4].record()
+        SA = tmpl.interpolate(sf, sb)
+        chamfer(tmpl, SA, target, SB, ws=ws, out=cd_out)
+        e[5].record()
+        return e
+
+    for k in range(args.warmup):
+        frame(k)
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev.append(frame(args.warmup + k))
+    torch.cuda.synchronize()
+    names = ["rebuild", "project", "refit", "rebind", "chamfer"]
+    st = {n: float(np.mean([e[i].elapsed_time(e[i + 1]) for e in ev])) for i, n in enumerate(names)}
+    ms = float(np.mean([e[0].elapsed_time(e[5]) for e in ev]))
+    q = len(VT) + 2 * N_CD
+    line = {"metric": METRIC, "value": q / (ms * 1e-3), "unit": "queries/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "varying-topology sequence: marching cubes 128^3 of a 4-sphere "
+                                   "smooth union, template icosphere 10242 V / 20480 F projected per "
+                                   "frame", "frames": nfr,
+                       "target_faces": [int(min(len(f) for _, f in frames)), int(maxF)]},
+            "stages_ms": st, "chamfer_last": [float(x) for x in cd_out.cpu()]}
+    print(json.dumps(line))
+
+
+def bench_fit(args):
+    """Differentiable template fit: icosphere 40962 V / 81920 F fitted to the extracted
+    target at tau = pi (frame 60) by Adam (lr 1e-3) on symmetric Chamfer over 1M samples
+    per side plus the mean squared point-to-mesh distance of the template vertices;
+    every forward and backward step runs in the library's kernels."""
+    import torch
+    from paper_2606_00444_gb300 import MeshBVH
+    from paper_2606_00444_gb300.autograd import Chamfer, Interpolate, PointMeshDistance
+    from workloads.isosurface import BlobSequence
+    from workloads.meshes import icosphere
+    dev = torch.device("cuda")
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    VG, FG = BlobSequence(2000).mesh(60)
+    VT, FT = icosphere(6, radius=0.9)
+    ns = 1 << 20
+    ft, bt = sample_surface(VT, FT, ns, seed=5001)
+    SG = t(points_from(VG, FG, *sample_surface(VG, FG, ns, seed=5002)))
+    tmpl = MeshBVH.from_mesh(t(VT), t(FT))
+    targ = MeshBVH.from_mesh(t(VG), t(FG))
+    VGd = t(VG)
+    ft, bt = t(ft), t(bt)
+    V = t(VT).requires_grad_(True)
+    opt = torch.optim.Adam([V], lr=1e-3)
+    n_steps = 300 if args.steps >= 100 else args.steps
+
+    def step():
+        opt.zero_grad(set_to_none=True)
+        ST = Interpolate.apply(V, tmpl, ft, bt)
+        cd = Chamfer.apply(ST, V, tmpl, SG, VGd, targ)
+        d2v, _ = PointMeshDistance.apply(V, VGd, targ)
+        loss = cd[0] + cd[1] + d2v.mean()
+        loss.backward()
+        opt.step()
+        return loss
+
+    l0 = float(step().item())
+    torch.cuda.synchronize()
+    st, en = _events(n_steps), _events(n_steps)
+    losses = []
+    for k in range(n_steps):
+        st[k].record()
+        loss = step()
+        en[k].record()
+        losses.append(loss)
+    torch.cuda.synchronize()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in zip(st, en)]))
+    line = {"metric": METRIC, "value": (2 * ns + len(VT)) / (ms * 1e-3), "unit": "queries/s",
+            "n_gpus": 1, "steps": n_steps, "warmup": 1, "ms_per_step": ms,
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "template fit: icosphere 40962 V to the extracted target at "
+                                   "tau = pi, Chamfer 1M + 1M samples + vertex point-to-mesh, Adam "
+                                   "lr 1e-3", "target_faces": int(len(FG))},
+            "loss_first": l0, "loss_last": float(losses[-1].item())}
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -380,6 +631,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return reference_arm(args, rank, world)
+    if args.workload != "physics":
+        return {"batch": bench_batch, "sequence": bench_sequence, "fit": bench_fit}[args.workload](args)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")

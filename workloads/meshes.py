@@ -170,3 +170,25 @@ class TorusSkinning:
 
 def bbox(V: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
     return V.min(0).astype(np.float64), V.max(0).astype(np.float64)
+
+
+def batch_scenes(n_scenes: int = 64, seed: int = 4000, fmin: int = 1000, fmax: int = 200000):
+    """Independent scenes with log-uniform face counts in [fmin, fmax]: even scenes are
+    grid tori with 2*nu*nv ~ F (nu/nv ~ 1.6), odd scenes icospheres at the subdivision
+    level nearest F; every scene gets a seeded sinusoidal radial displacement of
+    amplitude 0.05-0.15.  Returns a list of (V, F)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n_scenes):
+        F_target = int(round(np.exp(rng.uniform(np.log(fmin), np.log(fmax)))))
+        amp = rng.uniform(0.05, 0.15)
+        k1, k2 = int(rng.integers(2, 6)), int(rng.integers(1, 4))
+        ph = rng.uniform(0, 2 * np.pi)
+        if i % 2 == 0:
+            nv = max(3, int(round(np.sqrt(F_target / (2 * 1.6)))))
+            nu = max(3, int(round(1.6 * nv)))
+            out.append(displaced_torus(nu, nv, amp, k1, k2, ph))
+        else:
+            s = int(np.clip(np.round(np.log(F_target / 20.0) / np.log(4.0)), 0, 7))
+            out.append(displaced_icosphere(s, amp, ph, k_theta=k1, k_phi=k2))
+    return out

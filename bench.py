@@ -149,6 +149,10 @@ def gpu_arm(args, rank, world, local_rank):
     fixed = MeshBVH(nV, nF, dev).build(t(W.V0), F)
     rebuilt = MeshBVH(nV, nF, dev)
     rest = MeshBVH(nV, nF, dev).build(t(W.V0), F)
+    # traversal variant for the contact queries, chosen by timing on this workload
+    from paper_2606_00444_gb300.tune import tune_closest_point
+    fixed.refit(t(W.frames[0]))
+    tuned = tune_closest_point(fixed, P, CUTOFF)
     Vin = torch.empty(nV, 3, device=dev)
     contact = dict(face=torch.empty(N_PART, dtype=torch.int32, device=dev),
                    bary=torch.empty(N_PART, 3, device=dev), point=torch.empty(N_PART, 3, device=dev),
@@ -230,7 +234,9 @@ def gpu_arm(args, rank, world, local_rank):
     clocks = Clocks(local_rank)
     time.sleep(0.3)
     t0 = time.perf_counter()
+    torch.cuda.nvtx.range_push("timed")          # lets a profiler keep to the timed frames
     step_ms = timed_graph(args.steps, args.warmup)
+    torch.cuda.nvtx.range_pop()
     wall = time.perf_counter() - t0
     torch.cuda.synchronize()
     if world > 1:
@@ -291,6 +297,7 @@ def gpu_arm(args, rank, world, local_rank):
     d2h = N_PART * 8 + 16
 
     out = dict(ms=ms, wall=wall, step_ms=step_ms, stages=st, clocks=ck, e2e_ms=float(np.mean(e_ms)),
+               tuned=tuned,
                h2d=h2d, d2h=d2h, launches=launches_per_frame * args.steps,
                contact_hits=int((contact["face"] >= 0).sum().item()),
                chamfer=[float(x) for x in cd_out.cpu()])
@@ -677,6 +684,7 @@ def main():
         "gpu_launches": res["launches"],
         "contact_hits_per_frame": res["contact_hits"],
         "contact_ms_unsorted_particles": un,
+        "tuned_contact": {k: res["tuned"][k] for k in ("lanes", "variant", "tried")},
     }
     if not args.no_cpu_baseline and world == 1:
         import oracle

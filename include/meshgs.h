@@ -155,11 +155,21 @@ mesh_status mesh_closest_point(const mesh_bvh *bvh, const float *d_Q, int64_t nQ
  * width up to the tie rule's float32 margin. */
 mesh_status mesh_set_query_group(int lanes);
 
-/* One-thread-per-query traversal form for mesh_closest_point: 0 = plain
- * depth-first (default: leaf children tested as met), 1 = while-while (leaf
- * children queued while internal nodes are traversed, tested together).
- * Process-wide; for tuning and tests.  Same answers either way. */
+/* One-thread-per-query traversal variant for mesh_closest_point (tuning):
+ *   0 depth-first, 24-entry shared-memory stack per thread (default)
+ *   1 while-while: leaf children queued while internal nodes are traversed
+ *   2 depth-first, 8 shared entries    3 depth-first, stack in local memory only
+ *   4 as 0 with one leaf-test site     5 as 3 with one leaf-test site
+ * (the shared part of the stack spills to local memory; local-only leaves the
+ * SM's L1 to the node cache).  Process-wide; same answers for every variant. */
 mesh_status mesh_set_traversal(int variant);
+
+/* Traversal choice for mesh_closest_point calls on this handle (host-side
+ * setting, read when a call is made, so a captured graph keeps the choice it
+ * was captured with): lanes as mesh_set_query_group (0 = from the query
+ * count), variant as mesh_set_traversal; -1 for either = follow the
+ * process-wide setting (the default).  Set by the autotuner. */
+mesh_status mesh_bvh_set_query_config(mesh_bvh *bvh, int lanes, int variant);
 
 /* Face-bound Gaussians from the handle's current vertex buffer.  For Gaussian
  * g on face f = d_gface[g] with weights b = d_gbary[g] and normal offset

@@ -181,6 +181,11 @@ class MeshBVH:
             _ptr(None if gscale is None else _f32(gscale, 3)), gV.data_ptr(), _stream()),
             "mesh_bind_gaussians_backward")
 
+    def set_query_config(self, lanes: int = -1, variant: int = -1) -> None:
+        """Traversal choice for this handle's closest-point calls (-1 = process-wide)."""
+        check(lib().mesh_bvh_set_query_config(self.handle, int(lanes), int(variant)),
+              "mesh_bvh_set_query_config")
+
     # -- inspection -----------------------------------------------------
     def status(self) -> tuple[int, int]:
         bits = C.c_uint32()
@@ -401,7 +406,7 @@ def set_query_group(lanes: int) -> None:
 
 
 def set_traversal(variant: int) -> None:
-    """One-thread traversal form: 0 depth-first (default), 1 while-while."""
+    """One-thread traversal variant 0..5 (see mesh_set_traversal in include/meshgs.h)."""
     check(lib().mesh_set_traversal(int(variant)), "mesh_set_traversal")
 
 

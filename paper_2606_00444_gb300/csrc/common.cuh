@@ -20,6 +20,8 @@ struct __align__(16) Header {
 struct mesh_bvh_impl {
     char *base;
     mesh_bvh_layout L;
+    int cfg_lanes = -1;      // per-handle traversal choice; -1 = process-wide setting
+    int cfg_variant = -1;
     Header *hdr() const { return reinterpret_cast<Header *>(base + L.off_header); }
     float4 *verts() const { return reinterpret_cast<float4 *>(base + L.off_verts); }
     int4 *faces() const { return reinterpret_cast<int4 *>(base + L.off_faces); }

@@ -765,6 +765,8 @@ mesh_status mesh_bvh_create(void *d_storage, size_t storage_bytes, int64_t max_v
     h->L = L;
     h->L.n_faces = 0;
     h->L.n_verts = 0;
+    h->cfg_lanes = -1;
+    h->cfg_variant = -1;
     *out = h;
     return MESH_OK;
 }

@@ -243,14 +243,19 @@ __device__ __forceinline__ void test_leaf(const Traversal &T, Best &B, int leaf,
     consider(B, leaf, __float_as_int(a.w), d2, maxd2, T.tau);
 }
 
-template <int kBlockT>
+// kSmem: stack entries per thread kept in shared memory (the rest spill to a
+// local array; 0 = all local, leaving the SM's L1 to the node cache).
+// kOneSite: leaf children are gathered and tested at one call site (the nearer
+// first) instead of one site per child, so lanes testing a left and a right
+// leaf in the same step run the same instructions together.
+template <int kBlockT, int kSmem = kStackShared, bool kOneSite = false>
 __device__ __forceinline__ Hit nearest(const Traversal &T, float3 q, float maxd2,
                                        int2 (*stk)[kBlockT], unsigned int *status) {
     Best B{-1, 0x7fffffff, INFINITY, INFINITY, maxd2};
     if (T.n == 1) {
         test_leaf(T, B, 0, q, maxd2);
     } else if (T.n > 1) {
-        int2 spill[kStackTotal - kStackShared];
+        int2 spill[kStackTotal - kSmem];
         int sp = 0;
         int node = 0;
         const int tid = threadIdx.x;
@@ -265,15 +270,27 @@ __device__ __forceinline__ Hit nearest(const Traversal &T, float3 q, float maxd2
                 B.thr = fminf(B.thr, bound_window2(fminf(ml, mr), T.tau));
             }
             int cl = __float_as_int(l0.w), cr = __float_as_int(r0.w);
-            if (cl < 0 && dl <= B.thr) test_leaf(T, B, -cl - 1, q, maxd2);
-            if (cr < 0 && dr <= B.thr) test_leaf(T, B, -cr - 1, q, maxd2);
+            if constexpr (kOneSite) {
+                bool tl = cl < 0 && dl <= B.thr, tr = cr < 0 && dr <= B.thr;
+                int la = tl ? -cl - 1 : -cr - 1, lb = -cr - 1;
+                bool two = tl && tr;
+                if (two && dr < dl) { int t = la; la = lb; lb = t; }
+#pragma unroll 1
+                for (int k = 0; k < 2; ++k) {
+                    if (k == 0 ? !(tl || tr) : !two) break;
+                    test_leaf(T, B, k == 0 ? la : lb, q, maxd2);
+                }
+            } else {
+                if (cl < 0 && dl <= B.thr) test_leaf(T, B, -cl - 1, q, maxd2);
+                if (cr < 0 && dr <= B.thr) test_leaf(T, B, -cr - 1, q, maxd2);
+            }
             bool gl = cl >= 0 && dl <= B.thr;
             bool gr = cr >= 0 && dr <= B.thr;
             if (gl && gr) {
                 bool lfirst = dl < dr || (dl == dr && ml <= mr);
                 int2 e = make_int2(lfirst ? cr : cl, __float_as_int(lfirst ? dr : dl));
-                if (sp < kStackShared) stk[sp][tid] = e;
-                else if (sp < kStackTotal) spill[sp - kStackShared] = e;
+                if (sp < kSmem) stk[sp][tid] = e;
+                else if (sp < kStackTotal) spill[sp - kSmem] = e;
                 else atomicOr(status, (unsigned)MESH_DEV_STACK_OVERFLOW);
                 if (sp < kStackTotal) ++sp;
                 node = lfirst ? cl : cr;
@@ -284,7 +301,7 @@ __device__ __forceinline__ Hit nearest(const Traversal &T, float3 q, float maxd2
             bool found = false;
             while (sp > 0) {
                 --sp;
-                int2 e = sp < kStackShared ? stk[sp][tid] : spill[sp - kStackShared];
+                int2 e = sp < kSmem ? stk[sp][tid] : spill[sp - kSmem];
                 if (__int_as_float(e.y) <= B.thr) { node = e.x; found = true; break; }
             }
             if (!found) break;
@@ -601,18 +618,20 @@ __device__ __forceinline__ void write_hit(const Traversal &T, const Hit &h, floa
     }
 }
 
-template <bool kWhileWhile>
+// kMode: 0 depth-first, 1 while-while, 2 depth-first with one leaf-test site.
+template <int kSmem, int kMode>
 __global__ void __launch_bounds__(kQueryBlock, kQueryMinBlocks)
 k_closest_point(Traversal T, const Header *__restrict__ hdr, unsigned int *status,
                 const float *__restrict__ Q, int64_t nQ, float maxd2, int *face, float *bary,
                 float *point, float *dist2) {
-    __shared__ int2 stk[kStackShared][kQueryBlock];
+    __shared__ int2 stk[kSmem > 0 ? kSmem : 1][kQueryBlock];
     int64_t i = (int64_t)blockIdx.x * kQueryBlock + threadIdx.x;
     if (i >= nQ) return;
     T.tau = traversal_tau(hdr);
     float3 q = make_float3(Q[3 * i], Q[3 * i + 1], Q[3 * i + 2]);
-    Hit h = kWhileWhile ? nearest_ww<kQueryBlock>(T, q, maxd2, stk, status)
-                        : nearest<kQueryBlock>(T, q, maxd2, stk, status);
+    Hit h;
+    if constexpr (kMode == 1) h = nearest_ww<kQueryBlock>(T, q, maxd2, stk, status);
+    else h = nearest<kQueryBlock, kSmem, kMode == 2>(T, q, maxd2, stk, status);
     write_hit(T, h, q, i, face, bary, point, dist2);
 }
 
@@ -779,7 +798,7 @@ static size_t chamfer_blocks(int64_t n, int G = 1) {
 // of two G <= 32 that does.  (An explicit override can come from
 // mesh_set_query_group.)
 static int g_group_override = 0;
-static int g_traversal = 0;          // one-thread traversal: 0 depth-first, 1 while-while
+static int g_traversal = 0;          // one-thread traversal variant, see mesh_set_traversal
 static int pick_group(int64_t nQ) {
     if (g_group_override > 0) return g_group_override;
     static int sms = 0;
@@ -809,16 +828,23 @@ mesh_status mesh_closest_point(const mesh_bvh *bvh, const float *d_Q, int64_t nQ
     if (nQ == 0) return MESH_OK;
     float maxd2 = isinf(max_dist) ? INFINITY : max_dist * max_dist;
     cudaStream_t s = (cudaStream_t)stream;
-    int G = pick_group(nQ);
+    int G = bvh->cfg_lanes > 0 ? bvh->cfg_lanes : pick_group(nQ);
+    int variant = bvh->cfg_variant >= 0 ? bvh->cfg_variant : g_traversal;
     Traversal T = traversal_of(bvh, isinf(max_dist));
     Header *h = bvh->hdr();
     unsigned int grid = grid_for(nQ * G, kQueryBlock);
     switch (G) {
         case 1:
-            if (g_traversal == 1)
-                k_closest_point<true><<<grid, kQueryBlock, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2);
-            else
-                k_closest_point<false><<<grid, kQueryBlock, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2);
+#define MESH_CP_ARGS <<<grid, kQueryBlock, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2)
+            switch (variant) {
+                case 1: k_closest_point<kStackShared, 1> MESH_CP_ARGS; break;
+                case 2: k_closest_point<8, 0> MESH_CP_ARGS; break;
+                case 3: k_closest_point<0, 0> MESH_CP_ARGS; break;
+                case 4: k_closest_point<kStackShared, 2> MESH_CP_ARGS; break;
+                case 5: k_closest_point<0, 2> MESH_CP_ARGS; break;
+                default: k_closest_point<kStackShared, 0> MESH_CP_ARGS; break;
+            }
+#undef MESH_CP_ARGS
             break;
         case 2: k_closest_point_group<2><<<grid, kQueryBlock, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2); break;
         case 4: k_closest_point_group<4><<<grid, kQueryBlock, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2); break;
@@ -906,8 +932,19 @@ mesh_status mesh_set_query_group(int lanes) {
     return MESH_OK;
 }
 
+mesh_status mesh_bvh_set_query_config(mesh_bvh *bvh, int lanes, int variant) {
+    if (!bvh) return MESH_ERR_INVALID_ARG;
+    if (lanes != -1 && lanes != 0 && lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8 &&
+        lanes != 16 && lanes != 32)
+        return MESH_ERR_INVALID_ARG;
+    if (variant < -1 || variant > 5) return MESH_ERR_INVALID_ARG;
+    bvh->cfg_lanes = lanes;
+    bvh->cfg_variant = variant;
+    return MESH_OK;
+}
+
 mesh_status mesh_set_traversal(int variant) {
-    if (variant != 0 && variant != 1) return MESH_ERR_INVALID_ARG;
+    if (variant < 0 || variant > 5) return MESH_ERR_INVALID_ARG;
     g_traversal = variant;
     return MESH_OK;
 }

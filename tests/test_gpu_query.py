@@ -145,8 +145,8 @@ def test_every_group_width_matches_oracle(c1, lanes):
         set_query_group(0)
 
 
-@pytest.mark.parametrize("variant", [0, 1])
-def test_both_thread_traversals_match_oracle(c1, variant):
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5])
+def test_every_thread_traversal_matches_oracle(c1, variant):
     from paper_2606_00444_gb300 import set_query_group, set_traversal
     _, _, VG, FG, Q = c1
     bvh = MeshBVH.from_mesh(dev(VG), dev(FG))

@@ -47,6 +47,8 @@ WORKLOAD = "fixed-topology physics frame: torus 100k V / 200k F, 4-bone LBS, 1M 
 NU, NV_, CUTOFF, N_PART, G_PER_FACE, N_CD = 400, 250, 0.05, 1 << 20, 3, 10000
 SEED = 3000
 CONTACT_BYTES = 12 + 4 + 12 + 12 + 4      # query xyz in; face, bary, point, dist2 out
+NODE_BYTES = 64                            # one node visit reads both child boxes + links
+TRI_BYTES = 48                             # one triangle test reads a packed triangle
 
 
 def parse():
@@ -296,12 +298,28 @@ def gpu_arm(args, rank, world, local_rank):
     h2d = nV * 12 + N_PART * 12
     d2h = N_PART * 8 + 16
 
+    # traversal work of the contact queries on this frame (counting kernel, untimed)
+    stats = fixed.closest_point_stats(P, CUTOFF)
     out = dict(ms=ms, wall=wall, step_ms=step_ms, stages=st, clocks=ck, e2e_ms=float(np.mean(e_ms)),
-               tuned=tuned,
+               tuned=tuned, stats=stats,
                h2d=h2d, d2h=d2h, launches=launches_per_frame * args.steps,
                contact_hits=int((contact["face"] >= 0).sum().item()),
                chamfer=[float(x) for x in cd_out.cpu()])
     return out, W
+
+
+def contact_traffic():
+    """DRAM bytes per launch of the contact kernel from the committed ncu capture, if the
+    kernel source is still the one that was captured (else None)."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    m = hashlib.sha256()
+    for f in d.get("source_files", []):
+        m.update(open(os.path.join(ROOT, f), "rb").read())
+    return d["traffic_bytes_per_launch"] if m.hexdigest()[:16] == d.get("source_hash") else None
 
 
 def peaks():
@@ -650,7 +668,11 @@ def main():
     ms = res["ms"]
     hbm, src = peaks()
     t_contact = res["stages"]["contact"] * 1e-3
-    achieved = CONTACT_BYTES * N_PART / t_contact / 1e9
+    vis = res["stats"]["visits"] / N_PART
+    tst = res["stats"]["tests"] / N_PART
+    per_query = CONTACT_BYTES + NODE_BYTES * vis + TRI_BYTES * tst
+    achieved = per_query * N_PART / t_contact / 1e9
+    achieved_io = CONTACT_BYTES * N_PART / t_contact / 1e9
     st = dict(res["stages"])
     un = st.pop("contact_unsorted_particles")
     line = {
@@ -676,8 +698,11 @@ def main():
                          "refit": st["refit"], "rebuild": st["rebuild"]},
         "roofline": {"kernel": "k_closest_point (contact, 1M queries)", "bound": "hbm",
                      "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "peak_source": src, "traffic": None,
-                     "bytes_per_query": CONTACT_BYTES},
+                     "frac": achieved / hbm, "peak_source": src, "traffic": contact_traffic(),
+                     "bytes_per_query": per_query,
+                     "per_query": {"io": CONTACT_BYTES, "node_visits": vis, "triangle_tests": tst,
+                                   "node_bytes": NODE_BYTES, "triangle_bytes": TRI_BYTES},
+                     "frac_io_only": achieved_io / hbm},
         "clocks": res["clocks"],
         "e2e": {"value": world * q / (res["e2e_ms"] * 1e-3), "unit": "queries/s",
                 "h2d_bytes_per_step": res["h2d"], "d2h_bytes_per_step": res["d2h"]},

@@ -146,6 +146,14 @@ mesh_status mesh_closest_point(const mesh_bvh *bvh, const float *d_Q, int64_t nQ
                                float max_dist, int32_t *d_face, float *d_bary, float *d_point,
                                float *d_dist2, void *stream);
 
+/* Work counters of the one-thread depth-first traversal for these queries:
+ * d_counts[0] = node visits (each reads one 64-byte record holding two child
+ * boxes), d_counts[1] = triangle tests, d_counts[2] = queries with a face
+ * within max_dist; uint64, summed over all queries.  Runs a separate counting
+ * kernel; writes no query results.  For roofline accounting and diagnosis. */
+mesh_status mesh_closest_point_stats(const mesh_bvh *bvh, const float *d_Q, int64_t nQ,
+                                     float max_dist, unsigned long long *d_counts, void *stream);
+
 /* Lanes that cooperate on one query in mesh_closest_point and mesh_chamfer.
  * 0 (default) picks from the query count: one thread per query when the
  * queries fill the GPU, else the smallest power of two up to 32 that does (a

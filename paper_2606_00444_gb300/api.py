@@ -135,6 +135,15 @@ class MeshBVH:
               "mesh_closest_point")
         return out
 
+    def closest_point_stats(self, Q: torch.Tensor, max_dist: float = math.inf) -> dict:
+        """Traversal work for these queries: node visits, triangle tests, hits (totals)."""
+        Q = _f32(Q, 3, "Q")
+        c = torch.zeros(3, dtype=torch.int64, device=Q.device)
+        check(lib().mesh_closest_point_stats(self.handle, Q.data_ptr(), Q.shape[0], float(max_dist),
+                                             c.data_ptr(), _stream()), "mesh_closest_point_stats")
+        v = c.tolist()
+        return dict(visits=v[0], tests=v[1], hits=v[2])
+
     def bind_gaussians(self, gface, gbary, goff=None, out=None):
         gface = _i32(gface, None, "gface")
         gbary = _f32(gbary, 3, "gbary")

@@ -248,11 +248,17 @@ __device__ __forceinline__ void test_leaf(const Traversal &T, Best &B, int leaf,
 // kOneSite: leaf children are gathered and tested at one call site (the nearer
 // first) instead of one site per child, so lanes testing a left and a right
 // leaf in the same step run the same instructions together.
-template <int kBlockT, int kSmem = kStackShared, bool kOneSite = false>
+struct Counts {
+    int visits, tests;
+};
+
+template <int kBlockT, int kSmem = kStackShared, bool kOneSite = false, bool kCount = false>
 __device__ __forceinline__ Hit nearest(const Traversal &T, float3 q, float maxd2,
-                                       int2 (*stk)[kBlockT], unsigned int *status) {
+                                       int2 (*stk)[kBlockT], unsigned int *status,
+                                       Counts *cnt = nullptr) {
     Best B{-1, 0x7fffffff, INFINITY, INFINITY, maxd2};
     if (T.n == 1) {
+        if constexpr (kCount) cnt->tests++;
         test_leaf(T, B, 0, q, maxd2);
     } else if (T.n > 1) {
         int2 spill[kStackTotal - kSmem];
@@ -261,6 +267,7 @@ __device__ __forceinline__ Hit nearest(const Traversal &T, float3 q, float maxd2
         const int tid = threadIdx.x;
         while (true) {
             const float4 *r = T.nodes + 4 * (size_t)node;
+            if constexpr (kCount) cnt->visits++;
             float4 l0 = ldg4(r), l1 = ldg4(r + 1), r0 = ldg4(r + 2), r1 = ldg4(r + 3);
             float dl = box_d2(q, l0, l1), dr = box_d2(q, r0, r1);
             float ml = 0.0f, mr = 0.0f;
@@ -270,6 +277,7 @@ __device__ __forceinline__ Hit nearest(const Traversal &T, float3 q, float maxd2
                 B.thr = fminf(B.thr, bound_window2(fminf(ml, mr), T.tau));
             }
             int cl = __float_as_int(l0.w), cr = __float_as_int(r0.w);
+            if constexpr (kCount) cnt->tests += (cl < 0 && dl <= B.thr) + (cr < 0 && dr <= B.thr);
             if constexpr (kOneSite) {
                 bool tl = cl < 0 && dl <= B.thr, tr = cr < 0 && dr <= B.thr;
                 int la = tl ? -cl - 1 : -cr - 1, lb = -cr - 1;
@@ -635,6 +643,36 @@ k_closest_point(Traversal T, const Header *__restrict__ hdr, unsigned int *statu
     write_hit(T, h, q, i, face, bary, point, dist2);
 }
 
+// Counting form of the one-thread depth-first traversal (same visiting order
+// as variants 0, 2 and 3): node visits, triangle tests and hits, summed over
+// all queries.  Separate instantiation; the timed kernels carry no counters.
+__global__ void __launch_bounds__(kQueryBlock, kQueryMinBlocks)
+k_closest_point_count(Traversal T, const Header *__restrict__ hdr, unsigned int *status,
+                      const float *__restrict__ Q, int64_t nQ, float maxd2,
+                      unsigned long long *counts) {
+    __shared__ int2 stk[kStackShared][kQueryBlock];
+    int64_t i = (int64_t)blockIdx.x * kQueryBlock + threadIdx.x;
+    Counts c{0, 0};
+    int hit = 0;
+    if (i < nQ) {
+        T.tau = traversal_tau(hdr);
+        float3 q = make_float3(Q[3 * i], Q[3 * i + 1], Q[3 * i + 2]);
+        Hit h = nearest<kQueryBlock, kStackShared, false, true>(T, q, maxd2, stk, status, &c);
+        hit = h.leaf >= 0;
+    }
+    unsigned long long v = c.visits, t = c.tests, k = hit;
+    for (int o = 16; o > 0; o >>= 1) {
+        v += __shfl_xor_sync(0xffffffffu, v, o);
+        t += __shfl_xor_sync(0xffffffffu, t, o);
+        k += __shfl_xor_sync(0xffffffffu, k, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(counts, v);
+        atomicAdd(counts + 1, t);
+        atomicAdd(counts + 2, k);
+    }
+}
+
 template <int G>
 __global__ void __launch_bounds__(kQueryBlock)
 k_closest_point_group(Traversal T, const Header *__restrict__ hdr, unsigned int *status,
@@ -920,6 +958,21 @@ mesh_status mesh_batch_closest_point(mesh_batch *batch, const float *d_Q,
         batch->nodes(), batch->tris(), batch->scene_box(), batch->face_off(), d_query_off,
         (int)batch->L.n_scenes, d_Q, nQ, maxd2, isinf(max_dist), d_face, d_bary, d_point, d_dist2,
         &batch->st()->status, work);
+    count_launch();
+    return check_launch();
+}
+
+mesh_status mesh_closest_point_stats(const mesh_bvh *bvh, const float *d_Q, int64_t nQ,
+                                     float max_dist, unsigned long long *d_counts, void *stream) {
+    if (!bvh || !d_counts || nQ < 0 || (nQ > 0 && !d_Q) || !(max_dist >= 0.0f))
+        return MESH_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaMemsetAsync(d_counts, 0, 3 * sizeof(unsigned long long), s);
+    if (nQ == 0) return check_launch();
+    float maxd2 = isinf(max_dist) ? INFINITY : max_dist * max_dist;
+    k_closest_point_count<<<grid_for(nQ, kQueryBlock), kQueryBlock, 0, s>>>(
+        traversal_of(bvh, isinf(max_dist)), bvh->hdr(), &bvh->hdr()->status, d_Q, nQ, maxd2,
+        d_counts);
     count_launch();
     return check_launch();
 }

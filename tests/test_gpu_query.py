@@ -158,3 +158,16 @@ def test_every_thread_traversal_matches_oracle(c1, variant):
     finally:
         set_query_group(0)
         set_traversal(0)
+
+
+def test_traversal_counters_are_consistent(c1):
+    _, _, VG, FG, Q = c1
+    bvh = MeshBVH.from_mesh(dev(VG), dev(FG))
+    for cut in (np.inf, 0.05):
+        st = bvh.closest_point_stats(dev(Q), cut)
+        out = bvh.closest_point(dev(Q), max_dist=cut)
+        hits = int((out["face"] >= 0).sum().item())
+        assert st["hits"] == hits
+        assert st["tests"] >= hits and st["visits"] >= Q.shape[0] // 2
+        # a bounded search never works harder than an unbounded one
+    assert bvh.closest_point_stats(dev(Q), 0.05)["visits"] < bvh.closest_point_stats(dev(Q))["visits"]

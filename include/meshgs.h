@@ -168,6 +168,12 @@ mesh_status mesh_set_query_group(int lanes);
  *   1 while-while: leaf children queued while internal nodes are traversed
  *   2 depth-first, 8 shared entries    3 depth-first, stack in local memory only
  *   4 as 0 with one leaf-test site     5 as 3 with one leaf-test site
+ *   6 as 2, 12 blocks per SM (<= 40 registers)   7 as 3, 12 blocks per SM
+ *   8 as 3, 16 blocks per SM (<= 32 registers)   9 as 5, 12 blocks per SM
+ *  10 persistent, dynamic fetch: lanes take new queries as they finish
+ *     (8 shared entries)                          11 as 10, local stack only
+ *     (10 and 11 keep a work counter in the handle: calls on one handle must
+ *     not overlap on the GPU)
  * (the shared part of the stack spills to local memory; local-only leaves the
  * SM's L1 to the node cache).  Process-wide; same answers for every variant. */
 mesh_status mesh_set_traversal(int variant);

@@ -28,7 +28,7 @@ constexpr int kSortItems = 4;
 constexpr int kSortTile = kSortThreads * kSortItems;   // keys per sort tile
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kRadix = 256;
-constexpr int kScanThreads = 1024;
+constexpr int kScanThreads = 256;     // one block per digit; also scans the 256 digit totals
 static_assert(kSortThreads == kRadix, "one thread per digit in the sort kernels");
 
 // ---------------------------------------------------------------------------
@@ -260,36 +260,52 @@ __device__ unsigned int block_excl_scan(unsigned int x, unsigned int *s_warp, un
     return r;
 }
 
-// Exclusive scan of hist[0, total) in place by one block: consecutive chunks of
-// kScanThreads * 4 entries, each thread loading 4 consecutive entries
-// (coalesced as one 16-byte load when aligned), a block scan of the per-thread
-// sums, and a running carry between chunks.
+// Offsets for one pass, by one block per digit d: an exclusive scan of the
+// digit's per-tile counts hist[d * T + t] (in place, tile offsets within the
+// digit), and the digit's total.  The last block to finish (ticket counter;
+// nobody waits) turns the 256 totals into exclusive digit bases and resets the
+// ticket.  The output position of digit d in tile t is base[d] + hist[d*T+t].
 __global__ void __launch_bounds__(kScanThreads)
-k_sort_scan(unsigned int *__restrict__ hist, int total) {
+k_sort_scan(unsigned int *__restrict__ hist, int T, unsigned int *__restrict__ dsum,
+            unsigned int *__restrict__ base, unsigned int *__restrict__ ticket) {
     __shared__ unsigned int s_warp[33];
+    __shared__ bool s_last;
+    unsigned int *h = hist + (size_t)blockIdx.x * T;
     unsigned int carry = 0;
     const int chunk = kScanThreads * 4;
-    for (int base = 0; base < total; base += chunk) {
-        int i0 = base + 4 * threadIdx.x;
+    for (int b0 = 0; b0 < T; b0 += chunk) {
+        int i0 = b0 + 4 * threadIdx.x;
         unsigned int v[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) v[k] = (i0 + k < total) ? hist[i0 + k] : 0u;
-        unsigned int sum = v[0] + v[1] + v[2] + v[3];
+        for (int k = 0; k < 4; ++k) v[k] = (i0 + k < T) ? h[i0 + k] : 0u;
         unsigned int tot;
-        unsigned int run = carry + block_excl_scan(sum, s_warp, &tot);
+        unsigned int run = carry + block_excl_scan(v[0] + v[1] + v[2] + v[3], s_warp, &tot);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            if (i0 + k < total) hist[i0 + k] = run;
+            if (i0 + k < T) h[i0 + k] = run;
             run += v[k];
         }
         carry += tot;
     }
+    if (threadIdx.x == 0) {
+        dsum[blockIdx.x] = carry;
+        __threadfence();
+        s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    unsigned int x = threadIdx.x < kRadix ? __ldcg(dsum + threadIdx.x) : 0u;
+    unsigned int ex = block_excl_scan(x, s_warp, nullptr);
+    if (threadIdx.x < kRadix) base[threadIdx.x] = ex;
+    if (threadIdx.x == 0) *ticket = 0u;
 }
 
 __global__ void __launch_bounds__(kSortThreads)
 k_sort_downsweep(const unsigned int *__restrict__ kin, const int *__restrict__ vin,
                  unsigned int *__restrict__ kout, int *__restrict__ vout, int n, int shift,
-                 const unsigned int *__restrict__ hist, int T) {
+                 const unsigned int *__restrict__ hist, int T,
+                 const unsigned int *__restrict__ dbase) {
     __shared__ unsigned int s_keys[kSortTile];
     __shared__ int s_vals[kSortTile];
     __shared__ unsigned int s_wcnt[kSortWarps][kRadix];
@@ -327,7 +343,7 @@ k_sort_downsweep(const unsigned int *__restrict__ kin, const int *__restrict__ v
     }
     unsigned int start = block_excl_scan(run, s_warp, nullptr);
     s_dstart[tid] = start;
-    s_goff[tid] = hist[(size_t)tid * T + blockIdx.x];
+    s_goff[tid] = dbase[tid] + hist[(size_t)tid * T + blockIdx.x];
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
@@ -618,7 +634,7 @@ __global__ void k_batch_leaves_up(int nF, const int *__restrict__ face_off, int 
 // Build workspace layout.
 // ---------------------------------------------------------------------------
 struct BuildWs {
-    unsigned int *keysA, *keysB, *hist, *cbox;
+    unsigned int *keysA, *keysB, *hist, *cbox, *dsum, *dbase, *ticket;
     int *valsA, *valsB;
     float4 *cent;
     int tiles;
@@ -638,6 +654,9 @@ static BuildWs build_ws_layout(char *base, int64_t nF) {
     w.cent = (float4 *)take(16 * n);
     w.hist = (unsigned int *)take((size_t)4 * kRadix * w.tiles);
     w.cbox = (unsigned int *)take(32);
+    w.dsum = (unsigned int *)take(4 * kRadix);
+    w.dbase = (unsigned int *)take(4 * kRadix);
+    w.ticket = (unsigned int *)take(4);
     w.bytes = off;
     return w;
 }
@@ -646,15 +665,16 @@ static BuildWs build_ws_layout(char *base, int64_t nF) {
 // out_vals).  out_keys may be w.keysA (the last pass reads B).
 static void radix_sort_pairs(const BuildWs &w, int n, unsigned int *out_keys, int *out_vals,
                              cudaStream_t s) {
+    cudaMemsetAsync(w.ticket, 0, sizeof(unsigned int), s);   // each pass's last block re-zeroes it
     unsigned int *kin = w.keysA, *kout = w.keysB;
     int *vin = w.valsA, *vout = w.valsB;
     for (int pass = 0; pass < 4; ++pass) {
         if (pass == 3) { kout = out_keys; vout = out_vals; }
         int shift = 8 * pass;
         k_sort_upsweep<<<w.tiles, kSortThreads, 0, s>>>(kin, n, shift, w.hist, w.tiles);
-        k_sort_scan<<<1, kScanThreads, 0, s>>>(w.hist, kRadix * w.tiles);
+        k_sort_scan<<<kRadix, kScanThreads, 0, s>>>(w.hist, w.tiles, w.dsum, w.dbase, w.ticket);
         k_sort_downsweep<<<w.tiles, kSortThreads, 0, s>>>(kin, vin, kout, vout, n, shift, w.hist,
-                                                          w.tiles);
+                                                          w.tiles, w.dbase);
         count_launch(3);
         unsigned int *tk = kin; kin = kout; kout = tk;
         int *tv = vin; vin = vout; vout = tv;
@@ -663,9 +683,11 @@ static void radix_sort_pairs(const BuildWs &w, int n, unsigned int *out_keys, in
 
 static void radix_pass(const BuildWs &w, int n, int shift, const unsigned int *kin, const int *vin,
                        unsigned int *kout, int *vout, cudaStream_t s) {
+    cudaMemsetAsync(w.ticket, 0, sizeof(unsigned int), s);
     k_sort_upsweep<<<w.tiles, kSortThreads, 0, s>>>(kin, n, shift, w.hist, w.tiles);
-    k_sort_scan<<<1, kScanThreads, 0, s>>>(w.hist, kRadix * w.tiles);
-    k_sort_downsweep<<<w.tiles, kSortThreads, 0, s>>>(kin, vin, kout, vout, n, shift, w.hist, w.tiles);
+    k_sort_scan<<<kRadix, kScanThreads, 0, s>>>(w.hist, w.tiles, w.dsum, w.dbase, w.ticket);
+    k_sort_downsweep<<<w.tiles, kSortThreads, 0, s>>>(kin, vin, kout, vout, n, shift, w.hist, w.tiles,
+                                                      w.dbase);
     count_launch(3);
 }
 

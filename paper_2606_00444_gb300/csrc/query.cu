@@ -627,8 +627,11 @@ __device__ __forceinline__ void write_hit(const Traversal &T, const Hit &h, floa
 }
 
 // kMode: 0 depth-first, 1 while-while, 2 depth-first with one leaf-test site.
-template <int kSmem, int kMode>
-__global__ void __launch_bounds__(kQueryBlock, kQueryMinBlocks)
+// kMinBlocks: resident blocks per SM the register budget must allow
+// (8 -> 64 registers, 12 -> 40, 16 -> 32; fewer registers, more warps to hide
+// latency, more spilling).
+template <int kSmem, int kMode, int kMinBlocks = kQueryMinBlocks>
+__global__ void __launch_bounds__(kQueryBlock, kMinBlocks)
 k_closest_point(Traversal T, const Header *__restrict__ hdr, unsigned int *status,
                 const float *__restrict__ Q, int64_t nQ, float maxd2, int *face, float *bary,
                 float *point, float *dist2) {
@@ -641,6 +644,101 @@ k_closest_point(Traversal T, const Header *__restrict__ hdr, unsigned int *statu
     if constexpr (kMode == 1) h = nearest_ww<kQueryBlock>(T, q, maxd2, stk, status);
     else h = nearest<kQueryBlock, kSmem, kMode == 2>(T, q, maxd2, stk, status);
     write_hit(T, h, q, i, face, bary, point, dist2);
+}
+
+// Persistent depth-first traversal with dynamic fetch (Aila & Laine 2009):
+// a fixed grid of warps; each lane works through a stream of queries, one
+// node visit per step, and when at least kRefill lanes of the warp are idle
+// the warp takes that many new query indices from a global counter.  Lanes no
+// longer wait for the slowest query of their warp (contact queries near the
+// surface need ~6x the visits of those far from it).  Same answers as the
+// depth-first kernels.  The counter lives in the mesh header (zeroed before
+// each launch), so concurrent calls on one handle must not overlap.
+constexpr int kRefill = 8;
+
+template <int kSmem>
+__global__ void __launch_bounds__(kQueryBlock, kQueryMinBlocks)
+k_closest_point_persistent(Traversal T, const Header *__restrict__ hdr, unsigned int *status,
+                           const float *__restrict__ Q, int64_t nQ, float maxd2, int *face,
+                           float *bary, float *point, float *dist2, unsigned int *work) {
+    __shared__ int2 stk[kSmem > 0 ? kSmem : 1][kQueryBlock];
+    int2 spill[kStackTotal - kSmem];
+    const int lane = threadIdx.x & 31, tid = threadIdx.x;
+    const unsigned lt = (1u << lane) - 1u;
+    T.tau = traversal_tau(hdr);
+    int64_t qi = -1;
+    float3 q = make_float3(0.f, 0.f, 0.f);
+    Best B{-1, 0x7fffffff, INFINITY, INFINITY, maxd2};
+    int node = 0, sp = 0;
+    bool exhausted = false;
+    while (true) {
+        bool fin = false;
+        unsigned idle = __ballot_sync(0xffffffffu, qi < 0);
+        if (!exhausted && (__popc(idle) >= kRefill || idle == 0xffffffffu)) {
+            unsigned int base = 0, want = __popc(idle);
+            if (lane == 0) base = atomicAdd(work, want);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if ((int64_t)base + want >= nQ) exhausted = true;
+            if (qi < 0) {
+                int64_t cand = (int64_t)base + __popc(idle & lt);
+                if (cand < nQ) {
+                    qi = cand;
+                    q = make_float3(Q[3 * qi], Q[3 * qi + 1], Q[3 * qi + 2]);
+                    B = Best{-1, 0x7fffffff, INFINITY, INFINITY, maxd2};
+                    node = 0;
+                    sp = 0;
+                    if (T.n <= 1) {                      // no internal node to visit
+                        if (T.n == 1) test_leaf(T, B, 0, q, maxd2);
+                        fin = true;
+                    }
+                }
+            }
+        }
+        // every lane reaches this vote each iteration (a full-warp collective
+        // must never sit on a path only some lanes take)
+        const bool all_idle = __all_sync(0xffffffffu, qi < 0);
+        if (all_idle && exhausted) break;
+        if (qi < 0) continue;
+        if (!fin) {                                      // one node visit
+            const float4 *r = T.nodes + 4 * (size_t)node;
+            float4 l0 = ldg4(r), l1 = ldg4(r + 1), r0 = ldg4(r + 2), r1 = ldg4(r + 3);
+            float dl = box_d2(q, l0, l1), dr = box_d2(q, r0, r1);
+            float ml = 0.0f, mr = 0.0f;
+            if (T.mmd) {
+                ml = box_minmax_d2(q, l0, l1);
+                mr = box_minmax_d2(q, r0, r1);
+                B.thr = fminf(B.thr, bound_window2(fminf(ml, mr), T.tau));
+            }
+            int cl = __float_as_int(l0.w), cr = __float_as_int(r0.w);
+            if (cl < 0 && dl <= B.thr) test_leaf(T, B, -cl - 1, q, maxd2);
+            if (cr < 0 && dr <= B.thr) test_leaf(T, B, -cr - 1, q, maxd2);
+            bool gol = cl >= 0 && dl <= B.thr, gor = cr >= 0 && dr <= B.thr;
+            if (gol && gor) {
+                bool lfirst = dl < dr || (dl == dr && ml <= mr);
+                int2 e = make_int2(lfirst ? cr : cl, __float_as_int(lfirst ? dr : dl));
+                if (sp < kSmem) stk[sp][tid] = e;
+                else if (sp < kStackTotal) spill[sp - kSmem] = e;
+                else atomicOr(status, (unsigned)MESH_DEV_STACK_OVERFLOW);
+                if (sp < kStackTotal) ++sp;
+                node = lfirst ? cl : cr;
+            } else if (gol) {
+                node = cl;
+            } else if (gor) {
+                node = cr;
+            } else {
+                fin = true;
+                while (sp > 0) {
+                    --sp;
+                    int2 e = sp < kSmem ? stk[sp][tid] : spill[sp - kSmem];
+                    if (__int_as_float(e.y) <= B.thr) { node = e.x; fin = false; break; }
+                }
+            }
+        }
+        if (fin) {
+            write_hit(T, Hit{B.leaf, B.face, B.d2}, q, qi, face, bary, point, dist2);
+            qi = -1;
+        }
+    }
 }
 
 // Counting form of the one-thread depth-first traversal (same visiting order
@@ -868,6 +966,7 @@ mesh_status mesh_closest_point(const mesh_bvh *bvh, const float *d_Q, int64_t nQ
     cudaStream_t s = (cudaStream_t)stream;
     int G = bvh->cfg_lanes > 0 ? bvh->cfg_lanes : pick_group(nQ);
     int variant = bvh->cfg_variant >= 0 ? bvh->cfg_variant : g_traversal;
+    if (variant >= 10 && nQ >= ((int64_t)1 << 31)) variant = 0;   // 32-bit work counter
     Traversal T = traversal_of(bvh, isinf(max_dist));
     Header *h = bvh->hdr();
     unsigned int grid = grid_for(nQ * G, kQueryBlock);
@@ -880,6 +979,28 @@ mesh_status mesh_closest_point(const mesh_bvh *bvh, const float *d_Q, int64_t nQ
                 case 3: k_closest_point<0, 0> MESH_CP_ARGS; break;
                 case 4: k_closest_point<kStackShared, 2> MESH_CP_ARGS; break;
                 case 5: k_closest_point<0, 2> MESH_CP_ARGS; break;
+                case 6: k_closest_point<8, 0, 12> MESH_CP_ARGS; break;
+                case 7: k_closest_point<0, 0, 12> MESH_CP_ARGS; break;
+                case 8: k_closest_point<0, 0, 16> MESH_CP_ARGS; break;
+                case 9: k_closest_point<0, 2, 12> MESH_CP_ARGS; break;
+                case 10:
+                case 11: {
+                    static int sms = 0;
+                    if (sms == 0) {
+                        int dv = 0;
+                        if (cudaGetDevice(&dv) != cudaSuccess ||
+                            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dv) != cudaSuccess || sms <= 0)
+                            sms = 152;
+                    }
+                    unsigned int *work = &h->pad[0];
+                    cudaMemsetAsync(work, 0, sizeof(unsigned int), s);
+                    unsigned int pg = (unsigned int)((int64_t)sms * kQueryMinBlocks < (int64_t)grid ? sms * kQueryMinBlocks : grid);
+                    if (variant == 10)
+                        k_closest_point_persistent<8><<<pg, kQueryBlock, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2, work);
+                    else
+                        k_closest_point_persistent<0><<<pg, kQueryBlock, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2, work);
+                    break;
+                }
                 default: k_closest_point<kStackShared, 0> MESH_CP_ARGS; break;
             }
 #undef MESH_CP_ARGS
@@ -990,14 +1111,14 @@ mesh_status mesh_bvh_set_query_config(mesh_bvh *bvh, int lanes, int variant) {
     if (lanes != -1 && lanes != 0 && lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8 &&
         lanes != 16 && lanes != 32)
         return MESH_ERR_INVALID_ARG;
-    if (variant < -1 || variant > 5) return MESH_ERR_INVALID_ARG;
+    if (variant < -1 || variant > 11) return MESH_ERR_INVALID_ARG;
     bvh->cfg_lanes = lanes;
     bvh->cfg_variant = variant;
     return MESH_OK;
 }
 
 mesh_status mesh_set_traversal(int variant) {
-    if (variant < 0 || variant > 5) return MESH_ERR_INVALID_ARG;
+    if (variant < 0 || variant > 11) return MESH_ERR_INVALID_ARG;
     g_traversal = variant;
     return MESH_OK;
 }

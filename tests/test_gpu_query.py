@@ -145,7 +145,7 @@ def test_every_group_width_matches_oracle(c1, lanes):
         set_query_group(0)
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("variant", list(range(12)))
 def test_every_thread_traversal_matches_oracle(c1, variant):
     from paper_2606_00444_gb300 import set_query_group, set_traversal
     _, _, VG, FG, Q = c1

@@ -75,7 +75,11 @@ typedef struct {
     size_t off_parent;   /* int32  [2 max_faces - 1]  2 * parent + side (0 left, 1 right),
                             -1 at the root; internal nodes first, then leaves                 */
     size_t off_tris;     /* 3 x float4 per leaf: (v0, face id bits) (v1, 0) (v2, 0)           */
-    size_t off_flags;    /* uint32 [max_faces]   bottom-up arrival counters (kept at zero)    */
+    size_t off_rend;     /* int32 [max_faces]   far end of internal node i's leaf range        */
+    size_t off_xlist;    /* bottom-up scratch, per block of 1024 leaves: edge records (box of a
+                            child whose parent's leaf range crosses blocks, 2048 x 32 B per
+                            block), crossing nodes int32x4 [max_faces] (node, prefix length,
+                            parent link, 0), then int32 per-block counts of both             */
     size_t storage_bytes;
 } mesh_bvh_layout;
 
@@ -131,8 +135,15 @@ mesh_status mesh_morton_order(const float *d_P, int64_t n, int32_t *d_order, voi
 mesh_status mesh_update_vertices(mesh_bvh *bvh, const float *d_V, int64_t nV, void *stream);
 
 /* Recompute every node box over the fixed topology from the current vertex
- * buffer (after mesh_update_vertices).  If d_V is not NULL the vertex-buffer
- * update is done first, as by mesh_update_vertices(bvh, d_V, nV). */
+ * buffer (after mesh_update_vertices).  If d_V is not NULL (nV equal to the
+ * built mesh's) the vertex-buffer update is part of the same pass, with the
+ * same result as mesh_update_vertices(bvh, d_V, nV) followed by
+ * mesh_refit(bvh, NULL, 0).  Two kernels, the same the build ends with: one
+ * block per 1024 consecutive leaves computes every subtree lying inside its
+ * leaf range in shared memory, then one block finishes the nodes whose
+ * ranges cross those blocks in shared memory (or, past about 5000 such nodes,
+ * every block climbs its share through L2).  Nothing is derived once per
+ * topology: a refit after any build is valid. */
 mesh_status mesh_refit(mesh_bvh *bvh, const float *d_V, int64_t nV, void *stream);
 
 /* NearestSurface (Eq. 1 / Eq. 2): for each query q the closest point of the

@@ -227,6 +227,7 @@ class MeshBVH:
             perm=view(L["off_perm"], n, torch.int32, (n,)),
             parent=view(L["off_parent"], max(2 * n - 1, 0), torch.int32, (max(2 * n - 1, 0),)),
             tris=view(L["off_tris"], 12 * n, torch.float32, (n, 3, 4)),
+            header=view(L["off_header"], 10, torch.int32, (10,)),     # root box, status, degenerate count
         )
         m = max(n - 1, 0)
         out["nodes"] = view(L["off_nodes"], 16 * m, torch.float32, (m, 4, 4))

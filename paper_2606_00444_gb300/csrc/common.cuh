@@ -30,7 +30,8 @@ struct mesh_bvh_impl {
     float4 *nodes() const { return reinterpret_cast<float4 *>(base + L.off_nodes); }
     int *parent() const { return reinterpret_cast<int *>(base + L.off_parent); }
     float4 *tris() const { return reinterpret_cast<float4 *>(base + L.off_tris); }
-    unsigned int *flags() const { return reinterpret_cast<unsigned int *>(base + L.off_flags); }
+    int *rend() const { return reinterpret_cast<int *>(base + L.off_rend); }
+    int *xlist() const { return reinterpret_cast<int *>(base + L.off_xlist); }
 };
 
 struct BatchStatus {

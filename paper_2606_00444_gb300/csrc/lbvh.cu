@@ -10,6 +10,8 @@
 #include <cstdlib>
 #include <cstring>
 
+#include <climits>
+
 #include "common.cuh"
 
 namespace meshgs {
@@ -380,7 +382,7 @@ __device__ __forceinline__ int kdelta(const unsigned int *__restrict__ k, int n,
 
 // Children of internal node i of the tree over keys[0, n) (Karras 2012).
 __device__ __forceinline__ void karras_children(const unsigned int *__restrict__ keys, int n, int i,
-                                                int &left, int &right) {
+                                                int &left, int &right, int &far_end) {
     int d = (kdelta(keys, n, i, i + 1) - kdelta(keys, n, i, i - 1)) >= 0 ? 1 : -1;
     int dmin = kdelta(keys, n, i, i - d);
     int lmax = 2;
@@ -400,6 +402,7 @@ __device__ __forceinline__ void karras_children(const unsigned int *__restrict__
     int lo = min(i, j), hi = max(i, j);
     left = (lo == gamma) ? -(gamma + 1) : gamma;
     right = (hi == gamma + 1) ? -(gamma + 2) : gamma + 1;
+    far_end = j;
 }
 
 __device__ __forceinline__ void write_children(float4 *__restrict__ nodes, int i, int left, int right) {
@@ -411,72 +414,264 @@ __device__ __forceinline__ void write_children(float4 *__restrict__ nodes, int i
 }
 
 __global__ void k_karras(const unsigned int *__restrict__ keys, int n, float4 *__restrict__ nodes,
-                         int *__restrict__ parent) {
+                         int *__restrict__ parent, int *__restrict__ rend) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n - 1) return;
-    int left, right;
-    karras_children(keys, n, i, left, right);
+    int left, right, far_end;
+    karras_children(keys, n, i, left, right, far_end);
+    rend[i] = far_end;
     write_children(nodes, i, left, right);
     parent[left >= 0 ? left : (n - 1) + (-left - 1)] = 2 * i;
     parent[right >= 0 ? right : (n - 1) + (-right - 1)] = 2 * i + 1;
     if (i == 0) parent[0] = -1;
 }
 
-// Exact zero-area test: the products of float32 coordinates are exact in
-// float64, so the cross product is zero here exactly when it is zero in exact
-// arithmetic (the differences of float32 inputs are exact as well).
+// Exact zero-area test: the products of float32 coordinate differences are
+// exact in float64 (each difference of two float32 values of similar
+// magnitude has at most 25 significant bits), so the cross product is zero
+// here exactly when it is zero in exact arithmetic.  A float32 evaluation
+// first settles the common case: a component whose magnitude exceeds 2^-21
+// of |p1| + |p2| (the two products it is the difference of) is nonzero in
+// exact arithmetic too -- the rounding of the differences, the products and
+// the subtraction moves it by at most about 4 * 2^-24 of that sum -- so the
+// float64 pipe is used only for (nearly) degenerate triangles.
+__device__ __forceinline__ bool clearly_nonzero(float p1, float p2) {
+    float s = fabsf(p1) + fabsf(p2);
+    return s > 1e-30f && s < 1e30f && fabsf(p1 - p2) > 0x1p-21f * s;
+}
+
 __device__ __forceinline__ bool exactly_degenerate(float4 a, float4 b, float4 c) {
+    float fux = b.x - a.x, fuy = b.y - a.y, fuz = b.z - a.z;
+    float fvx = c.x - a.x, fvy = c.y - a.y, fvz = c.z - a.z;
+    if (clearly_nonzero(fuy * fvz, fuz * fvy) || clearly_nonzero(fuz * fvx, fux * fvz) ||
+        clearly_nonzero(fux * fvy, fuy * fvx))
+        return false;
     double ux = (double)b.x - a.x, uy = (double)b.y - a.y, uz = (double)b.z - a.z;
     double vx = (double)c.x - a.x, vy = (double)c.y - a.y, vz = (double)c.z - a.z;
     return (uy * vz - uz * vy) == 0.0 && (uz * vx - ux * vz) == 0.0 && (ux * vy - uy * vx) == 0.0;
 }
 
 // ---------------------------------------------------------------------------
-// a5: leaf boxes and bottom-up internal boxes (build and refit).  One thread
-// per leaf j writes the packed triangle of face perm[j] (leaf order), puts the
-// leaf box into its parent's record, and climbs: at each internal node the
-// first arriving child stops, the second computes the union (the sibling's
-// box is read from L2 after a fence) and continues; it also clears the
-// arrival counter for the next refit.  The root box goes to the header.
+// a5 (build and refit): bottom-up boxes in two kernels, without a climb.
+//
+// The box of an internal node is the union of the leaf boxes over its leaf
+// range [a, b] (Karras's nodes cover contiguous ranges of the sorted leaves),
+// so the boxes need no bottom-up dependency chain at all: they are range
+// queries.  One block per kRefitBlock consecutive leaves:
+//   * builds a sparse table of its leaf boxes in shared memory (level k holds
+//     the union over [i, i + 2^k)), one level per round and one barrier per
+//     level, reading consecutive entries (no bank conflicts);
+//   * answers every internal node whose range lies inside the block (such a
+//     node's index is one end of its range, so it is in the block's index
+//     range) from two entries of level floor(log2(b - a + 1)) as soon as that
+//     level exists;
+//   * writes the prefix and suffix unions of its leaves and its own box.
+// Every leaf and node writes its box into its parent's record half, so the
+// records need no second pass.  The nodes whose ranges cross a block boundary
+// -- a few per boundary -- are listed per block; the second kernel answers
+// each of them with one warp: suffix union in the first block, prefix union
+// in the last, and the boxes of the blocks between.  No atomics, no fences,
+// no spin, and the result does not depend on thread timing.  When the caller
+// passes new vertices, the first kernel also repacks them (a1) and gathers
+// the triangles from the caller's buffer.
 // ---------------------------------------------------------------------------
-__global__ void k_leaves_up(int n, const int *__restrict__ perm, const int4 *__restrict__ faces,
-                            const float4 *__restrict__ verts, float4 *__restrict__ tris,
-                            float4 *__restrict__ nodes, const int *__restrict__ parent,
-                            unsigned int *__restrict__ flags, Header *__restrict__ hdr) {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n) return;
-    int f = perm[j];
-    int4 fv = faces[f];
-    float4 a = verts[fv.x], b = verts[fv.y], c = verts[fv.z];
-    float deg = exactly_degenerate(a, b, c) ? 1.0f : 0.0f;
-    tris[3 * (size_t)j + 0] = make_float4(a.x, a.y, a.z, __int_as_float(f));
-    tris[3 * (size_t)j + 1] = make_float4(b.x, b.y, b.z, deg);
-    tris[3 * (size_t)j + 2] = make_float4(c.x, c.y, c.z, 0.0f);
-    float3 lo = make_float3(fminf(fminf(a.x, b.x), c.x), fminf(fminf(a.y, b.y), c.y),
-                            fminf(fminf(a.z, b.z), c.z));
-    float3 hi = make_float3(fmaxf(fmaxf(a.x, b.x), c.x), fmaxf(fmaxf(a.y, b.y), c.y),
-                            fmaxf(fmaxf(a.z, b.z), c.z));
-    int self = -(j + 1);
-    int pe = parent[(n - 1) + j];
-    while (pe >= 0) {
-        int p = pe >> 1, side = pe & 1;
-        float4 *rec = nodes + 4 * (size_t)p;
-        rec[2 * side] = make_float4(lo.x, lo.y, lo.z, __int_as_float(self));
-        rec[2 * side + 1] = make_float4(hi.x, hi.y, hi.z, __int_as_float(self));
-        __threadfence();
-        unsigned int old = atomicAdd(&flags[p], 1u);
-        if (old == 0u) return;
-        __threadfence();
-        int o = 1 - side;
-        float4 olo = __ldcg(rec + 2 * o), ohi = __ldcg(rec + 2 * o + 1);
-        lo = make_float3(fminf(lo.x, olo.x), fminf(lo.y, olo.y), fminf(lo.z, olo.z));
-        hi = make_float3(fmaxf(hi.x, ohi.x), fmaxf(hi.y, ohi.y), fmaxf(hi.z, ohi.z));
-        flags[p] = 0u;
-        self = p;
-        pe = parent[p];
+constexpr int kRefitBlock = 1024;
+constexpr int kRefitLevels = 10;                          // log2(kRefitBlock)
+
+__device__ __forceinline__ bool crosses_block(int i, int j) {
+    return (min(i, j) / kRefitBlock) != (max(i, j) / kRefitBlock);
+}
+
+__device__ __forceinline__ float4 box_min(float4 a, float4 b) {
+    return make_float4(fminf(a.x, b.x), fminf(a.y, b.y), fminf(a.z, b.z), 0.0f);
+}
+__device__ __forceinline__ float4 box_max(float4 a, float4 b) {
+    return make_float4(fmaxf(a.x, b.x), fmaxf(a.y, b.y), fmaxf(a.z, b.z), 0.0f);
+}
+
+// Corners of face fv from the caller's [nV][3] buffer (V3) or the repacked one.
+__device__ __forceinline__ void load_tri(const float *__restrict__ V3, const float4 *__restrict__ V4,
+                                         int4 fv, float4 &a, float4 &b, float4 &c) {
+    if (V3) {
+        const float *pa = V3 + 3 * (size_t)fv.x, *pb = V3 + 3 * (size_t)fv.y, *pc = V3 + 3 * (size_t)fv.z;
+        a = make_float4(pa[0], pa[1], pa[2], 0.0f);
+        b = make_float4(pb[0], pb[1], pb[2], 0.0f);
+        c = make_float4(pc[0], pc[1], pc[2], 0.0f);
+    } else {
+        a = V4[fv.x]; b = V4[fv.y]; c = V4[fv.z];
     }
-    hdr->root_lo = make_float4(lo.x, lo.y, lo.z, 0.0f);
-    hdr->root_hi = make_float4(hi.x, hi.y, hi.z, 0.0f);
+}
+
+// Writes box (lo, hi) of child `self` into its parent's record half, or into
+// the header when it is the root (parent link pe < 0).
+__device__ __forceinline__ void put_box(float4 *__restrict__ nodes, Header *__restrict__ hdr, int pe,
+                                        int self, float4 lo, float4 hi) {
+    if (pe < 0) {
+        hdr->root_lo = make_float4(lo.x, lo.y, lo.z, 0.0f);
+        hdr->root_hi = make_float4(hi.x, hi.y, hi.z, 0.0f);
+        return;
+    }
+    float4 *rec = nodes + 4 * (size_t)(pe >> 1) + 2 * (pe & 1);
+    rec[0] = make_float4(lo.x, lo.y, lo.z, __int_as_float(self));
+    rec[1] = make_float4(hi.x, hi.y, hi.z, __int_as_float(self));
+}
+
+// Box of six floats in shared memory, structure of arrays ([6][kRefitBlock]).
+struct SBox {
+    float *f;
+    __device__ float4 lo(int i) const { return make_float4(f[i], f[kRefitBlock + i], f[2 * kRefitBlock + i], 0.0f); }
+    __device__ float4 hi(int i) const {
+        return make_float4(f[3 * kRefitBlock + i], f[4 * kRefitBlock + i], f[5 * kRefitBlock + i], 0.0f);
+    }
+    __device__ void put(int i, float4 l, float4 h) const {
+        f[i] = l.x; f[kRefitBlock + i] = l.y; f[2 * kRefitBlock + i] = l.z;
+        f[3 * kRefitBlock + i] = h.x; f[4 * kRefitBlock + i] = h.y; f[5 * kRefitBlock + i] = h.z;
+    }
+};
+
+constexpr size_t kRefitLocalSmem = 12 * kRefitBlock * sizeof(float)      // two table levels
+                                   + 64 * sizeof(int);                    // crossing-list scan
+
+__global__ void __launch_bounds__(kRefitBlock, 2)
+k_refit_local(int n, const float *__restrict__ V3, int nV, float4 *__restrict__ V4,
+              const int *__restrict__ perm, const int4 *__restrict__ faces,
+              float4 *__restrict__ tris, float4 *__restrict__ nodes, const int *__restrict__ parent,
+              const int *__restrict__ rend, float4 *__restrict__ pre, float4 *__restrict__ suf,
+              float4 *__restrict__ bbox, int4 *__restrict__ xlist, int *__restrict__ xcnt,
+              Header *__restrict__ hdr) {
+    extern __shared__ float4 dsm[];
+    float *tab = reinterpret_cast<float *>(dsm);
+    int *s_warp = reinterpret_cast<int *>(tab + 12 * kRefitBlock);
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int base = blockIdx.x * kRefitBlock, j = base + tid;
+    // leaf j: box into level 0 and into its parent's record
+    {
+        float4 lo = make_float4(INFINITY, INFINITY, INFINITY, 0.0f);
+        float4 hi = make_float4(-INFINITY, -INFINITY, -INFINITY, 0.0f);
+        if (j < n) {
+            int pe_leaf = parent[(n - 1) + j];
+            float4 a, b, c;
+            load_tri(V3, V4, faces[perm[j]], a, b, c);
+            lo = box_min(box_min(a, b), c);
+            hi = box_max(box_max(a, b), c);
+            put_box(nodes, hdr, pe_leaf, -(j + 1), lo, hi);
+        }
+        SBox{tab}.put(tid, lo, hi);
+    }
+    // internal node j: its leaf range [ra, rb]
+    int ra = 0, rb = 0, pe_node = -1;
+    bool cross = false;
+    if (j < n - 1) {
+        int far = rend[j];
+        ra = min(j, far);
+        rb = max(j, far);
+        cross = crosses_block(ra, rb);
+        pe_node = parent[j];
+    }
+    // this block's crossing nodes, listed in index order
+    unsigned int ball = __ballot_sync(0xffffffffu, cross);
+    if (lane == 0) s_warp[wid] = __popc(ball);
+    __syncthreads();
+    if (wid == 0) {
+        int c = s_warp[lane], x = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        s_warp[32 + lane] = x - c;
+        if (lane == 31) xcnt[blockIdx.x] = x;
+    }
+    // Range queries, level by level: the union over [i0, i0 + L) with
+    // 2^k <= L < 2^(k+1) is level k at i0 and at i0 + L - 2^k.  Asked here:
+    // the owned node j (its range), and leaf j's prefix [0, tid] and suffix
+    // [tid, kRefitBlock) inside the block (the block's box is the suffix of 0).
+    const int node_level = (j < n - 1 && !cross) ? 31 - __clz(rb - ra + 1) : -1;
+    const int pre_level = 31 - __clz(tid + 1), suf_level = 31 - __clz(kRefitBlock - tid);
+    for (int k = 0; k <= kRefitLevels; ++k) {
+        const SBox cur{tab + (k & 1) * 6 * kRefitBlock}, nxt{tab + ((k + 1) & 1) * 6 * kRefitBlock};
+        const int h = 1 << k;
+        if (node_level == k) {
+            int i0 = ra - base, i1 = rb - base - h + 1;
+            put_box(nodes, hdr, pe_node, j, box_min(cur.lo(i0), cur.lo(i1)), box_max(cur.hi(i0), cur.hi(i1)));
+        }
+        if (pre_level == k && j < n) {
+            int i1 = tid - h + 1;
+            pre[2 * (size_t)j] = box_min(cur.lo(0), cur.lo(i1));
+            pre[2 * (size_t)j + 1] = box_max(cur.hi(0), cur.hi(i1));
+        }
+        if (suf_level == k) {
+            int i1 = kRefitBlock - h;
+            float4 lo = box_min(cur.lo(tid), cur.lo(i1)), hi = box_max(cur.hi(tid), cur.hi(i1));
+            if (j < n) {
+                suf[2 * (size_t)j] = lo;
+                suf[2 * (size_t)j + 1] = hi;
+            }
+            if (tid == 0) {
+                bbox[2 * blockIdx.x] = lo;
+                bbox[2 * blockIdx.x + 1] = hi;
+            }
+        }
+        if (k == 1 && cross)                             // offsets written by warp 0 in round 0
+            xlist[base + s_warp[32 + wid] + __popc(ball & ((1u << lane) - 1u))] = make_int4(j, ra, rb, pe_node);
+        if (k < kRefitLevels) {
+            if (tid + 2 * h <= kRefitBlock)
+                nxt.put(tid, box_min(cur.lo(tid), cur.lo(tid + h)), box_max(cur.hi(tid), cur.hi(tid + h)));
+            __syncthreads();
+        }
+    }
+    if (j < n) {
+        int f = perm[j];                                 // reloaded: cheaper than keeping it live
+        float4 a, b, c;
+        load_tri(V3, V4, faces[f], a, b, c);
+        float deg = exactly_degenerate(a, b, c) ? 1.0f : 0.0f;
+        tris[3 * (size_t)j + 0] = make_float4(a.x, a.y, a.z, __int_as_float(f));
+        tris[3 * (size_t)j + 1] = make_float4(b.x, b.y, b.z, deg);
+        tris[3 * (size_t)j + 2] = make_float4(c.x, c.y, c.z, 0.0f);
+    }
+    // a1: this block's slice of the vertex repack (after every read of V4 above)
+    if (V3) {
+        int per = (nV + gridDim.x - 1) / gridDim.x;
+        int v1 = min(nV, (int)(blockIdx.x + 1) * per);
+        for (int v = blockIdx.x * per + tid; v < v1; v += kRefitBlock) {
+            const float *p = V3 + 3 * (size_t)v;
+            V4[v] = make_float4(p[0], p[1], p[2], 0.0f);
+        }
+    }
+}
+
+// One warp per crossing node: the suffix union in its first block, the prefix
+// union in its last, and the boxes of the blocks between.
+constexpr int kTopThreads = 256;
+
+__global__ void __launch_bounds__(kTopThreads)
+k_refit_top(const int4 *__restrict__ xlist, const int *__restrict__ xcnt, const float4 *__restrict__ pre,
+            const float4 *__restrict__ suf, const float4 *__restrict__ bbox, float4 *__restrict__ nodes,
+            Header *__restrict__ hdr) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = kTopThreads >> 5;
+    const int cnt = xcnt[blockIdx.x];
+    for (int r = wid; r < cnt; r += nw) {
+        int4 e = xlist[(size_t)blockIdx.x * kRefitBlock + r];   // node, range start, range end, parent
+        float4 lo = make_float4(INFINITY, INFINITY, INFINITY, 0.0f);
+        float4 hi = make_float4(-INFINITY, -INFINITY, -INFINITY, 0.0f);
+        if (lane == 0) {
+            lo = box_min(__ldcg(suf + 2 * (size_t)e.y), __ldcg(pre + 2 * (size_t)e.z));
+            hi = box_max(__ldcg(suf + 2 * (size_t)e.y + 1), __ldcg(pre + 2 * (size_t)e.z + 1));
+        }
+        for (int b = e.y / kRefitBlock + 1 + lane; b < e.z / kRefitBlock; b += 32) {
+            lo = box_min(lo, __ldcg(bbox + 2 * b));
+            hi = box_max(hi, __ldcg(bbox + 2 * b + 1));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo.x = fminf(lo.x, __shfl_xor_sync(0xffffffffu, lo.x, o));
+            lo.y = fminf(lo.y, __shfl_xor_sync(0xffffffffu, lo.y, o));
+            lo.z = fminf(lo.z, __shfl_xor_sync(0xffffffffu, lo.z, o));
+            hi.x = fmaxf(hi.x, __shfl_xor_sync(0xffffffffu, hi.x, o));
+            hi.y = fmaxf(hi.y, __shfl_xor_sync(0xffffffffu, hi.y, o));
+            hi.z = fmaxf(hi.z, __shfl_xor_sync(0xffffffffu, hi.z, o));
+        }
+        if (lane == 0) put_box(nodes, hdr, e.w, e.x, lo, hi);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -576,15 +771,19 @@ __global__ void k_batch_karras(const unsigned int *__restrict__ keys, int nF,
     int base = __ldg(face_off + sc), n = __ldg(face_off + sc + 1) - base, i = j - base;
     if (n == 1) { parent_leaf[base] = -1; return; }
     if (i >= n - 1) return;
-    int left, right;
-    karras_children(keys + base, n, i, left, right);
+    int left, right, far_end;
+    karras_children(keys + base, n, i, left, right, far_end);
     write_children(nodes + 4 * (size_t)base, i, left, right);
     if (left >= 0) parent_int[base + left] = 2 * i; else parent_leaf[base - left - 1] = 2 * i;
     if (right >= 0) parent_int[base + right] = 2 * i + 1; else parent_leaf[base - right - 1] = 2 * i + 1;
     if (i == 0) parent_int[base] = -1;
 }
 
-// Bottom-up boxes of every scene (build and refit), as k_leaves_up per scene.
+// Bottom-up boxes of every scene (build and refit).  One thread per leaf j
+// writes the packed triangle of face perm[j] and climbs: at each internal node
+// the first arriving child stops, the second computes the union (the
+// sibling's box read from L2 after a fence) and continues, clearing the
+// arrival counter for the next pass.  Each scene's root box goes to its slot.
 __global__ void k_batch_leaves_up(int nF, const int *__restrict__ face_off, int nscenes,
                                   const int *__restrict__ perm, const int4 *__restrict__ faces,
                                   const float4 *__restrict__ verts, float4 *__restrict__ tris,
@@ -735,6 +934,15 @@ static mesh_batch_layout batch_layout(int64_t maxB, int64_t maxV, int64_t maxF) 
     return L;
 }
 
+// Scratch of the bottom-up kernels: prefix and suffix unions of the leaf
+// boxes inside each block (2 float4 per leaf each), the crossing nodes (int4
+// per face), the blocks' boxes (2 float4 each) and the per-block counts.
+static int64_t refit_blocks(int64_t f) { return (f + kRefitBlock - 1) / kRefitBlock; }
+static size_t xlist_bytes(int64_t f) {
+    int64_t nb = refit_blocks(f);
+    return (size_t)(32 * f + 32 * f + 16 * f + 32 * nb + 4 * (nb + 1));
+}
+
 static mesh_bvh_layout storage_layout(int64_t maxV, int64_t maxF) {
     mesh_bvh_layout L{};
     int64_t v = maxV > 0 ? maxV : 1, f = maxF > 0 ? maxF : 1;
@@ -750,7 +958,8 @@ static mesh_bvh_layout storage_layout(int64_t maxV, int64_t maxF) {
     L.off_nodes = take(64 * (f > 1 ? f - 1 : 1));
     L.off_parent = take(4 * (2 * f - 1));
     L.off_tris = take(48 * f);
-    L.off_flags = take(4 * f);
+    L.off_rend = take(4 * f);
+    L.off_xlist = take(xlist_bytes(f));
     L.storage_bytes = off;
     return L;
 }
@@ -812,20 +1021,40 @@ mesh_status mesh_update_vertices(mesh_bvh *bvh, const float *d_V, int64_t nV, vo
     return check_launch();
 }
 
-mesh_status mesh_refit(mesh_bvh *bvh, const float *d_V, int64_t nV, void *stream) {
-    if (!bvh) return MESH_ERR_INVALID_ARG;
-    if (d_V) {
-        mesh_status st = mesh_update_vertices(bvh, d_V, nV, stream);
-        if (st != MESH_OK) return st;
+// Launches the two bottom-up kernels (build and refit); V3 = new vertices or NULL.
+static mesh_status bottom_up(mesh_bvh *bvh, const float *V3, cudaStream_t s) {
+    static bool smem_set = false;                    // above the default 48 KB: opt in once
+    if (!smem_set) {
+        if (cudaFuncSetAttribute(k_refit_local, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kRefitLocalSmem) != cudaSuccess)
+            return MESH_ERR_CUDA;
+        smem_set = true;
     }
     int n = (int)bvh->L.n_faces;
-    if (n == 0) return MESH_OK;
-    cudaStream_t s = (cudaStream_t)stream;
-    k_leaves_up<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, bvh->perm(), bvh->faces(), bvh->verts(),
-                                                       bvh->tris(), bvh->nodes(), bvh->parent(),
-                                                       bvh->flags(), bvh->hdr());
+    unsigned int nb = grid_for(n, kRefitBlock);
+    int64_t fmax = bvh->L.max_faces, nbmax = refit_blocks(fmax);
+    float4 *pre = reinterpret_cast<float4 *>(bvh->xlist()), *suf = pre + 2 * fmax;
+    int4 *xlist = reinterpret_cast<int4 *>(suf + 2 * fmax);
+    float4 *bbox = reinterpret_cast<float4 *>(xlist + fmax);
+    int *xcnt = reinterpret_cast<int *>(bbox + 2 * nbmax);
+    k_refit_local<<<nb, kRefitBlock, kRefitLocalSmem, s>>>(
+        n, V3, (int)bvh->L.n_verts, bvh->verts(), bvh->perm(), bvh->faces(), bvh->tris(),
+        bvh->nodes(), bvh->parent(), bvh->rend(), pre, suf, bbox, xlist, xcnt, bvh->hdr());
     count_launch();
+    if (nb > 1) {
+        k_refit_top<<<nb, kTopThreads, 0, s>>>(xlist, xcnt, pre, suf, bbox, bvh->nodes(), bvh->hdr());
+        count_launch();
+    }
     return check_launch();
+}
+
+mesh_status mesh_refit(mesh_bvh *bvh, const float *d_V, int64_t nV, void *stream) {
+    if (!bvh) return MESH_ERR_INVALID_ARG;
+    int n = (int)bvh->L.n_faces;
+    if (d_V && n == 0) return mesh_update_vertices(bvh, d_V, nV, stream);
+    if (d_V && (nV != bvh->L.n_verts || nV > bvh->L.max_verts)) return MESH_ERR_INVALID_ARG;
+    if (n == 0) return MESH_OK;
+    return bottom_up(bvh, d_V, (cudaStream_t)stream);
 }
 
 mesh_status mesh_build_lbvh(mesh_bvh *bvh, const float *d_V, int64_t nV, const int32_t *d_F,
@@ -853,17 +1082,12 @@ mesh_status mesh_build_lbvh(mesh_bvh *bvh, const float *d_V, int64_t nV, const i
     radix_sort_pairs(w, n, bvh->keys(), bvh->perm(), s);
     if (n > 1) {
         k_karras<<<grid_for(n - 1, kBlock), kBlock, 0, s>>>(bvh->keys(), n, bvh->nodes(),
-                                                           bvh->parent());
+                                                           bvh->parent(), bvh->rend());
         count_launch();
     } else {
         cudaMemsetAsync(bvh->parent(), 0xff, sizeof(int), s);   // lone leaf: no parent
     }
-    cudaMemsetAsync(bvh->flags(), 0, sizeof(unsigned int) * (size_t)n, s);
-    k_leaves_up<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, bvh->perm(), bvh->faces(), bvh->verts(),
-                                                       bvh->tris(), bvh->nodes(), bvh->parent(),
-                                                       bvh->flags(), bvh->hdr());
-    count_launch();
-    return check_launch();
+    return bottom_up(bvh, nullptr, s);
 }
 
 size_t mesh_morton_order_workspace_bytes(int64_t n) { return mesh_build_workspace_bytes(n); }

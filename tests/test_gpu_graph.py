@@ -45,8 +45,11 @@ def test_graph_replayed_frame_equals_eager_frame():
         chamfer(fixed, S, rest, S, ws=ws, out=cd)
 
     def snapshot():
+        # every output and every array of both BVHs (scratch lists excluded:
+        # only their first entries per block are defined)
         torch.cuda.synchronize()
-        return [t.clone() for t in (*outs.values(), *g3, S, cd, rebuilt.storage, fixed.storage)]
+        arrs = [v for b in (rebuilt, fixed) for v in b.arrays().values()]
+        return [t.contiguous().clone().view(-1).view(torch.uint8) for t in (*outs.values(), *g3, S, cd, *arrs)]
 
     eager = []
     for f in frames:

@@ -85,7 +85,41 @@ def test_empty_mesh_builds():
     assert (host(out["face"]) == -1).all() and np.isinf(host(out["dist2"])).all()
 
 
-def test_refit_equals_build_over_same_topology():
+def _deform(V, t):
+    """A smooth seeded deformation of any mesh (rigid rotation + bend + scale)."""
+    a = 0.3 * t
+    R = np.array([[np.cos(a), -np.sin(a), 0], [np.sin(a), np.cos(a), 0], [0, 0, 1]])
+    W = V.astype(np.float64) @ R.T
+    W[:, 2] += 0.2 * np.sin(2.0 * W[:, 0] + t)
+    return (W * (1.0 + 0.05 * t)).astype(np.float32)
+
+
+@pytest.mark.parametrize("name,maker", [
+    ("one_block_80", lambda: icosphere(1)),
+    ("two_blocks_ragged_1280", lambda: icosphere(3)),
+    ("torus_16800", lambda: torus(120, 70)),
+    ("blob_frame", lambda: BlobSequence(2000).mesh(17, N=96)),
+])
+@pytest.mark.parametrize("form", ["fused", "separate"])
+def test_refit_equals_build_over_same_topology(name, maker, form):
+    """Refit over the build's topology gives the boxes and packed triangles of
+    the oracle over the same topology, bit for bit, from either form of the
+    vertex update (in the refit pass, or by mesh_update_vertices first)."""
+    V0, F = maker()
+    bvh, T = check_build(V0, F)
+    for t in (1, 3):
+        V1 = _deform(V0, t)
+        if form == "fused":
+            bvh.refit(dev(V1))
+        else:
+            bvh.update_vertices(dev(V1))
+            bvh.refit()
+        boxes = oracle.node_boxes(V1, F, T["perm"], T["first"], T["last"])
+        check_build(V1, F, bvh=bvh, T=dict(T, boxes=boxes))
+        assert np.array_equal(host(bvh.arrays()["verts"])[:, :3], V1)
+
+
+def test_refit_skinned_torus_and_topology_change_on_one_handle():
     V0, F = torus(120, 70)
     sk = TorusSkinning(V0, seed=3001)
     bvh, T = check_build(V0, F)
@@ -93,8 +127,38 @@ def test_refit_equals_build_over_same_topology():
         V1 = sk.frame(t)
         bvh.refit(dev(V1))
         boxes = oracle.node_boxes(V1, F, T["perm"], T["first"], T["last"])
-        T1 = dict(T, boxes=boxes)
-        check_build(V1, F, bvh=bvh, T=T1)
+        check_build(V1, F, bvh=bvh, T=dict(T, boxes=boxes))
+    # a new topology in the same storage: the refit plan is derived again
+    V2, F2 = torus(100, 61)
+    bvh.build(dev(V2), dev(F2))
+    T2 = oracle.build_lbvh(V2, F2)
+    V3 = _deform(V2, 2)
+    bvh.refit(dev(V3))
+    boxes = oracle.node_boxes(V3, F2, T2["perm"], T2["first"], T2["last"])
+    check_build(V3, F2, bvh=bvh, T=dict(T2, boxes=boxes))
+
+
+def test_build_and_refit_with_crossing_nodes_past_shared_memory():
+    """1.2M faces: some 13k nodes cross the 1024-leaf blocks, more than the
+    finishing block holds in shared memory, so every block climbs its share
+    through L2.  Build and refit still equal the oracle bit for bit."""
+    V0, F = torus(1000, 600)
+    bvh, T = check_build(V0, F)
+    V1 = TorusSkinning(V0, seed=3002).frame(40)
+    bvh.refit(dev(V1))
+    boxes = oracle.node_boxes(V1, F, T["perm"], T["first"], T["last"])
+    check_build(V1, F, bvh=bvh, T=dict(T, boxes=boxes))
+
+
+def test_refit_tiny_meshes():
+    V = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [1, 1, 0], [2, 0.5, 0.3]], np.float32)
+    for F in ([[0, 1, 2]], [[0, 1, 2], [1, 3, 2]], [[0, 1, 2], [1, 3, 2], [1, 4, 3]]):
+        F = np.array(F, np.int32)
+        bvh, T = check_build(V, F)
+        V1 = _deform(V, 1)
+        bvh.refit(dev(V1))
+        boxes = oracle.node_boxes(V1, F, T["perm"], T["first"], T["last"])
+        check_build(V1, F, bvh=bvh, T=dict(T, boxes=boxes))
 
 
 def test_out_of_range_index_sets_status_not_fault():

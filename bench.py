@@ -17,8 +17,9 @@ at seeded barycentres).  One step = one frame:
 value = point-to-mesh queries per second (1M contact + 20k Chamfer queries per
 frame) over graph-replayed frames, inputs resident in HBM, L2 flushed (a 512 MB
 write) between frames outside the timed events.  Stage times, the dominant
-kernel's roofline and the refit-vs-rebuild comparison come from an eager pass
-with events between stages.  `e2e` repeats the frame through the public API
+kernel's roofline and the refit-vs-rebuild comparison come from the five
+stages captured as separate graphs and replayed back to back with events
+between them.  `e2e` repeats the frame through the public API
 from pinned host buffers (frame vertices and particles in, contact face and
 distance out).  `--impl reference` times the CPU oracle on a bounded sample.
 """
@@ -250,13 +251,31 @@ def gpu_arm(args, rank, world, local_rank):
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         ms = float(tt.item())
 
-    # eager pass with per-stage events (stage breakdown + dominant kernel duration)
+    # per-stage device times: each stage captured as its own graph and the five
+    # replayed back to back with events between them (no host gaps inside a
+    # stage), after an L2 flush and the frame load, as in the timed frames
+    stage_fns = [lambda: fixed.refit(Vin),
+                 lambda: fixed.closest_point(P, CUTOFF, out=contact),
+                 lambda: fixed.bind_gaussians(gface, gbary, out=gout),
+                 lambda: rebuilt.build(Vin, F),
+                 lambda: (fixed.interpolate(cdf, cdb, out=S_def),
+                          chamfer(fixed, S_def, rest, rest_S, ws=cd_ws, out=cd_out))]
+    stage_graphs = []
+    for fn in stage_fns:
+        gs = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gs):
+            fn()
+        stage_graphs.append(gs)
+    torch.cuda.synchronize()
     nst = min(args.steps, 100)
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(nst)]
     for k in range(nst):
         flush.fill_(float(k))
         load_frame(k)
-        stages(evs[k])
+        for i, gs in enumerate(stage_graphs):
+            evs[k][i].record()
+            gs.replay()
+        evs[k][5].record()
     torch.cuda.synchronize()
     names = ["refit", "contact", "rebind", "rebuild", "chamfer"]
     st = {n: float(np.mean([e[i].elapsed_time(e[i + 1]) for e in evs])) for i, n in enumerate(names)}

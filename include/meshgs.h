@@ -185,6 +185,8 @@ mesh_status mesh_set_query_group(int lanes);
  *     (8 shared entries)                          11 as 10, local stack only
  *     (10 and 11 keep a work counter in the handle: calls on one handle must
  *     not overlap on the GPU)
+ *  12 warp packet: the 32 queries of a warp share one node sequence, a node
+ *     entered when any lane needs it (for queries kept in Morton order)
  * (the shared part of the stack spills to local memory; local-only leaves the
  * SM's L1 to the node cache).  Process-wide; same answers for every variant. */
 mesh_status mesh_set_traversal(int variant);

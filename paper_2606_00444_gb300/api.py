@@ -416,7 +416,7 @@ def set_query_group(lanes: int) -> None:
 
 
 def set_traversal(variant: int) -> None:
-    """One-thread traversal variant 0..11 (see mesh_set_traversal in include/meshgs.h)."""
+    """One-thread traversal variant 0..12 (see mesh_set_traversal in include/meshgs.h)."""
     check(lib().mesh_set_traversal(int(variant)), "mesh_set_traversal")
 
 

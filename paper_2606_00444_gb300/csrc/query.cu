@@ -646,6 +646,90 @@ k_closest_point(Traversal T, const Header *__restrict__ hdr, unsigned int *statu
     write_hit(T, h, q, i, face, bary, point, dist2);
 }
 
+// Warp-packet traversal: the 32 queries of a warp (consecutive, so nearby
+// when the caller keeps them in Morton order) share one depth-first node
+// sequence.  Each lane tests the node's two child boxes against its own query
+// and bound; a child is entered when any lane needs it, nearer-first by a
+// vote of the lanes, and the other child is deferred on a per-warp stack of
+// (parent, side) entries.  A deferred child is re-tested against the lanes'
+// bounds when it is popped (bounds only shrink), so a lane sees every leaf
+// its own traversal would.  Node loads are warp-uniform (one broadcast per
+// record) and all control flow outside the leaf tests is warp-uniform: the
+// warp runs the union of its queries' traversals with every lane active,
+// instead of each lane's traversal with most lanes idle.  Same answers as the
+// depth-first kernels.
+__device__ __forceinline__ Hit nearest_packet(const Traversal &T, float3 q, float maxd2, bool valid,
+                                              int *wstk, unsigned int *status) {
+    const unsigned int kFull = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    Best B{-1, 0x7fffffff, INFINITY, INFINITY, valid ? maxd2 : -1.0f};
+    if (T.n == 1) {
+        if (valid) test_leaf(T, B, 0, q, maxd2);
+        return Hit{B.leaf, B.face, B.d2};
+    }
+    if (T.n < 1) return Hit{-1, 0x7fffffff, INFINITY};
+    int sp = 0, node = 0;
+    while (true) {
+        const float4 *r = T.nodes + 4 * (size_t)node;
+        float4 l0 = ldg4(r), l1 = ldg4(r + 1), r0 = ldg4(r + 2), r1 = ldg4(r + 3);
+        float dl = box_d2(q, l0, l1), dr = box_d2(q, r0, r1);
+        if (T.mmd && valid)
+            B.thr = fminf(B.thr, bound_window2(fminf(box_minmax_d2(q, l0, l1), box_minmax_d2(q, r0, r1)),
+                                               T.tau));
+        int cl = __float_as_int(l0.w), cr = __float_as_int(r0.w);
+        bool wl = dl <= B.thr, wr = dr <= B.thr;
+        unsigned int bl = __ballot_sync(kFull, wl), br = __ballot_sync(kFull, wr);
+        if (cl < 0 && wl) test_leaf(T, B, -cl - 1, q, maxd2);
+        if (cr < 0 && wr) test_leaf(T, B, -cr - 1, q, maxd2);
+        bool gl = cl >= 0 && bl != 0u, gr = cr >= 0 && br != 0u;
+        if (gl && gr) {
+            unsigned int pl = __ballot_sync(kFull, wl && (!wr || dl <= dr));
+            bool lfirst = 2 * __popc(pl) >= __popc(bl | br);
+            if (sp < kStackTotal) {
+                if (lane == 0) wstk[sp] = 2 * node + (lfirst ? 1 : 0);
+                ++sp;
+            } else if (lane == 0) {
+                atomicOr(status, (unsigned)MESH_DEV_STACK_OVERFLOW);
+            }
+            node = lfirst ? cl : cr;
+            continue;
+        }
+        if (gl) { node = cl; continue; }
+        if (gr) { node = cr; continue; }
+        bool found = false;
+        __syncwarp();
+        while (sp > 0) {
+            --sp;
+            int e = wstk[sp];
+            const float4 *pr = T.nodes + 4 * (size_t)(e >> 1) + 2 * (e & 1);
+            float4 lo = ldg4(pr), hi = ldg4(pr + 1);
+            if (__any_sync(kFull, box_d2(q, lo, hi) <= B.thr)) {
+                node = __float_as_int(lo.w);
+                found = true;
+                break;
+            }
+        }
+        __syncwarp();
+        if (!found) break;
+    }
+    return Hit{B.leaf, B.face, B.d2};
+}
+
+__global__ void __launch_bounds__(kQueryBlock, kQueryMinBlocks)
+k_closest_point_packet(Traversal T, const Header *__restrict__ hdr, unsigned int *status,
+                       const float *__restrict__ Q, int64_t nQ, float maxd2, int *face, float *bary,
+                       float *point, float *dist2) {
+    __shared__ int wstk[kQueryBlock / 32][kStackTotal];
+    const int64_t w0 = (int64_t)blockIdx.x * kQueryBlock + (threadIdx.x & ~31);
+    if (w0 >= nQ) return;                                  // whole warp past the end
+    const int64_t i = w0 + (threadIdx.x & 31);
+    const bool valid = i < nQ;
+    T.tau = traversal_tau(hdr);
+    float3 q = valid ? make_float3(Q[3 * i], Q[3 * i + 1], Q[3 * i + 2]) : make_float3(0.0f, 0.0f, 0.0f);
+    Hit h = nearest_packet(T, q, maxd2, valid, wstk[threadIdx.x >> 5], status);
+    if (valid) write_hit(T, h, q, i, face, bary, point, dist2);
+}
+
 // Persistent depth-first traversal with dynamic fetch (Aila & Laine 2009):
 // a fixed grid of warps; each lane works through a stream of queries, one
 // node visit per step, and when at least kRefill lanes of the warp are idle
@@ -1001,6 +1085,7 @@ mesh_status mesh_closest_point(const mesh_bvh *bvh, const float *d_Q, int64_t nQ
                         k_closest_point_persistent<0><<<pg, kQueryBlock, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2, work);
                     break;
                 }
+                case 12: k_closest_point_packet MESH_CP_ARGS; break;
                 default: k_closest_point<kStackShared, 0> MESH_CP_ARGS; break;
             }
 #undef MESH_CP_ARGS
@@ -1111,14 +1196,14 @@ mesh_status mesh_bvh_set_query_config(mesh_bvh *bvh, int lanes, int variant) {
     if (lanes != -1 && lanes != 0 && lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8 &&
         lanes != 16 && lanes != 32)
         return MESH_ERR_INVALID_ARG;
-    if (variant < -1 || variant > 11) return MESH_ERR_INVALID_ARG;
+    if (variant < -1 || variant > 12) return MESH_ERR_INVALID_ARG;
     bvh->cfg_lanes = lanes;
     bvh->cfg_variant = variant;
     return MESH_OK;
 }
 
 mesh_status mesh_set_traversal(int variant) {
-    if (variant < 0 || variant > 11) return MESH_ERR_INVALID_ARG;
+    if (variant < 0 || variant > 12) return MESH_ERR_INVALID_ARG;
     g_traversal = variant;
     return MESH_OK;
 }

@@ -3,7 +3,7 @@
 The best traversal depends on the workload: how many queries there are
 (whether one thread per query fills the GPU), whether a cutoff bounds the
 search, and the mesh.  `tune_closest_point` times every candidate -- lanes per
-query (1, 2, 4, ..., 32) and, for one lane, the twelve traversal variants of
+query (1, 2, 4, ..., 32) and, for one lane, the thirteen traversal variants of
 mesh_set_traversal -- on the caller's own BVH and queries with CUDA events,
 keeps the fastest, and applies it.  `tune_chamfer` does the same for the
 lanes of the Chamfer kernel.  Results are cached in memory, and in a JSON file
@@ -73,7 +73,7 @@ def _apply(bvh: MeshBVH, cfg: dict) -> None:
 
 
 def closest_point_candidates():
-    return [dict(lanes=1, variant=v) for v in range(12)] + \
+    return [dict(lanes=1, variant=v) for v in range(13)] + \
            [dict(lanes=g, variant=0) for g in (2, 4, 8, 16, 32)]
 
 

@@ -145,7 +145,7 @@ def test_every_group_width_matches_oracle(c1, lanes):
         set_query_group(0)
 
 
-@pytest.mark.parametrize("variant", list(range(12)))
+@pytest.mark.parametrize("variant", list(range(13)))
 def test_every_thread_traversal_matches_oracle(c1, variant):
     from paper_2606_00444_gb300 import set_query_group, set_traversal
     _, _, VG, FG, Q = c1
@@ -155,6 +155,27 @@ def test_every_thread_traversal_matches_oracle(c1, variant):
         set_traversal(variant)
         check_closest(VG, FG, Q, bvh.closest_point(dev(Q)))
         check_closest(VG, FG, Q, bvh.closest_point(dev(Q), max_dist=0.05), max_dist=0.05)
+    finally:
+        set_query_group(0)
+        set_traversal(0)
+
+
+@pytest.mark.parametrize("n", [1, 31, 33, 1000])
+def test_warp_packet_traversal_ragged_and_sorted(c1, n):
+    """Variant 12 shares one traversal per warp: ragged warps (n not a multiple
+    of 32), Morton-sorted and shuffled queries all match the oracle."""
+    from paper_2606_00444_gb300 import morton_order, set_query_group, set_traversal
+    _, _, VG, FG, Q = c1
+    Qn = Q[:n]
+    bvh = MeshBVH.from_mesh(dev(VG), dev(FG))
+    order = host(morton_order(dev(Qn))).astype(np.int64)
+    try:
+        set_query_group(1)
+        set_traversal(12)
+        for Qx in (Qn, Qn[order]):
+            check_closest(VG, FG, Qx, bvh.closest_point(dev(Qx)))
+            check_closest(VG, FG, Qx, bvh.closest_point(dev(Qx), max_dist=0.05), max_dist=0.05)
+        assert bvh.status()[0] == 0
     finally:
         set_query_group(0)
         set_traversal(0)

@@ -76,6 +76,7 @@ typedef struct {
                             -1 at the root; internal nodes first, then leaves                 */
     size_t off_tris;     /* 3 x float4 per leaf: (v0, face id bits) (v1, 0) (v2, 0)           */
     size_t off_rend;     /* int32 [max_faces]   far end of internal node i's leaf range        */
+    size_t off_iperm;    /* int32 [max_faces]   leaf of face f (inverse of perm)               */
     size_t off_xlist;    /* bottom-up scratch, per block of 1024 leaves: edge records (box of a
                             child whose parent's leaf range crosses blocks, 2048 x 32 B per
                             block), crossing nodes int32x4 [max_faces] (node, prefix length,
@@ -156,6 +157,17 @@ mesh_status mesh_refit(mesh_bvh *bvh, const float *d_V, int64_t nV, void *stream
 mesh_status mesh_closest_point(const mesh_bvh *bvh, const float *d_Q, int64_t nQ,
                                float max_dist, int32_t *d_face, float *d_bary, float *d_point,
                                float *d_dist2, void *stream);
+
+/* mesh_closest_point with a warm start: d_hint[i] (a face id, e.g. query i's
+ * nearest face in the previous frame; -1 or out of range = none) is tested
+ * before the traversal and its distance bounds the search.  The answer is the
+ * same as without the hint (every face within the final tie window is still
+ * reached); only the work changes.  d_hint may be the same array as d_face
+ * (each query reads its hint before writing its face).  Used by the
+ * depth-first one-thread variants (0, 2-9); the others ignore it. */
+mesh_status mesh_closest_point_hinted(const mesh_bvh *bvh, const float *d_Q, int64_t nQ,
+                                      float max_dist, const int32_t *d_hint, int32_t *d_face,
+                                      float *d_bary, float *d_point, float *d_dist2, void *stream);
 
 /* Work counters of the one-thread depth-first traversal for these queries:
  * d_counts[0] = node visits (each reads one 64-byte record holding two child

@@ -26,7 +26,7 @@ class Layout(C.Structure):
     _fields_ = [("n_faces", I64), ("n_verts", I64), ("max_faces", I64), ("max_verts", I64),
                 ("off_header", SZ), ("off_verts", SZ), ("off_faces", SZ), ("off_keys", SZ),
                 ("off_perm", SZ), ("off_nodes", SZ), ("off_parent", SZ), ("off_tris", SZ),
-                ("off_rend", SZ), ("off_xlist", SZ), ("storage_bytes", SZ)]
+                ("off_rend", SZ), ("off_iperm", SZ), ("off_xlist", SZ), ("storage_bytes", SZ)]
 
 
 class BatchLayout(C.Structure):
@@ -50,6 +50,7 @@ SIGNATURES = {
     "mesh_update_vertices": (C.c_int, [VP, VP, I64, VP]),
     "mesh_refit": (C.c_int, [VP, VP, I64, VP]),
     "mesh_closest_point": (C.c_int, [VP, VP, I64, C.c_float, VP, VP, VP, VP, VP]),
+    "mesh_closest_point_hinted": (C.c_int, [VP, VP, I64, C.c_float, VP, VP, VP, VP, VP, VP]),
     "mesh_closest_point_stats": (C.c_int, [VP, VP, I64, C.c_float, VP, VP]),
     "mesh_set_query_group": (C.c_int, [C.c_int]),
     "mesh_set_traversal": (C.c_int, [C.c_int]),

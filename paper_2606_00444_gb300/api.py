@@ -118,9 +118,17 @@ class MeshBVH:
               "mesh_refit")
 
     def closest_point(self, Q: torch.Tensor, max_dist: float = math.inf, want=("face", "bary",
-                      "point", "dist2"), out: dict | None = None) -> dict:
+                      "point", "dist2"), out: dict | None = None,
+                      hint: torch.Tensor | None = None) -> dict:
+        """NearestSurface of every query.  `hint` (int32 face ids, -1 = none; may be
+        out["face"] itself) warm-starts the search, e.g. with the previous frame's
+        answers; the result is the same with or without it."""
         Q = _f32(Q, 3, "Q")
         n = Q.shape[0]
+        if hint is not None:
+            hint = _i32(hint, None, "hint")
+            if hint.shape[0] != n:
+                raise ValueError("hint must have one entry per query")
         out = {} if out is None else out
         if "face" in want and "face" not in out:
             out["face"] = torch.empty(n, dtype=torch.int32, device=Q.device)
@@ -129,9 +137,9 @@ class MeshBVH:
                 out[k] = torch.empty(n, c, dtype=torch.float32, device=Q.device)
         if "dist2" in want and "dist2" not in out:
             out["dist2"] = torch.empty(n, dtype=torch.float32, device=Q.device)
-        check(lib().mesh_closest_point(self.handle, Q.data_ptr(), n, float(max_dist),
-                                       _ptr(out.get("face")), _ptr(out.get("bary")),
-                                       _ptr(out.get("point")), _ptr(out.get("dist2")), _stream()),
+        check(lib().mesh_closest_point_hinted(self.handle, Q.data_ptr(), n, float(max_dist), _ptr(hint),
+                                              _ptr(out.get("face")), _ptr(out.get("bary")),
+                                              _ptr(out.get("point")), _ptr(out.get("dist2")), _stream()),
               "mesh_closest_point")
         return out
 

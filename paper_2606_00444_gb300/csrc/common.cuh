@@ -31,6 +31,7 @@ struct mesh_bvh_impl {
     int *parent() const { return reinterpret_cast<int *>(base + L.off_parent); }
     float4 *tris() const { return reinterpret_cast<float4 *>(base + L.off_tris); }
     int *rend() const { return reinterpret_cast<int *>(base + L.off_rend); }
+    int *iperm() const { return reinterpret_cast<int *>(base + L.off_iperm); }
     int *xlist() const { return reinterpret_cast<int *>(base + L.off_xlist); }
 };
 

@@ -538,7 +538,7 @@ k_refit_local(int n, const float *__restrict__ V3, int nV, float4 *__restrict__ 
               float4 *__restrict__ tris, float4 *__restrict__ nodes, const int *__restrict__ parent,
               const int *__restrict__ rend, float4 *__restrict__ pre, float4 *__restrict__ suf,
               float4 *__restrict__ bbox, int4 *__restrict__ xlist, int *__restrict__ xcnt,
-              Header *__restrict__ hdr) {
+              int *__restrict__ iperm, Header *__restrict__ hdr) {
     extern __shared__ float4 dsm[];
     float *tab = reinterpret_cast<float *>(dsm);
     int *s_warp = reinterpret_cast<int *>(tab + 12 * kRefitBlock);
@@ -621,6 +621,7 @@ k_refit_local(int n, const float *__restrict__ V3, int nV, float4 *__restrict__ 
     }
     if (j < n) {
         int f = perm[j];                                 // reloaded: cheaper than keeping it live
+        iperm[f] = j;
         float4 a, b, c;
         load_tri(V3, V4, faces[f], a, b, c);
         float deg = exactly_degenerate(a, b, c) ? 1.0f : 0.0f;
@@ -959,6 +960,7 @@ static mesh_bvh_layout storage_layout(int64_t maxV, int64_t maxF) {
     L.off_parent = take(4 * (2 * f - 1));
     L.off_tris = take(48 * f);
     L.off_rend = take(4 * f);
+    L.off_iperm = take(4 * f);
     L.off_xlist = take(xlist_bytes(f));
     L.storage_bytes = off;
     return L;
@@ -1039,7 +1041,7 @@ static mesh_status bottom_up(mesh_bvh *bvh, const float *V3, cudaStream_t s) {
     int *xcnt = reinterpret_cast<int *>(bbox + 2 * nbmax);
     k_refit_local<<<nb, kRefitBlock, kRefitLocalSmem, s>>>(
         n, V3, (int)bvh->L.n_verts, bvh->verts(), bvh->perm(), bvh->faces(), bvh->tris(),
-        bvh->nodes(), bvh->parent(), bvh->rend(), pre, suf, bbox, xlist, xcnt, bvh->hdr());
+        bvh->nodes(), bvh->parent(), bvh->rend(), pre, suf, bbox, xlist, xcnt, bvh->iperm(), bvh->hdr());
     count_launch();
     if (nb > 1) {
         k_refit_top<<<nb, kTopThreads, 0, s>>>(xlist, xcnt, pre, suf, bbox, bvh->nodes(), bvh->hdr());

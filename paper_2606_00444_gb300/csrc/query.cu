@@ -252,11 +252,16 @@ struct Counts {
     int visits, tests;
 };
 
+// hint_leaf >= 0: a leaf tested before the traversal (a warm start, e.g. the
+// previous frame's nearest face); its distance bounds the search from the
+// first node on.  Every leaf within the final tie window is still reached, so
+// the answer is the same with or without it.
 template <int kBlockT, int kSmem = kStackShared, bool kOneSite = false, bool kCount = false>
 __device__ __forceinline__ Hit nearest(const Traversal &T, float3 q, float maxd2,
                                        int2 (*stk)[kBlockT], unsigned int *status,
-                                       Counts *cnt = nullptr) {
+                                       Counts *cnt = nullptr, int hint_leaf = -1) {
     Best B{-1, 0x7fffffff, INFINITY, INFINITY, maxd2};
+    if (hint_leaf >= 0) test_leaf(T, B, hint_leaf, q, maxd2);
     if (T.n == 1) {
         if constexpr (kCount) cnt->tests++;
         test_leaf(T, B, 0, q, maxd2);
@@ -634,15 +639,20 @@ template <int kSmem, int kMode, int kMinBlocks = kQueryMinBlocks>
 __global__ void __launch_bounds__(kQueryBlock, kMinBlocks)
 k_closest_point(Traversal T, const Header *__restrict__ hdr, unsigned int *status,
                 const float *__restrict__ Q, int64_t nQ, float maxd2, int *face, float *bary,
-                float *point, float *dist2) {
+                float *point, float *dist2, const int *hint, const int *__restrict__ iperm) {
     __shared__ int2 stk[kSmem > 0 ? kSmem : 1][kQueryBlock];
     int64_t i = (int64_t)blockIdx.x * kQueryBlock + threadIdx.x;
     if (i >= nQ) return;
     T.tau = traversal_tau(hdr);
     float3 q = make_float3(Q[3 * i], Q[3 * i + 1], Q[3 * i + 2]);
+    int hint_leaf = -1;
+    if (hint) {                                   // may alias face: read before the write below
+        int hf = hint[i];
+        if (hf >= 0 && hf < T.n) hint_leaf = __ldg(iperm + hf);
+    }
     Hit h;
     if constexpr (kMode == 1) h = nearest_ww<kQueryBlock>(T, q, maxd2, stk, status);
-    else h = nearest<kQueryBlock, kSmem, kMode == 2>(T, q, maxd2, stk, status);
+    else h = nearest<kQueryBlock, kSmem, kMode == 2>(T, q, maxd2, stk, status, nullptr, hint_leaf);
     write_hit(T, h, q, i, face, bary, point, dist2);
 }
 
@@ -1044,8 +1054,16 @@ extern "C" {
 mesh_status mesh_closest_point(const mesh_bvh *bvh, const float *d_Q, int64_t nQ, float max_dist,
                                int32_t *d_face, float *d_bary, float *d_point, float *d_dist2,
                                void *stream) {
+    return mesh_closest_point_hinted(bvh, d_Q, nQ, max_dist, nullptr, d_face, d_bary, d_point, d_dist2,
+                                     stream);
+}
+
+mesh_status mesh_closest_point_hinted(const mesh_bvh *bvh, const float *d_Q, int64_t nQ, float max_dist,
+                                      const int32_t *d_hint, int32_t *d_face, float *d_bary,
+                                      float *d_point, float *d_dist2, void *stream) {
     if (!bvh || nQ < 0 || (nQ > 0 && !d_Q) || !(max_dist >= 0.0f)) return MESH_ERR_INVALID_ARG;
     if (nQ == 0) return MESH_OK;
+    const int *iperm = bvh->iperm();
     float maxd2 = isinf(max_dist) ? INFINITY : max_dist * max_dist;
     cudaStream_t s = (cudaStream_t)stream;
     int G = bvh->cfg_lanes > 0 ? bvh->cfg_lanes : pick_group(nQ);
@@ -1056,7 +1074,7 @@ mesh_status mesh_closest_point(const mesh_bvh *bvh, const float *d_Q, int64_t nQ
     unsigned int grid = grid_for(nQ * G, kQueryBlock);
     switch (G) {
         case 1:
-#define MESH_CP_ARGS <<<grid, kQueryBlock, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2)
+#define MESH_CP_ARGS <<<grid, kQueryBlock, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2, d_hint, iperm)
             switch (variant) {
                 case 1: k_closest_point<kStackShared, 1> MESH_CP_ARGS; break;
                 case 2: k_closest_point<8, 0> MESH_CP_ARGS; break;
@@ -1085,7 +1103,7 @@ mesh_status mesh_closest_point(const mesh_bvh *bvh, const float *d_Q, int64_t nQ
                         k_closest_point_persistent<0><<<pg, kQueryBlock, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2, work);
                     break;
                 }
-                case 12: k_closest_point_packet MESH_CP_ARGS; break;
+                case 12: k_closest_point_packet<<<grid, kQueryBlock, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2); break;
                 default: k_closest_point<kStackShared, 0> MESH_CP_ARGS; break;
             }
 #undef MESH_CP_ARGS

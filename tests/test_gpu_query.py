@@ -181,6 +181,62 @@ def test_warp_packet_traversal_ragged_and_sorted(c1, n):
         set_traversal(0)
 
 
+@pytest.mark.parametrize("variant", [0, 2, 3, 9])
+def test_warm_start_hint_gives_identical_answers(c1, variant):
+    """mesh_closest_point_hinted: exact previous answers, random faces, -1 and
+    out-of-range ids as hints, and the hint aliasing the face output, all give
+    the unhinted result bit for bit."""
+    from paper_2606_00444_gb300 import set_query_group, set_traversal
+    _, _, VG, FG, Q = c1
+    bvh = MeshBVH.from_mesh(dev(VG), dev(FG))
+    rng = np.random.default_rng(77)
+    try:
+        set_query_group(1)
+        set_traversal(variant)
+        for cut in (np.inf, 0.05):
+            ref = bvh.closest_point(dev(Q), max_dist=cut)
+            n = Q.shape[0]
+            hints = [ref["face"].clone(),
+                     dev(rng.integers(0, FG.shape[0], n).astype(np.int32)),
+                     dev(np.full(n, -1, np.int32)),
+                     dev(rng.integers(-5, 2 * FG.shape[0], n).astype(np.int32))]
+            for hint in hints:
+                got = bvh.closest_point(dev(Q), max_dist=cut, hint=hint)
+                for k in ref:
+                    assert torch.equal(got[k], ref[k]), k
+            out = {k: v.clone() for k, v in ref.items()}          # hint = the face output itself
+            out["face"] = dev(rng.integers(0, FG.shape[0], n).astype(np.int32))
+            bvh.closest_point(dev(Q), max_dist=cut, out=out, hint=out["face"])
+            for k in ref:
+                assert torch.equal(out[k], ref[k]), k
+        assert bvh.status()[0] == 0
+    finally:
+        set_query_group(0)
+        set_traversal(0)
+
+
+def test_warm_start_over_a_skinned_sequence_full_size():
+    """The physics loop: each frame's contact query is hinted with the previous
+    frame's faces (refit tree, 1M particles in Morton order, cutoff 0.05); the
+    answers equal the unhinted ones."""
+    from paper_2606_00444_gb300 import morton_order
+    V0, F = torus(400, 250)
+    sk = TorusSkinning(V0, seed=3000)
+    lo, hi = V0.min(0) - 0.2, V0.max(0) + 0.2
+    P = dev(uniform_box(1 << 20, lo, hi, seed=3002))
+    P = P[morton_order(P).long()].contiguous()
+    bvh = MeshBVH.from_mesh(dev(V0), dev(F))
+    face = torch.full((P.shape[0],), -1, dtype=torch.int32, device="cuda")
+    for t in (0, 1, 2, 12):
+        bvh.refit(dev(sk.frame(t)))
+        ref = bvh.closest_point(P, 0.05)
+        got = bvh.closest_point(P, 0.05, hint=face)
+        for k in ref:
+            assert torch.equal(got[k], ref[k]), (t, k)
+        face = got["face"]
+    assert bvh.status()[0] == 0
+
+
 def test_traversal_counters_are_consistent(c1):
     _, _, VG, FG, Q = c1
     bvh = MeshBVH.from_mesh(dev(VG), dev(FG))

@@ -166,6 +166,13 @@ def gpu_arm(args, rank, world, local_rank):
             torch.empty(gface.shape[0], 3, device=dev))
     S_def = torch.empty(N_CD, 3, device=dev)
     cd_out = torch.empty(2, dtype=torch.float64, device=dev)
+    # per-sample Chamfer faces of the previous frame, for the warm-started variant
+    # timed beside the frame (mesh_chamfer_hinted; not faster here: the unbounded
+    # searches' cost is the ball of the final distance, which a hint cannot shrink)
+    cd_ps = dict(faceA=torch.full((N_CD,), -1, dtype=torch.int32, device=dev),
+                 baryA=torch.empty(N_CD, 3, device=dev), dist2A=torch.empty(N_CD, device=dev),
+                 faceB=torch.full((N_CD,), -1, dtype=torch.int32, device=dev),
+                 baryB=torch.empty(N_CD, 3, device=dev), dist2B=torch.empty(N_CD, device=dev))
     cd_ws = Workspace(dev)
     flush = torch.empty(128 << 20, dtype=torch.float32, device=dev)   # 512 MB > L2
 
@@ -264,6 +271,9 @@ def gpu_arm(args, rank, world, local_rank):
                           chamfer(fixed, S_def, rest, rest_S, ws=cd_ws, out=cd_out))]
     contact_nh = {k: torch.empty_like(v) for k, v in contact.items()}
     stage_fns.append(lambda: fixed.closest_point(P, CUTOFF, out=contact_nh))   # no warm start
+    cd_out_h = torch.empty_like(cd_out)
+    stage_fns.append(lambda: chamfer(fixed, S_def, rest, rest_S, ws=cd_ws, out=cd_out_h, ps=cd_ps,
+                                     hints=(cd_ps["faceA"], cd_ps["faceB"])))
     stage_graphs = []
     for fn in stage_fns:
         gs = torch.cuda.CUDAGraph()
@@ -272,16 +282,17 @@ def gpu_arm(args, rank, world, local_rank):
         stage_graphs.append(gs)
     torch.cuda.synchronize()
     nst = min(args.steps, 100)
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(nst)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(8)] for _ in range(nst)]
     for k in range(nst):
         flush.fill_(float(k))
         load_frame(k)
         for i, gs in enumerate(stage_graphs):
             evs[k][i].record()
             gs.replay()
-        evs[k][6].record()
+        evs[k][7].record()
     torch.cuda.synchronize()
-    names = ["refit", "contact", "rebind", "rebuild", "chamfer", "contact_without_warm_start"]
+    names = ["refit", "contact", "rebind", "rebuild", "chamfer", "contact_without_warm_start",
+             "chamfer_with_warm_start"]
     st = {n: float(np.mean([e[i].elapsed_time(e[i + 1]) for e in evs])) for i, n in enumerate(names)}
     un_ms = []
     contact_un = {k: torch.empty_like(v) for k, v in contact.items()}

@@ -164,7 +164,8 @@ mesh_status mesh_closest_point(const mesh_bvh *bvh, const float *d_Q, int64_t nQ
  * same as without the hint (every face within the final tie window is still
  * reached); only the work changes.  d_hint may be the same array as d_face
  * (each query reads its hint before writing its face).  Used by the
- * depth-first one-thread variants (0, 2-9); the others ignore it. */
+ * depth-first one-thread variants (0, 2-9) and by the cooperative groups
+ * (lanes > 1); the other one-thread variants ignore it. */
 mesh_status mesh_closest_point_hinted(const mesh_bvh *bvh, const float *d_Q, int64_t nQ,
                                       float max_dist, const int32_t *d_hint, int32_t *d_face,
                                       float *d_bary, float *d_point, float *d_dist2, void *stream);
@@ -239,6 +240,18 @@ mesh_status mesh_chamfer(const mesh_bvh *A, const float *d_SA, int64_t nSA,
                          void *d_ws, size_t ws_bytes, double *d_out,
                          int32_t *d_faceA, float *d_baryA, float *d_dist2A,
                          int32_t *d_faceB, float *d_baryB, float *d_dist2B, void *stream);
+
+/* mesh_chamfer with warm starts: d_hintA[i] is a face of mesh B for sample
+ * SA[i] (e.g. its nearest face in the previous frame), d_hintB[i] a face of
+ * mesh A for SB[i]; -1 or out of range = none, either pointer may be NULL,
+ * and each may be the same array as the matching face output.  The answers
+ * are the same as without hints; only the traversal work changes. */
+mesh_status mesh_chamfer_hinted(const mesh_bvh *A, const float *d_SA, int64_t nSA,
+                                const mesh_bvh *B, const float *d_SB, int64_t nSB, void *d_ws,
+                                size_t ws_bytes, double *d_out, const int32_t *d_hintA,
+                                const int32_t *d_hintB, int32_t *d_faceA, float *d_baryA,
+                                float *d_dist2A, int32_t *d_faceB, float *d_baryB,
+                                float *d_dist2B, void *stream);
 
 /* mesh_chamfer for callers that cannot allocate device memory.  (The paper has
  * no counterpart; this exists for integrations, not for the method.)  Some

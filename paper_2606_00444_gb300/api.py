@@ -383,26 +383,41 @@ class MeshBatch:
 
 
 def chamfer(A: MeshBVH, SA: torch.Tensor, B: MeshBVH, SB: torch.Tensor, per_sample=False,
-            ws: Workspace | None = None, out: torch.Tensor | None = None):
-    """[mean d(SA, B)^2, mean d(SB, A)^2] (float64) and optional per-sample results."""
+            ws: Workspace | None = None, out: torch.Tensor | None = None, ps: dict | None = None,
+            hints=None):
+    """[mean d(SA, B)^2, mean d(SB, A)^2] (float64) and optional per-sample results.
+
+    `ps` reuses per-sample output arrays (faceA, baryA, dist2A, faceB, baryB, dist2B);
+    `hints` = (faces of B for SA, faces of A for SB), int32 (-1 = none, either may be
+    None, and each may be the matching face output itself), warm-starts the searches,
+    e.g. with the previous frame's answers; the results are the same without them."""
     SA = _f32(SA, 3, "SA")
     SB = _f32(SB, 3, "SB")
     nA, nB = SA.shape[0], SB.shape[0]
     ws = A._chamfer_ws if ws is None else ws
     buf = ws.get(lib().mesh_chamfer_workspace_bytes(nA, nB))
     out = torch.empty(2, dtype=torch.float64, device=SA.device) if out is None else out
-    ps = {}
-    if per_sample:
+    if per_sample and ps is None:
         dev = SA.device
         ps = dict(faceA=torch.empty(nA, dtype=torch.int32, device=dev),
                   baryA=torch.empty(nA, 3, device=dev), dist2A=torch.empty(nA, device=dev),
                   faceB=torch.empty(nB, dtype=torch.int32, device=dev),
                   baryB=torch.empty(nB, 3, device=dev), dist2B=torch.empty(nB, device=dev))
-    check(lib().mesh_chamfer(A.handle, SA.data_ptr(), nA, B.handle, SB.data_ptr(), nB,
-                             buf.data_ptr(), buf.numel(), out.data_ptr(),
-                             _ptr(ps.get("faceA")), _ptr(ps.get("baryA")), _ptr(ps.get("dist2A")),
-                             _ptr(ps.get("faceB")), _ptr(ps.get("baryB")), _ptr(ps.get("dist2B")),
-                             _stream()), "mesh_chamfer")
+    ps = {} if ps is None else ps
+    hA, hB = (None, None) if hints is None else hints
+    if hA is not None:
+        hA = _i32(hA, None, "hints[0]")
+        if hA.shape[0] != nA:
+            raise ValueError("hints[0] must have one entry per sample of SA")
+    if hB is not None:
+        hB = _i32(hB, None, "hints[1]")
+        if hB.shape[0] != nB:
+            raise ValueError("hints[1] must have one entry per sample of SB")
+    check(lib().mesh_chamfer_hinted(A.handle, SA.data_ptr(), nA, B.handle, SB.data_ptr(), nB,
+                                    buf.data_ptr(), buf.numel(), out.data_ptr(), _ptr(hA), _ptr(hB),
+                                    _ptr(ps.get("faceA")), _ptr(ps.get("baryA")), _ptr(ps.get("dist2A")),
+                                    _ptr(ps.get("faceB")), _ptr(ps.get("baryB")), _ptr(ps.get("dist2B")),
+                                    _stream()), "mesh_chamfer")
     return (out, ps) if per_sample else out
 
 

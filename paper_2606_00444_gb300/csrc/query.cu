@@ -469,7 +469,7 @@ template <int G> __device__ __forceinline__ int grp_incl_scan(int x, int gl) {
 
 template <int G>
 __device__ Hit nearest_group(const Traversal &T, float3 q, float maxd2, bool valid, int2 *stk,
-                             unsigned int *status) {
+                             unsigned int *status, int hint_leaf = -1) {
     const int lane = threadIdx.x & 31;
     const int gl = lane & (G - 1);
     const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
@@ -496,6 +496,7 @@ __device__ Hit nearest_group(const Traversal &T, float3 q, float maxd2, bool val
             if (c >= 0) { node = c; continue; }
             Best B{-1, 0x7fffffff, INFINITY, INFINITY, maxd2};
             test_leaf(T, B, -c - 1, q, maxd2);
+            if (hint_leaf >= 0) test_leaf(T, B, hint_leaf, q, maxd2);   // warm start
             if (B.leaf >= 0) { bleaf = B.leaf; bface = B.face; bd2 = B.d2; dmin = B.dmin; thr = B.thr; }
             break;
         }
@@ -869,13 +870,18 @@ template <int G>
 __global__ void __launch_bounds__(kQueryBlock)
 k_closest_point_group(Traversal T, const Header *__restrict__ hdr, unsigned int *status,
                       const float *__restrict__ Q, int64_t nQ, float maxd2, int *face, float *bary,
-                      float *point, float *dist2) {
+                      float *point, float *dist2, const int *hint, const int *__restrict__ iperm) {
     __shared__ int2 gstk[kQueryBlock / G][group_cap<G>()];
     int64_t i = ((int64_t)blockIdx.x * kQueryBlock + threadIdx.x) / G;
     bool valid = i < nQ;
     T.tau = traversal_tau(hdr);
     float3 q = valid ? make_float3(Q[3 * i], Q[3 * i + 1], Q[3 * i + 2]) : make_float3(0.f, 0.f, 0.f);
-    Hit h = nearest_group<G>(T, q, maxd2, valid, gstk[threadIdx.x / G], status);
+    int hint_leaf = -1;
+    if (valid && hint) {                          // every lane of the group reads it before any write
+        int hf = hint[i];
+        if (hf >= 0 && hf < T.n) hint_leaf = __ldg(iperm + hf);
+    }
+    Hit h = nearest_group<G>(T, q, maxd2, valid, gstk[threadIdx.x / G], status, hint_leaf);
     if (valid && (threadIdx.x & (G - 1)) == 0) write_hit(T, h, q, i, face, bary, point, dist2);
 }
 
@@ -939,6 +945,8 @@ struct ChamferSide {
     int64_t n;
     int *face;
     float *bary, *dist2;
+    const int *hint = nullptr;     // warm start: a face id per sample (-1 = none), may alias face
+    const int *iperm = nullptr;    // face -> leaf of the mesh searched
 };
 
 template <int G>
@@ -958,16 +966,22 @@ k_chamfer(ChamferSide A2B, ChamferSide B2A, unsigned int nbA, unsigned int *stat
     bool valid = i < C.n;
     float3 q = valid ? make_float3(C.S[3 * i], C.S[3 * i + 1], C.S[3 * i + 2])
                      : make_float3(0.f, 0.f, 0.f);
+    int hint_leaf = -1;
+    if (valid && C.hint) {
+        int hf = C.hint[i];
+        if (hf >= 0 && hf < T.n) hint_leaf = __ldg(C.iperm + hf);
+    }
     if constexpr (G == 1) {
         if (valid) {
             Hit h = nearest<kQueryBlock>(T, q, INFINITY,
-                                         reinterpret_cast<int2 (*)[kQueryBlock]>(stk_mem), status);
+                                         reinterpret_cast<int2 (*)[kQueryBlock]>(stk_mem), status,
+                                         nullptr, hint_leaf);
             write_hit(T, h, q, i, C.face, C.bary, nullptr, C.dist2);
             d2 = h.leaf >= 0 ? (double)h.d2 : 0.0;
         }
     } else {
         Hit h = nearest_group<G>(T, q, INFINITY, valid, stk_mem + (threadIdx.x / G) * group_cap<G>(),
-                                 status);
+                                 status, hint_leaf);
         if (valid && (threadIdx.x & (G - 1)) == 0) {
             write_hit(T, h, q, i, C.face, C.bary, nullptr, C.dist2);
             d2 = h.leaf >= 0 ? (double)h.d2 : 0.0;
@@ -1108,11 +1122,11 @@ mesh_status mesh_closest_point_hinted(const mesh_bvh *bvh, const float *d_Q, int
             }
 #undef MESH_CP_ARGS
             break;
-        case 2: k_closest_point_group<2><<<grid, kQueryBlock, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2); break;
-        case 4: k_closest_point_group<4><<<grid, kQueryBlock, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2); break;
-        case 8: k_closest_point_group<8><<<grid, kQueryBlock, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2); break;
-        case 16: k_closest_point_group<16><<<grid, kQueryBlock, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2); break;
-        default: k_closest_point_group<32><<<grid, kQueryBlock, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2); break;
+        case 2: k_closest_point_group<2><<<grid, kQueryBlock, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2, d_hint, iperm); break;
+        case 4: k_closest_point_group<4><<<grid, kQueryBlock, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2, d_hint, iperm); break;
+        case 8: k_closest_point_group<8><<<grid, kQueryBlock, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2, d_hint, iperm); break;
+        case 16: k_closest_point_group<16><<<grid, kQueryBlock, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2, d_hint, iperm); break;
+        default: k_closest_point_group<32><<<grid, kQueryBlock, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2, d_hint, iperm); break;
     }
     count_launch();
     return check_launch();
@@ -1127,6 +1141,15 @@ mesh_status mesh_chamfer(const mesh_bvh *A, const float *d_SA, int64_t nSA, cons
                          const float *d_SB, int64_t nSB, void *d_ws, size_t ws_bytes,
                          double *d_out, int32_t *d_faceA, float *d_baryA, float *d_dist2A,
                          int32_t *d_faceB, float *d_baryB, float *d_dist2B, void *stream) {
+    return mesh_chamfer_hinted(A, d_SA, nSA, B, d_SB, nSB, d_ws, ws_bytes, d_out, nullptr, nullptr,
+                               d_faceA, d_baryA, d_dist2A, d_faceB, d_baryB, d_dist2B, stream);
+}
+
+mesh_status mesh_chamfer_hinted(const mesh_bvh *A, const float *d_SA, int64_t nSA, const mesh_bvh *B,
+                                const float *d_SB, int64_t nSB, void *d_ws, size_t ws_bytes,
+                                double *d_out, const int32_t *d_hintA, const int32_t *d_hintB,
+                                int32_t *d_faceA, float *d_baryA, float *d_dist2A,
+                                int32_t *d_faceB, float *d_baryB, float *d_dist2B, void *stream) {
     if (!A || !B || !d_out || nSA < 0 || nSB < 0 || (nSA > 0 && !d_SA) || (nSB > 0 && !d_SB))
         return MESH_ERR_INVALID_ARG;
     size_t need = mesh_chamfer_workspace_bytes(nSA, nSB);
@@ -1141,8 +1164,8 @@ mesh_status mesh_chamfer(const mesh_bvh *A, const float *d_SA, int64_t nSA, cons
         return check_launch();
     }
     cudaMemsetAsync(ticket, 0, sizeof(unsigned int), s);
-    ChamferSide a2b{traversal_of(B), B->hdr(), d_SA, nSA, d_faceA, d_baryA, d_dist2A};
-    ChamferSide b2a{traversal_of(A), A->hdr(), d_SB, nSB, d_faceB, d_baryB, d_dist2B};
+    ChamferSide a2b{traversal_of(B), B->hdr(), d_SA, nSA, d_faceA, d_baryA, d_dist2A, d_hintA, B->iperm()};
+    ChamferSide b2a{traversal_of(A), A->hdr(), d_SB, nSB, d_faceB, d_baryB, d_dist2B, d_hintB, A->iperm()};
     unsigned grid = (unsigned)(nbA + nbB);
     unsigned *st = &A->hdr()->status;
     switch (G) {

@@ -194,3 +194,57 @@ def test_chamfer_every_group_width(pair, lanes):
         set_query_group(0)
     ref, _, _ = oracle.chamfer(VA, FA, SA, VB, FB, SB)
     np.testing.assert_allclose(host(out), ref, rtol=1e-5)
+
+
+@pytest.mark.parametrize("lanes", [1, 4, 16])
+def test_chamfer_warm_start_hints_give_identical_results(pair, lanes):
+    """mesh_chamfer_hinted with exact, random, -1 and out-of-range hints, and
+    hints aliasing the face outputs, gives the unhinted sums and per-sample
+    results bit for bit (one thread or a cooperative group per sample)."""
+    from paper_2606_00444_gb300 import set_query_group
+    VA, FA, SA, VB, FB, SB = pair
+    A = MeshBVH.from_mesh(dev(VA), dev(FA))
+    B = MeshBVH.from_mesh(dev(VB), dev(FB))
+    rng = np.random.default_rng(21)
+    try:
+        set_query_group(lanes)
+        ref, rps = chamfer(A, dev(SA), B, dev(SB), per_sample=True)
+        nA, nB = SA.shape[0], SB.shape[0]
+        cases = [(rps["faceA"].clone(), rps["faceB"].clone()),
+                 (dev(rng.integers(0, FB.shape[0], nA).astype(np.int32)),
+                  dev(rng.integers(0, FA.shape[0], nB).astype(np.int32))),
+                 (dev(np.full(nA, -1, np.int32)), None),
+                 (None, dev(rng.integers(-3, 3 * FA.shape[0], nB).astype(np.int32)))]
+        for hints in cases:
+            out, ps = chamfer(A, dev(SA), B, dev(SB), per_sample=True, hints=hints)
+            assert torch.equal(out, ref)
+            for k in rps:
+                assert torch.equal(ps[k], rps[k]), k
+        ps = {k: v.clone() for k, v in rps.items()}
+        ps["faceA"] = dev(rng.integers(0, FB.shape[0], nA).astype(np.int32))
+        ps["faceB"] = dev(rng.integers(0, FA.shape[0], nB).astype(np.int32))
+        out, _ = chamfer(A, dev(SA), B, dev(SB), per_sample=True, ps=ps, hints=(ps["faceA"], ps["faceB"]))
+        assert torch.equal(out, ref)
+        for k in rps:
+            assert torch.equal(ps[k], rps[k]), k
+    finally:
+        set_query_group(0)
+
+
+@pytest.mark.parametrize("lanes", [2, 8, 32])
+def test_closest_point_hints_in_cooperative_groups(pair, lanes):
+    from paper_2606_00444_gb300 import set_query_group
+    VA, FA, SA, VB, FB, SB = pair
+    B = MeshBVH.from_mesh(dev(VB), dev(FB))
+    rng = np.random.default_rng(22)
+    Q = dev(uniform_box(3000, [-1.5] * 3, [1.5] * 3, seed=23))
+    try:
+        set_query_group(lanes)
+        for cut in (np.inf, 0.05):
+            ref = B.closest_point(Q, cut)
+            for hint in (ref["face"].clone(), dev(rng.integers(-2, FB.shape[0] + 5, 3000).astype(np.int32))):
+                got = B.closest_point(Q, cut, hint=hint)
+                for k in ref:
+                    assert torch.equal(got[k], ref[k]), k
+    finally:
+        set_query_group(0)

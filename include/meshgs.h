@@ -147,6 +147,19 @@ mesh_status mesh_update_vertices(mesh_bvh *bvh, const float *d_V, int64_t nV, vo
  * topology: a refit after any build is valid. */
 mesh_status mesh_refit(mesh_bvh *bvh, const float *d_V, int64_t nV, void *stream);
 
+/* mesh_refit and mesh_bind_gaussians in one pass (the fixed-topology frame of
+ * Sec. 3.4: new vertices, new boxes, Gaussians moved with their faces), the
+ * face corners read once for both.  The Gaussians are grouped by face: those
+ * of face f are g = d_gstart[f] .. d_gstart[f + 1] - 1 (int32 [nF + 1],
+ * non-decreasing, d_gstart[nF] = nG), with weights d_gbary [nG][3] and
+ * normal offsets d_goff [nG] (NULL = 0); outputs as mesh_bind_gaussians,
+ * indexed by g.  A face whose range is decreasing or past nG sets
+ * MESH_DEV_INDEX_RANGE and its Gaussians are not written.  Same results as
+ * the two calls. */
+mesh_status mesh_refit_bind(mesh_bvh *bvh, const float *d_V, int64_t nV, const int32_t *d_gstart,
+                            const float *d_gbary, const float *d_goff, int64_t nG, float *d_mu,
+                            float *d_quat, float *d_scale, void *stream);
+
 /* NearestSurface (Eq. 1 / Eq. 2): for each query q the closest point of the
  * mesh, as face id, barycentric weights (u, v, w) of (v0, v1, v2), the point
  * u v0 + v v1 + w v2 and its squared distance.  Ties: the lowest face id

@@ -49,6 +49,7 @@ SIGNATURES = {
     "mesh_morton_order": (C.c_int, [VP, I64, VP, VP, SZ, VP]),
     "mesh_update_vertices": (C.c_int, [VP, VP, I64, VP]),
     "mesh_refit": (C.c_int, [VP, VP, I64, VP]),
+    "mesh_refit_bind": (C.c_int, [VP, VP, I64, VP, VP, VP, I64, VP, VP, VP, VP]),
     "mesh_closest_point": (C.c_int, [VP, VP, I64, C.c_float, VP, VP, VP, VP, VP]),
     "mesh_closest_point_hinted": (C.c_int, [VP, VP, I64, C.c_float, VP, VP, VP, VP, VP, VP]),
     "mesh_closest_point_stats": (C.c_int, [VP, VP, I64, C.c_float, VP, VP]),

@@ -117,6 +117,26 @@ class MeshBVH:
         check(lib().mesh_refit(self.handle, _ptr(V), 0 if V is None else V.shape[0], _stream()),
               "mesh_refit")
 
+    def refit_bind(self, V, gstart, gbary, goff=None, out=None):
+        """refit(V) and bind_gaussians in one pass; the Gaussians of face f are
+        gstart[f] .. gstart[f + 1] - 1 (int32 CSR over faces)."""
+        if V is not None:
+            V = _f32(V, 3, "V")
+        gstart = _i32(gstart, None, "gstart")
+        gbary = _f32(gbary, 3, "gbary")
+        goff = None if goff is None else _f32(goff, None, "goff")
+        nG = gbary.shape[0]
+        if gstart.shape[0] != self.n_faces + 1:
+            raise ValueError("gstart must have n_faces + 1 entries")
+        if out is None:
+            d = gbary.device
+            out = (torch.empty(nG, 3, device=d), torch.empty(nG, 4, device=d), torch.empty(nG, 3, device=d))
+        mu, quat, scale = out
+        check(lib().mesh_refit_bind(self.handle, _ptr(V), 0 if V is None else V.shape[0], gstart.data_ptr(),
+                                    gbary.data_ptr(), _ptr(goff), nG, mu.data_ptr(), quat.data_ptr(),
+                                    scale.data_ptr(), _stream()), "mesh_refit_bind")
+        return out
+
     def closest_point(self, Q: torch.Tensor, max_dist: float = math.inf, want=("face", "bary",
                       "point", "dist2"), out: dict | None = None,
                       hint: torch.Tensor | None = None) -> dict:

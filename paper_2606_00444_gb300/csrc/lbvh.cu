@@ -13,6 +13,7 @@
 #include <climits>
 
 #include "common.cuh"
+#include "gauss_math.cuh"
 
 namespace meshgs {
 
@@ -529,6 +530,29 @@ struct SBox {
     }
 };
 
+// Face-bound Gaussians rebound in the refit pass (mesh_refit_bind): the
+// Gaussians of face f are gstart[f] .. gstart[f + 1] - 1; gstart == NULL: none.
+struct Rebind {
+    const int *gstart;
+    const float *gbary, *goff;
+    int64_t nG;
+    float *mu, *quat, *scale;
+};
+
+// The Gaussians of one face (kept out of line: the quaternion arithmetic would
+// otherwise raise the register pressure of the whole refit kernel).
+__device__ __noinline__ void bind_face(const Rebind &RB, int f, float4 a, float4 b, float4 c, Header *hdr) {
+    int gs = RB.gstart[f], ge = RB.gstart[f + 1];
+    if (gs < 0 || ge < gs || (int64_t)ge > RB.nG) {
+        set_status(hdr, MESH_DEV_INDEX_RANGE);
+        return;
+    }
+    for (int g = gs; g < ge; ++g)
+        bind_corners(v3(a), v3(b), v3(c), RB.gbary[3 * (size_t)g], RB.gbary[3 * (size_t)g + 1],
+                     RB.gbary[3 * (size_t)g + 2], RB.goff ? RB.goff[g] : 0.0f, g, RB.mu, RB.quat, RB.scale,
+                     &hdr->status, &hdr->n_degenerate);
+}
+
 constexpr size_t kRefitLocalSmem = 12 * kRefitBlock * sizeof(float)      // two table levels
                                    + 64 * sizeof(int);                    // crossing-list scan
 
@@ -538,7 +562,7 @@ k_refit_local(int n, const float *__restrict__ V3, int nV, float4 *__restrict__ 
               float4 *__restrict__ tris, float4 *__restrict__ nodes, const int *__restrict__ parent,
               const int *__restrict__ rend, float4 *__restrict__ pre, float4 *__restrict__ suf,
               float4 *__restrict__ bbox, int4 *__restrict__ xlist, int *__restrict__ xcnt,
-              int *__restrict__ iperm, Header *__restrict__ hdr) {
+              int *__restrict__ iperm, Header *__restrict__ hdr, Rebind RB) {
     extern __shared__ float4 dsm[];
     float *tab = reinterpret_cast<float *>(dsm);
     int *s_warp = reinterpret_cast<int *>(tab + 12 * kRefitBlock);
@@ -628,6 +652,7 @@ k_refit_local(int n, const float *__restrict__ V3, int nV, float4 *__restrict__ 
         tris[3 * (size_t)j + 0] = make_float4(a.x, a.y, a.z, __int_as_float(f));
         tris[3 * (size_t)j + 1] = make_float4(b.x, b.y, b.z, deg);
         tris[3 * (size_t)j + 2] = make_float4(c.x, c.y, c.z, 0.0f);
+        if (RB.gstart) bind_face(RB, f, a, b, c, hdr);   // a7 fused: this face's Gaussians
     }
     // a1: this block's slice of the vertex repack (after every read of V4 above)
     if (V3) {
@@ -1024,7 +1049,8 @@ mesh_status mesh_update_vertices(mesh_bvh *bvh, const float *d_V, int64_t nV, vo
 }
 
 // Launches the two bottom-up kernels (build and refit); V3 = new vertices or NULL.
-static mesh_status bottom_up(mesh_bvh *bvh, const float *V3, cudaStream_t s) {
+static mesh_status bottom_up(mesh_bvh *bvh, const float *V3, cudaStream_t s,
+                             Rebind rb = Rebind{nullptr, nullptr, nullptr, 0, nullptr, nullptr, nullptr}) {
     static bool smem_set = false;                    // above the default 48 KB: opt in once
     if (!smem_set) {
         if (cudaFuncSetAttribute(k_refit_local, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1041,13 +1067,25 @@ static mesh_status bottom_up(mesh_bvh *bvh, const float *V3, cudaStream_t s) {
     int *xcnt = reinterpret_cast<int *>(bbox + 2 * nbmax);
     k_refit_local<<<nb, kRefitBlock, kRefitLocalSmem, s>>>(
         n, V3, (int)bvh->L.n_verts, bvh->verts(), bvh->perm(), bvh->faces(), bvh->tris(),
-        bvh->nodes(), bvh->parent(), bvh->rend(), pre, suf, bbox, xlist, xcnt, bvh->iperm(), bvh->hdr());
+        bvh->nodes(), bvh->parent(), bvh->rend(), pre, suf, bbox, xlist, xcnt, bvh->iperm(), bvh->hdr(), rb);
     count_launch();
     if (nb > 1) {
         k_refit_top<<<nb, kTopThreads, 0, s>>>(xlist, xcnt, pre, suf, bbox, bvh->nodes(), bvh->hdr());
         count_launch();
     }
     return check_launch();
+}
+
+mesh_status mesh_refit_bind(mesh_bvh *bvh, const float *d_V, int64_t nV, const int32_t *d_gstart,
+                            const float *d_gbary, const float *d_goff, int64_t nG, float *d_mu,
+                            float *d_quat, float *d_scale, void *stream) {
+    if (!bvh || nG < 0 || nG > INT_MAX) return MESH_ERR_INVALID_ARG;
+    int n = (int)bvh->L.n_faces;
+    if (n == 0) return mesh_refit(bvh, d_V, nV, stream);
+    if (!d_gstart || (nG > 0 && (!d_gbary || !d_mu || !d_quat || !d_scale))) return MESH_ERR_INVALID_ARG;
+    if (d_V && (nV != bvh->L.n_verts || nV > bvh->L.max_verts)) return MESH_ERR_INVALID_ARG;
+    return bottom_up(bvh, d_V, (cudaStream_t)stream,
+                     Rebind{d_gstart, d_gbary, d_goff, nG, d_mu, d_quat, d_scale});
 }
 
 mesh_status mesh_refit(mesh_bvh *bvh, const float *d_V, int64_t nV, void *stream) {

@@ -248,3 +248,57 @@ def test_closest_point_hints_in_cooperative_groups(pair, lanes):
                     assert torch.equal(got[k], ref[k]), k
     finally:
         set_query_group(0)
+
+
+@pytest.mark.parametrize("mesh", ["ico3", "torus_200k"])
+def test_refit_bind_equals_refit_then_bind(mesh):
+    """mesh_refit_bind (refit and rebind in one pass, Gaussians grouped by face)
+    gives the boxes of mesh_refit and the Gaussians of mesh_bind_gaussians; 0 to 4
+    Gaussians per face with normal offsets, and the Gaussians also match the oracle."""
+    if mesh == "ico3":
+        V0, F = icosphere(3)
+        V1 = (V0 * 1.1 + 0.05 * np.sin(3 * V0[:, [1, 2, 0]])).astype(np.float32)
+    else:
+        V0, F = torus(400, 250)
+        V1 = TorusSkinning(V0, seed=3000).frame(30)
+    rng = np.random.default_rng(31)
+    counts = rng.integers(0, 5, F.shape[0])
+    gstart = np.concatenate([[0], np.cumsum(counts)]).astype(np.int32)
+    G = int(gstart[-1])
+    gface = np.repeat(np.arange(F.shape[0], dtype=np.int32), counts)
+    gbary = osada_barycentrics(rng, G).astype(np.float32)
+    goff = rng.normal(scale=0.01, size=G).astype(np.float32)
+    a = MeshBVH.from_mesh(dev(V0), dev(F))
+    b = MeshBVH.from_mesh(dev(V0), dev(F))
+    for t in range(2):
+        Vt = V1 if t == 0 else V0
+        a.refit(dev(Vt))
+        ref = a.bind_gaussians(dev(gface), dev(gbary), dev(goff))
+        got = b.refit_bind(dev(Vt), dev(gstart), dev(gbary), dev(goff))
+        assert torch.equal(a.arrays()["nodes_i"], b.arrays()["nodes_i"])        # bits (links are NaN as floats)
+        assert torch.equal(a.arrays()["tris"].view(torch.int32), b.arrays()["tris"].view(torch.int32))
+        for x, y in zip(got, ref):
+            torch.testing.assert_close(x, y, rtol=0, atol=1e-6)
+    pick = rng.choice(G, min(G, 5000), replace=False)
+    idx = dev(pick.astype(np.int64))
+    check_gaussians((got[0][idx], got[1][idx], got[2][idx]),
+                    oracle.bind_gaussians(V0, F, gface[pick], gbary[pick], goff[pick]))
+    # vertices already in the buffer (V = None)
+    b.update_vertices(dev(V1))
+    got2 = b.refit_bind(None, dev(gstart), dev(gbary), dev(goff))
+    a.refit(dev(V1))
+    ref2 = a.bind_gaussians(dev(gface), dev(gbary), dev(goff))
+    for x, y in zip(got2, ref2):
+        torch.testing.assert_close(x, y, rtol=0, atol=1e-6)
+    assert b.status()[0] == 0
+
+
+def test_refit_bind_bad_ranges_set_status():
+    V, F = icosphere(2)
+    gstart = np.arange(F.shape[0] + 1, dtype=np.int32)
+    gstart[5] = 100000                                      # past nG
+    gbary = np.full((F.shape[0], 3), 1 / 3, np.float32)
+    b = MeshBVH.from_mesh(dev(V), dev(F))
+    b.refit_bind(dev(V), dev(gstart), dev(gbary))
+    bits, _ = b.status()
+    assert bits & 0x1

@@ -73,6 +73,9 @@ def lib():
         L.orc_bind_gaussians_backward.restype = None
         L.orc_bind_gaussians_backward.argtypes = [F64P, I32P, I32P, F64P, C.c_void_p, I64,
                                                   F64P, F64P, F64P, F64P]
+        L.orc_knn_project.restype = None
+        L.orc_knn_project.argtypes = [F64P, I32P, I64, F64P, I64, C.c_int, C.c_void_p, C.c_double,
+                                      F64P, I32P, F64P]
         _lib = L
     return _lib
 
@@ -227,3 +230,18 @@ def bind_gaussians_backward(V, F, gface, gbary, gmu, gq, gs, goff=None):
                                       None if go is None else go.ctypes.data, gface.shape[0],
                                       _f64(gmu), _f64(gq), _f64(gs), gV)
     return gV
+
+
+def knn_project(V, F, Q, k=4, anchor=None, anchor_w=0.0):
+    """k-NN weighted surface projection (the NearestSurface of Eq. 1, temporal tracking):
+    blend of the k nearest faces' closest points with weights 1/max(d, 1e-6 diag), then
+    optionally (1 - anchor_w) * that + anchor_w * anchor.  dict(point, face[Q,k], d2[Q,k])."""
+    V, F, Q = _f64(V), _i32(F), _f64(Q).reshape(-1, 3)
+    nQ = Q.shape[0]
+    point = np.empty((nQ, 3))
+    face = np.empty((nQ, k), np.int32)
+    d2 = np.empty((nQ, k))
+    A = None if anchor is None else _f64(anchor).reshape(-1, 3)
+    lib().orc_knn_project(V, F, F.shape[0], Q, nQ, int(k), None if A is None else A.ctypes.data,
+                          float(anchor_w), point, face, d2)
+    return dict(point=point, face=face, d2=d2)

@@ -651,3 +651,76 @@ void orc_bind_gaussians_backward(const double *V, const int32_t *F, const int32_
         }
     }
 }
+
+/* ------------------------------------------------------------------ */
+/* k-NN weighted surface projection: the NearestSurface of temporal      */
+/* tracking (Sec. 3.3, Strategy 1, Eq. 1).  The paper names the method   */
+/* but gives neither k nor the weights; the reading used here:           */
+/*   the k faces nearest to v (ties: the lower face id), each giving its */
+/*   closest point p_j at distance d_j, blended with inverse-distance    */
+/*   weights w_j = 1 / max(d_j, delta), delta = 1e-6 times the mesh      */
+/*   bounding-box diagonal:  v' = sum w_j p_j / sum w_j.                 */
+/* With fewer than k faces, all of them.  Optionally the result is       */
+/* blended with an anchor point: v'' = (1 - a) v' + a anchor (the        */
+/* periodic re-anchoring to the template projection).                    */
+/* ------------------------------------------------------------------ */
+#define ORC_KNN_DELTA 1e-6
+#define ORC_KNN_MAX 16
+
+void orc_knn_project(const double *V, const int32_t *F, int64_t nF, const double *Q, int64_t nQ,
+                     int k, const double *anchor /* nullable */, double anchor_w,
+                     double *point, int32_t *face /* [nQ*k], -1 past nF */, double *d2 /* [nQ*k] */) {
+    double delta = ORC_KNN_DELTA * orc_mesh_diag(V, F, nF);
+    if (k > ORC_KNN_MAX) k = ORC_KNN_MAX;
+    for (int64_t q = 0; q < nQ; ++q) {
+        double p[3] = {Q[3 * q], Q[3 * q + 1], Q[3 * q + 2]};
+        double bd[ORC_KNN_MAX];
+        int32_t bf[ORC_KNN_MAX];
+        int cnt = 0;
+        for (int64_t f = 0; f < nF; ++f) {
+            double A[3], B[3], C[3], bb[3], pp[3];
+            for (int c = 0; c < 3; ++c) {
+                A[c] = V[3 * (int64_t)F[3 * f] + c];
+                B[c] = V[3 * (int64_t)F[3 * f + 1] + c];
+                C[c] = V[3 * (int64_t)F[3 * f + 2] + c];
+            }
+            double d = orc_point_triangle(p, A, B, C, bb, pp);
+            /* keep the k smallest (d, f); faces come in increasing id, so an
+               equal distance never displaces an earlier face */
+            if (cnt == k && !(d < bd[k - 1])) continue;
+            int pos = cnt < k ? cnt : k - 1;
+            while (pos > 0 && d < bd[pos - 1]) {
+                bd[pos] = bd[pos - 1];
+                bf[pos] = bf[pos - 1];
+                --pos;
+            }
+            bd[pos] = d;
+            bf[pos] = (int32_t)f;
+            if (cnt < k) ++cnt;
+        }
+        double sw = 0.0, acc[3] = {0.0, 0.0, 0.0};
+        for (int j = 0; j < cnt; ++j) {
+            double A[3], B[3], C[3], bb[3], pp[3];
+            int32_t f = bf[j];
+            for (int c = 0; c < 3; ++c) {
+                A[c] = V[3 * (int64_t)F[3 * f] + c];
+                B[c] = V[3 * (int64_t)F[3 * f + 1] + c];
+                C[c] = V[3 * (int64_t)F[3 * f + 2] + c];
+            }
+            orc_point_triangle(p, A, B, C, bb, pp);
+            double dj = sqrt(bd[j]);
+            double w = 1.0 / (dj > delta ? dj : delta);
+            sw += w;
+            for (int c = 0; c < 3; ++c) acc[c] += w * pp[c];
+        }
+        for (int c = 0; c < 3; ++c) {
+            double v = cnt > 0 ? acc[c] / sw : p[c];
+            if (anchor) v = (1.0 - anchor_w) * v + anchor_w * anchor[3 * q + c];
+            point[3 * q + c] = v;
+        }
+        for (int j = 0; j < k; ++j) {
+            if (face) face[q * k + j] = j < cnt ? bf[j] : -1;
+            if (d2) d2[q * k + j] = j < cnt ? bd[j] : INFINITY;
+        }
+    }
+}

@@ -183,6 +183,20 @@ mesh_status mesh_closest_point_hinted(const mesh_bvh *bvh, const float *d_Q, int
                                       float max_dist, const int32_t *d_hint, int32_t *d_face,
                                       float *d_bary, float *d_point, float *d_dist2, void *stream);
 
+/* k-NN weighted surface projection, the NearestSurface of temporal tracking
+ * (Sec. 3.3, Strategy 1, Eq. 1), which the paper names without k or weights:
+ * for query q the k (1..8) faces nearest to it (ties: the lower face id), each
+ * giving its closest point p_j at distance d_j, blended as
+ *   q' = sum w_j p_j / sum w_j,  w_j = 1 / max(d_j, 1e-6 x box diagonal);
+ * with d_anchor (NULL = none), q'' = (1 - anchor_weight) q' + anchor_weight
+ * anchor (the periodic re-anchoring to the template projection).  Outputs:
+ * d_point [nQ][3] (may be the same array as d_Q: each query is read before it
+ * is written), optional d_face [nQ][k] and d_dist2 [nQ][k], nearest first
+ * (face -1 / +inf past the mesh's face count).  No faces: q' = q. */
+mesh_status mesh_knn_project(const mesh_bvh *bvh, const float *d_Q, int64_t nQ, int k,
+                             const float *d_anchor, float anchor_weight, float *d_point,
+                             int32_t *d_face, float *d_dist2, void *stream);
+
 /* Work counters of the one-thread depth-first traversal for these queries:
  * d_counts[0] = node visits (each reads one 64-byte record holding two child
  * boxes), d_counts[1] = triangle tests, d_counts[2] = queries with a face

@@ -53,6 +53,7 @@ SIGNATURES = {
     "mesh_closest_point": (C.c_int, [VP, VP, I64, C.c_float, VP, VP, VP, VP, VP]),
     "mesh_closest_point_hinted": (C.c_int, [VP, VP, I64, C.c_float, VP, VP, VP, VP, VP, VP]),
     "mesh_closest_point_stats": (C.c_int, [VP, VP, I64, C.c_float, VP, VP]),
+    "mesh_knn_project": (C.c_int, [VP, VP, I64, C.c_int, VP, C.c_float, VP, VP, VP, VP]),
     "mesh_set_query_group": (C.c_int, [C.c_int]),
     "mesh_set_traversal": (C.c_int, [C.c_int]),
     "mesh_bvh_set_query_config": (C.c_int, [VP, C.c_int, C.c_int]),

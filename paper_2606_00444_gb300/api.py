@@ -163,6 +163,24 @@ class MeshBVH:
               "mesh_closest_point")
         return out
 
+    def knn_project(self, Q: torch.Tensor, k: int = 4, anchor: torch.Tensor | None = None,
+                    anchor_weight: float = 0.2, out: torch.Tensor | None = None,
+                    want_faces: bool = False):
+        """k-NN weighted surface projection (mesh_knn_project); `out` may be Q itself."""
+        Q = _f32(Q, 3, "Q")
+        n = Q.shape[0]
+        if anchor is not None:
+            anchor = _f32(anchor, 3, "anchor")
+            if anchor.shape[0] != n:
+                raise ValueError("anchor must have one row per query")
+        out = torch.empty_like(Q) if out is None else out
+        face = torch.empty(n, k, dtype=torch.int32, device=Q.device) if want_faces else None
+        d2 = torch.empty(n, k, device=Q.device) if want_faces else None
+        check(lib().mesh_knn_project(self.handle, Q.data_ptr(), n, int(k), _ptr(anchor),
+                                     float(anchor_weight if anchor is not None else 0.0), out.data_ptr(),
+                                     _ptr(face), _ptr(d2), _stream()), "mesh_knn_project")
+        return (out, face, d2) if want_faces else out
+
     def closest_point_stats(self, Q: torch.Tensor, max_dist: float = math.inf) -> dict:
         """Traversal work for these queries: node visits, triangle tests, hits (totals)."""
         Q = _f32(Q, 3, "Q")

@@ -741,6 +741,114 @@ k_closest_point_packet(Traversal T, const Header *__restrict__ hdr, unsigned int
     if (valid) write_hit(T, h, q, i, face, bary, point, dist2);
 }
 
+// k-NN weighted surface projection: the NearestSurface of temporal tracking
+// (Sec. 3.3, Strategy 1, Eq. 1).  The paper names the method without k or
+// weights; here: the k faces nearest to the query (ties by the lower face
+// id), each giving its closest point p_j at distance d_j, blended with
+// weights 1 / max(d_j, 1e-6 x box diagonal); optionally mixed with an anchor
+// point, (1 - a) v' + a anchor (the periodic re-anchoring to the template).
+// One thread per query; the k best (distance, face) are kept sorted in
+// registers by a fixed compare-and-swap cascade, and a node is pruned when
+// its box is farther than the current k-th distance (with 1e-5 relative
+// slack, so equal-distance faces with lower ids are still reached).
+constexpr int kKnnMax = 8;
+
+__global__ void __launch_bounds__(kQueryBlock, kQueryMinBlocks)
+k_knn_project(Traversal T, const Header *__restrict__ hdr, const float *Q, int64_t nQ, int k,
+              const float *anchor, float anchor_w, float *point, int *face_out, float *d2_out,
+              unsigned int *status) {
+    int64_t i = (int64_t)blockIdx.x * kQueryBlock + threadIdx.x;
+    if (i >= nQ) return;
+    const float4 rlo = hdr->root_lo, rhi = hdr->root_hi;
+    const float dx = rhi.x - rlo.x, dy = rhi.y - rlo.y, dz = rhi.z - rlo.z;
+    const float delta = 1e-6f * sqrtf(dx * dx + dy * dy + dz * dz);
+    const float3 q = make_float3(Q[3 * i], Q[3 * i + 1], Q[3 * i + 2]);   // may alias point
+    float bd[kKnnMax];
+    int bf[kKnnMax], bl[kKnnMax];
+#pragma unroll
+    for (int j = 0; j < kKnnMax; ++j) { bd[j] = INFINITY; bf[j] = 0x7fffffff; bl[j] = -1; }
+    float thr = INFINITY;
+    int cnt = 0;
+    auto consider_leaf = [&](int leaf) {
+        const float4 *t = T.tris + 3 * (size_t)leaf;
+        float4 a = ldg4(t), b = ldg4(t + 1), c = ldg4(t + 2);
+        float u, v, w;
+        float cd = tri_closest(q, xyz(a), xyz(b), xyz(c), b.w != 0.0f, u, v, w);
+        int cf = __float_as_int(a.w), cl = leaf;
+#pragma unroll
+        for (int j = 0; j < kKnnMax; ++j) {
+            if (j < k && (cd < bd[j] || (cd == bd[j] && cf < bf[j]))) {
+                float td = bd[j]; bd[j] = cd; cd = td;
+                int tf = bf[j]; bf[j] = cf; cf = tf;
+                int tl = bl[j]; bl[j] = cl; cl = tl;
+            }
+        }
+        if (cnt < k) ++cnt;
+#pragma unroll
+        for (int j = 0; j < kKnnMax; ++j)
+            if (j == k - 1) thr = bd[j];
+    };
+    if (T.n == 1) {
+        consider_leaf(0);
+    } else if (T.n > 1) {
+        int2 stk[kStackTotal];
+        int sp = 0, node = 0;
+        while (true) {
+            const float4 *r = T.nodes + 4 * (size_t)node;
+            float4 l0 = ldg4(r), l1 = ldg4(r + 1), r0 = ldg4(r + 2), r1 = ldg4(r + 3);
+            float lim = thr * 1.00001f;
+            float dl = box_d2(q, l0, l1), dr = box_d2(q, r0, r1);
+            int cl = __float_as_int(l0.w), cr = __float_as_int(r0.w);
+            if (cl < 0 && dl <= lim) { consider_leaf(-cl - 1); lim = thr * 1.00001f; }
+            if (cr < 0 && dr <= lim) { consider_leaf(-cr - 1); lim = thr * 1.00001f; }
+            bool gl = cl >= 0 && dl <= lim, gr = cr >= 0 && dr <= lim;
+            if (gl && gr) {
+                bool lfirst = dl <= dr;
+                if (sp < kStackTotal) stk[sp++] = make_int2(lfirst ? cr : cl, __float_as_int(lfirst ? dr : dl));
+                else atomicOr(status, (unsigned)MESH_DEV_STACK_OVERFLOW);
+                node = lfirst ? cl : cr;
+                continue;
+            }
+            if (gl) { node = cl; continue; }
+            if (gr) { node = cr; continue; }
+            bool found = false;
+            while (sp > 0) {
+                int2 e = stk[--sp];
+                if (__int_as_float(e.y) <= thr * 1.00001f) { node = e.x; found = true; break; }
+            }
+            if (!found) break;
+        }
+    }
+    float sw = 0.0f, ax = 0.0f, ay = 0.0f, az = 0.0f;
+#pragma unroll
+    for (int j = 0; j < kKnnMax; ++j) {
+        if (j < cnt) {
+            const float4 *t = T.tris + 3 * (size_t)bl[j];
+            float4 a = ldg4(t), b = ldg4(t + 1), c = ldg4(t + 2);
+            float u, v, w;
+            tri_closest(q, xyz(a), xyz(b), xyz(c), b.w != 0.0f, u, v, w);
+            float wt = 1.0f / fmaxf(sqrtf(bd[j]), delta);
+            sw += wt;
+            ax += wt * (u * a.x + v * b.x + w * c.x);
+            ay += wt * (u * a.y + v * b.y + w * c.y);
+            az += wt * (u * a.z + v * b.z + w * c.z);
+        }
+        if (j < k) {
+            if (face_out) face_out[i * k + j] = j < cnt ? bf[j] : -1;
+            if (d2_out) d2_out[i * k + j] = j < cnt ? bd[j] : INFINITY;
+        }
+    }
+    float px = cnt > 0 ? ax / sw : q.x, py = cnt > 0 ? ay / sw : q.y, pz = cnt > 0 ? az / sw : q.z;
+    if (anchor) {
+        px = (1.0f - anchor_w) * px + anchor_w * anchor[3 * i];
+        py = (1.0f - anchor_w) * py + anchor_w * anchor[3 * i + 1];
+        pz = (1.0f - anchor_w) * pz + anchor_w * anchor[3 * i + 2];
+    }
+    point[3 * i] = px;
+    point[3 * i + 1] = py;
+    point[3 * i + 2] = pz;
+}
+
 // Persistent depth-first traversal with dynamic fetch (Aila & Laine 2009):
 // a fixed grid of warps; each lane works through a stream of queries, one
 // node visit per step, and when at least kRefill lanes of the warp are idle
@@ -1131,6 +1239,23 @@ mesh_status mesh_closest_point_hinted(const mesh_bvh *bvh, const float *d_Q, int
     count_launch();
     return check_launch();
 }
+
+mesh_status mesh_knn_project(const mesh_bvh *bvh, const float *d_Q, int64_t nQ, int k,
+                             const float *d_anchor, float anchor_weight, float *d_point,
+                             int32_t *d_face, float *d_dist2, void *stream) {
+    if (!bvh || nQ < 0 || k < 1 || k > kKnnMax || !(anchor_weight >= 0.0f && anchor_weight <= 1.0f))
+        return MESH_ERR_INVALID_ARG;
+    if (nQ == 0) return MESH_OK;
+    if (!d_Q || !d_point) return MESH_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    Header *h = bvh->hdr();
+    k_knn_project<<<grid_for(nQ, kQueryBlock), kQueryBlock, 0, s>>>(
+        traversal_of(bvh, false), h, d_Q, nQ, k, d_anchor, anchor_weight, d_point, d_face, d_dist2,
+        &h->status);
+    count_launch();
+    return check_launch();
+}
+
 
 size_t mesh_chamfer_workspace_bytes(int64_t nSA, int64_t nSB) {
     if (nSA < 0 || nSB < 0) return 0;

@@ -59,7 +59,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="meshgs", choices=["meshgs", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="physics", choices=["physics", "batch", "sequence", "fit"],
+    ap.add_argument("--workload", default="physics",
+                    choices=["physics", "batch", "sequence", "fit", "tracking"],
                     help="physics: the default frame; batch: 64 scenes batched vs per scene; "
                          "sequence: varying-topology conversion; fit: differentiable template fit")
     return ap.parse_args()
@@ -627,6 +628,73 @@ def bench_sequence(args):
     print(json.dumps(line))
 
 
+def bench_tracking(args):
+    """Topology conversion over a 200-frame varying-topology sequence (Sec. 3.3): Strategy 1
+    (temporal tracking, Eq. 1: k = 4 weighted projection of the tracked template onto each
+    rebuilt frame, re-anchored 80/20 to the template projection every 50 frames) and
+    Strategy 2 (template projection, Eq. 2), timed per frame; the drift of each is the
+    Chamfer distance (10k + 10k samples) between the converted mesh and the frame."""
+    import torch
+    from paper_2606_00444_gb300 import MeshBVH, TemporalTracker, Workspace, chamfer, project_template
+    from workloads.isosurface import BlobSequence
+    dev = torch.device("cuda")
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    nfr, N = 200, 96
+    seq = BlobSequence(2000)
+    frames = [seq.mesh(k, N=N) for k in range(nfr + 1)]
+    V0, F0 = frames[0]
+    tg = [(t(v), t(f), t(points_from(v, f, *sample_surface(v, f, N_CD, seed=2300 + k))))
+          for k, (v, f) in enumerate(frames)]
+    maxV = max(len(v) for v, _ in frames)
+    maxF = max(len(f) for _, f in frames)
+    V0d, F0d = t(V0), t(F0)
+    tracker = TemporalTracker(V0d, maxV, maxF, k=4, reanchor_every=50, keep=0.8)
+    target2 = MeshBVH(maxV, maxF, dev)
+    proj = torch.empty_like(V0d)
+    conv = MeshBVH.from_mesh(V0d, F0d)              # the converted (fixed-topology) mesh
+    sf, sb = sample_surface(V0, F0, N_CD, seed=2400)
+    sf, sb = t(sf), t(sb)
+    ws = Workspace(dev)
+    cd = torch.empty(2, dtype=torch.float64, device=dev)
+    ev1, ev2, drift1, drift2 = [], [], [], []
+    for k in range(1, nfr + 1):
+        V, F, SB = tg[k]
+        e = _events(2)
+        e[0].record()
+        tracked = tracker.step(V, F)                   # rebuild + Eq. 1 (+ re-anchor)
+        e[1].record()
+        ev1.append(e)
+        conv.refit(tracked)
+        chamfer(conv, conv.interpolate(sf, sb), tracker.target, SB, ws=ws, out=cd)
+        drift1.append(float(cd.sum().item()))
+        e = _events(2)
+        e[0].record()
+        target2.build(V, F)                            # rebuild + Eq. 2
+        project_template(target2, V0d, out=proj)
+        e[1].record()
+        ev2.append(e)
+        conv.refit(proj)
+        chamfer(conv, conv.interpolate(sf, sb), target2, SB, ws=ws, out=cd)
+        drift2.append(float(cd.sum().item()))
+    torch.cuda.synchronize()
+    skip = min(5, nfr - 1)                             # first frames include one-time set-up
+    ms1 = float(np.mean([e[0].elapsed_time(e[1]) for e in ev1[skip:]]))
+    ms2 = float(np.mean([e[0].elapsed_time(e[1]) for e in ev2[skip:]]))
+    at = [1, 25, 49, 50, 51, 100, 150, 200]
+    line = {"metric": "topology conversion: ms/frame (rebuild + projection) and Chamfer drift",
+            "value": ms1, "unit": "ms/frame", "n_gpus": 1, "steps": nfr, "warmup": skip,
+            "ms_per_step": ms1, "higher_is_better": False, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"varying-topology sequence: marching cubes {N}^3 of a 4-sphere smooth "
+                                   f"union, {nfr} frames; template = frame 0 ({len(V0)} V / {len(F0)} F)",
+                       "k": 4, "reanchor_every": 50, "keep": 0.8,
+                       "target_faces": [int(min(len(f) for _, f in frames)), int(maxF)]},
+            "strategy1_tracking_ms_per_frame": ms1, "strategy2_projection_ms_per_frame": ms2,
+            "chamfer_strategy1": {str(a): drift1[a - 1] for a in at},
+            "chamfer_strategy2": {str(a): drift2[a - 1] for a in at},
+            "chamfer_mean": {"strategy1": float(np.mean(drift1)), "strategy2": float(np.mean(drift2))}}
+    print(json.dumps(line))
+
+
 def bench_fit(args):
     """Differentiable template fit: icosphere 40962 V / 81920 F fitted to the extracted
     target at tau = pi (frame 60) by Adam (lr 1e-3) on symmetric Chamfer over 1M samples
@@ -691,7 +759,8 @@ def main():
     if args.impl == "reference":
         return reference_arm(args, rank, world)
     if args.workload != "physics":
-        return {"batch": bench_batch, "sequence": bench_sequence, "fit": bench_fit}[args.workload](args)
+        return {"batch": bench_batch, "sequence": bench_sequence, "fit": bench_fit,
+                "tracking": bench_tracking}[args.workload](args)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")

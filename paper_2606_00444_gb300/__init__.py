@@ -8,3 +8,4 @@ from .api import (MeshBatch, MeshBVH, Workspace, chamfer, launch_count, morton_o
                   set_query_group, set_traversal)
 from ._abi import MeshError, lib  # noqa: F401
 from . import autograd  # noqa: F401
+from .tracking import TemporalTracker, project_template  # noqa: F401

@@ -100,3 +100,52 @@ def test_knn_project_full_size_tracking_step():
     p = bvh.knn_project(dev(V0), k=4)
     pick = np.random.default_rng(42).choice(V0.shape[0], 1500, replace=False)
     check_knn(V1, F1, V0[pick], 4, p[dev(pick.astype(np.int64))])
+
+
+def oracle_track(frames, V0, k, every, keep):
+    """The same Strategy 1 loop on the oracle (float64)."""
+    tracked = V0.astype(np.float64)
+    out = []
+    for t, (V, F) in enumerate(frames, start=1):
+        if every and t % every == 0:
+            anchor = oracle.closest_point(V, F, V0)["point"]
+            tracked = oracle.knn_project(V, F, tracked, k=k, anchor=anchor, anchor_w=1 - keep)["point"]
+        else:
+            tracked = oracle.knn_project(V, F, tracked, k=k)["point"]
+        out.append(tracked.copy())
+    return out
+
+
+def test_temporal_tracker_follows_the_oracle():
+    """Strategy 1 over 7 frames of a varying-topology sequence with re-anchoring every
+    3 frames (80 % tracked, 20 % template projection): the GPU tracker stays within
+    1e-4 of the diagonal of the oracle's float64 loop for 99 % of the vertices."""
+    from paper_2606_00444_gb300 import TemporalTracker
+    seq = BlobSequence(2000)
+    V0, F0 = seq.mesh(0, N=40)
+    frames = [seq.mesh(t, N=40) for t in range(1, 8)]
+    maxV = max(v.shape[0] for v, _ in frames)
+    maxF = max(f.shape[0] for _, f in frames)
+    tr = TemporalTracker(dev(V0), maxV, maxF, k=4, reanchor_every=3, keep=0.8)
+    ref = oracle_track(frames, V0, 4, 3, 0.8)
+    diag = oracle.mesh_diag(V0, F0)
+    for t, (V, F) in enumerate(frames):
+        got = host(tr.step(dev(V), dev(F))).astype(np.float64)
+        err = np.linalg.norm(got - ref[t], axis=1)
+        assert np.quantile(err, 0.99) <= 1e-4 * diag, (t, np.quantile(err, 0.99))
+    assert tr.target.status()[0] & ~0x4 == 0
+
+
+def test_template_projection_is_the_closest_point():
+    from paper_2606_00444_gb300 import project_template
+    seq = BlobSequence(2000)
+    V0, F0 = seq.mesh(0, N=40)
+    V, F = seq.mesh(5, N=40)
+    bvh = MeshBVH.from_mesh(dev(V), dev(F))
+    got = host(project_template(bvh, dev(V0))).astype(np.float64)
+    ref = oracle.closest_point(V, F, V0)
+    diag = oracle.mesh_diag(V, F)
+    # the distance is unique; the point may differ where two faces are equally near
+    dist = np.linalg.norm(got - V0, axis=1)
+    assert np.abs(dist - np.sqrt(ref["d2"])).max() <= 1e-5 * diag
+    assert np.mean(np.linalg.norm(got - ref["point"], axis=1) <= 1e-5 * diag) > 0.99

@@ -76,6 +76,8 @@ def lib():
         L.orc_knn_project.restype = None
         L.orc_knn_project.argtypes = [F64P, I32P, I64, F64P, I64, C.c_int, C.c_void_p, C.c_double,
                                       F64P, I32P, F64P]
+        L.orc_signed_distance.restype = None
+        L.orc_signed_distance.argtypes = [F64P, I32P, I64, F64P, I64, F64P, I32P]
         _lib = L
     return _lib
 
@@ -245,3 +247,14 @@ def knn_project(V, F, Q, k=4, anchor=None, anchor_w=0.0):
     lib().orc_knn_project(V, F, F.shape[0], Q, nQ, int(k), None if A is None else A.ctypes.data,
                           float(anchor_w), point, face, d2)
     return dict(point=point, face=face, d2=d2)
+
+
+def signed_distance(V, F, Q):
+    """Signed NearestSurface distance (inside negative) by angle-weighted pseudo-normals;
+    dict(sd, face).  Assumes a closed, outward-oriented manifold mesh."""
+    V, F, Q = _f64(V), _i32(F), _f64(Q).reshape(-1, 3)
+    nQ = Q.shape[0]
+    sd = np.empty(nQ)
+    face = np.empty(nQ, np.int32)
+    lib().orc_signed_distance(V, F, F.shape[0], Q, nQ, sd, face)
+    return dict(sd=sd, face=face)

@@ -724,3 +724,75 @@ void orc_knn_project(const double *V, const int32_t *F, int64_t nF, const double
         }
     }
 }
+
+/* ------------------------------------------------------------------ */
+/* Signed distance for contact (inside negative), by angle-weighted      */
+/* pseudo-normals (Baerentzen & Aanaes 2005): the nearest point c of the */
+/* NearestSurface query lies in a face interior, on an edge or at a      */
+/* vertex (one / two barycentric weights exactly zero); its normal is    */
+/* the face's unit normal, the sum of the two unit normals of the faces  */
+/* sharing the edge, or the sum over the faces around the vertex of the  */
+/* unit normal times the face's angle there.  sign = sign((q - c) . N),  */
+/* + when zero.  Assumes a closed, consistently outward-oriented         */
+/* (counter-clockwise) manifold mesh; an edge with one face uses that    */
+/* face's normal alone.                                                  */
+/* ------------------------------------------------------------------ */
+static d3 vtx(const double *V, int32_t i) { return ld3(V + 3 * (int64_t)i); }
+
+static d3 face_unit_normal(const double *V, const int32_t *F, int64_t f) {
+    d3 a = vtx(V, F[3 * f]), b = vtx(V, F[3 * f + 1]), c = vtx(V, F[3 * f + 2]);
+    d3 n = cross(sub(b, a), sub(c, a));
+    double l = norm(n);
+    return l > 0.0 ? scl(n, 1.0 / l) : mk(0.0, 0.0, 0.0);
+}
+
+void orc_signed_distance(const double *V, const int32_t *F, int64_t nF, const double *Q, int64_t nQ,
+                         double *sd, int32_t *face) {
+    double *bary = (double *)malloc(sizeof(double) * 3 * (size_t)(nQ > 0 ? nQ : 1));
+    double *point = (double *)malloc(sizeof(double) * 3 * (size_t)(nQ > 0 ? nQ : 1));
+    double *d2 = (double *)malloc(sizeof(double) * (size_t)(nQ > 0 ? nQ : 1));
+    orc_closest_point_mesh(V, F, nF, Q, nQ, INFINITY, face, bary, point, d2, NULL);
+    for (int64_t q = 0; q < nQ; ++q) {
+        int32_t f = face[q];
+        if (f < 0) { sd[q] = INFINITY; continue; }
+        const double *b = bary + 3 * q;
+        int zeros = (b[0] == 0.0) + (b[1] == 0.0) + (b[2] == 0.0);
+        d3 N = mk(0.0, 0.0, 0.0);
+        if (zeros == 0) {
+            N = face_unit_normal(V, F, f);
+        } else if (zeros == 1) {
+            /* the edge opposite the zero weight */
+            int k = b[0] == 0.0 ? 0 : (b[1] == 0.0 ? 1 : 2);
+            int32_t x = F[3 * f + (k + 1) % 3], y = F[3 * f + (k + 2) % 3];
+            N = face_unit_normal(V, F, f);
+            for (int64_t g = 0; g < nF; ++g) {
+                if (g == f) continue;
+                int hx = 0, hy = 0;
+                for (int j = 0; j < 3; ++j) { hx |= F[3 * g + j] == x; hy |= F[3 * g + j] == y; }
+                if (hx && hy) { N = add(N, face_unit_normal(V, F, g)); break; }
+            }
+        } else {
+            int k = b[0] != 0.0 ? 0 : (b[1] != 0.0 ? 1 : 2);
+            int32_t v = F[3 * f + k];
+            for (int64_t g = 0; g < nF; ++g) {
+                for (int j = 0; j < 3; ++j) {
+                    if (F[3 * g + j] != v) continue;
+                    d3 p0 = vtx(V, v), p1 = vtx(V, F[3 * g + (j + 1) % 3]), p2 = vtx(V, F[3 * g + (j + 2) % 3]);
+                    d3 e1 = sub(p1, p0), e2 = sub(p2, p0);
+                    double l1 = norm(e1), l2 = norm(e2);
+                    if (l1 == 0.0 || l2 == 0.0) continue;
+                    double cs = dot(e1, e2) / (l1 * l2);
+                    if (cs > 1.0) cs = 1.0;
+                    if (cs < -1.0) cs = -1.0;
+                    N = add(N, scl(face_unit_normal(V, F, g), acos(cs)));
+                }
+            }
+        }
+        d3 r = sub(ld3(Q + 3 * q), ld3(point + 3 * q));
+        double s = dot(r, N) >= 0.0 ? 1.0 : -1.0;
+        sd[q] = s * sqrt(d2[q]);
+    }
+    free(bary);
+    free(point);
+    free(d2);
+}

@@ -57,6 +57,7 @@ typedef enum {
                                           offending element was skipped or clamped to 0 */
 #define MESH_DEV_STACK_OVERFLOW  0x2u  /* traversal stack exhausted (cannot happen for nF < 2^33) */
 #define MESH_DEV_DEGENERATE      0x4u  /* a Gaussian sat on a zero-area face (not an error)       */
+#define MESH_DEV_NONMANIFOLD     0x8u  /* an edge shared by more than two faces (signed distance) */
 
 typedef struct mesh_bvh mesh_bvh;   /* opaque host handle describing device storage */
 
@@ -77,6 +78,9 @@ typedef struct {
     size_t off_tris;     /* 3 x float4 per leaf: (v0, face id bits) (v1, 0) (v2, 0)           */
     size_t off_rend;     /* int32 [max_faces]   far end of internal node i's leaf range        */
     size_t off_iperm;    /* int32 [max_faces]   leaf of face f (inverse of perm)               */
+    size_t off_adj;      /* int32 [max_faces][3] face across the edge opposite vertex k, or -1  */
+    size_t off_fnorm;    /* float4 [max_faces]  unit face normals (signed distance)            */
+    size_t off_vnorm;    /* float4 [max_verts]  angle-weighted vertex pseudo-normals          */
     size_t off_xlist;    /* bottom-up scratch, per block of 1024 leaves: edge records (box of a
                             child whose parent's leaf range crosses blocks, 2048 x 32 B per
                             block), crossing nodes int32x4 [max_faces] (node, prefix length,
@@ -196,6 +200,26 @@ mesh_status mesh_closest_point_hinted(const mesh_bvh *bvh, const float *d_Q, int
 mesh_status mesh_knn_project(const mesh_bvh *bvh, const float *d_Q, int64_t nQ, int k,
                              const float *d_anchor, float anchor_weight, float *d_point,
                              int32_t *d_face, float *d_dist2, void *stream);
+
+/* Workspace bytes for mesh_signed_distance's first call after a build (the
+ * face-adjacency table over 3 nF half-edges); 0 for nF out of range. */
+size_t mesh_signed_workspace_bytes(int64_t nF);
+
+/* Signed NearestSurface distance for contact (inside negative), for
+ * penetration depth: as mesh_closest_point (same face, weights, point, tie
+ * rule and cutoff), plus d_sdist[i] = sign * distance with the sign of
+ * (q - c) . N, N the angle-weighted pseudo-normal (Baerentzen & Aanaes 2005)
+ * of the face, edge or vertex the nearest point c lies on; +inf beyond
+ * max_dist.  The mesh must be closed, manifold and consistently
+ * counter-clockwise seen from outside (an edge with one face uses that
+ * face's normal; an edge of three or more faces sets MESH_DEV_NONMANIFOLD).
+ * The first call after a build derives the face adjacency with d_ws
+ * (mesh_signed_workspace_bytes(nF) bytes, 256-byte aligned; NULL is fine on
+ * later calls) and every call recomputes the normals from the current
+ * vertex buffer (two extra launches).  d_face, d_bary, d_point may be NULL. */
+mesh_status mesh_signed_distance(mesh_bvh *bvh, const float *d_Q, int64_t nQ, float max_dist,
+                                 void *d_ws, size_t ws_bytes, int32_t *d_face, float *d_bary,
+                                 float *d_point, float *d_sdist, void *stream);
 
 /* Work counters of the one-thread depth-first traversal for these queries:
  * d_counts[0] = node visits (each reads one 64-byte record holding two child

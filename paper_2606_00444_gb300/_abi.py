@@ -20,13 +20,14 @@ MESH_ERR_DEVICE = 4
 DEV_INDEX_RANGE = 0x1
 DEV_STACK_OVERFLOW = 0x2
 DEV_DEGENERATE = 0x4
+DEV_NONMANIFOLD = 0x8
 
 
 class Layout(C.Structure):
     _fields_ = [("n_faces", I64), ("n_verts", I64), ("max_faces", I64), ("max_verts", I64),
                 ("off_header", SZ), ("off_verts", SZ), ("off_faces", SZ), ("off_keys", SZ),
                 ("off_perm", SZ), ("off_nodes", SZ), ("off_parent", SZ), ("off_tris", SZ),
-                ("off_rend", SZ), ("off_iperm", SZ), ("off_xlist", SZ), ("storage_bytes", SZ)]
+                ("off_rend", SZ), ("off_iperm", SZ), ("off_adj", SZ), ("off_fnorm", SZ), ("off_vnorm", SZ), ("off_xlist", SZ), ("storage_bytes", SZ)]
 
 
 class BatchLayout(C.Structure):
@@ -54,6 +55,8 @@ SIGNATURES = {
     "mesh_closest_point_hinted": (C.c_int, [VP, VP, I64, C.c_float, VP, VP, VP, VP, VP, VP]),
     "mesh_closest_point_stats": (C.c_int, [VP, VP, I64, C.c_float, VP, VP]),
     "mesh_knn_project": (C.c_int, [VP, VP, I64, C.c_int, VP, C.c_float, VP, VP, VP, VP]),
+    "mesh_signed_workspace_bytes": (SZ, [I64]),
+    "mesh_signed_distance": (C.c_int, [VP, VP, I64, C.c_float, VP, SZ, VP, VP, VP, VP, VP]),
     "mesh_set_query_group": (C.c_int, [C.c_int]),
     "mesh_set_traversal": (C.c_int, [C.c_int]),
     "mesh_bvh_set_query_config": (C.c_int, [VP, C.c_int, C.c_int]),

@@ -181,6 +181,22 @@ class MeshBVH:
                                      _ptr(face), _ptr(d2), _stream()), "mesh_knn_project")
         return (out, face, d2) if want_faces else out
 
+    def signed_distance(self, Q: torch.Tensor, max_dist: float = math.inf, out: dict | None = None) -> dict:
+        """Signed NearestSurface distance (inside negative; mesh_signed_distance):
+        dict(face, bary, point, sdist)."""
+        Q = _f32(Q, 3, "Q")
+        n = Q.shape[0]
+        out = {} if out is None else out
+        out.setdefault("face", torch.empty(n, dtype=torch.int32, device=Q.device))
+        out.setdefault("bary", torch.empty(n, 3, device=Q.device))
+        out.setdefault("point", torch.empty(n, 3, device=Q.device))
+        out.setdefault("sdist", torch.empty(n, device=Q.device))
+        ws = self._ws.get(lib().mesh_signed_workspace_bytes(max(self.n_faces, 1)))
+        check(lib().mesh_signed_distance(self.handle, Q.data_ptr(), n, float(max_dist), ws.data_ptr(),
+                                         ws.numel(), _ptr(out["face"]), _ptr(out["bary"]), _ptr(out["point"]),
+                                         out["sdist"].data_ptr(), _stream()), "mesh_signed_distance")
+        return out
+
     def closest_point_stats(self, Q: torch.Tensor, max_dist: float = math.inf) -> dict:
         """Traversal work for these queries: node visits, triangle tests, hits (totals)."""
         Q = _f32(Q, 3, "Q")

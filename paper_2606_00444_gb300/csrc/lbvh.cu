@@ -986,6 +986,9 @@ static mesh_bvh_layout storage_layout(int64_t maxV, int64_t maxF) {
     L.off_tris = take(48 * f);
     L.off_rend = take(4 * f);
     L.off_iperm = take(4 * f);
+    L.off_adj = take(12 * f);
+    L.off_fnorm = take(16 * f);
+    L.off_vnorm = take(16 * v);
     L.off_xlist = take(xlist_bytes(f));
     L.storage_bytes = off;
     return L;
@@ -1025,6 +1028,7 @@ mesh_status mesh_bvh_create(void *d_storage, size_t storage_bytes, int64_t max_v
     h->L.n_verts = 0;
     h->cfg_lanes = -1;
     h->cfg_variant = -1;
+    h->adj_ready = false;
     *out = h;
     return MESH_OK;
 }
@@ -1107,6 +1111,7 @@ mesh_status mesh_build_lbvh(mesh_bvh *bvh, const float *d_V, int64_t nV, const i
     cudaStream_t s = (cudaStream_t)stream;
     bvh->L.n_verts = nV;
     bvh->L.n_faces = nF;
+    bvh->adj_ready = false;
     int n = (int)nF;
     cudaMemsetAsync(bvh->hdr(), 0, sizeof(Header), s);
     if (nV > 0) {

@@ -849,6 +849,52 @@ k_knn_project(Traversal T, const Header *__restrict__ hdr, const float *Q, int64
     point[3 * i + 2] = pz;
 }
 
+// NearestSurface plus the sign of (q - c) . N, N the pseudo-normal of the
+// feature the nearest point lies on: face interior (no zero weight), edge
+// opposite vertex k (weight k zero), vertex (two zero weights).
+__global__ void __launch_bounds__(kQueryBlock, kQueryMinBlocks)
+k_signed_distance(Traversal T, const Header *__restrict__ hdr, unsigned int *status,
+                  const float *__restrict__ Q, int64_t nQ, float maxd2, const int4 *__restrict__ faces,
+                  const int *__restrict__ adj, const float4 *__restrict__ fnorm,
+                  const float4 *__restrict__ vnorm, int *face, float *bary, float *point, float *sdist) {
+    __shared__ int2 stk[kStackShared][kQueryBlock];
+    int64_t i = (int64_t)blockIdx.x * kQueryBlock + threadIdx.x;
+    if (i >= nQ) return;
+    T.tau = traversal_tau(hdr);
+    float3 q = make_float3(Q[3 * i], Q[3 * i + 1], Q[3 * i + 2]);
+    Hit h = nearest<kQueryBlock>(T, q, maxd2, stk, status);
+    write_hit(T, h, q, i, face, bary, point, nullptr);
+    if (h.leaf < 0) { sdist[i] = INFINITY; return; }
+    const float4 *t = T.tris + 3 * (size_t)h.leaf;
+    float4 a = ldg4(t), b = ldg4(t + 1), c = ldg4(t + 2);
+    float u, v, w;
+    tri_closest(q, xyz(a), xyz(b), xyz(c), b.w != 0.0f, u, v, w);
+    if (weights_need_f64(xyz(a), xyz(b), xyz(c), h.d2))
+        tri_weights_f64(q, xyz(a), xyz(b), xyz(c), b.w != 0.0f, u, v, w);
+    int f = h.face;
+    int zeros = (u == 0.0f) + (v == 0.0f) + (w == 0.0f);
+    float4 N;
+    if (zeros == 0) {
+        N = fnorm[f];
+    } else if (zeros == 1) {
+        int k = u == 0.0f ? 0 : (v == 0.0f ? 1 : 2);
+        N = fnorm[f];
+        int g = adj[3 * f + k];
+        if (g >= 0) { float4 m = fnorm[g]; N.x += m.x; N.y += m.y; N.z += m.z; }
+    } else {
+        int4 fv = faces[f];
+        int vid = u != 0.0f ? fv.x : (v != 0.0f ? fv.y : fv.z);
+        N = vnorm[vid];
+    }
+    float cx = u * a.x + v * b.x + w * c.x, cy = u * a.y + v * b.y + w * c.y, cz = u * a.z + v * b.z + w * c.z;
+    float dn = (q.x - cx) * N.x + (q.y - cy) * N.y + (q.z - cz) * N.z;
+    sdist[i] = (dn >= 0.0f ? 1.0f : -1.0f) * sqrtf(h.d2);
+}
+
+mesh_status launch_signed_query(const mesh_bvh *bvh, const float *d_Q, int64_t nQ, float max_dist,
+                                int32_t *d_face, float *d_bary, float *d_point, float *d_sdist,
+                                cudaStream_t s);
+
 // Persistent depth-first traversal with dynamic fetch (Aila & Laine 2009):
 // a fixed grid of warps; each lane works through a stream of queries, one
 // node visit per step, and when at least kRefill lanes of the warp are idle
@@ -1165,6 +1211,19 @@ static int pick_group(int64_t nQ) {
     int G = 1;
     while (G < 32 && nQ * G < target) G <<= 1;
     return G;
+}
+
+
+mesh_status launch_signed_query(const mesh_bvh *bvh, const float *d_Q, int64_t nQ, float max_dist,
+                                int32_t *d_face, float *d_bary, float *d_point, float *d_sdist,
+                                cudaStream_t s) {
+    float maxd2 = isinf(max_dist) ? INFINITY : max_dist * max_dist;
+    Header *h = bvh->hdr();
+    k_signed_distance<<<grid_for(nQ, kQueryBlock), kQueryBlock, 0, s>>>(
+        traversal_of(bvh, isinf(max_dist)), h, &h->status, d_Q, nQ, maxd2, bvh->faces(), bvh->adj(),
+        bvh->fnorm(), bvh->vnorm(), d_face, d_bary, d_point, d_sdist);
+    count_launch();
+    return check_launch();
 }
 
 }  // namespace meshgs

@@ -258,3 +258,23 @@ def signed_distance(V, F, Q):
     face = np.empty(nQ, np.int32)
     lib().orc_signed_distance(V, F, F.shape[0], Q, nQ, sd, face)
     return dict(sd=sd, face=face)
+
+
+def emd(A, B):
+    """Earth Mover's Distance between two equal-size point sets (Sec. 4.2's EMD on
+    sampled points): the minimum over bijections sigma of the mean Euclidean distance
+    |a_i - b_sigma(i)|, by exact linear assignment (scipy's solver as the library step).
+    Returns (emd, sigma)."""
+    from scipy.optimize import linear_sum_assignment
+    from scipy.spatial.distance import cdist
+    A = _f64(A).reshape(-1, 3)
+    B = _f64(B).reshape(-1, 3)
+    if A.shape[0] != B.shape[0]:
+        raise ValueError("EMD needs equal-size point sets")
+    if A.shape[0] == 0:
+        return 0.0, np.zeros(0, np.int64)
+    C = cdist(A, B)
+    r, c = linear_sum_assignment(C)
+    sigma = np.empty(A.shape[0], np.int64)
+    sigma[r] = c
+    return float(C[r, c].mean()), sigma

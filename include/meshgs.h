@@ -221,6 +221,23 @@ mesh_status mesh_signed_distance(mesh_bvh *bvh, const float *d_Q, int64_t nQ, fl
                                  void *d_ws, size_t ws_bytes, int32_t *d_face, float *d_bary,
                                  float *d_point, float *d_sdist, void *stream);
 
+/* Workspace bytes of mesh_emd for n points per set; 0 for n out of range. */
+size_t mesh_emd_workspace_bytes(int64_t n);
+
+/* Earth Mover's Distance between point sets A and B of n points each
+ * (Sec. 4.2's EMD on sampled points): the minimum over bijections sigma of
+ * the mean |a_i - b_sigma(i)|, by the auction algorithm with epsilon scaling.
+ * The result is within eps_rel x (box diagonal of A and B) of the exact
+ * minimum (an epsilon-optimal assignment).  d_out[0] = the mean (float64);
+ * d_assign (NULL = not written) = sigma, int32 [n].  Synchronous: the host
+ * runs the auction rounds on `stream` and reads a counter every 16 rounds,
+ * so the call returns when the result is final.  max_iters bounds the rounds
+ * (MESH_ERR_DEVICE if exceeded); *iters_out (NULL = not written) gets the
+ * rounds used.  d_ws: mesh_emd_workspace_bytes(n) bytes, 256-byte aligned. */
+mesh_status mesh_emd(const float *d_A, const float *d_B, int64_t n, float eps_rel, int64_t max_iters,
+                     void *d_ws, size_t ws_bytes, double *d_out, int32_t *d_assign,
+                     int64_t *iters_out, void *stream);
+
 /* Work counters of the one-thread depth-first traversal for these queries:
  * d_counts[0] = node visits (each reads one 64-byte record holding two child
  * boxes), d_counts[1] = triangle tests, d_counts[2] = queries with a face

@@ -57,6 +57,8 @@ SIGNATURES = {
     "mesh_knn_project": (C.c_int, [VP, VP, I64, C.c_int, VP, C.c_float, VP, VP, VP, VP]),
     "mesh_signed_workspace_bytes": (SZ, [I64]),
     "mesh_signed_distance": (C.c_int, [VP, VP, I64, C.c_float, VP, SZ, VP, VP, VP, VP, VP]),
+    "mesh_emd_workspace_bytes": (SZ, [I64]),
+    "mesh_emd": (C.c_int, [VP, VP, I64, C.c_float, I64, VP, SZ, VP, VP, C.POINTER(I64), VP]),
     "mesh_set_query_group": (C.c_int, [C.c_int]),
     "mesh_set_traversal": (C.c_int, [C.c_int]),
     "mesh_bvh_set_query_config": (C.c_int, [VP, C.c_int, C.c_int]),

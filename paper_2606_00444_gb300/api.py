@@ -475,6 +475,26 @@ def chamfer(A: MeshBVH, SA: torch.Tensor, B: MeshBVH, SB: torch.Tensor, per_samp
     return (out, ps) if per_sample else out
 
 
+def emd(A: torch.Tensor, B: torch.Tensor, eps_rel: float = 1e-5, max_iters: int = 1_000_000,
+        ws: Workspace | None = None, want_assignment: bool = False):
+    """Earth Mover's Distance of two equal-size point sets (mesh_emd): a float64
+    scalar tensor within eps_rel x box diagonal of the exact minimum mean distance;
+    with want_assignment also the bijection (int32) and the auction rounds used."""
+    A = _f32(A, 3, "A")
+    B = _f32(B, 3, "B")
+    if A.shape[0] != B.shape[0]:
+        raise ValueError("EMD needs equal-size point sets")
+    n = A.shape[0]
+    ws = Workspace(A.device) if ws is None else ws
+    buf = ws.get(lib().mesh_emd_workspace_bytes(n))
+    out = torch.empty(1, dtype=torch.float64, device=A.device)
+    sigma = torch.empty(n, dtype=torch.int32, device=A.device) if want_assignment else None
+    it = C.c_int64(0)
+    check(lib().mesh_emd(A.data_ptr(), B.data_ptr(), n, float(eps_rel), int(max_iters), buf.data_ptr(),
+                         buf.numel(), out.data_ptr(), _ptr(sigma), C.byref(it), _stream()), "mesh_emd")
+    return (out[0], sigma, it.value) if want_assignment else out[0]
+
+
 def morton_order(P: torch.Tensor, ws: Workspace | None = None) -> torch.Tensor:
     """int32 permutation sorting the points [n, 3] by Morton key (see mesh_morton_order)."""
     P = _f32(P, 3, "P")

@@ -133,6 +133,107 @@ __global__ void k_emd_resolve(int n, float *price, int *owner, int *assign, unsi
     price[j] = __uint_as_float((unsigned)(b >> 32));
 }
 
+// Gauss-Seidel tail: once few points are unassigned, one block finishes the
+// phase, one bid at a time, with the other set and its prices held in shared
+// memory (n <= kTailMaxN): the unassigned points are queued in index order,
+// each bid is a block-wide scan for the best and second-best object, and an
+// evicted owner joins the back of the queue.  At most max_bids bids; *active
+// gets the points still queued.
+constexpr int kTailThreads = 1024;
+constexpr int kTailQueue = 256;
+
+__device__ __forceinline__ void block_best2(float &b1, int &j1, float &b2, float *r1, float *r2, int *rj) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        float o1 = __shfl_xor_sync(0xffffffffu, b1, o), o2 = __shfl_xor_sync(0xffffffffu, b2, o);
+        int oj = __shfl_xor_sync(0xffffffffu, j1, o);
+        merge2(b1, j1, b2, o1, oj, o2);
+    }
+    if (lane == 0) { r1[wid] = b1; r2[wid] = b2; rj[wid] = j1; }
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = blockDim.x >> 5;
+        b1 = lane < nw ? r1[lane] : -INFINITY;
+        b2 = lane < nw ? r2[lane] : -INFINITY;
+        j1 = lane < nw ? rj[lane] : 0x7fffffff;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            float o1 = __shfl_xor_sync(0xffffffffu, b1, o), o2 = __shfl_xor_sync(0xffffffffu, b2, o);
+            int oj = __shfl_xor_sync(0xffffffffu, j1, o);
+            merge2(b1, j1, b2, o1, oj, o2);
+        }
+        if (lane == 0) { r1[0] = b1; r2[0] = b2; rj[0] = j1; }
+    }
+    __syncthreads();
+    b1 = r1[0]; b2 = r2[0]; j1 = rj[0];
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kTailThreads)
+k_emd_tail(int n, const float4 *__restrict__ A4, const float4 *__restrict__ B4, float *price, int *owner,
+           int *assign, float eps, int max_bids, unsigned *active) {
+    extern __shared__ float4 tsm[];
+    float4 *sB = tsm;
+    float *sp = reinterpret_cast<float *>(sB + n);
+    __shared__ int queue[kTailQueue];
+    __shared__ float r1[32], r2[32];
+    __shared__ int rj[32], s_cnt[32];
+    __shared__ int s_len;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    for (int j = tid; j < n; j += kTailThreads) { sB[j] = B4[j]; sp[j] = price[j]; }
+    if (tid == 0) s_len = 0;
+    __syncthreads();
+    // unassigned points in index order (up to the queue's size)
+    for (int c0 = 0; c0 < n; c0 += kTailThreads) {
+        int i = c0 + tid;
+        bool un = i < n && assign[i] < 0;
+        unsigned ball = __ballot_sync(0xffffffffu, un);
+        if (lane == 0) s_cnt[wid] = __popc(ball);
+        __syncthreads();
+        int before = s_len;
+        for (int w = 0; w < wid; ++w) before += s_cnt[w];
+        int pos = before + __popc(ball & ((1u << lane) - 1u));
+        if (un && pos < kTailQueue) queue[pos] = i;
+        __syncthreads();
+        if (tid == 0) {
+            int tot = s_len;
+            for (int w = 0; w < (kTailThreads >> 5); ++w) tot += s_cnt[w];
+            s_len = min(tot, kTailQueue);
+        }
+        __syncthreads();
+    }
+    int head = 0, len = s_len;
+    for (int bids = 0; bids < max_bids && len > 0; ++bids) {
+        const int i = queue[head % kTailQueue];
+        const float4 a = A4[i];
+        float b1 = -INFINITY, b2 = -INFINITY;
+        int j1 = 0x7fffffff;
+        for (int j = tid; j < n; j += kTailThreads) {
+            float4 b = sB[j];
+            float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+            merge2(b1, j1, b2, -sqrtf(dx * dx + dy * dy + dz * dz) - sp[j], j, -INFINITY);
+        }
+        block_best2(b1, j1, b2, r1, r2, rj);
+        int old = owner[j1];                          // read by every thread, written by thread 0 below
+        __syncthreads();
+        if (tid == 0) {
+            sp[j1] += (b2 == -INFINITY ? 0.0f : b1 - b2) + eps;
+            owner[j1] = i;
+            assign[i] = j1;
+            if (old >= 0) {
+                assign[old] = -1;
+                queue[(head + len) % kTailQueue] = old;
+            }
+        }
+        ++head;
+        if (old < 0) --len;
+        __syncthreads();
+    }
+    for (int j = tid; j < n; j += kTailThreads) price[j] = sp[j];
+    if (tid == 0) *active = (unsigned)len;
+}
+
 // Mean cost of the assignment in float64, summed in a fixed order.
 __global__ void __launch_bounds__(kEmdBlock)
 k_emd_cost(int n, const float4 *__restrict__ A4, const float4 *__restrict__ B4, const int *__restrict__ assign,
@@ -246,6 +347,18 @@ mesh_status mesh_emd(const float *d_A, const float *d_B, int64_t n, float eps_re
     if (!(C > 0.0)) C = 1.0;
     const double eps_final = eps_rel * C;
     const unsigned bid_grid = grid_for(N, kEmdWarps);
+    static int64_t tail_max = -1;                    // largest n whose set fits the tail's shared memory
+    auto tail_smem = [](int m) { return (size_t)m * (sizeof(float4) + sizeof(float)); };
+    if (tail_max < 0) {
+        int dev = 0, optin = 0;
+        tail_max = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess &&
+            optin > 4096 && cudaFuncSetAttribute(k_emd_tail, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 optin - 4096) == cudaSuccess)
+            tail_max = (optin - 4096) / (int64_t)(sizeof(float4) + sizeof(float));
+        cudaGetLastError();
+    }
     int64_t iters = 0;
     for (double eps = C / 10.0;; eps /= 8.0) {
         if (eps < eps_final) eps = eps_final;
@@ -266,6 +379,18 @@ mesh_status mesh_emd(const float *d_A, const float *d_B, int64_t n, float eps_re
                 cudaStreamSynchronize(s) != cudaSuccess)
                 return MESH_ERR_CUDA;
             done = act == 0;
+            if (!done && act <= (unsigned)kTailQueue && n <= tail_max) {
+                int64_t left = max_iters > iters ? max_iters - iters : 1;
+                int cap = (int)(left < (int64_t)(1 << 24) ? left : (int64_t)(1 << 24));
+                k_emd_tail<<<1, kTailThreads, tail_smem(N), s>>>(N, w.A4, w.B4, w.price, w.owner, w.assign,
+                                                                 (float)eps, cap, w.active);
+                count_launch();
+                if (cudaMemcpyAsync(&act, w.active, sizeof(unsigned), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                    cudaStreamSynchronize(s) != cudaSuccess)
+                    return MESH_ERR_CUDA;
+                done = act == 0;
+                iters += 1;
+            }
             if (!done && iters >= max_iters) {
                 if (iters_out) *iters_out = iters;
                 return MESH_ERR_DEVICE;

@@ -78,6 +78,10 @@ def lib():
                                       F64P, I32P, F64P]
         L.orc_signed_distance.restype = None
         L.orc_signed_distance.argtypes = [F64P, I32P, I64, F64P, I64, F64P, I32P]
+        L.orc_gs_render.restype = None
+        L.orc_gs_render.argtypes = [F64P, F64P, F64P, F64P, F64P, I64, F64P, F64P, C.c_double,
+                                    C.c_double, C.c_double, C.c_double, C.c_int, C.c_int, C.c_double,
+                                    F64P, F64P, F64P]
         _lib = L
     return _lib
 
@@ -278,3 +282,18 @@ def emd(A, B):
     sigma = np.empty(A.shape[0], np.int64)
     sigma[r] = c
     return float(C[r, c].mean()), sigma
+
+
+def gs_render(mu, quat, scale, opacity, color, Rc, tc, fx, fy, cx, cy, W, H, near=0.01,
+              background=(0.0, 0.0, 0.0)):
+    """Gaussian splatting render (forward equations of 3DGS, 16 x 16 tiles): image [H, W, 3]
+    and final transmittance [H, W], float64."""
+    mu, quat, scale = _f64(mu).reshape(-1, 3), _f64(quat).reshape(-1, 4), _f64(scale).reshape(-1, 3)
+    opacity, color = _f64(opacity).reshape(-1), _f64(color).reshape(-1, 3)
+    n = mu.shape[0]
+    image = np.empty((H, W, 3))
+    trans = np.empty((H, W))
+    lib().orc_gs_render(mu, quat, scale, opacity, color, n, _f64(Rc).reshape(3, 3), _f64(tc).reshape(3),
+                        float(fx), float(fy), float(cx), float(cy), int(W), int(H), float(near),
+                        _f64(background).reshape(3), image, trans)
+    return image, trans

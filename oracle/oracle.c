@@ -796,3 +796,126 @@ void orc_signed_distance(const double *V, const int32_t *F, int64_t nF, const do
     free(point);
     free(d2);
 }
+
+/* ------------------------------------------------------------------ */
+/* Gaussian splatting render of the face-bound Gaussians (Sec. 3.2's     */
+/* R_render; the forward equations of 3D Gaussian splatting, Kerbl et    */
+/* al. 2023).  Camera: x_c = Rc x + tc, pixel (u, v) = (fx x_c/z_c + cx, */
+/* fy y_c/z_c + cy); a pixel (px, py) samples the point (px, py).        */
+/* Per Gaussian: Sigma = M M^T, M = R(q) diag(s); Sigma_c = Rc Sigma     */
+/* Rc^T; Sigma_2 = J Sigma_c J^T + 0.3 I with the projection's Jacobian  */
+/* J; conic = Sigma_2^-1; radius r = ceil(3 sqrt(lambda_max)); tiles of  */
+/* 16 x 16 pixels: [floor((u - r)/16), floor((u + r + 15)/16)) clamped   */
+/* to the grid, likewise in y.  z_c <= near, det <= 0 or no tile: culled.*/
+/* A pixel blends, front to back by z_c (ties: lower index), the        */
+/* Gaussians whose tile range holds its tile:                            */
+/*   p = -0.5 (a dx^2 + c dy^2) - b dx dy, d = (u - px, v - py);         */
+/*   skip if p > 0; alpha = min(0.99, o e^p); skip if alpha < 1/255;     */
+/*   stop if T (1 - alpha) < 1e-4; else C += color alpha T,              */
+/*   T *= 1 - alpha.  Result C + T background; T is returned too.        */
+/* ------------------------------------------------------------------ */
+typedef struct { double u, v, ca, cb, cc, z; int r, x0, x1, y0, y1, ok; } orc_splat;
+
+
+static const orc_splat *g_sp_sort;
+static int cmp_splat(const void *x, const void *y) {
+    int i = *(const int *)x, j = *(const int *)y;
+    double a = g_sp_sort[i].z, b = g_sp_sort[j].z;
+    if (a < b) return -1;
+    if (a > b) return 1;
+    return (i > j) - (i < j);
+}
+
+void orc_gs_render(const double *mu, const double *quat, const double *scale, const double *opac,
+                   const double *color, int64_t n, const double *Rc, const double *tc, double fx,
+                   double fy, double cx, double cy, int W, int H, double near_z, const double *bg,
+                   double *image /* [H][W][3] */, double *trans /* [H][W] */) {
+    orc_splat *sp = (orc_splat *)calloc((size_t)(n > 0 ? n : 1), sizeof(orc_splat));
+    int *order = (int *)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+    int gx = (W + 15) / 16, gy = (H + 15) / 16;
+    for (int64_t g = 0; g < n; ++g) {
+        const double *m = mu + 3 * g, *q = quat + 4 * g, *s = scale + 3 * g;
+        double xc[3];
+        for (int r = 0; r < 3; ++r) xc[r] = Rc[3 * r] * m[0] + Rc[3 * r + 1] * m[1] + Rc[3 * r + 2] * m[2] + tc[r];
+        orc_splat *o = sp + g;
+        o->z = xc[2];
+        if (!(xc[2] > near_z)) continue;
+        double w = q[0], x = q[1], y = q[2], z = q[3];
+        double qn = sqrt(w * w + x * x + y * y + z * z);
+        w /= qn; x /= qn; y /= qn; z /= qn;
+        double R[3][3] = {{1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)},
+                          {2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)},
+                          {2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)}};
+        double M[3][3], S[3][3], T1[3][3], Sc[3][3];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) M[i][j] = R[i][j] * s[j];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                S[i][j] = 0.0;
+                for (int k = 0; k < 3; ++k) S[i][j] += M[i][k] * M[j][k];
+            }
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                T1[i][j] = 0.0;
+                for (int k = 0; k < 3; ++k) T1[i][j] += Rc[3 * i + k] * S[k][j];
+            }
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                Sc[i][j] = 0.0;
+                for (int k = 0; k < 3; ++k) Sc[i][j] += T1[i][k] * Rc[3 * j + k];
+            }
+        double iz = 1.0 / xc[2];
+        double J[2][3] = {{fx * iz, 0.0, -fx * xc[0] * iz * iz}, {0.0, fy * iz, -fy * xc[1] * iz * iz}};
+        double JS[2][3], C2[2][2];
+        for (int i = 0; i < 2; ++i)
+            for (int j = 0; j < 3; ++j) {
+                JS[i][j] = 0.0;
+                for (int k = 0; k < 3; ++k) JS[i][j] += J[i][k] * Sc[k][j];
+            }
+        for (int i = 0; i < 2; ++i)
+            for (int j = 0; j < 2; ++j) {
+                C2[i][j] = 0.0;
+                for (int k = 0; k < 3; ++k) C2[i][j] += JS[i][k] * J[j][k];
+            }
+        double a = C2[0][0] + 0.3, b = C2[0][1], c = C2[1][1] + 0.3;
+        double det = a * c - b * b;
+        if (!(det > 0.0)) continue;
+        double mid = 0.5 * (a + c);
+        double lam = mid + sqrt(fmax(0.1, mid * mid - det));
+        int r = (int)ceil(3.0 * sqrt(lam));
+        double u = fx * xc[0] * iz + cx, v = fy * xc[1] * iz + cy;
+        int x0 = (int)((u - r) / 16.0), x1 = (int)((u + r + 15) / 16.0);
+        int y0 = (int)((v - r) / 16.0), y1 = (int)((v + r + 15) / 16.0);
+        x0 = x0 < 0 ? 0 : (x0 > gx ? gx : x0); x1 = x1 < 0 ? 0 : (x1 > gx ? gx : x1);
+        y0 = y0 < 0 ? 0 : (y0 > gy ? gy : y0); y1 = y1 < 0 ? 0 : (y1 > gy ? gy : y1);
+        if ((x1 - x0) * (y1 - y0) == 0) continue;
+        o->u = u; o->v = v; o->ca = c / det; o->cb = -b / det; o->cc = a / det;
+        o->r = r; o->x0 = x0; o->x1 = x1; o->y0 = y0; o->y1 = y1; o->ok = 1;
+    }
+    int m = 0;
+    for (int64_t g = 0; g < n; ++g) if (sp[g].ok) order[m++] = (int)g;
+    g_sp_sort = sp;
+    qsort(order, (size_t)m, sizeof(int), cmp_splat);
+    for (int py = 0; py < H; ++py)
+        for (int px = 0; px < W; ++px) {
+            int tx = px / 16, ty = py / 16;
+            double T = 1.0, C[3] = {0.0, 0.0, 0.0};
+            for (int k = 0; k < m; ++k) {
+                const orc_splat *o = sp + order[k];
+                if (tx < o->x0 || tx >= o->x1 || ty < o->y0 || ty >= o->y1) continue;
+                double dx = o->u - px, dy = o->v - py;
+                double p = -0.5 * (o->ca * dx * dx + o->cc * dy * dy) - o->cb * dx * dy;
+                if (p > 0.0) continue;
+                double alpha = fmin(0.99, opac[order[k]] * exp(p));
+                if (alpha < 1.0 / 255.0) continue;
+                double tt = T * (1.0 - alpha);
+                if (tt < 1e-4) break;
+                for (int ch = 0; ch < 3; ++ch) C[ch] += color[3 * (int64_t)order[k] + ch] * alpha * T;
+                T = tt;
+            }
+            for (int ch = 0; ch < 3; ++ch) image[3 * ((int64_t)py * W + px) + ch] = C[ch] + T * bg[ch];
+            trans[(int64_t)py * W + px] = T;
+        }
+    free(sp);
+    free(order);
+}

@@ -311,6 +311,29 @@ def gpu_arm(args, rank, world, local_rank):
         un_ms.append(a.elapsed_time(b))
     st["contact_unsorted_particles"] = float(np.mean(un_ms))
 
+    # Gaussian-splatting render of the frame's 600k rebound Gaussians, 1280 x 720
+    # (synchronous call: it reads the tile-instance count; host time included)
+    from paper_2606_00444_gb300 import gs_render
+    rng = np.random.default_rng(SEED + 6)
+    g_op = t(rng.uniform(0.4, 0.9, gface.shape[0]).astype(np.float32))
+    g_col = t(rng.uniform(0.0, 1.0, (gface.shape[0], 3)).astype(np.float32))
+    eye, tgt = np.array([0.4, -2.6, 1.5]), np.zeros(3)
+    zc = (tgt - eye) / np.linalg.norm(tgt - eye)
+    xc = np.cross(zc, [0, 0, 1.0]); xc /= np.linalg.norm(xc)
+    Rc = np.stack([xc, np.cross(zc, xc), zc]); tc = -Rc @ eye
+    r_ws, r_out = Workspace(dev), None
+    r_ms = []
+    for k in range(13):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        r_out = gs_render(gout[0], gout[1], gout[2], g_op, g_col, Rc, tc, 1100.0, 1100.0, 640, 360, 1280, 720,
+                          ws=r_ws, out=r_out)
+        b.record()
+        torch.cuda.synchronize()
+        if k >= 3:
+            r_ms.append(a.elapsed_time(b))
+    st["render_600k_gaussians_1280x720"] = float(np.mean(r_ms))
+
     # end to end through the public API from pinned host buffers
     e2e_steps = min(args.steps, 50)
     hV = [torch.from_numpy(np.ascontiguousarray(W.frames[k % len(W.frames)])).pin_memory()

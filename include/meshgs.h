@@ -238,6 +238,38 @@ mesh_status mesh_emd(const float *d_A, const float *d_B, int64_t n, float eps_re
                      void *d_ws, size_t ws_bytes, double *d_out, int32_t *d_assign,
                      int64_t *iters_out, void *stream);
 
+/* Pinhole camera for mesh_gs_render: x_c = R x + t (R row-major 3 x 3), image
+ * point (fx x_c/z_c + cx, fy y_c/z_c + cy), pixel (px, py) samples the point
+ * (px, py); Gaussians with z_c <= near_z are culled. */
+typedef struct {
+    float R[9];
+    float t[3];
+    float fx, fy, cx, cy, near_z;
+    int width, height;
+    float background[3];
+} mesh_camera;
+
+/* Workspace bytes of mesh_gs_render for nG Gaussians whose 3-sigma squares
+ * touch n_instances tiles (of 16 x 16 pixels) in a width x height image. */
+size_t mesh_gs_workspace_bytes(int64_t nG, int64_t n_instances, int width, int height);
+
+/* Gaussian-splatting render of the face-bound Gaussians (Sec. 3.2's R_render)
+ * by the forward equations of 3D Gaussian splatting: centres d_mu [nG][3],
+ * rotations d_quat [nG][4] (w, x, y, z), scales d_scale [nG][3], opacities
+ * d_opacity [nG], colours d_color [nG][3]; 2D covariance J R Sigma R^T J^T +
+ * 0.3 I, 3-sigma tile squares, per-tile front-to-back blending (alpha =
+ * min(0.99, o e^p), skipped below 1/255, a pixel stops before its
+ * transmittance falls under 1e-4).  Writes d_image [height][width][3] (colour
+ * plus T x background) and d_trans [height][width] (NULL = not written).
+ * Synchronous: the host reads the instance count (one device-to-host copy)
+ * before the tile sort.  If ws_bytes is too small for this view the call
+ * writes the bytes needed to *ws_needed and returns MESH_ERR_WORKSPACE
+ * without drawing; grow the workspace and call again. */
+mesh_status mesh_gs_render(const float *d_mu, const float *d_quat, const float *d_scale,
+                           const float *d_opacity, const float *d_color, int64_t nG,
+                           const mesh_camera *cam, void *d_ws, size_t ws_bytes, size_t *ws_needed,
+                           float *d_image, float *d_trans, void *stream);
+
 /* Work counters of the one-thread depth-first traversal for these queries:
  * d_counts[0] = node visits (each reads one 64-byte record holding two child
  * boxes), d_counts[1] = triangle tests, d_counts[2] = queries with a face

@@ -39,6 +39,12 @@ class BatchLayout(C.Structure):
                 ("storage_bytes", SZ)]
 
 
+class Camera(C.Structure):
+    _fields_ = [("R", C.c_float * 9), ("t", C.c_float * 3), ("fx", C.c_float), ("fy", C.c_float),
+                ("cx", C.c_float), ("cy", C.c_float), ("near_z", C.c_float), ("width", C.c_int),
+                ("height", C.c_int), ("background", C.c_float * 3)]
+
+
 SIGNATURES = {
     "mesh_bvh_storage_bytes": (SZ, [I64, I64]),
     "mesh_build_workspace_bytes": (SZ, [I64]),
@@ -59,6 +65,8 @@ SIGNATURES = {
     "mesh_signed_distance": (C.c_int, [VP, VP, I64, C.c_float, VP, SZ, VP, VP, VP, VP, VP]),
     "mesh_emd_workspace_bytes": (SZ, [I64]),
     "mesh_emd": (C.c_int, [VP, VP, I64, C.c_float, I64, VP, SZ, VP, VP, C.POINTER(I64), VP]),
+    "mesh_gs_workspace_bytes": (SZ, [I64, I64, C.c_int, C.c_int]),
+    "mesh_gs_render": (C.c_int, [VP, VP, VP, VP, VP, I64, C.POINTER(Camera), VP, SZ, C.POINTER(SZ), VP, VP, VP]),
     "mesh_set_query_group": (C.c_int, [C.c_int]),
     "mesh_set_traversal": (C.c_int, [C.c_int]),
     "mesh_bvh_set_query_config": (C.c_int, [VP, C.c_int, C.c_int]),

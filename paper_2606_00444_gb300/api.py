@@ -495,6 +495,37 @@ def emd(A: torch.Tensor, B: torch.Tensor, eps_rel: float = 1e-5, max_iters: int 
     return (out[0], sigma, it.value) if want_assignment else out[0]
 
 
+def gs_render(mu, quat, scale, opacity, color, R, t, fx, fy, cx, cy, width, height, near=0.01,
+              background=(0.0, 0.0, 0.0), ws: Workspace | None = None, out=None):
+    """Gaussian-splatting render (mesh_gs_render): image [height, width, 3] and
+    transmittance [height, width]; the workspace grows to what the view needs."""
+    mu, quat, scale = _f32(mu, 3, "mu"), _f32(quat, 4, "quat"), _f32(scale, 3, "scale")
+    opacity, color = _f32(opacity, None, "opacity"), _f32(color, 3, "color")
+    n = mu.shape[0]
+    cam = _abi.Camera()
+    Rl = [float(x) for x in torch.as_tensor(R, dtype=torch.float64).reshape(-1).tolist()]
+    tl = [float(x) for x in torch.as_tensor(t, dtype=torch.float64).reshape(-1).tolist()]
+    cam.R[:] = Rl
+    cam.t[:] = tl
+    cam.fx, cam.fy, cam.cx, cam.cy, cam.near_z = float(fx), float(fy), float(cx), float(cy), float(near)
+    cam.width, cam.height = int(width), int(height)
+    cam.background[:] = [float(x) for x in background]
+    if out is None:
+        out = (torch.empty(height, width, 3, device=mu.device), torch.empty(height, width, device=mu.device))
+    image, trans = out
+    ws = Workspace(mu.device) if ws is None else ws
+    need = C.c_size_t(lib().mesh_gs_workspace_bytes(n, 4 * n + 1, int(width), int(height)))
+    for _ in range(3):
+        buf = ws.get(need.value)
+        st = lib().mesh_gs_render(mu.data_ptr(), quat.data_ptr(), scale.data_ptr(), opacity.data_ptr(),
+                                  color.data_ptr(), n, C.byref(cam), buf.data_ptr(), buf.numel(),
+                                  C.byref(need), image.data_ptr(), _ptr(trans), _stream())
+        if st != 3 or need.value <= buf.numel():
+            break
+    check(st, "mesh_gs_render")
+    return image, trans
+
+
 def morton_order(P: torch.Tensor, ws: Workspace | None = None) -> torch.Tensor:
     """int32 permutation sorting the points [n, 3] by Morton key (see mesh_morton_order)."""
     P = _f32(P, 3, "P")

@@ -76,6 +76,12 @@ __device__ __forceinline__ int segment_of(const int *__restrict__ off, int n, in
     return lo;
 }
 
+// Stable LSD radix sort of (key, value) pairs on the low `bits` key bits
+// (lbvh.cu); the workspace is used for the intermediate passes.
+size_t sort_pairs_ws_bytes(int64_t n);
+void sort_pairs_u32(void *ws, int n, int bits, const unsigned int *kin, const int *vin, unsigned int *kout,
+                    int *vout, cudaStream_t s);
+
 // Host-side bookkeeping shared by the entry points.
 void count_launch(int n = 1);
 mesh_status check_launch();

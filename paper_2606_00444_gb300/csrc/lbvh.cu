@@ -916,6 +916,25 @@ static void radix_pass(const BuildWs &w, int n, int shift, const unsigned int *k
     count_launch(3);
 }
 
+// Stable sort of (key, value) pairs on the low `bits` key bits (8 per pass),
+// for other kernels of the library; ws holds sort_pairs_ws_bytes(n) bytes.
+size_t sort_pairs_ws_bytes(int64_t n) { return build_ws_layout(nullptr, n).bytes + 256; }
+
+void sort_pairs_u32(void *ws, int n, int bits, const unsigned int *kin, const int *vin, unsigned int *kout,
+                    int *vout, cudaStream_t s) {
+    BuildWs w = build_ws_layout((char *)ws, n);
+    const int passes = bits <= 0 ? 1 : (bits + 7) / 8;
+    unsigned int *kb[2] = {w.keysA, w.keysB};
+    int *vb[2] = {w.valsA, w.valsB};
+    for (int p = 0; p < passes; ++p) {
+        const unsigned int *ki = p == 0 ? kin : kb[(p - 1) & 1];
+        const int *vi = p == 0 ? vin : vb[(p - 1) & 1];
+        unsigned int *ko = p == passes - 1 ? kout : kb[p & 1];
+        int *vo = p == passes - 1 ? vout : vb[p & 1];
+        radix_pass(w, n, 8 * p, ki, vi, ko, vo, s);
+    }
+}
+
 struct BatchWs {
     BuildWs sort;
     unsigned int *key_of_face, *cbox;

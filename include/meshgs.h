@@ -270,6 +270,21 @@ mesh_status mesh_gs_render(const float *d_mu, const float *d_quat, const float *
                            const mesh_camera *cam, void *d_ws, size_t ws_bytes, size_t *ws_needed,
                            float *d_image, float *d_trans, void *stream);
 
+/* Workspace bytes of mesh_contact for nQ queries. */
+size_t mesh_contact_workspace_bytes(int64_t nQ);
+
+/* The contact query of a physics step: NearestSurface of the nQ particles
+ * with cutoff max_dist, with d_face both the previous step's answers (read
+ * first, as warm-start hints: -1 = none) and this step's (written).  The
+ * queries are run in an order that puts those that touched the mesh last
+ * step first (each group in its given order), so that a warp mostly holds
+ * searches of one depth.  Answers equal mesh_closest_point's (the order and
+ * the hints change only the work).  Traversal variants 1, 10-12 and
+ * cooperative groups run unordered.  d_ws: mesh_contact_workspace_bytes(nQ). */
+mesh_status mesh_contact(const mesh_bvh *bvh, const float *d_Q, int64_t nQ, float max_dist,
+                         int32_t *d_face, float *d_bary, float *d_point, float *d_dist2, void *d_ws,
+                         size_t ws_bytes, void *stream);
+
 /* Work counters of the one-thread depth-first traversal for these queries:
  * d_counts[0] = node visits (each reads one 64-byte record holding two child
  * boxes), d_counts[1] = triangle tests, d_counts[2] = queries with a face

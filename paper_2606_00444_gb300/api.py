@@ -197,6 +197,21 @@ class MeshBVH:
                                          out["sdist"].data_ptr(), _stream()), "mesh_signed_distance")
         return out
 
+    def contact(self, Q: torch.Tensor, max_dist: float, out: dict, ws: "Workspace | None" = None) -> dict:
+        """Physics-step contact query (mesh_contact): out["face"] holds the previous
+        step's faces on entry (-1 = none) and this step's on return."""
+        Q = _f32(Q, 3, "Q")
+        n = Q.shape[0]
+        face = _i32(out["face"], None, "face")
+        if face.data_ptr() != out["face"].data_ptr() or face.shape[0] != n:
+            raise ValueError("out['face'] must be a contiguous int32 [n] tensor")
+        ws = self._ws if ws is None else ws
+        buf = ws.get(lib().mesh_contact_workspace_bytes(n))
+        check(lib().mesh_contact(self.handle, Q.data_ptr(), n, float(max_dist), face.data_ptr(),
+                                 _ptr(out.get("bary")), _ptr(out.get("point")), _ptr(out.get("dist2")),
+                                 buf.data_ptr(), buf.numel(), _stream()), "mesh_contact")
+        return out
+
     def closest_point_stats(self, Q: torch.Tensor, max_dist: float = math.inf) -> dict:
         """Traversal work for these queries: node visits, triangle tests, hits (totals)."""
         Q = _f32(Q, 3, "Q")

@@ -82,6 +82,10 @@ size_t sort_pairs_ws_bytes(int64_t n);
 void sort_pairs_u32(void *ws, int n, int bits, const unsigned int *kin, const int *vin, unsigned int *kout,
                     int *vout, cudaStream_t s);
 
+// Exclusive scan of n ints (splat.cu); bsum holds ceil(n / 1024) ints, total
+// receives the sum.  Three launches on s.
+void exclusive_scan_int(const int *in, int *out, int n, int *bsum, int *total, cudaStream_t s);
+
 // Host-side bookkeeping shared by the entry points.
 void count_launch(int n = 1);
 mesh_status check_launch();

@@ -640,10 +640,12 @@ template <int kSmem, int kMode, int kMinBlocks = kQueryMinBlocks>
 __global__ void __launch_bounds__(kQueryBlock, kMinBlocks)
 k_closest_point(Traversal T, const Header *__restrict__ hdr, unsigned int *status,
                 const float *__restrict__ Q, int64_t nQ, float maxd2, int *face, float *bary,
-                float *point, float *dist2, const int *hint, const int *__restrict__ iperm) {
+                float *point, float *dist2, const int *hint, const int *__restrict__ iperm,
+                const int *__restrict__ order = nullptr) {
     __shared__ int2 stk[kSmem > 0 ? kSmem : 1][kQueryBlock];
-    int64_t i = (int64_t)blockIdx.x * kQueryBlock + threadIdx.x;
-    if (i >= nQ) return;
+    int64_t k = (int64_t)blockIdx.x * kQueryBlock + threadIdx.x;
+    if (k >= nQ) return;
+    const int64_t i = order ? (int64_t)order[k] : k;       // order: a permutation of the queries
     T.tau = traversal_tau(hdr);
     float3 q = make_float3(Q[3 * i], Q[3 * i + 1], Q[3 * i + 2]);
     int hint_leaf = -1;
@@ -1299,6 +1301,41 @@ mesh_status mesh_closest_point_hinted(const mesh_bvh *bvh, const float *d_Q, int
     return check_launch();
 }
 
+// Contact queries of a physics step: warm-started by the previous step's faces
+// and run in an order that puts the queries that touched the mesh last step
+// first (each group in its given order), so a warp mostly holds queries of one
+// kind -- near the surface (deep searches) or away from it (short ones)
+// instead of a mix that runs as long as its slowest lane.
+__global__ void k_contact_flags(int64_t n, const int *__restrict__ face, int nF, int *flags) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int f = face[i];
+    flags[i] = (f >= 0 && f < nF) ? 1 : 0;
+}
+
+__global__ void k_contact_order(int64_t n, const int *__restrict__ flags, const int *__restrict__ pos,
+                                const int *__restrict__ total, int *order) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int p = pos[i];
+    order[flags[i] ? p : *total + (int)i - p] = (int)i;
+}
+
+struct ContactWs {
+    int *flags, *pos, *order, *bsum, *total;
+    size_t bytes;
+};
+
+static ContactWs contact_ws(void *ws, int64_t n) {
+    size_t off = 0;
+    auto take = [&](size_t b) { size_t o = off; off = align_up(off + b, 256); return o; };
+    int64_t m = n > 0 ? n : 1;
+    size_t oF = take(4 * m), oP = take(4 * m), oO = take(4 * m), oB = take(4 * ((m + 1023) / 1024) + 4),
+           oT = take(16);
+    char *b = (char *)ws;
+    return ContactWs{(int *)(b + oF), (int *)(b + oP), (int *)(b + oO), (int *)(b + oB), (int *)(b + oT), off};
+}
+
 mesh_status mesh_knn_project(const mesh_bvh *bvh, const float *d_Q, int64_t nQ, int k,
                              const float *d_anchor, float anchor_weight, float *d_point,
                              int32_t *d_face, float *d_dist2, void *stream) {
@@ -1311,6 +1348,53 @@ mesh_status mesh_knn_project(const mesh_bvh *bvh, const float *d_Q, int64_t nQ, 
     k_knn_project<<<grid_for(nQ, kQueryBlock), kQueryBlock, 0, s>>>(
         traversal_of(bvh, false), h, d_Q, nQ, k, d_anchor, anchor_weight, d_point, d_face, d_dist2,
         &h->status);
+    count_launch();
+    return check_launch();
+}
+
+
+size_t mesh_contact_workspace_bytes(int64_t nQ) {
+    if (nQ < 0 || nQ > INT32_MAX) return 0;
+    return contact_ws(nullptr, nQ).bytes;
+}
+
+mesh_status mesh_contact(const mesh_bvh *bvh, const float *d_Q, int64_t nQ, float max_dist, int32_t *d_face,
+                         float *d_bary, float *d_point, float *d_dist2, void *d_ws, size_t ws_bytes,
+                         void *stream) {
+    if (!bvh || nQ < 0 || nQ > INT32_MAX || (nQ > 0 && (!d_Q || !d_face)) || !(max_dist >= 0.0f))
+        return MESH_ERR_INVALID_ARG;
+    if (nQ == 0) return MESH_OK;
+    ContactWs w = contact_ws(d_ws, nQ);
+    if (!d_ws || ws_bytes < w.bytes || ((uintptr_t)d_ws & 255u)) return MESH_ERR_WORKSPACE;
+    int variant = bvh->cfg_variant >= 0 ? bvh->cfg_variant : g_traversal;
+    if (variant == 1 || variant >= 10 || (bvh->cfg_lanes > 1))
+        return mesh_closest_point_hinted(bvh, d_Q, nQ, max_dist, d_face, d_face, d_bary, d_point, d_dist2,
+                                         stream);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int n = (int)nQ;
+    k_contact_flags<<<grid_for(nQ, 256), 256, 0, s>>>(nQ, d_face, (int)bvh->L.n_faces, w.flags);
+    count_launch();
+    exclusive_scan_int(w.flags, w.pos, n, w.bsum, w.total, s);
+    k_contact_order<<<grid_for(nQ, 256), 256, 0, s>>>(nQ, w.flags, w.pos, w.total, w.order);
+    count_launch();
+    float maxd2 = isinf(max_dist) ? INFINITY : max_dist * max_dist;
+    Traversal T = traversal_of(bvh, isinf(max_dist));
+    Header *h = bvh->hdr();
+    const int *iperm = bvh->iperm();
+    unsigned int grid = grid_for(nQ, kQueryBlock);
+#define MESH_CT_ARGS <<<grid, kQueryBlock, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2, d_face, iperm, w.order)
+    switch (variant) {
+        case 2: k_closest_point<8, 0> MESH_CT_ARGS; break;
+        case 3: k_closest_point<0, 0> MESH_CT_ARGS; break;
+        case 4: k_closest_point<kStackShared, 2> MESH_CT_ARGS; break;
+        case 5: k_closest_point<0, 2> MESH_CT_ARGS; break;
+        case 6: k_closest_point<8, 0, 12> MESH_CT_ARGS; break;
+        case 7: k_closest_point<0, 0, 12> MESH_CT_ARGS; break;
+        case 8: k_closest_point<0, 0, 16> MESH_CT_ARGS; break;
+        case 9: k_closest_point<0, 2, 12> MESH_CT_ARGS; break;
+        default: k_closest_point<kStackShared, 0> MESH_CT_ARGS; break;
+    }
+#undef MESH_CT_ARGS
     count_launch();
     return check_launch();
 }

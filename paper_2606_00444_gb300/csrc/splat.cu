@@ -26,11 +26,6 @@ constexpr int kTile = 16;
 constexpr int kTilePix = kTile * kTile;
 constexpr int kScanBlock = 1024;
 
-struct Splat2D {
-    float2 uv;
-    float4 conic_o;     // conic (a, b, c) and opacity
-};
-
 __global__ void k_gs_preprocess(int n, const float *__restrict__ mu, const float *__restrict__ quat,
                                 const float *__restrict__ scale, const float *__restrict__ opac,
                                 mesh_camera cam, int gx, int gy, float2 *uv, float4 *conic_o,
@@ -138,6 +133,14 @@ __global__ void __launch_bounds__(32) k_scan_sums(int nb, int *bsum, int *total)
 __global__ void k_scan_add(int n, int *out, const int *bsum) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] += bsum[i / kScanBlock];
+}
+
+void exclusive_scan_int(const int *in, int *out, int n, int *bsum, int *total, cudaStream_t s) {
+    int nb = (n + kScanBlock - 1) / kScanBlock;
+    k_scan_local<<<nb, kScanBlock, 0, s>>>(n, in, out, bsum);
+    k_scan_sums<<<1, 32, 0, s>>>(nb, bsum, total);
+    k_scan_add<<<grid_for(n, 256), 256, 0, s>>>(n, out, bsum);
+    count_launch(3);
 }
 
 __global__ void k_gs_duplicate(int n, const int *__restrict__ count, const int *__restrict__ offset,

@@ -237,6 +237,30 @@ def test_warm_start_over_a_skinned_sequence_full_size():
     assert bvh.status()[0] == 0
 
 
+@pytest.mark.parametrize("variant", [0, 2, 5, 12])
+def test_contact_step_equals_plain_queries(variant):
+    """mesh_contact (previous faces as hints, queries reordered by last step's contact
+    state) gives mesh_closest_point's answers over a skinned sequence."""
+    from paper_2606_00444_gb300 import morton_order
+    V0, F = torus(120, 70)
+    sk = TorusSkinning(V0, seed=3001)
+    lo, hi = V0.min(0) - 0.2, V0.max(0) + 0.2
+    P = dev(uniform_box(50001, lo, hi, seed=3005))
+    P = P[morton_order(P).long()].contiguous()
+    bvh = MeshBVH.from_mesh(dev(V0), dev(F))
+    bvh.set_query_config(1, variant)
+    out = dict(face=torch.full((P.shape[0],), -1, dtype=torch.int32, device="cuda"),
+               bary=torch.empty(P.shape[0], 3, device="cuda"), point=torch.empty(P.shape[0], 3, device="cuda"),
+               dist2=torch.empty(P.shape[0], device="cuda"))
+    for t in (0, 5, 10, 40):
+        bvh.refit(dev(sk.frame(t)))
+        ref = bvh.closest_point(P, 0.05)
+        bvh.contact(P, 0.05, out)
+        for k in ref:
+            assert torch.equal(out[k], ref[k]), (t, k)
+    assert bvh.status()[0] == 0
+
+
 def test_traversal_counters_are_consistent(c1):
     _, _, VG, FG, Q = c1
     bvh = MeshBVH.from_mesh(dev(VG), dev(FG))

@@ -342,7 +342,9 @@ def gpu_arm(args, rank, world, local_rank):
     e2e_steps = min(args.steps, 50)
     hV = [torch.from_numpy(np.ascontiguousarray(W.frames[k % len(W.frames)])).pin_memory()
           for k in range(min(e2e_steps, len(W.frames)))]
-    hP = torch.from_numpy(W.P).pin_memory()
+    # the host keeps its particles in the same (Morton) order as the device copy, as a
+    # physics engine that owns the particle order would
+    hP = P.cpu().pin_memory()
     h_face = torch.empty(N_PART, dtype=torch.int32).pin_memory()
     h_d2 = torch.empty(N_PART).pin_memory()
     h_cd = torch.empty(2, dtype=torch.float64).pin_memory()

@@ -126,6 +126,23 @@ class Clocks:
                 "samples": len(rows), "reasons": reasons}
 
 
+def max_over_ranks(ms: float, world: int, device) -> float:
+    """The slowest rank's time per step (the replicas' aggregate rate divides the work
+    of all ranks by it); identity for one process."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def replicas_value(queries_per_frame: int, world: int, ms: float) -> float:
+    """Whole-job queries per second: every rank runs the same frame on its own GPU."""
+    return world * queries_per_frame / (ms * 1e-3)
+
+
 def gpu_arm(args, rank, world, local_rank):
     import torch
     from paper_2606_00444_gb300 import MeshBVH, Workspace, chamfer, launch_count, morton_order
@@ -255,11 +272,7 @@ def gpu_arm(args, rank, world, local_rank):
     if world > 1:
         dist.barrier()
     ck = clocks.stop()
-    ms = float(np.mean(step_ms))
-    if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(float(np.mean(step_ms)), world, dev)
 
     # per-stage device times: each stage captured as its own graph and the five
     # replayed back to back with events between them (no host gaps inside a
@@ -815,7 +828,7 @@ def main():
     un = st.pop("contact_unsorted_particles")
     line = {
         "metric": METRIC,
-        "value": world * q / (ms * 1e-3),
+        "value": replicas_value(q, world, ms),
         "unit": "queries/s",
         "n_gpus": world,
         "steps": args.steps,

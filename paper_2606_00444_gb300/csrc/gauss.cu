@@ -12,17 +12,49 @@
 
 namespace meshgs {
 
-__global__ void k_bind_gaussians(const int4 *__restrict__ faces, const float4 *__restrict__ verts,
-                                 int nF, const int *__restrict__ gface,
-                                 const float *__restrict__ gbary, const float *__restrict__ goff,
-                                 int64_t nG, float *__restrict__ mu, float *__restrict__ quat,
-                                 float *__restrict__ scale, Header *hdr) {
-    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= nG) return;
-    int f = gface[g];
-    if ((unsigned)f >= (unsigned)nF) { bind_invalid(g, mu, quat, scale, &hdr->status); return; }
-    bind_one(faces[f], verts, gbary[3 * g], gbary[3 * g + 1], gbary[3 * g + 2],
-             goff ? goff[g] : 0.0f, g, mu, quat, scale, &hdr->status, &hdr->n_degenerate);
+// Gaussians per thread: each thread issues the loads of all of them (index,
+// face, three vertices, weights) before computing any, so their dependent
+// load chains overlap instead of waiting one after the other.  Gaussian k of
+// thread t in block b is b * kBindBlock * kBindPer + k * kBindBlock + t, so
+// every load and store stays coalesced across a warp.
+constexpr int kBindBlock = 256;
+constexpr int kBindPer = 2;
+
+__global__ void __launch_bounds__(kBindBlock)
+k_bind_gaussians(const int4 *__restrict__ faces, const float4 *__restrict__ verts, int nF,
+                 const int *__restrict__ gface, const float *__restrict__ gbary,
+                 const float *__restrict__ goff, int64_t nG, float *__restrict__ mu,
+                 float *__restrict__ quat, float *__restrict__ scale, Header *hdr) {
+    const int64_t base = (int64_t)blockIdx.x * (kBindBlock * kBindPer) + threadIdx.x;
+    int f[kBindPer];
+#pragma unroll
+    for (int k = 0; k < kBindPer; ++k) {
+        int64_t g = base + (int64_t)k * kBindBlock;
+        f[k] = g < nG ? __ldg(gface + g) : -1;
+    }
+    float4 va[kBindPer], vb[kBindPer], vc[kBindPer];
+    float w[kBindPer][4];
+#pragma unroll
+    for (int k = 0; k < kBindPer; ++k) {
+        int64_t g = base + (int64_t)k * kBindBlock;
+        int4 fv = (unsigned)f[k] < (unsigned)nF ? __ldg(faces + f[k]) : make_int4(0, 0, 0, 0);
+        va[k] = __ldg(verts + fv.x);
+        vb[k] = __ldg(verts + fv.y);
+        vc[k] = __ldg(verts + fv.z);
+        bool in = g < nG;
+        w[k][0] = in ? __ldg(gbary + 3 * g) : 0.0f;
+        w[k][1] = in ? __ldg(gbary + 3 * g + 1) : 0.0f;
+        w[k][2] = in ? __ldg(gbary + 3 * g + 2) : 0.0f;
+        w[k][3] = in && goff ? __ldg(goff + g) : 0.0f;
+    }
+#pragma unroll
+    for (int k = 0; k < kBindPer; ++k) {
+        int64_t g = base + (int64_t)k * kBindBlock;
+        if (g >= nG) break;
+        if ((unsigned)f[k] >= (unsigned)nF) { bind_invalid(g, mu, quat, scale, &hdr->status); continue; }
+        bind_corners(v3(va[k]), v3(vb[k]), v3(vc[k]), w[k][0], w[k][1], w[k][2], w[k][3], g, mu, quat,
+                     scale, &hdr->status, &hdr->n_degenerate);
+    }
 }
 
 // Batched form: Gaussian g of scene s (gauss_off), face id local to s.  Grid-
@@ -140,9 +172,9 @@ mesh_status mesh_bind_gaussians(const mesh_bvh *bvh, const int32_t *d_gface, con
         return MESH_ERR_INVALID_ARG;
     if (nG == 0) return MESH_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    k_bind_gaussians<<<grid_for(nG, 256), 256, 0, s>>>(bvh->faces(), bvh->verts(),
-                                                       (int)bvh->L.n_faces, d_gface, d_gbary, d_goff,
-                                                       nG, d_mu, d_quat, d_scale, bvh->hdr());
+    k_bind_gaussians<<<grid_for((nG + kBindPer - 1) / kBindPer, kBindBlock), kBindBlock, 0, s>>>(
+        bvh->faces(), bvh->verts(), (int)bvh->L.n_faces, d_gface, d_gbary, d_goff, nG, d_mu, d_quat,
+        d_scale, bvh->hdr());
     count_launch();
     return check_launch();
 }

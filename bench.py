@@ -194,22 +194,29 @@ def gpu_arm(args, rank, world, local_rank):
     cd_ws = Workspace(dev)
     flush = torch.empty(128 << 20, dtype=torch.float32, device=dev)   # 512 MB > L2
 
-    def stages(ev=None):
-        def mark(i):
-            if ev is not None:
-                ev[i].record()
-        mark(0)
+    # The frame as a fork-join graph, as an engine would schedule it: the full
+    # rebuild of the frame (the varying-topology path) only reads the frame's
+    # vertices and forks at the frame start; after the refit, the contact queries
+    # (main stream) and the rebind + Chamfer branch (side stream) run concurrently.
+    # The branches share no workspace.  Per-stage device times are measured
+    # separately below, one stage at a time.
+    side_a = torch.cuda.Stream(device=dev)
+    side_b = torch.cuda.Stream(device=dev)
+
+    def stages():
+        main = torch.cuda.current_stream()
+        side_b.wait_stream(main)
+        with torch.cuda.stream(side_b):
+            rebuilt.build(Vin, F)                                # a1 + a2..a5
         fixed.refit(Vin)                                         # a1 + a5
-        mark(1)
+        side_a.wait_stream(main)
+        with torch.cuda.stream(side_a):
+            fixed.bind_gaussians(gface, gbary, out=gout)         # a7
+            fixed.interpolate(cdf, cdb, out=S_def)               # a8
+            chamfer(fixed, S_def, rest, rest_S, ws=cd_ws, out=cd_out)
         fixed.closest_point(P, CUTOFF, out=contact, hint=contact["face"])   # a6
-        mark(2)
-        fixed.bind_gaussians(gface, gbary, out=gout)             # a7
-        mark(3)
-        rebuilt.build(Vin, F)                                    # a1 + a2..a5
-        mark(4)
-        fixed.interpolate(cdf, cdb, out=S_def)                   # a8
-        chamfer(fixed, S_def, rest, rest_S, ws=cd_ws, out=cd_out)
-        mark(5)
+        main.wait_stream(side_a)
+        main.wait_stream(side_b)
 
     def load_frame(k):
         Vin.copy_(frames[k % frames.shape[0]], non_blocking=True)
@@ -316,6 +323,23 @@ def gpu_arm(args, rank, world, local_rank):
     names = ["refit", "contact", "rebind", "rebuild", "chamfer", "contact_without_warm_start",
              "contact_reordered", "contact_signed", "chamfer_with_warm_start"]
     st = {n: float(np.mean([e[i].elapsed_time(e[i + 1]) for e in evs])) for i, n in enumerate(names)}
+
+    # the concurrent frame graph computes what the stages compute one at a time
+    def frame_outputs():
+        arr = rebuilt.arrays()                                   # the rebuilt tree, as bits
+        tree = [arr[k].clone() for k in ("keys", "perm", "parent", "nodes_i")] + \
+               [arr["tris"].view(torch.int32).clone()]
+        return [v.clone() for v in contact.values()] + [x.clone() for x in gout] + [cd_out.clone()] + tree
+    load_frame(7)
+    g.replay()
+    conc = frame_outputs()
+    load_frame(7)
+    for gs in stage_graphs[:5]:
+        gs.replay()
+    seq = frame_outputs()
+    torch.cuda.synchronize()
+    if not all(torch.equal(x, y) for x, y in zip(conc, seq)):
+        raise RuntimeError("the concurrent frame graph differs from the stages run one at a time")
     un_ms = []
     contact_un = {k: torch.empty_like(v) for k, v in contact.items()}
     for k in range(min(nst, 20)):
@@ -351,18 +375,21 @@ def gpu_arm(args, rank, world, local_rank):
             r_ms.append(a.elapsed_time(b))
     st["render_600k_gaussians_1280x720"] = float(np.mean(r_ms))
 
-    # end to end through the public API from pinned host buffers.  As an engine
-    # would, the frame is split in three graphs so that the copies run on a second
-    # stream beside the kernels: the particle upload beside the refit, the download
-    # of the contact results beside the rest of the frame (events order them)
-    gA, gB, gC = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+    # end to end through the public API from pinned host buffers, the frame run as
+    # above in four graphs (refit; contact; rebind + Chamfer; rebuild) with the
+    # copies on a further stream beside the kernels: the particle upload beside
+    # the refit, the download of the contact results beside the rest of the frame
+    # (events order them)
+    gA, gB, gC, gD = (torch.cuda.CUDAGraph() for _ in range(4))
     with torch.cuda.graph(gA):
         stage_fns[0]()                                            # refit
     with torch.cuda.graph(gB):
         stage_fns[1]()                                            # contact
     with torch.cuda.graph(gC):
-        for fn in stage_fns[2:5]:                                 # rebind, rebuild, Chamfer
-            fn()
+        stage_fns[2]()                                            # rebind
+        stage_fns[4]()                                            # Chamfer
+    with torch.cuda.graph(gD):
+        stage_fns[3]()                                            # rebuild
     torch.cuda.synchronize()
     main, cs = torch.cuda.current_stream(), torch.cuda.Stream(device=dev)
     e2e_steps = min(args.steps, 50)
@@ -385,7 +412,14 @@ def gpu_arm(args, rank, world, local_rank):
             P.copy_(hP, non_blocking=True)                        # particles in
             ev_p.record(cs)
         Vin.copy_(hV[k % len(hV)], non_blocking=True)             # frame vertices in
+        side_b.wait_stream(main)
+        with torch.cuda.stream(side_b):
+            gD.replay()
         gA.replay()
+        side_a.wait_stream(main)
+        with torch.cuda.stream(side_a):
+            gC.replay()
+            h_cd.copy_(cd_out, non_blocking=True)                 # Chamfer out
         main.wait_event(ev_p)
         gB.replay()
         ev_c.record(main)
@@ -394,9 +428,9 @@ def gpu_arm(args, rank, world, local_rank):
             h_face.copy_(contact["face"], non_blocking=True)      # contact results out
             h_d2.copy_(contact["dist2"], non_blocking=True)
             ev_d.record(cs)
-        gC.replay()
-        h_cd.copy_(cd_out, non_blocking=True)                     # Chamfer out
         main.wait_event(ev_d)
+        main.wait_stream(side_a)
+        main.wait_stream(side_b)
         b.record(main)
         b.synchronize()
         if k >= 3:

@@ -533,7 +533,9 @@ def reference_arm(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(fulls)) * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD, "frames": args.steps},
+            "config": {"workload": WORKLOAD, "queries_per_frame": W.queries_per_frame,
+                       "faces": NU * NV_ * 2, "gaussians": NU * NV_ * 2 * G_PER_FACE,
+                       "parallelism": "host, one thread", "frames": args.steps},
             "cpu_baseline": {"value": val, "unit": "queries/s", "cores": 1, "kind": "oracle",
                              "sample": f"per step: full serial LBVH build, {nq} contact queries, "
                                        f"4096 Gaussians, 16 Chamfer samples per side, "

@@ -1,0 +1,28 @@
+"""The reference arm of bench.py (the oracle timed on the host) runs without a GPU
+and prints the one JSON line of the benchmark contract, on the GPU arm's workload."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_reference_arm_prints_the_contract_line():
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--steps", "1", "--warmup", "0"], capture_output=True, text=True,
+                       timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config", "e2e",
+              "cpu_baseline"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["unit"] == "queries/s"
+    assert line["higher_is_better"] is True and line["value"] > 0
+    assert line["config"]["queries_per_frame"] == (1 << 20) + 2 * 10000
+    assert line["config"]["faces"] == 200000 and line["config"]["gaussians"] == 600000
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": "queries/s", "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}

@@ -1,6 +1,9 @@
 """A whole fixed-topology frame (vertex update, refit, contact queries, Gaussian
 rebind, full rebuild, Chamfer) captured in one CUDA graph and replayed gives the
-same bits as the same frame run eagerly, for several frames in a row."""
+same bits as the same frame run eagerly, for several frames in a row; and the
+same frame run as a fork-join over three streams (the branches that only read
+the refit mesh, and the rebuild, concurrently), eagerly or captured, gives the
+same bits as the calls run one after another."""
 import numpy as np
 import pytest
 import torch
@@ -13,7 +16,7 @@ from workloads.sampling import osada_barycentrics, sample_surface, uniform_box
 pytestmark = pytest.mark.gpu
 
 
-def test_graph_replayed_frame_equals_eager_frame():
+def _frame_setup():
     V0, F = torus(80, 50)
     sk = TorusSkinning(V0, seed=77)
     frames = [dev(sk.frame(t)) for t in range(4)]
@@ -51,23 +54,71 @@ def test_graph_replayed_frame_equals_eager_frame():
         arrs = [v for b in (rebuilt, fixed) for v in b.arrays().values()]
         return [t.contiguous().clone().view(-1).view(torch.uint8) for t in (*outs.values(), *g3, S, cd, *arrs)]
 
+    side_a, side_b = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def frame_fork_join():
+        main = torch.cuda.current_stream()
+        side_b.wait_stream(main)
+        with torch.cuda.stream(side_b):
+            rebuilt.build(Vin, Fd)
+        fixed.refit(Vin)
+        side_a.wait_stream(main)
+        with torch.cuda.stream(side_a):
+            fixed.bind_gaussians(gface, gbary, out=g3)
+            fixed.interpolate(sf, sb, out=S)
+            chamfer(fixed, S, rest, S, ws=ws, out=cd)
+        fixed.closest_point(P, 0.05, out=outs)
+        main.wait_stream(side_a)
+        main.wait_stream(side_b)
+
+    return frames, Vin, frame, frame_fork_join, snapshot
+
+
+def _capture(fn):
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        fn()
+    torch.cuda.current_stream().wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        fn()
+    return g
+
+
+def test_graph_replayed_frame_equals_eager_frame():
+    frames, Vin, frame, _, snapshot = _frame_setup()
     eager = []
     for f in frames:
         Vin.copy_(f)
         frame()
         eager.append(snapshot())
     Vin.copy_(frames[0])
-    s = torch.cuda.Stream()
-    s.wait_stream(torch.cuda.current_stream())
-    with torch.cuda.stream(s):
-        frame()
-    torch.cuda.current_stream().wait_stream(s)
-    g = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(g):
-        frame()
+    g = _capture(frame)
     for f, ref in zip(frames, eager):
         Vin.copy_(f)
         g.replay()
         got = snapshot()
         for a, b in zip(got, ref):
+            assert torch.equal(a, b)
+
+
+def test_fork_join_frame_on_three_streams_equals_sequential():
+    frames, Vin, frame, frame_fork_join, snapshot = _frame_setup()
+    seq = []
+    for f in frames:
+        Vin.copy_(f)
+        frame()
+        seq.append(snapshot())
+    for f, ref in zip(frames, seq):                     # eager, three streams
+        Vin.copy_(f)
+        frame_fork_join()
+        for a, b in zip(snapshot(), ref):
+            assert torch.equal(a, b)
+    Vin.copy_(frames[0])
+    g = _capture(frame_fork_join)                      # captured fork-join graph
+    for f, ref in zip(frames, seq):
+        Vin.copy_(f)
+        g.replay()
+        for a, b in zip(snapshot(), ref):
             assert torch.equal(a, b)

@@ -176,7 +176,8 @@ def gpu_arm(args, rank, world, local_rank):
     tuned = tune_closest_point(fixed, P, CUTOFF)
     Vin = torch.empty(nV, 3, device=dev)
     # contact faces persist from frame to frame: each frame's query is warm-started
-    # with the previous frame's faces (mesh_closest_point_hinted; same answers)
+    # with the previous frame's faces (mesh_closest_point_hinted; the same answers up
+    # to near ties whose kept face depends on the order faces are met)
     contact = dict(face=torch.full((N_PART,), -1, dtype=torch.int32, device=dev),
                    bary=torch.empty(N_PART, 3, device=dev), point=torch.empty(N_PART, 3, device=dev),
                    dist2=torch.empty(N_PART, device=dev))
@@ -325,21 +326,26 @@ def gpu_arm(args, rank, world, local_rank):
     st = {n: float(np.mean([e[i].elapsed_time(e[i + 1]) for e in evs])) for i, n in enumerate(names)}
 
     # the concurrent frame graph computes what the stages compute one at a time
+    # (both from the same warm-start faces, so the inputs are identical)
     def frame_outputs():
         arr = rebuilt.arrays()                                   # the rebuilt tree, as bits
         tree = [arr[k].clone() for k in ("keys", "perm", "parent", "nodes_i")] + \
                [arr["tris"].view(torch.int32).clone()]
         return [v.clone() for v in contact.values()] + [x.clone() for x in gout] + [cd_out.clone()] + tree
+    hint0 = contact["face"].clone()
     load_frame(7)
     g.replay()
     conc = frame_outputs()
+    contact["face"].copy_(hint0)
     load_frame(7)
     for gs in stage_graphs[:5]:
         gs.replay()
     seq = frame_outputs()
     torch.cuda.synchronize()
-    if not all(torch.equal(x, y) for x, y in zip(conc, seq)):
-        raise RuntimeError("the concurrent frame graph differs from the stages run one at a time")
+    bad = [i for i, (x, y) in enumerate(zip(conc, seq)) if not torch.equal(x, y)]
+    if bad:
+        raise RuntimeError(f"the concurrent frame graph differs from the stages run one at a "
+                           f"time in outputs {bad}")
     un_ms = []
     contact_un = {k: torch.empty_like(v) for k, v in contact.items()}
     for k in range(min(nst, 20)):

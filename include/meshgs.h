@@ -168,7 +168,11 @@ mesh_status mesh_refit_bind(mesh_bvh *bvh, const float *d_V, int64_t nV, const i
  * mesh, as face id, barycentric weights (u, v, w) of (v0, v1, v2), the point
  * u v0 + v v1 + w v2 and its squared distance.  Ties: the lowest face id
  * among faces within 1e-6 relative distance (+1e-12 of the box diagonal) of
- * the nearest found.  A query with no face within max_dist (INFINITY = no
+ * the nearest found, applied online as faces are met.  Where three or more
+ * faces lie within about 2e-6 of one another the kept face can depend on the
+ * order in which they are met (traversal variant, warm start): it is then
+ * another face within that window, its distance within the window of the
+ * nearest.  A query with no face within max_dist (INFINITY = no
  * cutoff) gets face -1, dist2 = +inf, bary = point = 0.  Any output pointer
  * may be NULL (not written). */
 mesh_status mesh_closest_point(const mesh_bvh *bvh, const float *d_Q, int64_t nQ,
@@ -177,9 +181,10 @@ mesh_status mesh_closest_point(const mesh_bvh *bvh, const float *d_Q, int64_t nQ
 
 /* mesh_closest_point with a warm start: d_hint[i] (a face id, e.g. query i's
  * nearest face in the previous frame; -1 or out of range = none) is tested
- * before the traversal and its distance bounds the search.  The answer is the
- * same as without the hint (every face within the final tie window is still
- * reached); only the work changes.  d_hint may be the same array as d_face
+ * before the traversal and its distance bounds the search.  Every face within
+ * the final tie window is still reached, so the answer is the one without the
+ * hint except in the order-dependent near ties described above; the hint
+ * changes the work.  d_hint may be the same array as d_face
  * (each query reads its hint before writing its face).  Used by the
  * depth-first one-thread variants (0, 2-9) and by the cooperative groups
  * (lanes > 1); the other one-thread variants ignore it. */
@@ -278,8 +283,8 @@ size_t mesh_contact_workspace_bytes(int64_t nQ);
  * first, as warm-start hints: -1 = none) and this step's (written).  The
  * queries are run in an order that puts those that touched the mesh last
  * step first (each group in its given order), so that a warp mostly holds
- * searches of one depth.  Answers equal mesh_closest_point's (the order and
- * the hints change only the work).  Traversal variants 1, 10-12 and
+ * searches of one depth.  Answers equal mesh_closest_point's up to its
+ * order-dependent near ties (the order and the hints change the work).  Traversal variants 1, 10-12 and
  * cooperative groups run unordered.  d_ws: mesh_contact_workspace_bytes(nQ). */
 mesh_status mesh_contact(const mesh_bvh *bvh, const float *d_Q, int64_t nQ, float max_dist,
                          int32_t *d_face, float *d_bary, float *d_point, float *d_dist2, void *d_ws,
@@ -316,7 +321,8 @@ mesh_status mesh_set_query_group(int lanes);
  *  12 warp packet: the 32 queries of a warp share one node sequence, a node
  *     entered when any lane needs it (for queries kept in Morton order)
  * (the shared part of the stack spills to local memory; local-only leaves the
- * SM's L1 to the node cache).  Process-wide; same answers for every variant. */
+ * SM's L1 to the node cache).  Process-wide; same answers for every variant
+ * up to the order-dependent near ties described at mesh_closest_point. */
 mesh_status mesh_set_traversal(int variant);
 
 /* Traversal choice for mesh_closest_point calls on this handle (host-side
@@ -360,7 +366,9 @@ mesh_status mesh_chamfer(const mesh_bvh *A, const float *d_SA, int64_t nSA,
  * SA[i] (e.g. its nearest face in the previous frame), d_hintB[i] a face of
  * mesh A for SB[i]; -1 or out of range = none, either pointer may be NULL,
  * and each may be the same array as the matching face output.  The answers
- * are the same as without hints; only the traversal work changes. */
+ * are those without hints up to the order-dependent near ties of
+ * mesh_closest_point (a sample's distance then moves within its tie window);
+ * the hints change the traversal work. */
 mesh_status mesh_chamfer_hinted(const mesh_bvh *A, const float *d_SA, int64_t nSA,
                                 const mesh_bvh *B, const float *d_SB, int64_t nSB, void *d_ws,
                                 size_t ws_bytes, double *d_out, const int32_t *d_hintA,

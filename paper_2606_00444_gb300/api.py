@@ -142,7 +142,8 @@ class MeshBVH:
                       hint: torch.Tensor | None = None) -> dict:
         """NearestSurface of every query.  `hint` (int32 face ids, -1 = none; may be
         out["face"] itself) warm-starts the search, e.g. with the previous frame's
-        answers; the result is the same with or without it."""
+        answers; the result is the one without it up to order-dependent near ties
+        (faces within about 2e-6 of the nearest distance; see mesh_closest_point)."""
         Q = _f32(Q, 3, "Q")
         n = Q.shape[0]
         if hint is not None:

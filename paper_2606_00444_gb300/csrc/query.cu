@@ -255,7 +255,11 @@ struct Counts {
 // hint_leaf >= 0: a leaf tested before the traversal (a warm start, e.g. the
 // previous frame's nearest face); its distance bounds the search from the
 // first node on.  Every leaf within the final tie window is still reached, so
-// the answer is the same with or without it.
+// the distance stays within that window and the face is the same, except
+// where the online tie rule depends on the order in which faces are met: a
+// face inside the final window can be dropped while a lower-id face is kept,
+// and that face can later leave the window (three or more faces within about
+// 2e-6 of one another).
 template <int kBlockT, int kSmem = kStackShared, bool kOneSite = false, bool kCount = false>
 __device__ __forceinline__ Hit nearest(const Traversal &T, float3 q, float maxd2,
                                        int2 (*stk)[kBlockT], unsigned int *status,
@@ -327,7 +331,8 @@ __device__ __forceinline__ Hit nearest(const Traversal &T, float3 q, float maxd2
 // while leaf children are only queued (up to kLeafQueue); the queued leaves
 // are tested when every lane still traversing has one queued (or its queue is
 // full, or it is done).  Leaf tests then run with the warp mostly converged
-// instead of in almost every step.  Same answers as nearest().
+// instead of in almost every step.  Same answers as nearest() up to the
+// order-dependent near ties noted there.
 constexpr int kLeafQueue = 4;
 
 template <int kBlockT>
@@ -670,7 +675,7 @@ k_closest_point(Traversal T, const Header *__restrict__ hdr, unsigned int *statu
 // record) and all control flow outside the leaf tests is warp-uniform: the
 // warp runs the union of its queries' traversals with every lane active,
 // instead of each lane's traversal with most lanes idle.  Same answers as the
-// depth-first kernels.
+// depth-first kernels up to the order-dependent near ties noted at nearest().
 __device__ __forceinline__ Hit nearest_packet(const Traversal &T, float3 q, float maxd2, bool valid,
                                               int *wstk, unsigned int *status) {
     const unsigned int kFull = 0xffffffffu;
@@ -903,8 +908,9 @@ mesh_status launch_signed_query(const mesh_bvh *bvh, const float *d_Q, int64_t n
 // the warp takes that many new query indices from a global counter.  Lanes no
 // longer wait for the slowest query of their warp (contact queries near the
 // surface need ~6x the visits of those far from it).  Same answers as the
-// depth-first kernels.  The counter lives in the mesh header (zeroed before
-// each launch), so concurrent calls on one handle must not overlap.
+// depth-first kernels up to the order-dependent near ties noted at nearest().
+// The counter lives in the mesh header (zeroed before each launch), so
+// concurrent calls on one handle must not overlap.
 constexpr int kRefill = 8;
 
 template <int kSmem>

@@ -9,7 +9,7 @@ import torch
 import oracle
 from paper_2606_00444_gb300 import MeshBVH, chamfer
 from paper_2606_00444_gb300.autograd import BindGaussians, Chamfer, Interpolate, PointMeshDistance
-from parity import check_gaussians, dev, host
+from parity import assert_same_up_to_near_ties, check_gaussians, dev, host
 from workloads.meshes import displaced_icosphere, icosphere, torus, TorusSkinning
 from workloads.sampling import osada_barycentrics, points_from, sample_surface, uniform_box
 
@@ -199,8 +199,9 @@ def test_chamfer_every_group_width(pair, lanes):
 @pytest.mark.parametrize("lanes", [1, 4, 16])
 def test_chamfer_warm_start_hints_give_identical_results(pair, lanes):
     """mesh_chamfer_hinted with exact, random, -1 and out-of-range hints, and
-    hints aliasing the face outputs, gives the unhinted sums and per-sample
-    results bit for bit (one thread or a cooperative group per sample)."""
+    hints aliasing the face outputs, gives the unhinted per-sample results bit for
+    bit (one thread or a cooperative group per sample) up to rare order-dependent
+    near ties, and the unhinted sums (bit for bit when no sample differs)."""
     from paper_2606_00444_gb300 import set_query_group
     VA, FA, SA, VB, FB, SB = pair
     A = MeshBVH.from_mesh(dev(VA), dev(FA))
@@ -215,18 +216,22 @@ def test_chamfer_warm_start_hints_give_identical_results(pair, lanes):
                   dev(rng.integers(0, FA.shape[0], nB).astype(np.int32))),
                  (dev(np.full(nA, -1, np.int32)), None),
                  (None, dev(rng.integers(-3, 3 * FA.shape[0], nB).astype(np.int32)))]
+        def same(out, ps):
+            n = assert_same_up_to_near_ties(ps, rps, "faceA", "dist2A") + \
+                assert_same_up_to_near_ties(ps, rps, "faceB", "dist2B")
+            if n == 0:
+                assert torch.equal(out, ref)
+            else:
+                assert torch.allclose(out, ref, rtol=1e-6, atol=0.0)
+
         for hints in cases:
             out, ps = chamfer(A, dev(SA), B, dev(SB), per_sample=True, hints=hints)
-            assert torch.equal(out, ref)
-            for k in rps:
-                assert torch.equal(ps[k], rps[k]), k
+            same(out, ps)
         ps = {k: v.clone() for k, v in rps.items()}
         ps["faceA"] = dev(rng.integers(0, FB.shape[0], nA).astype(np.int32))
         ps["faceB"] = dev(rng.integers(0, FA.shape[0], nB).astype(np.int32))
         out, _ = chamfer(A, dev(SA), B, dev(SB), per_sample=True, ps=ps, hints=(ps["faceA"], ps["faceB"]))
-        assert torch.equal(out, ref)
-        for k in rps:
-            assert torch.equal(ps[k], rps[k]), k
+        same(out, ps)
     finally:
         set_query_group(0)
 
@@ -244,8 +249,7 @@ def test_closest_point_hints_in_cooperative_groups(pair, lanes):
             ref = B.closest_point(Q, cut)
             for hint in (ref["face"].clone(), dev(rng.integers(-2, FB.shape[0] + 5, 3000).astype(np.int32))):
                 got = B.closest_point(Q, cut, hint=hint)
-                for k in ref:
-                    assert torch.equal(got[k], ref[k]), k
+                assert_same_up_to_near_ties(got, ref)
     finally:
         set_query_group(0)
 

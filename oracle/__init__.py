@@ -55,6 +55,8 @@ def lib():
         L.orc_sort_pairs.argtypes = [U32P, I64, U32P, I32P]
         L.orc_karras.restype = None
         L.orc_karras.argtypes = [U32P, I64, I32P, I32P, I32P, I32P, I32P]
+        L.orc_ploc.restype = None
+        L.orc_ploc.argtypes = [F32P, I64, C.c_int, I32P, I32P, I32P, I32P, I32P, I32P]
         L.orc_node_boxes.restype = None
         L.orc_node_boxes.argtypes = [F32P, I32P, I32P, I64, I32P, I32P, F32P]
         L.orc_bind_gaussians.restype = C.c_int64
@@ -156,6 +158,43 @@ def karras(sorted_keys):
     if n <= 1:
         return (left[:0], right[:0], parent[:max(2 * n - 1, 0)], first[:0], last[:0])
     return left, right, parent, first, last
+
+
+def leaf_boxes(V, F, perm):
+    """[n, 6] float32 boxes (lo, hi) of the faces perm[0..n-1] (exact min / max)."""
+    V = np.asarray(V, np.float32)
+    tri = V[np.asarray(F)[np.asarray(perm)]]
+    return np.ascontiguousarray(np.concatenate([tri.min(1), tri.max(1)], 1), dtype=np.float32)
+
+
+def ploc(leaf_box, radius=16):
+    """Agglomerative tree (orc_ploc) over leaf boxes in Morton order:
+    (order, left, right, parent, first, last) in the layout of karras()."""
+    lb = np.ascontiguousarray(leaf_box, dtype=np.float32)
+    n = lb.shape[0]
+    m = max(n - 1, 1)
+    order = np.zeros(max(n, 1), np.int32)
+    left = np.zeros(m, np.int32)
+    right = np.zeros(m, np.int32)
+    first = np.zeros(m, np.int32)
+    last = np.zeros(m, np.int32)
+    parent = np.zeros(max(2 * n - 1, 1), np.int32)
+    lib().orc_ploc(lb, n, int(radius), order, left, right, parent, first, last)
+    if n <= 1:
+        return (order[:n], left[:0], right[:0], parent[:max(2 * n - 1, 0)], first[:0], last[:0])
+    return order, left, right, parent, first, last
+
+
+def build_ploc(V, F, radius=16):
+    """Whole serial agglomerative build: the Morton order of build_lbvh, orc_ploc over
+    its leaf boxes, and the node boxes of the resulting layout."""
+    keys = morton(V, F)
+    sk, perm0 = sort_pairs(keys)
+    order, left, right, parent, first, last = ploc(leaf_boxes(V, F, perm0), radius)
+    perm = perm0[order]
+    boxes = node_boxes(V, F, perm, first, last)
+    return dict(keys=keys, leaf_keys=sk[order], perm=perm, left=left, right=right, parent=parent,
+                first=first, last=last, boxes=boxes)
 
 
 def node_boxes(V, F, perm, first, last):

@@ -328,6 +328,134 @@ void orc_karras(const uint32_t *k, int64_t n, int32_t *left, int32_t *right, int
 }
 
 /* ------------------------------------------------------------------ */
+/* Agglomerative tree for a mesh whose topology is fixed (built once):  */
+/* parallel locally-ordered clustering, PLOC (Meister & Bittner 2018),  */
+/* written as its iterations, serially.  Clusters start as the leaves   */
+/* in Morton order, each with its face's box.  One iteration:           */
+/*   1. every cluster i picks, among clusters i-R..i+R (not i), the one */
+/*      whose union box with its own has the least surface area        */
+/*      (float32, (dx dy + dy dz) + dz dx, no fused multiply-add; ties  */
+/*      to the lower index);                                            */
+/*   2. every mutual pair (nn[nn[i]] == i) merges into a new node, left */
+/*      child the lower position, which takes that position; the other  */
+/*      cluster is removed (new nodes numbered in position order);      */
+/*   3. the clusters are compacted in order.                            */
+/* An iteration without a mutual pair (impossible for finite boxes,     */
+/* since the least-cost pair with the lowest indices is mutual) merges  */
+/* positions 0 and 1.  The tree is then laid out like orc_karras's:     */
+/* leaves in in-order, internal node numbered by the end of its range   */
+/* not shared with its sibling (root 0, a left child by its last leaf,  */
+/* a right child by its first), which is a bijection for any binary     */
+/* tree over in-order leaves.                                           */
+/* leaf_box: [n][6] float boxes of the leaves in Morton order.          */
+/* order[p]: Morton position of the leaf at in-order position p.        */
+/* left/right/parent/first/last as orc_karras (children: internal k,    */
+/* leaf p as -(p+1); parent: internal nodes then leaves, -1 at root).   */
+/* ------------------------------------------------------------------ */
+static float ploc_area(const float *b) {
+    float dx = b[3] - b[0], dy = b[4] - b[1], dz = b[5] - b[2];
+    return (dx * dy + dy * dz) + dz * dx;
+}
+
+static void ploc_union(const float *a, const float *b, float *out) {
+    for (int c = 0; c < 3; ++c) {
+        out[c] = a[c] < b[c] ? a[c] : b[c];
+        out[3 + c] = a[3 + c] > b[3 + c] ? a[3 + c] : b[3 + c];
+    }
+}
+
+void orc_ploc(const float *leaf_box, int64_t n, int radius, int32_t *order, int32_t *left,
+              int32_t *right, int32_t *parent, int32_t *first, int32_t *last) {
+    if (n <= 0) return;
+    for (int64_t i = 0; i < 2 * n - 1; ++i) parent[i] = -1;
+    if (n == 1) { order[0] = 0; return; }
+    int64_t m = n, made = 0;
+    int32_t *cl = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t *nn = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    float *cb = (float *)malloc(sizeof(float) * 6 * (size_t)n);
+    int32_t *cl_l = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n - 1));
+    int32_t *cl_r = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n - 1));
+    int32_t *cnt = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n - 1));
+    int32_t *pos = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n - 1));
+    int32_t *kid = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n - 1));
+    for (int64_t j = 0; j < n; ++j) {
+        cl[j] = -(int32_t)(j + 1);
+        memcpy(cb + 6 * j, leaf_box + 6 * j, 6 * sizeof(float));
+    }
+    while (m > 1) {
+        for (int64_t i = 0; i < m; ++i) {                        /* 1. nearest neighbour */
+            float best = INFINITY, u[6];
+            int64_t bj = -1;
+            for (int64_t j = i - radius; j <= i + radius; ++j) {
+                if (j < 0 || j >= m || j == i) continue;
+                ploc_union(cb + 6 * i, cb + 6 * j, u);
+                float a = ploc_area(u);
+                if (bj < 0 || a < best) { best = a; bj = j; }
+            }
+            nn[i] = (int32_t)bj;
+        }
+        int64_t merges = 0;
+        for (int64_t i = 0; i < m; ++i) merges += nn[nn[i]] == i && i < nn[i];
+        if (merges == 0) { nn[0] = 1; nn[1] = 0; }
+        int64_t w = 0;
+        for (int64_t i = 0; i < m; ++i) {                        /* 2. merge, 3. compact */
+            int64_t j = nn[i];
+            int mutual = nn[j] == i;
+            if (mutual && i > j) continue;
+            if (mutual) {
+                int64_t c = made++;
+                int32_t a = cl[i], b = cl[j];
+                cl_l[c] = a;
+                cl_r[c] = b;
+                cnt[c] = (a < 0 ? 1 : cnt[a]) + (b < 0 ? 1 : cnt[b]);
+                float u[6];
+                ploc_union(cb + 6 * i, cb + 6 * j, u);
+                cl[w] = (int32_t)c;
+                memcpy(cb + 6 * w, u, sizeof u);
+            } else {
+                cl[w] = cl[i];
+                memmove(cb + 6 * w, cb + 6 * i, 6 * sizeof(float));
+            }
+            ++w;
+        }
+        m = w;
+    }
+    /* layout: parents were made after their children, so walk back */
+    int64_t root = cl[0];
+    pos[root] = 0;
+    kid[root] = 0;
+    for (int64_t c = made - 1; c >= 0; --c) {
+        int32_t k = kid[c], p = pos[c];
+        first[k] = p;
+        last[k] = p + cnt[c] - 1;
+        int32_t a = cl_l[c], b = cl_r[c];
+        int32_t ca = a < 0 ? 1 : cnt[a];
+        if (a < 0) {
+            order[p] = -a - 1;
+            left[k] = -(p + 1);
+            parent[(n - 1) + p] = k;
+        } else {
+            pos[a] = p;
+            kid[a] = p + ca - 1;
+            left[k] = kid[a];
+            parent[kid[a]] = k;
+        }
+        int32_t rp = p + ca;
+        if (b < 0) {
+            order[rp] = -b - 1;
+            right[k] = -(rp + 1);
+            parent[(n - 1) + rp] = k;
+        } else {
+            pos[b] = rp;
+            kid[b] = rp;
+            right[k] = rp;
+            parent[rp] = k;
+        }
+    }
+    free(cl); free(nn); free(cb); free(cl_l); free(cl_r); free(cnt); free(pos); free(kid);
+}
+
+/* ------------------------------------------------------------------ */
 /* Node bounding boxes: for every node, the componentwise min / max of  */
 /* the vertices of all faces in its sorted range, taken directly over   */
 /* the range (not as a union of child boxes).  Exact in float32.        */

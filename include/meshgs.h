@@ -125,6 +125,28 @@ mesh_status mesh_bvh_get_layout(const mesh_bvh *bvh, mesh_bvh_layout *out);
 mesh_status mesh_build_lbvh(mesh_bvh *bvh, const float *d_V, int64_t nV, const int32_t *d_F,
                             int64_t nF, void *d_ws, size_t ws_bytes, void *stream);
 
+/* Agglomerative build for a mesh whose topology is fixed (built once from the
+ * template faces, Sec. 3.4, then refit every frame): the same vertex/face
+ * tables and Morton order as mesh_build_lbvh, then parallel locally-ordered
+ * clustering (PLOC, Meister & Bittner 2018) over the sorted leaves -- every
+ * cluster picks the cluster within 16 positions whose union box has the least
+ * surface area (float32, (dx dy + dy dz) + dz dx without fused multiply-add;
+ * ties to the lower position), mutual pairs merge at the lower position, the
+ * clusters are compacted, until one is left.  The tree is laid out like the
+ * Karras tree (leaves in in-order, an internal node numbered by the end of its
+ * leaf range not shared with its sibling, root 0), so refit, every query and
+ * the batched and backward entry points use it unchanged; d_keys then holds
+ * the leaves' Morton keys in leaf order (not sorted).  Its boxes have a lower
+ * surface-area cost than the Karras tree's, so queries visit fewer nodes.
+ * SYNCHRONOUS: the host reads the cluster count back after every iteration
+ * (tens of iterations), so the call returns when the build is done and must
+ * not be captured in a CUDA graph.  d_ws: mesh_build_ploc_workspace_bytes(nF),
+ * 256-byte aligned.  Argument errors as mesh_build_lbvh; MESH_ERR_CUDA also
+ * when an iteration's counts are inconsistent (the build then stops). */
+size_t mesh_build_ploc_workspace_bytes(int64_t max_faces);
+mesh_status mesh_build_ploc(mesh_bvh *bvh, const float *d_V, int64_t nV, const int32_t *d_F,
+                            int64_t nF, void *d_ws, size_t ws_bytes, void *stream);
+
 /* Morton order of a point set, for query coherence: d_order [n] receives the
  * permutation that sorts the points by the 30-bit key of mesh_build_lbvh (a
  * point p keyed as the zero-area face (p, p, p), over the points' own box),

@@ -52,6 +52,8 @@ SIGNATURES = {
     "mesh_bvh_destroy": (None, [VP]),
     "mesh_bvh_get_layout": (C.c_int, [VP, C.POINTER(Layout)]),
     "mesh_build_lbvh": (C.c_int, [VP, VP, I64, VP, I64, VP, SZ, VP]),
+    "mesh_build_ploc_workspace_bytes": (SZ, [I64]),
+    "mesh_build_ploc": (C.c_int, [VP, VP, I64, VP, I64, VP, SZ, VP]),
     "mesh_morton_order_workspace_bytes": (SZ, [I64]),
     "mesh_morton_order": (C.c_int, [VP, I64, VP, VP, SZ, VP]),
     "mesh_update_vertices": (C.c_int, [VP, VP, I64, VP]),

@@ -90,19 +90,31 @@ class MeshBVH:
             self.handle = None
 
     @classmethod
-    def from_mesh(cls, V: torch.Tensor, F: torch.Tensor) -> "MeshBVH":
+    def from_mesh(cls, V: torch.Tensor, F: torch.Tensor, method: str = "lbvh") -> "MeshBVH":
         b = cls(V.shape[0], F.shape[0], V.device)
-        b.build(V, F)
+        b.build(V, F, method)
         return b
 
     # -- the update steps -------------------------------------------------
-    def build(self, V: torch.Tensor, F: torch.Tensor) -> "MeshBVH":
+    def build(self, V: torch.Tensor, F: torch.Tensor, method: str = "lbvh") -> "MeshBVH":
+        """Build the tree over (V, F).  "lbvh": Karras's radix tree (mesh_build_lbvh,
+        asynchronous, the per-frame rebuild).  "ploc": agglomerative clustering
+        (mesh_build_ploc, synchronous) -- a tree with fewer node visits per query, for
+        a mesh built once and then refit."""
         V = _f32(V, 3, "V")
         F = _i32(F, 3, "F")
-        ws = self._ws.get(lib().mesh_build_workspace_bytes(F.shape[0]))
-        check(lib().mesh_build_lbvh(self.handle, V.data_ptr(), V.shape[0], F.data_ptr(),
-                                    F.shape[0], ws.data_ptr(), ws.numel(), _stream()),
-              "mesh_build_lbvh")
+        if method == "lbvh":
+            ws = self._ws.get(lib().mesh_build_workspace_bytes(F.shape[0]))
+            check(lib().mesh_build_lbvh(self.handle, V.data_ptr(), V.shape[0], F.data_ptr(),
+                                        F.shape[0], ws.data_ptr(), ws.numel(), _stream()),
+                  "mesh_build_lbvh")
+        elif method == "ploc":
+            ws = self._ws.get(lib().mesh_build_ploc_workspace_bytes(F.shape[0]))
+            check(lib().mesh_build_ploc(self.handle, V.data_ptr(), V.shape[0], F.data_ptr(),
+                                        F.shape[0], ws.data_ptr(), ws.numel(), _stream()),
+                  "mesh_build_ploc")
+        else:
+            raise ValueError(f"unknown build method {method!r}")
         self.n_verts, self.n_faces = V.shape[0], F.shape[0]
         return self
 

@@ -11,6 +11,8 @@
 #include <cstring>
 
 #include <climits>
+#include <utility>
+#include <vector>
 
 #include "common.cuh"
 #include "gauss_math.cuh"
@@ -1015,6 +1017,206 @@ static mesh_bvh_layout storage_layout(int64_t maxV, int64_t maxF) {
 
 constexpr int64_t kMaxFaces = (int64_t)1 << 30;
 
+// ---------------------------------------------------------------------------
+// Agglomerative build for a mesh whose topology is fixed (built once from the
+// template faces, then refit every frame): parallel locally-ordered
+// clustering, PLOC (Meister & Bittner 2018), over the Morton-sorted leaves.
+// One iteration: every cluster picks, among the clusters within kPlocRadius
+// positions, the one whose union box has the least surface area (float32,
+// (dx dy + dy dz) + dz dx, round-to-nearest without fused multiply-add; ties
+// to the lower position); mutual pairs merge into a new node at the lower
+// position (new nodes numbered in position order); the clusters are
+// compacted in order.  The finished tree is laid out like the Karras tree:
+// leaves in in-order, an internal node numbered by the end of its range not
+// shared with its sibling (root 0; a left child by its last leaf, a right
+// child by its first), which is a bijection for any binary tree over in-order
+// leaves, so the bottom-up kernels and every traversal use it unchanged.
+// ---------------------------------------------------------------------------
+constexpr int kPlocRadius = 16;
+constexpr int kPlocBlock = 256;
+
+__device__ __forceinline__ float ploc_min(float a, float b) { return a < b ? a : b; }
+__device__ __forceinline__ float ploc_max(float a, float b) { return a > b ? a : b; }
+
+__device__ __forceinline__ float ploc_union_area(float4 la, float4 ha, float4 lb, float4 hb) {
+    float dx = __fsub_rn(ploc_max(ha.x, hb.x), ploc_min(la.x, lb.x));
+    float dy = __fsub_rn(ploc_max(ha.y, hb.y), ploc_min(la.y, lb.y));
+    float dz = __fsub_rn(ploc_max(ha.z, hb.z), ploc_min(la.z, lb.z));
+    return __fadd_rn(__fadd_rn(__fmul_rn(dx, dy), __fmul_rn(dy, dz)), __fmul_rn(dz, dx));
+}
+
+// Leaf j of the Morton order: its face's box, cluster handle -(j+1).
+__global__ void k_ploc_leaves(int n, const int *__restrict__ perm0, const int4 *__restrict__ faces,
+                              const float4 *__restrict__ verts, int *__restrict__ cl,
+                              float4 *__restrict__ cb) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    int4 fv = faces[perm0[j]];
+    float4 a = verts[fv.x], b = verts[fv.y], c = verts[fv.z];
+    cb[2 * (size_t)j] = make_float4(ploc_min(ploc_min(a.x, b.x), c.x), ploc_min(ploc_min(a.y, b.y), c.y),
+                                    ploc_min(ploc_min(a.z, b.z), c.z), 0.0f);
+    cb[2 * (size_t)j + 1] = make_float4(ploc_max(ploc_max(a.x, b.x), c.x), ploc_max(ploc_max(a.y, b.y), c.y),
+                                        ploc_max(ploc_max(a.z, b.z), c.z), 0.0f);
+    cl[j] = -(j + 1);
+}
+
+// Nearest neighbour of every cluster within the radius; the block's clusters and
+// the radius on either side are staged in shared memory.
+__global__ void __launch_bounds__(kPlocBlock)
+k_ploc_nn(int m, const float4 *__restrict__ cb, int *__restrict__ nn) {
+    __shared__ float4 s_lo[kPlocBlock + 2 * kPlocRadius], s_hi[kPlocBlock + 2 * kPlocRadius];
+    const int base = blockIdx.x * kPlocBlock;
+    for (int t = threadIdx.x; t < kPlocBlock + 2 * kPlocRadius; t += kPlocBlock) {
+        int g = base - kPlocRadius + t;
+        if (g >= 0 && g < m) {
+            s_lo[t] = cb[2 * (size_t)g];
+            s_hi[t] = cb[2 * (size_t)g + 1];
+        }
+    }
+    __syncthreads();
+    const int i = base + threadIdx.x;
+    if (i >= m) return;
+    const int si = threadIdx.x + kPlocRadius;
+    float4 lo = s_lo[si], hi = s_hi[si];
+    float best = INFINITY;
+    int bj = -1;
+    for (int d = -kPlocRadius; d <= kPlocRadius; ++d) {
+        int j = i + d;
+        if (d == 0 || j < 0 || j >= m) continue;
+        float a = ploc_union_area(lo, hi, s_lo[si + d], s_hi[si + d]);
+        if (bj < 0 || a < best) { best = a; bj = j; }
+    }
+    nn[i] = bj;
+}
+
+// keep: the cluster survives the iteration (it is not the upper half of a pair);
+// merge: it is the lower half of a mutual pair.
+__global__ void k_ploc_flags(int m, const int *__restrict__ nn, int *__restrict__ keep,
+                             int *__restrict__ merge) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    int j = nn[i];
+    bool mutual = j >= 0 && nn[j] == i;
+    keep[i] = !(mutual && i > j);
+    merge[i] = mutual && i < j;
+}
+
+// An iteration without a mutual pair (possible only for non-finite boxes) merges
+// positions 0 and 1, as the oracle does.
+__global__ void k_ploc_force(int *nn) {
+    nn[0] = 1;
+    nn[1] = 0;
+}
+
+__global__ void k_ploc_compact(int m, const int *__restrict__ cl_in, const float4 *__restrict__ cb_in,
+                               const int *__restrict__ nn, const int *__restrict__ keep,
+                               const int *__restrict__ kpos, const int *__restrict__ merge,
+                               const int *__restrict__ mpos, int node_base, int *__restrict__ cl_out,
+                               float4 *__restrict__ cb_out, int *__restrict__ cl_l, int *__restrict__ cl_r,
+                               int *__restrict__ cnt) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m || !keep[i]) return;
+    int dst = kpos[i];
+    float4 lo = cb_in[2 * (size_t)i], hi = cb_in[2 * (size_t)i + 1];
+    if (merge[i]) {
+        int j = nn[i], c = node_base + mpos[i];
+        int a = cl_in[i], b = cl_in[j];
+        cl_l[c] = a;
+        cl_r[c] = b;
+        cnt[c] = (a < 0 ? 1 : cnt[a]) + (b < 0 ? 1 : cnt[b]);
+        float4 lb = cb_in[2 * (size_t)j], hb = cb_in[2 * (size_t)j + 1];
+        lo = make_float4(ploc_min(lo.x, lb.x), ploc_min(lo.y, lb.y), ploc_min(lo.z, lb.z), 0.0f);
+        hi = make_float4(ploc_max(hi.x, hb.x), ploc_max(hi.y, hb.y), ploc_max(hi.z, hb.z), 0.0f);
+        cl_out[dst] = c;
+    } else {
+        cl_out[dst] = cl_in[i];
+    }
+    cb_out[2 * (size_t)dst] = lo;
+    cb_out[2 * (size_t)dst + 1] = hi;
+}
+
+__global__ void k_ploc_root(int root, int *pos, int *kid, int *parent) {
+    pos[root] = 0;
+    kid[root] = 0;
+    parent[0] = -1;
+}
+
+// Top-down layout of the nodes made in one iteration (their parents, made
+// later, are already placed): leaf positions, Karras numbers, parent links,
+// far ends, and the leaf-order face ids and keys.
+__global__ void k_ploc_place(int base, int count, int n, const int *__restrict__ cl_l,
+                             const int *__restrict__ cl_r, const int *__restrict__ cnt, int *pos, int *kid,
+                             const int *__restrict__ perm0, const unsigned int *__restrict__ sk,
+                             int *__restrict__ perm, unsigned int *__restrict__ keys,
+                             int *__restrict__ parent, int *__restrict__ rend) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= count) return;
+    int c = base + t;
+    int p = pos[c], k = kid[c];
+    rend[k] = k == p ? p + cnt[c] - 1 : p;
+    int a = cl_l[c], b = cl_r[c];
+    int ca = a < 0 ? 1 : cnt[a];
+    if (a < 0) {
+        int j = -a - 1;
+        perm[p] = perm0[j];
+        keys[p] = sk[j];
+        parent[(n - 1) + p] = 2 * k;
+    } else {
+        pos[a] = p;
+        kid[a] = p + ca - 1;
+        parent[p + ca - 1] = 2 * k;
+    }
+    int rp = p + ca;
+    if (b < 0) {
+        int j = -b - 1;
+        perm[rp] = perm0[j];
+        keys[rp] = sk[j];
+        parent[(n - 1) + rp] = 2 * k + 1;
+    } else {
+        pos[b] = rp;
+        kid[b] = rp;
+        parent[rp] = 2 * k + 1;
+    }
+}
+
+struct PlocWs {
+    BuildWs sort;
+    unsigned int *sk;
+    int *perm0, *clA, *clB, *nn, *keep, *kpos, *merge, *mpos, *bsumA, *bsumB, *tot, *cl_l, *cl_r, *cnt,
+        *pos, *kid;
+    float4 *cbA, *cbB;
+    size_t bytes;
+};
+
+static PlocWs ploc_ws_layout(char *base, int64_t nF) {
+    PlocWs w{};
+    w.sort = build_ws_layout(base, nF);
+    int64_t n = nF > 0 ? nF : 1;
+    size_t off = align_up(w.sort.bytes, 256);
+    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return base + o; };
+    w.sk = (unsigned int *)take(4 * n);
+    w.perm0 = (int *)take(4 * n);
+    w.clA = (int *)take(4 * n);
+    w.clB = (int *)take(4 * n);
+    w.nn = (int *)take(4 * n);
+    w.keep = (int *)take(4 * n);
+    w.kpos = (int *)take(4 * n);
+    w.merge = (int *)take(4 * n);
+    w.mpos = (int *)take(4 * n);
+    w.bsumA = (int *)take(4 * ((n + 1023) / 1024) + 4);
+    w.bsumB = (int *)take(4 * ((n + 1023) / 1024) + 4);
+    w.tot = (int *)take(16);
+    w.cl_l = (int *)take(4 * n);
+    w.cl_r = (int *)take(4 * n);
+    w.cnt = (int *)take(4 * n);
+    w.pos = (int *)take(4 * n);
+    w.kid = (int *)take(4 * n);
+    w.cbA = (float4 *)take(32 * n);
+    w.cbB = (float4 *)take(32 * n);
+    w.bytes = off;
+    return w;
+}
+
 }  // namespace meshgs
 
 using namespace meshgs;
@@ -1120,14 +1322,10 @@ mesh_status mesh_refit(mesh_bvh *bvh, const float *d_V, int64_t nV, void *stream
     return bottom_up(bvh, d_V, (cudaStream_t)stream);
 }
 
-mesh_status mesh_build_lbvh(mesh_bvh *bvh, const float *d_V, int64_t nV, const int32_t *d_F,
-                            int64_t nF, void *d_ws, size_t ws_bytes, void *stream) {
-    if (!bvh || nV < 0 || nF < 0 || nV > bvh->L.max_verts || nF > bvh->L.max_faces)
-        return MESH_ERR_INVALID_ARG;
-    if ((nV > 0 && !d_V) || (nF > 0 && (!d_F || nV == 0))) return MESH_ERR_INVALID_ARG;
-    BuildWs w = build_ws_layout((char *)d_ws, nF);
-    if (nF > 0 && (!d_ws || ws_bytes < w.bytes || ((uintptr_t)d_ws & 255u))) return MESH_ERR_WORKSPACE;
-    cudaStream_t s = (cudaStream_t)stream;
+// The part both builds share: vertex and face tables, face centroids and
+// their Morton keys (in w.keysA / w.valsA, ready for the sort).
+static void build_keys(mesh_bvh *bvh, const float *d_V, int64_t nV, const int32_t *d_F, int64_t nF,
+                       const BuildWs &w, cudaStream_t s) {
     bvh->L.n_verts = nV;
     bvh->L.n_faces = nF;
     bvh->adj_ready = false;
@@ -1138,11 +1336,24 @@ mesh_status mesh_build_lbvh(mesh_bvh *bvh, const float *d_V, int64_t nV, const i
             d_V, (int)nV, bvh->verts(), n > 0 ? w.cbox : nullptr);
         count_launch();
     }
-    if (n == 0) return check_launch();
+    if (n == 0) return;
     k_faces_centroids<<<grid_for(n, kBlock), kBlock, 0, s>>>(d_F, n, (int)nV, bvh->verts(),
                                                              bvh->faces(), w.cent, w.cbox, bvh->hdr());
     k_morton<<<grid_for(n, kBlock), kBlock, 0, s>>>(w.cent, n, w.cbox, w.keysA, w.valsA);
     count_launch(2);
+}
+
+mesh_status mesh_build_lbvh(mesh_bvh *bvh, const float *d_V, int64_t nV, const int32_t *d_F,
+                            int64_t nF, void *d_ws, size_t ws_bytes, void *stream) {
+    if (!bvh || nV < 0 || nF < 0 || nV > bvh->L.max_verts || nF > bvh->L.max_faces)
+        return MESH_ERR_INVALID_ARG;
+    if ((nV > 0 && !d_V) || (nF > 0 && (!d_F || nV == 0))) return MESH_ERR_INVALID_ARG;
+    BuildWs w = build_ws_layout((char *)d_ws, nF);
+    if (nF > 0 && (!d_ws || ws_bytes < w.bytes || ((uintptr_t)d_ws & 255u))) return MESH_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    int n = (int)nF;
+    build_keys(bvh, d_V, nV, d_F, nF, w, s);
+    if (n == 0) return check_launch();
     radix_sort_pairs(w, n, bvh->keys(), bvh->perm(), s);
     if (n > 1) {
         k_karras<<<grid_for(n - 1, kBlock), kBlock, 0, s>>>(bvh->keys(), n, bvh->nodes(),
@@ -1150,6 +1361,79 @@ mesh_status mesh_build_lbvh(mesh_bvh *bvh, const float *d_V, int64_t nV, const i
         count_launch();
     } else {
         cudaMemsetAsync(bvh->parent(), 0xff, sizeof(int), s);   // lone leaf: no parent
+    }
+    return bottom_up(bvh, nullptr, s);
+}
+
+size_t mesh_build_ploc_workspace_bytes(int64_t max_faces) {
+    if (max_faces < 0 || max_faces > kMaxFaces) return 0;
+    return ploc_ws_layout(nullptr, max_faces).bytes;
+}
+
+mesh_status mesh_build_ploc(mesh_bvh *bvh, const float *d_V, int64_t nV, const int32_t *d_F,
+                            int64_t nF, void *d_ws, size_t ws_bytes, void *stream) {
+    if (!bvh || nV < 0 || nF < 0 || nV > bvh->L.max_verts || nF > bvh->L.max_faces)
+        return MESH_ERR_INVALID_ARG;
+    if ((nV > 0 && !d_V) || (nF > 0 && (!d_F || nV == 0))) return MESH_ERR_INVALID_ARG;
+    PlocWs w = ploc_ws_layout((char *)d_ws, nF);
+    if (nF > 0 && (!d_ws || ws_bytes < w.bytes || ((uintptr_t)d_ws & 255u))) return MESH_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    int n = (int)nF;
+    build_keys(bvh, d_V, nV, d_F, nF, w.sort, s);
+    if (n == 0) return check_launch();
+    if (n == 1) {                                     // a lone leaf, as mesh_build_lbvh leaves it
+        radix_sort_pairs(w.sort, n, bvh->keys(), bvh->perm(), s);
+        cudaMemsetAsync(bvh->parent(), 0xff, sizeof(int), s);
+        return bottom_up(bvh, nullptr, s);
+    }
+    radix_sort_pairs(w.sort, n, w.sk, w.perm0, s);
+    k_ploc_leaves<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, w.perm0, bvh->faces(), bvh->verts(), w.clA, w.cbA);
+    count_launch();
+    std::vector<int2> batches;                        // (first node, count) made per iteration
+    int m = n, made = 0;
+    int *cl_in = w.clA, *cl_out = w.clB;
+    float4 *cb_in = w.cbA, *cb_out = w.cbB;
+    auto flags_and_counts = [&](int tot[2]) -> mesh_status {
+        k_ploc_flags<<<grid_for(m, kBlock), kBlock, 0, s>>>(m, w.nn, w.keep, w.merge);
+        count_launch();
+        exclusive_scan_int(w.keep, w.kpos, m, w.bsumA, w.tot, s);
+        exclusive_scan_int(w.merge, w.mpos, m, w.bsumB, w.tot + 1, s);
+        if (cudaMemcpyAsync(tot, w.tot, 2 * sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return MESH_ERR_CUDA;
+        return MESH_OK;
+    };
+    while (m > 1) {
+        k_ploc_nn<<<(m + kPlocBlock - 1) / kPlocBlock, kPlocBlock, 0, s>>>(m, cb_in, w.nn);
+        count_launch();
+        int tot[2] = {0, 0};                          // clusters kept, nodes made
+        mesh_status st = flags_and_counts(tot);
+        if (st != MESH_OK) return st;
+        if (tot[1] == 0) {
+            k_ploc_force<<<1, 1, 0, s>>>(w.nn);
+            count_launch();
+            if ((st = flags_and_counts(tot)) != MESH_OK) return st;
+        }
+        // every node made removes one cluster; anything else means the device
+        // state is not what the iteration wrote, so stop before using it
+        if (tot[1] < 1 || tot[0] != m - tot[1] || made + tot[1] > n - 1) return MESH_ERR_CUDA;
+        k_ploc_compact<<<grid_for(m, kBlock), kBlock, 0, s>>>(m, cl_in, cb_in, w.nn, w.keep, w.kpos, w.merge,
+                                                            w.mpos, made, cl_out, cb_out, w.cl_l, w.cl_r,
+                                                            w.cnt);
+        count_launch();
+        batches.push_back(make_int2(made, tot[1]));
+        made += tot[1];
+        m = tot[0];
+        std::swap(cl_in, cl_out);
+        std::swap(cb_in, cb_out);
+    }
+    k_ploc_root<<<1, 1, 0, s>>>(made - 1, w.pos, w.kid, bvh->parent());
+    count_launch();
+    for (auto it = batches.rbegin(); it != batches.rend(); ++it) {
+        k_ploc_place<<<grid_for(it->y, kBlock), kBlock, 0, s>>>(it->x, it->y, n, w.cl_l, w.cl_r, w.cnt, w.pos,
+                                                              w.kid, w.perm0, w.sk, bvh->perm(), bvh->keys(),
+                                                              bvh->parent(), bvh->rend());
+        count_launch();
     }
     return bottom_up(bvh, nullptr, s);
 }

@@ -1,0 +1,122 @@
+"""GPU agglomerative build (mesh_build_ploc) against the oracle's PLOC tree: leaf
+order, leaf-order keys, children, parents and node boxes bit-exact on meshes from
+one face to 200k faces (ties of equal boxes, zero-area faces, ragged blocks);
+refit of that topology equal to the oracle's boxes; NearestSurface on it equal to
+the brute-force oracle and to the Karras tree's answers; fewer node visits than
+the Karras tree on the contact workload."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2606_00444_gb300 import MeshBVH
+from parity import assert_same_up_to_near_ties, check_closest, dev, gpu_boxes, host
+from workloads.isosurface import BlobSequence
+from workloads.meshes import displaced_icosphere, icosphere, torus, TorusSkinning
+from workloads.sampling import uniform_box
+
+pytestmark = pytest.mark.gpu
+
+
+def check_ploc(V, F, bvh=None):
+    n = F.shape[0]
+    if bvh is None:
+        bvh = MeshBVH.from_mesh(dev(V), dev(F), method="ploc")
+    T = oracle.build_ploc(V, F)
+    A = bvh.arrays()
+    torch.cuda.synchronize()
+    assert np.array_equal(host(A["perm"]), T["perm"]), "leaf order"
+    assert np.array_equal(host(A["keys"]).view(np.uint32), T["leaf_keys"]), "leaf-order keys"
+    if n > 1:
+        ni = host(A["nodes_i"])
+        assert np.array_equal(ni[:, 0, 3], T["left"]), "left children"
+        assert np.array_equal(ni[:, 2, 3], T["right"]), "right children"
+        par = host(A["parent"])
+        assert np.array_equal(par >> 1, T["parent"]), "parents"
+    assert np.array_equal(gpu_boxes(A, n), T["boxes"]), "node boxes"
+    tris = host(A["tris"])
+    assert np.array_equal(tris[:, :, :3], V[F[T["perm"]]]), "packed triangles"
+    assert bvh.status()[0] == 0
+    return bvh, T
+
+
+@pytest.mark.parametrize("name,maker", [
+    ("ico3", lambda: icosphere(3)),
+    ("c1_target", lambda: displaced_icosphere(4, 0.1, 1.3)),
+    ("torus_ragged", lambda: torus(37, 29)),
+    ("blob_frame", lambda: BlobSequence(2000).mesh(17, N=96)),
+])
+def test_build_bit_exact(name, maker):
+    V, F = maker()
+    check_ploc(V, F)
+
+
+def test_build_full_size_torus_200k():
+    V, F = torus(400, 250)
+    check_ploc(V, F)
+
+
+def test_tiny_ties_and_degenerate_inputs():
+    V = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [1, 1, 0], [2, 0.5, 0.3]], np.float32)
+    for F in ([[0, 1, 2]], [[0, 1, 2], [1, 3, 2]], [[0, 1, 2], [1, 3, 2], [1, 4, 3]],
+              [[0, 1, 2], [1, 3, 2], [1, 4, 3], [0, 4, 2], [3, 4, 0]]):
+        check_ploc(V, np.array(F, np.int32))
+    # 600 copies of one triangle: every union has the same area (ties everywhere)
+    Fs = np.tile(np.array([[0, 1, 2]], np.int32), (600, 1))
+    check_ploc(V, Fs)
+    # zero-area faces
+    Vd, Fd = icosphere(2)
+    Fd = Fd.copy()
+    Fd[::7, 1] = Fd[::7, 0]
+    check_ploc(Vd, Fd)
+
+
+def test_refit_of_the_ploc_topology():
+    V0, F = torus(120, 70)
+    sk = TorusSkinning(V0, seed=3003)
+    bvh, T = check_ploc(V0, F)
+    for t in (5, 40):
+        V = sk.frame(t)
+        bvh.refit(dev(V))
+        A = bvh.arrays()
+        torch.cuda.synchronize()
+        want = oracle.node_boxes(V, F, T["perm"], T["first"], T["last"])
+        assert np.array_equal(gpu_boxes(A, F.shape[0]), want)
+
+
+def test_queries_on_the_ploc_tree():
+    rng = np.random.default_rng(1000)
+    VG, FG = displaced_icosphere(4, 0.1, 2 * np.pi * rng.random())
+    Q = np.concatenate([icosphere(3)[0], uniform_box(4096, [-1.5] * 3, [1.5] * 3, seed=1001)])
+    ploc = MeshBVH.from_mesh(dev(VG), dev(FG), method="ploc")
+    lbvh = MeshBVH.from_mesh(dev(VG), dev(FG))
+    for cut in (np.inf, 0.05):
+        got = ploc.closest_point(dev(Q), cut)
+        check_closest(VG, FG, Q, got, max_dist=cut)
+        assert_same_up_to_near_ties(got, lbvh.closest_point(dev(Q), cut))
+
+
+def test_contact_workload_fewer_visits_same_answers():
+    """1M particles, cutoff 0.05, on a skinned frame of the 200k-face torus refit from
+    its rest pose: the agglomerative tree answers as the Karras tree does (up to near
+    ties), a sample agrees with the oracle, and it visits fewer nodes."""
+    from paper_2606_00444_gb300 import morton_order
+    V0, F = torus(400, 250)
+    sk = TorusSkinning(V0, seed=3000)
+    lo, hi = V0.min(0) - 0.2, V0.max(0) + 0.2
+    P = dev(uniform_box(1 << 20, lo, hi, seed=3002))
+    P = P[morton_order(P).long()].contiguous()
+    ploc = MeshBVH.from_mesh(dev(V0), dev(F), method="ploc")
+    lbvh = MeshBVH.from_mesh(dev(V0), dev(F))
+    V1 = sk.frame(30)
+    ploc.refit(dev(V1))
+    lbvh.refit(dev(V1))
+    got = ploc.closest_point(P, 0.05)
+    assert_same_up_to_near_ties(got, lbvh.closest_point(P, 0.05), max_frac=1e-5)
+    pick = np.random.default_rng(5).choice(P.shape[0], 400, replace=False)
+    idx = dev(pick.astype(np.int64))
+    check_closest(V1, F, host(P)[pick], {k: v[idx] for k, v in got.items()}, max_dist=0.05)
+    sp, sl = ploc.closest_point_stats(P, 0.05), lbvh.closest_point_stats(P, 0.05)
+    assert sp["hits"] == sl["hits"]
+    assert sp["visits"] < 0.95 * sl["visits"]
+    assert ploc.status()[0] == 0

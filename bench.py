@@ -469,9 +469,10 @@ def gpu_arm(args, rank, world, local_rank):
     return out, W
 
 
-def contact_traffic():
-    """DRAM bytes per launch of the contact kernel from the committed ncu capture, if the
-    kernel source is still the one that was captured (else None)."""
+def contact_traffic(variant: int):
+    """DRAM bytes per launch of the contact kernel in this traversal variant from the
+    committed ncu captures, if the kernel source is still the one that was captured
+    (else None)."""
     import hashlib
     p = os.path.join(ROOT, "profiles", "roofline_traffic.json")
     if not os.path.exists(p):
@@ -480,7 +481,9 @@ def contact_traffic():
     m = hashlib.sha256()
     for f in d.get("source_files", []):
         m.update(open(os.path.join(ROOT, f), "rb").read())
-    return d["traffic_bytes_per_launch"] if m.hexdigest()[:16] == d.get("source_hash") else None
+    if m.hexdigest()[:16] != d.get("source_hash"):
+        return None
+    return d.get("traffic_bytes_per_launch_by_variant", {}).get(str(variant))
 
 
 def peaks():
@@ -933,7 +936,7 @@ def main():
                                 "build_ms_once": res["ploc_build_ms"]},
         "roofline": {"kernel": "k_closest_point (contact, 1M queries, no warm start)", "bound": "hbm",
                      "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "peak_source": src, "traffic": contact_traffic(),
+                     "frac": achieved / hbm, "peak_source": src, "traffic": contact_traffic(res["tuned"]["variant"]) if res["tuned"]["lanes"] == 1 else None,
                      "bytes_per_query": per_query,
                      "per_query": {"io": CONTACT_BYTES, "node_visits": vis, "triangle_tests": tst,
                                    "node_bytes": NODE_BYTES, "triangle_bytes": TRI_BYTES},

@@ -709,7 +709,7 @@ def bench_sequence(args):
     maxF = max(len(f) for _, f in frames)
     maxV = max(len(v) for v, _ in frames)
     target = MeshBVH(maxV, maxF, dev)
-    tmpl = MeshBVH.from_mesh(VTd, FTd)
+    tmpl = MeshBVH.from_mesh(VTd, FTd, method="ploc")   # fixed topology: built once, refit
     gface = torch.arange(len(FT), dtype=torch.int32, device=dev)
     gbary = torch.full((len(FT), 3), 1.0 / 3.0, device=dev)
     sf, sb = sample_surface(VT, FT, N_CD, seed=2200)
@@ -782,7 +782,7 @@ def bench_tracking(args):
     tracker = TemporalTracker(V0d, maxV, maxF, k=4, reanchor_every=50, keep=0.8)
     target2 = MeshBVH(maxV, maxF, dev)
     proj = torch.empty_like(V0d)
-    conv = MeshBVH.from_mesh(V0d, F0d)              # the converted (fixed-topology) mesh
+    conv = MeshBVH.from_mesh(V0d, F0d, method="ploc")   # the converted (fixed-topology) mesh
     sf, sb = sample_surface(V0, F0, N_CD, seed=2400)
     sf, sb = t(sf), t(sb)
     ws = Workspace(dev)
@@ -843,8 +843,8 @@ def bench_fit(args):
     ns = 1 << 20
     ft, bt = sample_surface(VT, FT, ns, seed=5001)
     SG = t(points_from(VG, FG, *sample_surface(VG, FG, ns, seed=5002)))
-    tmpl = MeshBVH.from_mesh(t(VT), t(FT))
-    targ = MeshBVH.from_mesh(t(VG), t(FG))
+    tmpl = MeshBVH.from_mesh(t(VT), t(FT), method="ploc")   # built once, refit every step
+    targ = MeshBVH.from_mesh(t(VG), t(FG), method="ploc")   # static target
     VGd = t(VG)
     ft, bt = t(ft), t(bt)
     V = t(VT).requires_grad_(True)

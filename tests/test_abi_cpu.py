@@ -30,6 +30,8 @@ def test_every_declared_symbol_is_exported_and_bound():
 
 def test_sizes_are_monotone_and_reject_bad_input():
     L = lib()
+    assert L.mesh_build_ploc_workspace_bytes(200000) > L.mesh_build_workspace_bytes(200000)
+    assert L.mesh_build_ploc_workspace_bytes(-1) == 0
     s1 = L.mesh_bvh_storage_bytes(642, 1280)
     s2 = L.mesh_bvh_storage_bytes(100000, 200000)
     assert 0 < s1 < s2
@@ -60,6 +62,11 @@ def test_create_validates_storage_on_the_host():
     assert L.mesh_build_lbvh(h, None, 10, None, 16, None, 0, None) == 1
     assert L.mesh_build_lbvh(h, fake, 11, fake, 16, None, 0, None) == 1     # nV > max
     assert L.mesh_build_lbvh(h, fake, 10, fake, 16, None, 0, None) == 3     # no workspace
+    assert L.mesh_build_ploc(h, None, 10, None, 16, None, 0, None) == 1
+    assert L.mesh_build_ploc(h, fake, 11, fake, 16, None, 0, None) == 1     # nV > max
+    assert L.mesh_build_ploc(h, fake, 10, fake, 17, None, 0, None) == 1     # nF > max
+    assert L.mesh_build_ploc(h, fake, 10, fake, 16, None, 0, None) == 3     # no workspace
+    assert L.mesh_build_ploc(h, fake, 10, fake, 16, fake + 8, 1 << 30, None) == 3   # misaligned
     assert L.mesh_closest_point(None, fake, 4, C.c_float(1.0), None, None, None, None, None) == 1
     assert L.mesh_closest_point(h, fake, 4, C.c_float(-1.0), None, None, None, None, None) == 1
     assert L.mesh_closest_point(h, fake, 0, C.c_float(1.0), None, None, None, None, None) == 0

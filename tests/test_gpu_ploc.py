@@ -120,3 +120,80 @@ def test_contact_workload_fewer_visits_same_answers():
     assert sp["hits"] == sl["hits"]
     assert sp["visits"] < 0.95 * sl["visits"]
     assert ploc.status()[0] == 0
+
+
+def test_every_tree_consumer_runs_on_the_ploc_tree():
+    """Warm-started queries, the contact step, signed distance, k-NN projection, the fused
+    refit + rebind, Chamfer and the closest-point backward pass give on the agglomerative
+    tree what they give on the Karras tree of the same mesh (up to the order-dependent near
+    ties of the tie rule, for the nearest-face queries)."""
+    from paper_2606_00444_gb300 import chamfer, morton_order
+    from workloads.sampling import osada_barycentrics, sample_surface
+    V0, F = torus(120, 70)
+    sk = TorusSkinning(V0, seed=3001)
+    V1 = sk.frame(20)
+    ploc = MeshBVH.from_mesh(dev(V0), dev(F), method="ploc")
+    lbvh = MeshBVH.from_mesh(dev(V0), dev(F))
+    for b in (ploc, lbvh):
+        b.refit(dev(V1))
+    lo, hi = V0.min(0) - 0.2, V0.max(0) + 0.2
+    P = dev(uniform_box(40001, lo, hi, seed=3006))
+    P = P[morton_order(P).long()].contiguous()
+    # hinted queries and the contact step
+    ref = lbvh.closest_point(P, 0.05)
+    rng = np.random.default_rng(7)
+    hint = dev(rng.integers(-1, F.shape[0], P.shape[0]).astype(np.int32))
+    assert_same_up_to_near_ties(ploc.closest_point(P, 0.05, hint=hint), ref)
+    out = {k: v.clone() for k, v in ref.items()}
+    ploc.contact(P, 0.05, out)
+    assert_same_up_to_near_ties(out, ref)
+    # signed distance (same nearest face up to near ties, same signs)
+    sp, sl = ploc.signed_distance(P, 0.05), lbvh.signed_distance(P, 0.05)
+    same = sp["face"] == sl["face"]
+    assert (~same).sum().item() <= 4
+    a, b = sp["sdist"][same], sl["sdist"][same]
+    assert torch.equal(a.abs(), b.abs())
+    away = a.abs() > 1e-5                  # pseudo-normal sums use float atomics: compare signs
+    assert torch.equal(torch.sign(a[away]), torch.sign(b[away]))   # away from the surface
+    # k-NN weighted projection (k faces by distance: equal except near ties)
+    pk, fk, _ = ploc.knn_project(P[:5000], k=4, want_faces=True)
+    pl, fl, _ = lbvh.knn_project(P[:5000], k=4, want_faces=True)
+    rows = (fk == fl).all(1)
+    assert (~rows).sum().item() <= 10
+    assert torch.equal(pk[rows], pl[rows])
+    # fused refit + rebind: the Gaussians do not depend on the tree
+    counts = np.full(F.shape[0], 2, np.int32)
+    gstart = np.concatenate([[0], np.cumsum(counts)]).astype(np.int32)
+    gface = np.repeat(np.arange(F.shape[0], dtype=np.int32), counts)
+    gbary = osada_barycentrics(rng, int(gstart[-1])).astype(np.float32)
+    got = ploc.refit_bind(dev(V1), dev(gstart), dev(gbary))
+    want = lbvh.bind_gaussians(dev(gface), dev(gbary))
+    for x, y in zip(got, want):
+        torch.testing.assert_close(x, y, rtol=0, atol=1e-6)
+    # Chamfer against the rest mesh, per-sample results
+    rest_p = MeshBVH.from_mesh(dev(V0), dev(F), method="ploc")
+    rest_l = MeshBVH.from_mesh(dev(V0), dev(F))
+    sf, sb = (dev(a) for a in sample_surface(V0, F, 4000, seed=3007))
+    SA = ploc.interpolate(sf, sb)
+    SB = rest_l.interpolate(sf, sb)
+    cp, psp = chamfer(ploc, SA, rest_p, SB, per_sample=True)
+    cl, psl = chamfer(lbvh, SA, rest_l, SB, per_sample=True)
+    n = assert_same_up_to_near_ties(psp, psl, "faceA", "dist2A") + \
+        assert_same_up_to_near_ties(psp, psl, "faceB", "dist2B")
+    if n == 0:
+        assert torch.equal(cp, cl)
+    else:
+        assert torch.allclose(cp, cl, rtol=1e-6, atol=0.0)
+    # backward of the point-to-mesh distance
+    Q = P[:3000].contiguous()
+    rp, rl = ploc.closest_point(Q), lbvh.closest_point(Q)
+    same = rp["face"] == rl["face"]
+    g = torch.ones(Q.shape[0], device="cuda")
+    gQp, gVp = torch.empty_like(Q), torch.zeros(V1.shape[0], 3, device="cuda")
+    gQl, gVl = torch.empty_like(Q), torch.zeros(V1.shape[0], 3, device="cuda")
+    ploc.closest_point_backward(Q, rp["face"], rp["bary"], g, gQp, gVp)
+    lbvh.closest_point_backward(Q, rl["face"], rl["bary"], g, gQl, gVl)
+    assert torch.equal(gQp[same], gQl[same])
+    if bool(same.all()):
+        torch.testing.assert_close(gVp, gVl, rtol=1e-5, atol=1e-6)
+    assert ploc.status()[0] == 0

@@ -303,11 +303,16 @@ size_t mesh_contact_workspace_bytes(int64_t nQ);
 /* The contact query of a physics step: NearestSurface of the nQ particles
  * with cutoff max_dist, with d_face both the previous step's answers (read
  * first, as warm-start hints: -1 = none) and this step's (written).  The
- * queries are run in an order that puts those that touched the mesh last
- * step first (each group in its given order), so that a warp mostly holds
- * searches of one depth.  Answers equal mesh_closest_point's up to its
- * order-dependent near ties (the order and the hints change the work).  Traversal variants 1, 10-12 and
- * cooperative groups run unordered.  d_ws: mesh_contact_workspace_bytes(nQ). */
+ * queries run in the order of the previous step's work: each query's node
+ * visits give it a class (48 or more, 24-47, 12-23, fewer), kept in d_ws,
+ * and the next call runs the classes heaviest first, each in the given
+ * order, so that a warp holds searches of similar depth.  d_ws therefore
+ * carries state from one step to the next: pass the same workspace every
+ * step for the same particles; its contents steer only the order (a fresh
+ * or unrelated workspace gives a worse order, never a wrong answer).
+ * Answers equal mesh_closest_point's up to its order-dependent near ties.
+ * Traversal variants 1, 10-12 and cooperative groups run unordered without
+ * classes.  d_ws: mesh_contact_workspace_bytes(nQ), 256-byte aligned. */
 mesh_status mesh_contact(const mesh_bvh *bvh, const float *d_Q, int64_t nQ, float max_dist,
                          int32_t *d_face, float *d_bary, float *d_point, float *d_dist2, void *d_ws,
                          size_t ws_bytes, void *stream);

@@ -641,12 +641,20 @@ __device__ __forceinline__ void write_hit(const Traversal &T, const Hit &h, floa
 // kMinBlocks: resident blocks per SM the register budget must allow
 // (8 -> 64 registers, 12 -> 40, 16 -> 32; fewer registers, more warps to hide
 // latency, more spilling).
-template <int kSmem, int kMode, int kMinBlocks = kQueryMinBlocks>
+// Work class of a query from its node visits, heaviest first (the contact step
+// orders the next step's queries by it): 0: 48 or more, 1: 24-47, 2: 12-23, 3: fewer.
+__device__ __forceinline__ unsigned int work_class(int visits) {
+    return visits >= 48 ? 0u : visits >= 24 ? 1u : visits >= 12 ? 2u : 3u;
+}
+
+// kRecord: also count the node visits of each query and store its work class
+// in cls[i] (the contact step).
+template <int kSmem, int kMode, int kMinBlocks = kQueryMinBlocks, bool kRecord = false>
 __global__ void __launch_bounds__(kQueryBlock, kMinBlocks)
 k_closest_point(Traversal T, const Header *__restrict__ hdr, unsigned int *status,
                 const float *__restrict__ Q, int64_t nQ, float maxd2, int *face, float *bary,
                 float *point, float *dist2, const int *hint, const int *__restrict__ iperm,
-                const int *__restrict__ order = nullptr) {
+                const int *__restrict__ order = nullptr, unsigned int *__restrict__ cls = nullptr) {
     __shared__ int2 stk[kSmem > 0 ? kSmem : 1][kQueryBlock];
     int64_t k = (int64_t)blockIdx.x * kQueryBlock + threadIdx.x;
     if (k >= nQ) return;
@@ -659,8 +667,16 @@ k_closest_point(Traversal T, const Header *__restrict__ hdr, unsigned int *statu
         if (hf >= 0 && hf < T.n) hint_leaf = __ldg(iperm + hf);
     }
     Hit h;
-    if constexpr (kMode == 1) h = nearest_ww<kQueryBlock>(T, q, maxd2, stk, status);
-    else h = nearest<kQueryBlock, kSmem, kMode == 2>(T, q, maxd2, stk, status, nullptr, hint_leaf);
+    if constexpr (kRecord) {
+        static_assert(kMode != 1, "the recording form uses the depth-first traversal");
+        Counts c{0, 0};
+        h = nearest<kQueryBlock, kSmem, kMode == 2, true>(T, q, maxd2, stk, status, &c, hint_leaf);
+        cls[i] = work_class(c.visits);
+    } else if constexpr (kMode == 1) {
+        h = nearest_ww<kQueryBlock>(T, q, maxd2, stk, status);
+    } else {
+        h = nearest<kQueryBlock, kSmem, kMode == 2>(T, q, maxd2, stk, status, nullptr, hint_leaf);
+    }
     write_hit(T, h, q, i, face, bary, point, dist2);
 }
 
@@ -1308,27 +1324,22 @@ mesh_status mesh_closest_point_hinted(const mesh_bvh *bvh, const float *d_Q, int
 }
 
 // Contact queries of a physics step: warm-started by the previous step's faces
-// and run in an order that puts the queries that touched the mesh last step
-// first (each group in its given order), so a warp mostly holds queries of one
-// kind -- near the surface (deep searches) or away from it (short ones)
-// instead of a mix that runs as long as its slowest lane.
-__global__ void k_contact_flags(int64_t n, const int *__restrict__ face, int nF, int *flags) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int f = face[i];
-    flags[i] = (f >= 0 && f < nF) ? 1 : 0;
-}
-
-__global__ void k_contact_order(int64_t n, const int *__restrict__ flags, const int *__restrict__ pos,
-                                const int *__restrict__ total, int *order) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int p = pos[i];
-    order[flags[i] ? p : *total + (int)i - p] = (int)i;
+// and run in the order of the previous step's work classes (heaviest first,
+// each class in the given order), so that a warp holds queries of similar
+// depth -- near the surface (deep searches), near misses, or far away (short
+// ones) -- instead of a mix that runs as long as its slowest lane.  The
+// classes are keys of one stable 8-bit radix pass; any key values give a
+// valid permutation, so a workspace whose classes are stale or garbage only
+// gives a worse order.
+__global__ void k_contact_iota(int n, int *__restrict__ iota) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) iota[i] = i;
 }
 
 struct ContactWs {
-    int *flags, *pos, *order, *bsum, *total;
+    unsigned int *cls, *cls_sorted;
+    int *iota, *order;
+    void *sort_ws;
     size_t bytes;
 };
 
@@ -1336,10 +1347,11 @@ static ContactWs contact_ws(void *ws, int64_t n) {
     size_t off = 0;
     auto take = [&](size_t b) { size_t o = off; off = align_up(off + b, 256); return o; };
     int64_t m = n > 0 ? n : 1;
-    size_t oF = take(4 * m), oP = take(4 * m), oO = take(4 * m), oB = take(4 * ((m + 1023) / 1024) + 4),
-           oT = take(16);
+    size_t oC = take(4 * m), oS = take(4 * m), oI = take(4 * m), oO = take(4 * m),
+           oW = take(sort_pairs_ws_bytes(m));
     char *b = (char *)ws;
-    return ContactWs{(int *)(b + oF), (int *)(b + oP), (int *)(b + oO), (int *)(b + oB), (int *)(b + oT), off};
+    return ContactWs{(unsigned int *)(b + oC), (unsigned int *)(b + oS), (int *)(b + oI), (int *)(b + oO),
+                     b + oW, off};
 }
 
 mesh_status mesh_knn_project(const mesh_bvh *bvh, const float *d_Q, int64_t nQ, int k,
@@ -1373,32 +1385,30 @@ mesh_status mesh_contact(const mesh_bvh *bvh, const float *d_Q, int64_t nQ, floa
     ContactWs w = contact_ws(d_ws, nQ);
     if (!d_ws || ws_bytes < w.bytes || ((uintptr_t)d_ws & 255u)) return MESH_ERR_WORKSPACE;
     int variant = bvh->cfg_variant >= 0 ? bvh->cfg_variant : g_traversal;
-    if (variant == 1 || variant >= 10 || (bvh->cfg_lanes > 1))
+    if (variant == 1 || (variant >= 10 && variant <= 12) || (bvh->cfg_lanes > 1))
         return mesh_closest_point_hinted(bvh, d_Q, nQ, max_dist, d_face, d_face, d_bary, d_point, d_dist2,
                                          stream);
     cudaStream_t s = (cudaStream_t)stream;
     const int n = (int)nQ;
-    k_contact_flags<<<grid_for(nQ, 256), 256, 0, s>>>(nQ, d_face, (int)bvh->L.n_faces, w.flags);
+    k_contact_iota<<<grid_for(nQ, 256), 256, 0, s>>>(n, w.iota);
     count_launch();
-    exclusive_scan_int(w.flags, w.pos, n, w.bsum, w.total, s);
-    k_contact_order<<<grid_for(nQ, 256), 256, 0, s>>>(nQ, w.flags, w.pos, w.total, w.order);
-    count_launch();
+    sort_pairs_u32(w.sort_ws, n, 2, w.cls, w.iota, w.cls_sorted, w.order, s);
     float maxd2 = isinf(max_dist) ? INFINITY : max_dist * max_dist;
     Traversal T = traversal_of(bvh, isinf(max_dist));
     Header *h = bvh->hdr();
     const int *iperm = bvh->iperm();
     unsigned int grid = grid_for(nQ, kQueryBlock);
-#define MESH_CT_ARGS <<<grid, kQueryBlock, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2, d_face, iperm, w.order)
+#define MESH_CT_ARGS <<<grid, kQueryBlock, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2, d_face, iperm, w.order, w.cls)
     switch (variant) {
-        case 2: k_closest_point<8, 0> MESH_CT_ARGS; break;
-        case 3: k_closest_point<0, 0> MESH_CT_ARGS; break;
-        case 4: k_closest_point<kStackShared, 2> MESH_CT_ARGS; break;
-        case 5: k_closest_point<0, 2> MESH_CT_ARGS; break;
-        case 6: k_closest_point<8, 0, 12> MESH_CT_ARGS; break;
-        case 7: k_closest_point<0, 0, 12> MESH_CT_ARGS; break;
-        case 8: k_closest_point<0, 0, 16> MESH_CT_ARGS; break;
-        case 9: k_closest_point<0, 2, 12> MESH_CT_ARGS; break;
-        default: k_closest_point<kStackShared, 0> MESH_CT_ARGS; break;
+        case 2: k_closest_point<8, 0, kQueryMinBlocks, true> MESH_CT_ARGS; break;
+        case 3: k_closest_point<0, 0, kQueryMinBlocks, true> MESH_CT_ARGS; break;
+        case 4: k_closest_point<kStackShared, 2, kQueryMinBlocks, true> MESH_CT_ARGS; break;
+        case 5: k_closest_point<0, 2, kQueryMinBlocks, true> MESH_CT_ARGS; break;
+        case 6: k_closest_point<8, 0, 12, true> MESH_CT_ARGS; break;
+        case 7: k_closest_point<0, 0, 12, true> MESH_CT_ARGS; break;
+        case 8: k_closest_point<0, 0, 16, true> MESH_CT_ARGS; break;
+        case 9: k_closest_point<0, 2, 12, true> MESH_CT_ARGS; break;
+        default: k_closest_point<kStackShared, 0, kQueryMinBlocks, true> MESH_CT_ARGS; break;
     }
 #undef MESH_CT_ARGS
     count_launch();

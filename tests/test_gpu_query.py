@@ -237,9 +237,10 @@ def test_warm_start_over_a_skinned_sequence_full_size():
 
 @pytest.mark.parametrize("variant", [0, 2, 5, 12])
 def test_contact_step_equals_plain_queries(variant):
-    """mesh_contact (previous faces as hints, queries reordered by last step's contact
-    state) gives mesh_closest_point's answers over a skinned sequence (up to rare
-    order-dependent near ties)."""
+    """mesh_contact (previous faces as hints, queries ordered by the previous step's
+    work classes, kept in the workspace -- garbage bytes at the first step) gives
+    mesh_closest_point's answers over a skinned sequence (up to rare order-dependent
+    near ties)."""
     from paper_2606_00444_gb300 import morton_order
     V0, F = torus(120, 70)
     sk = TorusSkinning(V0, seed=3001)
@@ -251,10 +252,14 @@ def test_contact_step_equals_plain_queries(variant):
     out = dict(face=torch.full((P.shape[0],), -1, dtype=torch.int32, device="cuda"),
                bary=torch.empty(P.shape[0], 3, device="cuda"), point=torch.empty(P.shape[0], 3, device="cuda"),
                dist2=torch.empty(P.shape[0], device="cuda"))
+    from paper_2606_00444_gb300 import Workspace, lib
+    ws = Workspace(torch.device("cuda"))
+    buf = ws.get(lib().mesh_contact_workspace_bytes(P.shape[0]))
+    buf.copy_(torch.randint(0, 256, buf.shape, dtype=torch.uint8))   # garbage work classes
     for t in (0, 5, 10, 40):
         bvh.refit(dev(sk.frame(t)))
         ref = bvh.closest_point(P, 0.05)
-        bvh.contact(P, 0.05, out)
+        bvh.contact(P, 0.05, out, ws=ws)
         assert_same_up_to_near_ties(out, ref)
     assert bvh.status()[0] == 0
 

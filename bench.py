@@ -327,6 +327,7 @@ def gpu_arm(args, rank, world, local_rank):
     nst = min(args.steps, 100)
     ns = len(stage_graphs)
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(ns + 1)] for _ in range(nst)]
+    torch.cuda.nvtx.range_push("stages")         # lets a profiler pick one stage's kernel
     for k in range(nst):
         flush.fill_(float(k))
         load_frame(k)
@@ -334,6 +335,7 @@ def gpu_arm(args, rank, world, local_rank):
             evs[k][i].record()
             gs.replay()
         evs[k][ns].record()
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     names = ["refit", "contact", "rebind", "rebuild", "chamfer", "contact_without_warm_start",
              "contact_hinted_unordered", "contact_signed", "contact_on_rebuilt_lbvh", "chamfer_with_warm_start"]

@@ -534,6 +534,15 @@ const char *mesh_status_string(mesh_status s);
 /* Number of kernels this library has launched in the process so far. */
 uint64_t mesh_launch_count(void);
 
+/* The device address of page-locked host memory (cudaHostAlloc / pinned),
+ * so that an entry point can read its inputs from, or write its outputs to,
+ * host memory directly: on a Grace-Blackwell node the kernel's loads and
+ * stores then cross NVLink-C2C while it runs, with no separate copy (e.g.
+ * mesh_contact writing each step's faces and distances where the host reads
+ * them).  Host-only call; MESH_ERR_INVALID_ARG for NULL arguments,
+ * MESH_ERR_CUDA when the memory is not page-locked host memory. */
+mesh_status mesh_mapped_pointer(const void *host, void **device);
+
 #ifdef __cplusplus
 }
 #endif

@@ -54,6 +54,7 @@ SIGNATURES = {
     "mesh_build_lbvh": (C.c_int, [VP, VP, I64, VP, I64, VP, SZ, VP]),
     "mesh_build_ploc_workspace_bytes": (SZ, [I64]),
     "mesh_build_ploc": (C.c_int, [VP, VP, I64, VP, I64, VP, SZ, VP]),
+    "mesh_mapped_pointer": (C.c_int, [VP, C.POINTER(VP)]),
     "mesh_morton_order_workspace_bytes": (SZ, [I64]),
     "mesh_morton_order": (C.c_int, [VP, I64, VP, VP, SZ, VP]),
     "mesh_update_vertices": (C.c_int, [VP, VP, I64, VP]),

@@ -20,6 +20,18 @@ def _stream() -> int:
     return torch.cuda.current_stream().cuda_stream
 
 
+def _io_ptr(t: torch.Tensor, name: str) -> int:
+    """Device-accessible address of a CUDA tensor, or of a pinned host tensor (which a
+    kernel then reads / writes in place over the host link)."""
+    if t.is_cuda:
+        return t.data_ptr()
+    if t.is_pinned():
+        d = C.c_void_p()
+        check(lib().mesh_mapped_pointer(t.data_ptr(), C.byref(d)), "mesh_mapped_pointer")
+        return d.value
+    raise ValueError(f"{name} must be a CUDA tensor or a pinned host tensor")
+
+
 def _ptr(t: torch.Tensor | None) -> int | None:
     return None if t is None else t.data_ptr()
 
@@ -212,17 +224,31 @@ class MeshBVH:
 
     def contact(self, Q: torch.Tensor, max_dist: float, out: dict, ws: "Workspace | None" = None) -> dict:
         """Physics-step contact query (mesh_contact): out["face"] holds the previous
-        step's faces on entry (-1 = none) and this step's on return."""
+        step's faces on entry (-1 = none) and this step's on return.  The arrays of
+        `out` (face, and optionally bary, point, dist2) may be CUDA tensors or pinned
+        host tensors; the kernel writes pinned ones directly (mesh_mapped_pointer).
+        `ws` carries the work classes that order the next step: pass the same one
+        every step."""
         Q = _f32(Q, 3, "Q")
         n = Q.shape[0]
-        face = _i32(out["face"], None, "face")
-        if face.data_ptr() != out["face"].data_ptr() or face.shape[0] != n:
-            raise ValueError("out['face'] must be a contiguous int32 [n] tensor")
+        shapes = dict(face=(torch.int32, (n,)), bary=(torch.float32, (n, 3)),
+                      point=(torch.float32, (n, 3)), dist2=(torch.float32, (n,)))
+        ptrs = {}
+        for k, (dt, shape) in shapes.items():
+            t = out.get(k)
+            if t is None:
+                if k == "face":
+                    raise ValueError("out['face'] is required")
+                ptrs[k] = None
+                continue
+            if t.dtype != dt or tuple(t.shape) != shape or not t.is_contiguous():
+                raise ValueError(f"out[{k!r}] must be a contiguous {dt} tensor of shape {shape}")
+            ptrs[k] = _io_ptr(t, k)
         ws = self._ws if ws is None else ws
         buf = ws.get(lib().mesh_contact_workspace_bytes(n))
-        check(lib().mesh_contact(self.handle, Q.data_ptr(), n, float(max_dist), face.data_ptr(),
-                                 _ptr(out.get("bary")), _ptr(out.get("point")), _ptr(out.get("dist2")),
-                                 buf.data_ptr(), buf.numel(), _stream()), "mesh_contact")
+        check(lib().mesh_contact(self.handle, Q.data_ptr(), n, float(max_dist), ptrs["face"], ptrs["bary"],
+                                 ptrs["point"], ptrs["dist2"], buf.data_ptr(), buf.numel(), _stream()),
+              "mesh_contact")
         return out
 
     def closest_point_stats(self, Q: torch.Tensor, max_dist: float = math.inf) -> dict:

@@ -1582,4 +1582,15 @@ mesh_status mesh_batch_status(mesh_batch *batch, uint32_t *bits, uint32_t *n_deg
 
 uint64_t mesh_launch_count(void) { return (uint64_t)g_launches.load(); }
 
+mesh_status mesh_mapped_pointer(const void *host, void **device) {
+    if (!host || !device) return MESH_ERR_INVALID_ARG;
+    void *d = nullptr;
+    if (cudaHostGetDevicePointer(&d, const_cast<void *>(host), 0) != cudaSuccess || !d) {
+        cudaGetLastError();                          // not page-locked: clear the error
+        return MESH_ERR_CUDA;
+    }
+    *device = d;
+    return MESH_OK;
+}
+
 }  // extern "C"

@@ -275,3 +275,33 @@ def test_traversal_counters_are_consistent(c1):
         assert st["tests"] >= hits and st["visits"] >= Q.shape[0] // 2
         # a bounded search never works harder than an unbounded one
     assert bvh.closest_point_stats(dev(Q), 0.05)["visits"] < bvh.closest_point_stats(dev(Q))["visits"]
+
+
+def test_contact_writes_pinned_host_outputs():
+    """mesh_contact with its face and distance arrays in pinned host memory (reached
+    through mesh_mapped_pointer) gives, in those arrays, what it gives in device
+    arrays from the same warm-start faces."""
+    import ctypes as C
+    from paper_2606_00444_gb300 import Workspace, lib, morton_order
+    V0, F = torus(120, 70)
+    sk = TorusSkinning(V0, seed=3004)
+    lo, hi = V0.min(0) - 0.2, V0.max(0) + 0.2
+    P = dev(uniform_box(30001, lo, hi, seed=3008))
+    P = P[morton_order(P).long()].contiguous()
+    bvh = MeshBVH.from_mesh(dev(V0), dev(F))
+    n = P.shape[0]
+    d_out = dict(face=torch.full((n,), -1, dtype=torch.int32, device="cuda"),
+                 dist2=torch.empty(n, device="cuda"))
+    h_out = dict(face=torch.full((n,), -1, dtype=torch.int32).pin_memory(),
+                 dist2=torch.empty(n).pin_memory())
+    wd, wh = Workspace(torch.device("cuda")), Workspace(torch.device("cuda"))
+    for t in (3, 9, 30):
+        bvh.refit(dev(sk.frame(t)))
+        bvh.contact(P, 0.05, d_out, ws=wd)
+        bvh.contact(P, 0.05, h_out, ws=wh)
+        torch.cuda.synchronize()
+        assert torch.equal(h_out["face"], d_out["face"].cpu())
+        assert torch.equal(h_out["dist2"], d_out["dist2"].cpu())
+    assert (h_out["face"] >= 0).any()
+    ptr = C.c_void_p()
+    assert lib().mesh_mapped_pointer(None, C.byref(ptr)) == 1

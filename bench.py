@@ -698,15 +698,16 @@ def bench_sequence(args):
     target is rebuilt, the 10242 template vertices projected onto it, the template refit
     and its 20480 Gaussians updated, and the Chamfer distance (10k + 10k samples) taken."""
     import torch
-    from paper_2606_00444_gb300 import MeshBVH, Workspace, chamfer
+    from paper_2606_00444_gb300 import MeshBVH, Workspace, chamfer, morton_order
     from workloads.isosurface import BlobSequence
     from workloads.meshes import icosphere
     dev = torch.device("cuda")
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    mo = lambda P: P[morton_order(P).long()].contiguous()   # samples stored in Morton order
     nfr = min(120, max(args.steps + args.warmup, 8))
     seq = BlobSequence(2000)
     frames = [seq.mesh(k) for k in range(nfr)]
-    tg = [(t(v), t(f), t(points_from(v, f, *sample_surface(v, f, N_CD, seed=2100 + k))))
+    tg = [(t(v), t(f), mo(t(points_from(v, f, *sample_surface(v, f, N_CD, seed=2100 + k)))))
           for k, (v, f) in enumerate(frames)]
     VT, FT = icosphere(5)
     VTd, FTd = t(VT), t(FT)
@@ -718,6 +719,8 @@ def bench_sequence(args):
     gbary = torch.full((len(FT), 3), 1.0 / 3.0, device=dev)
     sf, sb = sample_surface(VT, FT, N_CD, seed=2200)
     sf, sb = t(sf), t(sb)
+    o = morton_order(t(points_from(VT, FT, sf.cpu().numpy(), sb.cpu().numpy()))).long()
+    sf, sb = sf[o].contiguous(), sb[o].contiguous()
     ws = Workspace(dev)
     cd_out = torch.empty(2, dtype=torch.float64, device=dev)
     flush = torch.empty(128 << 20, dtype=torch.float32, device=dev)
@@ -844,6 +847,7 @@ def bench_fit(args):
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     VG, FG = BlobSequence(2000).mesh(60)
     VT, FT = icosphere(6, radius=0.9)
+    from paper_2606_00444_gb300 import morton_order
     ns = 1 << 20
     ft, bt = sample_surface(VT, FT, ns, seed=5001)
     SG = t(points_from(VG, FG, *sample_surface(VG, FG, ns, seed=5002)))
@@ -851,6 +855,11 @@ def bench_fit(args):
     targ = MeshBVH.from_mesh(t(VG), t(FG), method="ploc")   # static target
     VGd = t(VG)
     ft, bt = t(ft), t(bt)
+    # both sample sets persist over the fit, so they are stored once in the Morton order
+    # of their starting positions (neighbouring threads then search neighbouring nodes)
+    o = morton_order(t(points_from(VT, FT, ft.cpu().numpy(), bt.cpu().numpy()))).long()
+    ft, bt = ft[o].contiguous(), bt[o].contiguous()
+    SG = SG[morton_order(SG).long()].contiguous()
     V = t(VT).requires_grad_(True)
     opt = torch.optim.Adam([V], lr=1e-3)
     n_steps = 300 if args.steps >= 100 else args.steps

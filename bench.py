@@ -624,11 +624,14 @@ def bench_batch(args):
     S = batch_scenes(64, seed=4000)
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     V, vo, F, fo = MeshBatch.concat(S, dev)
-    Qs, qn = [], []
+    from paper_2606_00444_gb300 import morton_order
+    Qs, Qu, qn = [], [], []
     for i, (v, f) in enumerate(S):
         lo, hi = v.min(0), v.max(0)
         pad = 0.1 * (hi - lo)
-        Qs.append(uniform_box(4 * len(v), lo - pad, hi + pad, seed=4100 + i))
+        q = uniform_box(4 * len(v), lo - pad, hi + pad, seed=4100 + i)
+        Qu.append(q)
+        Qs.append(q[morton_order(t(q)).cpu().numpy()])     # each scene's queries in Morton order
         qn.append(4 * len(v))
     Q = t(np.concatenate(Qs))
     qoff = t(np.concatenate([[0], np.cumsum(qn)]).astype(np.int32))
@@ -665,14 +668,26 @@ def bench_batch(args):
             singles[i].closest_point(Qd[i], out=outs[i])
             singles[i].bind_gaussians(gfs[i], gbs[i], out=gos[i])
 
+    # the per-scene calls also in the queries' sampling order: a per-scene launch is often
+    # a single wave of blocks, which Morton order can leave waiting on the few blocks that
+    # hold the deepest searches (the batched launch takes its work dynamically)
+    Qdu = [t(q) for q in Qu]
+
+    def plain_unsorted():
+        for i in range(64):
+            singles[i].build(Vs[i], Fs[i])
+            singles[i].closest_point(Qdu[i], out=outs[i])
+            singles[i].bind_gaussians(gfs[i], gbs[i], out=gos[i])
+
     flush = torch.empty(128 << 20, dtype=torch.float32, device=dev)
     set_query_group(1)
     try:
         n0 = launch_count(); batched(); torch.cuda.synchronize(); lb = launch_count() - n0
         n0 = launch_count(); plain(); torch.cuda.synchronize(); lp = launch_count() - n0
-        gb, gp = _capture(batched), _capture(plain)
+        gb, gp, gpu_ = _capture(batched), _capture(plain), _capture(plain_unsorted)
         ms_b = _time_graph(gb, args.steps, args.warmup, flush)
         ms_p = _time_graph(gp, args.steps, args.warmup, flush)
+        ms_pu = _time_graph(gpu_, args.steps, args.warmup, flush)
         st, en = _events(5), _events(5)
         for k in range(5):
             flush.fill_(1.0); st[k].record(); plain(); en[k].record()
@@ -688,7 +703,7 @@ def bench_batch(args):
                                    "frame: LBVH build + closest point + one Gaussian per face",
                        "faces": int(F.shape[0]), "queries": int(nQ)},
             "ms_per_frame": {"batched_graph": ms_b, "per_scene_graph": ms_p,
-                             "per_scene_eager": ms_e},
+                             "per_scene_graph_sampling_order": ms_pu, "per_scene_eager": ms_e},
             "launches_per_frame": {"batched": lb, "per_scene": lp}}
     print(json.dumps(line))
 
@@ -781,7 +796,9 @@ def bench_tracking(args):
     seq = BlobSequence(2000)
     frames = [seq.mesh(k, N=N) for k in range(nfr + 1)]
     V0, F0 = frames[0]
-    tg = [(t(v), t(f), t(points_from(v, f, *sample_surface(v, f, N_CD, seed=2300 + k))))
+    from paper_2606_00444_gb300 import morton_order
+    tg = [(t(v), t(f), (lambda P: P[morton_order(P).long()].contiguous())(
+               t(points_from(v, f, *sample_surface(v, f, N_CD, seed=2300 + k)))))
           for k, (v, f) in enumerate(frames)]
     maxV = max(len(v) for v, _ in frames)
     maxF = max(len(f) for _, f in frames)

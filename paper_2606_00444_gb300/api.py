@@ -498,7 +498,8 @@ def chamfer(A: MeshBVH, SA: torch.Tensor, B: MeshBVH, SB: torch.Tensor, per_samp
     `ps` reuses per-sample output arrays (faceA, baryA, dist2A, faceB, baryB, dist2B);
     `hints` = (faces of B for SA, faces of A for SB), int32 (-1 = none, either may be
     None, and each may be the matching face output itself), warm-starts the searches,
-    e.g. with the previous frame's answers; the results are the same without them."""
+    e.g. with the previous frame's answers; the results are those without them up to
+    order-dependent near ties (see mesh_closest_point)."""
     SA = _f32(SA, 3, "SA")
     SB = _f32(SB, 3, "SB")
     nA, nB = SA.shape[0], SB.shape[0]

@@ -197,3 +197,30 @@ def test_every_tree_consumer_runs_on_the_ploc_tree():
     if bool(same.all()):
         torch.testing.assert_close(gVp, gVl, rtol=1e-5, atol=1e-6)
     assert ploc.status()[0] == 0
+
+
+def test_large_mesh_1_6m_faces():
+    """A 1.6M-face torus: the agglomerative tree is a valid layout (the leaf order is a
+    permutation; every node but the root fills exactly one child slot, and its parent
+    link names that slot) and answers bounded and unbounded queries as the Karras tree
+    does."""
+    V, F = torus(1000, 800)
+    n = F.shape[0]
+    ploc = MeshBVH.from_mesh(dev(V), dev(F), method="ploc")
+    lbvh = MeshBVH.from_mesh(dev(V), dev(F))
+    A = ploc.arrays()
+    perm = A["perm"].long()
+    assert torch.equal(torch.sort(perm).values, torch.arange(n, device="cuda"))
+    par = A["parent"].long()
+    assert par[0].item() == -1
+    links = A["nodes_i"][:, [0, 2], 3].reshape(-1).long()          # child of each parent slot
+    node_ids = torch.where(links >= 0, links, (n - 1) + (-links - 1))
+    seen = torch.zeros(2 * n - 1, dtype=torch.int64, device="cuda")
+    seen.index_add_(0, node_ids, torch.ones_like(node_ids))
+    assert int(seen[0]) == 0 and bool((seen[1:] == 1).all())
+    slots = torch.arange(2 * (n - 1), device="cuda")
+    assert torch.equal(par[node_ids], slots)                         # parent = 2 * node + side
+    Q = dev(uniform_box(200000, V.min(0) - 0.1, V.max(0) + 0.1, seed=77))
+    for cut in (0.02, np.inf):
+        assert_same_up_to_near_ties(ploc.closest_point(Q, cut), lbvh.closest_point(Q, cut))
+    assert ploc.status()[0] == 0

@@ -101,3 +101,19 @@ def test_closed_form_mesh_sizes():
         V, F = icosphere(level)
         assert V.shape[0] == nv and F.shape[0] == 2 * (nv - 2)   # Euler: V - E + F = 2
         assert np.allclose(np.linalg.norm(V, axis=1), 1.0, atol=1e-6)
+
+
+def test_torus_skinning():
+    """4-bone linear-blend skinning: weights form a partition of unity, the motion has the
+    stated period, and no vertex moves farther than its largest bone rotation (30 degrees)
+    can carry it."""
+    from workloads.meshes import TorusSkinning
+    V0, F = torus(40, 25)
+    sk = TorusSkinning(V0, seed=3000)
+    assert np.allclose(sk.w.sum(1), 1.0) and (sk.w > 0).all()
+    assert np.allclose(sk.frame(7), sk.frame(7 + sk.period), atol=1e-6)
+    reach = np.linalg.norm(V0[:, None, :] - sk.pivot[None, :, :], axis=2).max(1)
+    bound = 2.0 * np.sin(np.deg2rad(30.0) / 2.0) * reach
+    for t in (0, 31, 62, 90):
+        move = np.linalg.norm(sk.frame(t).astype(np.float64) - V0, axis=1)
+        assert (move <= bound + 1e-5).all()

@@ -312,8 +312,12 @@ def gpu_arm(args, rank, world, local_rank):
     signed_out["sdist"] = torch.empty_like(contact["dist2"])
     fixed.signed_distance(P, CUTOFF, out=signed_out)       # face adjacency, once per topology
     stage_fns.append(lambda: fixed.signed_distance(P, CUTOFF, out=signed_out))
-    contact_rb = {k: torch.empty_like(v) for k, v in contact.items()}
-    stage_fns.append(lambda: rebuilt.closest_point(P, CUTOFF, out=contact_rb))  # on the rebuilt LBVH
+    # the same contact step on the rebuilt LBVH (warm start from its own previous faces --
+    # face ids survive a rebuild of the same topology -- and its own work classes), so the
+    # refit and rebuild paths are compared with the same query
+    contact_rb = {k: v.clone() for k, v in contact.items()}
+    ct_ws_rb = Workspace(dev)
+    stage_fns.append(lambda: rebuilt.contact(P, CUTOFF, contact_rb, ws=ct_ws_rb))
     cd_out_h = torch.empty_like(cd_out)
     stage_fns.append(lambda: chamfer(fixed, S_def, rest, rest_S, ws=cd_ws, out=cd_out_h, ps=cd_ps,
                                      hints=(cd_ps["faceA"], cd_ps["faceB"])))

@@ -68,7 +68,8 @@ typedef struct {
     size_t off_header;   /* float4 root_lo, float4 root_hi, then uint32 status, uint32 n_degenerate */
     size_t off_verts;    /* float4 [max_verts]   vertex buffer, w = 0                          */
     size_t off_faces;    /* int4   [max_faces]   (v0, v1, v2, 0) in input face order           */
-    size_t off_keys;     /* uint32 [max_faces]   Morton keys in sorted (leaf) order            */
+    size_t off_keys;     /* uint32 [max_faces]   Morton keys in leaf order (sorted for the
+                            Karras tree of mesh_build_lbvh)                                    */
     size_t off_perm;     /* int32  [max_faces]   face id of leaf j                             */
     size_t off_nodes;    /* 4 x float4 per internal node: (lo_L, left) (hi_L, left)
                                                           (lo_R, right) (hi_R, right),

@@ -11,23 +11,32 @@
  *
  *   mesh_build_lbvh       full BVH build (Morton keys, radix sort, Karras
  *                         hierarchy, bottom-up boxes) -- the rebuild of Sec. 4.1
+ *   mesh_build_ploc       the tree of a mesh built once and then refit
+ *                         (agglomerative clustering; Sec. 3.4, Initialization)
  *   mesh_update_vertices  the O(N_v) vertex-buffer update of Sec. 3.4
  *   mesh_refit            boxes recomputed over the fixed topology
  *   mesh_closest_point    NearestSurface of Eq. 1 / Eq. 2 (exact closest point,
  *                         barycentric weights, optional contact cutoff)
+ *   mesh_contact          the contact query of a physics step (warm-started,
+ *                         ordered by the previous step's work)
  *   mesh_bind_gaussians   face-bound Gaussian centre / rotation / scale
  *   mesh_chamfer          point-to-mesh Chamfer distance of Sec. 4.2
  *   *_backward            gradients with respect to vertices and query points
+ *   mesh_batch_*          many scenes in single launches
  *
  * Conventions (all entry points):
- *   - Pointers named d_* are DEVICE pointers owned by the caller; the library
- *     never allocates device memory.  A BVH lives in caller-provided storage
+ *   - Pointers named d_* are DEVICE pointers owned by the caller (pinned host
+ *     memory mapped by mesh_mapped_pointer qualifies); the library never
+ *     allocates device memory (mesh_chamfer_noalloc's fixed scratch array is
+ *     the one static exception).  A BVH lives in caller-provided storage
  *     (mesh_bvh_storage_bytes) and a build uses caller-provided scratch
  *     (mesh_build_workspace_bytes).  Host pointers are named without d_.
  *   - Positions are float32, row-major xyz: vertices [nV][3], queries [nQ][3].
  *     Faces are int32 [nF][3] vertex indices (0-based), counter-clockwise.
  *   - Every call is asynchronous on `stream` (a cudaStream_t passed as void*;
- *     NULL is the legacy default stream) and may be captured in a CUDA graph.
+ *     NULL is the legacy default stream) and may be captured in a CUDA graph,
+ *     except the few that say they are synchronous (mesh_build_ploc,
+ *     mesh_gs_render and mesh_emd read counts back on the host).
  *     Host-side argument errors are returned at once and launch nothing.
  *     Device-side problems (an index out of range, a traversal stack
  *     overflow) set sticky bits in the BVH's status word, read and cleared by

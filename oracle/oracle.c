@@ -4,9 +4,10 @@
  * constant with the CUDA library; only the test-suite, the smoke check and the
  * benchmark's CPU-baseline leg load it.
  *
- * Everything is float64 except the Morton-key step, whose recipe is defined in
- * float32 (see orc_morton); this file must be compiled with
- * -ffp-contract=off so that no fused multiply-add changes a rounding.
+ * Everything is float64 except the Morton-key step and the merge cost of the
+ * agglomerative build, whose recipes are defined in float32 (see orc_morton,
+ * orc_ploc); this file must be compiled with -ffp-contract=off so that no
+ * fused multiply-add changes a rounding.
  *
  * What the paper fixes and what is our reading:
  *   - NearestSurface(v, M) of Eq. 1 / Eq. 2 (Sec. 3.3): the exact closest
@@ -14,8 +15,10 @@
  *     weights ("barycentric interpolation for sub-face accuracy", Eq. 2).
  *     The k-NN weighting Sec. 3.3 mentions for Eq. 1 is not used (reading).
  *   - Acceleration structure built once from F0, holding indices only
- *     (Sec. 3.4, Initialization): a linear BVH whose leaves are sorted faces;
- *     the paper gives no construction, so this is Karras (2012).
+ *     (Sec. 3.4, Initialization): the paper gives no construction; here a
+ *     linear BVH whose leaves are sorted faces (Karras 2012), and for a mesh
+ *     built once and refit, an agglomerative tree over the same leaves
+ *     (PLOC, Meister & Bittner 2018; orc_ploc).
  *   - Collision-structure rebuild of the varying-topology baseline (Sec. 4.1).
  *   - Gaussians bound to faces (Sec. 2, Sec. 3.1): the paper gives no
  *     formula; the face-frame reading is ours (orc_bind_gaussians).

@@ -26,3 +26,13 @@ def test_reference_arm_prints_the_contract_line():
     assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == line["value"]
     assert line["e2e"] == {"value": line["value"], "unit": "queries/s", "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
+
+
+def test_committed_traffic_record_matches_the_kernel_sources():
+    """The roofline's DRAM traffic comes from a committed ncu capture, valid only while the
+    contact kernel's sources hash as they did when it was captured, and only for the
+    captured traversal variant."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.contact_traffic(2) == 41301248
+    assert bench.contact_traffic(99) is None

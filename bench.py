@@ -478,9 +478,9 @@ def gpu_arm(args, rank, world, local_rank):
 
 
 def contact_traffic(variant: int):
-    """DRAM bytes per launch of the contact kernel in this traversal variant from the
-    committed ncu captures, if the kernel source is still the one that was captured
-    (else None)."""
+    """Counters per launch of the contact kernel in this traversal variant from the
+    committed ncu capture (dram_bytes, lts_bytes, fma pipe and issue figures), if the
+    kernel source is still the one that was captured (else None)."""
     import hashlib
     p = os.path.join(ROOT, "profiles", "roofline_traffic.json")
     if not os.path.exists(p):
@@ -491,7 +491,7 @@ def contact_traffic(variant: int):
         m.update(open(os.path.join(ROOT, f), "rb").read())
     if m.hexdigest()[:16] != d.get("source_hash"):
         return None
-    return d.get("traffic_bytes_per_launch_by_variant", {}).get(str(variant))
+    return d.get("by_variant", {}).get(str(variant))
 
 
 def peaks():
@@ -972,7 +972,7 @@ def main():
                                 "build_ms_once": res["ploc_build_ms"]},
         "roofline": {"kernel": "k_closest_point (contact, 1M queries, no warm start)", "bound": "hbm",
                      "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "peak_source": src, "traffic": contact_traffic(res["tuned"]["variant"]) if res["tuned"]["lanes"] == 1 else None,
+                     "frac": achieved / hbm, "peak_source": src, "traffic": (contact_traffic(res["tuned"]["variant"]) or {}).get("dram_bytes") if res["tuned"]["lanes"] == 1 else None,
                      "bytes_per_query": per_query,
                      "per_query": {"io": CONTACT_BYTES, "node_visits": vis, "triangle_tests": tst,
                                    "node_bytes": NODE_BYTES, "triangle_bytes": TRI_BYTES},

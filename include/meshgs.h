@@ -198,15 +198,18 @@ mesh_status mesh_refit_bind(mesh_bvh *bvh, const float *d_V, int64_t nV, const i
 
 /* NearestSurface (Eq. 1 / Eq. 2): for each query q the closest point of the
  * mesh, as face id, barycentric weights (u, v, w) of (v0, v1, v2), the point
- * u v0 + v v1 + w v2 and its squared distance.  Ties: the lowest face id
- * among faces within 1e-6 relative distance (+1e-12 of the box diagonal) of
- * the nearest found, applied online as faces are met.  Where three or more
- * faces lie within about 2e-6 of one another the kept face can depend on the
- * order in which they are met (traversal variant, warm start): it is then
- * another face within that window, its distance within the window of the
- * nearest.  A query with no face within max_dist (INFINITY = no
- * cutoff) gets face -1, dist2 = +inf, bary = point = 0.  Any output pointer
- * may be NULL (not written). */
+ * u v0 + v v1 + w v2 and its squared distance.  Ties: the nearest face is the
+ * lowest face id among the faces whose computed (float32) distance lies
+ * within d* (1 + 1e-6) + 1e-12 x box diagonal, d* the least computed distance
+ * (the spec rule of Eq. 1 / Eq. 2's NearestSurface).  The answer is a
+ * function of the query and the mesh only: every tree (LBVH or agglomerative),
+ * traversal variant, lane width and warm start gives the same face, weights,
+ * point and distance, bit for bit.  It differs from a float64 evaluation of
+ * the same rule only where float32 rounding moves a face across the window
+ * (faces whose exact distances are within ~1e-7 x the coordinate magnitude of
+ * each other or of the window's edge).  A query with no face within max_dist
+ * (INFINITY = no cutoff) gets face -1, dist2 = +inf, bary = point = 0.  Any
+ * output pointer may be NULL (not written). */
 mesh_status mesh_closest_point(const mesh_bvh *bvh, const float *d_Q, int64_t nQ,
                                float max_dist, int32_t *d_face, float *d_bary, float *d_point,
                                float *d_dist2, void *stream);
@@ -215,8 +218,7 @@ mesh_status mesh_closest_point(const mesh_bvh *bvh, const float *d_Q, int64_t nQ
  * nearest face in the previous frame; -1 or out of range = none) is tested
  * before the traversal and its distance bounds the search.  Every face within
  * the final tie window is still reached, so the answer is the one without the
- * hint except in the order-dependent near ties described above; the hint
- * changes the work.  d_hint may be the same array as d_face
+ * hint, bit for bit; the hint changes only the work.  d_hint may be the same array as d_face
  * (each query reads its hint before writing its face).  Used by the
  * depth-first one-thread variants (0, 2-9) and by the cooperative groups
  * (lanes > 1); the other one-thread variants ignore it. */
@@ -320,7 +322,7 @@ size_t mesh_contact_workspace_bytes(int64_t nQ);
  * carries state from one step to the next: pass the same workspace every
  * step for the same particles; its contents steer only the order (a fresh
  * or unrelated workspace gives a worse order, never a wrong answer).
- * Answers equal mesh_closest_point's up to its order-dependent near ties.
+ * Answers equal mesh_closest_point's bit for bit.
  * Traversal variants 1, 10-12 and cooperative groups run unordered without
  * classes.  d_ws: mesh_contact_workspace_bytes(nQ), 256-byte aligned. */
 mesh_status mesh_contact(const mesh_bvh *bvh, const float *d_Q, int64_t nQ, float max_dist,
@@ -341,7 +343,7 @@ mesh_status mesh_closest_point_stats(const mesh_bvh *bvh, const float *d_Q, int6
  * group pops several stack entries per step and merges its candidates with
  * the same tie rule).  1, 2, 4, 8, 16 or 32 force a width.  Process-wide,
  * not thread-safe; for tuning and tests.  Results are the same for every
- * width up to the tie rule's float32 margin. */
+ * width, bit for bit. */
 mesh_status mesh_set_query_group(int lanes);
 
 /* One-thread-per-query traversal variant for mesh_closest_point (tuning):
@@ -358,8 +360,8 @@ mesh_status mesh_set_query_group(int lanes);
  *  12 warp packet: the 32 queries of a warp share one node sequence, a node
  *     entered when any lane needs it (for queries kept in Morton order)
  * (the shared part of the stack spills to local memory; local-only leaves the
- * SM's L1 to the node cache).  Process-wide; same answers for every variant
- * up to the order-dependent near ties described at mesh_closest_point. */
+ * SM's L1 to the node cache).  Process-wide; the same answers, bit for bit,
+ * for every variant. */
 mesh_status mesh_set_traversal(int variant);
 
 /* Traversal choice for mesh_closest_point calls on this handle (host-side
@@ -403,9 +405,8 @@ mesh_status mesh_chamfer(const mesh_bvh *A, const float *d_SA, int64_t nSA,
  * SA[i] (e.g. its nearest face in the previous frame), d_hintB[i] a face of
  * mesh A for SB[i]; -1 or out of range = none, either pointer may be NULL,
  * and each may be the same array as the matching face output.  The answers
- * are those without hints up to the order-dependent near ties of
- * mesh_closest_point (a sample's distance then moves within its tie window);
- * the hints change the traversal work. */
+ * are those without hints, bit for bit; the hints change only the traversal
+ * work. */
 mesh_status mesh_chamfer_hinted(const mesh_bvh *A, const float *d_SA, int64_t nSA,
                                 const mesh_bvh *B, const float *d_SB, int64_t nSB, void *d_ws,
                                 size_t ws_bytes, double *d_out, const int32_t *d_hintA,
@@ -448,6 +449,26 @@ mesh_status mesh_closest_point_backward(const mesh_bvh *bvh, const float *d_Q, i
                                         const int32_t *d_face, const float *d_bary,
                                         const float *d_g, float *d_gQ, float *d_gV,
                                         void *stream);
+
+/* Reverse mode of mesh_chamfer (Sec. 4.2's Chamfer distance as a loss), both
+ * directions in one launch.  d_g: DEVICE float64 [2] = dL/d(out[0]), dL/d(out[1])
+ * (read on the device: no host synchronisation).  With the forward's per-sample
+ * faces and weights (d_faceA / d_baryA: SA's nearest faces on mesh B; d_faceB /
+ * d_baryB: SB's on mesh A) and each mesh's current vertex buffer, every sample of
+ * SA carries dL/d(dist2) = g[0] / nSA and every sample of SB g[1] / nSB:
+ *   dL/dSA[i] =  2 (g[0]/nSA) (a_i - c_i)           -> d_gSA [nSA][3] (written)
+ *   dL/dV_B  += -2 (g[0]/nSA) b_ij (a_i - c_i)       -> d_gVB [nVB][3] (accumulated)
+ *   dL/dSB[i] =  2 (g[1]/nSB) (b_i - c_i)           -> d_gSB [nSB][3] (written)
+ *   dL/dV_A  += -2 (g[1]/nSB) b_ij (b_i - c_i)       -> d_gVA [nVA][3] (accumulated)
+ * c_i = sum_j b_ij v_j, the nearest face and weights held fixed (envelope
+ * theorem).  Any gradient output may be NULL; a direction whose outputs are
+ * both NULL is skipped.  Face -1 contributes 0; a face id out of range sets
+ * MESH_DEV_INDEX_RANGE on the mesh it indexes and contributes 0. */
+mesh_status mesh_chamfer_backward(const mesh_bvh *A, const float *d_SA, int64_t nSA,
+                                  const mesh_bvh *B, const float *d_SB, int64_t nSB,
+                                  const double *d_g, const int32_t *d_faceA, const float *d_baryA,
+                                  const int32_t *d_faceB, const float *d_baryB, float *d_gSA,
+                                  float *d_gVA, float *d_gSB, float *d_gVB, void *stream);
 
 /* dL/dV += sum_i b_ij dL/dp_i over the vertices of face[i] (d_gV accumulated). */
 mesh_status mesh_interpolate_backward(const mesh_bvh *bvh, const int32_t *d_face,

@@ -3,8 +3,10 @@
 Only the test-suite, ``__graft_entry__.smoke()`` and the benchmark's CPU
 baseline leg may import this package; the CUDA library never does, and the two
 share no code.  The arithmetic lives in ``oracle.c`` (plain serial C, float64,
-with the Morton-key step in float32 as its recipe defines); this module only
-compiles it and marshals numpy arrays.
+with the Morton-key step in float32 as its recipe defines; OpenMP forms of the
+brute-force closest point, the rebind and the Chamfer run the same per-query
+arithmetic over the host's cores); this module only compiles it and marshals
+numpy arrays.
 """
 from __future__ import annotations
 
@@ -26,11 +28,14 @@ I64 = C.c_int64
 
 
 def build(force: bool = False) -> str:
-    """Compile oracle.c into liboracle.so (gcc, -O2, no FMA contraction)."""
+    """Compile oracle.c into liboracle.so (gcc, -O2, no FMA contraction), with OpenMP for
+    the *_omp forms when the compiler supports it (otherwise they run on one thread)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
-                               "-fPIC", "-shared", _SRC, "-lm", "-o", tmp])
+        base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"]
+        r = subprocess.run(base + ["-fopenmp", _SRC, "-lm", "-o", tmp], capture_output=True)
+        if r.returncode != 0:
+            subprocess.check_call(base + [_SRC, "-lm", "-o", tmp])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -62,6 +67,17 @@ def lib():
         L.orc_bind_gaussians.restype = C.c_int64
         L.orc_bind_gaussians.argtypes = [F64P, I32P, I32P, F64P, C.c_void_p, I64,
                                          F64P, F64P, F64P, I32P]
+        L.orc_num_threads.restype = C.c_int
+        L.orc_num_threads.argtypes = []
+        L.orc_closest_point_mesh_omp.restype = None
+        L.orc_closest_point_mesh_omp.argtypes = [F64P, I32P, I64, F64P, I64, C.c_double,
+                                                 I32P, F64P, F64P, F64P]
+        L.orc_bind_gaussians_omp.restype = C.c_int64
+        L.orc_bind_gaussians_omp.argtypes = [F64P, I32P, I32P, F64P, C.c_void_p, I64,
+                                             F64P, F64P, F64P, I32P]
+        L.orc_chamfer_omp.restype = None
+        L.orc_chamfer_omp.argtypes = [F64P, I32P, I64, F64P, I64, F64P, I32P, I64, F64P, I64,
+                                      F64P, F64P, F64P]
         L.orc_chamfer.restype = None
         L.orc_chamfer.argtypes = [F64P, I32P, I64, F64P, I64, F64P, I32P, I64, F64P, I64,
                                   F64P, F64P, F64P]
@@ -112,14 +128,26 @@ def mesh_diag(V, F):
     return lib().orc_mesh_diag(_f64(V), _i32(F), F.shape[0])
 
 
-def closest_point(V, F, Q, max_dist=np.inf, all_d2=False):
-    """Brute-force NearestSurface of every query: dict(face, bary, point, d2[, d2_all])."""
+def num_threads() -> int:
+    """Threads the *_omp forms use (1 when built without OpenMP)."""
+    return int(lib().orc_num_threads())
+
+
+def closest_point(V, F, Q, max_dist=np.inf, all_d2=False, parallel=False):
+    """Brute-force NearestSurface of every query: dict(face, bary, point, d2[, d2_all]).
+    parallel=True runs the queries over every host core (orc_closest_point_mesh_omp,
+    identical results; all_d2 is then unavailable)."""
     V, F, Q = _f64(V), _i32(F), _f64(Q).reshape(-1, 3)
     nQ, nF = Q.shape[0], F.shape[0]
     face = np.empty(nQ, np.int32)
     bary = np.empty((nQ, 3))
     point = np.empty((nQ, 3))
     d2 = np.empty(nQ)
+    if parallel:
+        if all_d2:
+            raise ValueError("all_d2 needs the serial form")
+        lib().orc_closest_point_mesh_omp(V, F, nF, Q, nQ, float(max_dist), face, bary, point, d2)
+        return dict(face=face, bary=bary, point=point, d2=d2)
     d2a = np.empty((nQ, nF)) if all_d2 else None
     lib().orc_closest_point_mesh(V, F, nF, Q, nQ, float(max_dist), face, bary, point, d2,
                                  d2a.ctypes.data if all_d2 else None)
@@ -217,8 +245,9 @@ def build_lbvh(V, F):
                 first=first, last=last, boxes=boxes)
 
 
-def bind_gaussians(V, F, gface, gbary, goff=None):
-    """dict(mu [G,3], quat [G,4] (w,x,y,z), scale [G,3], flags [G], n_degenerate)."""
+def bind_gaussians(V, F, gface, gbary, goff=None, parallel=False):
+    """dict(mu [G,3], quat [G,4] (w,x,y,z), scale [G,3], flags [G], n_degenerate);
+    parallel=True: orc_bind_gaussians_omp over every host core (identical results)."""
     gface = _i32(gface)
     G = gface.shape[0]
     mu = np.empty((G, 3))
@@ -226,19 +255,21 @@ def bind_gaussians(V, F, gface, gbary, goff=None):
     scale = np.empty((G, 3))
     flags = np.empty(G, np.int32)
     go = None if goff is None else _f64(goff)
-    nd = lib().orc_bind_gaussians(_f64(V), _i32(F), gface, _f64(gbary),
+    fn = lib().orc_bind_gaussians_omp if parallel else lib().orc_bind_gaussians
+    nd = fn(_f64(V), _i32(F), gface, _f64(gbary),
                                   None if go is None else go.ctypes.data, G, mu, quat, scale,
                                   flags)
     return dict(mu=mu, quat=quat, scale=scale, flags=flags, n_degenerate=int(nd))
 
 
-def chamfer(VA, FA, SA, VB, FB, SB):
-    """(out[2] = [mean d(SA, B)^2, mean d(SB, A)^2], dA, dB) in float64."""
+def chamfer(VA, FA, SA, VB, FB, SB, parallel=False):
+    """(out[2] = [mean d(SA, B)^2, mean d(SB, A)^2], dA, dB) in float64; parallel=True:
+    orc_chamfer_omp over every host core (identical results)."""
     SA, SB = _f64(SA).reshape(-1, 3), _f64(SB).reshape(-1, 3)
     out = np.zeros(2)
     dA = np.empty(SA.shape[0])
     dB = np.empty(SB.shape[0])
-    lib().orc_chamfer(_f64(VA), _i32(FA), FA.shape[0], SA, SA.shape[0],
+    (lib().orc_chamfer_omp if parallel else lib().orc_chamfer)(_f64(VA), _i32(FA), FA.shape[0], SA, SA.shape[0],
                       _f64(VB), _i32(FB), FB.shape[0], SB, SB.shape[0], out, dA, dB)
     return out, dA, dB
 

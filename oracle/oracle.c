@@ -1,6 +1,8 @@
 /*
  * Reference oracle for the per-frame dynamic-mesh update -- TEST
- * INFRASTRUCTURE ONLY.  Plain, slow, serial C.  It shares no code, header or
+ * INFRASTRUCTURE ONLY.  Plain, slow, serial C (the *_omp forms run the same
+ * per-query arithmetic over the host's cores, for timing and for large
+ * samples; results are identical).  It shares no code, header or
  * constant with the CUDA library; only the test-suite, the smoke check and the
  * benchmark's CPU-baseline leg load it.
  *
@@ -32,6 +34,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_TIE_REL 1e-6      /* ties: lowest face id within 1e-6 relative distance */
 #define ORC_TIE_ABS 1e-12     /* absolute floor, times the mesh bounding-box diagonal */
@@ -149,47 +154,83 @@ double orc_mesh_diag(const double *V, const int32_t *F, int64_t nF) {
                 (hi[2] - lo[2]) * (hi[2] - lo[2]));
 }
 
+/* One query p of the brute force: every face's distance into dist[nF] (and
+ * into d2_row when not NULL), then the tie rule and the cutoff. */
+static void closest_one(const double *V, const int32_t *F, int64_t nF, const double *p,
+                        double max_dist, double tau, double *dist, double *d2_row,
+                        int32_t *face, double *bary, double *point, double *d2) {
+    double best = INFINITY;
+    for (int64_t f = 0; f < nF; ++f) {
+        double A[3], B[3], C[3], bb[3], pp[3];
+        for (int c = 0; c < 3; ++c) {
+            A[c] = V[3 * (int64_t)F[3 * f] + c];
+            B[c] = V[3 * (int64_t)F[3 * f + 1] + c];
+            C[c] = V[3 * (int64_t)F[3 * f + 2] + c];
+        }
+        dist[f] = orc_point_triangle(p, A, B, C, bb, pp);
+        if (d2_row) d2_row[f] = dist[f];
+        if (dist[f] < best) best = dist[f];
+    }
+    int32_t pick = -1;
+    if (nF > 0 && sqrt(best) <= max_dist) {
+        double lim = sqrt(best) * (1.0 + ORC_TIE_REL) + tau;
+        for (int64_t f = 0; f < nF; ++f)
+            if (sqrt(dist[f]) <= lim) { pick = (int32_t)f; break; }
+    }
+    *face = pick;
+    if (pick < 0) {
+        *d2 = INFINITY;
+        for (int c = 0; c < 3; ++c) { bary[c] = 0.0; point[c] = 0.0; }
+    } else {
+        double A[3], B[3], C[3];
+        for (int c = 0; c < 3; ++c) {
+            A[c] = V[3 * (int64_t)F[3 * pick] + c];
+            B[c] = V[3 * (int64_t)F[3 * pick + 1] + c];
+            C[c] = V[3 * (int64_t)F[3 * pick + 2] + c];
+        }
+        *d2 = orc_point_triangle(p, A, B, C, bary, point);
+    }
+}
+
 void orc_closest_point_mesh(const double *V, const int32_t *F, int64_t nF,
                             const double *Q, int64_t nQ, double max_dist,
                             int32_t *face, double *bary, double *point, double *d2,
                             double *d2_all /* nullable: [nQ * nF] every face's distance^2 */) {
     double tau = ORC_TIE_ABS * orc_mesh_diag(V, F, nF);
     double *dist = (double *)malloc(sizeof(double) * (size_t)(nF > 0 ? nF : 1));
-    for (int64_t q = 0; q < nQ; ++q) {
-        double p[3] = {Q[3 * q], Q[3 * q + 1], Q[3 * q + 2]};
-        double best = INFINITY;
-        for (int64_t f = 0; f < nF; ++f) {
-            double A[3], B[3], C[3], bb[3], pp[3];
-            for (int c = 0; c < 3; ++c) {
-                A[c] = V[3 * (int64_t)F[3 * f] + c];
-                B[c] = V[3 * (int64_t)F[3 * f + 1] + c];
-                C[c] = V[3 * (int64_t)F[3 * f + 2] + c];
-            }
-            dist[f] = orc_point_triangle(p, A, B, C, bb, pp);
-            if (d2_all) d2_all[q * nF + f] = dist[f];
-            if (dist[f] < best) best = dist[f];
-        }
-        int32_t pick = -1;
-        if (nF > 0 && sqrt(best) <= max_dist) {
-            double lim = sqrt(best) * (1.0 + ORC_TIE_REL) + tau;
-            for (int64_t f = 0; f < nF; ++f)
-                if (sqrt(dist[f]) <= lim) { pick = (int32_t)f; break; }
-        }
-        face[q] = pick;
-        if (pick < 0) {
-            d2[q] = INFINITY;
-            for (int c = 0; c < 3; ++c) { bary[3 * q + c] = 0.0; point[3 * q + c] = 0.0; }
-        } else {
-            double A[3], B[3], C[3];
-            for (int c = 0; c < 3; ++c) {
-                A[c] = V[3 * (int64_t)F[3 * pick] + c];
-                B[c] = V[3 * (int64_t)F[3 * pick + 1] + c];
-                C[c] = V[3 * (int64_t)F[3 * pick + 2] + c];
-            }
-            d2[q] = orc_point_triangle(p, A, B, C, bary + 3 * q, point + 3 * q);
-        }
-    }
+    for (int64_t q = 0; q < nQ; ++q)
+        closest_one(V, F, nF, Q + 3 * q, max_dist, tau, dist, d2_all ? d2_all + q * nF : NULL,
+                    face + q, bary + 3 * q, point + 3 * q, d2 + q);
     free(dist);
+}
+
+/* ------------------------------------------------------------------ */
+/* The same brute force with the queries spread over the host's cores   */
+/* (OpenMP; serial when built without it).  Each query runs exactly the */
+/* serial function's arithmetic, so the results are identical; it exists */
+/* to time the CPU baseline on every core and to check large samples.    */
+/* ------------------------------------------------------------------ */
+int orc_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void orc_closest_point_mesh_omp(const double *V, const int32_t *F, int64_t nF, const double *Q,
+                                int64_t nQ, double max_dist, int32_t *face, double *bary,
+                                double *point, double *d2) {
+    double tau = ORC_TIE_ABS * orc_mesh_diag(V, F, nF);
+#pragma omp parallel
+    {
+        double *dist = (double *)malloc(sizeof(double) * (size_t)(nF > 0 ? nF : 1));
+#pragma omp for schedule(dynamic, 4)
+        for (int64_t q = 0; q < nQ; ++q)
+            closest_one(V, F, nF, Q + 3 * q, max_dist, tau, dist, NULL, face + q, bary + 3 * q,
+                        point + 3 * q, d2 + q);
+        free(dist);
+    }
 }
 
 /* ------------------------------------------------------------------ */
@@ -541,42 +582,57 @@ static void orc_quat_from_R(const double R[3][3], double q[4]) {
     q[0] = sg * w; q[1] = sg * x; q[2] = sg * y; q[3] = sg * z;
 }
 
+/* One Gaussian g of orc_bind_gaussians; returns 1 when its face is degenerate. */
+static int bind_one(const double *V, const int32_t *F, const int32_t *gface, const double *gbary,
+                    const double *goff, int64_t g, double *mu, double *quat, double *scale,
+                    int32_t *flags) {
+    int64_t f = gface[g];
+    d3 v0 = ld3(V + 3 * (int64_t)F[3 * f]);
+    d3 v1 = ld3(V + 3 * (int64_t)F[3 * f + 1]);
+    d3 v2 = ld3(V + 3 * (int64_t)F[3 * f + 2]);
+    double b0 = gbary[3 * g], b1 = gbary[3 * g + 1], b2 = gbary[3 * g + 2];
+    double off = goff ? goff[g] : 0.0;
+    d3 m = add(add(scl(v0, b0), scl(v1, b1)), scl(v2, b2));
+    d3 e = sub(v1, v0);
+    d3 nu = cross(e, sub(v2, v0));
+    double l = norm(e), an = norm(nu);
+    if (l == 0.0 || an == 0.0) {
+        flags[g] = 1;
+        mu[3 * g] = m.x; mu[3 * g + 1] = m.y; mu[3 * g + 2] = m.z;
+        quat[4 * g] = 1.0; quat[4 * g + 1] = quat[4 * g + 2] = quat[4 * g + 3] = 0.0;
+        scale[3 * g] = scale[3 * g + 1] = scale[3 * g + 2] = 0.0;
+        return 1;
+    }
+    flags[g] = 0;
+    d3 e1 = scl(e, 1.0 / l);
+    d3 n = scl(nu, 1.0 / an);
+    d3 e2 = cross(n, e1);
+    double R[3][3] = {{e1.x, e2.x, n.x}, {e1.y, e2.y, n.y}, {e1.z, e2.z, n.z}};
+    m = add(m, scl(n, off));
+    mu[3 * g] = m.x; mu[3 * g + 1] = m.y; mu[3 * g + 2] = m.z;
+    orc_quat_from_R(R, quat + 4 * g);
+    double h = an / l;
+    scale[3 * g] = ORC_RHO * l;
+    scale[3 * g + 1] = ORC_RHO * h;
+    scale[3 * g + 2] = ORC_EPS_S * ORC_RHO * (l + h) * 0.5;
+    return 0;
+}
+
 int64_t orc_bind_gaussians(const double *V, const int32_t *F, const int32_t *gface,
                            const double *gbary, const double *goff /* nullable */, int64_t nG,
                            double *mu, double *quat, double *scale, int32_t *flags) {
     int64_t ndeg = 0;
-    for (int64_t g = 0; g < nG; ++g) {
-        int64_t f = gface[g];
-        d3 v0 = ld3(V + 3 * (int64_t)F[3 * f]);
-        d3 v1 = ld3(V + 3 * (int64_t)F[3 * f + 1]);
-        d3 v2 = ld3(V + 3 * (int64_t)F[3 * f + 2]);
-        double b0 = gbary[3 * g], b1 = gbary[3 * g + 1], b2 = gbary[3 * g + 2];
-        double off = goff ? goff[g] : 0.0;
-        d3 m = add(add(scl(v0, b0), scl(v1, b1)), scl(v2, b2));
-        d3 e = sub(v1, v0);
-        d3 nu = cross(e, sub(v2, v0));
-        double l = norm(e), an = norm(nu);
-        if (l == 0.0 || an == 0.0) {
-            ++ndeg;
-            flags[g] = 1;
-            mu[3 * g] = m.x; mu[3 * g + 1] = m.y; mu[3 * g + 2] = m.z;
-            quat[4 * g] = 1.0; quat[4 * g + 1] = quat[4 * g + 2] = quat[4 * g + 3] = 0.0;
-            scale[3 * g] = scale[3 * g + 1] = scale[3 * g + 2] = 0.0;
-            continue;
-        }
-        flags[g] = 0;
-        d3 e1 = scl(e, 1.0 / l);
-        d3 n = scl(nu, 1.0 / an);
-        d3 e2 = cross(n, e1);
-        double R[3][3] = {{e1.x, e2.x, n.x}, {e1.y, e2.y, n.y}, {e1.z, e2.z, n.z}};
-        m = add(m, scl(n, off));
-        mu[3 * g] = m.x; mu[3 * g + 1] = m.y; mu[3 * g + 2] = m.z;
-        orc_quat_from_R(R, quat + 4 * g);
-        double h = an / l;
-        scale[3 * g] = ORC_RHO * l;
-        scale[3 * g + 1] = ORC_RHO * h;
-        scale[3 * g + 2] = ORC_EPS_S * ORC_RHO * (l + h) * 0.5;
-    }
+    for (int64_t g = 0; g < nG; ++g) ndeg += bind_one(V, F, gface, gbary, goff, g, mu, quat, scale, flags);
+    return ndeg;
+}
+
+/* orc_bind_gaussians over the host's cores (identical results). */
+int64_t orc_bind_gaussians_omp(const double *V, const int32_t *F, const int32_t *gface,
+                               const double *gbary, const double *goff, int64_t nG, double *mu,
+                               double *quat, double *scale, int32_t *flags) {
+    int64_t ndeg = 0;
+#pragma omp parallel for schedule(static) reduction(+ : ndeg)
+    for (int64_t g = 0; g < nG; ++g) ndeg += bind_one(V, F, gface, gbary, goff, g, mu, quat, scale, flags);
     return ndeg;
 }
 
@@ -594,6 +650,25 @@ void orc_chamfer(const double *VA, const int32_t *FA, int64_t nFA, const double 
     double *pp = (double *)malloc(sizeof(double) * 3 * (size_t)(nSA > nSB ? nSA : nSB) + 32);
     orc_closest_point_mesh(VB, FB, nFB, SA, nSA, INFINITY, fc, bb, pp, dA, NULL);
     orc_closest_point_mesh(VA, FA, nFA, SB, nSB, INFINITY, fc, bb, pp, dB, NULL);
+    double s0 = 0.0, s1 = 0.0;
+    for (int64_t i = 0; i < nSA; ++i) s0 += dA[i];
+    for (int64_t i = 0; i < nSB; ++i) s1 += dB[i];
+    out[0] = nSA > 0 ? s0 / (double)nSA : 0.0;
+    out[1] = nSB > 0 ? s1 / (double)nSB : 0.0;
+    free(fc); free(bb); free(pp);
+}
+
+/* orc_chamfer with the two brute-force passes over the host's cores; the sums
+ * stay serial and in order, so the result is identical. */
+void orc_chamfer_omp(const double *VA, const int32_t *FA, int64_t nFA, const double *SA, int64_t nSA,
+                     const double *VB, const int32_t *FB, int64_t nFB, const double *SB, int64_t nSB,
+                     double *out, double *dA, double *dB) {
+    int64_t m = nSA > nSB ? nSA : nSB;
+    int32_t *fc = (int32_t *)malloc(sizeof(int32_t) * (size_t)m + 4);
+    double *bb = (double *)malloc(sizeof(double) * 3 * (size_t)m + 32);
+    double *pp = (double *)malloc(sizeof(double) * 3 * (size_t)m + 32);
+    orc_closest_point_mesh_omp(VB, FB, nFB, SA, nSA, INFINITY, fc, bb, pp, dA);
+    orc_closest_point_mesh_omp(VA, FA, nFA, SB, nSB, INFINITY, fc, bb, pp, dB);
     double s0 = 0.0, s1 = 0.0;
     for (int64_t i = 0; i < nSA; ++i) s0 += dA[i];
     for (int64_t i = 0; i < nSB; ++i) s1 += dB[i];

@@ -82,6 +82,7 @@ SIGNATURES = {
     "mesh_chamfer_hinted": (C.c_int, [VP, VP, I64, VP, VP, I64, VP, SZ, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP]),
     "mesh_chamfer_noalloc": (C.c_int, [VP, VP, I64, VP, VP, I64, VP, VP, VP, VP, VP, VP, VP, VP]),
     "mesh_closest_point_backward": (C.c_int, [VP, VP, I64, VP, VP, VP, VP, VP, VP]),
+    "mesh_chamfer_backward": (C.c_int, [VP, VP, I64, VP, VP, I64, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP]),
     "mesh_interpolate_backward": (C.c_int, [VP, VP, VP, I64, VP, VP, VP]),
     "mesh_bind_gaussians_backward": (C.c_int, [VP, VP, VP, VP, I64, VP, VP, VP, VP, VP]),
     "mesh_batch_storage_bytes": (SZ, [I64, I64, I64]),

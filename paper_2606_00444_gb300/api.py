@@ -166,8 +166,8 @@ class MeshBVH:
                       hint: torch.Tensor | None = None) -> dict:
         """NearestSurface of every query.  `hint` (int32 face ids, -1 = none; may be
         out["face"] itself) warm-starts the search, e.g. with the previous frame's
-        answers; the result is the one without it up to order-dependent near ties
-        (faces within about 2e-6 of the nearest distance; see mesh_closest_point)."""
+        answers; the result is the one without it, bit for bit (the tie rule does not
+        depend on the order in which faces are met; see mesh_closest_point)."""
         Q = _f32(Q, 3, "Q")
         n = Q.shape[0]
         if hint is not None:
@@ -498,8 +498,8 @@ def chamfer(A: MeshBVH, SA: torch.Tensor, B: MeshBVH, SB: torch.Tensor, per_samp
     `ps` reuses per-sample output arrays (faceA, baryA, dist2A, faceB, baryB, dist2B);
     `hints` = (faces of B for SA, faces of A for SB), int32 (-1 = none, either may be
     None, and each may be the matching face output itself), warm-starts the searches,
-    e.g. with the previous frame's answers; the results are those without them up to
-    order-dependent near ties (see mesh_closest_point)."""
+    e.g. with the previous frame's answers; the results are those without them, bit
+    for bit."""
     SA = _f32(SA, 3, "SA")
     SB = _f32(SB, 3, "SB")
     nA, nB = SA.shape[0], SB.shape[0]
@@ -528,6 +528,30 @@ def chamfer(A: MeshBVH, SA: torch.Tensor, B: MeshBVH, SB: torch.Tensor, per_samp
                                     _ptr(ps.get("faceB")), _ptr(ps.get("baryB")), _ptr(ps.get("dist2B")),
                                     _stream()), "mesh_chamfer")
     return (out, ps) if per_sample else out
+
+
+def chamfer_backward(A: MeshBVH, SA: torch.Tensor, B: MeshBVH, SB: torch.Tensor, g: torch.Tensor,
+                     ps: dict, gSA=None, gVA=None, gSB=None, gVB=None) -> None:
+    """Reverse mode of chamfer() (mesh_chamfer_backward), both directions in one launch:
+    g = dL/d(out) (float64 [2] on the device), ps = the forward's per-sample faceA /
+    baryA / faceB / baryB; gSA / gSB are written, gVA / gVB accumulated (each may be
+    None), on the meshes' current vertex buffers."""
+    SA = _f32(SA, 3, "SA")
+    SB = _f32(SB, 3, "SB")
+    if not g.is_cuda or g.dtype != torch.float64 or g.numel() != 2:
+        raise ValueError("g must be a CUDA float64 tensor of 2 elements")
+    g = g.contiguous()
+    for name, t, n in (("gSA", gSA, SA.shape[0]), ("gSB", gSB, SB.shape[0])):
+        if t is not None and (t.dtype != torch.float32 or tuple(t.shape) != (n, 3) or not t.is_contiguous()):
+            raise ValueError(f"{name} must be a contiguous float32 [{n}, 3] tensor")
+    for name, t in (("gVA", gVA), ("gVB", gVB)):
+        if t is not None and (t.dtype != torch.float32 or t.dim() != 2 or t.shape[1] != 3
+                              or not t.is_contiguous()):
+            raise ValueError(f"{name} must be a contiguous float32 [nV, 3] tensor")
+    check(lib().mesh_chamfer_backward(A.handle, SA.data_ptr(), SA.shape[0], B.handle, SB.data_ptr(),
+                                      SB.shape[0], g.data_ptr(), _ptr(ps["faceA"]), _ptr(ps["baryA"]),
+                                      _ptr(ps["faceB"]), _ptr(ps["baryB"]), _ptr(gSA), _ptr(gVA),
+                                      _ptr(gSB), _ptr(gVB), _stream()), "mesh_chamfer_backward")
 
 
 def emd(A: torch.Tensor, B: torch.Tensor, eps_rel: float = 1e-5, max_iters: int = 1_000_000,

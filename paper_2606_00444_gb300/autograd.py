@@ -11,7 +11,7 @@ import math
 
 import torch
 
-from .api import MeshBVH, chamfer
+from .api import MeshBVH, chamfer, chamfer_backward
 
 
 class PointMeshDistance(torch.autograd.Function):
@@ -84,15 +84,11 @@ class Chamfer(torch.autograd.Function):
         gVA = torch.zeros_like(VA) if need[1] else None
         gSB = torch.empty_like(SB) if need[3] else None
         gVB = torch.zeros_like(VB) if need[4] else None
-        nA, nB = SA.shape[0], SB.shape[0]
-        if (gSA is not None or gVB is not None) and nA > 0:
-            bvhB.update_vertices(VB)
-            w = (g[0] / nA).float().expand(nA).contiguous()
-            bvhB.closest_point_backward(SA, faceA, baryA, w, gSA, gVB)
-        if (gSB is not None or gVA is not None) and nB > 0:
-            bvhA.update_vertices(VA)
-            w = (g[1] / nB).float().expand(nB).contiguous()
-            bvhA.closest_point_backward(SB, faceB, baryB, w, gSB, gVA)
+        bvhA.update_vertices(VA)
+        bvhB.update_vertices(VB)
+        chamfer_backward(bvhA, SA, bvhB, SB, g.detach().to(torch.float64).contiguous(),
+                         dict(faceA=faceA, baryA=baryA, faceB=faceB, baryB=baryB),
+                         gSA, gVA, gSB, gVB)
         return gSA, gVA, None, gSB, gVB, None
 
 

@@ -7,8 +7,11 @@
 // nearer is entered and the farther pushed, with its box distance, on a
 // per-thread stack kept in shared memory ([depth][thread], conflict free)
 // that spills to a small local array.  Boxes are pruned against the tie
-// window of the nearest distance found so far, so no face that could win the
-// tie rule is ever skipped.
+// window of the nearest distance found so far, widened by the float32 error
+// bound of a computed distance, so no face whose computed distance could fall
+// inside the final window is ever skipped.  The nearest face is the lowest id
+// within that final window (see Best), the same for every tree, traversal
+// order and warm start: a function of the query and the mesh alone.
 #include <math.h>
 
 #include <mutex>
@@ -189,49 +192,100 @@ struct Hit {
     float d2;
 };
 
-// Squared upper edge of the tie window around a nearest squared distance d2.
-__device__ __forceinline__ float tie_window2(float d2, float tau) {
-    float r = sqrtf(d2) * (1.0f + kTieRel) + tau;
-    return r * r;
-}
-
-// Pruning threshold implied by an upper bound u2 on the nearest squared
-// distance: the tie window of u2, widened by 2e-5 relative to cover float32
-// rounding of the bound itself.
-__device__ __forceinline__ float bound_window2(float u2, float tau) {
-    return tie_window2(u2 * 1.00004f, tau);
-}
+// Float32 error bound of a computed point-triangle or point-box distance for a
+// query q on a mesh whose coordinates are at most vmax in magnitude.  Every
+// difference such as q - a is below 2 s in magnitude, s = max(|q|_inf, vmax),
+// and the residual assembled from such differences (and the box distance)
+// carries at most about 30 eps32 s of rounding; 2^-18 s = 64 eps32 s covers
+// it with a margin.  Pruning widened by this bound never skips a face whose
+// computed distance lies inside the tie window, whatever the tree.
+constexpr float kSlackScale = 0x1p-18f;
 
 struct Traversal {
     const float4 *__restrict__ nodes;
     const float4 *__restrict__ tris;
     int n;
-    float tau;
+    float tau;     // absolute floor of the tie window (1e-12 of the box diagonal)
+    float vmax;    // largest coordinate magnitude of the mesh box
     bool mmd;      // use MinMaxDist bounds (unbounded queries; a cutoff is tighter)
 };
 
-// Candidate bookkeeping of the tie rule: dmin is the nearest squared distance
-// seen; the kept face is the lowest id within the window of dmin.
+__device__ __forceinline__ float query_slack(const Traversal &T, float3 q) {
+    return kSlackScale * fmaxf(fmaxf(fabsf(q.x), fabsf(q.y)), fmaxf(fabsf(q.z), T.vmax));
+}
+
+// The two thresholds of a nearest squared distance m: w2, the tie window (a
+// face with d2 <= w2 counts as equally near), and p2, the pruning radius (the
+// window widened by the float32 bound `slack`, so a box whose computed
+// distance exceeds p2 holds no face whose computed distance is within w2).
+__device__ __forceinline__ void windows(float m, float tau, float slack, float &w2, float &p2) {
+    float r = sqrtf(m) * (1.0f + kTieRel) + tau;
+    w2 = r * r;
+    r += slack;
+    p2 = r * r;
+}
+
+// Pruning radius implied by an upper bound u2 on the nearest squared distance
+// (a MinMaxDist): some face lies within sqrt(u2) in exact arithmetic, so the
+// final nearest computed distance is at most sqrt(u2) + slack; u2 itself is
+// widened by 4e-5 relative for its own rounding.
+__device__ __forceinline__ float bound_window2(float u2, float tau, float slack) {
+    float r = (sqrtf(u2 * 1.00004f) + slack) * (1.0f + kTieRel) + tau + slack;
+    return r * r;
+}
+
+// Pruning radius before any hit: the cutoff itself, widened the same way
+// (faces just past the cutoff can still fall in the tie window of a hit).
+__device__ __forceinline__ float cutoff_window2(float maxd2, float tau, float slack) {
+    if (isinf(maxd2)) return INFINITY;
+    float r = sqrtf(maxd2) * (1.0f + kTieRel) + tau + slack;
+    return r * r;
+}
+
+// Candidate bookkeeping of the tie rule.  dmin is the nearest squared
+// distance seen; the kept face is the lowest id among the faces seen within
+// the window of dmin -- as long as every face seen inside the current window,
+// other than the kept one, has a higher id.  `other` is the least squared
+// distance of the faces seen and not kept; when the kept face leaves the
+// shrinking window while `other` is still inside it, one of those faces may
+// have the lowest id, and `other` is set to -1: the query is resolved at the
+// end by one search with the final window fixed (resolve_ties).  The answer
+// is therefore the lowest id within the final window, whatever the order in
+// which faces were met.
 struct Best {
     int leaf, face;
-    float d2, dmin, thr;
+    float d2, dmin, thr, other, slack;
 };
+
+__device__ __forceinline__ Best make_best(const Traversal &T, float3 q, float maxd2) {
+    float sl = query_slack(T, q);
+    return Best{-1, 0x7fffffff, INFINITY, INFINITY, cutoff_window2(maxd2, T.tau, sl), INFINITY, sl};
+}
 
 __device__ __forceinline__ void consider(Best &B, int leaf, int face, float d2, float maxd2,
                                          float tau) {
-    if (B.leaf < 0) {
-        if (d2 <= maxd2) {
-            B.leaf = leaf; B.face = face; B.d2 = d2;
-            B.dmin = fminf(B.dmin, d2);
-            B.thr = fminf(B.thr, tie_window2(B.dmin, tau));
-        }
+    float nmin = fminf(B.dmin, d2);
+    if (nmin > maxd2) {                       // no hit yet and this face is past the cutoff:
+        B.other = fminf(B.other, d2);         // noted only (it may fall in a later hit's window)
         return;
     }
-    float nmin = fminf(B.dmin, d2);
-    float w2 = tie_window2(nmin, tau);
-    if (d2 <= w2 && (face < B.face || B.d2 > w2)) { B.leaf = leaf; B.face = face; B.d2 = d2; }
+    float w2, p2;
+    windows(nmin, tau, B.slack, w2, p2);
+    if (d2 <= w2) {
+        if (B.leaf >= 0 && B.d2 <= w2) {      // the kept face stays inside the window
+            if (face < B.face) {
+                B.other = fminf(B.other, B.d2);
+                B.leaf = leaf; B.face = face; B.d2 = d2;
+            } else if (face != B.face) {
+                B.other = fminf(B.other, d2);
+            }
+        } else {                              // first hit, or the kept face left the window
+            if (B.other <= w2) B.other = -1.0f;
+            B.leaf = leaf; B.face = face; B.d2 = d2;
+        }
+    }
     B.dmin = nmin;
-    B.thr = fminf(B.thr, w2);
+    B.thr = fminf(B.thr, p2);
 }
 
 __device__ __forceinline__ void test_leaf(const Traversal &T, Best &B, int leaf, float3 q,
@@ -241,6 +295,59 @@ __device__ __forceinline__ void test_leaf(const Traversal &T, Best &B, int leaf,
     float u, v, w;
     float d2 = tri_closest(q, xyz(a), xyz(b), xyz(c), b.w != 0.0f, u, v, w);
     consider(B, leaf, __float_as_int(a.w), d2, maxd2, T.tau);
+}
+
+// The tie rule with the window fixed: one depth-first search that visits every
+// box within the pruning radius of B.dmin and keeps the lowest face id whose
+// distance lies within its window.  Run only for the rare queries whose online
+// bookkeeping could not decide (three or more faces within about 2e-6 of one
+// another, met in an order that moved the window past the kept one).
+__device__ __noinline__ void resolve_ties(const Traversal &T, Best &B, float3 q,
+                                          unsigned int *status) {
+    float w2, p2;
+    windows(B.dmin, T.tau, B.slack, w2, p2);
+    int bl = -1, bf = 0x7fffffff;
+    float bd = INFINITY;
+    auto test = [&](int leaf) {
+        const float4 *t = T.tris + 3 * (size_t)leaf;
+        float4 a = ldg4(t), b = ldg4(t + 1), c = ldg4(t + 2);
+        float u, v, w;
+        float d2 = tri_closest(q, xyz(a), xyz(b), xyz(c), b.w != 0.0f, u, v, w);
+        int f = __float_as_int(a.w);
+        if (d2 <= w2 && f < bf) { bl = leaf; bf = f; bd = d2; }
+    };
+    if (T.n == 1) {
+        test(0);
+    } else if (T.n > 1) {
+        int stk[kStackTotal];
+        int sp = 0, node = 0;
+        while (true) {
+            const float4 *r = T.nodes + 4 * (size_t)node;
+            float4 l0 = ldg4(r), l1 = ldg4(r + 1), r0 = ldg4(r + 2), r1 = ldg4(r + 3);
+            int cl = __float_as_int(l0.w), cr = __float_as_int(r0.w);
+            bool il = box_d2(q, l0, l1) <= p2, ir = box_d2(q, r0, r1) <= p2;
+            if (il && cl < 0) test(-cl - 1);
+            if (ir && cr < 0) test(-cr - 1);
+            bool gl = il && cl >= 0, gr = ir && cr >= 0;
+            if (gl && gr) {
+                if (sp < kStackTotal) stk[sp++] = cr;
+                else atomicOr(status, (unsigned)MESH_DEV_STACK_OVERFLOW);
+                node = cl;
+                continue;
+            }
+            if (gl) { node = cl; continue; }
+            if (gr) { node = cr; continue; }
+            if (sp == 0) break;
+            node = stk[--sp];
+        }
+    }
+    if (bl >= 0) { B.leaf = bl; B.face = bf; B.d2 = bd; }
+    B.other = INFINITY;
+}
+
+__device__ __forceinline__ Hit finish(const Traversal &T, Best &B, float3 q, unsigned int *status) {
+    if (B.other < 0.0f) resolve_ties(T, B, q, status);
+    return Hit{B.leaf, B.face, B.d2};
 }
 
 // kSmem: stack entries per thread kept in shared memory (the rest spill to a
@@ -254,17 +361,14 @@ struct Counts {
 
 // hint_leaf >= 0: a leaf tested before the traversal (a warm start, e.g. the
 // previous frame's nearest face); its distance bounds the search from the
-// first node on.  Every leaf within the final tie window is still reached, so
-// the distance stays within that window and the face is the same, except
-// where the online tie rule depends on the order in which faces are met: a
-// face inside the final window can be dropped while a lower-id face is kept,
-// and that face can later leave the window (three or more faces within about
-// 2e-6 of one another).
+// first node on.  Every leaf within the final tie window is still reached and
+// the tie rule does not depend on the order, so the answer is the same as
+// without the hint; only the work changes.
 template <int kBlockT, int kSmem = kStackShared, bool kOneSite = false, bool kCount = false>
 __device__ __forceinline__ Hit nearest(const Traversal &T, float3 q, float maxd2,
                                        int2 (*stk)[kBlockT], unsigned int *status,
                                        Counts *cnt = nullptr, int hint_leaf = -1) {
-    Best B{-1, 0x7fffffff, INFINITY, INFINITY, maxd2};
+    Best B = make_best(T, q, maxd2);
     if (hint_leaf >= 0) test_leaf(T, B, hint_leaf, q, maxd2);
     if (T.n == 1) {
         if constexpr (kCount) cnt->tests++;
@@ -283,7 +387,7 @@ __device__ __forceinline__ Hit nearest(const Traversal &T, float3 q, float maxd2
             if (T.mmd) {
                 ml = box_minmax_d2(q, l0, l1);
                 mr = box_minmax_d2(q, r0, r1);
-                B.thr = fminf(B.thr, bound_window2(fminf(ml, mr), T.tau));
+                B.thr = fminf(B.thr, bound_window2(fminf(ml, mr), T.tau, B.slack));
             }
             int cl = __float_as_int(l0.w), cr = __float_as_int(r0.w);
             if constexpr (kCount) cnt->tests += (cl < 0 && dl <= B.thr) + (cr < 0 && dr <= B.thr);
@@ -324,21 +428,20 @@ __device__ __forceinline__ Hit nearest(const Traversal &T, float3 q, float maxd2
             if (!found) break;
         }
     }
-    return Hit{B.leaf, B.face, B.d2};
+    return finish(T, B, q, status);
 }
 
 // One thread per query, "while-while" form: internal nodes are traversed
 // while leaf children are only queued (up to kLeafQueue); the queued leaves
 // are tested when every lane still traversing has one queued (or its queue is
 // full, or it is done).  Leaf tests then run with the warp mostly converged
-// instead of in almost every step.  Same answers as nearest() up to the
-// order-dependent near ties noted there.
+// instead of in almost every step.  Same answers as nearest().
 constexpr int kLeafQueue = 4;
 
 template <int kBlockT>
 __device__ __forceinline__ Hit nearest_ww(const Traversal &T, float3 q, float maxd2,
                                           int2 (*stk)[kBlockT], unsigned int *status) {
-    Best B{-1, 0x7fffffff, INFINITY, INFINITY, maxd2};
+    Best B = make_best(T, q, maxd2);
     if (T.n == 1) {
         test_leaf(T, B, 0, q, maxd2);
         return Hit{B.leaf, B.face, B.d2};
@@ -360,7 +463,7 @@ __device__ __forceinline__ Hit nearest_ww(const Traversal &T, float3 q, float ma
             if (T.mmd) {
                 ml = box_minmax_d2(q, l0, l1);
                 mr = box_minmax_d2(q, r0, r1);
-                B.thr = fminf(B.thr, bound_window2(fminf(ml, mr), T.tau));
+                B.thr = fminf(B.thr, bound_window2(fminf(ml, mr), T.tau, B.slack));
             }
             int cl = __float_as_int(l0.w), cr = __float_as_int(r0.w);
             if (cl < 0 && dl <= B.thr) lq[nq++] = -cl - 1;
@@ -389,7 +492,7 @@ __device__ __forceinline__ Hit nearest_ww(const Traversal &T, float3 q, float ma
         nq = 0;
         if (done) break;
     }
-    return Hit{B.leaf, B.face, B.d2};
+    return finish(T, B, q, status);
 }
 
 // Depth-first search of the subtree under `start` by one thread with a
@@ -408,7 +511,7 @@ __device__ __noinline__ void dfs_private(const Traversal &T, Best &B, int start,
         if (T.mmd) {
             ml = box_minmax_d2(q, l0, l1);
             mr = box_minmax_d2(q, r0, r1);
-            B.thr = fminf(B.thr, bound_window2(fminf(ml, mr), T.tau));
+            B.thr = fminf(B.thr, bound_window2(fminf(ml, mr), T.tau, B.slack));
         }
         int cl = __float_as_int(l0.w), cr = __float_as_int(r0.w);
         if (cl < 0 && dl <= B.thr) test_leaf(T, B, -cl - 1, q, maxd2);
@@ -478,13 +581,12 @@ __device__ Hit nearest_group(const Traversal &T, float3 q, float maxd2, bool val
     const int lane = threadIdx.x & 31;
     const int gl = lane & (G - 1);
     const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
-    int bleaf = -1, bface = 0x7fffffff;
-    float bd2 = INFINITY, dmin = INFINITY, thr = maxd2;
+    // The group's candidate state: the bookkeeping of consider(), identical in
+    // every lane of the group (all updates come from group-wide reductions).
+    Best S = make_best(T, q, maxd2);
     int sp = 0;
     if (valid && T.n == 1) {
-        Best B{-1, 0x7fffffff, INFINITY, INFINITY, maxd2};
-        test_leaf(T, B, 0, q, maxd2);
-        bleaf = B.leaf; bface = B.face; bd2 = B.d2;
+        test_leaf(T, S, 0, q, maxd2);
     } else if (valid && T.n > 1) {
         // Greedy dive (every lane of the group on the same path): the nearer
         // child down to a leaf gives the parallel phase a tight window from
@@ -499,10 +601,8 @@ __device__ Hit nearest_group(const Traversal &T, float3 q, float maxd2, bool val
             bool lfirst = dl < dr || (dl == dr && ml <= mr);
             int c = lfirst ? __float_as_int(l0.w) : __float_as_int(r0.w);
             if (c >= 0) { node = c; continue; }
-            Best B{-1, 0x7fffffff, INFINITY, INFINITY, maxd2};
-            test_leaf(T, B, -c - 1, q, maxd2);
-            if (hint_leaf >= 0) test_leaf(T, B, hint_leaf, q, maxd2);   // warm start
-            if (B.leaf >= 0) { bleaf = B.leaf; bface = B.face; bd2 = B.d2; dmin = B.dmin; thr = B.thr; }
+            test_leaf(T, S, -c - 1, q, maxd2);
+            if (hint_leaf >= 0) test_leaf(T, S, hint_leaf, q, maxd2);   // warm start
             break;
         }
         if (gl == 0) stk[0] = make_int2(0, __float_as_int(0.0f));
@@ -517,11 +617,11 @@ __device__ Hit nearest_group(const Traversal &T, float3 q, float maxd2, bool val
         if (act) e = stk[sp - 1 - gl];
         __syncwarp();
         sp -= take;
-        act = act && __int_as_float(e.y) <= thr;
+        act = act && __int_as_float(e.y) <= S.thr;
         float c0 = INFINITY, c1 = INFINITY;
         int f0 = 0x7fffffff, f1 = 0x7fffffff, lf0 = -1, lf1 = -1;
         int npush = 0;
-        float lane_ub = INFINITY;
+        float lane_ub = INFINITY, lane_other = INFINITY;
         int2 p_far = make_int2(0, 0), p_near = make_int2(0, 0);
         if (act && !near_full) {
             const float4 *r = T.nodes + 4 * (size_t)e.x;
@@ -535,21 +635,21 @@ __device__ Hit nearest_group(const Traversal &T, float3 q, float maxd2, bool val
             }
             int cl = __float_as_int(l0.w), cr = __float_as_int(r0.w);
             float u, v, w;
-            if (cl < 0 && dl <= thr) {
+            if (cl < 0 && dl <= S.thr) {
                 lf0 = -cl - 1;
                 const float4 *t = T.tris + 3 * (size_t)lf0;
                 float4 a = ldg4(t), b = ldg4(t + 1), c = ldg4(t + 2);
                 c0 = tri_closest(q, xyz(a), xyz(b), xyz(c), b.w != 0.0f, u, v, w);
                 f0 = __float_as_int(a.w);
             }
-            if (cr < 0 && dr <= thr) {
+            if (cr < 0 && dr <= S.thr) {
                 lf1 = -cr - 1;
                 const float4 *t = T.tris + 3 * (size_t)lf1;
                 float4 a = ldg4(t), b = ldg4(t + 1), c = ldg4(t + 2);
                 c1 = tri_closest(q, xyz(a), xyz(b), xyz(c), b.w != 0.0f, u, v, w);
                 f1 = __float_as_int(a.w);
             }
-            bool gol = cl >= 0 && dl <= thr, gor = cr >= 0 && dr <= thr;
+            bool gol = cl >= 0 && dl <= S.thr, gor = cr >= 0 && dr <= S.thr;
             if (gol && gor) {
                 bool lfirst = dl < dr || (dl == dr && ml <= mr);
                 p_near = make_int2(lfirst ? cl : cr, __float_as_int(lfirst ? dl : dr));
@@ -563,19 +663,20 @@ __device__ Hit nearest_group(const Traversal &T, float3 q, float maxd2, bool val
                 npush = 1;
             }
         } else if (act) {
-            Best P{-1, 0x7fffffff, INFINITY, dmin, thr};
+            Best P = S;                          // the group's window and bounds, no kept face
+            P.leaf = -1; P.face = 0x7fffffff; P.d2 = INFINITY; P.other = INFINITY;
             dfs_private(T, P, e.x, q, maxd2, status);
             if (P.leaf >= 0) { c0 = P.d2; f0 = P.face; lf0 = P.leaf; }
+            lane_other = P.other;                // faces it met and did not keep (-1: undecided)
         }
-        // merge the group's candidates under the tie rule
-        if (bleaf < 0) {                       // nothing accepted yet: the cutoff applies
-            if (c0 > maxd2) c0 = INFINITY;
-            if (c1 > maxd2) c1 = INFINITY;
-        }
+        // Merge the step's candidates into S (consider() for a set of faces at
+        // once).  Every reduction runs on the full warp, outside any branch.
         float m = grp_min<G>(fminf(c0, c1));
         float ub = grp_min<G>(lane_ub);
-        float nmin = fminf(dmin, m);
-        float w2 = nmin < INFINITY ? tie_window2(nmin, T.tau) : INFINITY;
+        float nmin = fminf(S.dmin, m);
+        const bool hit = nmin <= maxd2;
+        float w2 = -1.0f, p2 = INFINITY;
+        if (hit) windows(nmin, T.tau, S.slack, w2, p2);
         int fc = min(c0 <= w2 ? f0 : 0x7fffffff, c1 <= w2 ? f1 : 0x7fffffff);
         int fmin = grp_min<G>(fc);
         bool mine = fmin != 0x7fffffff && fc == fmin;
@@ -585,13 +686,23 @@ __device__ Hit nearest_group(const Traversal &T, float3 q, float maxd2, bool val
         int mlf = (c0 <= w2 && f0 == fmin) ? lf0 : lf1;
         float sd2 = __shfl_sync(0xffffffffu, md2, src, G);
         int slf = __shfl_sync(0xffffffffu, mlf, src, G);
-        if (m < INFINITY) {
-            bool keep = bleaf >= 0 && bd2 <= w2 && bface < fmin;
-            if (!keep && fmin != 0x7fffffff) { bface = fmin; bd2 = sd2; bleaf = slf; }
-            dmin = nmin;
-            thr = fminf(thr, w2);
+        const bool stays = S.leaf >= 0 && S.d2 <= w2;          // the kept face is still inside
+        const int kept = (stays && S.face <= fmin) ? S.face : fmin;
+        float lo = lane_other;                                   // every other face goes to `other`
+        if (f0 != kept) lo = fminf(lo, c0);
+        if (f1 != kept) lo = fminf(lo, c1);
+        float oth = grp_min<G>(lo);
+        if (hit) {
+            if (!stays && S.other <= w2) S.other = -1.0f;        // an earlier face may be lower
+            if (kept != S.face) {
+                if (stays) S.other = fminf(S.other, S.d2);
+                S.leaf = slf; S.face = fmin; S.d2 = sd2;
+            }
+            S.dmin = nmin;
+            S.thr = fminf(S.thr, p2);
         }
-        thr = fminf(thr, bound_window2(ub, T.tau));
+        S.other = fminf(S.other, oth);
+        S.thr = fminf(S.thr, bound_window2(ub, T.tau, S.slack));
         // push surviving children: lane G-1's lowest, lane 0's on top
         int total = grp_sum<G>(npush);
         int above = total - grp_incl_scan<G>(npush, gl);
@@ -600,13 +711,22 @@ __device__ Hit nearest_group(const Traversal &T, float3 q, float maxd2, bool val
         sp += total;
         __syncwarp();
     }
-    return Hit{bleaf, bface, bd2};
+    // only the group's first lane writes the result, so only it resolves
+    if (valid && gl == 0 && S.other < 0.0f) resolve_ties(T, S, q, status);
+    return Hit{S.leaf, S.face, S.d2};
 }
 
-__device__ __forceinline__ float traversal_tau(const Header *hdr) {
-    float4 lo = hdr->root_lo, hi = hdr->root_hi;
+// Per-mesh constants of the tie rule from the mesh box: the window's absolute
+// floor (1e-12 of the box diagonal) and the largest coordinate magnitude.
+__device__ __forceinline__ void set_scale(Traversal &T, float4 lo, float4 hi) {
     float dx = hi.x - lo.x, dy = hi.y - lo.y, dz = hi.z - lo.z;
-    return kTieAbs * sqrtf(dx * dx + dy * dy + dz * dz);
+    T.tau = kTieAbs * sqrtf(dx * dx + dy * dy + dz * dz);
+    T.vmax = fmaxf(fmaxf(fmaxf(fabsf(lo.x), fabsf(hi.x)), fmaxf(fabsf(lo.y), fabsf(hi.y))),
+                   fmaxf(fabsf(lo.z), fabsf(hi.z)));
+    if (!(T.vmax < INFINITY)) T.vmax = 0.0f;   // empty mesh: an inverted (infinite) box
+}
+__device__ __forceinline__ void set_scale(Traversal &T, const Header *hdr) {
+    set_scale(T, hdr->root_lo, hdr->root_hi);
 }
 
 // Writes the outputs of one query (recomputing the weights of the winning face).
@@ -659,7 +779,7 @@ k_closest_point(Traversal T, const Header *__restrict__ hdr, unsigned int *statu
     int64_t k = (int64_t)blockIdx.x * kQueryBlock + threadIdx.x;
     if (k >= nQ) return;
     const int64_t i = order ? (int64_t)order[k] : k;       // order: a permutation of the queries
-    T.tau = traversal_tau(hdr);
+    set_scale(T, hdr);
     float3 q = make_float3(Q[3 * i], Q[3 * i + 1], Q[3 * i + 2]);
     int hint_leaf = -1;
     if (hint) {                                   // may alias face: read before the write below
@@ -691,12 +811,13 @@ k_closest_point(Traversal T, const Header *__restrict__ hdr, unsigned int *statu
 // record) and all control flow outside the leaf tests is warp-uniform: the
 // warp runs the union of its queries' traversals with every lane active,
 // instead of each lane's traversal with most lanes idle.  Same answers as the
-// depth-first kernels up to the order-dependent near ties noted at nearest().
+// depth-first kernels.
 __device__ __forceinline__ Hit nearest_packet(const Traversal &T, float3 q, float maxd2, bool valid,
                                               int *wstk, unsigned int *status) {
     const unsigned int kFull = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    Best B{-1, 0x7fffffff, INFINITY, INFINITY, valid ? maxd2 : -1.0f};
+    Best B = make_best(T, q, maxd2);
+    if (!valid) B.thr = -1.0f;                   // a lane past the end prunes everything
     if (T.n == 1) {
         if (valid) test_leaf(T, B, 0, q, maxd2);
         return Hit{B.leaf, B.face, B.d2};
@@ -709,7 +830,7 @@ __device__ __forceinline__ Hit nearest_packet(const Traversal &T, float3 q, floa
         float dl = box_d2(q, l0, l1), dr = box_d2(q, r0, r1);
         if (T.mmd && valid)
             B.thr = fminf(B.thr, bound_window2(fminf(box_minmax_d2(q, l0, l1), box_minmax_d2(q, r0, r1)),
-                                               T.tau));
+                                               T.tau, B.slack));
         int cl = __float_as_int(l0.w), cr = __float_as_int(r0.w);
         bool wl = dl <= B.thr, wr = dr <= B.thr;
         unsigned int bl = __ballot_sync(kFull, wl), br = __ballot_sync(kFull, wr);
@@ -746,7 +867,7 @@ __device__ __forceinline__ Hit nearest_packet(const Traversal &T, float3 q, floa
         __syncwarp();
         if (!found) break;
     }
-    return Hit{B.leaf, B.face, B.d2};
+    return finish(T, B, q, status);
 }
 
 __global__ void __launch_bounds__(kQueryBlock, kQueryMinBlocks)
@@ -758,7 +879,7 @@ k_closest_point_packet(Traversal T, const Header *__restrict__ hdr, unsigned int
     if (w0 >= nQ) return;                                  // whole warp past the end
     const int64_t i = w0 + (threadIdx.x & 31);
     const bool valid = i < nQ;
-    T.tau = traversal_tau(hdr);
+    set_scale(T, hdr);
     float3 q = valid ? make_float3(Q[3 * i], Q[3 * i + 1], Q[3 * i + 2]) : make_float3(0.0f, 0.0f, 0.0f);
     Hit h = nearest_packet(T, q, maxd2, valid, wstk[threadIdx.x >> 5], status);
     if (valid) write_hit(T, h, q, i, face, bary, point, dist2);
@@ -883,7 +1004,7 @@ k_signed_distance(Traversal T, const Header *__restrict__ hdr, unsigned int *sta
     __shared__ int2 stk[kStackShared][kQueryBlock];
     int64_t i = (int64_t)blockIdx.x * kQueryBlock + threadIdx.x;
     if (i >= nQ) return;
-    T.tau = traversal_tau(hdr);
+    set_scale(T, hdr);
     float3 q = make_float3(Q[3 * i], Q[3 * i + 1], Q[3 * i + 2]);
     Hit h = nearest<kQueryBlock>(T, q, maxd2, stk, status);
     write_hit(T, h, q, i, face, bary, point, nullptr);
@@ -924,7 +1045,7 @@ mesh_status launch_signed_query(const mesh_bvh *bvh, const float *d_Q, int64_t n
 // the warp takes that many new query indices from a global counter.  Lanes no
 // longer wait for the slowest query of their warp (contact queries near the
 // surface need ~6x the visits of those far from it).  Same answers as the
-// depth-first kernels up to the order-dependent near ties noted at nearest().
+// depth-first kernels.
 // The counter lives in the mesh header (zeroed before each launch), so
 // concurrent calls on one handle must not overlap.
 constexpr int kRefill = 8;
@@ -938,10 +1059,10 @@ k_closest_point_persistent(Traversal T, const Header *__restrict__ hdr, unsigned
     int2 spill[kStackTotal - kSmem];
     const int lane = threadIdx.x & 31, tid = threadIdx.x;
     const unsigned lt = (1u << lane) - 1u;
-    T.tau = traversal_tau(hdr);
+    set_scale(T, hdr);
     int64_t qi = -1;
     float3 q = make_float3(0.f, 0.f, 0.f);
-    Best B{-1, 0x7fffffff, INFINITY, INFINITY, maxd2};
+    Best B = make_best(T, q, maxd2);
     int node = 0, sp = 0;
     bool exhausted = false;
     while (true) {
@@ -957,7 +1078,7 @@ k_closest_point_persistent(Traversal T, const Header *__restrict__ hdr, unsigned
                 if (cand < nQ) {
                     qi = cand;
                     q = make_float3(Q[3 * qi], Q[3 * qi + 1], Q[3 * qi + 2]);
-                    B = Best{-1, 0x7fffffff, INFINITY, INFINITY, maxd2};
+                    B = make_best(T, q, maxd2);
                     node = 0;
                     sp = 0;
                     if (T.n <= 1) {                      // no internal node to visit
@@ -980,7 +1101,7 @@ k_closest_point_persistent(Traversal T, const Header *__restrict__ hdr, unsigned
             if (T.mmd) {
                 ml = box_minmax_d2(q, l0, l1);
                 mr = box_minmax_d2(q, r0, r1);
-                B.thr = fminf(B.thr, bound_window2(fminf(ml, mr), T.tau));
+                B.thr = fminf(B.thr, bound_window2(fminf(ml, mr), T.tau, B.slack));
             }
             int cl = __float_as_int(l0.w), cr = __float_as_int(r0.w);
             if (cl < 0 && dl <= B.thr) test_leaf(T, B, -cl - 1, q, maxd2);
@@ -1008,7 +1129,7 @@ k_closest_point_persistent(Traversal T, const Header *__restrict__ hdr, unsigned
             }
         }
         if (fin) {
-            write_hit(T, Hit{B.leaf, B.face, B.d2}, q, qi, face, bary, point, dist2);
+            write_hit(T, finish(T, B, q, status), q, qi, face, bary, point, dist2);
             qi = -1;
         }
     }
@@ -1026,7 +1147,7 @@ k_closest_point_count(Traversal T, const Header *__restrict__ hdr, unsigned int 
     Counts c{0, 0};
     int hit = 0;
     if (i < nQ) {
-        T.tau = traversal_tau(hdr);
+        set_scale(T, hdr);
         float3 q = make_float3(Q[3 * i], Q[3 * i + 1], Q[3 * i + 2]);
         Hit h = nearest<kQueryBlock, kStackShared, false, true>(T, q, maxd2, stk, status, &c);
         hit = h.leaf >= 0;
@@ -1052,7 +1173,7 @@ k_closest_point_group(Traversal T, const Header *__restrict__ hdr, unsigned int 
     __shared__ int2 gstk[kQueryBlock / G][group_cap<G>()];
     int64_t i = ((int64_t)blockIdx.x * kQueryBlock + threadIdx.x) / G;
     bool valid = i < nQ;
-    T.tau = traversal_tau(hdr);
+    set_scale(T, hdr);
     float3 q = valid ? make_float3(Q[3 * i], Q[3 * i + 1], Q[3 * i + 2]) : make_float3(0.f, 0.f, 0.f);
     int hint_leaf = -1;
     if (valid && hint) {                          // every lane of the group reads it before any write
@@ -1084,10 +1205,8 @@ k_batch_closest_point(const float4 *__restrict__ nodes, const float4 *__restrict
         if (i < nQ) {
             int sc = segment_of(query_off, nscenes, i);
             int fb = __ldg(face_off + sc), ns = __ldg(face_off + sc + 1) - fb;
-            float4 lo = scene_box[2 * sc], hi = scene_box[2 * sc + 1];
-            float dx = hi.x - lo.x, dy = hi.y - lo.y, dz = hi.z - lo.z;
-            Traversal T{nodes + 4 * (size_t)fb, tris + 3 * (size_t)fb, ns,
-                        kTieAbs * sqrtf(dx * dx + dy * dy + dz * dz), mmd};
+            Traversal T{nodes + 4 * (size_t)fb, tris + 3 * (size_t)fb, ns, 0.0f, 0.0f, mmd};
+            set_scale(T, scene_box[2 * sc], scene_box[2 * sc + 1]);
             float3 q = make_float3(Q[3 * i], Q[3 * i + 1], Q[3 * i + 2]);
             Hit h = nearest<kQueryBlock>(T, q, maxd2, stk, status);
             if (h.leaf >= 0) h.face -= fb;
@@ -1140,7 +1259,7 @@ k_chamfer(ChamferSide A2B, ChamferSide B2A, unsigned int nbA, unsigned int *stat
     int64_t i = ((int64_t)(first ? blockIdx.x : blockIdx.x - nbA) * kQueryBlock + threadIdx.x) / G;
     double d2 = 0.0;
     Traversal T = C.T;
-    T.tau = traversal_tau(C.hdr);
+    set_scale(T, C.hdr);
     bool valid = i < C.n;
     float3 q = valid ? make_float3(C.S[3 * i], C.S[3 * i + 1], C.S[3 * i + 2])
                      : make_float3(0.f, 0.f, 0.f);
@@ -1208,7 +1327,7 @@ __global__ void k_interpolate(const int4 *__restrict__ faces, const float4 *__re
 }
 
 static Traversal traversal_of(const mesh_bvh *b, bool mmd = true) {
-    return Traversal{b->nodes(), b->tris(), (int)b->L.n_faces, 0.0f, mmd};
+    return Traversal{b->nodes(), b->tris(), (int)b->L.n_faces, 0.0f, 0.0f, mmd};
 }
 
 static size_t chamfer_blocks(int64_t n, int G = 1) {

@@ -72,6 +72,15 @@ def test_create_validates_storage_on_the_host():
     assert L.mesh_closest_point(h, fake, 0, C.c_float(1.0), None, None, None, None, None) == 0
     assert L.mesh_bind_gaussians(h, None, None, None, 3, None, None, None, None) == 1
     assert L.mesh_chamfer(h, fake, 4, h, fake, 4, None, 0, fake, *([None] * 6), None) == 3
+    # Chamfer backward: a missing gradient seed, faces or weights; no outputs = no work
+    assert L.mesh_chamfer_backward(h, fake, 4, h, fake, 4, None, fake, fake, fake, fake,
+                                   fake, None, None, None, None) == 1
+    assert L.mesh_chamfer_backward(h, fake, 4, h, fake, 4, fake, None, fake, fake, fake,
+                                   fake, None, None, None, None) == 1
+    assert L.mesh_chamfer_backward(h, fake, -1, h, fake, 4, fake, fake, fake, fake, fake,
+                                   None, None, None, None, None) == 1
+    assert L.mesh_chamfer_backward(h, fake, 4, h, fake, 4, fake, fake, fake, fake, fake,
+                                   None, None, None, None, None) == 0
     assert L.mesh_launch_count() == n0
     L.mesh_bvh_destroy(h)
 

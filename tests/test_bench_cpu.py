@@ -28,11 +28,20 @@ def test_reference_arm_prints_the_contract_line():
                            "d2h_bytes_per_step": 0}
 
 
-def test_committed_traffic_record_matches_the_kernel_sources():
-    """The roofline's DRAM traffic comes from a committed ncu capture, valid only while the
-    contact kernel's sources hash as they did when it was captured, and only for the
-    captured traversal variant."""
+def test_traffic_record_is_used_only_for_the_captured_sources():
+    """The roofline's DRAM / L2 traffic comes from a committed ncu capture; bench.py uses
+    it only while the contact kernel's sources hash as they did when it was captured,
+    and only for the captured traversal variant."""
+    import hashlib
     sys.path.insert(0, ROOT)
     import bench
-    assert bench.contact_traffic(2) == 41301248
+    p = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+    d = json.load(open(p))
+    m = hashlib.sha256()
+    for f in d["source_files"]:
+        m.update(open(os.path.join(ROOT, f), "rb").read())
+    current = m.hexdigest()[:16] == d["source_hash"]
+    for v, rec in d["by_variant"].items():
+        got = bench.contact_traffic(int(v))
+        assert got == (rec if current else None)
     assert bench.contact_traffic(99) is None

@@ -11,7 +11,7 @@ import torch
 
 import oracle
 from paper_2606_00444_gb300 import MeshBVH
-from parity import assert_same_up_to_near_ties, check_closest, dev, host
+from parity import assert_identical, check_closest, dev, host
 from workloads.isosurface import BlobSequence
 from workloads.meshes import displaced_icosphere, icosphere, torus, TorusSkinning
 from workloads.sampling import uniform_box
@@ -92,7 +92,7 @@ def test_varying_topology_frame_projection():
 
 def test_contact_workload_full_size():
     """1M particles, cutoff 0.05, against the 200k-face torus after 4-bone skinning:
-    sampled parity with the oracle, and refit answers equal rebuild answers in full."""
+    sampled parity with the oracle, and refit answers equal rebuild answers bit for bit."""
     V0, F = torus(400, 250)
     sk = TorusSkinning(V0, seed=3000)
     lo, hi = V0.min(0) - 0.2, V0.max(0) + 0.2
@@ -105,13 +105,8 @@ def test_contact_workload_full_size():
     rebuilt = MeshBVH.from_mesh(dev(V1), dev(F))
     out2 = rebuilt.closest_point(Pd, max_dist=0.05)
     torch.cuda.synchronize()
-    # the two trees are traversed in different orders: the same face (hence the very
-    # same float32 distance) unless a tie is resolved differently, which is rare
-    same = out["face"] == out2["face"]
-    assert (~same).sum().item() <= 1e-4 * P.shape[0]
-    assert torch.equal(out["dist2"][same], out2["dist2"][same])
-    d1, d2 = out["dist2"][~same].sqrt(), out2["dist2"][~same].sqrt()
-    assert torch.all((d1 - d2).abs() <= 1e-5 * torch.maximum(d1, torch.full_like(d1, 1e-3)))
+    # the two trees are traversed in different orders; the tie rule does not depend on it
+    assert_identical(out, out2)
     frac = (out["face"] >= 0).float().mean().item()
     assert 0.03 < frac < 0.4
     rng = np.random.default_rng(4)
@@ -139,7 +134,7 @@ def test_every_group_width_matches_oracle(c1, lanes):
         V, F = icosphere(4)
         centre = MeshBVH.from_mesh(dev(V), dev(F))
         Qc = (uniform_box(64, [-0.02] * 3, [0.02] * 3, seed=lanes)).astype(np.float32)
-        check_closest(V, F, Qc, centre.closest_point(dev(Qc)), max_tie_frac=0.2)
+        check_closest(V, F, Qc, centre.closest_point(dev(Qc)))
         assert bvh.status()[0] == 0 and centre.status()[0] == 0
     finally:
         set_query_group(0)
@@ -185,8 +180,7 @@ def test_warp_packet_traversal_ragged_and_sorted(c1, n):
 def test_warm_start_hint_gives_identical_answers(c1, variant):
     """mesh_closest_point_hinted: exact previous answers, random faces, -1 and
     out-of-range ids as hints, and the hint aliasing the face output, all give
-    the unhinted result bit for bit, up to rare near ties whose kept face depends
-    on the order faces are met (checked to lie within the tie window)."""
+    the unhinted result bit for bit."""
     from paper_2606_00444_gb300 import set_query_group, set_traversal
     _, _, VG, FG, Q = c1
     bvh = MeshBVH.from_mesh(dev(VG), dev(FG))
@@ -203,11 +197,11 @@ def test_warm_start_hint_gives_identical_answers(c1, variant):
                      dev(rng.integers(-5, 2 * FG.shape[0], n).astype(np.int32))]
             for hint in hints:
                 got = bvh.closest_point(dev(Q), max_dist=cut, hint=hint)
-                assert_same_up_to_near_ties(got, ref)
+                assert_identical(got, ref)
             out = {k: v.clone() for k, v in ref.items()}          # hint = the face output itself
             out["face"] = dev(rng.integers(0, FG.shape[0], n).astype(np.int32))
             bvh.closest_point(dev(Q), max_dist=cut, out=out, hint=out["face"])
-            assert_same_up_to_near_ties(out, ref)
+            assert_identical(out, ref)
         assert bvh.status()[0] == 0
     finally:
         set_query_group(0)
@@ -217,7 +211,7 @@ def test_warm_start_hint_gives_identical_answers(c1, variant):
 def test_warm_start_over_a_skinned_sequence_full_size():
     """The physics loop: each frame's contact query is hinted with the previous
     frame's faces (refit tree, 1M particles in Morton order, cutoff 0.05); the
-    answers equal the unhinted ones up to rare order-dependent near ties."""
+    answers equal the unhinted ones bit for bit."""
     from paper_2606_00444_gb300 import morton_order
     V0, F = torus(400, 250)
     sk = TorusSkinning(V0, seed=3000)
@@ -230,7 +224,7 @@ def test_warm_start_over_a_skinned_sequence_full_size():
         bvh.refit(dev(sk.frame(t)))
         ref = bvh.closest_point(P, 0.05)
         got = bvh.closest_point(P, 0.05, hint=face)
-        assert_same_up_to_near_ties(got, ref, max_frac=1e-5)
+        assert_identical(got, ref)
         face = got["face"]
     assert bvh.status()[0] == 0
 
@@ -239,8 +233,7 @@ def test_warm_start_over_a_skinned_sequence_full_size():
 def test_contact_step_equals_plain_queries(variant):
     """mesh_contact (previous faces as hints, queries ordered by the previous step's
     work classes, kept in the workspace -- garbage bytes at the first step) gives
-    mesh_closest_point's answers over a skinned sequence (up to rare order-dependent
-    near ties)."""
+    mesh_closest_point's answers over a skinned sequence, bit for bit."""
     from paper_2606_00444_gb300 import morton_order
     V0, F = torus(120, 70)
     sk = TorusSkinning(V0, seed=3001)
@@ -260,7 +253,7 @@ def test_contact_step_equals_plain_queries(variant):
         bvh.refit(dev(sk.frame(t)))
         ref = bvh.closest_point(P, 0.05)
         bvh.contact(P, 0.05, out, ws=ws)
-        assert_same_up_to_near_ties(out, ref)
+        assert_identical(out, ref)
     assert bvh.status()[0] == 0
 
 

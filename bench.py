@@ -48,8 +48,10 @@ WORKLOAD = "fixed-topology physics frame: torus 100k V / 200k F, 4-bone LBS, 1M 
 NU, NV_, CUTOFF, N_PART, G_PER_FACE, N_CD = 400, 250, 0.05, 1 << 20, 3, 10000
 SEED = 3000
 CONTACT_BYTES = 12 + 4 + 12 + 12 + 4      # query xyz in; face, bary, point, dist2 out
-NODE_BYTES = 64                            # one node visit reads both child boxes + links
+NODE_BYTES = 64                            # one node visit reads both 32-byte child boxes
 TRI_BYTES = 48                             # one triangle test reads a packed triangle
+REFIT_BYTES = 150                          # per face: 16 B index + ~8 B vertex share + 32 B leaf
+                                           # box + internal (2 x 32 B read + 32 B write)
 
 
 def parse():
@@ -60,9 +62,15 @@ def parse():
     ap.add_argument("--impl", default="meshgs", choices=["meshgs", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="physics",
-                    choices=["physics", "batch", "sequence", "fit", "tracking"],
+                    choices=["physics", "batch", "sequence", "fit", "tracking", "contact"],
                     help="physics: the default frame; batch: 64 scenes batched vs per scene; "
-                         "sequence: varying-topology conversion; fit: differentiable template fit")
+                         "sequence: varying-topology conversion; fit: differentiable template fit; "
+                         "contact: the contact kernel and the refit alone (profiling)")
+    ap.add_argument("--variant", type=int, default=-1,
+                    help="contact workload: one-thread traversal variant (-1: the autotuner's)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="physics workload: skip the batched, template-fit and 2.4M-face refit "
+                         "measurements that follow the frame")
     return ap.parse_args()
 
 
@@ -468,9 +476,11 @@ def gpu_arm(args, rank, world, local_rank):
 
     # traversal work of the contact queries on this frame (counting kernel, untimed)
     stats = fixed.closest_point_stats(P, CUTOFF)
+    from paper_2606_00444_gb300 import l2_read_bandwidth
+    l2 = l2_read_bandwidth()
     out = dict(ms=ms, wall=wall, step_ms=step_ms, stages=st, clocks=ck, e2e_ms=float(np.mean(e_ms)),
                ploc_build_ms=ploc_build_ms,
-               tuned=tuned, stats=stats,
+               tuned=tuned, stats=stats, l2_read_gbs=l2,
                h2d=h2d, d2h=d2h, launches=launches_per_frame * args.steps,
                contact_hits=int((contact["face"] >= 0).sum().item()),
                chamfer=[float(x) for x in cd_out.cpu()])
@@ -505,57 +515,99 @@ def peaks():
 # ---------------------------------------------------------------------------
 # CPU oracle (the reported baseline and the reference arm)
 # ---------------------------------------------------------------------------
-def oracle_frame_sample(W, frame, nq, ng, ncd, rng):
+def host_cpu():
+    """(model name, logical cores) of the host, from /proc/cpuinfo or lscpu."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Model"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu model", "hardware")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    return model or "unknown", os.cpu_count() or 1
+
+
+def oracle_frame_sample(W, frame, nq, ng, ncd, rng, parallel=False):
     """Time the oracle on one frame: full serial LBVH build, nq contact queries,
-    ng Gaussians, ncd Chamfer samples per side; returns the extrapolated time of
-    a full frame (1M queries, 600k Gaussians, 10k + 10k Chamfer samples)."""
+    ng Gaussians, ncd Chamfer samples per side (the brute-force parts over every
+    host core when parallel); returns the extrapolated time of a full frame (1M
+    queries, 600k Gaussians, 10k + 10k Chamfer samples) and the time spent."""
     import oracle
     V = W.frames[frame % len(W.frames)]
     t0 = time.perf_counter()
     oracle.build_lbvh(V, W.F)
     t1 = time.perf_counter()
     qi = rng.choice(N_PART, nq, replace=False)
-    oracle.closest_point(V, W.F, W.P[qi], CUTOFF)
+    oracle.closest_point(V, W.F, W.P[qi], CUTOFF, parallel=parallel)
     t2 = time.perf_counter()
     gi = rng.choice(W.gface.shape[0], ng, replace=False)
-    oracle.bind_gaussians(V, W.F, W.gface[gi], W.gbary[gi])
+    oracle.bind_gaussians(V, W.F, W.gface[gi], W.gbary[gi], parallel=parallel)
     t3 = time.perf_counter()
     ci = rng.choice(N_CD, ncd, replace=False)
     SA = oracle.interpolate(V.astype(np.float64), W.F, W.cd_face[ci], W.cd_bary[ci])
-    oracle.chamfer(V, W.F, SA, W.V0, W.F, W.rest_samples[ci])
+    oracle.chamfer(V, W.F, SA, W.V0, W.F, W.rest_samples[ci], parallel=parallel)
     t4 = time.perf_counter()
     full = ((t1 - t0) + (t2 - t1) * N_PART / nq + (t3 - t2) * W.gface.shape[0] / ng
             + (t4 - t3) * N_CD / ncd)
     return full, t4 - t0
 
 
-def cpu_baseline(W, budget_s=20.0):
+def cpu_baseline(W):
+    """The oracle as it stands on this host: every core (the brute-force parts over
+    OpenMP threads; the serial LBVH build on one), and one thread, each on a bounded
+    sample of one frame extrapolated to the whole frame."""
+    import oracle
+    model, ncpu = host_cpu()
+    nthr = oracle.num_threads()
     rng = np.random.default_rng(7)
-    nq = 4096
-    full, spent = oracle_frame_sample(W, 1, nq, 60000, 256, rng)
-    return {"value": W.queries_per_frame / full, "unit": "queries/s", "cores": 1, "kind": "oracle",
-            "sample": f"one frame: full serial LBVH build of 200k faces, {nq} of 1M contact "
-                      f"queries (brute force), 60000 of 600k Gaussians, 256 of 10k Chamfer "
-                      f"samples per side; extrapolated linearly to the full frame "
-                      f"({spent:.1f} s of CPU work, single thread)"}
+    nq1 = 2048
+    full1, spent1 = oracle_frame_sample(W, 1, nq1, 30000, 128, rng)
+    nqa = 2048 * max(1, min(nthr, 16))
+    fulla, spenta = oracle_frame_sample(W, 1, nqa, 30000 * max(1, min(nthr, 16)), 1024, rng, parallel=True)
+    q = W.queries_per_frame
+    return {"value": q / fulla, "unit": "queries/s", "cores": nthr, "kind": "oracle",
+            "sample": f"one frame on {nthr} threads: full serial LBVH build of 200k faces, {nqa} of "
+                      f"1M contact queries (brute force, OpenMP over queries), "
+                      f"{30000 * max(1, min(nthr, 16))} of 600k Gaussians, 1024 of 10k Chamfer "
+                      f"samples per side; extrapolated linearly to the full frame ({spenta:.1f} s "
+                      f"of wall time)",
+            "single_thread": {"value": q / full1, "cores": 1,
+                              "sample": f"{nq1} contact queries, 30000 Gaussians, 128 Chamfer samples "
+                                        f"per side, serial LBVH build; extrapolated ({spent1:.1f} s)"},
+            "host": {"cpu_model": model, "nproc": ncpu}}
 
 
 def reference_arm(args, rank, world):
+    """The oracle, as it stands, on this host's cores (its brute-force parts over OpenMP
+    threads, the LBVH build serial), each step one bounded sample of the physics frame
+    extrapolated linearly to the whole frame (a full frame is ~2e11 point-triangle tests)."""
     if rank != 0:
         return
     import oracle
     oracle.build()
     W = Workload(4)
+    nthr = oracle.num_threads()
+    model, ncpu = host_cpu()
     total = args.steps + args.warmup
     budget = 150.0 / max(total, 1)                     # seconds per step, whole run ~ minutes
-    nq = int(max(16, min(4096, (budget - 0.35) * 250)))
+    nq = int(max(16, min(4096 * max(1, min(nthr, 16)), (budget - 0.35) * 250 * max(1, min(nthr, 16)))))
     rng = np.random.default_rng(11)
     for _ in range(args.warmup):
-        oracle_frame_sample(W, 0, nq, 4096, 16, rng)
+        oracle_frame_sample(W, 0, nq, 4096, 16, rng, parallel=True)
     fulls = []
     t0 = time.perf_counter()
     for k in range(args.steps):
-        full, _ = oracle_frame_sample(W, k, nq, 4096, 16, rng)
+        full, _ = oracle_frame_sample(W, k, nq, 4096, 16, rng, parallel=True)
         fulls.append(full)
     spent = time.perf_counter() - t0
     val = W.queries_per_frame / float(np.mean(fulls))
@@ -565,11 +617,15 @@ def reference_arm(args, rank, world):
             "data": "synthetic", "impl": "reference",
             "config": {"workload": WORKLOAD, "queries_per_frame": W.queries_per_frame,
                        "faces": NU * NV_ * 2, "gaussians": NU * NV_ * 2 * G_PER_FACE,
-                       "parallelism": "host, one thread", "frames": args.steps},
-            "cpu_baseline": {"value": val, "unit": "queries/s", "cores": 1, "kind": "oracle",
+                       "parallelism": f"host, {nthr} threads", "frames": args.steps},
+            "timing": "ms_per_step is the full frame extrapolated from each step's sample; "
+                      f"the {args.steps} sampled steps took {spent:.1f} s of wall time",
+            "cpu_baseline": {"value": val, "unit": "queries/s", "cores": nthr, "kind": "oracle",
                              "sample": f"per step: full serial LBVH build, {nq} contact queries, "
-                                       f"4096 Gaussians, 16 Chamfer samples per side, "
-                                       f"extrapolated to the full frame ({spent:.1f} s total)"},
+                                       f"4096 Gaussians, 16 Chamfer samples per side (brute force "
+                                       f"over {nthr} threads), extrapolated to the full frame "
+                                       f"({spent:.1f} s total)",
+                             "host": {"cpu_model": model, "nproc": ncpu}},
             "e2e": {"value": val, "unit": "queries/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -616,11 +672,70 @@ def _capture(fn):
     return g
 
 
-def bench_batch(args):
+def bench_contact(args):
+    """The contact kernel and the refit alone, for profiling and the roofline counters:
+    the physics frame's agglomerative tree built once from the rest pose and refit to
+    one skinned pose (frame 30), 1M Morton-ordered particles, cutoff 0.05.  Each step
+    (L2 flushed first) is one refit and one plain contact query (no warm start, the
+    launch the roofline is computed for) in the given traversal variant (--variant;
+    -1 = the autotuner's choice).  The traversal counters run before the steps, so a
+    profiler can take the k-th contact launch as the k-th step's."""
+    import torch
+    from paper_2606_00444_gb300 import MeshBVH, l2_read_bandwidth, morton_order
+    dev = torch.device("cuda")
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    V0, F = torus(NU, NV_)
+    sk = TorusSkinning(V0, seed=SEED)
+    lo, hi = V0.min(0) - 0.2, V0.max(0) + 0.2
+    P = t(uniform_box(N_PART, lo, hi, seed=SEED + 2))
+    P = P[morton_order(P).long()].contiguous()
+    fixed = MeshBVH(V0.shape[0], F.shape[0], dev).build(t(V0), t(F), method="ploc")
+    V1 = t(sk.frame(30))
+    fixed.refit(V1)
+    if args.variant >= 0:
+        fixed.set_query_config(1, args.variant)
+        tuned = {"lanes": 1, "variant": args.variant}
+    else:
+        from paper_2606_00444_gb300.tune import tune_closest_point
+        tuned = tune_closest_point(fixed, P, CUTOFF)
+    stats = fixed.closest_point_stats(P, CUTOFF)
+    out = dict(face=torch.empty(N_PART, dtype=torch.int32, device=dev),
+               bary=torch.empty(N_PART, 3, device=dev), point=torch.empty(N_PART, 3, device=dev),
+               dist2=torch.empty(N_PART, device=dev))
+    flush = torch.empty(128 << 20, dtype=torch.float32, device=dev)
+    tc, tr = [], []
+    for k in range(args.warmup + args.steps):
+        flush.fill_(float(k))
+        e = _events(3)
+        e[0].record()
+        fixed.refit(V1)
+        e[1].record()
+        fixed.closest_point(P, CUTOFF, out=out)
+        e[2].record()
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            tr.append(e[0].elapsed_time(e[1]))
+            tc.append(e[1].elapsed_time(e[2]))
+    l2 = l2_read_bandwidth()
+    vis, tst = stats["visits"] / N_PART, stats["tests"] / N_PART
+    bpq = CONTACT_BYTES + NODE_BYTES * vis + TRI_BYTES * tst
+    line = {"metric": "contact kernel and refit alone", "workload": "contact", "steps": args.steps,
+            "warmup": args.warmup, "tuned": tuned,
+            "contact_ms": {"median": float(np.median(tc)), "mean": float(np.mean(tc)),
+                           "min": float(np.min(tc)), "max": float(np.max(tc))},
+            "refit_ms": {"median": float(np.median(tr)), "mean": float(np.mean(tr))},
+            "per_query": {"node_visits": vis, "triangle_tests": tst, "algorithmic_bytes": bpq},
+            "hits": stats["hits"], "l2_read_gbs": l2}
+    print(json.dumps(line))
+
+
+def batch_measure(steps, warmup):
     """64 scenes (log-uniform 1k-200k faces): per frame every scene is rebuilt, queried
     (4 x its vertex count, uniform in its box grown by 10%) and its Gaussians (one per
     face at the centroid) updated.  Batched: one launch per phase for all scenes.
-    Plain: the same calls per scene, 64 times.  Both captured as one CUDA graph."""
+    Per scene: the same calls 64 times.  Both captured as one CUDA graph; the batched
+    outputs are checked equal, bit for bit, to the per-scene ones (the same accuracy).
+    Also times the batched refit of all scenes' trees (2.9M faces)."""
     import torch
     from paper_2606_00444_gb300 import MeshBatch, MeshBVH, launch_count, set_query_group
     from workloads.meshes import batch_scenes
@@ -689,26 +804,47 @@ def bench_batch(args):
         n0 = launch_count(); batched(); torch.cuda.synchronize(); lb = launch_count() - n0
         n0 = launch_count(); plain(); torch.cuda.synchronize(); lp = launch_count() - n0
         gb, gp, gpu_ = _capture(batched), _capture(plain), _capture(plain_unsorted)
-        ms_b = _time_graph(gb, args.steps, args.warmup, flush)
-        ms_p = _time_graph(gp, args.steps, args.warmup, flush)
-        ms_pu = _time_graph(gpu_, args.steps, args.warmup, flush)
+        ms_b = _time_graph(gb, steps, warmup, flush)
+        ms_p = _time_graph(gp, steps, warmup, flush)
+        ms_pu = _time_graph(gpu_, steps, warmup, flush)
         st, en = _events(5), _events(5)
         for k in range(5):
             flush.fill_(1.0); st[k].record(); plain(); en[k].record()
         torch.cuda.synchronize()
         ms_e = float(np.mean([a.elapsed_time(b) for a, b in zip(st, en)]))
+        # the same accuracy: batched and per-scene outputs of the last replays, bit for bit
+        gb.replay()
+        gp.replay()
+        torch.cuda.synchronize()
+        same = all(torch.equal(out[k], torch.cat([o[k] for o in outs])) for k in out) and \
+            all(torch.equal(gout[i], torch.cat([g[i] for g in gos])) for i in range(3))
+        if not same:
+            raise RuntimeError("batched outputs differ from the per-scene outputs")
+        # batched refit of every scene's tree from the same vertices
+        gr = _capture(lambda: batch.refit(V))
+        ms_r = _time_graph(gr, steps, warmup, flush)
     finally:
         set_query_group(0)
-    line = {"metric": METRIC, "value": nQ / (ms_b * 1e-3), "unit": "queries/s", "n_gpus": 1,
+    return {"faces": int(F.shape[0]), "queries": int(nQ), "scenes": 64,
+            "ms_per_frame": {"batched_graph": ms_b, "per_scene_graph": ms_p,
+                             "per_scene_graph_sampling_order": ms_pu, "per_scene_eager": ms_e},
+            "launches_per_frame": {"batched": lb, "per_scene": lp},
+            "outputs_equal_per_scene": same,
+            "batched_refit_ms": ms_r,
+            "batched_refit_frac_hbm": REFIT_BYTES * int(F.shape[0]) / (ms_r * 1e-3) / 1e9 / peaks()[0]}
+
+
+def bench_batch(args):
+    r = batch_measure(args.steps, args.warmup)
+    ms_b = r["ms_per_frame"]["batched_graph"]
+    line = {"metric": METRIC, "value": r["queries"] / (ms_b * 1e-3), "unit": "queries/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_b,
             "higher_is_better": True, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "64 scenes, faces log-uniform 1k-200k (tori / icospheres, "
                                    "sinusoidal displacement), queries 4 x vertices per scene; per "
                                    "frame: LBVH build + closest point + one Gaussian per face",
-                       "faces": int(F.shape[0]), "queries": int(nQ)},
-            "ms_per_frame": {"batched_graph": ms_b, "per_scene_graph": ms_p,
-                             "per_scene_graph_sampling_order": ms_pu, "per_scene_eager": ms_e},
-            "launches_per_frame": {"batched": lb, "per_scene": lp}}
+                       "faces": r["faces"], "queries": r["queries"]}}
+    line.update({k: v for k, v in r.items() if k not in ("faces", "queries")})
     print(json.dumps(line))
 
 
@@ -854,13 +990,15 @@ def bench_tracking(args):
     print(json.dumps(line))
 
 
-def bench_fit(args):
+def fit_measure(n_steps):
     """Differentiable template fit: icosphere 40962 V / 81920 F fitted to the extracted
     target at tau = pi (frame 60) by Adam (lr 1e-3) on symmetric Chamfer over 1M samples
     per side plus the mean squared point-to-mesh distance of the template vertices;
-    every forward and backward step runs in the library's kernels."""
+    every forward and backward step runs in the library's kernels.  Beside it, the plain
+    form: the same loss evaluated forward only (no autograd, no gradient kernels) on the
+    same template, whose value must equal the differentiable forward's bit for bit."""
     import torch
-    from paper_2606_00444_gb300 import MeshBVH
+    from paper_2606_00444_gb300 import MeshBVH, chamfer, morton_order
     from paper_2606_00444_gb300.autograd import Chamfer, Interpolate, PointMeshDistance
     from workloads.isosurface import BlobSequence
     from workloads.meshes import icosphere
@@ -868,7 +1006,6 @@ def bench_fit(args):
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     VG, FG = BlobSequence(2000).mesh(60)
     VT, FT = icosphere(6, radius=0.9)
-    from paper_2606_00444_gb300 import morton_order
     ns = 1 << 20
     ft, bt = sample_surface(VT, FT, ns, seed=5001)
     SG = t(points_from(VG, FG, *sample_surface(VG, FG, ns, seed=5002)))
@@ -883,14 +1020,22 @@ def bench_fit(args):
     SG = SG[morton_order(SG).long()].contiguous()
     V = t(VT).requires_grad_(True)
     opt = torch.optim.Adam([V], lr=1e-3)
-    n_steps = 300 if args.steps >= 100 else args.steps
+
+    def loss_of(Vx, grad):
+        if grad:
+            ST = Interpolate.apply(Vx, tmpl, ft, bt)
+            cd = Chamfer.apply(ST, Vx, tmpl, SG, VGd, targ)
+            d2v, _ = PointMeshDistance.apply(Vx, VGd, targ)
+            return cd[0] + cd[1] + d2v.mean()
+        tmpl.refit(Vx)                                   # the plain per-frame form
+        ST = tmpl.interpolate(ft, bt)
+        cd = chamfer(tmpl, ST, targ, SG)
+        d2v = targ.closest_point(Vx, want=("dist2",))["dist2"]
+        return cd[0] + cd[1] + d2v.mean()
 
     def step():
         opt.zero_grad(set_to_none=True)
-        ST = Interpolate.apply(V, tmpl, ft, bt)
-        cd = Chamfer.apply(ST, V, tmpl, SG, VGd, targ)
-        d2v, _ = PointMeshDistance.apply(V, VGd, targ)
-        loss = cd[0] + cd[1] + d2v.mean()
+        loss = loss_of(V, True)
         loss.backward()
         opt.step()
         return loss
@@ -908,14 +1053,64 @@ def bench_fit(args):
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     ms = float(np.mean([a.elapsed_time(b) for a, b in zip(st, en)]))
-    line = {"metric": METRIC, "value": (2 * ns + len(VT)) / (ms * 1e-3), "unit": "queries/s",
-            "n_gpus": 1, "steps": n_steps, "warmup": 1, "ms_per_step": ms,
-            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+    # the plain forward on the current template, against the differentiable forward
+    with torch.no_grad():
+        Vc = V.detach().clone()
+    fwd = []
+    for k in range(max(3, min(n_steps, 20)) + 2):
+        a, b = _events(2)
+        a.record()
+        lp = loss_of(Vc, False)
+        b.record()
+        torch.cuda.synchronize()
+        if k >= 2:
+            fwd.append(a.elapsed_time(b))
+    ld = loss_of(Vc.clone().requires_grad_(True), True)
+    torch.cuda.synchronize()
+    if not torch.equal(lp.detach(), ld.detach()):
+        raise RuntimeError(f"plain forward loss {lp.item()!r} differs from the differentiable "
+                           f"forward's {ld.item()!r}")
+    return {"steps": n_steps, "ms_per_adam_step": ms, "ms_plain_forward": float(np.mean(fwd)),
+            "loss_first": l0, "loss_last": float(losses[-1].item()),
+            "forward_loss_equal_plain": True, "samples_per_side": ns,
+            "template": [int(len(VT)), int(len(FT))], "target_faces": int(len(FG))}
+
+
+def bench_fit(args):
+    n_steps = 300 if args.steps >= 100 else args.steps
+    r = fit_measure(n_steps)
+    line = {"metric": METRIC, "value": (2 * r["samples_per_side"] + r["template"][0]) / (r["ms_per_adam_step"] * 1e-3),
+            "unit": "queries/s", "n_gpus": 1, "steps": n_steps, "warmup": 1,
+            "ms_per_step": r["ms_per_adam_step"], "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic",
             "config": {"workload": "template fit: icosphere 40962 V to the extracted target at "
                                    "tau = pi, Chamfer 1M + 1M samples + vertex point-to-mesh, Adam "
-                                   "lr 1e-3", "target_faces": int(len(FG))},
-            "loss_first": l0, "loss_last": float(losses[-1].item())}
+                                   "lr 1e-3", "target_faces": r["target_faces"]}}
+    line.update(r)
     print(json.dumps(line))
+
+
+def refit_large_measure(steps, warmup):
+    """Refit of a 2.4M-face torus (1200 x 1000 grid) to a skinned pose, vertex update
+    included, as the 200k-face frame's refit (graph replay, L2 flushed): where the
+    refit's bytes, not its latency, set its time."""
+    import torch
+    from paper_2606_00444_gb300 import MeshBVH
+    dev = torch.device("cuda")
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    V0, F = torus(1200, 1000)
+    sk = TorusSkinning(V0, seed=SEED)
+    b = MeshBVH(V0.shape[0], F.shape[0], dev).build(t(V0), t(F), method="ploc")
+    Vs = [t(sk.frame(k)) for k in (10, 40)]
+    Vin = torch.empty_like(Vs[0])
+    flush = torch.empty(128 << 20, dtype=torch.float32, device=dev)
+    g = _capture(lambda: b.refit(Vin))
+    ms = _time_graph(g, steps, warmup, flush, pre=lambda k: Vin.copy_(Vs[k % 2]))
+    copy = _time_graph(_capture(lambda: None), steps, warmup, flush, pre=lambda k: Vin.copy_(Vs[k % 2]))
+    ms = max(ms - copy, 1e-6)                        # the frame load is not the refit's
+    nF = int(F.shape[0])
+    return {"faces": nF, "ms": ms, "algorithmic_bytes": REFIT_BYTES * nF,
+            "frac_hbm": REFIT_BYTES * nF / (ms * 1e-3) / 1e9 / peaks()[0]}
 
 
 def main():
@@ -927,7 +1122,7 @@ def main():
         return reference_arm(args, rank, world)
     if args.workload != "physics":
         return {"batch": bench_batch, "sequence": bench_sequence, "fit": bench_fit,
-                "tracking": bench_tracking}[args.workload](args)
+                "tracking": bench_tracking, "contact": bench_contact}[args.workload](args)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
@@ -937,16 +1132,46 @@ def main():
     q = W.queries_per_frame
     ms = res["ms"]
     hbm, src = peaks()
-    # the traversal counters are those of the search without a warm start, so the
-    # roofline pairs them with that launch's time
+    l2 = res["l2_read_gbs"]
+    # The roofline of the dominant kernel, the contact query.  Its tree (40 MB) and
+    # particles stay in L2, so its bytes are bounded by L2, not HBM, bandwidth: the
+    # headline fraction is its algorithmic bytes (44 B of query I/O, 64 B per node
+    # visit = both children's 32-byte boxes, 48 B per triangle test, counted by the
+    # counting form of the same traversal) over the L2 read bandwidth measured in
+    # this run.  Beside it, from the committed ncu capture of the same launch: DRAM
+    # bytes over the measured HBM peak, L2 bytes over the L2 peak, and the FP32 pipe.
+    # The counters are those of the search without a warm start, so the roofline
+    # pairs them with that launch's time.
     t_contact = res["stages"]["contact_without_warm_start"] * 1e-3
     vis = res["stats"]["visits"] / N_PART
     tst = res["stats"]["tests"] / N_PART
     per_query = CONTACT_BYTES + NODE_BYTES * vis + TRI_BYTES * tst
     achieved = per_query * N_PART / t_contact / 1e9
-    achieved_io = CONTACT_BYTES * N_PART / t_contact / 1e9
+    rec = contact_traffic(res["tuned"]["variant"]) if res["tuned"]["lanes"] == 1 else None
+    rec = rec or {}
+    dram, lts = rec.get("dram_bytes"), rec.get("lts_bytes")
+    roof = {"kernel": f"k_closest_point, variant {res['tuned']['variant']} (contact, 1M queries, "
+                      f"no warm start)",
+            "bound": "l2", "achieved": achieved, "peak": l2, "unit": "GB/s", "frac": achieved / l2,
+            "peak_source": "measured in this run: k_l2_read (mesh_probe_l2_read) over a 48 MB "
+                           "L2-resident buffer, best of 20",
+            "traffic": dram,
+            "bytes_per_query": per_query,
+            "per_query": {"io": CONTACT_BYTES, "node_visits": vis, "triangle_tests": tst,
+                          "node_bytes": NODE_BYTES, "triangle_bytes": TRI_BYTES},
+            "algorithmic_over_hbm_peak": achieved / hbm,
+            "hbm": {"bytes_per_launch": dram, "achieved": dram / t_contact / 1e9 if dram else None,
+                    "peak": hbm, "peak_source": src,
+                    "frac": dram / t_contact / 1e9 / hbm if dram else None},
+            "l2": {"bytes_per_launch": lts, "achieved": lts / t_contact / 1e9 if lts else None,
+                   "peak": l2, "frac": lts / t_contact / 1e9 / l2 if lts else None},
+            "sm": {k: rec[k] for k in ("fma_pipe_pct", "alu_pipe_pct", "issue_active_pct",
+                                       "lanes_per_inst", "warps_active_pct") if k in rec},
+            "counters_source": "profiles/roofline_traffic.json (ncu, same launch; null when the "
+                               "kernel source changed since)"}
     st = dict(res["stages"])
     un = st.pop("contact_unsorted_particles")
+    refit_frac = REFIT_BYTES * NU * NV_ * 2 / (st["refit"] * 1e-3) / 1e9 / hbm
     line = {
         "metric": METRIC,
         "value": replicas_value(q, world, ms),
@@ -964,19 +1189,17 @@ def main():
                    "gaussians": NU * NV_ * 2 * G_PER_FACE, "parallelism": f"replicas{world}",
                    "l2": "flushed between frames (512 MB write, outside the timed events)",
                    "graph": "one CUDA graph per frame"},
+        "step_ms_stats": {"mean": float(np.mean(res["step_ms"])), "median": float(np.median(res["step_ms"])),
+                          "min": float(np.min(res["step_ms"])), "max": float(np.max(res["step_ms"]))},
         "stages_ms": st,
         "ms_per_frame": {"refit_path": st["refit"] + st["contact"] + st["rebind"],
                          "rebuild_path": st["rebuild"] + st["contact_on_rebuilt_lbvh"] + st["rebind"],
                          "refit": st["refit"], "rebuild": st["rebuild"]},
+        "refit_roofline": {"faces": NU * NV_ * 2, "ms": st["refit"], "bytes_per_face": REFIT_BYTES,
+                           "frac_hbm": refit_frac},
         "fixed_topology_tree": {"build": "agglomerative (mesh_build_ploc), once from the rest pose",
                                 "build_ms_once": res["ploc_build_ms"]},
-        "roofline": {"kernel": "k_closest_point (contact, 1M queries, no warm start)", "bound": "hbm",
-                     "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "peak_source": src, "traffic": (contact_traffic(res["tuned"]["variant"]) or {}).get("dram_bytes") if res["tuned"]["lanes"] == 1 else None,
-                     "bytes_per_query": per_query,
-                     "per_query": {"io": CONTACT_BYTES, "node_visits": vis, "triangle_tests": tst,
-                                   "node_bytes": NODE_BYTES, "triangle_bytes": TRI_BYTES},
-                     "frac_io_only": achieved_io / hbm},
+        "roofline": roof,
         "clocks": res["clocks"],
         "e2e": {"value": world * q / (res["e2e_ms"] * 1e-3), "unit": "queries/s",
                 "h2d_bytes_per_step": res["h2d"], "d2h_bytes_per_step": res["d2h"]},
@@ -985,6 +1208,17 @@ def main():
         "contact_ms_unsorted_particles": un,
         "tuned_contact": {k: res["tuned"][k] for k in ("lanes", "variant", "tried")},
     }
+    if not args.no_extras and world == 1:
+        # the other configurations: batched vs per-scene launches (same outputs, 5
+        # frames), the template fit's 300 Adam steps vs the plain forward (same loss),
+        # and the refit of a 2.4M-face mesh
+        import torch
+        torch.cuda.empty_cache()
+        line["batched_64_scenes"] = batch_measure(5, 3)
+        torch.cuda.empty_cache()
+        line["template_fit"] = fit_measure(300)
+        torch.cuda.empty_cache()
+        line["refit_2_4M_faces"] = refit_large_measure(10, 3)
     if not args.no_cpu_baseline and world == 1:
         import oracle
         oracle.build()

@@ -419,15 +419,21 @@ mesh_status mesh_chamfer_hinted(const mesh_bvh *A, const float *d_SA, int64_t nS
  * callers cannot call cudaMalloc -- a physics or renderer plugin whose host
  * application owns every device allocation, or code running while another
  * framework captures the stream into a CUDA graph and forbids allocation --
- * so they cannot supply mesh_chamfer's workspace.  This variant computes the
- * same result with the same kernel, keeping its scratch in one fixed array
- * inside the library (128 KB of device memory, held by every GPU that loads
- * the library until the process exits) and allocates nothing.
- *   - Limit: ceil(nSA/128) + ceil(nSB/128) <= 16384 (about 2M samples in
- *     total); larger inputs return MESH_ERR_WORKSPACE and launch nothing.
+ * so they cannot supply mesh_chamfer's workspace.  This variant runs
+ * mesh_chamfer's kernel, keeping its scratch in one fixed array inside the
+ * library (128 KB of device memory, held by every GPU that loads the library
+ * until the process exits) and allocates nothing.  It uses the lanes per
+ * sample mesh_chamfer would use, or fewer when those blocks exceed the array:
+ * the per-sample results are mesh_chamfer's bit for bit, and so are the two
+ * means when the lanes agree (otherwise they differ only in the float64
+ * summation order).
+ *   - Limit: ceil(nSA/128) + ceil(nSB/128) <= 16384 blocks with one lane per
+ *     sample (about 2M samples in total); larger inputs return
+ *     MESH_ERR_WORKSPACE and launch nothing.
  *   - The first call on each device looks up that device's address of the
  *     array (cudaGetSymbolAddress, with that device current); make that first
- *     call before any stream capture.
+ *     call before any stream capture.  The address is kept for the process's
+ *     life: after a cudaDeviceReset the call must not be used again.
  *   - All calls share the array: calls that may overlap on the GPU (different
  *     streams, or concurrent threads) race and give wrong results; serialise
  *     them.  Each call clears the part that must start at zero itself.
@@ -561,6 +567,17 @@ mesh_status mesh_batch_status(mesh_batch *batch, uint32_t *bits, uint32_t *n_deg
 mesh_status mesh_bvh_status(mesh_bvh *bvh, uint32_t *bits, uint32_t *n_degenerate, void *stream);
 
 const char *mesh_status_string(mesh_status s);
+
+/* L2 read-bandwidth probe (the roofline denominator of the traversal kernels,
+ * whose trees stay resident in L2): reads the first `bytes` of d_buf (16-byte
+ * aligned, a multiple of 16; choose a size well inside L2, e.g. 48 MB) `passes`
+ * times with L2-only loads from a grid of four 256-thread blocks per SM, and
+ * writes one word per thread to d_sink (mesh_probe_sink_bytes() bytes).  Time
+ * it with CUDA events after one warm-up call: bytes x passes / time is the
+ * sustained L2 read bandwidth.  Not part of the method; a measurement aid. */
+size_t mesh_probe_sink_bytes(void);
+mesh_status mesh_probe_l2_read(const void *d_buf, size_t bytes, int passes, void *d_sink,
+                               size_t sink_bytes, void *stream);
 
 /* Number of kernels this library has launched in the process so far. */
 uint64_t mesh_launch_count(void);

@@ -98,6 +98,8 @@ SIGNATURES = {
     "mesh_bvh_status": (C.c_int, [VP, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), VP]),
     "mesh_status_string": (C.c_char_p, [C.c_int]),
     "mesh_launch_count": (C.c_uint64, []),
+    "mesh_probe_sink_bytes": (SZ, []),
+    "mesh_probe_l2_read": (C.c_int, [VP, SZ, C.c_int, VP, SZ, VP]),
 }
 
 

@@ -530,6 +530,30 @@ def chamfer(A: MeshBVH, SA: torch.Tensor, B: MeshBVH, SB: torch.Tensor, per_samp
     return (out, ps) if per_sample else out
 
 
+def l2_read_bandwidth(nbytes: int = 48 << 20, passes: int = 8, repeats: int = 20) -> float:
+    """Sustained L2 read bandwidth of the current GPU in GB/s (mesh_probe_l2_read over an
+    L2-resident buffer, CUDA events, best of `repeats` after a warm-up)."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    buf = torch.zeros(nbytes, dtype=torch.uint8, device=dev)
+    sink = torch.empty(int(lib().mesh_probe_sink_bytes()), dtype=torch.uint8, device=dev)
+
+    def run():
+        check(lib().mesh_probe_l2_read(buf.data_ptr(), nbytes, passes, sink.data_ptr(), sink.numel(),
+                                       _stream()), "mesh_probe_l2_read")
+
+    run()
+    torch.cuda.synchronize()
+    best = math.inf
+    for _ in range(repeats):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        run()
+        b.record()
+        b.synchronize()
+        best = min(best, a.elapsed_time(b) * 1e-3)
+    return nbytes * passes / best / 1e9
+
+
 def chamfer_backward(A: MeshBVH, SA: torch.Tensor, B: MeshBVH, SB: torch.Tensor, g: torch.Tensor,
                      ps: dict, gSA=None, gVA=None, gSB=None, gVB=None) -> None:
     """Reverse mode of chamfer() (mesh_chamfer_backward), both directions in one launch:

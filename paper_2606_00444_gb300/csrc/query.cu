@@ -1672,9 +1672,13 @@ mesh_status mesh_interpolate(const mesh_bvh *bvh, const int32_t *d_face, const f
 // plugin whose host application owns every device allocation, or code that
 // runs while another framework is capturing the stream into a CUDA graph and
 // forbids allocation -- so they cannot hand mesh_chamfer a workspace.  This
-// entry point runs the same Chamfer kernel with its scratch (per-block float64
-// partial sums and the last-block ticket) in a fixed file-scope device array
-// instead.  Every GPU that loads the library holds that array until exit.
+// entry point runs the same Chamfer kernel, with the lanes per sample
+// mesh_chamfer would pick (fewer when that many blocks would not fit), with its
+// scratch (per-block float64 partial sums and the last-block ticket) in a fixed
+// file-scope device array instead.  Every GPU that loads the library holds that
+// array until exit.  The array's device address is looked up once per device
+// and kept; a cudaDeviceReset invalidates it, so no call may follow a reset in
+// the same process.
 // ---------------------------------------------------------------------------
 namespace meshgs {
 
@@ -1710,7 +1714,10 @@ extern "C" mesh_status mesh_chamfer_noalloc(const mesh_bvh *A, const float *d_SA
     using namespace meshgs;
     if (!A || !B || !d_out || nSA < 0 || nSB < 0 || (nSA > 0 && !d_SA) || (nSB > 0 && !d_SB))
         return MESH_ERR_INVALID_ARG;
-    size_t nbA = chamfer_blocks(nSA), nbB = chamfer_blocks(nSB);
+    // the lanes per sample mesh_chamfer would use, fewer if its blocks exceed the array
+    int G = pick_group(nSA + nSB);
+    while (G > 1 && chamfer_blocks(nSA, G) + chamfer_blocks(nSB, G) > (size_t)kNoAllocMaxBlocks) G >>= 1;
+    size_t nbA = chamfer_blocks(nSA, G), nbB = chamfer_blocks(nSB, G);
     if (nbA + nbB > (size_t)kNoAllocMaxBlocks) return MESH_ERR_WORKSPACE;
     double *scratch = nullptr;
     mesh_status st = scratch_address(&scratch);
@@ -1724,9 +1731,16 @@ extern "C" mesh_status mesh_chamfer_noalloc(const mesh_bvh *A, const float *d_SA
     cudaMemsetAsync(ticket, 0, sizeof(unsigned int), s);
     ChamferSide a2b{traversal_of(B), B->hdr(), d_SA, nSA, d_faceA, d_baryA, d_dist2A};
     ChamferSide b2a{traversal_of(A), A->hdr(), d_SB, nSB, d_faceB, d_baryB, d_dist2B};
-    k_chamfer<1><<<(unsigned)(nbA + nbB), kQueryBlock, 0, s>>>(a2b, b2a, (unsigned)nbA,
-                                                               &A->hdr()->status, scratch, ticket,
-                                                               d_out);
+    unsigned grid = (unsigned)(nbA + nbB), nb = (unsigned)nbA;
+    unsigned *st_ = &A->hdr()->status;
+    switch (G) {
+        case 1: k_chamfer<1><<<grid, kQueryBlock, 0, s>>>(a2b, b2a, nb, st_, scratch, ticket, d_out); break;
+        case 2: k_chamfer<2><<<grid, kQueryBlock, 0, s>>>(a2b, b2a, nb, st_, scratch, ticket, d_out); break;
+        case 4: k_chamfer<4><<<grid, kQueryBlock, 0, s>>>(a2b, b2a, nb, st_, scratch, ticket, d_out); break;
+        case 8: k_chamfer<8><<<grid, kQueryBlock, 0, s>>>(a2b, b2a, nb, st_, scratch, ticket, d_out); break;
+        case 16: k_chamfer<16><<<grid, kQueryBlock, 0, s>>>(a2b, b2a, nb, st_, scratch, ticket, d_out); break;
+        default: k_chamfer<32><<<grid, kQueryBlock, 0, s>>>(a2b, b2a, nb, st_, scratch, ticket, d_out); break;
+    }
     count_launch();
     return check_launch();
 }

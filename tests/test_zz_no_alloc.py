@@ -10,13 +10,12 @@ already run).  It passes alone in a fresh process and after the rest of the suit
 """
 import ctypes as C
 
-import numpy as np
 import pytest
 import torch
 
 from paper_2606_00444_gb300 import MeshBVH
 from paper_2606_00444_gb300._abi import lib
-from parity import dev, host
+from parity import dev
 from workloads.meshes import displaced_icosphere, icosphere
 from workloads.sampling import points_from, sample_surface
 
@@ -65,11 +64,11 @@ def test_noalloc_chamfer_matches_workspace_chamfer_twice():
         ps = _outputs(SA.shape[0], SB.shape[0])
         assert _call_noalloc(A, SA, B, SB, out, ps) == 0
         torch.cuda.synchronize()
-        np.testing.assert_allclose(host(out), host(ref), rtol=1e-5)
-        for k in ("faceA", "faceB"):
-            assert torch.equal(ps[k], ref_ps[k])
-        for k in ("dist2A", "dist2B", "baryA", "baryB"):
-            np.testing.assert_allclose(host(ps[k]), host(ref_ps[k]), rtol=1e-5, atol=1e-7)
+        # the same kernel instantiation (the same lanes per sample) as mesh_chamfer here,
+        # and the tie rule does not depend on the traversal: every output is identical
+        assert torch.equal(out, ref)
+        for k in ps:
+            assert torch.equal(ps[k], ref_ps[k]), k
 
 
 def test_noalloc_chamfer_refuses_inputs_beyond_its_limit():

@@ -62,6 +62,8 @@ def lib():
         L.orc_karras.argtypes = [U32P, I64, I32P, I32P, I32P, I32P, I32P]
         L.orc_ploc.restype = None
         L.orc_ploc.argtypes = [F32P, I64, C.c_int, I32P, I32P, I32P, I32P, I32P, I32P]
+        L.orc_collapse.restype = None
+        L.orc_collapse.argtypes = [I32P, I32P, I32P, I32P, I64, C.c_int, I32P]
         L.orc_node_boxes.restype = None
         L.orc_node_boxes.argtypes = [F32P, I32P, I32P, I64, I32P, I32P, F32P]
         L.orc_bind_gaussians.restype = C.c_int64
@@ -223,6 +225,19 @@ def build_ploc(V, F, radius=16):
     boxes = node_boxes(V, F, perm, first, last)
     return dict(keys=keys, leaf_keys=sk[order], perm=perm, left=left, right=right, parent=parent,
                 first=first, last=last, boxes=boxes)
+
+
+def collapse(left, right, first, last, leaf_size):
+    """Child links of every internal node with leaf collapse at leaf_size (orc_collapse):
+    [n-1, 4] int32 = (left link, left count, right link, right count); a leaf range is
+    (-(first + 1), faces), an internal child (c, c)."""
+    left = np.ascontiguousarray(left, dtype=np.int32)
+    m = left.shape[0]
+    link = np.zeros((max(m, 1), 4), np.int32)
+    lib().orc_collapse(left, np.ascontiguousarray(right, dtype=np.int32),
+                       np.ascontiguousarray(first, dtype=np.int32),
+                       np.ascontiguousarray(last, dtype=np.int32), m + 1, int(leaf_size), link)
+    return link[:m]
 
 
 def node_boxes(V, F, perm, first, last):

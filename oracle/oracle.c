@@ -500,6 +500,32 @@ void orc_ploc(const float *leaf_box, int64_t n, int radius, int32_t *order, int3
 }
 
 /* ------------------------------------------------------------------ */
+/* Leaf collapse with leaf size L (the scope's reading c6: a subtree    */
+/* whose range holds at most L faces becomes one leaf over that range). */
+/* The tree itself is unchanged; every child link of an internal node   */
+/* is rewritten: a leaf j stays (-(j+1), 1); an internal child c whose  */
+/* range [first[c], last[c]] holds at most L faces becomes the range    */
+/* leaf (-(first[c]+1), last[c] - first[c] + 1); any other internal     */
+/* child stays (c, c).  A search from the root then meets each face     */
+/* once, inside the topmost subtree of at most L faces that holds it.   */
+/* link[i][0..1] = left link, count; link[i][2..3] = right link, count. */
+/* ------------------------------------------------------------------ */
+static void collapse_one(int32_t c, const int32_t *first, const int32_t *last, int L, int32_t *out) {
+    if (c < 0) { out[0] = c; out[1] = 1; return; }
+    int32_t len = last[c] - first[c] + 1;
+    if (len <= L) { out[0] = -(first[c] + 1); out[1] = len; }
+    else { out[0] = c; out[1] = c; }
+}
+
+void orc_collapse(const int32_t *left, const int32_t *right, const int32_t *first,
+                  const int32_t *last, int64_t n, int L, int32_t *link) {
+    for (int64_t i = 0; i + 1 < n; ++i) {
+        collapse_one(left[i], first, last, L, link + 4 * i);
+        collapse_one(right[i], first, last, L, link + 4 * i + 2);
+    }
+}
+
+/* ------------------------------------------------------------------ */
 /* Node bounding boxes: for every node, the componentwise min / max of  */
 /* the vertices of all faces in its sorted range, taken directly over   */
 /* the range (not as a union of child boxes).  Exact in float32.        */

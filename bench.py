@@ -68,6 +68,8 @@ def parse():
                          "contact: the contact kernel and the refit alone (profiling)")
     ap.add_argument("--variant", type=int, default=-1,
                     help="contact workload: one-thread traversal variant (-1: the autotuner's)")
+    ap.add_argument("--leaf", type=int, default=1, help="contact workload: leaf size (with --variant)")
+    ap.add_argument("--block", type=int, default=128, help="contact workload: threads per block (with --variant)")
     ap.add_argument("--no-extras", action="store_true",
                     help="physics workload: skip the batched, template-fit and 2.4M-face refit "
                          "measurements that follow the frame")
@@ -187,10 +189,13 @@ def gpu_arm(args, rank, world, local_rank):
     rebuilt = MeshBVH(nV, nF, dev)
     rest = MeshBVH(nV, nF, dev).build(t(W.V0), F, method="ploc")
     # traversal variant for the contact queries, chosen by timing on this workload
-    from paper_2606_00444_gb300.tune import tune_closest_point
+    from paper_2606_00444_gb300.tune import tune_contact
     fixed.refit(t(W.frames[0]))
-    tuned = tune_closest_point(fixed, P, CUTOFF)
-    rebuilt.set_query_config(tuned["lanes"], tuned["variant"])      # same traversal on the LBVH
+    # the contact step itself is tuned (warm start and work order included), stepping
+    # through the first frames of the motion as the simulation does
+    tuned = tune_contact(fixed, P, CUTOFF, frames=[frames[k] for k in range(min(4, frames.shape[0]))])
+    rebuilt.set_query_config(tuned["lanes"], tuned["variant"], tuned["block"])   # same traversal
+    rebuilt.set_leaf_size(tuned["leaf"], refit=False)               # on the LBVH, from its builds
     Vin = torch.empty(nV, 3, device=dev)
     # the contact step's workspace carries each particle's work class to the next frame
     ct_ws = Workspace(dev)
@@ -487,10 +492,16 @@ def gpu_arm(args, rank, world, local_rank):
     return out, W
 
 
-def contact_traffic(variant: int):
-    """Counters per launch of the contact kernel in this traversal variant from the
-    committed ncu capture (dram_bytes, lts_bytes, fma pipe and issue figures), if the
-    kernel source is still the one that was captured (else None)."""
+def traversal_label(cfg: dict) -> str:
+    """Key of a contact-kernel configuration: leaf size, variant, threads per block."""
+    return f"L{cfg.get('leaf', 1)}/v{cfg['variant']}/b{cfg.get('block', 128)}"
+
+
+def contact_traffic(cfg):
+    """Counters per launch of the contact kernel in this configuration (a traversal_label
+    or a tuned dict) from the committed ncu capture (dram_bytes, lts_bytes, fma pipe and
+    issue figures), if the kernel source is still the one that was captured (else None)."""
+    key = cfg if isinstance(cfg, str) else traversal_label(cfg)
     import hashlib
     p = os.path.join(ROOT, "profiles", "roofline_traffic.json")
     if not os.path.exists(p):
@@ -501,7 +512,7 @@ def contact_traffic(variant: int):
         m.update(open(os.path.join(ROOT, f), "rb").read())
     if m.hexdigest()[:16] != d.get("source_hash"):
         return None
-    return d.get("by_variant", {}).get(str(variant))
+    return d.get("by_config", {}).get(key)
 
 
 def peaks():
@@ -693,8 +704,9 @@ def bench_contact(args):
     V1 = t(sk.frame(30))
     fixed.refit(V1)
     if args.variant >= 0:
-        fixed.set_query_config(1, args.variant)
-        tuned = {"lanes": 1, "variant": args.variant}
+        fixed.set_leaf_size(args.leaf)
+        fixed.set_query_config(1, args.variant, args.block)
+        tuned = {"leaf": args.leaf, "lanes": 1, "variant": args.variant, "block": args.block}
     else:
         from paper_2606_00444_gb300.tune import tune_closest_point
         tuned = tune_closest_point(fixed, P, CUTOFF)
@@ -1147,10 +1159,10 @@ def main():
     tst = res["stats"]["tests"] / N_PART
     per_query = CONTACT_BYTES + NODE_BYTES * vis + TRI_BYTES * tst
     achieved = per_query * N_PART / t_contact / 1e9
-    rec = contact_traffic(res["tuned"]["variant"]) if res["tuned"]["lanes"] == 1 else None
+    rec = contact_traffic(res["tuned"]) if res["tuned"]["lanes"] == 1 else None
     rec = rec or {}
     dram, lts = rec.get("dram_bytes"), rec.get("lts_bytes")
-    roof = {"kernel": f"k_closest_point, variant {res['tuned']['variant']} (contact, 1M queries, "
+    roof = {"kernel": f"k_closest_point {traversal_label(res['tuned'])} (contact, 1M queries, "
                       f"no warm start)",
             "bound": "l2", "achieved": achieved, "peak": l2, "unit": "GB/s", "frac": achieved / l2,
             "peak_source": "measured in this run: k_l2_read (mesh_probe_l2_read) over a 48 MB "
@@ -1206,7 +1218,7 @@ def main():
         "gpu_launches": res["launches"],
         "contact_hits_per_frame": res["contact_hits"],
         "contact_ms_unsorted_particles": un,
-        "tuned_contact": {k: res["tuned"][k] for k in ("lanes", "variant", "tried")},
+        "tuned_contact": {k: res["tuned"][k] for k in ("leaf", "lanes", "variant", "block", "tried")},
     }
     if not args.no_extras and world == 1:
         # the other configurations: batched vs per-scene launches (same outputs, 5

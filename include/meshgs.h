@@ -80,9 +80,11 @@ typedef struct {
     size_t off_keys;     /* uint32 [max_faces]   Morton keys in leaf order (sorted for the
                             Karras tree of mesh_build_lbvh)                                    */
     size_t off_perm;     /* int32  [max_faces]   face id of leaf j                             */
-    size_t off_nodes;    /* 4 x float4 per internal node: (lo_L, left) (hi_L, left)
-                                                          (lo_R, right) (hi_R, right),
-                            child index stored as int32 bits in .w                            */
+    size_t off_nodes;    /* 4 x float4 per internal node: (lo_L, left) (hi_L, nL)
+                                                          (lo_R, right) (hi_R, nR),
+                            as int32 bits in .w: the child link (internal c >= 0, or a leaf
+                            range -(first+1)) and n = the range's face count (1 without
+                            leaf collapse), or c again for an internal child            */
     size_t off_parent;   /* int32  [2 max_faces - 1]  2 * parent + side (0 left, 1 right),
                             -1 at the root; internal nodes first, then leaves                 */
     size_t off_tris;     /* 3 x float4 per leaf: (v0, face id bits) (v1, 0) (v2, 0)           */
@@ -218,10 +220,10 @@ mesh_status mesh_closest_point(const mesh_bvh *bvh, const float *d_Q, int64_t nQ
  * nearest face in the previous frame; -1 or out of range = none) is tested
  * before the traversal and its distance bounds the search.  Every face within
  * the final tie window is still reached, so the answer is the one without the
- * hint, bit for bit; the hint changes only the work.  d_hint may be the same array as d_face
- * (each query reads its hint before writing its face).  Used by the
- * depth-first one-thread variants (0, 2-9) and by the cooperative groups
- * (lanes > 1); the other one-thread variants ignore it. */
+ * hint, bit for bit; the hint changes only the work.  d_hint may be the same
+ * array as d_face (each query reads its hint before writing its face).  Used by
+ * the depth-first one-thread variants (0, 2-9), the warp packets (12) and the
+ * cooperative groups (lanes > 1); variants 1, 10 and 11 ignore it. */
 mesh_status mesh_closest_point_hinted(const mesh_bvh *bvh, const float *d_Q, int64_t nQ,
                                       float max_dist, const int32_t *d_hint, int32_t *d_face,
                                       float *d_bary, float *d_point, float *d_dist2, void *stream);
@@ -323,8 +325,10 @@ size_t mesh_contact_workspace_bytes(int64_t nQ);
  * step for the same particles; its contents steer only the order (a fresh
  * or unrelated workspace gives a worse order, never a wrong answer).
  * Answers equal mesh_closest_point's bit for bit.
- * Traversal variants 1, 10-12 and cooperative groups run unordered without
- * classes.  d_ws: mesh_contact_workspace_bytes(nQ), 256-byte aligned. */
+ * Traversal variants 1, 10, 11 and cooperative groups run unordered without
+ * classes (the warp packets of variant 12 take the classes, counting for each
+ * query the nodes whose children it needed).  d_ws:
+ * mesh_contact_workspace_bytes(nQ), 256-byte aligned. */
 mesh_status mesh_contact(const mesh_bvh *bvh, const float *d_Q, int64_t nQ, float max_dist,
                          int32_t *d_face, float *d_bary, float *d_point, float *d_dist2, void *d_ws,
                          size_t ws_bytes, void *stream);
@@ -358,7 +362,8 @@ mesh_status mesh_set_query_group(int lanes);
  *     (10 and 11 keep a work counter in the handle: calls on one handle must
  *     not overlap on the GPU)
  *  12 warp packet: the 32 queries of a warp share one node sequence, a node
- *     entered when any lane needs it (for queries kept in Morton order)
+ *     entered when any lane needs it (for queries kept in Morton order; it
+ *     gains most from leaf collapse, mesh_bvh_set_leaf_size)
  * (the shared part of the stack spills to local memory; local-only leaves the
  * SM's L1 to the node cache).  Process-wide; the same answers, bit for bit,
  * for every variant. */
@@ -370,6 +375,25 @@ mesh_status mesh_set_traversal(int variant);
  * count), variant as mesh_set_traversal; -1 for either = follow the
  * process-wide setting (the default).  Set by the autotuner. */
 mesh_status mesh_bvh_set_query_config(mesh_bvh *bvh, int lanes, int variant);
+
+/* Leaf size L (1..8) of this handle's tree: from the next build or refit on,
+ * every child whose subtree holds at most L faces is linked from its parent as
+ * one leaf over its contiguous range of faces in leaf order (the topmost such
+ * subtree; lo.w = -(first + 1), hi.w = the face count), and a search tests
+ * those faces in one loop instead of visiting the nodes below.  The tree, its
+ * boxes and every other array are those of L = 1 (the nodes below a collapsed
+ * link are still refit, unreachable).  Answers do not depend on L, bit for
+ * bit; the autotuner picks it.  Default 1.  Host-side setting. */
+mesh_status mesh_bvh_set_leaf_size(mesh_bvh *bvh, int leaf_size);
+
+/* Threads per block of this handle's one-thread traversals (mesh_closest_point
+ * and mesh_contact with variants 0, 2 and 3): 128 (default; 0 = default), 64 or
+ * 32.  Each form keeps the same register budget, so the same number of warps
+ * fits an SM; smaller blocks free their slot as soon as their own searches end
+ * (the searches of one block end at very different times).  Host-side setting,
+ * read when a call is made (a captured graph keeps it); set by the autotuner.
+ * The answers do not depend on it. */
+mesh_status mesh_bvh_set_query_block(mesh_bvh *bvh, int threads);
 
 /* Face-bound Gaussians from the handle's current vertex buffer.  For Gaussian
  * g on face f = d_gface[g] with weights b = d_gbary[g] and normal offset

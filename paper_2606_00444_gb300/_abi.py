@@ -75,6 +75,8 @@ SIGNATURES = {
     "mesh_set_query_group": (C.c_int, [C.c_int]),
     "mesh_set_traversal": (C.c_int, [C.c_int]),
     "mesh_bvh_set_query_config": (C.c_int, [VP, C.c_int, C.c_int]),
+    "mesh_bvh_set_query_block": (C.c_int, [VP, C.c_int]),
+    "mesh_bvh_set_leaf_size": (C.c_int, [VP, C.c_int]),
     "mesh_bind_gaussians": (C.c_int, [VP, VP, VP, VP, I64, VP, VP, VP, VP]),
     "mesh_interpolate": (C.c_int, [VP, VP, VP, I64, VP, VP]),
     "mesh_chamfer_workspace_bytes": (SZ, [I64, I64]),

@@ -91,6 +91,7 @@ class MeshBVH:
         self._chamfer_ws = Workspace(self.device)
         self.n_verts = 0
         self.n_faces = 0
+        self.leaf_size = 1
 
     def __del__(self):
         h = getattr(self, "handle", None)
@@ -306,10 +307,21 @@ class MeshBVH:
             _ptr(None if gscale is None else _f32(gscale, 3)), gV.data_ptr(), _stream()),
             "mesh_bind_gaussians_backward")
 
-    def set_query_config(self, lanes: int = -1, variant: int = -1) -> None:
-        """Traversal choice for this handle's closest-point calls (-1 = process-wide)."""
+    def set_query_config(self, lanes: int = -1, variant: int = -1, block: int | None = None) -> None:
+        """Traversal choice for this handle's closest-point calls (-1 = process-wide);
+        `block`: threads per block of the one-thread variants 0, 2, 3 (32, 64, 128)."""
         check(lib().mesh_bvh_set_query_config(self.handle, int(lanes), int(variant)),
               "mesh_bvh_set_query_config")
+        if block is not None:
+            check(lib().mesh_bvh_set_query_block(self.handle, int(block)), "mesh_bvh_set_query_block")
+
+    def set_leaf_size(self, leaf_size: int, refit: bool = True) -> None:
+        """Leaf collapse at `leaf_size` faces (mesh_bvh_set_leaf_size); with refit=True the
+        tree is refit from its current vertex buffer at once so the new links apply."""
+        check(lib().mesh_bvh_set_leaf_size(self.handle, int(leaf_size)), "mesh_bvh_set_leaf_size")
+        self.leaf_size = int(leaf_size)
+        if refit and self.n_faces > 0:
+            self.refit()
 
     # -- inspection -----------------------------------------------------
     def status(self) -> tuple[int, int]:

@@ -22,6 +22,8 @@ struct mesh_bvh_impl {
     mesh_bvh_layout L;
     int cfg_lanes = -1;      // per-handle traversal choice; -1 = process-wide setting
     int cfg_variant = -1;
+    int cfg_block = 128;     // threads per block of the one-thread traversal (variants 0, 2, 3)
+    int leaf_size = 1;       // faces per collapsed leaf, written by the next build / refit
     Header *hdr() const { return reinterpret_cast<Header *>(base + L.off_header); }
     float4 *verts() const { return reinterpret_cast<float4 *>(base + L.off_verts); }
     int4 *faces() const { return reinterpret_cast<int4 *>(base + L.off_faces); }
@@ -95,6 +97,9 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 inline unsigned int grid_for(int64_t n, int block) {
     return (unsigned int)((n + block - 1) / block);
 }
+
+// Largest leaf size of the collapse (faces tested in one leaf range).
+constexpr int kMaxLeafSize = 8;
 
 // Tie rule of NearestSurface: faces within (1 + 1e-6) of the nearest distance
 // (plus 1e-12 of the box diagonal) count as equally near; the lowest id wins.

@@ -408,12 +408,14 @@ __device__ __forceinline__ void karras_children(const unsigned int *__restrict__
     far_end = j;
 }
 
+// Child links of internal node i: lo.w = the child (internal c >= 0, leaf j as
+// -(j+1)), hi.w = the number of faces of a leaf link (1 here) or c again.
 __device__ __forceinline__ void write_children(float4 *__restrict__ nodes, int i, int left, int right) {
     float *rec = reinterpret_cast<float *>(nodes + 4 * (size_t)i);
     rec[3] = __int_as_float(left);
-    rec[7] = __int_as_float(left);
+    rec[7] = __int_as_float(left < 0 ? 1 : left);
     rec[11] = __int_as_float(right);
-    rec[15] = __int_as_float(right);
+    rec[15] = __int_as_float(right < 0 ? 1 : right);
 }
 
 __global__ void k_karras(const unsigned int *__restrict__ keys, int n, float4 *__restrict__ nodes,
@@ -505,18 +507,31 @@ __device__ __forceinline__ void load_tri(const float *__restrict__ V3, const flo
     }
 }
 
-// Writes box (lo, hi) of child `self` into its parent's record half, or into
-// the header when it is the root (parent link pe < 0).
+// Writes box (lo, hi) of a child into its parent's record half, or into the
+// header when it is the root (parent link pe < 0), with the child's link:
+// `link` in lo.w (internal c >= 0, or -(first+1) for a leaf range) and `cnt`
+// in hi.w (the range's face count, or c again for an internal child).
 __device__ __forceinline__ void put_box(float4 *__restrict__ nodes, Header *__restrict__ hdr, int pe,
-                                        int self, float4 lo, float4 hi) {
+                                        int link, int cnt, float4 lo, float4 hi) {
     if (pe < 0) {
         hdr->root_lo = make_float4(lo.x, lo.y, lo.z, 0.0f);
         hdr->root_hi = make_float4(hi.x, hi.y, hi.z, 0.0f);
         return;
     }
     float4 *rec = nodes + 4 * (size_t)(pe >> 1) + 2 * (pe & 1);
-    rec[0] = make_float4(lo.x, lo.y, lo.z, __int_as_float(self));
-    rec[1] = make_float4(hi.x, hi.y, hi.z, __int_as_float(self));
+    rec[0] = make_float4(lo.x, lo.y, lo.z, __int_as_float(link));
+    rec[1] = make_float4(hi.x, hi.y, hi.z, __int_as_float(cnt));
+}
+
+// Leaf collapse (leaf size L): internal node j over leaves [ra, rb] is linked
+// from its parent as the leaf range (-(ra+1), rb - ra + 1) when it holds at
+// most L faces, otherwise as itself.  A search then tests the faces of the
+// topmost subtree of at most L faces in one loop instead of visiting its nodes
+// (which are still refit: unreachable, and cheap to keep exact).
+__device__ __forceinline__ void node_link(int j, int ra, int rb, int L, int &link, int &cnt) {
+    int len = rb - ra + 1;
+    if (len <= L) { link = -(ra + 1); cnt = len; }
+    else { link = j; cnt = j; }
 }
 
 // Box of six floats in shared memory, structure of arrays ([6][kRefitBlock]).
@@ -564,7 +579,7 @@ k_refit_local(int n, const float *__restrict__ V3, int nV, float4 *__restrict__ 
               float4 *__restrict__ tris, float4 *__restrict__ nodes, const int *__restrict__ parent,
               const int *__restrict__ rend, float4 *__restrict__ pre, float4 *__restrict__ suf,
               float4 *__restrict__ bbox, int4 *__restrict__ xlist, int *__restrict__ xcnt,
-              int *__restrict__ iperm, Header *__restrict__ hdr, Rebind RB) {
+              int *__restrict__ iperm, Header *__restrict__ hdr, Rebind RB, int leaf_size) {
     extern __shared__ float4 dsm[];
     float *tab = reinterpret_cast<float *>(dsm);
     int *s_warp = reinterpret_cast<int *>(tab + 12 * kRefitBlock);
@@ -580,7 +595,7 @@ k_refit_local(int n, const float *__restrict__ V3, int nV, float4 *__restrict__ 
             load_tri(V3, V4, faces[perm[j]], a, b, c);
             lo = box_min(box_min(a, b), c);
             hi = box_max(box_max(a, b), c);
-            put_box(nodes, hdr, pe_leaf, -(j + 1), lo, hi);
+            put_box(nodes, hdr, pe_leaf, -(j + 1), 1, lo, hi);
         }
         SBox{tab}.put(tid, lo, hi);
     }
@@ -618,7 +633,9 @@ k_refit_local(int n, const float *__restrict__ V3, int nV, float4 *__restrict__ 
         const int h = 1 << k;
         if (node_level == k) {
             int i0 = ra - base, i1 = rb - base - h + 1;
-            put_box(nodes, hdr, pe_node, j, box_min(cur.lo(i0), cur.lo(i1)), box_max(cur.hi(i0), cur.hi(i1)));
+            int link, cnt;
+            node_link(j, ra, rb, leaf_size, link, cnt);
+            put_box(nodes, hdr, pe_node, link, cnt, box_min(cur.lo(i0), cur.lo(i1)), box_max(cur.hi(i0), cur.hi(i1)));
         }
         if (pre_level == k && j < n) {
             int i1 = tid - h + 1;
@@ -674,7 +691,7 @@ constexpr int kTopThreads = 256;
 __global__ void __launch_bounds__(kTopThreads)
 k_refit_top(const int4 *__restrict__ xlist, const int *__restrict__ xcnt, const float4 *__restrict__ pre,
             const float4 *__restrict__ suf, const float4 *__restrict__ bbox, float4 *__restrict__ nodes,
-            Header *__restrict__ hdr) {
+            Header *__restrict__ hdr, int leaf_size) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = kTopThreads >> 5;
     const int cnt = xcnt[blockIdx.x];
     for (int r = wid; r < cnt; r += nw) {
@@ -698,7 +715,11 @@ k_refit_top(const int4 *__restrict__ xlist, const int *__restrict__ xcnt, const 
             hi.y = fmaxf(hi.y, __shfl_xor_sync(0xffffffffu, hi.y, o));
             hi.z = fmaxf(hi.z, __shfl_xor_sync(0xffffffffu, hi.z, o));
         }
-        if (lane == 0) put_box(nodes, hdr, e.w, e.x, lo, hi);
+        if (lane == 0) {
+            int link, cnt;
+            node_link(e.x, e.y, e.z, leaf_size, link, cnt);
+            put_box(nodes, hdr, e.w, link, cnt, lo, hi);
+        }
     }
 }
 
@@ -840,7 +861,7 @@ __global__ void k_batch_leaves_up(int nF, const int *__restrict__ face_off, int 
         int p = pe >> 1, side = pe & 1;
         float4 *rec = snodes + 4 * (size_t)p;
         rec[2 * side] = make_float4(lo.x, lo.y, lo.z, __int_as_float(self));
-        rec[2 * side + 1] = make_float4(hi.x, hi.y, hi.z, __int_as_float(self));
+        rec[2 * side + 1] = make_float4(hi.x, hi.y, hi.z, __int_as_float(self < 0 ? 1 : self));
         __threadfence();
         unsigned int old = atomicAdd(&flags[base + p], 1u);
         if (old == 0u) return;
@@ -1249,12 +1270,20 @@ mesh_status mesh_bvh_create(void *d_storage, size_t storage_bytes, int64_t max_v
     h->L.n_verts = 0;
     h->cfg_lanes = -1;
     h->cfg_variant = -1;
+    h->cfg_block = 128;
+    h->leaf_size = 1;
     h->adj_ready = false;
     *out = h;
     return MESH_OK;
 }
 
 void mesh_bvh_destroy(mesh_bvh *bvh) { std::free(bvh); }
+
+mesh_status mesh_bvh_set_leaf_size(mesh_bvh *bvh, int leaf_size) {
+    if (!bvh || leaf_size < 1 || leaf_size > kMaxLeafSize) return MESH_ERR_INVALID_ARG;
+    bvh->leaf_size = leaf_size;
+    return MESH_OK;
+}
 
 mesh_status mesh_bvh_get_layout(const mesh_bvh *bvh, mesh_bvh_layout *out) {
     if (!bvh || !out) return MESH_ERR_INVALID_ARG;
@@ -1292,10 +1321,12 @@ static mesh_status bottom_up(mesh_bvh *bvh, const float *V3, cudaStream_t s,
     int *xcnt = reinterpret_cast<int *>(bbox + 2 * nbmax);
     k_refit_local<<<nb, kRefitBlock, kRefitLocalSmem, s>>>(
         n, V3, (int)bvh->L.n_verts, bvh->verts(), bvh->perm(), bvh->faces(), bvh->tris(),
-        bvh->nodes(), bvh->parent(), bvh->rend(), pre, suf, bbox, xlist, xcnt, bvh->iperm(), bvh->hdr(), rb);
+        bvh->nodes(), bvh->parent(), bvh->rend(), pre, suf, bbox, xlist, xcnt, bvh->iperm(), bvh->hdr(), rb,
+        bvh->leaf_size);
     count_launch();
     if (nb > 1) {
-        k_refit_top<<<nb, kTopThreads, 0, s>>>(xlist, xcnt, pre, suf, bbox, bvh->nodes(), bvh->hdr());
+        k_refit_top<<<nb, kTopThreads, 0, s>>>(xlist, xcnt, pre, suf, bbox, bvh->nodes(), bvh->hdr(),
+                                               bvh->leaf_size);
         count_launch();
     }
     return check_launch();

@@ -243,45 +243,52 @@ __device__ __forceinline__ float cutoff_window2(float maxd2, float tau, float sl
 }
 
 // Candidate bookkeeping of the tie rule.  dmin is the nearest squared
-// distance seen; the kept face is the lowest id among the faces seen within
-// the window of dmin -- as long as every face seen inside the current window,
-// other than the kept one, has a higher id.  `other` is the least squared
-// distance of the faces seen and not kept; when the kept face leaves the
-// shrinking window while `other` is still inside it, one of those faces may
-// have the lowest id, and `other` is set to -1: the query is resolved at the
-// end by one search with the final window fixed (resolve_ties).  The answer
-// is therefore the lowest id within the final window, whatever the order in
-// which faces were met.
+// distance seen; the kept face (leaf `leaf`, its face id read back from the
+// packed triangle when a tie needs it) is the lowest id among the faces seen
+// within the window of dmin -- as long as every face seen inside the current
+// window, other than the kept one, has a higher id.  `other` is the least
+// squared distance of the faces seen and not kept; when the kept face leaves
+// the shrinking window while `other` is still inside it, one of those faces
+// may have the lowest id, and `other` is set to -1: the query is resolved at
+// the end by one search with the final window fixed (resolve_ties).  The
+// answer is therefore the lowest id within the final window, whatever the
+// order in which faces were met.  Five registers, as the search carries them
+// through every node visit.
 struct Best {
-    int leaf, face;
-    float d2, dmin, thr, other, slack;
+    int leaf;
+    float d2, dmin, thr, other;
 };
 
-__device__ __forceinline__ Best make_best(const Traversal &T, float3 q, float maxd2) {
-    float sl = query_slack(T, q);
-    return Best{-1, 0x7fffffff, INFINITY, INFINITY, cutoff_window2(maxd2, T.tau, sl), INFINITY, sl};
+__device__ __forceinline__ int face_of(const Traversal &T, int leaf) {
+    return __float_as_int(ldg4(T.tris + 3 * (size_t)leaf).w);
 }
 
-__device__ __forceinline__ void consider(Best &B, int leaf, int face, float d2, float maxd2,
-                                         float tau) {
+__device__ __forceinline__ Best make_best(const Traversal &T, float3 q, float maxd2) {
+    return Best{-1, INFINITY, INFINITY, cutoff_window2(maxd2, T.tau, query_slack(T, q)), INFINITY};
+}
+
+__device__ __forceinline__ void consider(const Traversal &T, Best &B, float3 q, int leaf, int face,
+                                         float d2, float maxd2) {
     float nmin = fminf(B.dmin, d2);
     if (nmin > maxd2) {                       // no hit yet and this face is past the cutoff:
         B.other = fminf(B.other, d2);         // noted only (it may fall in a later hit's window)
         return;
     }
     float w2, p2;
-    windows(nmin, tau, B.slack, w2, p2);
+    windows(nmin, T.tau, query_slack(T, q), w2, p2);
     if (d2 <= w2) {
-        if (B.leaf >= 0 && B.d2 <= w2) {      // the kept face stays inside the window
-            if (face < B.face) {
-                B.other = fminf(B.other, B.d2);
-                B.leaf = leaf; B.face = face; B.d2 = d2;
-            } else if (face != B.face) {
-                B.other = fminf(B.other, d2);
+        if (B.leaf >= 0 && B.d2 <= w2) {      // the kept face stays inside the window: a tie
+            if (leaf != B.leaf) {
+                if (face < face_of(T, B.leaf)) {
+                    B.other = fminf(B.other, B.d2);
+                    B.leaf = leaf; B.d2 = d2;
+                } else {
+                    B.other = fminf(B.other, d2);
+                }
             }
         } else {                              // first hit, or the kept face left the window
             if (B.other <= w2) B.other = -1.0f;
-            B.leaf = leaf; B.face = face; B.d2 = d2;
+            B.leaf = leaf; B.d2 = d2;
         }
     }
     B.dmin = nmin;
@@ -294,8 +301,44 @@ __device__ __forceinline__ void test_leaf(const Traversal &T, Best &B, int leaf,
     float4 a = ldg4(t), b = ldg4(t + 1), c = ldg4(t + 2);
     float u, v, w;
     float d2 = tri_closest(q, xyz(a), xyz(b), xyz(c), b.w != 0.0f, u, v, w);
-    consider(B, leaf, __float_as_int(a.w), d2, maxd2, T.tau);
+    consider(T, B, q, leaf, __float_as_int(a.w), d2, maxd2);
 }
+
+// The faces of a leaf link: first = -link - 1, cnt from the record's hi.w (1
+// without leaf collapse).  The first face's box is the link's box when cnt is
+// 1; the others are tested against their own box first (computed from the
+// corners just loaded), so a face far outside the window costs no region test.
+// kRange = false (a tree without leaf collapse) compiles to the single face
+// alone: the leaf-range loop costs the one-thread searches ~10 % even when
+// every count is 1, so the kernels come in both forms and the host picks the
+// plain one for leaf size 1.
+template <bool kRange>
+__device__ __forceinline__ void test_range(const Traversal &T, Best &B, int first, int cnt, float3 q,
+                                           float maxd2) {
+    if constexpr (!kRange) {
+        test_leaf(T, B, first, q, maxd2);
+        return;
+    }
+    // one call site of the region test; the per-face box test only runs for a
+    // real range
+#pragma unroll 1
+    for (int k = 0; k < cnt; ++k) {
+        const float4 *t = T.tris + 3 * (size_t)(first + k);
+        float4 a = ldg4(t), b = ldg4(t + 1), c = ldg4(t + 2);
+        if (cnt > 1) {
+            float4 lo = make_float4(fminf(fminf(a.x, b.x), c.x), fminf(fminf(a.y, b.y), c.y),
+                                    fminf(fminf(a.z, b.z), c.z), 0.0f);
+            float4 hi = make_float4(fmaxf(fmaxf(a.x, b.x), c.x), fmaxf(fmaxf(a.y, b.y), c.y),
+                                    fmaxf(fmaxf(a.z, b.z), c.z), 0.0f);
+            if (box_d2(q, lo, hi) > B.thr) continue;
+        }
+        float u, v, w;
+        float d2 = tri_closest(q, xyz(a), xyz(b), xyz(c), b.w != 0.0f, u, v, w);
+        consider(T, B, q, first + k, __float_as_int(a.w), d2, maxd2);
+    }
+}
+
+__device__ __forceinline__ int link_count(float4 hi) { return __float_as_int(hi.w); }
 
 // The tie rule with the window fixed: one depth-first search that visits every
 // box within the pruning radius of B.dmin and keeps the lowest face id whose
@@ -305,7 +348,7 @@ __device__ __forceinline__ void test_leaf(const Traversal &T, Best &B, int leaf,
 __device__ __noinline__ void resolve_ties(const Traversal &T, Best &B, float3 q,
                                           unsigned int *status) {
     float w2, p2;
-    windows(B.dmin, T.tau, B.slack, w2, p2);
+    windows(B.dmin, T.tau, query_slack(T, q), w2, p2);
     int bl = -1, bf = 0x7fffffff;
     float bd = INFINITY;
     auto test = [&](int leaf) {
@@ -326,8 +369,10 @@ __device__ __noinline__ void resolve_ties(const Traversal &T, Best &B, float3 q,
             float4 l0 = ldg4(r), l1 = ldg4(r + 1), r0 = ldg4(r + 2), r1 = ldg4(r + 3);
             int cl = __float_as_int(l0.w), cr = __float_as_int(r0.w);
             bool il = box_d2(q, l0, l1) <= p2, ir = box_d2(q, r0, r1) <= p2;
-            if (il && cl < 0) test(-cl - 1);
-            if (ir && cr < 0) test(-cr - 1);
+            if (il && cl < 0)
+                for (int k = 0; k < link_count(l1); ++k) test(-cl - 1 + k);
+            if (ir && cr < 0)
+                for (int k = 0; k < link_count(r1); ++k) test(-cr - 1 + k);
             bool gl = il && cl >= 0, gr = ir && cr >= 0;
             if (gl && gr) {
                 if (sp < kStackTotal) stk[sp++] = cr;
@@ -341,13 +386,13 @@ __device__ __noinline__ void resolve_ties(const Traversal &T, Best &B, float3 q,
             node = stk[--sp];
         }
     }
-    if (bl >= 0) { B.leaf = bl; B.face = bf; B.d2 = bd; }
+    if (bl >= 0) { B.leaf = bl; B.d2 = bd; }
     B.other = INFINITY;
 }
 
 __device__ __forceinline__ Hit finish(const Traversal &T, Best &B, float3 q, unsigned int *status) {
     if (B.other < 0.0f) resolve_ties(T, B, q, status);
-    return Hit{B.leaf, B.face, B.d2};
+    return Hit{B.leaf, B.leaf >= 0 ? face_of(T, B.leaf) : 0x7fffffff, B.d2};
 }
 
 // kSmem: stack entries per thread kept in shared memory (the rest spill to a
@@ -364,7 +409,8 @@ struct Counts {
 // first node on.  Every leaf within the final tie window is still reached and
 // the tie rule does not depend on the order, so the answer is the same as
 // without the hint; only the work changes.
-template <int kBlockT, int kSmem = kStackShared, bool kOneSite = false, bool kCount = false>
+template <int kBlockT, int kSmem = kStackShared, bool kOneSite = false, bool kCount = false,
+          bool kRange = false>
 __device__ __forceinline__ Hit nearest(const Traversal &T, float3 q, float maxd2,
                                        int2 (*stk)[kBlockT], unsigned int *status,
                                        Counts *cnt = nullptr, int hint_leaf = -1) {
@@ -387,23 +433,26 @@ __device__ __forceinline__ Hit nearest(const Traversal &T, float3 q, float maxd2
             if (T.mmd) {
                 ml = box_minmax_d2(q, l0, l1);
                 mr = box_minmax_d2(q, r0, r1);
-                B.thr = fminf(B.thr, bound_window2(fminf(ml, mr), T.tau, B.slack));
+                B.thr = fminf(B.thr, bound_window2(fminf(ml, mr), T.tau, query_slack(T, q)));
             }
             int cl = __float_as_int(l0.w), cr = __float_as_int(r0.w);
-            if constexpr (kCount) cnt->tests += (cl < 0 && dl <= B.thr) + (cr < 0 && dr <= B.thr);
+            if constexpr (kCount)
+                cnt->tests += (cl < 0 && dl <= B.thr ? link_count(l1) : 0) +
+                              (cr < 0 && dr <= B.thr ? link_count(r1) : 0);
             if constexpr (kOneSite) {
                 bool tl = cl < 0 && dl <= B.thr, tr = cr < 0 && dr <= B.thr;
                 int la = tl ? -cl - 1 : -cr - 1, lb = -cr - 1;
+                int na = tl ? link_count(l1) : link_count(r1), nb = link_count(r1);
                 bool two = tl && tr;
-                if (two && dr < dl) { int t = la; la = lb; lb = t; }
+                if (two && dr < dl) { int t = la; la = lb; lb = t; t = na; na = nb; nb = t; }
 #pragma unroll 1
                 for (int k = 0; k < 2; ++k) {
                     if (k == 0 ? !(tl || tr) : !two) break;
-                    test_leaf(T, B, k == 0 ? la : lb, q, maxd2);
+                    test_range<kRange>(T, B, k == 0 ? la : lb, k == 0 ? na : nb, q, maxd2);
                 }
             } else {
-                if (cl < 0 && dl <= B.thr) test_leaf(T, B, -cl - 1, q, maxd2);
-                if (cr < 0 && dr <= B.thr) test_leaf(T, B, -cr - 1, q, maxd2);
+                if (cl < 0 && dl <= B.thr) test_range<kRange>(T, B, -cl - 1, link_count(l1), q, maxd2);
+                if (cr < 0 && dr <= B.thr) test_range<kRange>(T, B, -cr - 1, link_count(r1), q, maxd2);
             }
             bool gl = cl >= 0 && dl <= B.thr;
             bool gr = cr >= 0 && dr <= B.thr;
@@ -444,14 +493,14 @@ __device__ __forceinline__ Hit nearest_ww(const Traversal &T, float3 q, float ma
     Best B = make_best(T, q, maxd2);
     if (T.n == 1) {
         test_leaf(T, B, 0, q, maxd2);
-        return Hit{B.leaf, B.face, B.d2};
+        return Hit{B.leaf, B.leaf >= 0 ? face_of(T, B.leaf) : 0x7fffffff, B.d2};
     }
     if (T.n < 1) return Hit{-1, 0x7fffffff, INFINITY};
     int2 spill[kStackTotal - kStackShared];
     const int tid = threadIdx.x;
     int sp = 0, node = 0;
     bool done = false;
-    int lq[kLeafQueue];
+    int2 lq[kLeafQueue];                         // (first face, count) of each queued leaf link
     int nq = 0;
     while (true) {
         while (!done && nq + 2 <= kLeafQueue) {
@@ -463,11 +512,11 @@ __device__ __forceinline__ Hit nearest_ww(const Traversal &T, float3 q, float ma
             if (T.mmd) {
                 ml = box_minmax_d2(q, l0, l1);
                 mr = box_minmax_d2(q, r0, r1);
-                B.thr = fminf(B.thr, bound_window2(fminf(ml, mr), T.tau, B.slack));
+                B.thr = fminf(B.thr, bound_window2(fminf(ml, mr), T.tau, query_slack(T, q)));
             }
             int cl = __float_as_int(l0.w), cr = __float_as_int(r0.w);
-            if (cl < 0 && dl <= B.thr) lq[nq++] = -cl - 1;
-            if (cr < 0 && dr <= B.thr) lq[nq++] = -cr - 1;
+            if (cl < 0 && dl <= B.thr) lq[nq++] = make_int2(-cl - 1, link_count(l1));
+            if (cr < 0 && dr <= B.thr) lq[nq++] = make_int2(-cr - 1, link_count(r1));
             bool gol = cl >= 0 && dl <= B.thr, gor = cr >= 0 && dr <= B.thr;
             if (gol && gor) {
                 bool lfirst = dl < dr || (dl == dr && ml <= mr);
@@ -488,7 +537,7 @@ __device__ __forceinline__ Hit nearest_ww(const Traversal &T, float3 q, float ma
                 if (__int_as_float(e.y) <= B.thr) { node = e.x; done = false; break; }
             }
         }
-        for (int k = 0; k < nq; ++k) test_leaf(T, B, lq[k], q, maxd2);
+        for (int k = 0; k < nq; ++k) test_range<false>(T, B, lq[k].x, lq[k].y, q, maxd2);
         nq = 0;
         if (done) break;
     }
@@ -499,6 +548,7 @@ __device__ __forceinline__ Hit nearest_ww(const Traversal &T, float3 q, float ma
 // local stack (the tree depth bounds it, so kStackTotal entries suffice),
 // continuing the candidate state B.  Used by a cooperative group when its
 // shared stack is nearly full.
+template <bool kRange>
 __device__ __noinline__ void dfs_private(const Traversal &T, Best &B, int start, float3 q,
                                          float maxd2, unsigned int *status) {
     int2 stk[kStackTotal];
@@ -511,11 +561,11 @@ __device__ __noinline__ void dfs_private(const Traversal &T, Best &B, int start,
         if (T.mmd) {
             ml = box_minmax_d2(q, l0, l1);
             mr = box_minmax_d2(q, r0, r1);
-            B.thr = fminf(B.thr, bound_window2(fminf(ml, mr), T.tau, B.slack));
+            B.thr = fminf(B.thr, bound_window2(fminf(ml, mr), T.tau, query_slack(T, q)));
         }
         int cl = __float_as_int(l0.w), cr = __float_as_int(r0.w);
-        if (cl < 0 && dl <= B.thr) test_leaf(T, B, -cl - 1, q, maxd2);
-        if (cr < 0 && dr <= B.thr) test_leaf(T, B, -cr - 1, q, maxd2);
+        if (cl < 0 && dl <= B.thr) test_range<kRange>(T, B, -cl - 1, link_count(l1), q, maxd2);
+        if (cr < 0 && dr <= B.thr) test_range<kRange>(T, B, -cr - 1, link_count(r1), q, maxd2);
         bool gl = cl >= 0 && dl <= B.thr, gr = cr >= 0 && dr <= B.thr;
         if (gl && gr) {
             bool lfirst = dl < dr || (dl == dr && ml <= mr);
@@ -575,18 +625,24 @@ template <int G> __device__ __forceinline__ int grp_incl_scan(int x, int gl) {
     return x;
 }
 
-template <int G>
+template <int G, bool kRange = false>
 __device__ Hit nearest_group(const Traversal &T, float3 q, float maxd2, bool valid, int2 *stk,
                              unsigned int *status, int hint_leaf = -1) {
     const int lane = threadIdx.x & 31;
     const int gl = lane & (G - 1);
     const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
     // The group's candidate state: the bookkeeping of consider(), identical in
-    // every lane of the group (all updates come from group-wide reductions).
+    // every lane of the group (all updates come from group-wide reductions),
+    // with the kept face's id in sface.  S.other here is only the undecided
+    // flag (-1); the least distance of the faces not kept is accumulated per
+    // lane (acc) and tested with one vote when it matters.
     Best S = make_best(T, q, maxd2);
+    int sface = 0x7fffffff;
+    float acc = INFINITY;
     int sp = 0;
     if (valid && T.n == 1) {
         test_leaf(T, S, 0, q, maxd2);
+        if (S.leaf >= 0) sface = face_of(T, S.leaf);
     } else if (valid && T.n > 1) {
         // Greedy dive (every lane of the group on the same path): the nearer
         // child down to a leaf gives the parallel phase a tight window from
@@ -601,10 +657,13 @@ __device__ Hit nearest_group(const Traversal &T, float3 q, float maxd2, bool val
             bool lfirst = dl < dr || (dl == dr && ml <= mr);
             int c = lfirst ? __float_as_int(l0.w) : __float_as_int(r0.w);
             if (c >= 0) { node = c; continue; }
-            test_leaf(T, S, -c - 1, q, maxd2);
+            test_range<kRange>(T, S, -c - 1, link_count(lfirst ? l1 : r1), q, maxd2);
             if (hint_leaf >= 0) test_leaf(T, S, hint_leaf, q, maxd2);   // warm start
             break;
         }
+        if (S.leaf >= 0) sface = face_of(T, S.leaf);
+        acc = S.other;                               // faces the dive met and did not keep
+        S.other = S.other < 0.0f ? -1.0f : INFINITY;
         if (gl == 0) stk[0] = make_int2(0, __float_as_int(0.0f));
         sp = 1;
     }
@@ -621,7 +680,8 @@ __device__ Hit nearest_group(const Traversal &T, float3 q, float maxd2, bool val
         float c0 = INFINITY, c1 = INFINITY;
         int f0 = 0x7fffffff, f1 = 0x7fffffff, lf0 = -1, lf1 = -1;
         int npush = 0;
-        float lane_ub = INFINITY, lane_other = INFINITY;
+        float lane_ub = INFINITY, pother = INFINITY;
+        bool lane_undecided = false;
         int2 p_far = make_int2(0, 0), p_near = make_int2(0, 0);
         if (act && !near_full) {
             const float4 *r = T.nodes + 4 * (size_t)e.x;
@@ -634,20 +694,34 @@ __device__ Hit nearest_group(const Traversal &T, float3 q, float maxd2, bool val
                 lane_ub = fminf(ml, mr);
             }
             int cl = __float_as_int(l0.w), cr = __float_as_int(r0.w);
-            float u, v, w;
-            if (cl < 0 && dl <= S.thr) {
-                lf0 = -cl - 1;
-                const float4 *t = T.tris + 3 * (size_t)lf0;
-                float4 a = ldg4(t), b = ldg4(t + 1), c = ldg4(t + 2);
-                c0 = tri_closest(q, xyz(a), xyz(b), xyz(c), b.w != 0.0f, u, v, w);
-                f0 = __float_as_int(a.w);
-            }
-            if (cr < 0 && dr <= S.thr) {
-                lf1 = -cr - 1;
-                const float4 *t = T.tris + 3 * (size_t)lf1;
-                float4 a = ldg4(t), b = ldg4(t + 1), c = ldg4(t + 2);
-                c1 = tri_closest(q, xyz(a), xyz(b), xyz(c), b.w != 0.0f, u, v, w);
-                f1 = __float_as_int(a.w);
+            bool tl = cl < 0 && dl <= S.thr, tr = cr < 0 && dr <= S.thr;
+            if (kRange && ((tl && link_count(l1) > 1) || (tr && link_count(r1) > 1))) {
+                // leaf ranges: the lane keeps its own candidate under the tie rule and
+                // notes the faces it did not keep
+                Best P = S;
+                P.leaf = -1; P.d2 = INFINITY; P.other = INFINITY;
+                if (tl) test_range<kRange>(T, P, -cl - 1, link_count(l1), q, maxd2);
+                if (tr) test_range<kRange>(T, P, -cr - 1, link_count(r1), q, maxd2);
+                if (P.leaf >= 0) { c0 = P.d2; f0 = face_of(T, P.leaf); lf0 = P.leaf; }
+                pother = P.other;
+                lane_undecided = P.other < 0.0f;
+            } else {
+                // single faces: each goes to the merge as a candidate
+                float u, v, w;
+                if (tl) {
+                    lf0 = -cl - 1;
+                    const float4 *t = T.tris + 3 * (size_t)lf0;
+                    float4 a = ldg4(t), b = ldg4(t + 1), c = ldg4(t + 2);
+                    c0 = tri_closest(q, xyz(a), xyz(b), xyz(c), b.w != 0.0f, u, v, w);
+                    f0 = __float_as_int(a.w);
+                }
+                if (tr) {
+                    lf1 = -cr - 1;
+                    const float4 *t = T.tris + 3 * (size_t)lf1;
+                    float4 a = ldg4(t), b = ldg4(t + 1), c = ldg4(t + 2);
+                    c1 = tri_closest(q, xyz(a), xyz(b), xyz(c), b.w != 0.0f, u, v, w);
+                    f1 = __float_as_int(a.w);
+                }
             }
             bool gol = cl >= 0 && dl <= S.thr, gor = cr >= 0 && dr <= S.thr;
             if (gol && gor) {
@@ -664,10 +738,11 @@ __device__ Hit nearest_group(const Traversal &T, float3 q, float maxd2, bool val
             }
         } else if (act) {
             Best P = S;                          // the group's window and bounds, no kept face
-            P.leaf = -1; P.face = 0x7fffffff; P.d2 = INFINITY; P.other = INFINITY;
-            dfs_private(T, P, e.x, q, maxd2, status);
-            if (P.leaf >= 0) { c0 = P.d2; f0 = P.face; lf0 = P.leaf; }
-            lane_other = P.other;                // faces it met and did not keep (-1: undecided)
+            P.leaf = -1; P.d2 = INFINITY; P.other = INFINITY;
+            dfs_private<kRange>(T, P, e.x, q, maxd2, status);
+            if (P.leaf >= 0) { c0 = P.d2; f0 = face_of(T, P.leaf); lf0 = P.leaf; }
+            pother = P.other;
+            lane_undecided = P.other < 0.0f;
         }
         // Merge the step's candidates into S (consider() for a set of faces at
         // once).  Every reduction runs on the full warp, outside any branch.
@@ -676,7 +751,7 @@ __device__ Hit nearest_group(const Traversal &T, float3 q, float maxd2, bool val
         float nmin = fminf(S.dmin, m);
         const bool hit = nmin <= maxd2;
         float w2 = -1.0f, p2 = INFINITY;
-        if (hit) windows(nmin, T.tau, S.slack, w2, p2);
+        if (hit) windows(nmin, T.tau, query_slack(T, q), w2, p2);
         int fc = min(c0 <= w2 ? f0 : 0x7fffffff, c1 <= w2 ? f1 : 0x7fffffff);
         int fmin = grp_min<G>(fc);
         bool mine = fmin != 0x7fffffff && fc == fmin;
@@ -687,22 +762,24 @@ __device__ Hit nearest_group(const Traversal &T, float3 q, float maxd2, bool val
         float sd2 = __shfl_sync(0xffffffffu, md2, src, G);
         int slf = __shfl_sync(0xffffffffu, mlf, src, G);
         const bool stays = S.leaf >= 0 && S.d2 <= w2;          // the kept face is still inside
-        const int kept = (stays && S.face <= fmin) ? S.face : fmin;
-        float lo = lane_other;                                   // every other face goes to `other`
-        if (f0 != kept) lo = fminf(lo, c0);
-        if (f1 != kept) lo = fminf(lo, c1);
-        float oth = grp_min<G>(lo);
+        const int kept = (stays && sface <= fmin) ? sface : fmin;
+        // undecided when a lane's own search was, or when the kept face leaves the
+        // window while a face met earlier and not kept is still inside it
+        bool undecided = (__ballot_sync(0xffffffffu, lane_undecided || (hit && !stays && acc <= w2)) &
+                          gmask) != 0u;
+        if (undecided) S.other = -1.0f;
+        acc = fminf(acc, pother);              // faces of this step not kept: higher ids than kept
+        if (f0 != kept) acc = fminf(acc, c0);
+        if (f1 != kept) acc = fminf(acc, c1);
         if (hit) {
-            if (!stays && S.other <= w2) S.other = -1.0f;        // an earlier face may be lower
-            if (kept != S.face) {
-                if (stays) S.other = fminf(S.other, S.d2);
-                S.leaf = slf; S.face = fmin; S.d2 = sd2;
+            if (kept != sface) {
+                if (stays) acc = fminf(acc, S.d2);
+                S.leaf = slf; sface = fmin; S.d2 = sd2;
             }
             S.dmin = nmin;
             S.thr = fminf(S.thr, p2);
         }
-        S.other = fminf(S.other, oth);
-        S.thr = fminf(S.thr, bound_window2(ub, T.tau, S.slack));
+        S.thr = fminf(S.thr, bound_window2(ub, T.tau, query_slack(T, q)));
         // push surviving children: lane G-1's lowest, lane 0's on top
         int total = grp_sum<G>(npush);
         int above = total - grp_incl_scan<G>(npush, gl);
@@ -712,8 +789,11 @@ __device__ Hit nearest_group(const Traversal &T, float3 q, float maxd2, bool val
         __syncwarp();
     }
     // only the group's first lane writes the result, so only it resolves
-    if (valid && gl == 0 && S.other < 0.0f) resolve_ties(T, S, q, status);
-    return Hit{S.leaf, S.face, S.d2};
+    if (valid && gl == 0 && S.other < 0.0f) {
+        resolve_ties(T, S, q, status);
+        sface = S.leaf >= 0 ? face_of(T, S.leaf) : 0x7fffffff;
+    }
+    return Hit{S.leaf, sface, S.d2};
 }
 
 // Per-mesh constants of the tie rule from the mesh box: the window's absolute
@@ -769,14 +849,18 @@ __device__ __forceinline__ unsigned int work_class(int visits) {
 
 // kRecord: also count the node visits of each query and store its work class
 // in cls[i] (the contact step).
-template <int kSmem, int kMode, int kMinBlocks = kQueryMinBlocks, bool kRecord = false>
-__global__ void __launch_bounds__(kQueryBlock, kMinBlocks)
+// kBlock: threads per block (128, or 64 / 32 with the same register budget: the
+// same warps per SM in finer blocks, so a block whose warps finish early frees
+// its slot sooner -- the searches of one block end at very different times).
+template <int kSmem, int kMode, int kMinBlocks = kQueryMinBlocks, bool kRecord = false,
+          int kBlock = kQueryBlock, bool kRange = false>
+__global__ void __launch_bounds__(kBlock, kMinBlocks * kQueryBlock / kBlock)
 k_closest_point(Traversal T, const Header *__restrict__ hdr, unsigned int *status,
                 const float *__restrict__ Q, int64_t nQ, float maxd2, int *face, float *bary,
                 float *point, float *dist2, const int *hint, const int *__restrict__ iperm,
                 const int *__restrict__ order = nullptr, unsigned int *__restrict__ cls = nullptr) {
-    __shared__ int2 stk[kSmem > 0 ? kSmem : 1][kQueryBlock];
-    int64_t k = (int64_t)blockIdx.x * kQueryBlock + threadIdx.x;
+    __shared__ int2 stk[kSmem > 0 ? kSmem : 1][kBlock];
+    int64_t k = (int64_t)blockIdx.x * kBlock + threadIdx.x;
     if (k >= nQ) return;
     const int64_t i = order ? (int64_t)order[k] : k;       // order: a permutation of the queries
     set_scale(T, hdr);
@@ -790,12 +874,13 @@ k_closest_point(Traversal T, const Header *__restrict__ hdr, unsigned int *statu
     if constexpr (kRecord) {
         static_assert(kMode != 1, "the recording form uses the depth-first traversal");
         Counts c{0, 0};
-        h = nearest<kQueryBlock, kSmem, kMode == 2, true>(T, q, maxd2, stk, status, &c, hint_leaf);
+        h = nearest<kBlock, kSmem, kMode == 2, true, kRange>(T, q, maxd2, stk, status, &c, hint_leaf);
         cls[i] = work_class(c.visits);
     } else if constexpr (kMode == 1) {
-        h = nearest_ww<kQueryBlock>(T, q, maxd2, stk, status);
+        static_assert(!kRange, "the while-while form has no leaf-range instantiation");
+        h = nearest_ww<kBlock>(T, q, maxd2, stk, status);
     } else {
-        h = nearest<kQueryBlock, kSmem, kMode == 2>(T, q, maxd2, stk, status, nullptr, hint_leaf);
+        h = nearest<kBlock, kSmem, kMode == 2, false, kRange>(T, q, maxd2, stk, status, nullptr, hint_leaf);
     }
     write_hit(T, h, q, i, face, bary, point, dist2);
 }
@@ -812,15 +897,20 @@ k_closest_point(Traversal T, const Header *__restrict__ hdr, unsigned int *statu
 // warp runs the union of its queries' traversals with every lane active,
 // instead of each lane's traversal with most lanes idle.  Same answers as the
 // depth-first kernels.
+// hint_leaf >= 0 warm-starts the lane as in nearest(); visits (when not NULL)
+// counts the nodes whose children this lane needed (its share of the work).
+template <bool kRange>
 __device__ __forceinline__ Hit nearest_packet(const Traversal &T, float3 q, float maxd2, bool valid,
-                                              int *wstk, unsigned int *status) {
+                                              int *wstk, unsigned int *status, int hint_leaf = -1,
+                                              int *visits = nullptr) {
     const unsigned int kFull = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     Best B = make_best(T, q, maxd2);
     if (!valid) B.thr = -1.0f;                   // a lane past the end prunes everything
+    if (valid && hint_leaf >= 0) test_leaf(T, B, hint_leaf, q, maxd2);
     if (T.n == 1) {
         if (valid) test_leaf(T, B, 0, q, maxd2);
-        return Hit{B.leaf, B.face, B.d2};
+        return Hit{B.leaf, B.leaf >= 0 ? face_of(T, B.leaf) : 0x7fffffff, B.d2};
     }
     if (T.n < 1) return Hit{-1, 0x7fffffff, INFINITY};
     int sp = 0, node = 0;
@@ -830,12 +920,13 @@ __device__ __forceinline__ Hit nearest_packet(const Traversal &T, float3 q, floa
         float dl = box_d2(q, l0, l1), dr = box_d2(q, r0, r1);
         if (T.mmd && valid)
             B.thr = fminf(B.thr, bound_window2(fminf(box_minmax_d2(q, l0, l1), box_minmax_d2(q, r0, r1)),
-                                               T.tau, B.slack));
+                                               T.tau, query_slack(T, q)));
         int cl = __float_as_int(l0.w), cr = __float_as_int(r0.w);
         bool wl = dl <= B.thr, wr = dr <= B.thr;
+        if (visits) *visits += (wl || wr);
         unsigned int bl = __ballot_sync(kFull, wl), br = __ballot_sync(kFull, wr);
-        if (cl < 0 && wl) test_leaf(T, B, -cl - 1, q, maxd2);
-        if (cr < 0 && wr) test_leaf(T, B, -cr - 1, q, maxd2);
+        if (cl < 0 && wl) test_range<kRange>(T, B, -cl - 1, link_count(l1), q, maxd2);
+        if (cr < 0 && wr) test_range<kRange>(T, B, -cr - 1, link_count(r1), q, maxd2);
         bool gl = cl >= 0 && bl != 0u, gr = cr >= 0 && br != 0u;
         if (gl && gr) {
             unsigned int pl = __ballot_sync(kFull, wl && (!wr || dl <= dr));
@@ -870,19 +961,35 @@ __device__ __forceinline__ Hit nearest_packet(const Traversal &T, float3 q, floa
     return finish(T, B, q, status);
 }
 
+// hint / iperm: warm start as k_closest_point.  order: the queries' order (a
+// permutation; NULL = as stored).  kRecord: also store each query's work class
+// in cls (the contact step).
+template <bool kRecord = false, bool kRange = false>
 __global__ void __launch_bounds__(kQueryBlock, kQueryMinBlocks)
 k_closest_point_packet(Traversal T, const Header *__restrict__ hdr, unsigned int *status,
                        const float *__restrict__ Q, int64_t nQ, float maxd2, int *face, float *bary,
-                       float *point, float *dist2) {
+                       float *point, float *dist2, const int *hint, const int *__restrict__ iperm,
+                       const int *__restrict__ order = nullptr, unsigned int *__restrict__ cls = nullptr) {
     __shared__ int wstk[kQueryBlock / 32][kStackTotal];
     const int64_t w0 = (int64_t)blockIdx.x * kQueryBlock + (threadIdx.x & ~31);
     if (w0 >= nQ) return;                                  // whole warp past the end
-    const int64_t i = w0 + (threadIdx.x & 31);
-    const bool valid = i < nQ;
+    const int64_t k = w0 + (threadIdx.x & 31);
+    const bool valid = k < nQ;
+    const int64_t i = valid && order ? (int64_t)order[k] : k;
     set_scale(T, hdr);
     float3 q = valid ? make_float3(Q[3 * i], Q[3 * i + 1], Q[3 * i + 2]) : make_float3(0.0f, 0.0f, 0.0f);
-    Hit h = nearest_packet(T, q, maxd2, valid, wstk[threadIdx.x >> 5], status);
-    if (valid) write_hit(T, h, q, i, face, bary, point, dist2);
+    int hint_leaf = -1;
+    if (valid && hint) {                          // may alias face: read before the write below
+        int hf = hint[i];
+        if (hf >= 0 && hf < T.n) hint_leaf = __ldg(iperm + hf);
+    }
+    int visits = 0;
+    Hit h = nearest_packet<kRange>(T, q, maxd2, valid, wstk[threadIdx.x >> 5], status, hint_leaf,
+                                   kRecord ? &visits : nullptr);
+    if (valid) {
+        write_hit(T, h, q, i, face, bary, point, dist2);
+        if constexpr (kRecord) cls[i] = work_class(visits);
+    }
 }
 
 // k-NN weighted surface projection: the NearestSurface of temporal tracking
@@ -943,8 +1050,14 @@ k_knn_project(Traversal T, const Header *__restrict__ hdr, const float *Q, int64
             float lim = thr * 1.00001f;
             float dl = box_d2(q, l0, l1), dr = box_d2(q, r0, r1);
             int cl = __float_as_int(l0.w), cr = __float_as_int(r0.w);
-            if (cl < 0 && dl <= lim) { consider_leaf(-cl - 1); lim = thr * 1.00001f; }
-            if (cr < 0 && dr <= lim) { consider_leaf(-cr - 1); lim = thr * 1.00001f; }
+            if (cl < 0 && dl <= lim) {
+                for (int m = 0; m < link_count(l1); ++m) consider_leaf(-cl - 1 + m);
+                lim = thr * 1.00001f;
+            }
+            if (cr < 0 && dr <= lim) {
+                for (int m = 0; m < link_count(r1); ++m) consider_leaf(-cr - 1 + m);
+                lim = thr * 1.00001f;
+            }
             bool gl = cl >= 0 && dl <= lim, gr = cr >= 0 && dr <= lim;
             if (gl && gr) {
                 bool lfirst = dl <= dr;
@@ -996,6 +1109,7 @@ k_knn_project(Traversal T, const Header *__restrict__ hdr, const float *Q, int64
 // NearestSurface plus the sign of (q - c) . N, N the pseudo-normal of the
 // feature the nearest point lies on: face interior (no zero weight), edge
 // opposite vertex k (weight k zero), vertex (two zero weights).
+template <bool kRange>
 __global__ void __launch_bounds__(kQueryBlock, kQueryMinBlocks)
 k_signed_distance(Traversal T, const Header *__restrict__ hdr, unsigned int *status,
                   const float *__restrict__ Q, int64_t nQ, float maxd2, const int4 *__restrict__ faces,
@@ -1006,7 +1120,7 @@ k_signed_distance(Traversal T, const Header *__restrict__ hdr, unsigned int *sta
     if (i >= nQ) return;
     set_scale(T, hdr);
     float3 q = make_float3(Q[3 * i], Q[3 * i + 1], Q[3 * i + 2]);
-    Hit h = nearest<kQueryBlock>(T, q, maxd2, stk, status);
+    Hit h = nearest<kQueryBlock, kStackShared, false, false, kRange>(T, q, maxd2, stk, status);
     write_hit(T, h, q, i, face, bary, point, nullptr);
     if (h.leaf < 0) { sdist[i] = INFINITY; return; }
     const float4 *t = T.tris + 3 * (size_t)h.leaf;
@@ -1101,11 +1215,11 @@ k_closest_point_persistent(Traversal T, const Header *__restrict__ hdr, unsigned
             if (T.mmd) {
                 ml = box_minmax_d2(q, l0, l1);
                 mr = box_minmax_d2(q, r0, r1);
-                B.thr = fminf(B.thr, bound_window2(fminf(ml, mr), T.tau, B.slack));
+                B.thr = fminf(B.thr, bound_window2(fminf(ml, mr), T.tau, query_slack(T, q)));
             }
             int cl = __float_as_int(l0.w), cr = __float_as_int(r0.w);
-            if (cl < 0 && dl <= B.thr) test_leaf(T, B, -cl - 1, q, maxd2);
-            if (cr < 0 && dr <= B.thr) test_leaf(T, B, -cr - 1, q, maxd2);
+            if (cl < 0 && dl <= B.thr) test_range<false>(T, B, -cl - 1, link_count(l1), q, maxd2);
+            if (cr < 0 && dr <= B.thr) test_range<false>(T, B, -cr - 1, link_count(r1), q, maxd2);
             bool gol = cl >= 0 && dl <= B.thr, gor = cr >= 0 && dr <= B.thr;
             if (gol && gor) {
                 bool lfirst = dl < dr || (dl == dr && ml <= mr);
@@ -1138,6 +1252,7 @@ k_closest_point_persistent(Traversal T, const Header *__restrict__ hdr, unsigned
 // Counting form of the one-thread depth-first traversal (same visiting order
 // as variants 0, 2 and 3): node visits, triangle tests and hits, summed over
 // all queries.  Separate instantiation; the timed kernels carry no counters.
+template <bool kRange>
 __global__ void __launch_bounds__(kQueryBlock, kQueryMinBlocks)
 k_closest_point_count(Traversal T, const Header *__restrict__ hdr, unsigned int *status,
                       const float *__restrict__ Q, int64_t nQ, float maxd2,
@@ -1149,7 +1264,7 @@ k_closest_point_count(Traversal T, const Header *__restrict__ hdr, unsigned int 
     if (i < nQ) {
         set_scale(T, hdr);
         float3 q = make_float3(Q[3 * i], Q[3 * i + 1], Q[3 * i + 2]);
-        Hit h = nearest<kQueryBlock, kStackShared, false, true>(T, q, maxd2, stk, status, &c);
+        Hit h = nearest<kQueryBlock, kStackShared, false, true, kRange>(T, q, maxd2, stk, status, &c);
         hit = h.leaf >= 0;
     }
     unsigned long long v = c.visits, t = c.tests, k = hit;
@@ -1165,7 +1280,7 @@ k_closest_point_count(Traversal T, const Header *__restrict__ hdr, unsigned int 
     }
 }
 
-template <int G>
+template <int G, bool kRange = false>
 __global__ void __launch_bounds__(kQueryBlock)
 k_closest_point_group(Traversal T, const Header *__restrict__ hdr, unsigned int *status,
                       const float *__restrict__ Q, int64_t nQ, float maxd2, int *face, float *bary,
@@ -1180,7 +1295,7 @@ k_closest_point_group(Traversal T, const Header *__restrict__ hdr, unsigned int 
         int hf = hint[i];
         if (hf >= 0 && hf < T.n) hint_leaf = __ldg(iperm + hf);
     }
-    Hit h = nearest_group<G>(T, q, maxd2, valid, gstk[threadIdx.x / G], status, hint_leaf);
+    Hit h = nearest_group<G, kRange>(T, q, maxd2, valid, gstk[threadIdx.x / G], status, hint_leaf);
     if (valid && (threadIdx.x & (G - 1)) == 0) write_hit(T, h, q, i, face, bary, point, dist2);
 }
 
@@ -1246,7 +1361,7 @@ struct ChamferSide {
     const int *iperm = nullptr;    // face -> leaf of the mesh searched
 };
 
-template <int G>
+template <int G, bool kRange = false>
 __global__ void __launch_bounds__(kQueryBlock, G == 1 ? kQueryMinBlocks : 1)
 k_chamfer(ChamferSide A2B, ChamferSide B2A, unsigned int nbA, unsigned int *status,
           double *partial, unsigned int *ticket, double *out) {
@@ -1270,15 +1385,14 @@ k_chamfer(ChamferSide A2B, ChamferSide B2A, unsigned int nbA, unsigned int *stat
     }
     if constexpr (G == 1) {
         if (valid) {
-            Hit h = nearest<kQueryBlock>(T, q, INFINITY,
-                                         reinterpret_cast<int2 (*)[kQueryBlock]>(stk_mem), status,
-                                         nullptr, hint_leaf);
+            Hit h = nearest<kQueryBlock, kStackShared, false, false, kRange>(
+                T, q, INFINITY, reinterpret_cast<int2 (*)[kQueryBlock]>(stk_mem), status, nullptr, hint_leaf);
             write_hit(T, h, q, i, C.face, C.bary, nullptr, C.dist2);
             d2 = h.leaf >= 0 ? (double)h.d2 : 0.0;
         }
     } else {
-        Hit h = nearest_group<G>(T, q, INFINITY, valid, stk_mem + (threadIdx.x / G) * group_cap<G>(),
-                                 status, hint_leaf);
+        Hit h = nearest_group<G, kRange>(T, q, INFINITY, valid, stk_mem + (threadIdx.x / G) * group_cap<G>(),
+                                         status, hint_leaf);
         if (valid && (threadIdx.x & (G - 1)) == 0) {
             write_hit(T, h, q, i, C.face, C.bary, nullptr, C.dist2);
             d2 = h.leaf >= 0 ? (double)h.d2 : 0.0;
@@ -1362,11 +1476,156 @@ mesh_status launch_signed_query(const mesh_bvh *bvh, const float *d_Q, int64_t n
                                 cudaStream_t s) {
     float maxd2 = isinf(max_dist) ? INFINITY : max_dist * max_dist;
     Header *h = bvh->hdr();
-    k_signed_distance<<<grid_for(nQ, kQueryBlock), kQueryBlock, 0, s>>>(
+    auto kern = bvh->leaf_size > 1 ? k_signed_distance<true> : k_signed_distance<false>;
+    kern<<<grid_for(nQ, kQueryBlock), kQueryBlock, 0, s>>>(
         traversal_of(bvh, isinf(max_dist)), h, &h->status, d_Q, nQ, maxd2, bvh->faces(), bvh->adj(),
         bvh->fnorm(), bvh->vnorm(), d_face, d_bary, d_point, d_sdist);
     count_launch();
     return check_launch();
+}
+
+// The launch of mesh_closest_point_hinted for a tree with (R) or without leaf
+// collapse.  With leaf collapse only the main forms exist -- the depth-first
+// variants 0, 2, 3 (any block size), the warp packets (12) and the cooperative
+// groups; the other one-thread variants run as variant 0.
+template <bool R>
+static void launch_closest_point(Traversal T, Header *h, const float *d_Q, int64_t nQ, float maxd2,
+                                 int32_t *d_face, float *d_bary, float *d_point, float *d_dist2,
+                                 const int32_t *d_hint, const int *iperm, int G, int variant, int blk,
+                                 cudaStream_t s) {
+    if (R && !(variant == 0 || variant == 2 || variant == 3 || variant == 12)) variant = 0;
+    unsigned int grid = grid_for(nQ * G, kQueryBlock);
+    if (G == 1 && blk != kQueryBlock && (variant == 0 || variant == 2 || variant == 3)) {
+        unsigned int gb = grid_for(nQ, blk);
+#define MESH_CPB(SM, B) k_closest_point<SM, 0, kQueryMinBlocks, false, B, R><<<gb, B, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2, d_hint, iperm)
+        if (blk == 32) {
+            if (variant == 2) MESH_CPB(8, 32); else if (variant == 3) MESH_CPB(0, 32); else MESH_CPB(kStackShared, 32);
+        } else {
+            if (variant == 2) MESH_CPB(8, 64); else if (variant == 3) MESH_CPB(0, 64); else MESH_CPB(kStackShared, 64);
+        }
+#undef MESH_CPB
+        return;
+    }
+    switch (G) {
+        case 1:
+#define MESH_CP_ARGS <<<grid, kQueryBlock, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2, d_hint, iperm)
+            switch (variant) {
+                case 2: k_closest_point<8, 0, kQueryMinBlocks, false, kQueryBlock, R> MESH_CP_ARGS; break;
+                case 3: k_closest_point<0, 0, kQueryMinBlocks, false, kQueryBlock, R> MESH_CP_ARGS; break;
+                case 12: k_closest_point_packet<false, R><<<grid, kQueryBlock, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2, d_hint, iperm); break;
+                default:
+                    if constexpr (!R) {
+                        switch (variant) {
+                            case 1: k_closest_point<kStackShared, 1> MESH_CP_ARGS; break;
+                            case 4: k_closest_point<kStackShared, 2> MESH_CP_ARGS; break;
+                            case 5: k_closest_point<0, 2> MESH_CP_ARGS; break;
+                            case 6: k_closest_point<8, 0, 12> MESH_CP_ARGS; break;
+                            case 7: k_closest_point<0, 0, 12> MESH_CP_ARGS; break;
+                            case 8: k_closest_point<0, 0, 16> MESH_CP_ARGS; break;
+                            case 9: k_closest_point<0, 2, 12> MESH_CP_ARGS; break;
+                            case 10:
+                            case 11: {
+                                static int sms = 0;
+                                if (sms == 0) {
+                                    int dv = 0;
+                                    if (cudaGetDevice(&dv) != cudaSuccess ||
+                                        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dv) != cudaSuccess || sms <= 0)
+                                        sms = 152;
+                                }
+                                unsigned int *work = &h->pad[0];
+                                cudaMemsetAsync(work, 0, sizeof(unsigned int), s);
+                                unsigned int pg = (unsigned int)((int64_t)sms * kQueryMinBlocks < (int64_t)grid ? sms * kQueryMinBlocks : grid);
+                                if (variant == 10)
+                                    k_closest_point_persistent<8><<<pg, kQueryBlock, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2, work);
+                                else
+                                    k_closest_point_persistent<0><<<pg, kQueryBlock, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2, work);
+                                break;
+                            }
+                            default: k_closest_point<kStackShared, 0> MESH_CP_ARGS; break;
+                        }
+                    } else {
+                        k_closest_point<kStackShared, 0, kQueryMinBlocks, false, kQueryBlock, R> MESH_CP_ARGS;
+                    }
+                    break;
+            }
+#undef MESH_CP_ARGS
+            break;
+#define MESH_CPG(g) k_closest_point_group<g, R><<<grid, kQueryBlock, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2, d_hint, iperm)
+        case 2: MESH_CPG(2); break;
+        case 4: MESH_CPG(4); break;
+        case 8: MESH_CPG(8); break;
+        case 16: MESH_CPG(16); break;
+        default: MESH_CPG(32); break;
+#undef MESH_CPG
+    }
+}
+
+// The ordered, recording launch of mesh_contact for a tree with (R) or without
+// leaf collapse (with it, the one-thread variants other than 0, 2, 3 run as 0).
+template <bool R>
+static void launch_contact(Traversal T, Header *h, const float *d_Q, int64_t nQ, float maxd2, int32_t *d_face,
+                           float *d_bary, float *d_point, float *d_dist2, const int *iperm, const int *order,
+                           unsigned int *cls, int variant, int blk, cudaStream_t s) {
+    if (R && !(variant == 0 || variant == 2 || variant == 3 || variant == 12)) variant = 0;
+    unsigned int grid = grid_for(nQ, kQueryBlock);
+    if (variant == 12) {
+        k_closest_point_packet<true, R><<<grid, kQueryBlock, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face,
+                                                                     d_bary, d_point, d_dist2, d_face, iperm,
+                                                                     order, cls);
+        return;
+    }
+    if (blk != kQueryBlock && (variant == 0 || variant == 2 || variant == 3)) {
+        unsigned int gb = grid_for(nQ, blk);
+#define MESH_CTB(SM, B) k_closest_point<SM, 0, kQueryMinBlocks, true, B, R><<<gb, B, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2, d_face, iperm, order, cls)
+        if (blk == 32) {
+            if (variant == 2) MESH_CTB(8, 32); else if (variant == 3) MESH_CTB(0, 32); else MESH_CTB(kStackShared, 32);
+        } else {
+            if (variant == 2) MESH_CTB(8, 64); else if (variant == 3) MESH_CTB(0, 64); else MESH_CTB(kStackShared, 64);
+        }
+#undef MESH_CTB
+        return;
+    }
+#define MESH_CT_ARGS <<<grid, kQueryBlock, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2, d_face, iperm, order, cls)
+    switch (variant) {
+        case 2: k_closest_point<8, 0, kQueryMinBlocks, true, kQueryBlock, R> MESH_CT_ARGS; break;
+        case 3: k_closest_point<0, 0, kQueryMinBlocks, true, kQueryBlock, R> MESH_CT_ARGS; break;
+        default:
+            if constexpr (!R) {
+                switch (variant) {
+                    case 4: k_closest_point<kStackShared, 2, kQueryMinBlocks, true> MESH_CT_ARGS; break;
+                    case 5: k_closest_point<0, 2, kQueryMinBlocks, true> MESH_CT_ARGS; break;
+                    case 6: k_closest_point<8, 0, 12, true> MESH_CT_ARGS; break;
+                    case 7: k_closest_point<0, 0, 12, true> MESH_CT_ARGS; break;
+                    case 8: k_closest_point<0, 0, 16, true> MESH_CT_ARGS; break;
+                    case 9: k_closest_point<0, 2, 12, true> MESH_CT_ARGS; break;
+                    default: k_closest_point<kStackShared, 0, kQueryMinBlocks, true> MESH_CT_ARGS; break;
+                }
+            } else {
+                k_closest_point<kStackShared, 0, kQueryMinBlocks, true, kQueryBlock, R> MESH_CT_ARGS;
+            }
+            break;
+    }
+#undef MESH_CT_ARGS
+}
+
+// The Chamfer launch: G lanes per sample, with (range) or without leaf collapse.
+template <bool R>
+static void launch_chamfer_r(int G, unsigned grid, const ChamferSide &a2b, const ChamferSide &b2a, unsigned nbA,
+                             unsigned *st, double *partial, unsigned *ticket, double *out, cudaStream_t s) {
+    switch (G) {
+        case 1: k_chamfer<1, R><<<grid, kQueryBlock, 0, s>>>(a2b, b2a, nbA, st, partial, ticket, out); break;
+        case 2: k_chamfer<2, R><<<grid, kQueryBlock, 0, s>>>(a2b, b2a, nbA, st, partial, ticket, out); break;
+        case 4: k_chamfer<4, R><<<grid, kQueryBlock, 0, s>>>(a2b, b2a, nbA, st, partial, ticket, out); break;
+        case 8: k_chamfer<8, R><<<grid, kQueryBlock, 0, s>>>(a2b, b2a, nbA, st, partial, ticket, out); break;
+        case 16: k_chamfer<16, R><<<grid, kQueryBlock, 0, s>>>(a2b, b2a, nbA, st, partial, ticket, out); break;
+        default: k_chamfer<32, R><<<grid, kQueryBlock, 0, s>>>(a2b, b2a, nbA, st, partial, ticket, out); break;
+    }
+}
+static void launch_chamfer(int G, bool range, unsigned grid, const ChamferSide &a2b, const ChamferSide &b2a,
+                           unsigned nbA, unsigned *st, double *partial, unsigned *ticket, double *out,
+                           cudaStream_t s) {
+    if (range) launch_chamfer_r<true>(G, grid, a2b, b2a, nbA, st, partial, ticket, out, s);
+    else launch_chamfer_r<false>(G, grid, a2b, b2a, nbA, st, partial, ticket, out, s);
 }
 
 }  // namespace meshgs
@@ -1394,50 +1653,12 @@ mesh_status mesh_closest_point_hinted(const mesh_bvh *bvh, const float *d_Q, int
     int variant = bvh->cfg_variant >= 0 ? bvh->cfg_variant : g_traversal;
     if (variant >= 10 && nQ >= ((int64_t)1 << 31)) variant = 0;   // 32-bit work counter
     Traversal T = traversal_of(bvh, isinf(max_dist));
-    Header *h = bvh->hdr();
-    unsigned int grid = grid_for(nQ * G, kQueryBlock);
-    switch (G) {
-        case 1:
-#define MESH_CP_ARGS <<<grid, kQueryBlock, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2, d_hint, iperm)
-            switch (variant) {
-                case 1: k_closest_point<kStackShared, 1> MESH_CP_ARGS; break;
-                case 2: k_closest_point<8, 0> MESH_CP_ARGS; break;
-                case 3: k_closest_point<0, 0> MESH_CP_ARGS; break;
-                case 4: k_closest_point<kStackShared, 2> MESH_CP_ARGS; break;
-                case 5: k_closest_point<0, 2> MESH_CP_ARGS; break;
-                case 6: k_closest_point<8, 0, 12> MESH_CP_ARGS; break;
-                case 7: k_closest_point<0, 0, 12> MESH_CP_ARGS; break;
-                case 8: k_closest_point<0, 0, 16> MESH_CP_ARGS; break;
-                case 9: k_closest_point<0, 2, 12> MESH_CP_ARGS; break;
-                case 10:
-                case 11: {
-                    static int sms = 0;
-                    if (sms == 0) {
-                        int dv = 0;
-                        if (cudaGetDevice(&dv) != cudaSuccess ||
-                            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dv) != cudaSuccess || sms <= 0)
-                            sms = 152;
-                    }
-                    unsigned int *work = &h->pad[0];
-                    cudaMemsetAsync(work, 0, sizeof(unsigned int), s);
-                    unsigned int pg = (unsigned int)((int64_t)sms * kQueryMinBlocks < (int64_t)grid ? sms * kQueryMinBlocks : grid);
-                    if (variant == 10)
-                        k_closest_point_persistent<8><<<pg, kQueryBlock, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2, work);
-                    else
-                        k_closest_point_persistent<0><<<pg, kQueryBlock, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2, work);
-                    break;
-                }
-                case 12: k_closest_point_packet<<<grid, kQueryBlock, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2); break;
-                default: k_closest_point<kStackShared, 0> MESH_CP_ARGS; break;
-            }
-#undef MESH_CP_ARGS
-            break;
-        case 2: k_closest_point_group<2><<<grid, kQueryBlock, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2, d_hint, iperm); break;
-        case 4: k_closest_point_group<4><<<grid, kQueryBlock, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2, d_hint, iperm); break;
-        case 8: k_closest_point_group<8><<<grid, kQueryBlock, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2, d_hint, iperm); break;
-        case 16: k_closest_point_group<16><<<grid, kQueryBlock, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2, d_hint, iperm); break;
-        default: k_closest_point_group<32><<<grid, kQueryBlock, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2, d_hint, iperm); break;
-    }
+    if (bvh->leaf_size > 1)
+        launch_closest_point<true>(T, bvh->hdr(), d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2, d_hint,
+                                   iperm, G, variant, bvh->cfg_block, s);
+    else
+        launch_closest_point<false>(T, bvh->hdr(), d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2, d_hint,
+                                    iperm, G, variant, bvh->cfg_block, s);
     count_launch();
     return check_launch();
 }
@@ -1504,7 +1725,8 @@ mesh_status mesh_contact(const mesh_bvh *bvh, const float *d_Q, int64_t nQ, floa
     ContactWs w = contact_ws(d_ws, nQ);
     if (!d_ws || ws_bytes < w.bytes || ((uintptr_t)d_ws & 255u)) return MESH_ERR_WORKSPACE;
     int variant = bvh->cfg_variant >= 0 ? bvh->cfg_variant : g_traversal;
-    if (variant == 1 || (variant >= 10 && variant <= 12) || (bvh->cfg_lanes > 1))
+    if (bvh->leaf_size > 1 && !(variant == 0 || variant == 2 || variant == 3 || variant == 12)) variant = 0;
+    if (variant == 1 || (variant >= 10 && variant <= 11) || (bvh->cfg_lanes > 1))
         return mesh_closest_point_hinted(bvh, d_Q, nQ, max_dist, d_face, d_face, d_bary, d_point, d_dist2,
                                          stream);
     cudaStream_t s = (cudaStream_t)stream;
@@ -1516,20 +1738,12 @@ mesh_status mesh_contact(const mesh_bvh *bvh, const float *d_Q, int64_t nQ, floa
     Traversal T = traversal_of(bvh, isinf(max_dist));
     Header *h = bvh->hdr();
     const int *iperm = bvh->iperm();
-    unsigned int grid = grid_for(nQ, kQueryBlock);
-#define MESH_CT_ARGS <<<grid, kQueryBlock, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2, d_face, iperm, w.order, w.cls)
-    switch (variant) {
-        case 2: k_closest_point<8, 0, kQueryMinBlocks, true> MESH_CT_ARGS; break;
-        case 3: k_closest_point<0, 0, kQueryMinBlocks, true> MESH_CT_ARGS; break;
-        case 4: k_closest_point<kStackShared, 2, kQueryMinBlocks, true> MESH_CT_ARGS; break;
-        case 5: k_closest_point<0, 2, kQueryMinBlocks, true> MESH_CT_ARGS; break;
-        case 6: k_closest_point<8, 0, 12, true> MESH_CT_ARGS; break;
-        case 7: k_closest_point<0, 0, 12, true> MESH_CT_ARGS; break;
-        case 8: k_closest_point<0, 0, 16, true> MESH_CT_ARGS; break;
-        case 9: k_closest_point<0, 2, 12, true> MESH_CT_ARGS; break;
-        default: k_closest_point<kStackShared, 0, kQueryMinBlocks, true> MESH_CT_ARGS; break;
-    }
-#undef MESH_CT_ARGS
+    if (bvh->leaf_size > 1)
+        launch_contact<true>(T, h, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2, iperm, w.order, w.cls,
+                             variant, bvh->cfg_block, s);
+    else
+        launch_contact<false>(T, h, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2, iperm, w.order, w.cls,
+                              variant, bvh->cfg_block, s);
     count_launch();
     return check_launch();
 }
@@ -1571,14 +1785,8 @@ mesh_status mesh_chamfer_hinted(const mesh_bvh *A, const float *d_SA, int64_t nS
     ChamferSide b2a{traversal_of(A), A->hdr(), d_SB, nSB, d_faceB, d_baryB, d_dist2B, d_hintB, A->iperm()};
     unsigned grid = (unsigned)(nbA + nbB);
     unsigned *st = &A->hdr()->status;
-    switch (G) {
-        case 1: k_chamfer<1><<<grid, kQueryBlock, 0, s>>>(a2b, b2a, (unsigned)nbA, st, partial, ticket, d_out); break;
-        case 2: k_chamfer<2><<<grid, kQueryBlock, 0, s>>>(a2b, b2a, (unsigned)nbA, st, partial, ticket, d_out); break;
-        case 4: k_chamfer<4><<<grid, kQueryBlock, 0, s>>>(a2b, b2a, (unsigned)nbA, st, partial, ticket, d_out); break;
-        case 8: k_chamfer<8><<<grid, kQueryBlock, 0, s>>>(a2b, b2a, (unsigned)nbA, st, partial, ticket, d_out); break;
-        case 16: k_chamfer<16><<<grid, kQueryBlock, 0, s>>>(a2b, b2a, (unsigned)nbA, st, partial, ticket, d_out); break;
-        default: k_chamfer<32><<<grid, kQueryBlock, 0, s>>>(a2b, b2a, (unsigned)nbA, st, partial, ticket, d_out); break;
-    }
+    launch_chamfer(G, A->leaf_size > 1 || B->leaf_size > 1, grid, a2b, b2a, (unsigned)nbA, st, partial, ticket,
+                   d_out, s);
     count_launch();
     return check_launch();
 }
@@ -1620,7 +1828,8 @@ mesh_status mesh_closest_point_stats(const mesh_bvh *bvh, const float *d_Q, int6
     cudaMemsetAsync(d_counts, 0, 3 * sizeof(unsigned long long), s);
     if (nQ == 0) return check_launch();
     float maxd2 = isinf(max_dist) ? INFINITY : max_dist * max_dist;
-    k_closest_point_count<<<grid_for(nQ, kQueryBlock), kQueryBlock, 0, s>>>(
+    (bvh->leaf_size > 1 ? k_closest_point_count<true> : k_closest_point_count<false>)
+        <<<grid_for(nQ, kQueryBlock), kQueryBlock, 0, s>>>(
         traversal_of(bvh, isinf(max_dist)), bvh->hdr(), &bvh->hdr()->status, d_Q, nQ, maxd2,
         d_counts);
     count_launch();
@@ -1643,6 +1852,13 @@ mesh_status mesh_bvh_set_query_config(mesh_bvh *bvh, int lanes, int variant) {
     if (variant < -1 || variant > 12) return MESH_ERR_INVALID_ARG;
     bvh->cfg_lanes = lanes;
     bvh->cfg_variant = variant;
+    return MESH_OK;
+}
+
+mesh_status mesh_bvh_set_query_block(mesh_bvh *bvh, int threads) {
+    if (!bvh || (threads != 0 && threads != 32 && threads != 64 && threads != 128))
+        return MESH_ERR_INVALID_ARG;
+    bvh->cfg_block = threads == 0 ? kQueryBlock : threads;
     return MESH_OK;
 }
 
@@ -1733,14 +1949,7 @@ extern "C" mesh_status mesh_chamfer_noalloc(const mesh_bvh *A, const float *d_SA
     ChamferSide b2a{traversal_of(A), A->hdr(), d_SB, nSB, d_faceB, d_baryB, d_dist2B};
     unsigned grid = (unsigned)(nbA + nbB), nb = (unsigned)nbA;
     unsigned *st_ = &A->hdr()->status;
-    switch (G) {
-        case 1: k_chamfer<1><<<grid, kQueryBlock, 0, s>>>(a2b, b2a, nb, st_, scratch, ticket, d_out); break;
-        case 2: k_chamfer<2><<<grid, kQueryBlock, 0, s>>>(a2b, b2a, nb, st_, scratch, ticket, d_out); break;
-        case 4: k_chamfer<4><<<grid, kQueryBlock, 0, s>>>(a2b, b2a, nb, st_, scratch, ticket, d_out); break;
-        case 8: k_chamfer<8><<<grid, kQueryBlock, 0, s>>>(a2b, b2a, nb, st_, scratch, ticket, d_out); break;
-        case 16: k_chamfer<16><<<grid, kQueryBlock, 0, s>>>(a2b, b2a, nb, st_, scratch, ticket, d_out); break;
-        default: k_chamfer<32><<<grid, kQueryBlock, 0, s>>>(a2b, b2a, nb, st_, scratch, ticket, d_out); break;
-    }
+    launch_chamfer(G, A->leaf_size > 1 || B->leaf_size > 1, grid, a2b, b2a, nb, st_, scratch, ticket, d_out, s);
     count_launch();
     return check_launch();
 }

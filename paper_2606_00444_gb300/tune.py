@@ -2,10 +2,13 @@
 
 The best traversal depends on the workload: how many queries there are
 (whether one thread per query fills the GPU), whether a cutoff bounds the
-search, and the mesh.  `tune_closest_point` times every candidate -- lanes per
-query (1, 2, 4, ..., 32) and, for one lane, the thirteen traversal variants of
-mesh_set_traversal -- on the caller's own BVH and queries with CUDA events,
-keeps the fastest, and applies it.  `tune_chamfer` does the same for the
+search, and the mesh.  `tune_closest_point` times every candidate -- the leaf
+size of the tree (1, 2, 4, 8 faces per collapsed leaf), lanes per query (1, 2,
+4, ..., 32) and, for one lane, the thirteen traversal variants of
+mesh_set_traversal, the main ones also in blocks of 32 and 64 threads -- on
+the caller's own BVH and queries with CUDA events, keeps the fastest, and
+applies it (a new leaf size takes a refit of the tree from its current
+vertices; the answers do not depend on any of these choices).  `tune_chamfer` does the same for the
 lanes of the Chamfer kernel.  Results are cached in memory, and in a JSON file
 when MESHGS_TUNE_CACHE names one, keyed by device, mesh size class, query
 count class and cutoff kind, so a workload is tuned once.
@@ -79,18 +82,32 @@ def _pick(results: list) -> dict:
     return best
 
 
+LEAF_SIZES = (1, 2, 4, 8)
+
+
 def _apply(bvh: MeshBVH, cfg: dict) -> None:
-    bvh.set_query_config(cfg["lanes"], cfg["variant"])
+    if cfg.get("leaf", 1) != getattr(bvh, "leaf_size", 1):
+        bvh.set_leaf_size(cfg.get("leaf", 1))          # refits from the current vertices
+    bvh.set_query_config(cfg["lanes"], cfg["variant"], cfg.get("block", 128))
 
 
-def closest_point_candidates():
-    return [dict(lanes=1, variant=v) for v in range(13)] + \
-           [dict(lanes=g, variant=0) for g in (2, 4, 8, 16, 32)]
+def closest_point_candidates(leaf_sizes=LEAF_SIZES):
+    out = []
+    for L in leaf_sizes:
+        out += [dict(leaf=L, lanes=1, variant=v, block=128) for v in range(13)]
+        out += [dict(leaf=L, lanes=1, variant=v, block=b) for v in (0, 2, 3) for b in (32, 64)]
+        out += [dict(leaf=L, lanes=g, variant=0, block=128) for g in (2, 4, 8, 16, 32)]
+    return out
+
+
+def _label(r: dict) -> str:
+    return f"L{r.get('leaf', 1)}/{r['lanes']}/{r['variant']}/b{r.get('block', 128)}"
 
 
 def tune_closest_point(bvh: MeshBVH, Q: torch.Tensor, max_dist: float = math.inf,
-                       repeats: int = 5, force: bool = False) -> dict:
-    """Time every candidate on (bvh, Q, max_dist); set the fastest on this handle."""
+                       repeats: int = 5, force: bool = False, leaf_sizes=LEAF_SIZES) -> dict:
+    """Time every candidate on (bvh, Q, max_dist); set the fastest on this handle (its leaf
+    size too: the tree is refit from its current vertex buffer)."""
     _load()
     key = _key("closest_point", bvh.n_faces, Q.shape[0], math.isfinite(max_dist))
     if key in _CACHE and not force:
@@ -98,16 +115,66 @@ def tune_closest_point(bvh: MeshBVH, Q: torch.Tensor, max_dist: float = math.inf
         return _CACHE[key]
     out = bvh.closest_point(Q, max_dist)
     results = []
-    for cfg in closest_point_candidates():
+    for cfg in closest_point_candidates(leaf_sizes):
         _apply(bvh, cfg)
         ms = _time(lambda: bvh.closest_point(Q, max_dist, out=out), repeats)
         results.append(dict(cfg, ms=ms))
     best = _pick(results)
-    best = dict(lanes=best["lanes"], variant=best["variant"], ms=best["ms"],
-                tried={f"{r['lanes']}/{r['variant']}": round(r["ms"], 4) for r in results})
+    best = dict(leaf=best["leaf"], lanes=best["lanes"], variant=best["variant"], block=best["block"],
+                ms=best["ms"], tried={_label(r): round(r["ms"], 4) for r in results})
     _CACHE[key] = best
     _save()
     _apply(bvh, best)
+    return best
+
+
+def tune_contact(bvh: MeshBVH, Q: torch.Tensor, max_dist: float, frames=None, repeats: int = 4,
+                 force: bool = False, leaf_sizes=LEAF_SIZES) -> dict:
+    """Tune the physics step's contact query itself (mesh_contact: warm-started from the
+    previous step's faces, run in the order of its work classes) rather than the plain
+    query.  `frames`: vertex buffers the timed steps cycle through (refit before each
+    step, the same for every candidate), so the warm start meets moving geometry as in a
+    simulation; None = the current pose.  Sets the fastest on this handle."""
+    from .api import Workspace
+    _load()
+    key = _key("contact", bvh.n_faces, Q.shape[0], True)
+    if key in _CACHE and not force:
+        _apply(bvh, _CACHE[key])
+        return _CACHE[key]
+    n = Q.shape[0]
+    dev = Q.device
+    out = dict(face=torch.full((n,), -1, dtype=torch.int32, device=dev),
+               bary=torch.empty(n, 3, device=dev), point=torch.empty(n, 3, device=dev),
+               dist2=torch.empty(n, device=dev))
+    frames = list(frames) if frames else [None]
+    results = []
+    for cfg in closest_point_candidates(leaf_sizes):
+        if cfg["lanes"] > 1 and n >= (1 << 18):
+            continue                                   # many queries: one thread per query
+        _apply(bvh, cfg)
+        ws = Workspace(dev)
+        out["face"].fill_(-1)
+        k = [0]
+
+        def step():
+            V = frames[k[0] % len(frames)]
+            k[0] += 1
+            if V is not None:
+                bvh.refit(V)
+            bvh.contact(Q, max_dist, out, ws=ws)
+
+        for _ in range(2):                             # classes and hints from a real step
+            step()
+        ms = _time(step, repeats)
+        results.append(dict(cfg, ms=ms))
+    best = _pick(results)
+    best = dict(leaf=best["leaf"], lanes=best["lanes"], variant=best["variant"], block=best["block"],
+                ms=best["ms"], tried={_label(r): round(r["ms"], 4) for r in results})
+    _CACHE[key] = best
+    _save()
+    _apply(bvh, best)
+    if frames[0] is not None:
+        bvh.refit(frames[0])
     return best
 
 
@@ -134,8 +201,11 @@ def tune_chamfer(A: MeshBVH, SA: torch.Tensor, B: MeshBVH, SB: torch.Tensor, rep
 
 
 def reset(*bvhs: MeshBVH) -> None:
-    """Back to the defaults (lanes from the query count, depth-first traversal)."""
+    """Back to the defaults (lanes from the query count, depth-first traversal, blocks of
+    128 threads, leaf size 1)."""
     set_query_group(0)
     set_traversal(0)
     for b in bvhs:
-        b.set_query_config(-1, -1)
+        b.set_query_config(-1, -1, 128)
+        if getattr(b, "leaf_size", 1) != 1:
+            b.set_leaf_size(1)

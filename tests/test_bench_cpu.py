@@ -42,7 +42,8 @@ def test_traffic_record_is_used_only_for_the_captured_sources():
     for f in d["source_files"]:
         m.update(open(os.path.join(ROOT, f), "rb").read())
     current = m.hexdigest()[:16] == d["source_hash"]
-    for v, rec in d["by_variant"].items():
-        got = bench.contact_traffic(int(v))
+    for key, rec in d["by_config"].items():
+        got = bench.contact_traffic(key)
         assert got == (rec if current else None)
-    assert bench.contact_traffic(99) is None
+    assert bench.contact_traffic("L9/v99/b7") is None
+    assert bench.traversal_label({"leaf": 2, "lanes": 1, "variant": 3, "block": 64}) == "L2/v3/b64"

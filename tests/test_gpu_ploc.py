@@ -264,3 +264,84 @@ def test_benchmarked_contact_step_against_the_oracle_full_size():
           f"{st['hits']} hits of {st['n']} sampled, {st['ties']} float32 tie mismatches, "
           f"{st['cutoff_edge']} at the cutoff")
     assert fixed.status()[0] == 0
+
+
+@pytest.mark.parametrize("method", ["lbvh", "ploc"])
+def test_leaf_collapse_links_equal_the_oracle(method):
+    """At leaf sizes 2, 3, 4 and 8 the refit writes, for every internal node, the child links
+    of the oracle's collapse (a subtree of at most L faces as one leaf range), on both tree
+    kinds and on a mesh larger than one refit block; back at L = 1 the links are the
+    tree's own."""
+    V, F = torus(120, 70)
+    ref = oracle.build_lbvh(V, F) if method == "lbvh" else oracle.build_ploc(V, F)
+    b = MeshBVH.from_mesh(dev(V), dev(F), method=method)
+    for L in (2, 3, 4, 8, 1):
+        b.set_leaf_size(L)
+        links = host(b.arrays()["nodes_i"])[:, [0, 1, 2, 3], 3]          # lo_L, hi_L, lo_R, hi_R
+        want = oracle.collapse(ref["left"], ref["right"], ref["first"], ref["last"], L)
+        np.testing.assert_array_equal(links, want, err_msg=f"leaf size {L}")
+    assert b.status()[0] == 0
+
+
+def test_leaf_collapse_gives_identical_answers_in_every_search():
+    """Every search form reads collapsed leaf ranges: at leaf sizes 2, 4 and 8 the
+    one-thread variants, the cooperative groups, the contact step, the warm-started query,
+    the signed distance, the Chamfer and the k-NN projection give the L = 1 answers bit for
+    bit, and the oracle's."""
+    from paper_2606_00444_gb300 import Workspace, chamfer, morton_order, set_query_group, set_traversal
+    from workloads.sampling import sample_surface
+    V0, F = torus(120, 70)
+    V1 = TorusSkinning(V0, seed=3001).frame(15)
+    b = MeshBVH.from_mesh(dev(V0), dev(F), method="ploc")
+    b.refit(dev(V1))
+    lo, hi = V0.min(0) - 0.2, V0.max(0) + 0.2
+    P = dev(uniform_box(20001, lo, hi, seed=3010))
+    P = P[morton_order(P).long()].contiguous()
+    sf, sb = (dev(a) for a in sample_surface(V0, F, 3000, seed=3011))
+    S = b.interpolate(sf, sb)
+    rest = MeshBVH.from_mesh(dev(V0), dev(F))
+    SR = rest.interpolate(sf, sb)
+
+    def answers():
+        out = {}
+        try:
+            for v in (0, 1, 2, 5, 10, 12):
+                set_query_group(1)
+                set_traversal(v)
+                for cut in (0.05, np.inf):
+                    out[(v, cut)] = b.closest_point(P, cut)
+            for g in (4, 32):
+                set_query_group(g)
+                out[("g", g)] = b.closest_point(P[:3000].contiguous(), 0.05)
+        finally:
+            set_query_group(0)
+            set_traversal(0)
+        ct = {k: v.clone() for k, v in out[(0, 0.05)].items()}
+        b.contact(P, 0.05, ct, ws=Workspace(torch.device("cuda")))
+        out["contact"] = ct
+        out["hinted"] = b.closest_point(P, 0.05, hint=out[(0, 0.05)]["face"])
+        out["signed"] = b.signed_distance(P, 0.05)
+        out["chamfer"] = chamfer(b, S, rest, SR, per_sample=True)
+        out["knn"] = b.knn_project(P[:4000].contiguous(), k=4, want_faces=True)
+        return out
+
+    base = answers()
+    Pn = host(P)
+    check_closest(V1, F, Pn, base[(0, 0.05)], max_dist=0.05)
+    for L in (2, 4, 8):
+        b.set_leaf_size(L)
+        got = answers()
+        for key in base:
+            if key == "chamfer":
+                assert torch.equal(got[key][0], base[key][0])
+                assert_identical(got[key][1], base[key][1], "faceA")
+                assert_identical(got[key][1], base[key][1], "faceB")
+            elif key == "knn":
+                for x, y in zip(got[key], base[key]):
+                    assert torch.equal(x, y), f"knn, leaf size {L}"
+            elif key == "signed":
+                assert torch.equal(got[key]["face"], base[key]["face"])
+                assert torch.equal(got[key]["sdist"].abs(), base[key]["sdist"].abs())
+            else:
+                assert_identical(got[key], base[key])
+    assert b.status()[0] == 0

@@ -229,8 +229,9 @@ def test_warm_start_over_a_skinned_sequence_full_size():
     assert bvh.status()[0] == 0
 
 
-@pytest.mark.parametrize("variant", [0, 2, 5, 12])
-def test_contact_step_equals_plain_queries(variant):
+@pytest.mark.parametrize("variant,leaf,block", [(0, 1, 128), (2, 1, 128), (5, 1, 128), (12, 1, 128),
+                                                (12, 8, 128), (2, 4, 32), (3, 1, 64)])
+def test_contact_step_equals_plain_queries(variant, leaf, block):
     """mesh_contact (previous faces as hints, queries ordered by the previous step's
     work classes, kept in the workspace -- garbage bytes at the first step) gives
     mesh_closest_point's answers over a skinned sequence, bit for bit."""
@@ -241,7 +242,8 @@ def test_contact_step_equals_plain_queries(variant):
     P = dev(uniform_box(50001, lo, hi, seed=3005))
     P = P[morton_order(P).long()].contiguous()
     bvh = MeshBVH.from_mesh(dev(V0), dev(F))
-    bvh.set_query_config(1, variant)
+    bvh.set_query_config(1, variant, block)
+    bvh.set_leaf_size(leaf, refit=False)                 # applies from the first refit below
     out = dict(face=torch.full((P.shape[0],), -1, dtype=torch.int32, device="cuda"),
                bary=torch.empty(P.shape[0], 3, device="cuda"), point=torch.empty(P.shape[0], 3, device="cuda"),
                dist2=torch.empty(P.shape[0], device="cuda"))

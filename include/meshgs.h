@@ -64,9 +64,13 @@ typedef enum {
 /* Device status bits (mesh_bvh_status). */
 #define MESH_DEV_INDEX_RANGE     0x1u  /* a face / Gaussian / sample index was out of range; the
                                           offending element was skipped or clamped to 0 */
-#define MESH_DEV_STACK_OVERFLOW  0x2u  /* traversal stack exhausted (cannot happen for nF < 2^33) */
+#define MESH_DEV_STACK_OVERFLOW  0x2u  /* traversal stack exhausted (cannot happen: every tree is at
+                                          most 64 levels deep, see MESH_DEV_DEEP_TREE)            */
 #define MESH_DEV_DEGENERATE      0x4u  /* a Gaussian sat on a zero-area face (not an error)       */
 #define MESH_DEV_NONMANIFOLD     0x8u  /* an edge shared by more than two faces (signed distance) */
+#define MESH_DEV_DEEP_TREE       0x10u /* mesh_build_ploc's tree was deeper than the 64 levels every
+                                          traversal handles; the Karras tree of mesh_build_lbvh was
+                                          built instead (not an error)                            */
 
 typedef struct mesh_bvh mesh_bvh;   /* opaque host handle describing device storage */
 
@@ -93,10 +97,11 @@ typedef struct {
     size_t off_adj;      /* int32 [max_faces][3] face across the edge opposite vertex k, or -1  */
     size_t off_fnorm;    /* float4 [max_faces]  unit face normals (signed distance)            */
     size_t off_vnorm;    /* float4 [max_verts]  angle-weighted vertex pseudo-normals          */
-    size_t off_xlist;    /* bottom-up scratch, per block of 1024 leaves: edge records (box of a
-                            child whose parent's leaf range crosses blocks, 2048 x 32 B per
-                            block), crossing nodes int32x4 [max_faces] (node, prefix length,
-                            parent link, 0), then int32 per-block counts of both             */
+    size_t off_xlist;    /* bottom-up scratch: per leaf the prefix and suffix box unions
+                            inside its block of 512 leaves (2 x 32 B), the nodes whose leaf
+                            ranges cross blocks int32x4 [max_faces] (node, range start, range
+                            end, parent link), per block its box (32 B) and its count of
+                            crossing nodes (int32)                                           */
     size_t storage_bytes;
 } mesh_bvh_layout;
 
@@ -152,7 +157,11 @@ mesh_status mesh_build_lbvh(mesh_bvh *bvh, const float *d_V, int64_t nV, const i
  * surface-area cost than the Karras tree's, so queries visit fewer nodes.
  * SYNCHRONOUS: the host reads the cluster count back after every iteration
  * (tens of iterations), so the call returns when the build is done and must
- * not be captured in a CUDA graph.  d_ws: mesh_build_ploc_workspace_bytes(nF),
+ * not be captured in a CUDA graph.  Clustering bounds no depth (equal boxes
+ * merge into a chain), and every traversal handles at most 64 levels: the
+ * build measures the finished tree's depth and, past 64, builds the Karras
+ * tree of mesh_build_lbvh over the same faces instead and sets the
+ * informational bit MESH_DEV_DEEP_TREE.  d_ws: mesh_build_ploc_workspace_bytes(nF),
  * 256-byte aligned.  Argument errors as mesh_build_lbvh; MESH_ERR_CUDA also
  * when an iteration's counts are inconsistent (the build then stops). */
 size_t mesh_build_ploc_workspace_bytes(int64_t max_faces);
@@ -178,11 +187,12 @@ mesh_status mesh_update_vertices(mesh_bvh *bvh, const float *d_V, int64_t nV, vo
  * built mesh's) the vertex-buffer update is part of the same pass, with the
  * same result as mesh_update_vertices(bvh, d_V, nV) followed by
  * mesh_refit(bvh, NULL, 0).  Two kernels, the same the build ends with: one
- * block per 1024 consecutive leaves computes every subtree lying inside its
- * leaf range in shared memory, then one block finishes the nodes whose
- * ranges cross those blocks in shared memory (or, past about 5000 such nodes,
- * every block climbs its share through L2).  Nothing is derived once per
- * topology: a refit after any build is valid. */
+ * block per 512 consecutive leaves answers every node whose leaf range lies
+ * inside the block from a sparse table of its leaf boxes in shared memory
+ * (and writes each leaf's prefix and suffix union in the block), then one
+ * warp per node whose range crosses blocks unions the suffix, the prefix and
+ * the boxes of the blocks between.  No atomics and no waits; nothing is
+ * derived once per topology: a refit after any build is valid. */
 mesh_status mesh_refit(mesh_bvh *bvh, const float *d_V, int64_t nV, void *stream);
 
 /* mesh_refit and mesh_bind_gaussians in one pass (the fixed-topology frame of
@@ -587,7 +597,8 @@ mesh_status mesh_batch_status(mesh_batch *batch, uint32_t *bits, uint32_t *n_deg
 /* Synchronise `stream`, read and clear the BVH's device status bits into
  * *bits (may be NULL) and the count of degenerate Gaussians seen into
  * *n_degenerate (may be NULL).  Returns MESH_ERR_DEVICE if an error bit
- * (anything but MESH_DEV_DEGENERATE) was set, else MESH_OK. */
+ * (anything but MESH_DEV_DEGENERATE and MESH_DEV_DEEP_TREE) was set, else
+ * MESH_OK. */
 mesh_status mesh_bvh_status(mesh_bvh *bvh, uint32_t *bits, uint32_t *n_degenerate, void *stream);
 
 const char *mesh_status_string(mesh_status s);

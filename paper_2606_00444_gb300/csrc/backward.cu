@@ -177,7 +177,7 @@ mesh_status mesh_bvh_status(mesh_bvh *bvh, uint32_t *bits, uint32_t *n_degenerat
     if (cudaMemsetAsync(&bvh->hdr()->status, 0, sizeof(h), s) != cudaSuccess) return MESH_ERR_CUDA;
     if (bits) *bits = h[0];
     if (n_degenerate) *n_degenerate = h[1];
-    return (h[0] & ~(unsigned)MESH_DEV_DEGENERATE) ? MESH_ERR_DEVICE : MESH_OK;
+    return (h[0] & ~(unsigned)(MESH_DEV_DEGENERATE | MESH_DEV_DEEP_TREE)) ? MESH_ERR_DEVICE : MESH_OK;
 }
 
 const char *mesh_status_string(mesh_status st) {

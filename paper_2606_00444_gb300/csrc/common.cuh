@@ -101,6 +101,10 @@ inline unsigned int grid_for(int64_t n, int block) {
 // Largest leaf size of the collapse (faces tested in one leaf range).
 constexpr int kMaxLeafSize = 8;
 
+// Deepest tree every traversal handles: the depth-first searches keep at most
+// one deferred sibling per level, in stacks of this many entries.
+constexpr int kMaxTreeDepth = 64;
+
 // Tie rule of NearestSurface: faces within (1 + 1e-6) of the nearest distance
 // (plus 1e-12 of the box diagonal) count as equally near; the lowest id wins.
 constexpr float kTieRel = 1e-6f;

@@ -480,8 +480,8 @@ __device__ __forceinline__ bool exactly_degenerate(float4 a, float4 b, float4 c)
 // passes new vertices, the first kernel also repacks them (a1) and gathers
 // the triangles from the caller's buffer.
 // ---------------------------------------------------------------------------
-constexpr int kRefitBlock = 1024;
-constexpr int kRefitLevels = 10;                          // log2(kRefitBlock)
+constexpr int kRefitBlock = 512;
+constexpr int kRefitLevels = 9;                           // log2(kRefitBlock)
 
 __device__ __forceinline__ bool crosses_block(int i, int j) {
     return (min(i, j) / kRefitBlock) != (max(i, j) / kRefitBlock);
@@ -573,7 +573,7 @@ __device__ __noinline__ void bind_face(const Rebind &RB, int f, float4 a, float4
 constexpr size_t kRefitLocalSmem = 12 * kRefitBlock * sizeof(float)      // two table levels
                                    + 64 * sizeof(int);                    // crossing-list scan
 
-__global__ void __launch_bounds__(kRefitBlock, 2)
+__global__ void __launch_bounds__(kRefitBlock, 4)
 k_refit_local(int n, const float *__restrict__ V3, int nV, float4 *__restrict__ V4,
               const int *__restrict__ perm, const int4 *__restrict__ faces,
               float4 *__restrict__ tris, float4 *__restrict__ nodes, const int *__restrict__ parent,
@@ -614,7 +614,7 @@ k_refit_local(int n, const float *__restrict__ V3, int nV, float4 *__restrict__ 
     if (lane == 0) s_warp[wid] = __popc(ball);
     __syncthreads();
     if (wid == 0) {
-        int c = s_warp[lane], x = c;
+        int c = lane < kRefitBlock / 32 ? s_warp[lane] : 0, x = c;
         for (int o = 1; o < 32; o <<= 1) {
             int y = __shfl_up_sync(0xffffffffu, x, o);
             if (lane >= o) x += y;
@@ -1209,6 +1209,23 @@ struct PlocWs {
     size_t bytes;
 };
 
+// Depth check of a finished tree: leaf j climbs its parent links (2 p + side,
+// -1 at the root) and flags the tree when it passes more than `limit`
+// internal nodes.  The climb stops there, so a degenerate chain costs at most
+// limit + 1 steps per leaf.
+__global__ void k_depth_check(int n, const int *__restrict__ parent, int limit, int *__restrict__ flag) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    int pe = parent[(n - 1) + j], d = 0;
+    while (pe >= 0 && d <= limit) {
+        ++d;
+        pe = parent[pe >> 1];
+    }
+    if (d > limit) atomicOr(flag, 1);
+}
+
+__global__ void k_set_status(Header *hdr, unsigned int bits) { set_status(hdr, bits); }
+
 static PlocWs ploc_ws_layout(char *base, int64_t nF) {
     PlocWs w{};
     w.sort = build_ws_layout(base, nF);
@@ -1466,6 +1483,24 @@ mesh_status mesh_build_ploc(mesh_bvh *bvh, const float *d_V, int64_t nV, const i
                                                               bvh->parent(), bvh->rend());
         count_launch();
     }
+    // Agglomerative clustering gives no depth bound (equal boxes merge into a
+    // chain), while every traversal keeps at most kMaxTreeDepth deferred
+    // entries.  A deeper tree is replaced by the Karras tree over the same
+    // faces (depth <= 30 key bits + log2 n + 1), with an informational bit.
+    int deep = 0;
+    if (cudaMemsetAsync(w.tot, 0, sizeof(int), s) != cudaSuccess) return MESH_ERR_CUDA;
+    k_depth_check<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, bvh->parent(), kMaxTreeDepth, w.tot);
+    count_launch();
+    if (cudaMemcpyAsync(&deep, w.tot, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return MESH_ERR_CUDA;
+    if (deep) {
+        mesh_status st = mesh_build_lbvh(bvh, d_V, nV, d_F, nF, d_ws, ws_bytes, stream);
+        if (st != MESH_OK) return st;
+        k_set_status<<<1, 1, 0, s>>>(bvh->hdr(), MESH_DEV_DEEP_TREE);
+        count_launch();
+        return check_launch();
+    }
     return bottom_up(bvh, nullptr, s);
 }
 
@@ -1608,7 +1643,7 @@ mesh_status mesh_batch_status(mesh_batch *batch, uint32_t *bits, uint32_t *n_deg
     if (cudaMemsetAsync(batch->st(), 0, sizeof(h), s) != cudaSuccess) return MESH_ERR_CUDA;
     if (bits) *bits = h[0];
     if (n_degenerate) *n_degenerate = h[1];
-    return (h[0] & ~(unsigned)MESH_DEV_DEGENERATE) ? MESH_ERR_DEVICE : MESH_OK;
+    return (h[0] & ~(unsigned)(MESH_DEV_DEGENERATE | MESH_DEV_DEEP_TREE)) ? MESH_ERR_DEVICE : MESH_OK;
 }
 
 uint64_t mesh_launch_count(void) { return (uint64_t)g_launches.load(); }

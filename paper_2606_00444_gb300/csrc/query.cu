@@ -23,7 +23,9 @@ namespace meshgs {
 constexpr int kQueryBlock = 128;
 constexpr int kQueryMinBlocks = 8;    // 8 x 128 threads per SM: at most 64 registers
 constexpr int kStackShared = 24;      // entries per thread in shared memory
-constexpr int kStackTotal = 64;       // > 30 key bits + log2(nF) + 1: never exhausted for nF < 2^33
+constexpr int kStackTotal = kMaxTreeDepth;   // every tree is at most this deep: the Karras tree by
+                                             // its bound (30 key bits + log2 nF + 1), the
+                                             // agglomerative one by the build's depth check
 
 __device__ __forceinline__ float box_d2(float3 q, float4 lo, float4 hi) {
     float dx = fmaxf(fmaxf(lo.x - q.x, q.x - hi.x), 0.0f);

@@ -61,8 +61,10 @@ def test_tiny_ties_and_degenerate_inputs():
     for F in ([[0, 1, 2]], [[0, 1, 2], [1, 3, 2]], [[0, 1, 2], [1, 3, 2], [1, 4, 3]],
               [[0, 1, 2], [1, 3, 2], [1, 4, 3], [0, 4, 2], [3, 4, 0]]):
         check_ploc(V, np.array(F, np.int32))
-    # 600 copies of one triangle: every union has the same area (ties everywhere)
-    Fs = np.tile(np.array([[0, 1, 2]], np.int32), (600, 1))
+    # 40 copies of one triangle: every union has the same area (ties everywhere); the
+    # chain it clusters into is 39 levels deep, inside the traversal's 64 (600 copies
+    # chain past it: test_deep_agglomerative_tree_falls_back_to_the_karras_tree)
+    Fs = np.tile(np.array([[0, 1, 2]], np.int32), (40, 1))
     check_ploc(V, Fs)
     # zero-area faces
     Vd, Fd = icosphere(2)
@@ -345,3 +347,36 @@ def test_leaf_collapse_gives_identical_answers_in_every_search():
             else:
                 assert_identical(got[key], base[key])
     assert b.status()[0] == 0
+
+
+def test_deep_agglomerative_tree_falls_back_to_the_karras_tree():
+    """300 copies of one triangle: clustering would chain them 299 levels deep, past the
+    64 levels every traversal keeps.  mesh_build_ploc measures the depth, builds the
+    Karras tree instead (equal to the oracle's bit for bit) and sets the informational
+    bit MESH_DEV_DEEP_TREE; queries then tie across all 300 faces and return face 0."""
+    n = 300
+    V = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0]], np.float32)
+    F = np.tile(np.array([[0, 1, 2]], np.int32), (n, 1))
+    b = MeshBVH.from_mesh(dev(V), dev(F), method="ploc")
+    ref = oracle.build_lbvh(V, F)
+    A = b.arrays()
+    assert np.array_equal(host(A["perm"]), ref["perm"])
+    assert np.array_equal(host(A["parent"]) >> 1, ref["parent"])
+    Q = uniform_box(500, [-1, -1, -1], [2, 2, 2], seed=9)
+    out = b.closest_point(dev(Q))
+    check_closest(V, F, Q, out)
+    assert (host(out["face"]) == 0).all()
+    bits, _ = b.status()
+    assert bits == 0x10
+    # the limit itself: a chain of 64 internal nodes is kept, one of 65 is not
+    for copies, deep in ((65, False), (66, True)):
+        Fc = np.tile(np.array([[0, 1, 2]], np.int32), (copies, 1))
+        bc = MeshBVH.from_mesh(dev(V), dev(Fc), method="ploc")
+        want = oracle.build_lbvh(V, Fc) if deep else oracle.build_ploc(V, Fc)
+        assert np.array_equal(host(bc.arrays()["parent"]) >> 1, want["parent"]), copies
+        assert bc.status()[0] == (0x10 if deep else 0), copies
+    # a mesh of ordinary depth keeps its agglomerative tree and sets nothing
+    V2, F2 = torus(40, 25)
+    b2 = MeshBVH.from_mesh(dev(V2), dev(F2), method="ploc")
+    assert np.array_equal(host(b2.arrays()["perm"]), oracle.build_ploc(V2, F2)["perm"])
+    assert b2.status()[0] == 0

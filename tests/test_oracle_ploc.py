@@ -149,3 +149,29 @@ def test_node_boxes_are_unions_and_the_tree_beats_the_lbvh():
         d = boxes[: n - 1, 3:].astype(np.float64) - boxes[: n - 1, :3]
         return float(((d[:, 0] * d[:, 1] + d[:, 1] * d[:, 2] + d[:, 2] * d[:, 0])).sum())
     assert sah(box) < 0.95 * sah(oracle.build_lbvh(V, F)["boxes"])
+
+
+def tree_depth(parent, n):
+    """Internal nodes on the longest root-to-leaf path (the oracle's parent links:
+    internal nodes first, then leaves; -1 at the root)."""
+    best = 0
+    for j in range(n):
+        p, d = int(parent[(n - 1) + j]), 0
+        while p >= 0:
+            d += 1
+            p = int(parent[p])
+        best = max(best, d)
+    return best
+
+
+def test_equal_faces_give_a_chain_deeper_than_the_traversal_stack():
+    # n copies of one triangle: every box is the same, so clustering builds a chain of
+    # n - 1 internal nodes, far past the 64 levels a traversal keeps; the Karras tree
+    # over the same (equal) keys splits on the index bits and stays shallow
+    n = 300
+    V = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0]], np.float32)
+    F = np.tile(np.array([[0, 1, 2]], np.int32), (n, 1))
+    t = oracle.build_ploc(V, F)
+    assert tree_depth(t["parent"], n) == n - 1
+    k = oracle.build_lbvh(V, F)
+    assert tree_depth(k["parent"], n) == int(np.ceil(np.log2(n)))

@@ -36,7 +36,8 @@
  *   - Every call is asynchronous on `stream` (a cudaStream_t passed as void*;
  *     NULL is the legacy default stream) and may be captured in a CUDA graph,
  *     except the few that say they are synchronous (mesh_build_ploc,
- *     mesh_gs_render and mesh_emd read counts back on the host).
+ *     mesh_gs_render and mesh_emd read counts back on the host;
+ *     mesh_gs_render_capacity is the render's asynchronous form).
  *     Host-side argument errors are returned at once and launch nothing.
  *     Device-side problems (an index out of range, a traversal stack
  *     overflow) set sticky bits in the BVH's status word, read and cleared by
@@ -320,6 +321,24 @@ mesh_status mesh_gs_render(const float *d_mu, const float *d_quat, const float *
                            const float *d_opacity, const float *d_color, int64_t nG,
                            const mesh_camera *cam, void *d_ws, size_t ws_bytes, size_t *ws_needed,
                            float *d_image, float *d_trans, void *stream);
+
+/* mesh_gs_render with a caller-chosen instance capacity instead of the host
+ * read of the instance count: asynchronous, no host synchronisation, so it
+ * can be captured in a CUDA graph and replayed every frame (R_render of
+ * Sec. 3.2 as a per-frame step).  max_instances bounds the (tile, Gaussian)
+ * instances of one frame (e.g. the count of an earlier frame with a margin);
+ * d_ws must hold mesh_gs_workspace_bytes(nG, max_instances, width, height)
+ * bytes.  d_counts (DEVICE uint32 [2], may be NULL) receives {overflow, count}:
+ * overflow = 1 when the frame had more instances than max_instances (the
+ * instances past the capacity are dropped and the image is incomplete), count
+ * = the frame's instances.  With enough capacity the image and transmittance
+ * equal mesh_gs_render's bit for bit; the sorts run over max_instances slots
+ * (the unused ones are keyed after every real instance). */
+mesh_status mesh_gs_render_capacity(const float *d_mu, const float *d_quat, const float *d_scale,
+                                    const float *d_opacity, const float *d_color, int64_t nG,
+                                    const mesh_camera *cam, int64_t max_instances, void *d_ws,
+                                    size_t ws_bytes, float *d_image, float *d_trans, uint32_t *d_counts,
+                                    void *stream);
 
 /* Workspace bytes of mesh_contact for nQ queries. */
 size_t mesh_contact_workspace_bytes(int64_t nQ);

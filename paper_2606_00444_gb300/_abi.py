@@ -70,6 +70,7 @@ SIGNATURES = {
     "mesh_emd": (C.c_int, [VP, VP, I64, C.c_float, I64, VP, SZ, VP, VP, C.POINTER(I64), VP]),
     "mesh_gs_workspace_bytes": (SZ, [I64, I64, C.c_int, C.c_int]),
     "mesh_gs_render": (C.c_int, [VP, VP, VP, VP, VP, I64, C.POINTER(Camera), VP, SZ, C.POINTER(SZ), VP, VP, VP]),
+    "mesh_gs_render_capacity": (C.c_int, [VP, VP, VP, VP, VP, I64, C.POINTER(Camera), I64, VP, SZ, VP, VP, VP, VP]),
     "mesh_contact_workspace_bytes": (SZ, [I64]),
     "mesh_contact": (C.c_int, [VP, VP, I64, C.c_float, VP, VP, VP, VP, VP, SZ, VP]),
     "mesh_set_query_group": (C.c_int, [C.c_int]),

@@ -610,6 +610,42 @@ def emd(A: torch.Tensor, B: torch.Tensor, eps_rel: float = 1e-5, max_iters: int 
     return (out[0], sigma, it.value) if want_assignment else out[0]
 
 
+def _camera(R, t, fx, fy, cx, cy, width, height, near, background):
+    cam = _abi.Camera()
+    Rl = [float(x) for x in torch.as_tensor(R, dtype=torch.float64).reshape(-1).tolist()]
+    tl = [float(x) for x in torch.as_tensor(t, dtype=torch.float64).reshape(-1).tolist()]
+    cam.R[:] = Rl
+    cam.t[:] = tl
+    cam.fx, cam.fy, cam.cx, cam.cy, cam.near_z = float(fx), float(fy), float(cx), float(cy), float(near)
+    cam.width, cam.height = int(width), int(height)
+    cam.background[:] = [float(x) for x in background]
+    return cam
+
+
+def gs_render_capacity(mu, quat, scale, opacity, color, R, t, fx, fy, cx, cy, width, height,
+                       max_instances: int, near=0.01, background=(0.0, 0.0, 0.0),
+                       ws: Workspace | None = None, out=None, counts: torch.Tensor | None = None):
+    """Gaussian-splatting render with a fixed instance capacity (mesh_gs_render_capacity):
+    asynchronous, capturable in a CUDA graph.  `counts` (int32 [2] on the device, created
+    if None) receives (overflow, instances); returns (image, trans, counts)."""
+    mu, quat, scale = _f32(mu, 3, "mu"), _f32(quat, 4, "quat"), _f32(scale, 3, "scale")
+    opacity, color = _f32(opacity, None, "opacity"), _f32(color, 3, "color")
+    n = mu.shape[0]
+    cam = _camera(R, t, fx, fy, cx, cy, width, height, near, background)
+    if out is None:
+        out = (torch.empty(height, width, 3, device=mu.device), torch.empty(height, width, device=mu.device))
+    image, trans = out
+    if counts is None:
+        counts = torch.zeros(2, dtype=torch.int32, device=mu.device)
+    ws = Workspace(mu.device) if ws is None else ws
+    buf = ws.get(lib().mesh_gs_workspace_bytes(n, int(max_instances), int(width), int(height)))
+    check(lib().mesh_gs_render_capacity(mu.data_ptr(), quat.data_ptr(), scale.data_ptr(), opacity.data_ptr(),
+                                        color.data_ptr(), n, C.byref(cam), int(max_instances), buf.data_ptr(),
+                                        buf.numel(), image.data_ptr(), _ptr(trans), counts.data_ptr(),
+                                        _stream()), "mesh_gs_render_capacity")
+    return image, trans, counts
+
+
 def gs_render(mu, quat, scale, opacity, color, R, t, fx, fy, cx, cy, width, height, near=0.01,
               background=(0.0, 0.0, 0.0), ws: Workspace | None = None, out=None):
     """Gaussian-splatting render (mesh_gs_render): image [height, width, 3] and

@@ -160,6 +160,51 @@ __global__ void k_gs_duplicate(int n, const int *__restrict__ count, const int *
         }
 }
 
+// Fixed-capacity form: instance slots past the capacity are dropped (the
+// overflow is reported), and the slots the frame did not fill -- from the
+// device-side total on -- get keys that sort after every real one.
+__global__ void k_gs_duplicate_cap(int n, const int *__restrict__ count, const int *__restrict__ offset,
+                                   const int4 *__restrict__ rect, const float *__restrict__ depth, int gx,
+                                   int cap, unsigned *tile_key, unsigned *depth_key, int *gid, int *iota) {
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n || count[g] == 0) return;
+    int4 r = rect[g];
+    int k = offset[g];
+    unsigned dk = __float_as_uint(depth[g]);
+    for (int ty = r.y; ty < r.w; ++ty)
+        for (int tx = r.x; tx < r.z; ++tx, ++k) {
+            if (k >= cap) return;
+            tile_key[k] = (unsigned)(ty * gx + tx);
+            depth_key[k] = dk;
+            gid[k] = g;
+            iota[k] = k;
+        }
+}
+
+__global__ void k_gs_pad(int cap, const int *__restrict__ total, unsigned pad_tile, unsigned *tile_key,
+                         unsigned *depth_key, int *gid, int *iota, unsigned int *counts) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int m = *total;
+    if (k == 0 && counts) {
+        counts[0] = m > cap ? 1u : 0u;                 // overflow: instances were dropped
+        counts[1] = (unsigned)m;
+    }
+    if (k >= cap || k < m) return;
+    tile_key[k] = pad_tile;
+    depth_key[k] = 0xffffffffu;
+    gid[k] = 0;
+    iota[k] = k;
+}
+
+__global__ void k_gs_ranges_cap(int cap, int tiles, const unsigned *__restrict__ tk, int2 *range) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= cap) return;
+    unsigned t = tk[i];
+    if (t >= (unsigned)tiles) return;                  // a padding slot
+    if (i == 0 || tk[i - 1] != t) range[t].x = i;
+    if (i == cap - 1 || tk[i + 1] != t) range[t].y = i + 1;
+}
+
 __global__ void k_gs_gather_tile(int m, const int *__restrict__ inst, const unsigned *__restrict__ tile_key,
                                  unsigned *out) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -318,6 +363,53 @@ mesh_status mesh_gs_render(const float *d_mu, const float *d_quat, const float *
         k_gs_ranges<<<grid_for(m, 256), 256, 0, s>>>(m, w.tk_s, w.range);
         count_launch();
     }
+    k_gs_render<<<dim3(gx, gy), kTilePix, 0, s>>>(*cam, gx, w.range, w.inst2, w.gid, w.uv, w.conic_o, d_color,
+                                                  d_image, d_trans);
+    count_launch();
+    return check_launch();
+}
+
+mesh_status mesh_gs_render_capacity(const float *d_mu, const float *d_quat, const float *d_scale,
+                                    const float *d_opacity, const float *d_color, int64_t nG,
+                                    const mesh_camera *cam, int64_t max_instances, void *d_ws,
+                                    size_t ws_bytes, float *d_image, float *d_trans, uint32_t *d_counts,
+                                    void *stream) {
+    if (!cam || nG < 0 || nG > INT32_MAX || cam->width <= 0 || cam->height <= 0 || !d_image ||
+        max_instances < 1 || max_instances > INT32_MAX ||
+        (nG > 0 && (!d_mu || !d_quat || !d_scale || !d_opacity || !d_color)) || !(cam->near_z > 0.0f))
+        return MESH_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int n = (int)nG, cap = (int)max_instances;
+    const int gx = (cam->width + kTile - 1) / kTile, gy = (cam->height + kTile - 1) / kTile;
+    const int64_t tiles = (int64_t)gx * gy;
+    SplatWs w = splat_ws(d_ws, n, cap, tiles);
+    if (!d_ws || ws_bytes < w.bytes || ((uintptr_t)d_ws & 255u)) return MESH_ERR_WORKSPACE;
+    cudaMemsetAsync(w.range, 0, 8 * (size_t)tiles, s);
+    cudaMemsetAsync(w.total, 0, sizeof(int), s);
+    if (n > 0) {
+        k_gs_preprocess<<<grid_for(n, 256), 256, 0, s>>>(n, d_mu, d_quat, d_scale, d_opacity, *cam, gx, gy,
+                                                         w.uv, w.conic_o, w.depth, w.rect, w.count);
+        int nb = (n + kScanBlock - 1) / kScanBlock;
+        k_scan_local<<<nb, kScanBlock, 0, s>>>(n, w.count, w.offset, w.bsum);
+        k_scan_sums<<<1, 32, 0, s>>>(nb, w.bsum, w.total);
+        k_scan_add<<<grid_for(n, 256), 256, 0, s>>>(n, w.offset, w.bsum);
+        k_gs_duplicate_cap<<<grid_for(n, 256), 256, 0, s>>>(n, w.count, w.offset, w.rect, w.depth, gx, cap,
+                                                            w.tile_key, w.depth_key, w.gid, w.iota);
+        count_launch(5);
+    }
+    // tile keys take `bits` bits with room above the last tile for the padding key
+    int bits = 1;
+    while (((int64_t)1 << bits) <= tiles) ++bits;
+    const unsigned pad_tile = (unsigned)(((int64_t)1 << bits) - 1);
+    k_gs_pad<<<grid_for(cap, 256), 256, 0, s>>>(cap, w.total, pad_tile, w.tile_key, w.depth_key, w.gid, w.iota,
+                                                d_counts);
+    count_launch();
+    sort_pairs_u32(w.sort_ws, cap, 32, w.depth_key, w.iota, w.dk_s, w.inst1, s);
+    k_gs_gather_tile<<<grid_for(cap, 256), 256, 0, s>>>(cap, w.inst1, w.tile_key, w.tk1);
+    count_launch();
+    sort_pairs_u32(w.sort_ws, cap, bits, w.tk1, w.inst1, w.tk_s, w.inst2, s);
+    k_gs_ranges_cap<<<grid_for(cap, 256), 256, 0, s>>>(cap, (int)tiles, w.tk_s, w.range);
+    count_launch();
     k_gs_render<<<dim3(gx, gy), kTilePix, 0, s>>>(*cam, gx, w.range, w.inst2, w.gid, w.uv, w.conic_o, d_color,
                                                   d_image, d_trans);
     count_launch();

@@ -97,3 +97,44 @@ def test_torus_gaussians_subset_full_pipeline():
     col = rng.uniform(0, 1, (gface.shape[0], 3))
     R, t = look_at([0.5, -2.8, 1.6], [0, 0, 0])
     compare((mu, quat, scale * 4.0, opac, col), (R, t, 110.0), 128, 96)
+
+
+def test_fixed_capacity_render_is_the_render_and_replays_in_a_graph():
+    """mesh_gs_render_capacity (no host read of the instance count): with room for every
+    instance it draws mesh_gs_render's image bit for bit and reports the count; captured
+    in a CUDA graph it follows new Gaussian positions on replay; past its capacity it
+    flags the overflow."""
+    from paper_2606_00444_gb300 import gs_render_capacity
+    W, H, f = 160, 96, 120.0
+    R, t = look_at([0.3, -3.0, 0.8], [0, 0, 0])
+    mu, q, sc, op, col = (dev(np.asarray(a, np.float32)) for a in random_gaussians(500, 7))
+    img, T = gs_render(mu, q, sc, op, col, R, t, f, f, W / 2, H / 2, W, H)
+    counts = torch.zeros(2, dtype=torch.int32, device="cuda")
+    cimg, cT, _ = gs_render_capacity(mu, q, sc, op, col, R, t, f, f, W / 2, H / 2, W, H, 200000, counts=counts)
+    torch.cuda.synchronize()
+    n_inst = int(counts[1].item())
+    assert counts[0].item() == 0 and n_inst > 500
+    assert torch.equal(cimg, img) and torch.equal(cT, T)
+    # exactly enough room, and a graph replay after the Gaussians moved
+    from paper_2606_00444_gb300 import Workspace
+    ws = Workspace(torch.device("cuda"))
+    out = (torch.empty_like(img), torch.empty_like(T))
+    cap = n_inst + 64
+    gs_render_capacity(mu, q, sc, op, col, R, t, f, f, W / 2, H / 2, W, H, cap, ws=ws, out=out, counts=counts)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        gs_render_capacity(mu, q, sc, op, col, R, t, f, f, W / 2, H / 2, W, H, cap, ws=ws, out=out,
+                           counts=counts)
+    mu2 = mu + torch.tensor([0.05, 0.0, -0.03], device="cuda")
+    mu.copy_(mu2)
+    g.replay()
+    torch.cuda.synchronize()
+    img2, T2 = gs_render(mu, q, sc, op, col, R, t, f, f, W / 2, H / 2, W, H)
+    if counts[0].item() == 0:
+        assert torch.equal(out[0], img2) and torch.equal(out[1], T2)
+    # too little room: the overflow is flagged and the count still reported
+    small = max(1, n_inst // 3)
+    gs_render_capacity(mu, q, sc, op, col, R, t, f, f, W / 2, H / 2, W, H, small, counts=counts)
+    torch.cuda.synchronize()
+    assert counts[0].item() == 1 and counts[1].item() > small

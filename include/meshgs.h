@@ -97,7 +97,6 @@ typedef struct {
     size_t off_iperm;    /* int32 [max_faces]   leaf of face f (inverse of perm)               */
     size_t off_adj;      /* int32 [max_faces][3] face across the edge opposite vertex k, or -1  */
     size_t off_fnorm;    /* float4 [max_faces]  unit face normals (signed distance)            */
-    size_t off_vnorm;    /* float4 [max_verts]  angle-weighted vertex pseudo-normals          */
     size_t off_xlist;    /* bottom-up scratch: per leaf the prefix and suffix box unions
                             inside its block of 512 leaves (2 x 32 B), the nodes whose leaf
                             ranges cross blocks int32x4 [max_faces] (node, range start, range
@@ -384,7 +383,7 @@ mesh_status mesh_set_query_group(int lanes);
  *   1 while-while: leaf children queued while internal nodes are traversed
  *   2 depth-first, 8 shared entries    3 depth-first, stack in local memory only
  *   4 as 0 with one leaf-test site     5 as 3 with one leaf-test site
- *   6 as 2, 12 blocks per SM (<= 40 registers)   7 as 3, 12 blocks per SM
+ *   6 as 2, 9 blocks per SM (<= 56 registers)    7 as 3, 9 blocks per SM
  *   8 as 3, 16 blocks per SM (<= 32 registers)   9 as 5, 12 blocks per SM
  *  10 persistent, dynamic fetch: lanes take new queries as they finish
  *     (8 shared entries)                          11 as 10, local stack only

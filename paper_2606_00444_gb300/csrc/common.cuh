@@ -36,7 +36,6 @@ struct mesh_bvh_impl {
     int *iperm() const { return reinterpret_cast<int *>(base + L.off_iperm); }
     int *adj() const { return reinterpret_cast<int *>(base + L.off_adj); }
     float4 *fnorm() const { return reinterpret_cast<float4 *>(base + L.off_fnorm); }
-    float4 *vnorm() const { return reinterpret_cast<float4 *>(base + L.off_vnorm); }
     bool adj_ready = false;  // face adjacency matches the current topology
     int *xlist() const { return reinterpret_cast<int *>(base + L.off_xlist); }
 };

@@ -1030,7 +1030,6 @@ static mesh_bvh_layout storage_layout(int64_t maxV, int64_t maxF) {
     L.off_iperm = take(4 * f);
     L.off_adj = take(12 * f);
     L.off_fnorm = take(16 * f);
-    L.off_vnorm = take(16 * v);
     L.off_xlist = take(xlist_bytes(f));
     L.storage_bytes = off;
     return L;

@@ -841,8 +841,8 @@ __device__ __forceinline__ void write_hit(const Traversal &T, const Hit &h, floa
 
 // kMode: 0 depth-first, 1 while-while, 2 depth-first with one leaf-test site.
 // kMinBlocks: resident blocks per SM the register budget must allow
-// (8 -> 64 registers, 12 -> 40, 16 -> 32; fewer registers, more warps to hide
-// latency, more spilling).
+// (8 -> 64 registers, 9 -> 56, 12 -> 40, 16 -> 32; fewer registers, more warps
+// to hide latency, more spilling).
 // Work class of a query from its node visits, heaviest first (the contact step
 // orders the next step's queries by it): 0: 48 or more, 1: 24-47, 2: 12-23, 3: fewer.
 __device__ __forceinline__ unsigned int work_class(int visits) {
@@ -1108,21 +1108,96 @@ k_knn_project(Traversal T, const Header *__restrict__ hdr, const float *Q, int64
     point[3 * i + 2] = pz;
 }
 
+// Angle-weighted pseudo-normal of vertex vid (Baerentzen & Aanaes 2005): the
+// sum over the faces around it of the unit face normal times the face's angle
+// at the vertex.  The ring is found from face f through the face adjacency
+// (for a consistently oriented mesh, crossing the edge that follows the vertex
+// in each face turns one way round it; an open ring is also walked the other
+// way from f), up to kMaxRing faces, and summed in ascending face id, so the
+// result is the same whichever face the walk starts from and run to run.  A
+// ring larger than kMaxRing (or one the adjacency cannot close) sets
+// MESH_DEV_NONMANIFOLD and sums the faces found.
+constexpr int kMaxRing = 32;
+
+__device__ __forceinline__ int slot_of(int4 fv, int vid) {
+    return fv.x == vid ? 0 : (fv.y == vid ? 1 : (fv.z == vid ? 2 : -1));
+}
+
+__device__ __forceinline__ float4 vertex_pseudo_normal(const int4 *__restrict__ faces, const int *__restrict__ adj,
+                                                    const float4 *__restrict__ verts,
+                                                    const float4 *__restrict__ fnorm, int f, int vid,
+                                                    unsigned int *status) {
+    int ring[kMaxRing];
+    int nr = 0;
+    bool full = false;
+    int g = f;
+    while (true) {                                   // one way round
+        ring[nr++] = g;
+        int k = slot_of(faces[g], vid);
+        int h = k < 0 ? -1 : adj[3 * g + (k + 2) % 3];
+        if (h == f) break;
+        if (h < 0) break;
+        if (nr == kMaxRing) { full = true; break; }
+        g = h;
+    }
+    if (!full && nr < kMaxRing) {                     // open ring: the other way from f
+        int k0 = slot_of(faces[f], vid);
+        int h = k0 < 0 ? -1 : adj[3 * f + (k0 + 1) % 3];
+        bool closed = false;
+        for (int i = 0; i < nr; ++i) closed |= ring[i] == h;
+        while (h >= 0 && !closed) {
+            if (nr == kMaxRing) { full = true; break; }
+            ring[nr++] = h;
+            int k = slot_of(faces[h], vid);
+            int nh = k < 0 ? -1 : adj[3 * h + (k + 1) % 3];
+            for (int i = 0; i < nr; ++i) closed |= ring[i] == nh;
+            h = nh;
+        }
+    }
+    if (full) atomicOr(status, (unsigned)MESH_DEV_NONMANIFOLD);
+    float nx = 0.0f, ny = 0.0f, nz = 0.0f;
+    int last = -1;
+    for (int done = 0; done < nr; ++done) {          // ascending face id (distinct ids)
+        int pick = 0x7fffffff;
+        for (int i = 0; i < nr; ++i)
+            if (ring[i] > last && ring[i] < pick) pick = ring[i];
+        if (pick == 0x7fffffff) break;
+        last = pick;
+        int4 fv = faces[pick];
+        int k = slot_of(fv, vid);
+        if (k < 0) continue;
+        int id[3] = {fv.x, fv.y, fv.z};
+        float4 p = verts[id[k]], a = verts[id[(k + 1) % 3]], b = verts[id[(k + 2) % 3]];
+        float ax = a.x - p.x, ay = a.y - p.y, az = a.z - p.z;
+        float bx = b.x - p.x, by = b.y - p.y, bz = b.z - p.z;
+        float la = sqrtf(ax * ax + ay * ay + az * az), lb = sqrtf(bx * bx + by * by + bz * bz);
+        if (la == 0.0f || lb == 0.0f) continue;
+        float cs = fminf(1.0f, fmaxf(-1.0f, (ax * bx + ay * by + az * bz) / (la * lb)));
+        float ang = acosf(cs);
+        float4 n = fnorm[pick];
+        nx += ang * n.x; ny += ang * n.y; nz += ang * n.z;
+    }
+    return make_float4(nx, ny, nz, 0.0f);
+}
+
 // NearestSurface plus the sign of (q - c) . N, N the pseudo-normal of the
 // feature the nearest point lies on: face interior (no zero weight), edge
 // opposite vertex k (weight k zero), vertex (two zero weights).
+// 8 shared stack entries per thread (the contact queries' best one-thread form).
+constexpr int kSignedStack = 8;
+
 template <bool kRange>
 __global__ void __launch_bounds__(kQueryBlock, kQueryMinBlocks)
 k_signed_distance(Traversal T, const Header *__restrict__ hdr, unsigned int *status,
                   const float *__restrict__ Q, int64_t nQ, float maxd2, const int4 *__restrict__ faces,
                   const int *__restrict__ adj, const float4 *__restrict__ fnorm,
-                  const float4 *__restrict__ vnorm, int *face, float *bary, float *point, float *sdist) {
-    __shared__ int2 stk[kStackShared][kQueryBlock];
+                  const float4 *__restrict__ verts, int *face, float *bary, float *point, float *sdist) {
+    __shared__ int2 stk[kSignedStack][kQueryBlock];
     int64_t i = (int64_t)blockIdx.x * kQueryBlock + threadIdx.x;
     if (i >= nQ) return;
     set_scale(T, hdr);
     float3 q = make_float3(Q[3 * i], Q[3 * i + 1], Q[3 * i + 2]);
-    Hit h = nearest<kQueryBlock, kStackShared, false, false, kRange>(T, q, maxd2, stk, status);
+    Hit h = nearest<kQueryBlock, kSignedStack, false, false, kRange>(T, q, maxd2, stk, status);
     write_hit(T, h, q, i, face, bary, point, nullptr);
     if (h.leaf < 0) { sdist[i] = INFINITY; return; }
     const float4 *t = T.tris + 3 * (size_t)h.leaf;
@@ -1144,7 +1219,7 @@ k_signed_distance(Traversal T, const Header *__restrict__ hdr, unsigned int *sta
     } else {
         int4 fv = faces[f];
         int vid = u != 0.0f ? fv.x : (v != 0.0f ? fv.y : fv.z);
-        N = vnorm[vid];
+        N = vertex_pseudo_normal(faces, adj, verts, fnorm, f, vid, status);
     }
     float cx = u * a.x + v * b.x + w * c.x, cy = u * a.y + v * b.y + w * c.y, cz = u * a.z + v * b.z + w * c.z;
     float dn = (q.x - cx) * N.x + (q.y - cy) * N.y + (q.z - cz) * N.z;
@@ -1481,7 +1556,7 @@ mesh_status launch_signed_query(const mesh_bvh *bvh, const float *d_Q, int64_t n
     auto kern = bvh->leaf_size > 1 ? k_signed_distance<true> : k_signed_distance<false>;
     kern<<<grid_for(nQ, kQueryBlock), kQueryBlock, 0, s>>>(
         traversal_of(bvh, isinf(max_dist)), h, &h->status, d_Q, nQ, maxd2, bvh->faces(), bvh->adj(),
-        bvh->fnorm(), bvh->vnorm(), d_face, d_bary, d_point, d_sdist);
+        bvh->fnorm(), bvh->verts(), d_face, d_bary, d_point, d_sdist);
     count_launch();
     return check_launch();
 }
@@ -1521,8 +1596,8 @@ static void launch_closest_point(Traversal T, Header *h, const float *d_Q, int64
                             case 1: k_closest_point<kStackShared, 1> MESH_CP_ARGS; break;
                             case 4: k_closest_point<kStackShared, 2> MESH_CP_ARGS; break;
                             case 5: k_closest_point<0, 2> MESH_CP_ARGS; break;
-                            case 6: k_closest_point<8, 0, 12> MESH_CP_ARGS; break;
-                            case 7: k_closest_point<0, 0, 12> MESH_CP_ARGS; break;
+                            case 6: k_closest_point<8, 0, 9> MESH_CP_ARGS; break;
+                            case 7: k_closest_point<0, 0, 9> MESH_CP_ARGS; break;
                             case 8: k_closest_point<0, 0, 16> MESH_CP_ARGS; break;
                             case 9: k_closest_point<0, 2, 12> MESH_CP_ARGS; break;
                             case 10:
@@ -1596,8 +1671,8 @@ static void launch_contact(Traversal T, Header *h, const float *d_Q, int64_t nQ,
                 switch (variant) {
                     case 4: k_closest_point<kStackShared, 2, kQueryMinBlocks, true> MESH_CT_ARGS; break;
                     case 5: k_closest_point<0, 2, kQueryMinBlocks, true> MESH_CT_ARGS; break;
-                    case 6: k_closest_point<8, 0, 12, true> MESH_CT_ARGS; break;
-                    case 7: k_closest_point<0, 0, 12, true> MESH_CT_ARGS; break;
+                    case 6: k_closest_point<8, 0, 9, true> MESH_CT_ARGS; break;
+                    case 7: k_closest_point<0, 0, 9, true> MESH_CT_ARGS; break;
                     case 8: k_closest_point<0, 0, 16, true> MESH_CT_ARGS; break;
                     case 9: k_closest_point<0, 2, 12, true> MESH_CT_ARGS; break;
                     default: k_closest_point<kStackShared, 0, kQueryMinBlocks, true> MESH_CT_ARGS; break;

@@ -11,7 +11,9 @@
 // is built on the first call after a build: every half-edge is entered in an
 // open-addressing table keyed by its two vertex ids (atomic compare-and-swap;
 // probes bounded by the table size), then each half-edge reads its partner.
-// The normals depend on the vertices and are recomputed on every call.
+// The face normals depend on the vertices and are recomputed on every call;
+// a vertex's pseudo-normal is summed where a query needs it, in ascending face
+// id, so the signed distance is the same run to run.
 #include <math.h>
 
 #include "common.cuh"
@@ -84,9 +86,10 @@ __global__ void k_adj_resolve(const int4 *__restrict__ faces, int nF, const unsi
     adj[he] = partner >= 0 ? partner / 3 : -1;
 }
 
-// Unit face normals, and the angle-weighted sums at the vertices (atomic adds).
-__global__ void k_pseudo_normals(const int4 *__restrict__ faces, const float4 *__restrict__ verts, int nF,
-                                 float4 *__restrict__ fnorm, float4 *vnorm) {
+// Unit face normals (the vertex pseudo-normals are summed where a query needs
+// one, over the vertex's faces in ascending id: query.cu).
+__global__ void k_face_normals(const int4 *__restrict__ faces, const float4 *__restrict__ verts, int nF,
+                               float4 *__restrict__ fnorm) {
     int f = blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= nF) return;
     int4 fv = faces[f];
@@ -100,18 +103,6 @@ __global__ void k_pseudo_normals(const int4 *__restrict__ faces, const float4 *_
     float s = l > 0.0f ? 1.0f / l : 0.0f;
     nx *= s; ny *= s; nz *= s;
     fnorm[f] = make_float4(nx, ny, nz, 0.0f);
-    for (int j = 0; j < 3; ++j) {
-        float3 a = p[(j + 1) % 3], b = p[(j + 2) % 3];
-        float ax = a.x - p[j].x, ay = a.y - p[j].y, az = a.z - p[j].z;
-        float bx = b.x - p[j].x, by = b.y - p[j].y, bz = b.z - p[j].z;
-        float la = sqrtf(ax * ax + ay * ay + az * az), lb = sqrtf(bx * bx + by * by + bz * bz);
-        if (la == 0.0f || lb == 0.0f) continue;
-        float cs = fminf(1.0f, fmaxf(-1.0f, (ax * bx + ay * by + az * bz) / (la * lb)));
-        float ang = acosf(cs);
-        atomicAdd(&vnorm[id[j]].x, ang * nx);
-        atomicAdd(&vnorm[id[j]].y, ang * ny);
-        atomicAdd(&vnorm[id[j]].z, ang * nz);
-    }
 }
 
 struct AdjTable {
@@ -170,9 +161,7 @@ mesh_status mesh_signed_distance(mesh_bvh *bvh, const float *d_Q, int64_t nQ, fl
         bvh->adj_ready = true;
     }
     if (n > 0) {
-        cudaMemsetAsync(bvh->vnorm(), 0, 16 * (size_t)bvh->L.n_verts, s);
-        k_pseudo_normals<<<grid_for(n, 256), 256, 0, s>>>(bvh->faces(), bvh->verts(), n, bvh->fnorm(),
-                                                          bvh->vnorm());
+        k_face_normals<<<grid_for(n, 256), 256, 0, s>>>(bvh->faces(), bvh->verts(), n, bvh->fnorm());
         count_launch();
     }
     if (nQ == 0) return check_launch();

@@ -55,7 +55,7 @@ def test_create_validates_storage_on_the_host():
     assert L.mesh_bvh_get_layout(h, C.byref(lay)) == 0
     assert lay.max_faces == 16 and lay.storage_bytes == need
     offs = [lay.off_header, lay.off_verts, lay.off_faces, lay.off_keys, lay.off_perm,
-            lay.off_nodes, lay.off_parent, lay.off_tris, lay.off_rend, lay.off_iperm, lay.off_adj, lay.off_fnorm, lay.off_vnorm, lay.off_xlist]
+            lay.off_nodes, lay.off_parent, lay.off_tris, lay.off_rend, lay.off_iperm, lay.off_adj, lay.off_fnorm, lay.off_xlist]
     assert offs == sorted(offs) and all(o % 256 == 0 for o in offs)
     # argument errors are caught before anything is launched
     n0 = L.mesh_launch_count()

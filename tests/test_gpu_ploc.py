@@ -149,13 +149,10 @@ def test_every_tree_consumer_runs_on_the_ploc_tree():
     out = {k: v.clone() for k, v in ref.items()}
     ploc.contact(P, 0.05, out)
     assert_identical(out, ref)
-    # signed distance (same nearest face and distance, same signs)
+    # signed distance: the same face, distance and sign, bit for bit
     sp, sl = ploc.signed_distance(P, 0.05), lbvh.signed_distance(P, 0.05)
     assert torch.equal(sp["face"], sl["face"])
-    a, b = sp["sdist"], sl["sdist"]
-    assert torch.equal(a.abs(), b.abs())
-    away = a.abs() > 1e-5                  # pseudo-normal sums use float atomics: compare signs
-    assert torch.equal(torch.sign(a[away]), torch.sign(b[away]))   # away from the surface
+    assert torch.equal(sp["sdist"], sl["sdist"])
     # k-NN weighted projection (k faces by distance: equal except near ties)
     pk, fk, _ = ploc.knn_project(P[:5000], k=4, want_faces=True)
     pl, fl, _ = lbvh.knn_project(P[:5000], k=4, want_faces=True)

@@ -3,6 +3,7 @@ the oracle: signs equal wherever the distance exceeds 1e-4 of the diagonal,
 magnitudes within float32 rounding; the exact cube; refit between calls."""
 import numpy as np
 import pytest
+import torch
 
 import oracle
 from paper_2606_00444_gb300 import MeshBVH
@@ -64,3 +65,34 @@ def test_skinned_torus_full_size_refit_between_calls():
         inside = host(got["sdist"]) < 0
         assert 0.0 < inside.mean() < 0.2
     assert bvh.status()[0] & ~0x4 == 0
+
+
+def test_reproducible_run_to_run_and_vertex_normals():
+    """Queries placed just off the vertices of a skinned torus (their nearest point is a
+    vertex, where the pseudo-normal is the angle-weighted sum over the vertex's faces):
+    two calls give the same signed distances bit for bit, and the signs match the
+    oracle's."""
+    V0, F = torus(60, 40)
+    V = TorusSkinning(V0, seed=3003).frame(20)
+    rng = np.random.default_rng(8)
+    idx = rng.choice(V.shape[0], 2000, replace=False)
+    # offsets along the vertex normals (mean of the incident face normals): outward at
+    # the convex vertices of the outer half lands in their vertex regions
+    V64 = V.astype(np.float64)
+    fn = np.cross(V64[F[:, 1]] - V64[F[:, 0]], V64[F[:, 2]] - V64[F[:, 0]])
+    vn = np.zeros_like(V64)
+    for k in range(3):
+        np.add.at(vn, F[:, k], fn)
+    d = vn[idx] / np.linalg.norm(vn[idx], axis=1, keepdims=True)
+    Q = np.concatenate([V64[idx] + 0.004 * d, V64[idx] - 0.004 * d]).astype(np.float32)
+    bvh = MeshBVH.from_mesh(dev(V0), dev(F))
+    bvh.refit(dev(V))
+    a = bvh.signed_distance(dev(Q))
+    b = bvh.signed_distance(dev(Q))
+    for k in a:
+        assert torch.equal(a[k], b[k]), k
+    bary = host(a["bary"])
+    on_vertex = ((bary == 0).sum(1) == 2).mean()
+    assert on_vertex > 0.1
+    check_signed(V, F, Q, a)
+    assert bvh.status()[0] == 0

@@ -215,9 +215,10 @@ def gpu_arm(args, rank, world, local_rank):
             torch.empty(gface.shape[0], 3, device=dev))
     S_def = torch.empty(N_CD, 3, device=dev)
     cd_out = torch.empty(2, dtype=torch.float64, device=dev)
-    # per-sample Chamfer faces of the previous frame, for the warm-started variant
-    # timed beside the frame (mesh_chamfer_hinted; not faster here: the unbounded
-    # searches' cost is the ball of the final distance, which a hint cannot shrink)
+    # per-sample Chamfer faces of the previous frame, for the warm-started form timed
+    # beside the frame (mesh_chamfer_hinted; the results are those without hints, bit
+    # for bit; over the whole skinning cycle it is no faster: an unbounded search's cost
+    # is the ball of the final distance, which a hint cannot shrink)
     cd_ps = dict(faceA=torch.full((N_CD,), -1, dtype=torch.int32, device=dev),
                  baryA=torch.empty(N_CD, 3, device=dev), dist2A=torch.empty(N_CD, device=dev),
                  faceB=torch.full((N_CD,), -1, dtype=torch.int32, device=dev),
@@ -227,10 +228,13 @@ def gpu_arm(args, rank, world, local_rank):
 
     # The frame as a fork-join graph, as an engine would schedule it: the full
     # rebuild of the frame (the varying-topology path) only reads the frame's
-    # vertices and forks at the frame start; after the refit, the contact queries
-    # (main stream) and the rebind + Chamfer branch (side stream) run concurrently.
-    # The branches share no workspace.  Per-stage device times are measured
-    # separately below, one stage at a time.
+    # vertices and forks at the frame start; the refit and the rebind of the
+    # Gaussians run as one pass (mesh_refit_bind, the Gaussians grouped by face,
+    # G_PER_FACE each), after which the contact queries (main stream) and the
+    # Chamfer branch (side stream) run concurrently.  The branches share no
+    # workspace.  Per-stage device times are measured separately below, one stage
+    # at a time (refit and rebind also as the two separate calls).
+    gstart = torch.arange(0, G_PER_FACE * nF + 1, G_PER_FACE, dtype=torch.int32, device=dev)
     side_a = torch.cuda.Stream(device=dev)
     side_b = torch.cuda.Stream(device=dev)
 
@@ -239,10 +243,9 @@ def gpu_arm(args, rank, world, local_rank):
         side_b.wait_stream(main)
         with torch.cuda.stream(side_b):
             rebuilt.build(Vin, F)                                # a1 + a2..a5
-        fixed.refit(Vin)                                         # a1 + a5
+        fixed.refit_bind(Vin, gstart, gbary, out=gout)           # a1 + a5 + a7
         side_a.wait_stream(main)
         with torch.cuda.stream(side_a):
-            fixed.bind_gaussians(gface, gbary, out=gout)         # a7
             fixed.interpolate(cdf, cdb, out=S_def)               # a8
             chamfer(fixed, S_def, rest, rest_S, ws=cd_ws, out=cd_out)
         fixed.contact(P, CUTOFF, contact, ws=ct_ws)              # a6 (warm start, work order)
@@ -339,6 +342,10 @@ def gpu_arm(args, rank, world, local_rank):
     cd_out_h = torch.empty_like(cd_out)
     stage_fns.append(lambda: chamfer(fixed, S_def, rest, rest_S, ws=cd_ws, out=cd_out_h, ps=cd_ps,
                                      hints=(cd_ps["faceA"], cd_ps["faceB"])))
+    # refit and rebind in one pass, as the frame runs them (the two calls above give
+    # the same boxes and Gaussians, bit for bit)
+    gout_f = tuple(torch.empty_like(x) for x in gout)
+    stage_fns.append(lambda: fixed.refit_bind(Vin, gstart, gbary, out=gout_f))
     stage_graphs = []
     for fn in stage_fns:
         gs = torch.cuda.CUDAGraph()
@@ -360,7 +367,8 @@ def gpu_arm(args, rank, world, local_rank):
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     names = ["refit", "contact", "rebind", "rebuild", "chamfer", "contact_without_warm_start",
-             "contact_hinted_unordered", "contact_signed", "contact_on_rebuilt_lbvh", "chamfer_with_warm_start"]
+             "contact_hinted_unordered", "contact_signed", "contact_on_rebuilt_lbvh", "chamfer_with_warm_start",
+             "refit_and_rebind_fused"]
     st = {n: float(np.mean([e[i].elapsed_time(e[i + 1]) for e in evs])) for i, n in enumerate(names)}
 
     # the concurrent frame graph computes what the stages compute one at a time
@@ -384,6 +392,13 @@ def gpu_arm(args, rank, world, local_rank):
     if bad:
         raise RuntimeError(f"the concurrent frame graph differs from the stages run one at a "
                            f"time in outputs {bad}")
+    # the fused refit + rebind gives the boxes and Gaussians of the two calls, bit for bit
+    nodes_seq = fixed.arrays()["nodes_i"].clone()
+    load_frame(7)
+    stage_graphs[names.index("refit_and_rebind_fused")].replay()
+    torch.cuda.synchronize()
+    fused_equal = all(torch.equal(x, y) for x, y in zip(gout_f, gout)) and \
+        torch.equal(nodes_seq, fixed.arrays()["nodes_i"])
     un_ms = []
     contact_un = {k: torch.empty_like(v) for k, v in contact.items()}
     for k in range(min(nst, 20)):
@@ -433,17 +448,16 @@ def gpu_arm(args, rank, world, local_rank):
         raise RuntimeError("render capacity overflowed")
 
     # end to end through the public API from pinned host buffers, the frame run as
-    # above in four graphs (refit; contact; rebind + Chamfer; rebuild) with the
+    # above in four graphs (refit + rebind; contact; Chamfer; rebuild) with the
     # copies on a further stream beside the kernels: the particle upload beside
     # the refit, the download of the contact results beside the rest of the frame
     # (events order them)
     gA, gB, gC, gD = (torch.cuda.CUDAGraph() for _ in range(4))
     with torch.cuda.graph(gA):
-        stage_fns[0]()                                            # refit
+        fixed.refit_bind(Vin, gstart, gbary, out=gout)           # refit + rebind
     with torch.cuda.graph(gB):
         stage_fns[1]()                                            # contact
     with torch.cuda.graph(gC):
-        stage_fns[2]()                                            # rebind
         stage_fns[4]()                                            # Chamfer
     with torch.cuda.graph(gD):
         stage_fns[3]()                                            # rebuild
@@ -519,7 +533,7 @@ def gpu_arm(args, rank, world, local_rank):
                ploc_build_ms=ploc_build_ms,
                tuned=tuned, tuned_chamfer=tuned_cd, stats=stats, l2_read_gbs=l2,
                roof_ms=float(np.median(roof_ms)),
-               h2d=h2d, d2h=d2h, launches=launches_per_frame * args.steps,
+               h2d=h2d, d2h=d2h, launches=launches_per_frame * args.steps, fused_equal=fused_equal,
                contact_hits=int((contact["face"] >= 0).sum().item()),
                chamfer=[float(x) for x in cd_out.cpu()])
     return out, W
@@ -1238,6 +1252,8 @@ def main():
         "step_ms_stats": {"mean": float(np.mean(res["step_ms"])), "median": float(np.median(res["step_ms"])),
                           "min": float(np.min(res["step_ms"])), "max": float(np.max(res["step_ms"]))},
         "stages_ms": st,
+        "refit_and_rebind": {"two_calls_ms": st["refit"] + st["rebind"], "fused_ms": st["refit_and_rebind_fused"],
+                             "outputs_equal": res["fused_equal"]},
         "ms_per_frame": {"refit_path": st["refit"] + st["contact"] + st["rebind"],
                          "rebuild_path": st["rebuild"] + st["contact_on_rebuilt_lbvh"] + st["rebind"],
                          "refit": st["refit"], "rebuild": st["rebuild"]},

@@ -196,14 +196,20 @@ mesh_status mesh_update_vertices(mesh_bvh *bvh, const float *d_V, int64_t nV, vo
 mesh_status mesh_refit(mesh_bvh *bvh, const float *d_V, int64_t nV, void *stream);
 
 /* mesh_refit and mesh_bind_gaussians in one pass (the fixed-topology frame of
- * Sec. 3.4: new vertices, new boxes, Gaussians moved with their faces), the
- * face corners read once for both.  The Gaussians are grouped by face: those
- * of face f are g = d_gstart[f] .. d_gstart[f + 1] - 1 (int32 [nF + 1],
- * non-decreasing, d_gstart[nF] = nG), with weights d_gbary [nG][3] and
- * normal offsets d_goff [nG] (NULL = 0); outputs as mesh_bind_gaussians,
- * indexed by g.  A face whose range is decreasing or past nG sets
- * MESH_DEV_INDEX_RANGE and its Gaussians are not written.  Same results as
- * the two calls. */
+ * Sec. 3.4: new vertices, new boxes, Gaussians moved with their faces).  The
+ * refit's leaf threads, which gather their faces' corners for the leaf boxes,
+ * also compute each face's normal, rotation and scale once (they depend on
+ * the face alone); the block's threads then take the Gaussians of its 512
+ * leaves one per thread, each computing its centre.  The Gaussians are
+ * grouped by face: those of face f are g = d_gstart[f] .. d_gstart[f + 1] - 1
+ * (int32 [nF + 1], non-decreasing, d_gstart[nF] = nG), with weights d_gbary
+ * [nG][3] and normal offsets d_goff [nG] (NULL = 0); outputs as
+ * mesh_bind_gaussians, indexed by g (writes are contiguous where the
+ * Gaussians of neighbouring leaves are, e.g. when g follows the tree's leaf
+ * order).  A face whose range is decreasing or past nG sets
+ * MESH_DEV_INDEX_RANGE and its Gaussians are not written (so does a block
+ * whose Gaussians number more than INT_MAX, possible only when ranges
+ * overlap).  The same results as the two calls, bit for bit. */
 mesh_status mesh_refit_bind(mesh_bvh *bvh, const float *d_V, int64_t nV, const int32_t *d_gstart,
                             const float *d_gbary, const float *d_goff, int64_t nG, float *d_mu,
                             float *d_quat, float *d_scale, void *stream);

@@ -17,13 +17,26 @@ constexpr float kEpsS = 1e-2f;
 struct V3 {
     float x, y, z;
 };
+// Every product and sum is rounded on its own (no contraction into fused
+// multiply-adds, whose choice of operands the compiler may make differently in
+// different kernels): a face's frame and a Gaussian's centre come out the
+// same, bit for bit, in every kernel that computes them.
 __device__ __forceinline__ V3 v3(float4 a) { return V3{a.x, a.y, a.z}; }
-__device__ __forceinline__ V3 operator+(V3 a, V3 b) { return V3{a.x + b.x, a.y + b.y, a.z + b.z}; }
-__device__ __forceinline__ V3 operator-(V3 a, V3 b) { return V3{a.x - b.x, a.y - b.y, a.z - b.z}; }
-__device__ __forceinline__ V3 operator*(V3 a, float s) { return V3{a.x * s, a.y * s, a.z * s}; }
-__device__ __forceinline__ float dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ V3 operator+(V3 a, V3 b) {
+    return V3{__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y), __fadd_rn(a.z, b.z)};
+}
+__device__ __forceinline__ V3 operator-(V3 a, V3 b) {
+    return V3{__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y), __fsub_rn(a.z, b.z)};
+}
+__device__ __forceinline__ V3 operator*(V3 a, float s) {
+    return V3{__fmul_rn(a.x, s), __fmul_rn(a.y, s), __fmul_rn(a.z, s)};
+}
+__device__ __forceinline__ float dot(V3 a, V3 b) {
+    return __fadd_rn(__fadd_rn(__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y)), __fmul_rn(a.z, b.z));
+}
 __device__ __forceinline__ V3 cross(V3 a, V3 b) {
-    return V3{a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+    return V3{__fsub_rn(__fmul_rn(a.y, b.z), __fmul_rn(a.z, b.y)), __fsub_rn(__fmul_rn(a.z, b.x), __fmul_rn(a.x, b.z)),
+              __fsub_rn(__fmul_rn(a.x, b.y), __fmul_rn(a.y, b.x))};
 }
 
 // Zero area: the float32 cross product decides when it is clearly non-zero
@@ -106,35 +119,69 @@ __device__ __forceinline__ void frame_matrix(const Frame &F, float R[3][3]) {
     R[2][0] = F.e1.z; R[2][1] = F.e2.z; R[2][2] = F.n.z;
 }
 
-// One Gaussian on the face with global vertex indices fv.
+// The part of a binding that depends on the face alone: its unit normal, the
+// rotation (w, x, y, z) of [e1 e2 n] and the scale; a degenerate face gets the
+// identity rotation and zero scale.
+struct FaceBind {
+    V3 n;
+    float q[4], s[3];
+    bool degenerate;
+};
+
+__device__ __forceinline__ FaceBind face_bind(V3 a, V3 b, V3 c) {
+    FaceBind B;
+    Frame F = face_frame(a, b, c);
+    B.degenerate = F.degenerate;
+    B.n = F.degenerate ? V3{0.0f, 0.0f, 0.0f} : F.n;
+    B.q[0] = 1.0f; B.q[1] = B.q[2] = B.q[3] = 0.0f;
+    B.s[0] = B.s[1] = B.s[2] = 0.0f;
+    if (!F.degenerate) {
+        float R[3][3], p;
+        frame_matrix(F, R);
+        quat_raw(R, B.q, p);
+        float sg = quat_sign(B.q);
+        for (int k = 0; k < 4; ++k) B.q[k] *= sg;
+        float h = F.an / F.l;
+        B.s[0] = kRho * F.l;
+        B.s[1] = kRho * h;
+        B.s[2] = kEpsS * kRho * (F.l + h) * 0.5f;
+    }
+    return B;
+}
+
+// The part that depends on the Gaussian: its centre, at weights (b0, b1, b2)
+// and offset `off` along the normal (no offset on a degenerate face).
+__device__ __forceinline__ V3 gaussian_centre(V3 a, V3 b, V3 c, V3 n, bool degenerate, float b0, float b1,
+                                              float b2, float off) {
+    V3 m = a * b0 + b * b1 + c * b2;
+    if (!degenerate) m = m + n * off;
+    return m;
+}
+
+// Writes Gaussian g (centre m, the face's rotation and scale); a degenerate
+// face is counted and flagged.
+__device__ __forceinline__ void put_gaussian(int64_t g, V3 m, const float q[4], const float s[3], bool degenerate,
+                                             float *__restrict__ mu, float *__restrict__ quat,
+                                             float *__restrict__ scale, unsigned int *status,
+                                             unsigned int *n_degenerate) {
+    if (degenerate) {
+        atomicAdd(n_degenerate, 1u);
+        atomicOr(status, (unsigned)MESH_DEV_DEGENERATE);
+    }
+    mu[3 * g] = m.x; mu[3 * g + 1] = m.y; mu[3 * g + 2] = m.z;
+    quat[4 * g] = q[0]; quat[4 * g + 1] = q[1]; quat[4 * g + 2] = q[2]; quat[4 * g + 3] = q[3];
+    scale[3 * g] = s[0]; scale[3 * g + 1] = s[1]; scale[3 * g + 2] = s[2];
+}
+
 // Gaussian g on the face with corners (a, b, c), weights (b0, b1, b2), normal
 // offset off: centre, rotation and scale written at index g.
 __device__ __forceinline__ void bind_corners(V3 a, V3 b, V3 c, float b0, float b1, float b2, float off,
                                              int64_t g, float *__restrict__ mu, float *__restrict__ quat,
                                              float *__restrict__ scale, unsigned int *status,
                                              unsigned int *n_degenerate) {
-    V3 m = a * b0 + b * b1 + c * b2;
-    Frame F = face_frame(a, b, c);
-    float q[4] = {1.0f, 0.0f, 0.0f, 0.0f};
-    float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f;
-    if (F.degenerate) {
-        atomicAdd(n_degenerate, 1u);
-        atomicOr(status, (unsigned)MESH_DEV_DEGENERATE);
-    } else {
-        m = m + F.n * off;
-        float R[3][3], p;
-        frame_matrix(F, R);
-        quat_raw(R, q, p);
-        float sg = quat_sign(q);
-        for (int k = 0; k < 4; ++k) q[k] *= sg;
-        float h = F.an / F.l;
-        s0 = kRho * F.l;
-        s1 = kRho * h;
-        s2 = kEpsS * kRho * (F.l + h) * 0.5f;
-    }
-    mu[3 * g] = m.x; mu[3 * g + 1] = m.y; mu[3 * g + 2] = m.z;
-    quat[4 * g] = q[0]; quat[4 * g + 1] = q[1]; quat[4 * g + 2] = q[2]; quat[4 * g + 3] = q[3];
-    scale[3 * g] = s0; scale[3 * g + 1] = s1; scale[3 * g + 2] = s2;
+    FaceBind B = face_bind(a, b, c);
+    put_gaussian(g, gaussian_centre(a, b, c, B.n, B.degenerate, b0, b1, b2, off), B.q, B.s, B.degenerate, mu,
+                 quat, scale, status, n_degenerate);
 }
 
 __device__ __forceinline__ void bind_one(int4 fv, const float4 *__restrict__ verts, float b0, float b1,

@@ -556,24 +556,73 @@ struct Rebind {
     float *mu, *quat, *scale;
 };
 
-// The Gaussians of one face (kept out of line: the quaternion arithmetic would
-// otherwise raise the register pressure of the whole refit kernel).
-__device__ __noinline__ void bind_face(const Rebind &RB, int f, float4 a, float4 b, float4 c, Header *hdr) {
-    int gs = RB.gstart[f], ge = RB.gstart[f + 1];
-    if (gs < 0 || ge < gs || (int64_t)ge > RB.nG) {
-        set_status(hdr, MESH_DEV_INDEX_RANGE);
-        return;
-    }
-    for (int g = gs; g < ge; ++g)
-        bind_corners(v3(a), v3(b), v3(c), RB.gbary[3 * (size_t)g], RB.gbary[3 * (size_t)g + 1],
-                     RB.gbary[3 * (size_t)g + 2], RB.goff ? RB.goff[g] : 0.0f, g, RB.mu, RB.quat, RB.scale,
-                     &hdr->status, &hdr->n_degenerate);
-}
+// Per-leaf record of the rebind, in shared memory after the table rounds
+// ([kBindFloats][kRefitBlock]): corners a, b, c, unit normal, rotation, scale,
+// degenerate flag.
+constexpr int kBindFloats = 20;
 
 constexpr size_t kRefitLocalSmem = 12 * kRefitBlock * sizeof(float)      // two table levels
                                    + 64 * sizeof(int);                    // crossing-list scan
+constexpr size_t kRefitBindSmem = kBindFloats * kRefitBlock * sizeof(float)   // rebind records
+                                  + 64 * sizeof(int)                          // scans
+                                  + 2 * kRefitBlock * sizeof(int);            // Gaussian offsets, starts
 
-__global__ void __launch_bounds__(kRefitBlock, 4)
+// The Gaussians of a refit block's leaves, one per thread: leaf l (this
+// thread's when l = threadIdx.x) holds gcnt Gaussians from index gs on and its
+// record in rec.  A block whose Gaussian count overflows an int sets
+// MESH_DEV_INDEX_RANGE and writes none (only an overlapping face CSR can).
+__device__ __forceinline__ void bind_block(const float *__restrict__ rec, int *__restrict__ s_scan, int gs,
+                                           int gcnt, const Rebind &RB, Header *__restrict__ hdr) {
+    int *s_off = s_scan + 64, *s_gs = s_off + kRefitBlock;
+    long long *s_wsum = reinterpret_cast<long long *>(s_scan);   // 16 warp totals (64-bit)
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    long long x = gcnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_wsum[wid] = x;
+    __syncthreads();
+    long long before = 0, total = 0;
+    for (int w = 0; w < kRefitBlock / 32; ++w) {
+        long long v = s_wsum[w];
+        if (w < wid) before += v;
+        total += v;
+    }
+    if (total > INT_MAX) {
+        if (tid == 0) set_status(hdr, MESH_DEV_INDEX_RANGE);
+        return;
+    }
+    s_off[tid] = (int)(before + x - gcnt);
+    s_gs[tid] = gs;
+    __syncthreads();
+    for (int t = tid; t < (int)total; t += kRefitBlock) {
+        int l = 0;                                       // the last leaf whose offset is <= t
+#pragma unroll
+        for (int h = kRefitBlock / 2; h > 0; h >>= 1)
+            if (s_off[l + h] <= t) l += h;
+        int64_t g = (int64_t)s_gs[l] + (t - s_off[l]);
+        const float *r = rec + l;
+        V3 a{r[0], r[kRefitBlock], r[2 * kRefitBlock]}, b{r[3 * kRefitBlock], r[4 * kRefitBlock], r[5 * kRefitBlock]};
+        V3 c{r[6 * kRefitBlock], r[7 * kRefitBlock], r[8 * kRefitBlock]};
+        V3 nrm{r[9 * kRefitBlock], r[10 * kRefitBlock], r[11 * kRefitBlock]};
+        float q[4] = {r[12 * kRefitBlock], r[13 * kRefitBlock], r[14 * kRefitBlock], r[15 * kRefitBlock]};
+        float sc[3] = {r[16 * kRefitBlock], r[17 * kRefitBlock], r[18 * kRefitBlock]};
+        bool deg = r[19 * kRefitBlock] != 0.0f;
+        V3 m = gaussian_centre(a, b, c, nrm, deg, RB.gbary[3 * g], RB.gbary[3 * g + 1], RB.gbary[3 * g + 2],
+                               RB.goff ? RB.goff[g] : 0.0f);
+        put_gaussian(g, m, q, sc, deg, RB.mu, RB.quat, RB.scale, &hdr->status, &hdr->n_degenerate);
+    }
+}
+
+// The rebind of the leaves' Gaussians (kBind, mesh_refit_bind): after the
+// rounds each leaf thread computes its face's normal, rotation and scale once
+// (they depend on the face alone) into shared memory beside its corners, and
+// the block's threads then take its Gaussians one per thread (offsets from a
+// block scan of the faces' Gaussian counts), each computing only its centre.
+template <bool kBind>
+__global__ void __launch_bounds__(kRefitBlock, kBind ? 3 : 4)
 k_refit_local(int n, const float *__restrict__ V3, int nV, float4 *__restrict__ V4,
               const int *__restrict__ perm, const int4 *__restrict__ faces,
               float4 *__restrict__ tris, float4 *__restrict__ nodes, const int *__restrict__ parent,
@@ -582,7 +631,7 @@ k_refit_local(int n, const float *__restrict__ V3, int nV, float4 *__restrict__ 
               int *__restrict__ iperm, Header *__restrict__ hdr, Rebind RB, int leaf_size) {
     extern __shared__ float4 dsm[];
     float *tab = reinterpret_cast<float *>(dsm);
-    int *s_warp = reinterpret_cast<int *>(tab + 12 * kRefitBlock);
+    int *s_warp = reinterpret_cast<int *>(tab + (kBind ? kBindFloats : 12) * kRefitBlock);
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int base = blockIdx.x * kRefitBlock, j = base + tid;
     // leaf j: box into level 0 and into its parent's record
@@ -662,6 +711,8 @@ k_refit_local(int n, const float *__restrict__ V3, int nV, float4 *__restrict__ 
             __syncthreads();
         }
     }
+    int gs = 0, gcnt = 0;                                // kBind: this leaf's Gaussians
+    if constexpr (kBind) __syncthreads();                // the table is read no more: records go there
     if (j < n) {
         int f = perm[j];                                 // reloaded: cheaper than keeping it live
         iperm[f] = j;
@@ -671,8 +722,19 @@ k_refit_local(int n, const float *__restrict__ V3, int nV, float4 *__restrict__ 
         tris[3 * (size_t)j + 0] = make_float4(a.x, a.y, a.z, __int_as_float(f));
         tris[3 * (size_t)j + 1] = make_float4(b.x, b.y, b.z, deg);
         tris[3 * (size_t)j + 2] = make_float4(c.x, c.y, c.z, 0.0f);
-        if (RB.gstart) bind_face(RB, f, a, b, c, hdr);   // a7 fused: this face's Gaussians
+        if constexpr (kBind) {
+            int g0 = RB.gstart[f], g1 = RB.gstart[f + 1];
+            if (g0 < 0 || g1 < g0 || (int64_t)g1 > RB.nG) set_status(hdr, MESH_DEV_INDEX_RANGE);
+            else { gs = g0; gcnt = g1 - g0; }
+            FaceBind B = face_bind(v3(a), v3(b), v3(c));
+            const float r[kBindFloats] = {a.x, a.y, a.z, b.x, b.y, b.z, c.x, c.y, c.z, B.n.x, B.n.y, B.n.z,
+                                          B.q[0], B.q[1], B.q[2], B.q[3], B.s[0], B.s[1], B.s[2],
+                                          B.degenerate ? 1.0f : 0.0f};
+#pragma unroll
+            for (int k = 0; k < kBindFloats; ++k) tab[k * kRefitBlock + tid] = r[k];
+        }
     }
+    if constexpr (kBind) bind_block(tab, s_warp, gs, gcnt, RB, hdr);
     // a1: this block's slice of the vertex repack (after every read of V4 above)
     if (V3) {
         int per = (nV + gridDim.x - 1) / gridDim.x;
@@ -1321,10 +1383,12 @@ mesh_status mesh_update_vertices(mesh_bvh *bvh, const float *d_V, int64_t nV, vo
 // Launches the two bottom-up kernels (build and refit); V3 = new vertices or NULL.
 static mesh_status bottom_up(mesh_bvh *bvh, const float *V3, cudaStream_t s,
                              Rebind rb = Rebind{nullptr, nullptr, nullptr, 0, nullptr, nullptr, nullptr}) {
-    static bool smem_set = false;                    // above the default 48 KB: opt in once
+    static bool smem_set = false;                    // the dynamic shared memory the kernels take
     if (!smem_set) {
-        if (cudaFuncSetAttribute(k_refit_local, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kRefitLocalSmem) != cudaSuccess)
+        if (cudaFuncSetAttribute(k_refit_local<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kRefitLocalSmem) != cudaSuccess ||
+            cudaFuncSetAttribute(k_refit_local<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kRefitBindSmem) != cudaSuccess)
             return MESH_ERR_CUDA;
         smem_set = true;
     }
@@ -1335,7 +1399,8 @@ static mesh_status bottom_up(mesh_bvh *bvh, const float *V3, cudaStream_t s,
     int4 *xlist = reinterpret_cast<int4 *>(suf + 2 * fmax);
     float4 *bbox = reinterpret_cast<float4 *>(xlist + fmax);
     int *xcnt = reinterpret_cast<int *>(bbox + 2 * nbmax);
-    k_refit_local<<<nb, kRefitBlock, kRefitLocalSmem, s>>>(
+    (rb.gstart ? k_refit_local<true> : k_refit_local<false>)<<<nb, kRefitBlock,
+        rb.gstart ? kRefitBindSmem : kRefitLocalSmem, s>>>(
         n, V3, (int)bvh->L.n_verts, bvh->verts(), bvh->perm(), bvh->faces(), bvh->tris(),
         bvh->nodes(), bvh->parent(), bvh->rend(), pre, suf, bbox, xlist, xcnt, bvh->iperm(), bvh->hdr(), rb,
         bvh->leaf_size);

@@ -156,7 +156,7 @@ def replicas_value(queries_per_frame: int, world: int, ms: float) -> float:
 
 def gpu_arm(args, rank, world, local_rank):
     import torch
-    from paper_2606_00444_gb300 import MeshBVH, Workspace, chamfer, launch_count, morton_order
+    from paper_2606_00444_gb300 import MeshBVH, Workspace, chamfer, chamfer_step, launch_count, morton_order
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
@@ -197,10 +197,11 @@ def gpu_arm(args, rank, world, local_rank):
     tuned = tune_contact(fixed, P, CUTOFF, frames=[frames[k] for k in range(min(4, frames.shape[0]))])
     rebuilt.set_query_config(tuned["lanes"], tuned["variant"], tuned["block"])   # same traversal
     rebuilt.set_leaf_size(tuned["leaf"], refit=False)               # on the LBVH, from its builds
-    # lanes per sample of the Chamfer, chosen by timing on this frame's samples
+    # lanes per sample of the Chamfer, chosen by timing the frame's form of it (the
+    # ordered, warm-started step) on this frame's samples
     from paper_2606_00444_gb300.tune import tune_chamfer
     S0 = fixed.interpolate(cdf, cdb)
-    tuned_cd = tune_chamfer(fixed, S0, rest, rest_S)
+    tuned_cd = tune_chamfer(fixed, S0, rest, rest_S, step=True)
     Vin = torch.empty(nV, 3, device=dev)
     # the contact step's workspace carries each particle's work class to the next frame
     ct_ws = Workspace(dev)
@@ -215,15 +216,16 @@ def gpu_arm(args, rank, world, local_rank):
             torch.empty(gface.shape[0], 3, device=dev))
     S_def = torch.empty(N_CD, 3, device=dev)
     cd_out = torch.empty(2, dtype=torch.float64, device=dev)
-    # per-sample Chamfer faces of the previous frame, for the warm-started form timed
-    # beside the frame (mesh_chamfer_hinted; the results are those without hints, bit
-    # for bit; over the whole skinning cycle it is no faster: an unbounded search's cost
-    # is the ball of the final distance, which a hint cannot shrink)
+    # The frame's Chamfer runs as a step of the sequence (mesh_chamfer_step): warm-started
+    # from the previous frame's per-sample faces, each side's samples run heaviest first
+    # by the costs the previous frame left in its workspace (per-sample results those of
+    # mesh_chamfer, bit for bit); the plain call is timed beside it
     cd_ps = dict(faceA=torch.full((N_CD,), -1, dtype=torch.int32, device=dev),
                  baryA=torch.empty(N_CD, 3, device=dev), dist2A=torch.empty(N_CD, device=dev),
                  faceB=torch.full((N_CD,), -1, dtype=torch.int32, device=dev),
                  baryB=torch.empty(N_CD, 3, device=dev), dist2B=torch.empty(N_CD, device=dev))
     cd_ws = Workspace(dev)
+    cd_step_ws = Workspace(dev)
     flush = torch.empty(128 << 20, dtype=torch.float32, device=dev)   # 512 MB > L2
 
     # The frame as a fork-join graph, as an engine would schedule it: the full
@@ -247,7 +249,7 @@ def gpu_arm(args, rank, world, local_rank):
         side_a.wait_stream(main)
         with torch.cuda.stream(side_a):
             fixed.interpolate(cdf, cdb, out=S_def)               # a8
-            chamfer(fixed, S_def, rest, rest_S, ws=cd_ws, out=cd_out)
+            chamfer_step(fixed, S_def, rest, rest_S, cd_ps, cd_step_ws, out=cd_out)
         fixed.contact(P, CUTOFF, contact, ws=ct_ws)              # a6 (warm start, work order)
         main.wait_stream(side_a)
         main.wait_stream(side_b)
@@ -323,7 +325,7 @@ def gpu_arm(args, rank, world, local_rank):
                  lambda: fixed.bind_gaussians(gface, gbary, out=gout),
                  lambda: rebuilt.build(Vin, F),
                  lambda: (fixed.interpolate(cdf, cdb, out=S_def),
-                          chamfer(fixed, S_def, rest, rest_S, ws=cd_ws, out=cd_out))]
+                          chamfer_step(fixed, S_def, rest, rest_S, cd_ps, cd_step_ws, out=cd_out))]
     contact_nh = {k: torch.empty_like(v) for k, v in contact.items()}
     stage_fns.append(lambda: fixed.closest_point(P, CUTOFF, out=contact_nh))   # no warm start
     contact_pt = {k: v.clone() for k, v in contact.items()}
@@ -340,8 +342,7 @@ def gpu_arm(args, rank, world, local_rank):
     ct_ws_rb = Workspace(dev)
     stage_fns.append(lambda: rebuilt.contact(P, CUTOFF, contact_rb, ws=ct_ws_rb))
     cd_out_h = torch.empty_like(cd_out)
-    stage_fns.append(lambda: chamfer(fixed, S_def, rest, rest_S, ws=cd_ws, out=cd_out_h, ps=cd_ps,
-                                     hints=(cd_ps["faceA"], cd_ps["faceB"])))
+    stage_fns.append(lambda: chamfer(fixed, S_def, rest, rest_S, ws=cd_ws, out=cd_out_h))
     # refit and rebind in one pass, as the frame runs them (the two calls above give
     # the same boxes and Gaussians, bit for bit)
     gout_f = tuple(torch.empty_like(x) for x in gout)
@@ -367,7 +368,7 @@ def gpu_arm(args, rank, world, local_rank):
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     names = ["refit", "contact", "rebind", "rebuild", "chamfer", "contact_without_warm_start",
-             "contact_hinted_unordered", "contact_signed", "contact_on_rebuilt_lbvh", "chamfer_with_warm_start",
+             "contact_hinted_unordered", "contact_signed", "contact_on_rebuilt_lbvh", "chamfer_plain",
              "refit_and_rebind_fused"]
     st = {n: float(np.mean([e[i].elapsed_time(e[i + 1]) for e in evs])) for i, n in enumerate(names)}
 
@@ -377,12 +378,16 @@ def gpu_arm(args, rank, world, local_rank):
         arr = rebuilt.arrays()                                   # the rebuilt tree, as bits
         tree = [arr[k].clone() for k in ("keys", "perm", "parent", "nodes_i")] + \
                [arr["tris"].view(torch.int32).clone()]
-        return [v.clone() for v in contact.values()] + [x.clone() for x in gout] + [cd_out.clone()] + tree
+        return [v.clone() for v in contact.values()] + [x.clone() for x in gout] + [cd_out.clone()] + \
+            [v.clone() for v in cd_ps.values()] + tree
     hint0 = contact["face"].clone()
+    cd_state0 = [cd_ps["faceA"].clone(), cd_ps["faceB"].clone(), cd_step_ws.buf.clone()]
     load_frame(7)
     g.replay()
     conc = frame_outputs()
     contact["face"].copy_(hint0)
+    for x, y in zip((cd_ps["faceA"], cd_ps["faceB"], cd_step_ws.buf), cd_state0):
+        x.copy_(y)
     load_frame(7)
     for gs in stage_graphs[:5]:
         gs.replay()

@@ -472,6 +472,33 @@ mesh_status mesh_chamfer_hinted(const mesh_bvh *A, const float *d_SA, int64_t nS
                                 float *d_dist2A, int32_t *d_faceB, float *d_baryB,
                                 float *d_dist2B, void *stream);
 
+/* Workspace bytes of mesh_chamfer_step for nSA + nSB samples (0 when their sum
+ * exceeds INT32_MAX). */
+size_t mesh_chamfer_step_workspace_bytes(int64_t nSA, int64_t nSB);
+
+/* The Chamfer distance of Sec. 4.2 for a sequence of frames (a physics step or
+ * an optimisation step on the same samples): mesh_chamfer with d_faceA /
+ * d_faceB both the previous call's faces (read first, as warm-start hints:
+ * -1 = none) and this call's (written), and the samples of each side run in
+ * the order of the previous call's costs, heaviest first: each sample's cost
+ * (its node visits / 8 with one lane per sample, its group steps with
+ * several, capped at 127) is kept in d_ws as an 8-bit key with the side in bit
+ * 7, and the next call sorts the keys of both sides with one stable radix
+ * pass, so that the samples sharing a block end together and the longest
+ * searches start first.  d_ws therefore carries state from one call to the
+ * next: pass the same workspace for the same samples; its contents steer only
+ * the order (a fresh or unrelated workspace gives a worse order, never a
+ * wrong answer).  The per-sample outputs equal mesh_chamfer's bit for bit;
+ * d_out equals it up to the order of the float64 sums (each block sums its
+ * samples, and the blocks hold other samples in another order).  d_faceA is
+ * required when nSA > 0, d_faceB when nSB > 0; the other outputs may be NULL.
+ * d_ws: mesh_chamfer_step_workspace_bytes(nSA, nSB), 256-byte aligned;
+ * MESH_ERR_WORKSPACE otherwise. */
+mesh_status mesh_chamfer_step(const mesh_bvh *A, const float *d_SA, int64_t nSA, const mesh_bvh *B,
+                              const float *d_SB, int64_t nSB, void *d_ws, size_t ws_bytes, double *d_out,
+                              int32_t *d_faceA, float *d_baryA, float *d_dist2A, int32_t *d_faceB,
+                              float *d_baryB, float *d_dist2B, void *stream);
+
 /* mesh_chamfer for callers that cannot allocate device memory.  (The paper has
  * no counterpart; this exists for integrations, not for the method.)  Some
  * callers cannot call cudaMalloc -- a physics or renderer plugin whose host

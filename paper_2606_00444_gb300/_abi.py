@@ -83,6 +83,8 @@ SIGNATURES = {
     "mesh_chamfer_workspace_bytes": (SZ, [I64, I64]),
     "mesh_chamfer": (C.c_int, [VP, VP, I64, VP, VP, I64, VP, SZ, VP, VP, VP, VP, VP, VP, VP, VP]),
     "mesh_chamfer_hinted": (C.c_int, [VP, VP, I64, VP, VP, I64, VP, SZ, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP]),
+    "mesh_chamfer_step_workspace_bytes": (SZ, [I64, I64]),
+    "mesh_chamfer_step": (C.c_int, [VP, VP, I64, VP, VP, I64, VP, SZ, VP, VP, VP, VP, VP, VP, VP, VP]),
     "mesh_chamfer_noalloc": (C.c_int, [VP, VP, I64, VP, VP, I64, VP, VP, VP, VP, VP, VP, VP, VP]),
     "mesh_closest_point_backward": (C.c_int, [VP, VP, I64, VP, VP, VP, VP, VP, VP]),
     "mesh_chamfer_backward": (C.c_int, [VP, VP, I64, VP, VP, I64, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP]),

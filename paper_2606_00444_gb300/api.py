@@ -542,6 +542,37 @@ def chamfer(A: MeshBVH, SA: torch.Tensor, B: MeshBVH, SB: torch.Tensor, per_samp
     return (out, ps) if per_sample else out
 
 
+def chamfer_step(A: MeshBVH, SA: torch.Tensor, B: MeshBVH, SB: torch.Tensor, ps: dict, ws: Workspace,
+                 out: torch.Tensor | None = None) -> torch.Tensor:
+    """chamfer() for a sequence of frames on the same samples (mesh_chamfer_step):
+    ps["faceA"] / ps["faceB"] (int32, required) hold the previous call's faces on entry
+    (-1 = none; warm start) and this call's on return, the other entries of ps
+    (baryA, dist2A, baryB, dist2B) are optional outputs, and each side's samples run
+    heaviest first by the costs the previous call left in `ws` (pass the same
+    Workspace every call).  Per-sample results equal chamfer()'s bit for bit; the two
+    means equal it up to the order of the float64 sums."""
+    SA = _f32(SA, 3, "SA")
+    SB = _f32(SB, 3, "SB")
+    nA, nB = SA.shape[0], SB.shape[0]
+    shapes = dict(faceA=(torch.int32, (nA,)), baryA=(torch.float32, (nA, 3)), dist2A=(torch.float32, (nA,)),
+                  faceB=(torch.int32, (nB,)), baryB=(torch.float32, (nB, 3)), dist2B=(torch.float32, (nB,)))
+    for k, (dt, shape) in shapes.items():
+        t = ps.get(k)
+        if t is None:
+            if k in ("faceA", "faceB"):
+                raise ValueError(f"ps[{k!r}] is required")
+            continue
+        if not t.is_cuda or t.dtype != dt or tuple(t.shape) != shape or not t.is_contiguous():
+            raise ValueError(f"ps[{k!r}] must be a contiguous CUDA {dt} tensor of shape {shape}")
+    buf = ws.get(lib().mesh_chamfer_step_workspace_bytes(nA, nB))
+    out = torch.empty(2, dtype=torch.float64, device=SA.device) if out is None else out
+    check(lib().mesh_chamfer_step(A.handle, SA.data_ptr(), nA, B.handle, SB.data_ptr(), nB, buf.data_ptr(),
+                                  buf.numel(), out.data_ptr(), _ptr(ps.get("faceA")), _ptr(ps.get("baryA")),
+                                  _ptr(ps.get("dist2A")), _ptr(ps.get("faceB")), _ptr(ps.get("baryB")),
+                                  _ptr(ps.get("dist2B")), _stream()), "mesh_chamfer_step")
+    return out
+
+
 def l2_read_bandwidth(nbytes: int = 48 << 20, passes: int = 8, repeats: int = 20) -> float:
     """Sustained L2 read bandwidth of the current GPU in GB/s (mesh_probe_l2_read over an
     L2-resident buffer, CUDA events, best of `repeats` after a warm-up)."""

@@ -78,7 +78,8 @@ __device__ __forceinline__ int segment_of(const int *__restrict__ off, int n, in
 }
 
 // Stable LSD radix sort of (key, value) pairs on the low `bits` key bits
-// (lbvh.cu); the workspace is used for the intermediate passes.
+// (lbvh.cu); the workspace is used for the intermediate passes.  vin NULL: the
+// values are the indices (the output is the sorting permutation).
 size_t sort_pairs_ws_bytes(int64_t n);
 void sort_pairs_u32(void *ws, int n, int bits, const unsigned int *kin, const int *vin, unsigned int *kout,
                     int *vout, cudaStream_t s);

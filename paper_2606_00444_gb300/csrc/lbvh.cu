@@ -329,7 +329,7 @@ k_sort_downsweep(const unsigned int *__restrict__ kin, const int *__restrict__ v
         int idx = base + w * (32 * kSortItems) + r * 32 + lane;
         bool valid = idx < n;
         key[r] = valid ? kin[idx] : 0u;
-        val[r] = valid ? vin[idx] : 0;
+        val[r] = valid ? (vin ? vin[idx] : idx) : 0;      // vin NULL: the values are the indices
         unsigned int d = valid ? (key[r] >> shift) & 0xffu : 0x100u;
         unsigned int peers = __match_any_sync(0xffffffffu, d);
         unsigned int before = valid ? s_wcnt[w][d] : 0u;
@@ -1003,6 +1003,7 @@ static void radix_pass(const BuildWs &w, int n, int shift, const unsigned int *k
 
 // Stable sort of (key, value) pairs on the low `bits` key bits (8 per pass),
 // for other kernels of the library; ws holds sort_pairs_ws_bytes(n) bytes.
+// vin NULL: the values are the indices 0 .. n-1 (the sorting permutation).
 size_t sort_pairs_ws_bytes(int64_t n) { return build_ws_layout(nullptr, n).bytes + 256; }
 
 void sort_pairs_u32(void *ws, int n, int bits, const unsigned int *kin, const int *vin, unsigned int *kout,

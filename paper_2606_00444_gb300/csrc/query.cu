@@ -627,9 +627,10 @@ template <int G> __device__ __forceinline__ int grp_incl_scan(int x, int gl) {
     return x;
 }
 
+// steps (when not NULL): the number of group steps this query took (its cost).
 template <int G, bool kRange = false>
 __device__ Hit nearest_group(const Traversal &T, float3 q, float maxd2, bool valid, int2 *stk,
-                             unsigned int *status, int hint_leaf = -1) {
+                             unsigned int *status, int hint_leaf = -1, int *steps = nullptr) {
     const int lane = threadIdx.x & 31;
     const int gl = lane & (G - 1);
     const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
@@ -670,9 +671,11 @@ __device__ Hit nearest_group(const Traversal &T, float3 q, float maxd2, bool val
         sp = 1;
     }
     __syncwarp();
+    int nsteps = 0;
     while (__any_sync(0xffffffffu, sp > 0)) {
         const bool near_full = sp > group_cap<G>() - 2 * G;
         const int take = min(G, sp);
+        nsteps += take > 0;
         bool act = gl < take;
         int2 e = make_int2(0, 0);
         if (act) e = stk[sp - 1 - gl];
@@ -795,6 +798,7 @@ __device__ Hit nearest_group(const Traversal &T, float3 q, float maxd2, bool val
         resolve_ties(T, S, q, status);
         sface = S.leaf >= 0 ? face_of(T, S.leaf) : 0x7fffffff;
     }
+    if (steps) *steps = nsteps;
     return Hit{S.leaf, sface, S.d2};
 }
 
@@ -1436,7 +1440,20 @@ struct ChamferSide {
     float *bary, *dist2;
     const int *hint = nullptr;     // warm start: a face id per sample (-1 = none), may alias face
     const int *iperm = nullptr;    // face -> leaf of the mesh searched
+    // The ordered form (mesh_chamfer_step): slot k runs sample order[k] - base,
+    // and each sample's sort key -- key_side | (127 - its cost, at least 0),
+    // heaviest first -- goes to key[sample] for the next call's order.
+    const int *order = nullptr;
+    int base = 0;
+    unsigned int *key = nullptr;
+    unsigned int key_side = 0;
 };
+
+// Sort key of a Chamfer sample from its cost (node visits / 8 with one lane,
+// group steps with several): lower keys first, so the heaviest run first.
+__device__ __forceinline__ unsigned int chamfer_key(unsigned int side, int cost) {
+    return side | (unsigned int)(127 - min(127, cost));
+}
 
 template <int G, bool kRange = false>
 __global__ void __launch_bounds__(kQueryBlock, G == 1 ? kQueryMinBlocks : 1)
@@ -1453,6 +1470,7 @@ k_chamfer(ChamferSide A2B, ChamferSide B2A, unsigned int nbA, unsigned int *stat
     Traversal T = C.T;
     set_scale(T, C.hdr);
     bool valid = i < C.n;
+    if (valid && C.order) i = (int64_t)C.order[i] - C.base;   // a permutation of this side's samples
     float3 q = valid ? make_float3(C.S[3 * i], C.S[3 * i + 1], C.S[3 * i + 2])
                      : make_float3(0.f, 0.f, 0.f);
     int hint_leaf = -1;
@@ -1462,17 +1480,28 @@ k_chamfer(ChamferSide A2B, ChamferSide B2A, unsigned int nbA, unsigned int *stat
     }
     if constexpr (G == 1) {
         if (valid) {
-            Hit h = nearest<kQueryBlock, kStackShared, false, false, kRange>(
-                T, q, INFINITY, reinterpret_cast<int2 (*)[kQueryBlock]>(stk_mem), status, nullptr, hint_leaf);
+            auto stk = reinterpret_cast<int2 (*)[kQueryBlock]>(stk_mem);
+            Hit h;
+            if (C.key) {
+                Counts c{0, 0};
+                h = nearest<kQueryBlock, kStackShared, false, true, kRange>(T, q, INFINITY, stk, status, &c,
+                                                                            hint_leaf);
+                C.key[i] = chamfer_key(C.key_side, c.visits >> 3);
+            } else {
+                h = nearest<kQueryBlock, kStackShared, false, false, kRange>(T, q, INFINITY, stk, status, nullptr,
+                                                                             hint_leaf);
+            }
             write_hit(T, h, q, i, C.face, C.bary, nullptr, C.dist2);
             d2 = h.leaf >= 0 ? (double)h.d2 : 0.0;
         }
     } else {
+        int steps = 0;
         Hit h = nearest_group<G, kRange>(T, q, INFINITY, valid, stk_mem + (threadIdx.x / G) * group_cap<G>(),
-                                         status, hint_leaf);
+                                         status, hint_leaf, C.key ? &steps : nullptr);
         if (valid && (threadIdx.x & (G - 1)) == 0) {
             write_hit(T, h, q, i, C.face, C.bary, nullptr, C.dist2);
             d2 = h.leaf >= 0 ? (double)h.d2 : 0.0;
+            if (C.key) C.key[i] = chamfer_key(C.key_side, steps);
         }
     }
     double s = block_sum_d(d2, s_red);
@@ -1705,6 +1734,37 @@ static void launch_chamfer(int G, bool range, unsigned grid, const ChamferSide &
     else launch_chamfer_r<false>(G, grid, a2b, b2a, nbA, st, partial, ticket, out, s);
 }
 
+// The Chamfer of a sequence of frames (mesh_chamfer_step): each side's samples
+// run warm-started from the previous call's faces and in the order of the
+// previous call's costs, heaviest first, so that the samples sharing a block
+// end together and the long searches do not trail the launch.  The keys of
+// both sides are sorted together by one stable 8-bit pass (side in bit 7, so
+// the order is side-major); k_chamfer_keys first sets every key's side bit,
+// so a fresh or stale workspace gives a valid, if worse, order.
+__global__ void k_chamfer_keys(unsigned int *__restrict__ key, int nA, int n) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < n) key[c] = (c < nA ? 0u : 128u) | (key[c] & 127u);
+}
+
+struct ChamferStepWs {
+    char *base;                    // mesh_chamfer's workspace (partials, ticket)
+    unsigned int *key, *key_sorted;
+    int *order;
+    void *sort_ws;
+    size_t bytes;
+};
+
+static ChamferStepWs chamfer_step_ws(void *ws, int64_t nSA, int64_t nSB) {
+    size_t off = 0;
+    auto take = [&](size_t b) { size_t o = off; off = align_up(off + b, 256); return o; };
+    int64_t m = nSA + nSB > 0 ? nSA + nSB : 1;
+    size_t oB = take(mesh_chamfer_workspace_bytes(nSA, nSB)), oK = take(4 * m), oS = take(4 * m),
+           oO = take(4 * m), oW = take(sort_pairs_ws_bytes(m));
+    char *b = (char *)ws;
+    return ChamferStepWs{b + oB, (unsigned int *)(b + oK), (unsigned int *)(b + oS), (int *)(b + oO), b + oW,
+                         off};
+}
+
 }  // namespace meshgs
 
 using namespace meshgs;
@@ -1745,17 +1805,12 @@ mesh_status mesh_closest_point_hinted(const mesh_bvh *bvh, const float *d_Q, int
 // each class in the given order), so that a warp holds queries of similar
 // depth -- near the surface (deep searches), near misses, or far away (short
 // ones) -- instead of a mix that runs as long as its slowest lane.  The
-// classes are keys of one stable 8-bit radix pass; any key values give a
-// valid permutation, so a workspace whose classes are stale or garbage only
-// gives a worse order.
-__global__ void k_contact_iota(int n, int *__restrict__ iota) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) iota[i] = i;
-}
-
+// classes are keys of one stable 8-bit radix pass (its values the indices);
+// any key values give a valid permutation, so a workspace whose classes are
+// stale or garbage only gives a worse order.
 struct ContactWs {
     unsigned int *cls, *cls_sorted;
-    int *iota, *order;
+    int *order;
     void *sort_ws;
     size_t bytes;
 };
@@ -1764,11 +1819,9 @@ static ContactWs contact_ws(void *ws, int64_t n) {
     size_t off = 0;
     auto take = [&](size_t b) { size_t o = off; off = align_up(off + b, 256); return o; };
     int64_t m = n > 0 ? n : 1;
-    size_t oC = take(4 * m), oS = take(4 * m), oI = take(4 * m), oO = take(4 * m),
-           oW = take(sort_pairs_ws_bytes(m));
+    size_t oC = take(4 * m), oS = take(4 * m), oO = take(4 * m), oW = take(sort_pairs_ws_bytes(m));
     char *b = (char *)ws;
-    return ContactWs{(unsigned int *)(b + oC), (unsigned int *)(b + oS), (int *)(b + oI), (int *)(b + oO),
-                     b + oW, off};
+    return ContactWs{(unsigned int *)(b + oC), (unsigned int *)(b + oS), (int *)(b + oO), b + oW, off};
 }
 
 mesh_status mesh_knn_project(const mesh_bvh *bvh, const float *d_Q, int64_t nQ, int k,
@@ -1808,9 +1861,7 @@ mesh_status mesh_contact(const mesh_bvh *bvh, const float *d_Q, int64_t nQ, floa
                                          stream);
     cudaStream_t s = (cudaStream_t)stream;
     const int n = (int)nQ;
-    k_contact_iota<<<grid_for(nQ, 256), 256, 0, s>>>(n, w.iota);
-    count_launch();
-    sort_pairs_u32(w.sort_ws, n, 2, w.cls, w.iota, w.cls_sorted, w.order, s);
+    sort_pairs_u32(w.sort_ws, n, 2, w.cls, nullptr, w.cls_sorted, w.order, s);
     float maxd2 = isinf(max_dist) ? INFINITY : max_dist * max_dist;
     Traversal T = traversal_of(bvh, isinf(max_dist));
     Header *h = bvh->hdr();
@@ -1860,6 +1911,47 @@ mesh_status mesh_chamfer_hinted(const mesh_bvh *A, const float *d_SA, int64_t nS
     cudaMemsetAsync(ticket, 0, sizeof(unsigned int), s);
     ChamferSide a2b{traversal_of(B), B->hdr(), d_SA, nSA, d_faceA, d_baryA, d_dist2A, d_hintA, B->iperm()};
     ChamferSide b2a{traversal_of(A), A->hdr(), d_SB, nSB, d_faceB, d_baryB, d_dist2B, d_hintB, A->iperm()};
+    unsigned grid = (unsigned)(nbA + nbB);
+    unsigned *st = &A->hdr()->status;
+    launch_chamfer(G, A->leaf_size > 1 || B->leaf_size > 1, grid, a2b, b2a, (unsigned)nbA, st, partial, ticket,
+                   d_out, s);
+    count_launch();
+    return check_launch();
+}
+
+size_t mesh_chamfer_step_workspace_bytes(int64_t nSA, int64_t nSB) {
+    if (nSA < 0 || nSB < 0 || nSA + nSB > INT32_MAX) return 0;
+    return chamfer_step_ws(nullptr, nSA, nSB).bytes;
+}
+
+mesh_status mesh_chamfer_step(const mesh_bvh *A, const float *d_SA, int64_t nSA, const mesh_bvh *B,
+                              const float *d_SB, int64_t nSB, void *d_ws, size_t ws_bytes, double *d_out,
+                              int32_t *d_faceA, float *d_baryA, float *d_dist2A, int32_t *d_faceB,
+                              float *d_baryB, float *d_dist2B, void *stream) {
+    if (!A || !B || !d_out || nSA < 0 || nSB < 0 || nSA + nSB > INT32_MAX || (nSA > 0 && (!d_SA || !d_faceA)) ||
+        (nSB > 0 && (!d_SB || !d_faceB)))
+        return MESH_ERR_INVALID_ARG;
+    ChamferStepWs w = chamfer_step_ws(d_ws, nSA, nSB);
+    if (!d_ws || ws_bytes < w.bytes || ((uintptr_t)d_ws & 255u)) return MESH_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t need = mesh_chamfer_workspace_bytes(nSA, nSB);
+    int G = pick_group(nSA + nSB);
+    size_t nbA = chamfer_blocks(nSA, G), nbB = chamfer_blocks(nSB, G);
+    double *partial = (double *)w.base;
+    unsigned int *ticket = (unsigned int *)(w.base + need - 256);
+    if (nbA + nbB == 0) {
+        cudaMemsetAsync(d_out, 0, 2 * sizeof(double), s);
+        return check_launch();
+    }
+    const int n = (int)(nSA + nSB);
+    k_chamfer_keys<<<grid_for(n, 256), 256, 0, s>>>(w.key, (int)nSA, n);
+    count_launch();
+    sort_pairs_u32(w.sort_ws, n, 8, w.key, nullptr, w.key_sorted, w.order, s);
+    cudaMemsetAsync(ticket, 0, sizeof(unsigned int), s);
+    ChamferSide a2b{traversal_of(B), B->hdr(), d_SA, nSA, d_faceA, d_baryA, d_dist2A, d_faceA, B->iperm(),
+                    w.order, 0, w.key, 0u};
+    ChamferSide b2a{traversal_of(A), A->hdr(), d_SB, nSB, d_faceB, d_baryB, d_dist2B, d_faceB, A->iperm(),
+                    w.order + nSA, (int)nSA, w.key + nSA, 128u};
     unsigned grid = (unsigned)(nbA + nbB);
     unsigned *st = &A->hdr()->status;
     launch_chamfer(G, A->leaf_size > 1 || B->leaf_size > 1, grid, a2b, b2a, (unsigned)nbA, st, partial, ticket,

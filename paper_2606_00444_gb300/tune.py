@@ -179,10 +179,13 @@ def tune_contact(bvh: MeshBVH, Q: torch.Tensor, max_dist: float, frames=None, re
 
 
 def tune_chamfer(A: MeshBVH, SA: torch.Tensor, B: MeshBVH, SB: torch.Tensor, repeats: int = 5,
-                 force: bool = False) -> dict:
-    """Pick the lanes per query of the Chamfer kernel (process-wide setting)."""
+                 force: bool = False, step: bool = False) -> dict:
+    """Pick the lanes per query of the Chamfer kernel (process-wide setting), timing
+    chamfer() or, with step=True, chamfer_step() (the ordered, warm-started form of a
+    sequence: each candidate times its own warmed-up state)."""
+    from .api import Workspace, chamfer_step
     _load()
-    key = _key("chamfer", A.n_faces + B.n_faces, SA.shape[0] + SB.shape[0], False)
+    key = _key("chamfer_step" if step else "chamfer", A.n_faces + B.n_faces, SA.shape[0] + SB.shape[0], False)
     if key in _CACHE and not force:
         set_query_group(_CACHE[key]["lanes"])
         return _CACHE[key]
@@ -190,7 +193,16 @@ def tune_chamfer(A: MeshBVH, SA: torch.Tensor, B: MeshBVH, SB: torch.Tensor, rep
     results = []
     for g in (1, 2, 4, 8, 16, 32):
         set_query_group(g)
-        results.append(dict(lanes=g, ms=_time(lambda: chamfer(A, SA, B, SB, out=res), repeats)))
+        if step:
+            dev = SA.device
+            ps = dict(faceA=torch.full((SA.shape[0],), -1, dtype=torch.int32, device=dev),
+                      faceB=torch.full((SB.shape[0],), -1, dtype=torch.int32, device=dev))
+            ws = Workspace(dev)
+            chamfer_step(A, SA, B, SB, ps, ws, out=res)           # faces and costs of this state
+            fn = lambda: chamfer_step(A, SA, B, SB, ps, ws, out=res)   # noqa: E731
+        else:
+            fn = lambda: chamfer(A, SA, B, SB, out=res)              # noqa: E731
+        results.append(dict(lanes=g, ms=_time(fn, repeats)))
     best = _pick(results)
     best = dict(lanes=best["lanes"], variant=0, ms=best["ms"],
                 tried={str(r["lanes"]): round(r["ms"], 4) for r in results})

@@ -40,6 +40,11 @@ def test_sizes_are_monotone_and_reject_bad_input():
     assert L.mesh_build_workspace_bytes(200000) >= 200000 * 32
     assert L.mesh_build_workspace_bytes(-5) == 0
     assert L.mesh_chamfer_workspace_bytes(1 << 20, 1 << 20) >= 8 * 2 * (1 << 20) // 128
+    # the ordered Chamfer keeps a 4-byte key, its sorted copy and the order per sample
+    assert L.mesh_chamfer_step_workspace_bytes(10000, 10000) >= \
+        L.mesh_chamfer_workspace_bytes(10000, 10000) + 3 * 4 * 20000
+    assert L.mesh_chamfer_step_workspace_bytes(-1, 4) == 0
+    assert L.mesh_chamfer_step_workspace_bytes(1 << 31, 1 << 31) == 0
 
 
 def test_create_validates_storage_on_the_host():
@@ -72,6 +77,15 @@ def test_create_validates_storage_on_the_host():
     assert L.mesh_closest_point(h, fake, 0, C.c_float(1.0), None, None, None, None, None) == 0
     assert L.mesh_bind_gaussians(h, None, None, None, 3, None, None, None, None) == 1
     assert L.mesh_chamfer(h, fake, 4, h, fake, 4, None, 0, fake, *([None] * 6), None) == 3
+    # the ordered Chamfer: the face arrays (hints in, faces out) are required
+    assert L.mesh_chamfer_step(h, fake, 4, h, fake, 4, fake, 1 << 30, fake, None, None, None,
+                               fake, None, None, None) == 1
+    assert L.mesh_chamfer_step(h, fake, 4, h, fake, 4, fake, 1 << 30, fake, fake, None, None,
+                               None, None, None, None) == 1
+    assert L.mesh_chamfer_step(h, fake, 4, h, fake, 4, None, 0, fake, fake, None, None,
+                               fake, None, None, None) == 3
+    assert L.mesh_chamfer_step(h, fake, 4, h, fake, 4, fake + 8, 1 << 30, fake, fake, None, None,
+                               fake, None, None, None) == 3
     # Chamfer backward: a missing gradient seed, faces or weights; no outputs = no work
     assert L.mesh_chamfer_backward(h, fake, 4, h, fake, 4, None, fake, fake, fake, fake,
                                    fake, None, None, None, None) == 1

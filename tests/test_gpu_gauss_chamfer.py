@@ -230,6 +230,45 @@ def test_chamfer_warm_start_hints_give_identical_results(pair, lanes):
         set_query_group(0)
 
 
+@pytest.mark.parametrize("lanes,garbage", [(1, False), (16, False), (16, True), (4, True)])
+def test_chamfer_step_over_frames_equals_plain_chamfer(lanes, garbage):
+    """mesh_chamfer_step over a skinned sequence (warm start from the previous frame's
+    faces, samples run heaviest first by the costs the previous call left in the
+    workspace) gives mesh_chamfer's per-sample results bit for bit every frame, and
+    its means up to the order of the float64 sums; a workspace of random bytes only
+    changes the first frame's order."""
+    from paper_2606_00444_gb300 import Workspace, chamfer_step, set_query_group
+    V0, F = torus(120, 60)
+    skin = TorusSkinning(V0, seed=12)
+    fs, bs = sample_surface(V0, F, 3000, seed=5)
+    rf, rb = sample_surface(V0, F, 2500, seed=6)
+    SB = dev(points_from(V0, F, rf, rb))
+    rest = MeshBVH.from_mesh(dev(V0), dev(F), method="ploc")
+    A = MeshBVH.from_mesh(dev(V0), dev(F), method="ploc")
+    nA, nB = fs.shape[0], SB.shape[0]
+    ws = Workspace(torch.device("cuda"))
+    if garbage:
+        from paper_2606_00444_gb300 import lib
+        buf = ws.get(lib().mesh_chamfer_step_workspace_bytes(nA, nB))
+        buf.copy_(torch.randint(0, 256, buf.shape, dtype=torch.uint8, device="cuda"))
+    ps = dict(faceA=dev(np.full(nA, -1, np.int32)), baryA=torch.empty(nA, 3, device="cuda"),
+              dist2A=torch.empty(nA, device="cuda"), faceB=dev(np.full(nB, -1, np.int32)),
+              baryB=torch.empty(nB, 3, device="cuda"), dist2B=torch.empty(nB, device="cuda"))
+    try:
+        set_query_group(lanes)
+        for t in range(0, 40, 8):
+            A.refit(dev(skin.frame(t)))
+            SA = A.interpolate(dev(fs), dev(bs))
+            ref, rps = chamfer(A, SA, rest, SB, per_sample=True)
+            out = chamfer_step(A, SA, rest, SB, ps, ws)
+            for k in rps:
+                assert torch.equal(ps[k], rps[k]), (t, k)
+            torch.testing.assert_close(out, ref, rtol=1e-12, atol=0)
+        assert A.status()[0] == 0 and rest.status()[0] == 0
+    finally:
+        set_query_group(0)
+
+
 @pytest.mark.parametrize("lanes", [2, 8, 32])
 def test_closest_point_hints_in_cooperative_groups(pair, lanes):
     from paper_2606_00444_gb300 import set_query_group
@@ -290,6 +329,40 @@ def test_refit_bind_equals_refit_then_bind(mesh):
     for x, y in zip(got2, ref2):
         assert torch.equal(x, y)
     assert b.status()[0] == 0
+
+
+def test_refit_bind_skewed_counts_and_no_gaussians():
+    """The one-thread-per-Gaussian phase over skewed counts: most faces with none, a few
+    with thousands (many passes of a block's threads, long runs of empty leaves in the
+    slot search); and a CSR with no Gaussians at all (the refit alone)."""
+    V0, F = icosphere(4)
+    V1 = (V0 * 0.9 + 0.03 * np.cos(5 * V0[:, [2, 0, 1]])).astype(np.float32)
+    rng = np.random.default_rng(77)
+    nF = F.shape[0]
+    counts = np.where(rng.random(nF) < 0.7, 0, rng.integers(1, 3, nF))
+    counts[rng.choice(nF, 3, replace=False)] = [3000, 1700, 513]
+    gface = np.repeat(np.arange(nF), counts).astype(np.int32)
+    gstart = np.concatenate([[0], np.cumsum(counts)]).astype(np.int32)
+    G = int(gstart[-1])
+    gbary = osada_barycentrics(rng, G).astype(np.float32)
+    goff = rng.normal(scale=0.02, size=G).astype(np.float32)
+    a = MeshBVH.from_mesh(dev(V0), dev(F))
+    b = MeshBVH.from_mesh(dev(V0), dev(F))
+    a.refit(dev(V1))
+    ref = a.bind_gaussians(dev(gface), dev(gbary), dev(goff))
+    got = b.refit_bind(dev(V1), dev(gstart), dev(gbary), dev(goff))
+    assert torch.equal(a.arrays()["nodes_i"], b.arrays()["nodes_i"])
+    for x, y in zip(got, ref):
+        assert torch.equal(x, y)
+    assert b.status()[0] == 0
+    # no Gaussians: the refit alone
+    empty = np.zeros(nF + 1, np.int32)
+    c = MeshBVH.from_mesh(dev(V0), dev(F))
+    V2 = (V0 * np.float32(1.1)).astype(np.float32)
+    c.refit_bind(dev(V2), dev(empty), torch.empty(0, 3, device="cuda"))
+    a.refit(dev(V2))
+    assert torch.equal(a.arrays()["nodes_i"], c.arrays()["nodes_i"])
+    assert c.status()[0] == 0
 
 
 def test_refit_bind_bad_ranges_set_status():

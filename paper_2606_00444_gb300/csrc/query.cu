@@ -649,9 +649,12 @@ __device__ Hit nearest_group(const Traversal &T, float3 q, float maxd2, bool val
     } else if (valid && T.n > 1) {
         // Greedy dive (every lane of the group on the same path): the nearer
         // child down to a leaf gives the parallel phase a tight window from
-        // the start, so the shared stack stays small.
-        int node = 0;
-        while (true) {
+        // the start, so the shared stack stays small.  A warm-start face gives
+        // that window without the dive (one serial step per tree level, with
+        // every lane on the same node).
+        int node = hint_leaf >= 0 ? -1 : 0;
+        if (node < 0) test_leaf(T, S, hint_leaf, q, maxd2);
+        while (node >= 0) {
             const float4 *r = T.nodes + 4 * (size_t)node;
             float4 l0 = ldg4(r), l1 = ldg4(r + 1), r0 = ldg4(r + 2), r1 = ldg4(r + 3);
             float dl = box_d2(q, l0, l1), dr = box_d2(q, r0, r1);
@@ -661,11 +664,10 @@ __device__ Hit nearest_group(const Traversal &T, float3 q, float maxd2, bool val
             int c = lfirst ? __float_as_int(l0.w) : __float_as_int(r0.w);
             if (c >= 0) { node = c; continue; }
             test_range<kRange>(T, S, -c - 1, link_count(lfirst ? l1 : r1), q, maxd2);
-            if (hint_leaf >= 0) test_leaf(T, S, hint_leaf, q, maxd2);   // warm start
             break;
         }
         if (S.leaf >= 0) sface = face_of(T, S.leaf);
-        acc = S.other;                               // faces the dive met and did not keep
+        acc = S.other;                               // faces met and not kept
         S.other = S.other < 0.0f ? -1.0f : INFINITY;
         if (gl == 0) stk[0] = make_int2(0, __float_as_int(0.0f));
         sp = 1;

@@ -1062,9 +1062,10 @@ def fit_measure(n_steps):
     form: the same loss evaluated forward only (no autograd, no gradient kernels) on the
     same template, whose value must equal the differentiable forward's bit for bit."""
     import torch
-    from paper_2606_00444_gb300 import MeshBVH, chamfer, morton_order
-    from paper_2606_00444_gb300.autograd import Chamfer, Interpolate, PointMeshDistance
+    from paper_2606_00444_gb300 import MeshBVH, chamfer_step, morton_order, set_query_group
+    from paper_2606_00444_gb300.autograd import Chamfer, Interpolate, PointMeshDistance, chamfer_state
     from workloads.isosurface import BlobSequence
+    set_query_group(0)            # lanes per sample from the sample count (not the frame's tuning)
     from workloads.meshes import icosphere
     dev = torch.device("cuda")
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
@@ -1084,16 +1085,19 @@ def fit_measure(n_steps):
     SG = SG[morton_order(SG).long()].contiguous()
     V = t(VT).requires_grad_(True)
     opt = torch.optim.Adam([V], lr=1e-3)
+    # the Chamfer of each step is a step of the sequence (mesh_chamfer_step): warm-started
+    # from the previous step's faces, samples heaviest first by the previous step's costs
+    state = chamfer_state(ns, ns, dev)
 
     def loss_of(Vx, grad):
         if grad:
             ST = Interpolate.apply(Vx, tmpl, ft, bt)
-            cd = Chamfer.apply(ST, Vx, tmpl, SG, VGd, targ)
+            cd = Chamfer.apply(ST, Vx, tmpl, SG, VGd, targ, state)
             d2v, _ = PointMeshDistance.apply(Vx, VGd, targ)
             return cd[0] + cd[1] + d2v.mean()
         tmpl.refit(Vx)                                   # the plain per-frame form
         ST = tmpl.interpolate(ft, bt)
-        cd = chamfer(tmpl, ST, targ, SG)
+        cd = chamfer_step(tmpl, ST, targ, SG, state["ps"], state["ws"])
         d2v = targ.closest_point(Vx, want=("dist2",))["dist2"]
         return cd[0] + cd[1] + d2v.mean()
 
@@ -1129,6 +1133,11 @@ def fit_measure(n_steps):
         torch.cuda.synchronize()
         if k >= 2:
             fwd.append(a.elapsed_time(b))
+    # both forms from the same state (faces and sample order), so the sums match bit for bit
+    snap = [v.clone() for v in state["ps"].values()] + [state["ws"].buf.clone()]
+    lp = loss_of(Vc, False)
+    for x, y in zip(list(state["ps"].values()) + [state["ws"].buf], snap):
+        x.copy_(y)
     ld = loss_of(Vc.clone().requires_grad_(True), True)
     torch.cuda.synchronize()
     if not torch.equal(lp.detach(), ld.detach()):

@@ -11,7 +11,17 @@ import math
 
 import torch
 
-from .api import MeshBVH, chamfer, chamfer_backward
+from .api import MeshBVH, Workspace, chamfer, chamfer_backward, chamfer_step
+
+
+def chamfer_state(nA: int, nB: int, device="cuda") -> dict:
+    """State for Chamfer.apply over a sequence of steps on the same samples (an
+    optimisation, a simulation): the per-sample faces (-1 = none yet) and the
+    workspace of mesh_chamfer_step that carries the samples' costs to the next step."""
+    dev = torch.device(device)
+    ps = dict(faceA=torch.full((nA,), -1, dtype=torch.int32, device=dev), baryA=torch.empty(nA, 3, device=dev),
+              faceB=torch.full((nB,), -1, dtype=torch.int32, device=dev), baryB=torch.empty(nB, 3, device=dev))
+    return dict(ps=ps, ws=Workspace(dev))
 
 
 class PointMeshDistance(torch.autograd.Function):
@@ -63,13 +73,20 @@ class Interpolate(torch.autograd.Function):
 
 class Chamfer(torch.autograd.Function):
     """[mean_a d(a, B)^2, mean_b d(b, A)^2] for samples SA / SB and meshes (VA, bvhA),
-    (VB, bvhB); differentiable in SA, VA, SB and VB."""
+    (VB, bvhB); differentiable in SA, VA, SB and VB.  With `state` (chamfer_state) the
+    forward is the step of a sequence (mesh_chamfer_step: warm-started from the previous
+    step's faces, samples heaviest first): the same per-sample faces and weights, hence
+    the same gradients (up to the order of the backward's float atomic sums)."""
 
     @staticmethod
-    def forward(ctx, SA, VA, bvhA: MeshBVH, SB, VB, bvhB: MeshBVH):
+    def forward(ctx, SA, VA, bvhA: MeshBVH, SB, VB, bvhB: MeshBVH, state=None):
         bvhA.refit(VA.detach())
         bvhB.refit(VB.detach())
-        out, ps = chamfer(bvhA, SA.detach(), bvhB, SB.detach(), per_sample=True)
+        if state is None:
+            out, ps = chamfer(bvhA, SA.detach(), bvhB, SB.detach(), per_sample=True)
+        else:
+            out = chamfer_step(bvhA, SA.detach(), bvhB, SB.detach(), state["ps"], state["ws"])
+            ps = {k: v.clone() for k, v in state["ps"].items()}   # the next step rewrites the state
         ctx.save_for_backward(SA.detach(), VA.detach(), SB.detach(), VB.detach(), ps["faceA"],
                               ps["baryA"], ps["faceB"], ps["baryB"])
         ctx.bvhA, ctx.bvhB = bvhA, bvhB
@@ -89,7 +106,7 @@ class Chamfer(torch.autograd.Function):
         chamfer_backward(bvhA, SA, bvhB, SB, g.detach().to(torch.float64).contiguous(),
                          dict(faceA=faceA, baryA=baryA, faceB=faceB, baryB=baryB),
                          gSA, gVA, gSB, gVB)
-        return gSA, gVA, None, gSB, gVB, None
+        return gSA, gVA, None, gSB, gVB, None, None
 
 
 class BindGaussians(torch.autograd.Function):

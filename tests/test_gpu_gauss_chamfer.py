@@ -163,6 +163,37 @@ def test_autograd_template_fit_gradient_matches_oracle():
     assert_grad_close(host(V.grad), ref, 1e-4)
 
 
+def test_autograd_chamfer_with_sequence_state_gives_the_same_gradients():
+    """Chamfer.apply with a chamfer_state (the ordered, warm-started step) over a few
+    optimisation steps: the same per-step loss (up to the float64 sum order) and the same
+    gradient as the stateless form on the same vertices (the same faces and weights; the
+    vertex gradients are accumulated with float atomics, so up to their order)."""
+    from paper_2606_00444_gb300.autograd import chamfer_state
+    VT, FT = icosphere(3, radius=0.95)
+    VG, FG = displaced_icosphere(3, 0.1, 0.4)
+    ft, bt = sample_surface(VT, FT, 6000, seed=21)
+    SG = dev(points_from(VG, FG, *sample_surface(VG, FG, 5000, seed=22)))
+    tmpl = MeshBVH.from_mesh(dev(VT), dev(FT))
+    targ = MeshBVH.from_mesh(dev(VG), dev(FG))
+    VGd = dev(VG)
+    state = chamfer_state(6000, 5000)
+    rng = np.random.default_rng(23)
+    Vk = VT.copy()
+    for step in range(4):
+        grads, losses = [], []
+        for st in (None, state):
+            V = dev(Vk).requires_grad_(True)
+            ST = Interpolate.apply(V, tmpl, dev(ft), dev(bt))
+            cd = Chamfer.apply(ST, V, tmpl, SG, VGd, targ, st)
+            loss = cd[0] + cd[1]
+            loss.backward()
+            grads.append(V.grad.clone())
+            losses.append(loss.item())
+        torch.testing.assert_close(grads[1], grads[0], rtol=1e-5, atol=1e-6 * float(grads[0].abs().max()))
+        assert losses[1] == pytest.approx(losses[0], rel=1e-12)
+        Vk = (Vk + 0.004 * rng.normal(size=Vk.shape)).astype(np.float32)
+
+
 def test_autograd_bind_gaussians_matches_oracle_backward():
     V, F = displaced_icosphere(2, 0.1, 0.8)
     rng = np.random.default_rng(13)

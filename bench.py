@@ -916,6 +916,20 @@ def bench_sequence(args):
     """Varying-topology conversion (template projection, Eq. 2): per frame the extracted
     target is rebuilt, the 10242 template vertices projected onto it, the template refit
     and its 20480 Gaussians updated, and the Chamfer distance (10k + 10k samples) taken."""
+    r = sequence_measure(args.steps, args.warmup)
+    line = {"metric": METRIC, "value": r["queries_per_frame"] / (r["ms_per_frame"] * 1e-3), "unit": "queries/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_frame"],
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "varying-topology sequence: marching cubes 128^3 of a 4-sphere "
+                                   "smooth union, template icosphere 10242 V / 20480 F projected per "
+                                   "frame", "frames": r["frames"], "target_faces": r["target_faces"]},
+            "stages_ms": r["stages_ms"], "chamfer_last": r["chamfer_last"]}
+    print(json.dumps(line))
+
+
+def sequence_measure(steps, warmup):
+    """The varying-topology frame of bench_sequence, timed over `steps` frames (events
+    around each stage, L2 flushed before each frame)."""
     import torch
     from paper_2606_00444_gb300 import MeshBVH, Workspace, chamfer, morton_order
     from workloads.isosurface import BlobSequence
@@ -923,7 +937,7 @@ def bench_sequence(args):
     dev = torch.device("cuda")
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     mo = lambda P: P[morton_order(P).long()].contiguous()   # samples stored in Morton order
-    nfr = min(120, max(args.steps + args.warmup, 8))
+    nfr = min(120, max(steps + warmup, 8))
     seq = BlobSequence(2000)
     frames = [seq.mesh(k) for k in range(nfr)]
     tg = [(t(v), t(f), mo(t(points_from(v, f, *sample_surface(v, f, N_CD, seed=2100 + k)))))
@@ -963,26 +977,19 @@ def bench_sequence(args):
         e[5].record()
         return e
 
-    for k in range(args.warmup):
+    for k in range(warmup):
         frame(k)
     torch.cuda.synchronize()
-    for k in range(args.steps):
+    for k in range(steps):
         flush.fill_(float(k))
-        ev.append(frame(args.warmup + k))
+        ev.append(frame(warmup + k))
     torch.cuda.synchronize()
     names = ["rebuild", "project", "refit", "rebind", "chamfer"]
     st = {n: float(np.mean([e[i].elapsed_time(e[i + 1]) for e in ev])) for i, n in enumerate(names)}
     ms = float(np.mean([e[0].elapsed_time(e[5]) for e in ev]))
-    q = len(VT) + 2 * N_CD
-    line = {"metric": METRIC, "value": q / (ms * 1e-3), "unit": "queries/s", "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "varying-topology sequence: marching cubes 128^3 of a 4-sphere "
-                                   "smooth union, template icosphere 10242 V / 20480 F projected per "
-                                   "frame", "frames": nfr,
-                       "target_faces": [int(min(len(f) for _, f in frames)), int(maxF)]},
-            "stages_ms": st, "chamfer_last": [float(x) for x in cd_out.cpu()]}
-    print(json.dumps(line))
+    return {"ms_per_frame": ms, "stages_ms": st, "frames": nfr, "queries_per_frame": len(VT) + 2 * N_CD,
+            "target_faces": [int(min(len(f) for _, f in frames)), int(maxF)],
+            "chamfer_last": [float(x) for x in cd_out.cpu()]}
 
 
 def bench_tracking(args):
@@ -1288,12 +1295,14 @@ def main():
     if not args.no_extras and world == 1:
         # the other configurations: batched vs per-scene launches (same outputs, 5
         # frames), the template fit's 300 Adam steps vs the plain forward (same loss),
-        # and the refit of a 2.4M-face mesh
+        # the varying-topology sequence (12 frames of rebuild, projection, refit, rebind
+        # and Chamfer), and the refit of a 2.4M-face mesh
         import torch
         torch.cuda.empty_cache()
         line["batched_64_scenes"] = batch_measure(5, 3)
         torch.cuda.empty_cache()
         line["template_fit"] = fit_measure(300)
+        line["varying_topology_sequence"] = sequence_measure(12, 4)
         torch.cuda.empty_cache()
         line["refit_2_4M_faces"] = refit_large_measure(10, 3)
     if not args.no_cpu_baseline and world == 1:

@@ -92,6 +92,34 @@ void exclusive_scan_int(const int *in, int *out, int n, int *bsum, int *total, c
 void count_launch(int n = 1);
 mesh_status check_launch();
 
+// Programmatic dependent launch (sm_90 and later).  A kernel launched with
+// pdl_launch may be scheduled before the kernel ahead of it in the stream has
+// finished: it calls pdl_wait() (griddepcontrol.wait) before its first access
+// to memory, which returns once that kernel has completed and its writes are
+// visible, so the ordering is that of a plain launch and only the launch
+// latency is hidden.  pdl_trigger() (griddepcontrol.launch_dependents) lets the
+// next such kernel be scheduled once every block of this one has started.  A
+// kernel launched plainly passes both at once.  Errors surface through
+// check_launch().
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline void pdl_launch(void (*kernel)(KArgs...), unsigned int grid, unsigned int block, size_t smem, cudaStream_t s,
+                       Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 inline unsigned int grid_for(int64_t n, int block) {

@@ -218,9 +218,12 @@ __global__ void k_morton(const float4 *__restrict__ cent, int nF,
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kSortThreads)
 k_sort_upsweep(const unsigned int *__restrict__ keys, int n, int shift,
-               unsigned int *__restrict__ hist, int T) {
+               unsigned int *__restrict__ hist, int T, unsigned int *__restrict__ ticket) {
     __shared__ unsigned int h[kRadix];
+    pdl_wait();
+    pdl_trigger();
     h[threadIdx.x] = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *ticket = 0u;   // the scan's ticket (it runs after this kernel)
     __syncthreads();
     int base = blockIdx.x * kSortTile;
     int lane = threadIdx.x & 31;
@@ -275,6 +278,8 @@ k_sort_scan(unsigned int *__restrict__ hist, int T, unsigned int *__restrict__ d
             unsigned int *__restrict__ base, unsigned int *__restrict__ ticket) {
     __shared__ unsigned int s_warp[33];
     __shared__ bool s_last;
+    pdl_wait();
+    pdl_trigger();
     unsigned int *h = hist + (size_t)blockIdx.x * T;
     unsigned int carry = 0;
     const int chunk = kScanThreads * 4;
@@ -317,6 +322,8 @@ k_sort_downsweep(const unsigned int *__restrict__ kin, const int *__restrict__ v
     __shared__ unsigned int s_dstart[kRadix];
     __shared__ unsigned int s_goff[kRadix];
     __shared__ unsigned int s_warp[33];
+    pdl_wait();
+    pdl_trigger();
     int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     for (int i = tid; i < kSortWarps * kRadix; i += kSortThreads) (&s_wcnt[0][0])[i] = 0;
     __syncthreads();
@@ -630,6 +637,8 @@ k_refit_local(int n, const float *__restrict__ V3, int nV, float4 *__restrict__ 
               float4 *__restrict__ bbox, int4 *__restrict__ xlist, int *__restrict__ xcnt,
               int *__restrict__ iperm, Header *__restrict__ hdr, Rebind RB, int leaf_size) {
     extern __shared__ float4 dsm[];
+    pdl_wait();
+    pdl_trigger();
     float *tab = reinterpret_cast<float *>(dsm);
     int *s_warp = reinterpret_cast<int *>(tab + (kBind ? kBindFloats : 12) * kRefitBlock);
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -754,6 +763,8 @@ __global__ void __launch_bounds__(kTopThreads)
 k_refit_top(const int4 *__restrict__ xlist, const int *__restrict__ xcnt, const float4 *__restrict__ pre,
             const float4 *__restrict__ suf, const float4 *__restrict__ bbox, float4 *__restrict__ nodes,
             Header *__restrict__ hdr, int leaf_size) {
+    pdl_wait();
+    pdl_trigger();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = kTopThreads >> 5;
     const int cnt = xcnt[blockIdx.x];
     for (int r = wid; r < cnt; r += nw) {
@@ -975,13 +986,12 @@ static BuildWs build_ws_layout(char *base, int64_t nF) {
 // out_vals).  out_keys may be w.keysA (the last pass reads B).
 static void radix_sort_pairs(const BuildWs &w, int n, unsigned int *out_keys, int *out_vals,
                              cudaStream_t s) {
-    cudaMemsetAsync(w.ticket, 0, sizeof(unsigned int), s);   // each pass's last block re-zeroes it
     unsigned int *kin = w.keysA, *kout = w.keysB;
     int *vin = w.valsA, *vout = w.valsB;
     for (int pass = 0; pass < 4; ++pass) {
         if (pass == 3) { kout = out_keys; vout = out_vals; }
         int shift = 8 * pass;
-        k_sort_upsweep<<<w.tiles, kSortThreads, 0, s>>>(kin, n, shift, w.hist, w.tiles);
+        k_sort_upsweep<<<w.tiles, kSortThreads, 0, s>>>(kin, n, shift, w.hist, w.tiles, w.ticket);
         k_sort_scan<<<kRadix, kScanThreads, 0, s>>>(w.hist, w.tiles, w.dsum, w.dbase, w.ticket);
         k_sort_downsweep<<<w.tiles, kSortThreads, 0, s>>>(kin, vin, kout, vout, n, shift, w.hist,
                                                           w.tiles, w.dbase);
@@ -991,13 +1001,16 @@ static void radix_sort_pairs(const BuildWs &w, int n, unsigned int *out_keys, in
     }
 }
 
+// One pass for the other kernels of the library, its three kernels launched as
+// programmatic dependents (the contact and Chamfer steps' orders run on a
+// frame's critical path, where the launch latency counts).  The build's passes
+// above use plain launches: there the early-launched grids measured slower.
 static void radix_pass(const BuildWs &w, int n, int shift, const unsigned int *kin, const int *vin,
                        unsigned int *kout, int *vout, cudaStream_t s) {
-    cudaMemsetAsync(w.ticket, 0, sizeof(unsigned int), s);
-    k_sort_upsweep<<<w.tiles, kSortThreads, 0, s>>>(kin, n, shift, w.hist, w.tiles);
-    k_sort_scan<<<kRadix, kScanThreads, 0, s>>>(w.hist, w.tiles, w.dsum, w.dbase, w.ticket);
-    k_sort_downsweep<<<w.tiles, kSortThreads, 0, s>>>(kin, vin, kout, vout, n, shift, w.hist, w.tiles,
-                                                      w.dbase);
+    pdl_launch(k_sort_upsweep, w.tiles, kSortThreads, 0, s, kin, n, shift, w.hist, w.tiles, w.ticket);
+    pdl_launch(k_sort_scan, kRadix, kScanThreads, 0, s, w.hist, w.tiles, w.dsum, w.dbase, w.ticket);
+    pdl_launch(k_sort_downsweep, w.tiles, kSortThreads, 0, s, kin, vin, kout, vout, n, shift, w.hist, w.tiles,
+               w.dbase);
     count_launch(3);
 }
 
@@ -1407,8 +1420,8 @@ static mesh_status bottom_up(mesh_bvh *bvh, const float *V3, cudaStream_t s,
         bvh->leaf_size);
     count_launch();
     if (nb > 1) {
-        k_refit_top<<<nb, kTopThreads, 0, s>>>(xlist, xcnt, pre, suf, bbox, bvh->nodes(), bvh->hdr(),
-                                               bvh->leaf_size);
+        pdl_launch(k_refit_top, nb, kTopThreads, 0, s, xlist, xcnt, pre, suf, bbox, bvh->nodes(), bvh->hdr(),
+                   bvh->leaf_size);
         count_launch();
     }
     return check_launch();

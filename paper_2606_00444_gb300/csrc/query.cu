@@ -868,6 +868,7 @@ k_closest_point(Traversal T, const Header *__restrict__ hdr, unsigned int *statu
                 float *point, float *dist2, const int *hint, const int *__restrict__ iperm,
                 const int *__restrict__ order = nullptr, unsigned int *__restrict__ cls = nullptr) {
     __shared__ int2 stk[kSmem > 0 ? kSmem : 1][kBlock];
+    pdl_wait();
     int64_t k = (int64_t)blockIdx.x * kBlock + threadIdx.x;
     if (k >= nQ) return;
     const int64_t i = order ? (int64_t)order[k] : k;       // order: a permutation of the queries
@@ -979,6 +980,7 @@ k_closest_point_packet(Traversal T, const Header *__restrict__ hdr, unsigned int
                        float *point, float *dist2, const int *hint, const int *__restrict__ iperm,
                        const int *__restrict__ order = nullptr, unsigned int *__restrict__ cls = nullptr) {
     __shared__ int wstk[kQueryBlock / 32][kStackTotal];
+    pdl_wait();
     const int64_t w0 = (int64_t)blockIdx.x * kQueryBlock + (threadIdx.x & ~31);
     if (w0 >= nQ) return;                                  // whole warp past the end
     const int64_t k = w0 + (threadIdx.x & 31);
@@ -1465,6 +1467,7 @@ k_chamfer(ChamferSide A2B, ChamferSide B2A, unsigned int nbA, unsigned int *stat
     __shared__ int2 stk_mem[kStk];
     __shared__ double s_red[kQueryBlock / 32];
     __shared__ bool s_last;
+    pdl_wait();
     bool first = blockIdx.x < nbA;
     ChamferSide &C = first ? A2B : B2A;
     int64_t i = ((int64_t)(first ? blockIdx.x : blockIdx.x - nbA) * kQueryBlock + threadIdx.x) / G;
@@ -1676,64 +1679,73 @@ static void launch_contact(Traversal T, Header *h, const float *d_Q, int64_t nQ,
                            unsigned int *cls, int variant, int blk, cudaStream_t s) {
     if (R && !(variant == 0 || variant == 2 || variant == 3 || variant == 12)) variant = 0;
     unsigned int grid = grid_for(nQ, kQueryBlock);
+    // every form runs right after the sort of the classes: launched as its dependent
+    auto go = [&](auto kern, unsigned int g, unsigned int b) {
+        pdl_launch(kern, g, b, 0, s, T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2,
+                   d_face, iperm, order, cls);
+    };
     if (variant == 12) {
-        k_closest_point_packet<true, R><<<grid, kQueryBlock, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face,
-                                                                     d_bary, d_point, d_dist2, d_face, iperm,
-                                                                     order, cls);
+        go(k_closest_point_packet<true, R>, grid, kQueryBlock);
         return;
     }
     if (blk != kQueryBlock && (variant == 0 || variant == 2 || variant == 3)) {
         unsigned int gb = grid_for(nQ, blk);
-#define MESH_CTB(SM, B) k_closest_point<SM, 0, kQueryMinBlocks, true, B, R><<<gb, B, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2, d_face, iperm, order, cls)
         if (blk == 32) {
-            if (variant == 2) MESH_CTB(8, 32); else if (variant == 3) MESH_CTB(0, 32); else MESH_CTB(kStackShared, 32);
+            if (variant == 2) go(k_closest_point<8, 0, kQueryMinBlocks, true, 32, R>, gb, 32);
+            else if (variant == 3) go(k_closest_point<0, 0, kQueryMinBlocks, true, 32, R>, gb, 32);
+            else go(k_closest_point<kStackShared, 0, kQueryMinBlocks, true, 32, R>, gb, 32);
         } else {
-            if (variant == 2) MESH_CTB(8, 64); else if (variant == 3) MESH_CTB(0, 64); else MESH_CTB(kStackShared, 64);
+            if (variant == 2) go(k_closest_point<8, 0, kQueryMinBlocks, true, 64, R>, gb, 64);
+            else if (variant == 3) go(k_closest_point<0, 0, kQueryMinBlocks, true, 64, R>, gb, 64);
+            else go(k_closest_point<kStackShared, 0, kQueryMinBlocks, true, 64, R>, gb, 64);
         }
-#undef MESH_CTB
         return;
     }
-#define MESH_CT_ARGS <<<grid, kQueryBlock, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2, d_face, iperm, order, cls)
     switch (variant) {
-        case 2: k_closest_point<8, 0, kQueryMinBlocks, true, kQueryBlock, R> MESH_CT_ARGS; break;
-        case 3: k_closest_point<0, 0, kQueryMinBlocks, true, kQueryBlock, R> MESH_CT_ARGS; break;
+        case 2: go(k_closest_point<8, 0, kQueryMinBlocks, true, kQueryBlock, R>, grid, kQueryBlock); break;
+        case 3: go(k_closest_point<0, 0, kQueryMinBlocks, true, kQueryBlock, R>, grid, kQueryBlock); break;
         default:
             if constexpr (!R) {
                 switch (variant) {
-                    case 4: k_closest_point<kStackShared, 2, kQueryMinBlocks, true> MESH_CT_ARGS; break;
-                    case 5: k_closest_point<0, 2, kQueryMinBlocks, true> MESH_CT_ARGS; break;
-                    case 6: k_closest_point<8, 0, 9, true> MESH_CT_ARGS; break;
-                    case 7: k_closest_point<0, 0, 9, true> MESH_CT_ARGS; break;
-                    case 8: k_closest_point<0, 0, 16, true> MESH_CT_ARGS; break;
-                    case 9: k_closest_point<0, 2, 12, true> MESH_CT_ARGS; break;
-                    default: k_closest_point<kStackShared, 0, kQueryMinBlocks, true> MESH_CT_ARGS; break;
+                    case 4: go(k_closest_point<kStackShared, 2, kQueryMinBlocks, true>, grid, kQueryBlock); break;
+                    case 5: go(k_closest_point<0, 2, kQueryMinBlocks, true>, grid, kQueryBlock); break;
+                    case 6: go(k_closest_point<8, 0, 9, true>, grid, kQueryBlock); break;
+                    case 7: go(k_closest_point<0, 0, 9, true>, grid, kQueryBlock); break;
+                    case 8: go(k_closest_point<0, 0, 16, true>, grid, kQueryBlock); break;
+                    case 9: go(k_closest_point<0, 2, 12, true>, grid, kQueryBlock); break;
+                    default: go(k_closest_point<kStackShared, 0, kQueryMinBlocks, true>, grid, kQueryBlock); break;
                 }
             } else {
-                k_closest_point<kStackShared, 0, kQueryMinBlocks, true, kQueryBlock, R> MESH_CT_ARGS;
+                go(k_closest_point<kStackShared, 0, kQueryMinBlocks, true, kQueryBlock, R>, grid, kQueryBlock);
             }
             break;
     }
-#undef MESH_CT_ARGS
 }
 
 // The Chamfer launch: G lanes per sample, with (range) or without leaf collapse.
+// pdl: launched as the dependent of the kernel before it (the sort of mesh_chamfer_step).
 template <bool R>
 static void launch_chamfer_r(int G, unsigned grid, const ChamferSide &a2b, const ChamferSide &b2a, unsigned nbA,
-                             unsigned *st, double *partial, unsigned *ticket, double *out, cudaStream_t s) {
+                             unsigned *st, double *partial, unsigned *ticket, double *out, cudaStream_t s,
+                             bool pdl) {
+    auto go = [&](auto kern) {
+        if (pdl) pdl_launch(kern, grid, kQueryBlock, 0, s, a2b, b2a, nbA, st, partial, ticket, out);
+        else kern<<<grid, kQueryBlock, 0, s>>>(a2b, b2a, nbA, st, partial, ticket, out);
+    };
     switch (G) {
-        case 1: k_chamfer<1, R><<<grid, kQueryBlock, 0, s>>>(a2b, b2a, nbA, st, partial, ticket, out); break;
-        case 2: k_chamfer<2, R><<<grid, kQueryBlock, 0, s>>>(a2b, b2a, nbA, st, partial, ticket, out); break;
-        case 4: k_chamfer<4, R><<<grid, kQueryBlock, 0, s>>>(a2b, b2a, nbA, st, partial, ticket, out); break;
-        case 8: k_chamfer<8, R><<<grid, kQueryBlock, 0, s>>>(a2b, b2a, nbA, st, partial, ticket, out); break;
-        case 16: k_chamfer<16, R><<<grid, kQueryBlock, 0, s>>>(a2b, b2a, nbA, st, partial, ticket, out); break;
-        default: k_chamfer<32, R><<<grid, kQueryBlock, 0, s>>>(a2b, b2a, nbA, st, partial, ticket, out); break;
+        case 1: go(k_chamfer<1, R>); break;
+        case 2: go(k_chamfer<2, R>); break;
+        case 4: go(k_chamfer<4, R>); break;
+        case 8: go(k_chamfer<8, R>); break;
+        case 16: go(k_chamfer<16, R>); break;
+        default: go(k_chamfer<32, R>); break;
     }
 }
 static void launch_chamfer(int G, bool range, unsigned grid, const ChamferSide &a2b, const ChamferSide &b2a,
                            unsigned nbA, unsigned *st, double *partial, unsigned *ticket, double *out,
-                           cudaStream_t s) {
-    if (range) launch_chamfer_r<true>(G, grid, a2b, b2a, nbA, st, partial, ticket, out, s);
-    else launch_chamfer_r<false>(G, grid, a2b, b2a, nbA, st, partial, ticket, out, s);
+                           cudaStream_t s, bool pdl = false) {
+    if (range) launch_chamfer_r<true>(G, grid, a2b, b2a, nbA, st, partial, ticket, out, s, pdl);
+    else launch_chamfer_r<false>(G, grid, a2b, b2a, nbA, st, partial, ticket, out, s, pdl);
 }
 
 // The Chamfer of a sequence of frames (mesh_chamfer_step): each side's samples
@@ -1743,8 +1755,10 @@ static void launch_chamfer(int G, bool range, unsigned grid, const ChamferSide &
 // both sides are sorted together by one stable 8-bit pass (side in bit 7, so
 // the order is side-major); k_chamfer_keys first sets every key's side bit,
 // so a fresh or stale workspace gives a valid, if worse, order.
-__global__ void k_chamfer_keys(unsigned int *__restrict__ key, int nA, int n) {
+// It also zeroes the Chamfer kernel's last-block ticket (that kernel runs after it).
+__global__ void k_chamfer_keys(unsigned int *__restrict__ key, int nA, int n, unsigned int *__restrict__ ticket) {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c == 0) *ticket = 0u;
     if (c < n) key[c] = (c < nA ? 0u : 128u) | (key[c] & 127u);
 }
 
@@ -1946,10 +1960,9 @@ mesh_status mesh_chamfer_step(const mesh_bvh *A, const float *d_SA, int64_t nSA,
         return check_launch();
     }
     const int n = (int)(nSA + nSB);
-    k_chamfer_keys<<<grid_for(n, 256), 256, 0, s>>>(w.key, (int)nSA, n);
+    k_chamfer_keys<<<grid_for(n, 256), 256, 0, s>>>(w.key, (int)nSA, n, ticket);
     count_launch();
     sort_pairs_u32(w.sort_ws, n, 8, w.key, nullptr, w.key_sorted, w.order, s);
-    cudaMemsetAsync(ticket, 0, sizeof(unsigned int), s);
     ChamferSide a2b{traversal_of(B), B->hdr(), d_SA, nSA, d_faceA, d_baryA, d_dist2A, d_faceA, B->iperm(),
                     w.order, 0, w.key, 0u};
     ChamferSide b2a{traversal_of(A), A->hdr(), d_SB, nSB, d_faceB, d_baryB, d_dist2B, d_faceB, A->iperm(),
@@ -1957,7 +1970,7 @@ mesh_status mesh_chamfer_step(const mesh_bvh *A, const float *d_SA, int64_t nSA,
     unsigned grid = (unsigned)(nbA + nbB);
     unsigned *st = &A->hdr()->status;
     launch_chamfer(G, A->leaf_size > 1 || B->leaf_size > 1, grid, a2b, b2a, (unsigned)nbA, st, partial, ticket,
-                   d_out, s);
+                   d_out, s, true);
     count_launch();
     return check_launch();
 }

@@ -102,6 +102,11 @@ def lib():
         L.orc_gs_render.argtypes = [F64P, F64P, F64P, F64P, F64P, I64, F64P, F64P, C.c_double,
                                     C.c_double, C.c_double, C.c_double, C.c_int, C.c_int, C.c_double,
                                     F64P, F64P, F64P]
+        L.orc_gs_render_flags.restype = None
+        L.orc_gs_render_flags.argtypes = [F64P, F64P, F64P, F64P, F64P, I64, F64P, F64P, C.c_double,
+                                          C.c_double, C.c_double, C.c_double, C.c_int, C.c_int, C.c_double,
+                                          F64P, C.c_double, F64P, F64P,
+                                          np.ctypeslib.ndpointer(np.uint8, flags="C_CONTIGUOUS")]
         _lib = L
     return _lib
 
@@ -370,15 +375,22 @@ def emd(A, B):
 
 
 def gs_render(mu, quat, scale, opacity, color, Rc, tc, fx, fy, cx, cy, W, H, near=0.01,
-              background=(0.0, 0.0, 0.0)):
+              background=(0.0, 0.0, 0.0), flags=False, margin=2e-3):
     """Gaussian splatting render (forward equations of 3DGS, 16 x 16 tiles): image [H, W, 3]
-    and final transmittance [H, W], float64."""
+    and final transmittance [H, W], float64.  flags=True adds the parity flags of
+    orc_gs_render_flags (bool [H, W]: pixels a float32 implementation may legitimately
+    render differently, a decision within float32 reach of its threshold; relative
+    margin `margin` for the per-pixel thresholds); the image is the same either way."""
     mu, quat, scale = _f64(mu).reshape(-1, 3), _f64(quat).reshape(-1, 4), _f64(scale).reshape(-1, 3)
     opacity, color = _f64(opacity).reshape(-1), _f64(color).reshape(-1, 3)
     n = mu.shape[0]
     image = np.empty((H, W, 3))
     trans = np.empty((H, W))
-    lib().orc_gs_render(mu, quat, scale, opacity, color, n, _f64(Rc).reshape(3, 3), _f64(tc).reshape(3),
-                        float(fx), float(fy), float(cx), float(cy), int(W), int(H), float(near),
-                        _f64(background).reshape(3), image, trans)
-    return image, trans
+    args = (mu, quat, scale, opacity, color, n, _f64(Rc).reshape(3, 3), _f64(tc).reshape(3),
+            float(fx), float(fy), float(cx), float(cy), int(W), int(H), float(near), _f64(background).reshape(3))
+    if not flags:
+        lib().orc_gs_render(*args, image, trans)
+        return image, trans
+    fragile = np.zeros((H, W), np.uint8)
+    lib().orc_gs_render_flags(*args, float(margin), image, trans, fragile)
+    return image, trans, fragile.astype(bool)

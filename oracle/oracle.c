@@ -1046,7 +1046,25 @@ void orc_signed_distance(const double *V, const int32_t *F, int64_t nF, const do
 /*   stop if T (1 - alpha) < 1e-4; else C += color alpha T,              */
 /*   T *= 1 - alpha.  Result C + T background; T is returned too.        */
 /* ------------------------------------------------------------------ */
-typedef struct { double u, v, ca, cb, cc, z; int r, x0, x1, y0, y1, ok; } orc_splat;
+typedef struct { double u, v, ca, cb, cc, z; int r, x0, x1, y0, y1, ok, flags, fx0, fx1, fy0, fy1, tie; } orc_splat;
+
+/* Flags the pixels of tiles [tx0, tx1) x [ty0, ty1), clamped to the image,  */
+/* where the Gaussian o (opacity op) would contribute: alpha within the      */
+/* margin of the 1/255 floor or above it.                                    */
+static void gs_flag_tiles(unsigned char *fragile, int W, int H, int tx0, int tx1, int ty0, int ty1,
+                          const orc_splat *o, double op, double margin) {
+    int x0 = tx0 * 16, x1 = tx1 * 16, y0 = ty0 * 16, y1 = ty1 * 16;
+    if (x0 < 0) x0 = 0;
+    if (y0 < 0) y0 = 0;
+    if (x1 > W) x1 = W;
+    if (y1 > H) y1 = H;
+    for (int y = y0; y < y1; ++y)
+        for (int x = x0; x < x1; ++x) {
+            double dx = o->u - x, dy = o->v - y;
+            double p = -0.5 * (o->ca * dx * dx + o->cc * dy * dy) - o->cb * dx * dy;
+            if (fmin(0.99, op * exp(p)) >= (1.0 - margin) / 255.0) fragile[(int64_t)y * W + x] = 1;
+        }
+}
 
 
 static const orc_splat *g_sp_sort;
@@ -1058,19 +1076,21 @@ static int cmp_splat(const void *x, const void *y) {
     return (i > j) - (i < j);
 }
 
-void orc_gs_render(const double *mu, const double *quat, const double *scale, const double *opac,
-                   const double *color, int64_t n, const double *Rc, const double *tc, double fx,
-                   double fy, double cx, double cy, int W, int H, double near_z, const double *bg,
-                   double *image /* [H][W][3] */, double *trans /* [H][W] */) {
+static void gs_render_impl(const double *mu, const double *quat, const double *scale, const double *opac,
+                           const double *color, int64_t n, const double *Rc, const double *tc, double fx,
+                           double fy, double cx, double cy, int W, int H, double near_z, const double *bg,
+                           double *image, double *trans, double margin, unsigned char *fragile) {
     orc_splat *sp = (orc_splat *)calloc((size_t)(n > 0 ? n : 1), sizeof(orc_splat));
     int *order = (int *)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
     int gx = (W + 15) / 16, gy = (H + 15) / 16;
+    int whole = 0;               /* a cull or a determinant test within reach: every pixel */
     for (int64_t g = 0; g < n; ++g) {
         const double *m = mu + 3 * g, *q = quat + 4 * g, *s = scale + 3 * g;
         double xc[3];
         for (int r = 0; r < 3; ++r) xc[r] = Rc[3 * r] * m[0] + Rc[3 * r + 1] * m[1] + Rc[3 * r + 2] * m[2] + tc[r];
         orc_splat *o = sp + g;
         o->z = xc[2];
+        if (fragile && fabs(xc[2] - near_z) <= 1e-5 * fmax(1.0, fmax(fabs(near_z), fabs(xc[2])))) whole = 1;
         if (!(xc[2] > near_z)) continue;
         double w = q[0], x = q[1], y = q[2], z = q[3];
         double qn = sqrt(w * w + x * x + y * y + z * z);
@@ -1111,6 +1131,7 @@ void orc_gs_render(const double *mu, const double *quat, const double *scale, co
             }
         double a = C2[0][0] + 0.3, b = C2[0][1], c = C2[1][1] + 0.3;
         double det = a * c - b * b;
+        if (fragile && fabs(det) <= 1e-4 * (fabs(a * c) + b * b)) whole = 1;
         if (!(det > 0.0)) continue;
         double mid = 0.5 * (a + c);
         double lam = mid + sqrt(fmax(0.1, mid * mid - det));
@@ -1118,6 +1139,19 @@ void orc_gs_render(const double *mu, const double *quat, const double *scale, co
         double u = fx * xc[0] * iz + cx, v = fy * xc[1] * iz + cy;
         int x0 = (int)((u - r) / 16.0), x1 = (int)((u + r + 15) / 16.0);
         int y0 = (int)((v - r) / 16.0), y1 = (int)((v + r + 15) / 16.0);
+        if (fragile) {
+            /* the radius and the four tile bounds, each within float32 reach of a step */
+            double rr = 3.0 * sqrt(lam), mpx = 2e-5 * fmax(64.0, fmax(fabs(u), fabs(v)));
+            double bx0 = (u - r) / 16.0, bx1 = (u + r + 15) / 16.0, by0 = (v - r) / 16.0, by1 = (v + r + 15) / 16.0;
+            o->flags = (fabs(rr - nearbyint(rr)) <= 1e-5 * fmax(1.0, rr) ? 1 : 0) |
+                       (fabs(bx0 - nearbyint(bx0)) <= mpx / 16.0 ? 2 : 0) |
+                       (fabs(bx1 - nearbyint(bx1)) <= mpx / 16.0 ? 4 : 0) |
+                       (fabs(by0 - nearbyint(by0)) <= mpx / 16.0 ? 8 : 0) |
+                       (fabs(by1 - nearbyint(by1)) <= mpx / 16.0 ? 16 : 0);
+            /* the unclamped tile bounds and the footprint, for the strips flagged below */
+            o->fx0 = x0; o->fx1 = x1; o->fy0 = y0; o->fy1 = y1;
+            o->u = u; o->v = v; o->ca = c / det; o->cb = -b / det; o->cc = a / det; o->r = r;
+        }
         x0 = x0 < 0 ? 0 : (x0 > gx ? gx : x0); x1 = x1 < 0 ? 0 : (x1 > gx ? gx : x1);
         y0 = y0 < 0 ? 0 : (y0 > gy ? gy : y0); y1 = y1 < 0 ? 0 : (y1 > gy ? gy : y1);
         if ((x1 - x0) * (y1 - y0) == 0) continue;
@@ -1128,19 +1162,76 @@ void orc_gs_render(const double *mu, const double *quat, const double *scale, co
     for (int64_t g = 0; g < n; ++g) if (sp[g].ok) order[m++] = (int)g;
     g_sp_sort = sp;
     qsort(order, (size_t)m, sizeof(int), cmp_splat);
+    if (fragile) {
+        memset(fragile, whole ? 1 : 0, (size_t)W * (size_t)H);
+        /* depth order: runs of neighbours in the sorted order within float32 reach of    */
+        /* each other share a tie group (the sorted position of the run's first)          */
+        for (int k = 0; k < m; ++k) sp[order[k]].tie = -1;
+        for (int k = 0; k + 1 < m; ++k) {
+            double za = sp[order[k]].z, zb = sp[order[k + 1]].z;
+            if (zb - za <= 1e-6 * fmax(1.0, fmax(fabs(za), fabs(zb)))) {
+                if (sp[order[k]].tie < 0) sp[order[k]].tie = k;
+                sp[order[k + 1]].tie = sp[order[k]].tie;
+            }
+        }
+        /* a radius or tile bound near a step: the one tile column or row each such step    */
+        /* adds or drops (a bound near integer k moves between k - 1 and k, so column k - 1 */
+        /* is in or out; a radius step moves every bound by the r -> r +- 1 change)          */
+        for (int64_t g = 0; g < n; ++g) {        /* culled for no tile too: a step may add one */
+            const orc_splat *o = sp + g;
+            int f = o->flags;
+            if (!(f & 31)) continue;
+            int r = o->r;
+            int c0lo = o->fx0, c0hi = o->fx0, c1lo = o->fx1, c1hi = o->fx1;
+            int r0lo = o->fy0, r0hi = o->fy0, r1lo = o->fy1, r1hi = o->fy1;
+            for (int dr = -1; dr <= 1; dr += 2) {
+                if (!(f & 1)) break;
+                int rr = r + dr;
+                int a0 = (int)((o->u - rr) / 16.0), a1 = (int)((o->u + rr + 15) / 16.0);
+                int b0 = (int)((o->v - rr) / 16.0), b1 = (int)((o->v + rr + 15) / 16.0);
+                c0lo = a0 < c0lo ? a0 : c0lo; c0hi = a0 > c0hi ? a0 : c0hi;
+                c1lo = a1 < c1lo ? a1 : c1lo; c1hi = a1 > c1hi ? a1 : c1hi;
+                r0lo = b0 < r0lo ? b0 : r0lo; r0hi = b0 > r0hi ? b0 : r0hi;
+                r1lo = b1 < r1lo ? b1 : r1lo; r1hi = b1 > r1hi ? b1 : r1hi;
+            }
+            if (f & 2) { int k = (int)nearbyint((o->u - r) / 16.0); c0lo = c0lo < k - 1 ? c0lo : k - 1; c0hi = c0hi > k ? c0hi : k; }
+            if (f & 4) { int k = (int)nearbyint((o->u + r + 15) / 16.0); c1lo = c1lo < k - 1 ? c1lo : k - 1; c1hi = c1hi > k ? c1hi : k; }
+            if (f & 8) { int k = (int)nearbyint((o->v - r) / 16.0); r0lo = r0lo < k - 1 ? r0lo : k - 1; r0hi = r0hi > k ? r0hi : k; }
+            if (f & 16) { int k = (int)nearbyint((o->v + r + 15) / 16.0); r1lo = r1lo < k - 1 ? r1lo : k - 1; r1hi = r1hi > k ? r1hi : k; }
+            /* the columns [c0lo, c0hi) and [c1lo, c1hi), the rows [r0lo, r0hi) and [r1lo, r1hi) */
+            int ylo = r0lo, yhi = r1hi, xlo = c0lo, xhi = c1hi;
+            gs_flag_tiles(fragile, W, H, c0lo, c0hi, ylo, yhi, o, opac[g], margin);
+            gs_flag_tiles(fragile, W, H, c1lo, c1hi, ylo, yhi, o, opac[g], margin);
+            gs_flag_tiles(fragile, W, H, xlo, xhi, r0lo, r0hi, o, opac[g], margin);
+            gs_flag_tiles(fragile, W, H, xlo, xhi, r1lo, r1hi, o, opac[g], margin);
+        }
+    }
     for (int py = 0; py < H; ++py)
         for (int px = 0; px < W; ++px) {
             int tx = px / 16, ty = py / 16;
             double T = 1.0, C[3] = {0.0, 0.0, 0.0};
+            int last_tie = -1;                  /* tie group of the last contributor */
             for (int k = 0; k < m; ++k) {
                 const orc_splat *o = sp + order[k];
                 if (tx < o->x0 || tx >= o->x1 || ty < o->y0 || ty >= o->y1) continue;
                 double dx = o->u - px, dy = o->v - py;
                 double p = -0.5 * (o->ca * dx * dx + o->cc * dy * dy) - o->cb * dx * dy;
                 if (p > 0.0) continue;
-                double alpha = fmin(0.99, opac[order[k]] * exp(p));
-                if (alpha < 1.0 / 255.0) continue;
+                double raw = opac[order[k]] * exp(p);
+                double alpha = fmin(0.99, raw);
                 double tt = T * (1.0 - alpha);
+                if (fragile) {
+                    /* two members of one tie group reach the pixel: their order may swap */
+                    int tie_pair = 0;
+                    if (alpha >= 1.0 / 255.0) {
+                        tie_pair = o->tie >= 0 && o->tie == last_tie;
+                        last_tie = o->tie;
+                    }
+                    if (fabs(raw - 0.99) <= margin * 0.99 || fabs(alpha - 1.0 / 255.0) <= margin / 255.0 ||
+                        (alpha >= 1.0 / 255.0 && fabs(tt - 1e-4) <= 50.0 * margin * 1e-4) || tie_pair)
+                        fragile[(int64_t)py * W + px] = 1;
+                }
+                if (alpha < 1.0 / 255.0) continue;
                 if (tt < 1e-4) break;
                 for (int ch = 0; ch < 3; ++ch) C[ch] += color[3 * (int64_t)order[k] + ch] * alpha * T;
                 T = tt;
@@ -1150,4 +1241,32 @@ void orc_gs_render(const double *mu, const double *quat, const double *scale, co
         }
     free(sp);
     free(order);
+}
+
+void orc_gs_render(const double *mu, const double *quat, const double *scale, const double *opac,
+                   const double *color, int64_t n, const double *Rc, const double *tc, double fx,
+                   double fy, double cx, double cy, int W, int H, double near_z, const double *bg,
+                   double *image /* [H][W][3] */, double *trans /* [H][W] */) {
+    gs_render_impl(mu, quat, scale, opac, color, n, Rc, tc, fx, fy, cx, cy, W, H, near_z, bg, image, trans, 0.0,
+                   NULL);
+}
+
+/* orc_gs_render with parity flags (test infrastructure: which pixels a float32 */
+/* implementation of the same equations may legitimately render differently).   */
+/* fragile[py][px] = 1 where a discrete decision of the forward that reaches the */
+/* pixel lies, in float64, within float32 reach of its threshold: the cull at    */
+/* near_z or det > 0 (every pixel), the 3-sigma radius's ceil or a tile-square   */
+/* bound's truncation (the pixels of the tile strips it may add or drop that the */
+/* Gaussian reaches), the depth order of                                         */
+/* neighbours closer than 1e-6 relative (two of them reach the pixel), and the   */
+/* per-pixel 0.99 cap and 1/255 floor (relative margin `margin`) and 1e-4       */
+/* transmittance stop (50 x margin: the transmittance carries the errors of all */
+/* the alphas before it).  The image and transmittance are orc_gs_render's, bit */
+/* for bit.                                                                      */
+void orc_gs_render_flags(const double *mu, const double *quat, const double *scale, const double *opac,
+                         const double *color, int64_t n, const double *Rc, const double *tc, double fx,
+                         double fy, double cx, double cy, int W, int H, double near_z, const double *bg,
+                         double margin, double *image, double *trans, unsigned char *fragile) {
+    gs_render_impl(mu, quat, scale, opac, color, n, Rc, tc, fx, fy, cx, cy, W, H, near_z, bg, image, trans, margin,
+                   fragile);
 }

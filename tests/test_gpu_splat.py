@@ -1,7 +1,10 @@
 """GPU Gaussian-splatting render against the oracle's float64 restatement of the
-3DGS forward equations.  Float32 vs float64 moves a few pixels across the
-alpha thresholds (1/255, the 1e-4 transmittance cut-off, the 3-sigma tile
-square), so the bar is: mean error below 2e-4, 99.5 % of pixels within 2e-3,
+3DGS forward equations.  Float32 may take a discrete decision of the forward the
+other way where float64 puts it within float32 reach of its threshold (the 1/255
+alpha floor, the 0.99 cap, the 1e-4 transmittance stop, the 3-sigma radius and
+tile square, the depth order of near-equal depths); the oracle flags those pixels
+(orc_gs_render_flags) and they are counted.  Every other pixel, colour and
+transmittance, must agree within PIXEL_TOL, the mean error within MEAN_TOL, and
 closed-form scenes within 1e-5."""
 import numpy as np
 import pytest
@@ -27,19 +30,41 @@ def look_at(eye, target, up=(0, 0, 1)):
     return R, -R @ eye
 
 
+# Both sides render the same float32 inputs; the kernel's float32 arithmetic moves a
+# projected centre by a few ulp (~1e-5 pixel at ~100 pixels from the principal point), an
+# exponent p by ~1e-5 and an alpha by ~1e-5 of itself, and a pixel's colour is a sum of
+# alpha-weighted colours of total weight at most 1: unflagged pixels agree to a few 1e-6
+# (measured: at most 1.8e-6 over these scenes), so PIXEL_TOL = 1e-5.  The oracle flags a
+# per-pixel threshold within MARGIN (relative) of its value, 4x the alpha error bound for
+# images up to 128 pixels (scaled with the image size beyond).  Dense face-bound scenes flag
+# up to ~8 % of their pixels (mostly near-equal depths of Gaussians that overlap).
+PIXEL_TOL = 1e-5
+MEAN_TOL = 2e-5
+MARGIN = 2e-4
+FLAGGED_MAX = 0.10
+
+
 def compare(args, cam, W, H, bg=(0.05, 0.1, 0.2), strict=None):
     mu, quat, scale, opac, col = args
     R, t, f = cam
     img, T = gs_render(*(dev(np.asarray(a, np.float32)) for a in args), R, t, f, f, W / 2, H / 2, W, H,
                        background=bg)
-    rimg, rT = oracle.gs_render(mu, quat, scale, opac, col, R, t, f, f, W / 2, H / 2, W, H, 0.01, bg)
-    err = np.abs(host(img) - rimg)
+    # the oracle renders the float32 inputs the kernel was given (camera included), in float64
+    f32 = lambda a: np.asarray(np.asarray(a, np.float32), np.float64)   # noqa: E731
+    rimg, rT, frag = oracle.gs_render(*(f32(a) for a in args), f32(R), f32(t), float(np.float32(f)),
+                                      float(np.float32(f)), W / 2, H / 2, W, H, 0.01, f32(bg), flags=True,
+                                      margin=MARGIN * max(1.0, max(W, H) / 128))
+    err = np.abs(host(img) - rimg).max(2)
+    terr = np.abs(host(T) - rT)
     if strict is not None:
-        assert err.max() <= strict and np.abs(host(T) - rT).max() <= strict
+        assert err.max() <= strict and terr.max() <= strict
         return
-    assert err.mean() <= 2e-4, err.mean()
-    assert np.mean(err.max(2) <= 2e-3) >= 0.995
-    assert np.mean(np.abs(host(T) - rT) <= 2e-3) >= 0.995
+    ok = ~frag
+    print(f"flagged {frag.mean():.4%} of {frag.size} pixels; unflagged max colour error "
+          f"{err[ok].max():.3g}, transmittance {terr[ok].max():.3g}; mean {err.mean():.3g}")
+    assert frag.mean() <= FLAGGED_MAX
+    assert err[ok].max() <= PIXEL_TOL and terr[ok].max() <= PIXEL_TOL
+    assert err.mean() <= MEAN_TOL
 
 
 def random_gaussians(n, seed):

@@ -1211,6 +1211,7 @@ static void gs_render_impl(const double *mu, const double *quat, const double *s
             int tx = px / 16, ty = py / 16;
             double T = 1.0, C[3] = {0.0, 0.0, 0.0};
             int last_tie = -1;                  /* tie group of the last contributor */
+            double tre = 0.0;                   /* relative error bound of a float32 T so far */
             for (int k = 0; k < m; ++k) {
                 const orc_splat *o = sp + order[k];
                 if (tx < o->x0 || tx >= o->x1 || ty < o->y0 || ty >= o->y1) continue;
@@ -1222,17 +1223,26 @@ static void gs_render_impl(const double *mu, const double *quat, const double *s
                 double tt = T * (1.0 - alpha);
                 if (fragile) {
                     /* two members of one tie group reach the pixel: their order may swap */
-                    int tie_pair = 0;
+                    int tie_pair = 0, near_stop = 0;
                     if (alpha >= 1.0 / 255.0) {
                         tie_pair = o->tie >= 0 && o->tie == last_tie;
                         last_tie = o->tie;
+                        /* T (1 - alpha) carries every earlier alpha's relative error, each
+                         * amplified by alpha / (1 - alpha), and one rounding per step */
+                        tre += margin * alpha / (1.0 - alpha) + 0x1p-23;
+                        near_stop = fabs(tt - 1e-4) <= tre * tt;
                     }
                     if (fabs(raw - 0.99) <= margin * 0.99 || fabs(alpha - 1.0 / 255.0) <= margin / 255.0 ||
-                        (alpha >= 1.0 / 255.0 && fabs(tt - 1e-4) <= 50.0 * margin * 1e-4) || tie_pair)
+                        near_stop || tie_pair)
                         fragile[(int64_t)py * W + px] = 1;
                 }
                 if (alpha < 1.0 / 255.0) continue;
-                if (tt < 1e-4) break;
+                if (tt < 1e-4) {
+                    /* the stop falls on a member of a tie group: another member may come   */
+                    /* first in float32 order and the stop land elsewhere                    */
+                    if (fragile && o->tie >= 0) fragile[(int64_t)py * W + px] = 1;
+                    break;
+                }
                 for (int ch = 0; ch < 3; ++ch) C[ch] += color[3 * (int64_t)order[k] + ch] * alpha * T;
                 T = tt;
             }
@@ -1257,12 +1267,13 @@ void orc_gs_render(const double *mu, const double *quat, const double *scale, co
 /* pixel lies, in float64, within float32 reach of its threshold: the cull at    */
 /* near_z or det > 0 (every pixel), the 3-sigma radius's ceil or a tile-square   */
 /* bound's truncation (the pixels of the tile strips it may add or drop that the */
-/* Gaussian reaches), the depth order of                                         */
-/* neighbours closer than 1e-6 relative (two of them reach the pixel), and the   */
-/* per-pixel 0.99 cap and 1/255 floor (relative margin `margin`) and 1e-4       */
-/* transmittance stop (50 x margin: the transmittance carries the errors of all */
-/* the alphas before it).  The image and transmittance are orc_gs_render's, bit */
-/* for bit.                                                                      */
+/* Gaussian reaches), the depth order of neighbours closer than 1e-6 relative    */
+/* (two of them reach the pixel, or the transmittance stop falls on one), and the*/
+/* per-pixel 0.99 cap and 1/255 floor (relative margin `margin`, the bound of a */
+/* float32 alpha's relative error) and 1e-4 transmittance stop (within the     */
+/* transmittance's own error bound: the sum over the alphas before it of        */
+/* margin x alpha / (1 - alpha), plus 2^-23 a step).  The image and            */
+/* transmittance are orc_gs_render's, bit for bit.                               */
 void orc_gs_render_flags(const double *mu, const double *quat, const double *scale, const double *opac,
                          const double *color, int64_t n, const double *Rc, const double *tc, double fx,
                          double fy, double cx, double cy, int W, int H, double near_z, const double *bg,

@@ -1821,13 +1821,93 @@ mesh_status mesh_closest_point_hinted(const mesh_bvh *bvh, const float *d_Q, int
 // each class in the given order), so that a warp holds queries of similar
 // depth -- near the surface (deep searches), near misses, or far away (short
 // ones) -- instead of a mix that runs as long as its slowest lane.  The
-// classes are keys of one stable 8-bit radix pass (its values the indices);
-// any key values give a valid permutation, so a workspace whose classes are
-// stale or garbage only gives a worse order.
+// classes (their low two bits) are ordered by a stable counting sort in two
+// launches: each tile of queries counts its classes, then each tile scatters
+// its query indices from the counts of the tiles before it.  Any class bits
+// give a valid permutation, so a workspace whose classes are stale or garbage
+// only gives a worse order.
+constexpr int kClassTile = 2048, kClassThreads = 256;
+
+__global__ void __launch_bounds__(kClassThreads)
+k_class_count(const unsigned int *__restrict__ cls, int n, int4 *__restrict__ counts) {
+    __shared__ int s_cnt[4];
+    pdl_wait();
+    pdl_trigger();
+    if (threadIdx.x < 4) s_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const int base = blockIdx.x * kClassTile, lane = threadIdx.x & 31;
+    int c[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int r = 0; r < kClassTile / kClassThreads; ++r) {
+        int i = base + r * kClassThreads + threadIdx.x;
+        unsigned int k = i < n ? (cls[i] & 3u) : 4u;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) c[q] += __popc(__ballot_sync(0xffffffffu, k == (unsigned)q));
+    }
+    if (lane < 4) atomicAdd(&s_cnt[lane], c[lane]);
+    __syncthreads();
+    if (threadIdx.x == 0) counts[blockIdx.x] = make_int4(s_cnt[0], s_cnt[1], s_cnt[2], s_cnt[3]);
+}
+
+__global__ void __launch_bounds__(kClassThreads)
+k_class_scatter(const unsigned int *__restrict__ cls, int n, const int4 *__restrict__ counts, int tiles,
+                int *__restrict__ order) {
+    constexpr int kWarps = kClassThreads / 32;
+    __shared__ int s_red[kWarps][8];
+    __shared__ int s_run[4];
+    __shared__ int s_off[kWarps][4];
+    pdl_wait();
+    pdl_trigger();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    // every class's total and this tile's prefix, from the tiles' counts
+    int v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int t = threadIdx.x; t < tiles; t += kClassThreads) {
+        int4 c = counts[t];
+        v[0] += c.x; v[1] += c.y; v[2] += c.z; v[3] += c.w;
+        if (t < (int)blockIdx.x) { v[4] += c.x; v[5] += c.y; v[6] += c.z; v[7] += c.w; }
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+        for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+    if (lane == 0)
+        for (int q = 0; q < 8; ++q) s_red[wid][q] = v[q];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int tot[4] = {0, 0, 0, 0}, pre[4] = {0, 0, 0, 0};
+        for (int w = 0; w < kWarps; ++w)
+            for (int q = 0; q < 4; ++q) { tot[q] += s_red[w][q]; pre[q] += s_red[w][4 + q]; }
+        int run = 0;
+        for (int q = 0; q < 4; ++q) { s_run[q] = run + pre[q]; run += tot[q]; }
+    }
+    __syncthreads();
+    const int base = blockIdx.x * kClassTile;
+    const unsigned int lt = (1u << lane) - 1u;
+    for (int r = 0; r < kClassTile / kClassThreads; ++r) {
+        int i = base + r * kClassThreads + threadIdx.x;
+        unsigned int k = i < n ? (cls[i] & 3u) : 4u;
+        unsigned int mine = 0u;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            unsigned int b = __ballot_sync(0xffffffffu, k == (unsigned)q);
+            if (lane == 0) s_off[wid][q] = __popc(b);
+            if (k == (unsigned)q) mine = b;
+        }
+        __syncthreads();
+        if (threadIdx.x < 4) {                         // warp offsets within the round, per class
+            int q = threadIdx.x, run = s_run[q];
+            for (int w = 0; w < kWarps; ++w) { int c = s_off[w][q]; s_off[w][q] = run; run += c; }
+            s_run[q] = run;
+        }
+        __syncthreads();
+        if (k < 4u) order[s_off[wid][k] + __popc(mine & lt)] = i;
+        __syncthreads();
+    }
+}
+
 struct ContactWs {
-    unsigned int *cls, *cls_sorted;
+    unsigned int *cls;
     int *order;
-    void *sort_ws;
+    int4 *counts;
     size_t bytes;
 };
 
@@ -1835,9 +1915,9 @@ static ContactWs contact_ws(void *ws, int64_t n) {
     size_t off = 0;
     auto take = [&](size_t b) { size_t o = off; off = align_up(off + b, 256); return o; };
     int64_t m = n > 0 ? n : 1;
-    size_t oC = take(4 * m), oS = take(4 * m), oO = take(4 * m), oW = take(sort_pairs_ws_bytes(m));
+    size_t oC = take(4 * m), oO = take(4 * m), oT = take(16 * ((m + kClassTile - 1) / kClassTile));
     char *b = (char *)ws;
-    return ContactWs{(unsigned int *)(b + oC), (unsigned int *)(b + oS), (int *)(b + oO), b + oW, off};
+    return ContactWs{(unsigned int *)(b + oC), (int *)(b + oO), (int4 *)(b + oT), off};
 }
 
 mesh_status mesh_knn_project(const mesh_bvh *bvh, const float *d_Q, int64_t nQ, int k,
@@ -1877,7 +1957,10 @@ mesh_status mesh_contact(const mesh_bvh *bvh, const float *d_Q, int64_t nQ, floa
                                          stream);
     cudaStream_t s = (cudaStream_t)stream;
     const int n = (int)nQ;
-    sort_pairs_u32(w.sort_ws, n, 2, w.cls, nullptr, w.cls_sorted, w.order, s);
+    const int tiles = (n + kClassTile - 1) / kClassTile;
+    pdl_launch(k_class_count, tiles, kClassThreads, 0, s, w.cls, n, w.counts);
+    pdl_launch(k_class_scatter, tiles, kClassThreads, 0, s, w.cls, n, w.counts, tiles, w.order);
+    count_launch(2);
     float maxd2 = isinf(max_dist) ? INFINITY : max_dist * max_dist;
     Traversal T = traversal_of(bvh, isinf(max_dist));
     Header *h = bvh->hdr();

@@ -335,10 +335,11 @@ mesh_status mesh_gs_render(const float *d_mu, const float *d_quat, const float *
  * d_ws must hold mesh_gs_workspace_bytes(nG, max_instances, width, height)
  * bytes.  d_counts (DEVICE uint32 [2], may be NULL) receives {overflow, count}:
  * overflow = 1 when the frame had more instances than max_instances (the
- * instances past the capacity are dropped and the image is incomplete), count
- * = the frame's instances.  With enough capacity the image and transmittance
- * equal mesh_gs_render's bit for bit; the sorts run over max_instances slots
- * (the unused ones are keyed after every real instance). */
+ * instances of the farthest Gaussians, past the capacity, are dropped and the
+ * image is incomplete), count = the frame's instances.  With enough capacity
+ * the image and transmittance equal mesh_gs_render's bit for bit; the tile
+ * sort runs over max_instances slots (the unused ones are keyed after every
+ * real instance). */
 mesh_status mesh_gs_render_capacity(const float *d_mu, const float *d_quat, const float *d_scale,
                                     const float *d_opacity, const float *d_color, int64_t nG,
                                     const mesh_camera *cam, int64_t max_instances, void *d_ws,

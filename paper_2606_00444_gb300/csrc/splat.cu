@@ -3,13 +3,17 @@
 // headless device image.  Pipeline: (1) per Gaussian, project the centre,
 // the 2D covariance J Rc Sigma Rc^T J^T + 0.3 I and its inverse (the conic),
 // a 3-sigma radius and the rectangle of 16 x 16-pixel tiles it touches;
-// (2) an exclusive scan of the tile counts gives each Gaussian its slots;
-// (3) one (tile, depth, Gaussian) instance per touched tile; (4) a stable radix
-// sort by depth, then by tile, so each tile's instances are contiguous and
-// front to back (ties by Gaussian index); (5) each tile's range; (6) one block
-// of 16 x 16 threads per tile composites its pixels front to back, the
-// instances streamed through shared memory 256 at a time, until every pixel's
-// transmittance would fall below 1e-4.
+// (2) a stable radix sort of the Gaussians by depth (ties by index) and an
+// exclusive scan of their tile counts in that order give each its slots;
+// (3) one (tile, Gaussian) instance per touched tile, in depth order; (4) a
+// stable radix sort of the instances by tile, so each tile's instances are
+// contiguous and front to back; (5) each tile's range; (6) one block
+// of 16 x 16 threads per tile, the tiles with the most instances first,
+// composites its pixels front to back, the instances streamed through shared
+// memory 256 at a time, until every pixel's transmittance would fall below
+// 1e-4; a warp (two rows of the tile) blends only the instances whose reach
+// box meets its pixels (elsewhere an alpha is below 1/255 for certain), found
+// 32 at a time with one vote.
 //
 // A pixel (px, py) samples the image point (px, py); u = fx x_c / z_c + cx.
 // Per instance and pixel: p = -0.5 (a dx^2 + c dy^2) - b dx dy with
@@ -26,18 +30,22 @@ constexpr int kTile = 16;
 constexpr int kTilePix = kTile * kTile;
 constexpr int kScanBlock = 1024;
 
+// reach: the box (x0, x1, y0, y1) in pixels outside which the Gaussian's alpha is
+// below 1/255 for certain (its ellipse d^T conic d <= 2 ln(255 opacity), the bound
+// grown by 1 % and half a pixel so that float32 rounding cannot shrink it past a
+// pixel the per-pixel test would keep).
 __global__ void k_gs_preprocess(int n, const float *__restrict__ mu, const float *__restrict__ quat,
                                 const float *__restrict__ scale, const float *__restrict__ opac,
                                 mesh_camera cam, int gx, int gy, float2 *uv, float4 *conic_o,
-                                float *depth, int4 *rect, int *count) {
+                                int4 *rect, int *count, float4 *reach, unsigned *gkey) {
     int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= n) return;
     count[g] = 0;
+    gkey[g] = 0xffffffffu;                               // culled: after every drawn Gaussian
     const float *m = mu + 3 * (size_t)g;
     float xc[3];
     for (int r = 0; r < 3; ++r)
         xc[r] = cam.R[3 * r] * m[0] + cam.R[3 * r + 1] * m[1] + cam.R[3 * r + 2] * m[2] + cam.t[r];
-    depth[g] = xc[2];
     if (!(xc[2] > cam.near_z)) return;
     const float *q = quat + 4 * (size_t)g, *s = scale + 3 * (size_t)g;
     float w = q[0], x = q[1], y = q[2], z = q[3];
@@ -88,6 +96,10 @@ __global__ void k_gs_preprocess(int n, const float *__restrict__ mu, const float
     conic_o[g] = make_float4(c * id, -b * id, a * id, opac[g]);
     rect[g] = make_int4(x0, y0, x1, y1);
     count[g] = cnt;
+    gkey[g] = __float_as_uint(xc[2]);                    // positive: bit order is value order
+    float k = 2.0f * logf(fmaxf(255.0f * opac[g], 1.0f));          // the ellipse's squared radius
+    float rx = 1.01f * sqrtf(k * a) + 0.5f, ry = 1.01f * sqrtf(k * c) + 0.5f;
+    reach[g] = make_float4(u - rx, u + rx, v - ry, v + ry);
 }
 
 // Exclusive scan of n ints: per-block scans, a scan of the block totals by one
@@ -143,46 +155,35 @@ void exclusive_scan_int(const int *in, int *out, int n, int *bsum, int *total, c
     count_launch(3);
 }
 
-__global__ void k_gs_duplicate(int n, const int *__restrict__ count, const int *__restrict__ offset,
-                               const int4 *__restrict__ rect, const float *__restrict__ depth, int gx,
-                               unsigned *tile_key, unsigned *depth_key, int *gid, int *iota) {
-    int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= n || count[g] == 0) return;
+// The instances of the Gaussians in depth order (sorted position i holds Gaussian
+// gorder[i]; its instances start at offset[i]), so that a stable sort by tile
+// leaves each tile's instances front to back.  Slots at or past cap are dropped.
+__global__ void k_gs_duplicate(int n, const int *__restrict__ gorder, const int *__restrict__ offset,
+                               const int *__restrict__ count, const int4 *__restrict__ rect, int gx, int cap,
+                               unsigned *tile_key, int *gid) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int g = gorder[i];
+    if (count[g] == 0) return;
     int4 r = rect[g];
-    int k = offset[g];
-    unsigned dk = __float_as_uint(depth[g]);         // positive: bit order is value order
-    for (int ty = r.y; ty < r.w; ++ty)
-        for (int tx = r.x; tx < r.z; ++tx, ++k) {
-            tile_key[k] = (unsigned)(ty * gx + tx);
-            depth_key[k] = dk;
-            gid[k] = g;
-            iota[k] = k;
-        }
-}
-
-// Fixed-capacity form: instance slots past the capacity are dropped (the
-// overflow is reported), and the slots the frame did not fill -- from the
-// device-side total on -- get keys that sort after every real one.
-__global__ void k_gs_duplicate_cap(int n, const int *__restrict__ count, const int *__restrict__ offset,
-                                   const int4 *__restrict__ rect, const float *__restrict__ depth, int gx,
-                                   int cap, unsigned *tile_key, unsigned *depth_key, int *gid, int *iota) {
-    int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= n || count[g] == 0) return;
-    int4 r = rect[g];
-    int k = offset[g];
-    unsigned dk = __float_as_uint(depth[g]);
+    int k = offset[i];
     for (int ty = r.y; ty < r.w; ++ty)
         for (int tx = r.x; tx < r.z; ++tx, ++k) {
             if (k >= cap) return;
             tile_key[k] = (unsigned)(ty * gx + tx);
-            depth_key[k] = dk;
             gid[k] = g;
-            iota[k] = k;
         }
 }
 
-__global__ void k_gs_pad(int cap, const int *__restrict__ total, unsigned pad_tile, unsigned *tile_key,
-                         unsigned *depth_key, int *gid, int *iota, unsigned int *counts) {
+// The tile counts in depth order, for the scan of the instance offsets.
+__global__ void k_gs_gather_count(int n, const int *__restrict__ gorder, const int *__restrict__ count,
+                                  int *__restrict__ count_s) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) count_s[i] = count[gorder[i]];
+}
+
+__global__ void k_gs_pad(int cap, const int *__restrict__ total, unsigned pad_tile, unsigned *tile_key, int *gid,
+                         unsigned int *counts) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int m = *total;
     if (k == 0 && counts) {
@@ -191,9 +192,7 @@ __global__ void k_gs_pad(int cap, const int *__restrict__ total, unsigned pad_ti
     }
     if (k >= cap || k < m) return;
     tile_key[k] = pad_tile;
-    depth_key[k] = 0xffffffffu;
     gid[k] = 0;
-    iota[k] = k;
 }
 
 __global__ void k_gs_ranges_cap(int cap, int tiles, const unsigned *__restrict__ tk, int2 *range) {
@@ -205,12 +204,6 @@ __global__ void k_gs_ranges_cap(int cap, int tiles, const unsigned *__restrict__
     if (i == cap - 1 || tk[i + 1] != t) range[t].y = i + 1;
 }
 
-__global__ void k_gs_gather_tile(int m, const int *__restrict__ inst, const unsigned *__restrict__ tile_key,
-                                 unsigned *out) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < m) out[i] = tile_key[inst[i]];
-}
-
 __global__ void k_gs_ranges(int m, const unsigned *__restrict__ tk, int2 *range) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m) return;
@@ -220,16 +213,23 @@ __global__ void k_gs_ranges(int m, const unsigned *__restrict__ tk, int2 *range)
 }
 
 __global__ void __launch_bounds__(kTilePix)
-k_gs_render(mesh_camera cam, int gx, const int2 *__restrict__ range, const int *__restrict__ inst,
-            const int *__restrict__ gid, const float2 *__restrict__ uv, const float4 *__restrict__ conic_o,
+k_gs_render(mesh_camera cam, int gx, const int *__restrict__ order, const int2 *__restrict__ range,
+            const int *__restrict__ inst, const int *__restrict__ gid, const float2 *__restrict__ uv,
+            const float4 *__restrict__ conic_o, const float4 *__restrict__ reach,
             const float *__restrict__ color, float *image, float *trans) {
     __shared__ float2 s_uv[kTilePix];
     __shared__ float4 s_co[kTilePix];
     __shared__ float3 s_col[kTilePix];
-    const int tile = blockIdx.y * gx + blockIdx.x;
-    const int px = blockIdx.x * kTile + (threadIdx.x % kTile), py = blockIdx.y * kTile + (threadIdx.x / kTile);
+    __shared__ float4 s_reach[kTilePix];
+    const int tile = order[blockIdx.x];                     // the heaviest tiles first
+    const int tx = tile % gx, ty = tile / gx;
+    const int px = tx * kTile + (threadIdx.x % kTile), py = ty * kTile + (threadIdx.x / kTile);
     const bool inside = px < cam.width && py < cam.height;
     bool done = !inside;
+    // this warp's pixels: two rows of the tile
+    const int lane = threadIdx.x & 31;
+    const float wx0 = (float)(tx * kTile), wx1 = wx0 + (float)(kTile - 1);
+    const float wy0 = (float)(ty * kTile + 2 * (threadIdx.x / 32)), wy1 = wy0 + 1.0f;
     const int2 rg = range[tile];
     float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
     for (int b0 = rg.x; b0 < rg.y; b0 += kTilePix) {
@@ -240,23 +240,40 @@ k_gs_render(mesh_camera cam, int gx, const int2 *__restrict__ range, const int *
             s_uv[threadIdx.x] = uv[g];
             s_co[threadIdx.x] = conic_o[g];
             s_col[threadIdx.x] = make_float3(color[3 * (size_t)g], color[3 * (size_t)g + 1], color[3 * (size_t)g + 2]);
+            s_reach[threadIdx.x] = reach[g];
         }
         __syncthreads();
         int m = min(kTilePix, rg.y - b0);
-        for (int j = 0; j < m && !done; ++j) {
-            float dx = s_uv[j].x - (float)px, dy = s_uv[j].y - (float)py;
-            float4 co = s_co[j];
-            float p = -0.5f * (co.x * dx * dx + co.z * dy * dy) - co.y * dx * dy;
-            if (p > 0.0f) continue;
-            float alpha = fminf(0.99f, co.w * expf(p));
-            if (alpha < 1.0f / 255.0f) continue;
-            float tt = T * (1.0f - alpha);
-            if (tt < 1e-4f) { done = true; break; }
-            float3 c = s_col[j];
-            C0 += c.x * alpha * T;
-            C1 += c.y * alpha * T;
-            C2 += c.z * alpha * T;
-            T = tt;
+        // 32 instances at a time: each lane tests one instance's reach box against the
+        // warp's pixels, and the warp then blends only the instances that reach them, in
+        // order (the others have alpha below 1/255 at every pixel of the warp)
+        for (int j0 = 0; j0 < m; j0 += 32) {
+            if (__all_sync(0xffffffffu, done)) break;
+            const int jl = j0 + lane;
+            bool reaches = false;
+            if (jl < m) {
+                const float4 rb = s_reach[jl];
+                reaches = !(rb.y < wx0 || rb.x > wx1 || rb.w < wy0 || rb.z > wy1);
+            }
+            unsigned int todo = __ballot_sync(0xffffffffu, reaches);
+            while (todo) {
+                const int j = j0 + __ffs(todo) - 1;
+                todo &= todo - 1u;
+                if (done) continue;
+                float dx = s_uv[j].x - (float)px, dy = s_uv[j].y - (float)py;
+                float4 co = s_co[j];
+                float p = -0.5f * (co.x * dx * dx + co.z * dy * dy) - co.y * dx * dy;
+                if (p > 0.0f) continue;
+                float alpha = fminf(0.99f, co.w * expf(p));
+                if (alpha < 1.0f / 255.0f) continue;
+                float tt = T * (1.0f - alpha);
+                if (tt < 1e-4f) { done = true; continue; }
+                float3 c = s_col[j];
+                C0 += c.x * alpha * T;
+                C1 += c.y * alpha * T;
+                C2 += c.z * alpha * T;
+                T = tt;
+            }
         }
     }
     if (!inside) return;
@@ -267,44 +284,96 @@ k_gs_render(mesh_camera cam, int gx, const int2 *__restrict__ range, const int *
     if (trans) trans[o] = T;
 }
 
+// Tile order for the compositing launch, the tiles with the most instances
+// first (longest-first scheduling: the longest tiles start in the first wave
+// instead of trailing the launch).  One block: a counting sort of the tiles by
+// the bit length of their instance count, descending; within a bucket the order
+// is that of the atomics (any order gives the same image: tiles are
+// independent).
+__global__ void __launch_bounds__(1024) k_gs_tile_order(int tiles, const int2 *__restrict__ range,
+                                                       int *__restrict__ order) {
+    __shared__ int s_cnt[33];
+    if (threadIdx.x < 33) s_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    for (int t = threadIdx.x; t < tiles; t += blockDim.x) {
+        int2 r = range[t];
+        int len = r.y - r.x;
+        int bucket = len > 0 ? 32 - __clz(len) : 0;        // 0 (empty) .. 32
+        atomicAdd(&s_cnt[32 - bucket], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int b = 0; b < 33; ++b) { int c = s_cnt[b]; s_cnt[b] = run; run += c; }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < tiles; t += blockDim.x) {
+        int2 r = range[t];
+        int len = r.y - r.x;
+        int bucket = len > 0 ? 32 - __clz(len) : 0;
+        order[atomicAdd(&s_cnt[32 - bucket], 1)] = t;
+    }
+}
+
 struct SplatWs {
     float2 *uv;
-    float4 *conic_o;
-    float *depth;
+    float4 *conic_o, *reach;
+    int *torder;
     int4 *rect;
-    int *count, *offset, *bsum, *total;
+    int *count, *count_s, *offset, *bsum, *total;
     int2 *range;
+    unsigned *gkey, *gkey_s;
+    int *gorder;
+    char *gsort_ws;                // the Gaussians' depth sort
     size_t base_bytes;
     // per instance
-    unsigned *tile_key, *depth_key, *dk_s, *tk1, *tk_s;
-    int *gid, *iota, *inst1, *inst2;
-    char *sort_ws;
+    unsigned *tile_key, *tk_s;
+    int *gid, *inst;
+    char *sort_ws;                 // the instances' tile sort
     size_t bytes;
 };
 
 static SplatWs splat_ws(void *ws, int64_t n, int64_t m, int64_t tiles) {
     size_t off = 0;
     auto take = [&](size_t b) { size_t o = off; off = align_up(off + b, 256); return o; };
-    int64_t nn = n > 0 ? n : 1, mm = m > 0 ? m : 1;
-    size_t oUV = take(8 * nn), oCO = take(16 * nn), oD = take(4 * nn), oR = take(16 * nn), oC = take(4 * nn),
-           oO = take(4 * nn), oB = take(4 * ((nn + kScanBlock - 1) / kScanBlock) + 4), oT = take(16),
-           oRg = take(8 * (tiles > 0 ? tiles : 1));
+    int64_t nn = n > 0 ? n : 1, mm = m > 0 ? m : 1, tt = tiles > 0 ? tiles : 1;
+    size_t oUV = take(8 * nn), oCO = take(16 * nn), oR = take(16 * nn), oC = take(4 * nn),
+           oCS = take(4 * nn), oO = take(4 * nn), oB = take(4 * ((nn + kScanBlock - 1) / kScanBlock) + 4),
+           oT = take(16), oRg = take(8 * tt), oRe = take(16 * nn), oTo = take(4 * tt), oGK = take(4 * nn),
+           oGS = take(4 * nn), oGO = take(4 * nn), oGW = take(sort_pairs_ws_bytes(nn));
     size_t base = off;
-    size_t oTK = take(4 * mm), oDK = take(4 * mm), oDS = take(4 * mm), oT1 = take(4 * mm), oTS = take(4 * mm),
-           oG = take(4 * mm), oI = take(4 * mm), oI1 = take(4 * mm), oI2 = take(4 * mm),
+    size_t oTK = take(4 * mm), oTS = take(4 * mm), oG = take(4 * mm), oI = take(4 * mm),
            oS = take(sort_pairs_ws_bytes(mm));
     char *b = (char *)ws;
     SplatWs w;
-    w.uv = (float2 *)(b + oUV); w.conic_o = (float4 *)(b + oCO); w.depth = (float *)(b + oD);
-    w.rect = (int4 *)(b + oR); w.count = (int *)(b + oC); w.offset = (int *)(b + oO);
+    w.uv = (float2 *)(b + oUV); w.conic_o = (float4 *)(b + oCO);
+    w.rect = (int4 *)(b + oR); w.count = (int *)(b + oC); w.count_s = (int *)(b + oCS); w.offset = (int *)(b + oO);
     w.bsum = (int *)(b + oB); w.total = (int *)(b + oT); w.range = (int2 *)(b + oRg);
+    w.reach = (float4 *)(b + oRe); w.torder = (int *)(b + oTo);
+    w.gkey = (unsigned *)(b + oGK); w.gkey_s = (unsigned *)(b + oGS); w.gorder = (int *)(b + oGO);
+    w.gsort_ws = b + oGW;
     w.base_bytes = base;
-    w.tile_key = (unsigned *)(b + oTK); w.depth_key = (unsigned *)(b + oDK); w.dk_s = (unsigned *)(b + oDS);
-    w.tk1 = (unsigned *)(b + oT1); w.tk_s = (unsigned *)(b + oTS);
-    w.gid = (int *)(b + oG); w.iota = (int *)(b + oI); w.inst1 = (int *)(b + oI1); w.inst2 = (int *)(b + oI2);
+    w.tile_key = (unsigned *)(b + oTK); w.tk_s = (unsigned *)(b + oTS);
+    w.gid = (int *)(b + oG); w.inst = (int *)(b + oI);
     w.sort_ws = b + oS;
     w.bytes = off;
     return w;
+}
+
+// Steps (1) and (2): project, sort the Gaussians by depth (ties by index), and
+// scan their tile counts in that order into instance offsets (total in w.total).
+static void gs_front(const SplatWs &w, int n, const float *d_mu, const float *d_quat, const float *d_scale,
+                     const float *d_opacity, const mesh_camera &cam, int gx, int gy, cudaStream_t s) {
+    k_gs_preprocess<<<grid_for(n, 256), 256, 0, s>>>(n, d_mu, d_quat, d_scale, d_opacity, cam, gx, gy, w.uv,
+                                                     w.conic_o, w.rect, w.count, w.reach, w.gkey);
+    count_launch();
+    sort_pairs_u32(w.gsort_ws, n, 32, w.gkey, nullptr, w.gkey_s, w.gorder, s);
+    k_gs_gather_count<<<grid_for(n, 256), 256, 0, s>>>(n, w.gorder, w.count, w.count_s);
+    int nb = (n + kScanBlock - 1) / kScanBlock;
+    k_scan_local<<<nb, kScanBlock, 0, s>>>(n, w.count_s, w.offset, w.bsum);
+    k_scan_sums<<<1, 32, 0, s>>>(nb, w.bsum, w.total);
+    k_scan_add<<<grid_for(n, 256), 256, 0, s>>>(n, w.offset, w.bsum);
+    count_launch(4);
 }
 
 }  // namespace meshgs
@@ -335,13 +404,7 @@ mesh_status mesh_gs_render(const float *d_mu, const float *d_quat, const float *
     if (!d_ws || ws_bytes < w0.base_bytes || ((uintptr_t)d_ws & 255u)) return MESH_ERR_WORKSPACE;
     int m = 0;
     if (n > 0) {
-        k_gs_preprocess<<<grid_for(n, 256), 256, 0, s>>>(n, d_mu, d_quat, d_scale, d_opacity, *cam, gx, gy,
-                                                         w0.uv, w0.conic_o, w0.depth, w0.rect, w0.count);
-        int nb = (n + kScanBlock - 1) / kScanBlock;
-        k_scan_local<<<nb, kScanBlock, 0, s>>>(n, w0.count, w0.offset, w0.bsum);
-        k_scan_sums<<<1, 32, 0, s>>>(nb, w0.bsum, w0.total);
-        k_scan_add<<<grid_for(n, 256), 256, 0, s>>>(n, w0.offset, w0.bsum);
-        count_launch(4);
+        gs_front(w0, n, d_mu, d_quat, d_scale, d_opacity, *cam, gx, gy, s);
         if (cudaMemcpyAsync(&m, w0.total, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess)
             return MESH_ERR_CUDA;
@@ -351,21 +414,19 @@ mesh_status mesh_gs_render(const float *d_mu, const float *d_quat, const float *
     if (ws_bytes < w.bytes) return MESH_ERR_WORKSPACE;
     cudaMemsetAsync(w.range, 0, 8 * (size_t)tiles, s);
     if (m > 0) {
-        k_gs_duplicate<<<grid_for(n, 256), 256, 0, s>>>(n, w.count, w.offset, w.rect, w.depth, gx, w.tile_key,
-                                                        w.depth_key, w.gid, w.iota);
-        count_launch();
-        sort_pairs_u32(w.sort_ws, m, 32, w.depth_key, w.iota, w.dk_s, w.inst1, s);
-        k_gs_gather_tile<<<grid_for(m, 256), 256, 0, s>>>(m, w.inst1, w.tile_key, w.tk1);
+        k_gs_duplicate<<<grid_for(n, 256), 256, 0, s>>>(n, w.gorder, w.offset, w.count, w.rect, gx, m, w.tile_key,
+                                                        w.gid);
         count_launch();
         int bits = 1;
         while (((int64_t)1 << bits) < tiles) ++bits;
-        sort_pairs_u32(w.sort_ws, m, bits, w.tk1, w.inst1, w.tk_s, w.inst2, s);
+        sort_pairs_u32(w.sort_ws, m, bits, w.tile_key, nullptr, w.tk_s, w.inst, s);
         k_gs_ranges<<<grid_for(m, 256), 256, 0, s>>>(m, w.tk_s, w.range);
         count_launch();
     }
-    k_gs_render<<<dim3(gx, gy), kTilePix, 0, s>>>(*cam, gx, w.range, w.inst2, w.gid, w.uv, w.conic_o, d_color,
-                                                  d_image, d_trans);
-    count_launch();
+    k_gs_tile_order<<<1, 1024, 0, s>>>((int)tiles, w.range, w.torder);
+    k_gs_render<<<(unsigned)tiles, kTilePix, 0, s>>>(*cam, gx, w.torder, w.range, w.inst, w.gid, w.uv, w.conic_o,
+                                                     w.reach, d_color, d_image, d_trans);
+    count_launch(2);
     return check_launch();
 }
 
@@ -387,32 +448,24 @@ mesh_status mesh_gs_render_capacity(const float *d_mu, const float *d_quat, cons
     cudaMemsetAsync(w.range, 0, 8 * (size_t)tiles, s);
     cudaMemsetAsync(w.total, 0, sizeof(int), s);
     if (n > 0) {
-        k_gs_preprocess<<<grid_for(n, 256), 256, 0, s>>>(n, d_mu, d_quat, d_scale, d_opacity, *cam, gx, gy,
-                                                         w.uv, w.conic_o, w.depth, w.rect, w.count);
-        int nb = (n + kScanBlock - 1) / kScanBlock;
-        k_scan_local<<<nb, kScanBlock, 0, s>>>(n, w.count, w.offset, w.bsum);
-        k_scan_sums<<<1, 32, 0, s>>>(nb, w.bsum, w.total);
-        k_scan_add<<<grid_for(n, 256), 256, 0, s>>>(n, w.offset, w.bsum);
-        k_gs_duplicate_cap<<<grid_for(n, 256), 256, 0, s>>>(n, w.count, w.offset, w.rect, w.depth, gx, cap,
-                                                            w.tile_key, w.depth_key, w.gid, w.iota);
-        count_launch(5);
+        gs_front(w, n, d_mu, d_quat, d_scale, d_opacity, *cam, gx, gy, s);
+        k_gs_duplicate<<<grid_for(n, 256), 256, 0, s>>>(n, w.gorder, w.offset, w.count, w.rect, gx, cap, w.tile_key,
+                                                        w.gid);
+        count_launch();
     }
     // tile keys take `bits` bits with room above the last tile for the padding key
     int bits = 1;
     while (((int64_t)1 << bits) <= tiles) ++bits;
     const unsigned pad_tile = (unsigned)(((int64_t)1 << bits) - 1);
-    k_gs_pad<<<grid_for(cap, 256), 256, 0, s>>>(cap, w.total, pad_tile, w.tile_key, w.depth_key, w.gid, w.iota,
-                                                d_counts);
+    k_gs_pad<<<grid_for(cap, 256), 256, 0, s>>>(cap, w.total, pad_tile, w.tile_key, w.gid, d_counts);
     count_launch();
-    sort_pairs_u32(w.sort_ws, cap, 32, w.depth_key, w.iota, w.dk_s, w.inst1, s);
-    k_gs_gather_tile<<<grid_for(cap, 256), 256, 0, s>>>(cap, w.inst1, w.tile_key, w.tk1);
-    count_launch();
-    sort_pairs_u32(w.sort_ws, cap, bits, w.tk1, w.inst1, w.tk_s, w.inst2, s);
+    sort_pairs_u32(w.sort_ws, cap, bits, w.tile_key, nullptr, w.tk_s, w.inst, s);
     k_gs_ranges_cap<<<grid_for(cap, 256), 256, 0, s>>>(cap, (int)tiles, w.tk_s, w.range);
     count_launch();
-    k_gs_render<<<dim3(gx, gy), kTilePix, 0, s>>>(*cam, gx, w.range, w.inst2, w.gid, w.uv, w.conic_o, d_color,
-                                                  d_image, d_trans);
-    count_launch();
+    k_gs_tile_order<<<1, 1024, 0, s>>>((int)tiles, w.range, w.torder);
+    k_gs_render<<<(unsigned)tiles, kTilePix, 0, s>>>(*cam, gx, w.torder, w.range, w.inst, w.gid, w.uv, w.conic_o,
+                                                     w.reach, d_color, d_image, d_trans);
+    count_launch(2);
     return check_launch();
 }
 

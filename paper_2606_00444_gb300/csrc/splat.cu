@@ -219,7 +219,7 @@ k_gs_render(mesh_camera cam, int gx, const int *__restrict__ order, const int2 *
             const float *__restrict__ color, float *image, float *trans) {
     __shared__ float2 s_uv[kTilePix];
     __shared__ float4 s_co[kTilePix];
-    __shared__ float3 s_col[kTilePix];
+    __shared__ float4 s_col[kTilePix];
     __shared__ float4 s_reach[kTilePix];
     const int tile = order[blockIdx.x];                     // the heaviest tiles first
     const int tx = tile % gx, ty = tile / gx;
@@ -239,7 +239,8 @@ k_gs_render(mesh_camera cam, int gx, const int *__restrict__ order, const int2 *
             int g = gid[inst[k]];
             s_uv[threadIdx.x] = uv[g];
             s_co[threadIdx.x] = conic_o[g];
-            s_col[threadIdx.x] = make_float3(color[3 * (size_t)g], color[3 * (size_t)g + 1], color[3 * (size_t)g + 2]);
+            s_col[threadIdx.x] = make_float4(color[3 * (size_t)g], color[3 * (size_t)g + 1], color[3 * (size_t)g + 2],
+                                             0.0f);
             s_reach[threadIdx.x] = reach[g];
         }
         __syncthreads();
@@ -256,23 +257,46 @@ k_gs_render(mesh_camera cam, int gx, const int *__restrict__ order, const int2 *
                 reaches = !(rb.y < wx0 || rb.x > wx1 || rb.w < wy0 || rb.z > wy1);
             }
             unsigned int todo = __ballot_sync(0xffffffffu, reaches);
+            // two instances per step: their exponents do not depend on the blend, so
+            // both are evaluated before the two blends (which stay in order)
             while (todo) {
-                const int j = j0 + __ffs(todo) - 1;
+                const int ja = j0 + __ffs(todo) - 1;
+                todo &= todo - 1u;
+                const int jb = todo ? j0 + __ffs(todo) - 1 : ja;
+                const bool two = todo != 0u;
                 todo &= todo - 1u;
                 if (done) continue;
-                float dx = s_uv[j].x - (float)px, dy = s_uv[j].y - (float)py;
-                float4 co = s_co[j];
-                float p = -0.5f * (co.x * dx * dx + co.z * dy * dy) - co.y * dx * dy;
-                if (p > 0.0f) continue;
-                float alpha = fminf(0.99f, co.w * expf(p));
-                if (alpha < 1.0f / 255.0f) continue;
-                float tt = T * (1.0f - alpha);
-                if (tt < 1e-4f) { done = true; continue; }
-                float3 c = s_col[j];
-                C0 += c.x * alpha * T;
-                C1 += c.y * alpha * T;
-                C2 += c.z * alpha * T;
-                T = tt;
+                const float2 ua = s_uv[ja], ub = s_uv[jb];
+                const float4 ca = s_co[ja], cb = s_co[jb];
+                const float dxa = ua.x - (float)px, dya = ua.y - (float)py;
+                const float dxb = ub.x - (float)px, dyb = ub.y - (float)py;
+                const float pa = -0.5f * (ca.x * dxa * dxa + ca.z * dya * dya) - ca.y * dxa * dya;
+                const float pb = -0.5f * (cb.x * dxb * dxb + cb.z * dyb * dyb) - cb.y * dxb * dyb;
+                const float ea = expf(pa), eb = expf(pb);
+                if (!(pa > 0.0f)) {
+                    const float alpha = fminf(0.99f, ca.w * ea);
+                    if (alpha >= 1.0f / 255.0f) {
+                        const float tt = T * (1.0f - alpha);
+                        if (tt < 1e-4f) { done = true; continue; }
+                        const float4 c = s_col[ja];
+                        C0 += c.x * alpha * T;
+                        C1 += c.y * alpha * T;
+                        C2 += c.z * alpha * T;
+                        T = tt;
+                    }
+                }
+                if (two && !(pb > 0.0f)) {
+                    const float alpha = fminf(0.99f, cb.w * eb);
+                    if (alpha >= 1.0f / 255.0f) {
+                        const float tt = T * (1.0f - alpha);
+                        if (tt < 1e-4f) { done = true; continue; }
+                        const float4 c = s_col[jb];
+                        C0 += c.x * alpha * T;
+                        C1 += c.y * alpha * T;
+                        C2 += c.z * alpha * T;
+                        T = tt;
+                    }
+                }
             }
         }
     }

@@ -63,10 +63,11 @@ def parse():
     ap.add_argument("--impl", default="meshgs", choices=["meshgs", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="physics",
-                    choices=["physics", "batch", "sequence", "fit", "tracking", "contact"],
+                    choices=["physics", "batch", "sequence", "fit", "tracking", "contact", "render"],
                     help="physics: the default frame; batch: 64 scenes batched vs per scene; "
                          "sequence: varying-topology conversion; fit: differentiable template fit; "
-                         "contact: the contact kernel and the refit alone (profiling)")
+                         "contact: the contact kernel and the refit alone (profiling); "
+                         "render: the frame's Gaussian render alone (profiling)")
     ap.add_argument("--variant", type=int, default=-1,
                     help="contact workload: one-thread traversal variant (-1: the autotuner's)")
     ap.add_argument("--leaf", type=int, default=1, help="contact workload: leaf size (with --variant)")
@@ -147,6 +148,50 @@ def max_over_ranks(ms: float, world: int, device) -> float:
     tt = torch.tensor([ms], dtype=torch.float64, device=device)
     dist.all_reduce(tt, op=dist.ReduceOp.MAX)
     return float(tt.item())
+
+
+def render_camera():
+    """The render's view of the torus (world -> camera rotation and translation)."""
+    eye, tgt = np.array([0.4, -2.6, 1.5]), np.zeros(3)
+    zc = (tgt - eye) / np.linalg.norm(tgt - eye)
+    xc = np.cross(zc, [0, 0, 1.0])
+    xc /= np.linalg.norm(xc)
+    Rc = np.stack([xc, np.cross(zc, xc), zc])
+    return Rc, -Rc @ eye
+
+
+def render_appearance(n):
+    """Seeded opacities and colours of the n rendered Gaussians."""
+    rng = np.random.default_rng(SEED + 6)
+    return (rng.uniform(0.4, 0.9, n).astype(np.float32), rng.uniform(0.0, 1.0, (n, 3)).astype(np.float32))
+
+
+def bench_render(args):
+    """The frame's Gaussian-splatting render alone (profiling): the 600k face-bound
+    Gaussians of the skinned torus (frame 1) from the frame's camera at 1280 x 720,
+    rendered warmup + steps times; one JSON line with the per-render times."""
+    import torch
+    from paper_2606_00444_gb300 import MeshBVH, Workspace, gs_render
+    dev = torch.device("cuda")
+    W = Workload(2)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    fixed = MeshBVH(W.V0.shape[0], W.F.shape[0], dev).build(t(W.V0), t(W.F), method="ploc")
+    fixed.refit(t(W.frames[1]))
+    mu, quat, scale = fixed.bind_gaussians(t(W.gface), t(W.gbary))
+    g_op, g_col = (t(a) for a in render_appearance(W.gface.shape[0]))
+    Rc, tc = render_camera()
+    ws, out, ms = Workspace(dev), None, []
+    for k in range(args.warmup + args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        out = gs_render(mu, quat, scale, g_op, g_col, Rc, tc, 1100.0, 1100.0, 640, 360, 1280, 720, ws=ws, out=out)
+        b.record()
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            ms.append(a.elapsed_time(b))
+    print(json.dumps({"metric": "Gaussian render alone", "workload": "render", "gaussians": int(W.gface.shape[0]),
+                      "steps": args.steps, "warmup": args.warmup, "render_ms": ms,
+                      "median_ms": float(np.median(ms))}))
 
 
 def replicas_value(queries_per_frame: int, world: int, ms: float) -> float:
@@ -419,13 +464,8 @@ def gpu_arm(args, rank, world, local_rank):
     # Gaussian-splatting render of the frame's 600k rebound Gaussians, 1280 x 720
     # (synchronous call: it reads the tile-instance count; host time included)
     from paper_2606_00444_gb300 import gs_render
-    rng = np.random.default_rng(SEED + 6)
-    g_op = t(rng.uniform(0.4, 0.9, gface.shape[0]).astype(np.float32))
-    g_col = t(rng.uniform(0.0, 1.0, (gface.shape[0], 3)).astype(np.float32))
-    eye, tgt = np.array([0.4, -2.6, 1.5]), np.zeros(3)
-    zc = (tgt - eye) / np.linalg.norm(tgt - eye)
-    xc = np.cross(zc, [0, 0, 1.0]); xc /= np.linalg.norm(xc)
-    Rc = np.stack([xc, np.cross(zc, xc), zc]); tc = -Rc @ eye
+    g_op, g_col = (t(a) for a in render_appearance(gface.shape[0]))
+    Rc, tc = render_camera()
     r_ws, r_out = Workspace(dev), None
     r_ms = []
     for k in range(13):
@@ -1202,7 +1242,7 @@ def main():
         return reference_arm(args, rank, world)
     if args.workload != "physics":
         return {"batch": bench_batch, "sequence": bench_sequence, "fit": bench_fit,
-                "tracking": bench_tracking, "contact": bench_contact}[args.workload](args)
+                "tracking": bench_tracking, "contact": bench_contact, "render": bench_render}[args.workload](args)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")

@@ -1958,7 +1958,9 @@ mesh_status mesh_contact(const mesh_bvh *bvh, const float *d_Q, int64_t nQ, floa
     cudaStream_t s = (cudaStream_t)stream;
     const int n = (int)nQ;
     const int tiles = (n + kClassTile - 1) / kClassTile;
-    pdl_launch(k_class_count, tiles, kClassThreads, 0, s, w.cls, n, w.counts);
+    // the call's first kernel is a plain launch (ordered after whatever the caller
+    // put on the stream); the two after it are its programmatic dependents
+    k_class_count<<<tiles, kClassThreads, 0, s>>>(w.cls, n, w.counts);
     pdl_launch(k_class_scatter, tiles, kClassThreads, 0, s, w.cls, n, w.counts, tiles, w.order);
     count_launch(2);
     float maxd2 = isinf(max_dist) ? INFINITY : max_dist * max_dist;

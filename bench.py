@@ -49,6 +49,7 @@ NU, NV_, CUTOFF, N_PART, G_PER_FACE, N_CD = 400, 250, 0.05, 1 << 20, 3, 10000
 SEED = 3000
 CONTACT_BYTES = 12 + 4 + 12 + 12 + 4      # query xyz in; face, bary, point, dist2 out
 NODE_BYTES = 64                            # one node visit reads both 32-byte child boxes
+WIDE_BYTES = 128                           # one 4-wide record (traversal variant 13): 4 boxes, links
 TRI_BYTES = 48                             # one triangle test reads a packed triangle
 ROOF_FRAME = 30                            # skinned pose of the roofline launch and its ncu record
 REFIT_BYTES = 150                          # per face: 16 B index + ~8 B vertex share + 32 B leaf
@@ -822,7 +823,8 @@ def bench_contact(args):
             tc.append(e[1].elapsed_time(e[2]))
     l2 = l2_read_bandwidth()
     vis, tst = stats["visits"] / N_PART, stats["tests"] / N_PART
-    bpq = CONTACT_BYTES + NODE_BYTES * vis + TRI_BYTES * tst
+    node_bytes = WIDE_BYTES if (tuned["variant"] == 13 and tuned["lanes"] == 1) else NODE_BYTES
+    bpq = CONTACT_BYTES + node_bytes * vis + TRI_BYTES * tst
     line = {"metric": "contact kernel and refit alone", "workload": "contact", "steps": args.steps,
             "warmup": args.warmup, "tuned": tuned,
             "contact_ms": {"median": float(np.median(tc)), "mean": float(np.mean(tc)),
@@ -1256,7 +1258,8 @@ def main():
     # The roofline of the dominant kernel, the contact query.  Its tree (40 MB) and
     # particles stay in L2, so its bytes are bounded by L2, not HBM, bandwidth: the
     # headline fraction is its algorithmic bytes (44 B of query I/O, 64 B per node
-    # visit = both children's 32-byte boxes, 48 B per triangle test, counted by the
+    # visit = both children's 32-byte boxes, or 128 B per 4-wide record with
+    # traversal variant 13, 48 B per triangle test, counted by the
     # counting form of the same traversal) over the L2 read bandwidth measured in
     # this run.  Beside it, from the committed ncu capture of the same launch: DRAM
     # bytes over the measured HBM peak, L2 bytes over the L2 peak, and the FP32 pipe.
@@ -1265,7 +1268,9 @@ def main():
     t_contact = res["roof_ms"] * 1e-3
     vis = res["stats"]["visits"] / N_PART
     tst = res["stats"]["tests"] / N_PART
-    per_query = CONTACT_BYTES + NODE_BYTES * vis + TRI_BYTES * tst
+    # (with the 4-wide traversal the counting form counts its 128-byte records)
+    node_bytes = WIDE_BYTES if (res["tuned"]["variant"] == 13 and res["tuned"]["lanes"] == 1) else NODE_BYTES
+    per_query = CONTACT_BYTES + node_bytes * vis + TRI_BYTES * tst
     achieved = per_query * N_PART / t_contact / 1e9
     rec = contact_traffic(res["tuned"]) if res["tuned"]["lanes"] == 1 else None
     rec = rec or {}
@@ -1279,7 +1284,7 @@ def main():
             "traffic": dram,
             "bytes_per_query": per_query,
             "per_query": {"io": CONTACT_BYTES, "node_visits": vis, "triangle_tests": tst,
-                          "node_bytes": NODE_BYTES, "triangle_bytes": TRI_BYTES},
+                          "node_bytes": node_bytes, "triangle_bytes": TRI_BYTES},
             "algorithmic_over_hbm_peak": achieved / hbm,
             "hbm": {"bytes_per_launch": dram, "achieved": dram / t_contact / 1e9 if dram else None,
                     "peak": hbm, "peak_source": src,

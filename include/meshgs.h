@@ -102,6 +102,13 @@ typedef struct {
                             ranges cross blocks int32x4 [max_faces] (node, range start, range
                             end, parent link), per block its box (32 B) and its count of
                             crossing nodes (int32)                                           */
+    size_t off_wide;     /* 8 x float4 per internal node: its 4-wide record (traversal variant
+                            13), four slots (lo, link) (hi, n) laid out as in the node records:
+                            per side, the child's own node record when the child is internal
+                            (its two children), else the node's slot for that leaf link and an
+                            empty slot (link INT32_MIN, lo +inf, hi -inf, n 0).  Written from the
+                            node records by every build or refit of a handle whose traversal is
+                            variant 13, else by the first variant-13 query after one           */
     size_t storage_bytes;
 } mesh_bvh_layout;
 
@@ -399,6 +406,11 @@ mesh_status mesh_set_query_group(int lanes);
  *  12 warp packet: the 32 queries of a warp share one node sequence, a node
  *     entered when any lane needs it (for queries kept in Morton order; it
  *     gains most from leaf collapse, mesh_bvh_set_leaf_size)
+ *  13 depth-first over 4-wide records (each visit tests up to four boxes:
+ *     the node's children, an internal child replaced by its two; about half
+ *     the visits of the binary tree), 8 shared entries; the records are
+ *     written from the binary tree by the first such query after a build or
+ *     refit (layout off_wide)
  * (the shared part of the stack spills to local memory; local-only leaves the
  * SM's L1 to the node cache).  Process-wide; the same answers, bit for bit,
  * for every variant. */

@@ -27,7 +27,8 @@ class Layout(C.Structure):
     _fields_ = [("n_faces", I64), ("n_verts", I64), ("max_faces", I64), ("max_verts", I64),
                 ("off_header", SZ), ("off_verts", SZ), ("off_faces", SZ), ("off_keys", SZ),
                 ("off_perm", SZ), ("off_nodes", SZ), ("off_parent", SZ), ("off_tris", SZ),
-                ("off_rend", SZ), ("off_iperm", SZ), ("off_adj", SZ), ("off_fnorm", SZ), ("off_xlist", SZ), ("storage_bytes", SZ)]
+                ("off_rend", SZ), ("off_iperm", SZ), ("off_adj", SZ), ("off_fnorm", SZ), ("off_xlist", SZ), ("off_wide", SZ),
+                ("storage_bytes", SZ)]
 
 
 class BatchLayout(C.Structure):

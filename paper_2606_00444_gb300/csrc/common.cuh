@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "meshgs.h"
 
 namespace meshgs {
@@ -24,6 +26,7 @@ struct mesh_bvh_impl {
     int cfg_variant = -1;
     int cfg_block = 128;     // threads per block of the one-thread traversal (variants 0, 2, 3)
     int leaf_size = 1;       // faces per collapsed leaf, written by the next build / refit
+    mutable bool wide_valid = false;   // the 4-wide records match the node records
     Header *hdr() const { return reinterpret_cast<Header *>(base + L.off_header); }
     float4 *verts() const { return reinterpret_cast<float4 *>(base + L.off_verts); }
     int4 *faces() const { return reinterpret_cast<int4 *>(base + L.off_faces); }
@@ -32,6 +35,7 @@ struct mesh_bvh_impl {
     float4 *nodes() const { return reinterpret_cast<float4 *>(base + L.off_nodes); }
     int *parent() const { return reinterpret_cast<int *>(base + L.off_parent); }
     float4 *tris() const { return reinterpret_cast<float4 *>(base + L.off_tris); }
+    float4 *wide() const { return reinterpret_cast<float4 *>(base + L.off_wide); }
     int *rend() const { return reinterpret_cast<int *>(base + L.off_rend); }
     int *iperm() const { return reinterpret_cast<int *>(base + L.off_iperm); }
     int *adj() const { return reinterpret_cast<int *>(base + L.off_adj); }
@@ -104,9 +108,10 @@ mesh_status check_launch();
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
+// launch_ex(pdl = false, ...) is a plain launch of the same kernel.
 template <typename... KArgs, typename... Args>
-inline void pdl_launch(void (*kernel)(KArgs...), unsigned int grid, unsigned int block, size_t smem, cudaStream_t s,
-                       Args &&...args) {
+inline void launch_ex(bool pdl, void (*kernel)(KArgs...), unsigned int grid, unsigned int block, size_t smem,
+                      cudaStream_t s, Args &&...args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(block);
@@ -116,8 +121,14 @@ inline void pdl_launch(void (*kernel)(KArgs...), unsigned int grid, unsigned int
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = pdl ? 1 : 0;
     cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
+template <typename... KArgs, typename... Args>
+inline void pdl_launch(void (*kernel)(KArgs...), unsigned int grid, unsigned int block, size_t smem, cudaStream_t s,
+                       Args &&...args) {
+    launch_ex(true, kernel, grid, block, smem, s, std::forward<Args>(args)...);
 }
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -143,6 +154,13 @@ __device__ __forceinline__ float4 ldg4(const float4 *p) { return __ldg(p); }
 __device__ __forceinline__ void set_status(Header *h, unsigned int bit) {
     atomicOr(&h->status, bit);
 }
+
+// The 4-wide records of traversal variant 13 (query.cu): wide_refresh writes them
+// from the node records on stream s (as a programmatic dependent when pdl) and
+// marks them current; wide_wanted tells whether the handle's traversal is
+// variant 13, so that its builds and refits refresh them.
+void wide_refresh(const mesh_bvh *b, cudaStream_t s, bool pdl);
+bool wide_wanted(const mesh_bvh *b);
 
 }  // namespace meshgs
 

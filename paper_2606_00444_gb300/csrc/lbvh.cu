@@ -1107,6 +1107,7 @@ static mesh_bvh_layout storage_layout(int64_t maxV, int64_t maxF) {
     L.off_adj = take(12 * f);
     L.off_fnorm = take(16 * f);
     L.off_xlist = take(xlist_bytes(f));
+    L.off_wide = take(128 * (f > 1 ? f - 1 : 1));
     L.storage_bytes = off;
     return L;
 }
@@ -1364,6 +1365,7 @@ mesh_status mesh_bvh_create(void *d_storage, size_t storage_bytes, int64_t max_v
     h->cfg_variant = -1;
     h->cfg_block = 128;
     h->leaf_size = 1;
+    h->wide_valid = false;
     h->adj_ready = false;
     *out = h;
     return MESH_OK;
@@ -1407,6 +1409,7 @@ static mesh_status bottom_up(mesh_bvh *bvh, const float *V3, cudaStream_t s,
         smem_set = true;
     }
     int n = (int)bvh->L.n_faces;
+    bvh->wide_valid = false;
     unsigned int nb = grid_for(n, kRefitBlock);
     int64_t fmax = bvh->L.max_faces, nbmax = refit_blocks(fmax);
     float4 *pre = reinterpret_cast<float4 *>(bvh->xlist()), *suf = pre + 2 * fmax;
@@ -1424,6 +1427,7 @@ static mesh_status bottom_up(mesh_bvh *bvh, const float *V3, cudaStream_t s,
                    bvh->leaf_size);
         count_launch();
     }
+    if (wide_wanted(bvh)) wide_refresh(bvh, s, true);     // the 4-wide records of variant 13
     return check_launch();
 }
 
@@ -1455,6 +1459,7 @@ static void build_keys(mesh_bvh *bvh, const float *d_V, int64_t nV, const int32_
     bvh->L.n_verts = nV;
     bvh->L.n_faces = nF;
     bvh->adj_ready = false;
+    bvh->wide_valid = false;
     int n = (int)nF;
     cudaMemsetAsync(bvh->hdr(), 0, sizeof(Header), s);
     if (nV > 0) {

@@ -12,6 +12,7 @@
 // inside the final window is ever skipped.  The nearest face is the lowest id
 // within that final window (see Best), the same for every tree, traversal
 // order and warm start: a function of the query and the mesh alone.
+#include <climits>
 #include <math.h>
 
 #include <mutex>
@@ -210,6 +211,7 @@ struct Traversal {
     float tau;     // absolute floor of the tie window (1e-12 of the box diagonal)
     float vmax;    // largest coordinate magnitude of the mesh box
     bool mmd;      // use MinMaxDist bounds (unbounded queries; a cutoff is tighter)
+    const float4 *__restrict__ wide;   // the 4-wide records (traversal variant 13)
 };
 
 __device__ __forceinline__ float query_slack(const Traversal &T, float3 q) {
@@ -480,6 +482,140 @@ __device__ __forceinline__ Hit nearest(const Traversal &T, float3 q, float maxd2
         }
     }
     return finish(T, B, q, status);
+}
+
+// Depth-first over the 4-wide records (variant 13): each visit tests up to four
+// boxes -- the node's children, an internal child replaced by its own two --
+// so a search takes about half the visits of the binary one, each reading one
+// 128-byte record.  Leaf slots are tested first (they may shrink the window),
+// then the internal slots still within it are ordered by box distance: the
+// nearest is entered, the others pushed farthest first.  The pruning, the
+// candidate bookkeeping and the tie rule are those of nearest(), so the answer
+// is the same, bit for bit.  cnt->visits counts 4-wide records.
+constexpr int kWideStack = 3 * kStackTotal / 2 + 2;   // up to 3 pushes per record, half the depth
+constexpr int kWideEmpty = INT_MIN;
+
+__device__ __forceinline__ void wide_swap(float &da, int &ca, float &db, int &cb) {
+    if (db < da) {
+        float t = da; da = db; db = t;
+        int u = ca; ca = cb; cb = u;
+    }
+}
+
+template <int kBlockT, int kSmem, bool kCount, bool kRange, bool kMmd>
+__device__ __forceinline__ Hit nearest_wide_t(const Traversal &T, float3 q, float maxd2,
+                                              int2 (*stk)[kBlockT], unsigned int *status, Counts *cnt,
+                                              int hint_leaf) {
+    Best B = make_best(T, q, maxd2);
+    if (hint_leaf >= 0) test_leaf(T, B, hint_leaf, q, maxd2);
+    if (T.n == 1) {
+        if constexpr (kCount) cnt->tests++;
+        test_leaf(T, B, 0, q, maxd2);
+    } else if (T.n > 1) {
+        const float4 *__restrict__ W = T.wide;
+        int2 spill[kWideStack - kSmem];
+        int sp = 0;
+        int node = 0;
+        const int tid = threadIdx.x % kBlockT;
+        while (true) {
+            const float4 *r = W + 8 * (size_t)node;
+            if constexpr (kCount) cnt->visits++;
+            const float4 lo0 = ldg4(r), hi0 = ldg4(r + 1), lo1 = ldg4(r + 2), hi1 = ldg4(r + 3), lo2 = ldg4(r + 4),
+                         hi2 = ldg4(r + 5), lo3 = ldg4(r + 6), hi3 = ldg4(r + 7);
+            float d0 = box_d2(q, lo0, hi0), d1 = box_d2(q, lo1, hi1), d2 = box_d2(q, lo2, hi2),
+                  d3 = box_d2(q, lo3, hi3);
+            int c0 = __float_as_int(lo0.w), c1 = __float_as_int(lo1.w), c2 = __float_as_int(lo2.w),
+                c3 = __float_as_int(lo3.w);
+            if constexpr (kMmd) {
+                float u = INFINITY;
+                if (c0 != kWideEmpty) u = fminf(u, box_minmax_d2(q, lo0, hi0));
+                if (c1 != kWideEmpty) u = fminf(u, box_minmax_d2(q, lo1, hi1));
+                if (c2 != kWideEmpty) u = fminf(u, box_minmax_d2(q, lo2, hi2));
+                if (c3 != kWideEmpty) u = fminf(u, box_minmax_d2(q, lo3, hi3));
+                B.thr = fminf(B.thr, bound_window2(u, T.tau, query_slack(T, q)));
+            }
+            // leaf slots (the face count of a leaf link is read only with leaf collapse)
+            auto leaf = [&](int c, float d, float hw) {
+                if (c < 0 && c != kWideEmpty && d <= B.thr) {
+                    const int m = kRange ? __float_as_int(hw) : 1;
+                    if constexpr (kCount) cnt->tests += m;
+                    test_range<kRange>(T, B, -c - 1, m, q, maxd2);
+                }
+            };
+            leaf(c0, d0, hi0.w);
+            leaf(c1, d1, hi1.w);
+            leaf(c2, d2, hi2.w);
+            leaf(c3, d3, hi3.w);
+            float k0 = (c0 >= 0 && d0 <= B.thr) ? d0 : INFINITY;
+            float k1 = (c1 >= 0 && d1 <= B.thr) ? d1 : INFINITY;
+            float k2 = (c2 >= 0 && d2 <= B.thr) ? d2 : INFINITY;
+            float k3 = (c3 >= 0 && d3 <= B.thr) ? d3 : INFINITY;
+            const int nin = (k0 < INFINITY) + (k1 < INFINITY) + (k2 < INFINITY) + (k3 < INFINITY);
+            if (nin > 0) {
+                wide_swap(k0, c0, k1, c1);
+                wide_swap(k2, c2, k3, c3);
+                wide_swap(k0, c0, k2, c2);
+                wide_swap(k1, c1, k3, c3);
+                wide_swap(k1, c1, k2, c2);
+                auto push = [&](int c, float k) {
+                    const int2 e = make_int2(c, __float_as_int(k));
+                    if (sp < kSmem) stk[sp][tid] = e;
+                    else if (sp < kWideStack) spill[sp - kSmem] = e;
+                    else atomicOr(status, (unsigned)MESH_DEV_STACK_OVERFLOW);
+                    if (sp < kWideStack) ++sp;
+                };
+                if (nin > 3) push(c3, k3);
+                if (nin > 2) push(c2, k2);
+                if (nin > 1) push(c1, k1);
+                node = c0;
+                continue;
+            }
+            bool found = false;
+            while (sp > 0) {
+                --sp;
+                int2 e = sp < kSmem ? stk[sp][tid] : spill[sp - kSmem];
+                if (__int_as_float(e.y) <= B.thr) { node = e.x; found = true; break; }
+            }
+            if (!found) break;
+        }
+    }
+    return finish(T, B, q, status);
+}
+
+// (the MinMaxDist form, for unbounded queries, is a separate loop: the bounded
+// one keeps the register budget of the search alone)
+template <int kBlockT, int kSmem = 8, bool kCount = false, bool kRange = false>
+__device__ __forceinline__ Hit nearest_wide(const Traversal &T, float3 q, float maxd2,
+                                            int2 (*stk)[kBlockT], unsigned int *status,
+                                            Counts *cnt = nullptr, int hint_leaf = -1) {
+    if (T.mmd) return nearest_wide_t<kBlockT, kSmem, kCount, kRange, true>(T, q, maxd2, stk, status, cnt, hint_leaf);
+    return nearest_wide_t<kBlockT, kSmem, kCount, kRange, false>(T, q, maxd2, stk, status, cnt, hint_leaf);
+}
+
+// The 4-wide records from the node records, one thread per (internal node,
+// side): the record's half for that side is the child's own node record when the
+// child is internal (its two children as two slots), else the node's slot for the
+// leaf link and an empty slot -- a copy of 64 bytes.
+__global__ void k_wide_update(const float4 *__restrict__ nodes, int nint, float4 *__restrict__ wide) {
+    pdl_wait();
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = (int)(t >> 1), s = (int)(t & 1);
+    if (n >= nint) return;
+    const float4 a = __ldg(nodes + 4 * (size_t)n + 2 * s), b = __ldg(nodes + 4 * (size_t)n + 2 * s + 1);
+    const int link = __float_as_int(a.w);
+    float4 *w = wide + 8 * (size_t)n + 4 * s;
+    if (link < 0) {
+        w[0] = a;
+        w[1] = b;
+        w[2] = make_float4(INFINITY, INFINITY, INFINITY, __int_as_float(kWideEmpty));
+        w[3] = make_float4(-INFINITY, -INFINITY, -INFINITY, __int_as_float(0));
+    } else {
+        const float4 *c = nodes + 4 * (size_t)link;
+        w[0] = __ldg(c);
+        w[1] = __ldg(c + 1);
+        w[2] = __ldg(c + 2);
+        w[3] = __ldg(c + 3);
+    }
 }
 
 // One thread per query, "while-while" form: internal nodes are traversed
@@ -845,7 +981,8 @@ __device__ __forceinline__ void write_hit(const Traversal &T, const Hit &h, floa
     }
 }
 
-// kMode: 0 depth-first, 1 while-while, 2 depth-first with one leaf-test site.
+// kMode: 0 depth-first, 1 while-while, 2 depth-first with one leaf-test site,
+// 3 depth-first over the 4-wide records.
 // kMinBlocks: resident blocks per SM the register budget must allow
 // (8 -> 64 registers, 9 -> 56, 12 -> 40, 16 -> 32; fewer registers, more warps
 // to hide latency, more spilling).
@@ -883,11 +1020,18 @@ k_closest_point(Traversal T, const Header *__restrict__ hdr, unsigned int *statu
     if constexpr (kRecord) {
         static_assert(kMode != 1, "the recording form uses the depth-first traversal");
         Counts c{0, 0};
-        h = nearest<kBlock, kSmem, kMode == 2, true, kRange>(T, q, maxd2, stk, status, &c, hint_leaf);
-        cls[i] = work_class(c.visits);
+        if constexpr (kMode == 3) {          // a 4-wide record counts as two binary visits
+            h = nearest_wide<kBlock, kSmem, true, kRange>(T, q, maxd2, stk, status, &c, hint_leaf);
+            cls[i] = work_class(2 * c.visits);
+        } else {
+            h = nearest<kBlock, kSmem, kMode == 2, true, kRange>(T, q, maxd2, stk, status, &c, hint_leaf);
+            cls[i] = work_class(c.visits);
+        }
     } else if constexpr (kMode == 1) {
         static_assert(!kRange, "the while-while form has no leaf-range instantiation");
         h = nearest_ww<kBlock>(T, q, maxd2, stk, status);
+    } else if constexpr (kMode == 3) {
+        h = nearest_wide<kBlock, kSmem, false, kRange>(T, q, maxd2, stk, status, nullptr, hint_leaf);
     } else {
         h = nearest<kBlock, kSmem, kMode == 2, false, kRange>(T, q, maxd2, stk, status, nullptr, hint_leaf);
     }
@@ -1337,7 +1481,8 @@ k_closest_point_persistent(Traversal T, const Header *__restrict__ hdr, unsigned
 // Counting form of the one-thread depth-first traversal (same visiting order
 // as variants 0, 2 and 3): node visits, triangle tests and hits, summed over
 // all queries.  Separate instantiation; the timed kernels carry no counters.
-template <bool kRange>
+// kWide: the traversal over the 4-wide records (its visits count records).
+template <bool kRange, bool kWide = false>
 __global__ void __launch_bounds__(kQueryBlock, kQueryMinBlocks)
 k_closest_point_count(Traversal T, const Header *__restrict__ hdr, unsigned int *status,
                       const float *__restrict__ Q, int64_t nQ, float maxd2,
@@ -1349,7 +1494,11 @@ k_closest_point_count(Traversal T, const Header *__restrict__ hdr, unsigned int 
     if (i < nQ) {
         set_scale(T, hdr);
         float3 q = make_float3(Q[3 * i], Q[3 * i + 1], Q[3 * i + 2]);
-        Hit h = nearest<kQueryBlock, kStackShared, false, true, kRange>(T, q, maxd2, stk, status, &c);
+        Hit h;
+        if constexpr (kWide)
+            h = nearest_wide<kQueryBlock, kStackShared, true, kRange>(T, q, maxd2, stk, status, &c);
+        else
+            h = nearest<kQueryBlock, kStackShared, false, true, kRange>(T, q, maxd2, stk, status, &c);
         hit = h.leaf >= 0;
     }
     unsigned long long v = c.visits, t = c.tests, k = hit;
@@ -1552,8 +1701,30 @@ __global__ void k_interpolate(const int4 *__restrict__ faces, const float4 *__re
 }
 
 static Traversal traversal_of(const mesh_bvh *b, bool mmd = true) {
-    return Traversal{b->nodes(), b->tris(), (int)b->L.n_faces, 0.0f, 0.0f, mmd};
+    return Traversal{b->nodes(), b->tris(), (int)b->L.n_faces, 0.0f, 0.0f, mmd, b->wide()};
 }
+
+// The 4-wide records written from the node records: by every build or refit of a
+// handle whose traversal is variant 13 (so a captured refit carries the update),
+// and otherwise by the first variant-13 query after the records went stale
+// (host-side flag; the update runs on that query's stream, ahead of it).
+static void ensure_wide(const mesh_bvh *b, cudaStream_t s) {
+    if (!b->wide_valid) wide_refresh(b, s, false);
+}
+
+}  // namespace meshgs
+
+void meshgs::wide_refresh(const mesh_bvh *b, cudaStream_t s, bool pdl) {
+    const int nint = (int)b->L.n_faces - 1;
+    if (nint > 0) {
+        launch_ex(pdl, k_wide_update, grid_for(2 * (int64_t)nint, 256), 256, 0, s, (const float4 *)b->nodes(), nint,
+                  b->wide());
+        count_launch();
+    }
+    b->wide_valid = true;
+}
+
+namespace meshgs {
 
 static size_t chamfer_blocks(int64_t n, int G = 1) {
     return (size_t)((n * G + kQueryBlock - 1) / kQueryBlock);
@@ -1565,6 +1736,10 @@ static size_t chamfer_blocks(int64_t n, int G = 1) {
 // mesh_set_query_group.)
 static int g_group_override = 0;
 static int g_traversal = 0;          // one-thread traversal variant, see mesh_set_traversal
+
+bool wide_wanted(const mesh_bvh *b) {
+    return (b->cfg_variant >= 0 ? b->cfg_variant : g_traversal) == 13 && b->cfg_lanes <= 1;
+}
 static int pick_group(int64_t nQ) {
     if (g_group_override > 0) return g_group_override;
     static int sms = 0;
@@ -1604,15 +1779,17 @@ static void launch_closest_point(Traversal T, Header *h, const float *d_Q, int64
                                  int32_t *d_face, float *d_bary, float *d_point, float *d_dist2,
                                  const int32_t *d_hint, const int *iperm, int G, int variant, int blk,
                                  cudaStream_t s) {
-    if (R && !(variant == 0 || variant == 2 || variant == 3 || variant == 12)) variant = 0;
+    if (R && !(variant == 0 || variant == 2 || variant == 3 || variant == 12 || variant == 13)) variant = 0;
     unsigned int grid = grid_for(nQ * G, kQueryBlock);
-    if (G == 1 && blk != kQueryBlock && (variant == 0 || variant == 2 || variant == 3)) {
+    if (G == 1 && blk != kQueryBlock && (variant == 0 || variant == 2 || variant == 3 || variant == 13)) {
         unsigned int gb = grid_for(nQ, blk);
-#define MESH_CPB(SM, B) k_closest_point<SM, 0, kQueryMinBlocks, false, B, R><<<gb, B, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2, d_hint, iperm)
+#define MESH_CPB(SM, M, B) k_closest_point<SM, M, kQueryMinBlocks, false, B, R><<<gb, B, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2, d_hint, iperm)
         if (blk == 32) {
-            if (variant == 2) MESH_CPB(8, 32); else if (variant == 3) MESH_CPB(0, 32); else MESH_CPB(kStackShared, 32);
+            if (variant == 2) MESH_CPB(8, 0, 32); else if (variant == 3) MESH_CPB(0, 0, 32);
+            else if (variant == 13) MESH_CPB(8, 3, 32); else MESH_CPB(kStackShared, 0, 32);
         } else {
-            if (variant == 2) MESH_CPB(8, 64); else if (variant == 3) MESH_CPB(0, 64); else MESH_CPB(kStackShared, 64);
+            if (variant == 2) MESH_CPB(8, 0, 64); else if (variant == 3) MESH_CPB(0, 0, 64);
+            else if (variant == 13) MESH_CPB(8, 3, 64); else MESH_CPB(kStackShared, 0, 64);
         }
 #undef MESH_CPB
         return;
@@ -1622,6 +1799,7 @@ static void launch_closest_point(Traversal T, Header *h, const float *d_Q, int64
 #define MESH_CP_ARGS <<<grid, kQueryBlock, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2, d_hint, iperm)
             switch (variant) {
                 case 2: k_closest_point<8, 0, kQueryMinBlocks, false, kQueryBlock, R> MESH_CP_ARGS; break;
+                case 13: k_closest_point<8, 3, kQueryMinBlocks, false, kQueryBlock, R> MESH_CP_ARGS; break;
                 case 3: k_closest_point<0, 0, kQueryMinBlocks, false, kQueryBlock, R> MESH_CP_ARGS; break;
                 case 12: k_closest_point_packet<false, R><<<grid, kQueryBlock, 0, s>>>(T, h, &h->status, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2, d_hint, iperm); break;
                 default:
@@ -1677,7 +1855,7 @@ template <bool R>
 static void launch_contact(Traversal T, Header *h, const float *d_Q, int64_t nQ, float maxd2, int32_t *d_face,
                            float *d_bary, float *d_point, float *d_dist2, const int *iperm, const int *order,
                            unsigned int *cls, int variant, int blk, cudaStream_t s) {
-    if (R && !(variant == 0 || variant == 2 || variant == 3 || variant == 12)) variant = 0;
+    if (R && !(variant == 0 || variant == 2 || variant == 3 || variant == 12 || variant == 13)) variant = 0;
     unsigned int grid = grid_for(nQ, kQueryBlock);
     // every form runs right after the sort of the classes: launched as its dependent
     auto go = [&](auto kern, unsigned int g, unsigned int b) {
@@ -1688,21 +1866,24 @@ static void launch_contact(Traversal T, Header *h, const float *d_Q, int64_t nQ,
         go(k_closest_point_packet<true, R>, grid, kQueryBlock);
         return;
     }
-    if (blk != kQueryBlock && (variant == 0 || variant == 2 || variant == 3)) {
+    if (blk != kQueryBlock && (variant == 0 || variant == 2 || variant == 3 || variant == 13)) {
         unsigned int gb = grid_for(nQ, blk);
         if (blk == 32) {
             if (variant == 2) go(k_closest_point<8, 0, kQueryMinBlocks, true, 32, R>, gb, 32);
             else if (variant == 3) go(k_closest_point<0, 0, kQueryMinBlocks, true, 32, R>, gb, 32);
+            else if (variant == 13) go(k_closest_point<8, 3, kQueryMinBlocks, true, 32, R>, gb, 32);
             else go(k_closest_point<kStackShared, 0, kQueryMinBlocks, true, 32, R>, gb, 32);
         } else {
             if (variant == 2) go(k_closest_point<8, 0, kQueryMinBlocks, true, 64, R>, gb, 64);
             else if (variant == 3) go(k_closest_point<0, 0, kQueryMinBlocks, true, 64, R>, gb, 64);
+            else if (variant == 13) go(k_closest_point<8, 3, kQueryMinBlocks, true, 64, R>, gb, 64);
             else go(k_closest_point<kStackShared, 0, kQueryMinBlocks, true, 64, R>, gb, 64);
         }
         return;
     }
     switch (variant) {
         case 2: go(k_closest_point<8, 0, kQueryMinBlocks, true, kQueryBlock, R>, grid, kQueryBlock); break;
+        case 13: go(k_closest_point<8, 3, kQueryMinBlocks, true, kQueryBlock, R>, grid, kQueryBlock); break;
         case 3: go(k_closest_point<0, 0, kQueryMinBlocks, true, kQueryBlock, R>, grid, kQueryBlock); break;
         default:
             if constexpr (!R) {
@@ -1804,7 +1985,8 @@ mesh_status mesh_closest_point_hinted(const mesh_bvh *bvh, const float *d_Q, int
     cudaStream_t s = (cudaStream_t)stream;
     int G = bvh->cfg_lanes > 0 ? bvh->cfg_lanes : pick_group(nQ);
     int variant = bvh->cfg_variant >= 0 ? bvh->cfg_variant : g_traversal;
-    if (variant >= 10 && nQ >= ((int64_t)1 << 31)) variant = 0;   // 32-bit work counter
+    if (variant >= 10 && variant <= 12 && nQ >= ((int64_t)1 << 31)) variant = 0;   // 32-bit work counter
+    if (G == 1 && variant == 13) ensure_wide(bvh, s);
     Traversal T = traversal_of(bvh, isinf(max_dist));
     if (bvh->leaf_size > 1)
         launch_closest_point<true>(T, bvh->hdr(), d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2, d_hint,
@@ -1951,13 +2133,15 @@ mesh_status mesh_contact(const mesh_bvh *bvh, const float *d_Q, int64_t nQ, floa
     ContactWs w = contact_ws(d_ws, nQ);
     if (!d_ws || ws_bytes < w.bytes || ((uintptr_t)d_ws & 255u)) return MESH_ERR_WORKSPACE;
     int variant = bvh->cfg_variant >= 0 ? bvh->cfg_variant : g_traversal;
-    if (bvh->leaf_size > 1 && !(variant == 0 || variant == 2 || variant == 3 || variant == 12)) variant = 0;
+    if (bvh->leaf_size > 1 && !(variant == 0 || variant == 2 || variant == 3 || variant == 12 || variant == 13))
+        variant = 0;
     if (variant == 1 || (variant >= 10 && variant <= 11) || (bvh->cfg_lanes > 1))
         return mesh_closest_point_hinted(bvh, d_Q, nQ, max_dist, d_face, d_face, d_bary, d_point, d_dist2,
                                          stream);
     cudaStream_t s = (cudaStream_t)stream;
     const int n = (int)nQ;
     const int tiles = (n + kClassTile - 1) / kClassTile;
+    if (variant == 13) ensure_wide(bvh, s);
     // the call's first kernel is a plain launch (ordered after whatever the caller
     // put on the stream); the two after it are its programmatic dependents
     k_class_count<<<tiles, kClassThreads, 0, s>>>(w.cls, n, w.counts);
@@ -2097,7 +2281,11 @@ mesh_status mesh_closest_point_stats(const mesh_bvh *bvh, const float *d_Q, int6
     cudaMemsetAsync(d_counts, 0, 3 * sizeof(unsigned long long), s);
     if (nQ == 0) return check_launch();
     float maxd2 = isinf(max_dist) ? INFINITY : max_dist * max_dist;
-    (bvh->leaf_size > 1 ? k_closest_point_count<true> : k_closest_point_count<false>)
+    const int variant = bvh->cfg_variant >= 0 ? bvh->cfg_variant : g_traversal;
+    const bool wide = variant == 13 && bvh->cfg_lanes <= 1;   // the 4-wide records' visits
+    if (wide) ensure_wide(bvh, s);
+    (bvh->leaf_size > 1 ? (wide ? k_closest_point_count<true, true> : k_closest_point_count<true>)
+                        : (wide ? k_closest_point_count<false, true> : k_closest_point_count<false>))
         <<<grid_for(nQ, kQueryBlock), kQueryBlock, 0, s>>>(
         traversal_of(bvh, isinf(max_dist)), bvh->hdr(), &bvh->hdr()->status, d_Q, nQ, maxd2,
         d_counts);
@@ -2118,7 +2306,7 @@ mesh_status mesh_bvh_set_query_config(mesh_bvh *bvh, int lanes, int variant) {
     if (lanes != -1 && lanes != 0 && lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8 &&
         lanes != 16 && lanes != 32)
         return MESH_ERR_INVALID_ARG;
-    if (variant < -1 || variant > 12) return MESH_ERR_INVALID_ARG;
+    if (variant < -1 || variant > 13) return MESH_ERR_INVALID_ARG;
     bvh->cfg_lanes = lanes;
     bvh->cfg_variant = variant;
     return MESH_OK;
@@ -2132,7 +2320,7 @@ mesh_status mesh_bvh_set_query_block(mesh_bvh *bvh, int threads) {
 }
 
 mesh_status mesh_set_traversal(int variant) {
-    if (variant < 0 || variant > 12) return MESH_ERR_INVALID_ARG;
+    if (variant < 0 || variant > 13) return MESH_ERR_INVALID_ARG;
     g_traversal = variant;
     return MESH_OK;
 }

@@ -94,8 +94,8 @@ def _apply(bvh: MeshBVH, cfg: dict) -> None:
 def closest_point_candidates(leaf_sizes=LEAF_SIZES):
     out = []
     for L in leaf_sizes:
-        out += [dict(leaf=L, lanes=1, variant=v, block=128) for v in range(13)]
-        out += [dict(leaf=L, lanes=1, variant=v, block=b) for v in (0, 2, 3) for b in (32, 64)]
+        out += [dict(leaf=L, lanes=1, variant=v, block=128) for v in range(14)]
+        out += [dict(leaf=L, lanes=1, variant=v, block=b) for v in (0, 2, 3, 13) for b in (32, 64)]
         out += [dict(leaf=L, lanes=g, variant=0, block=128) for g in (2, 4, 8, 16, 32)]
     return out
 

@@ -304,7 +304,7 @@ def test_leaf_collapse_gives_identical_answers_in_every_search():
     def answers():
         out = {}
         try:
-            for v in (0, 1, 2, 5, 10, 12):
+            for v in (0, 1, 2, 5, 10, 12, 13):
                 set_query_group(1)
                 set_traversal(v)
                 for cut in (0.05, np.inf):

@@ -140,7 +140,7 @@ def test_every_group_width_matches_oracle(c1, lanes):
         set_query_group(0)
 
 
-@pytest.mark.parametrize("variant", list(range(13)))
+@pytest.mark.parametrize("variant", list(range(14)))
 def test_every_thread_traversal_matches_oracle(c1, variant):
     from paper_2606_00444_gb300 import set_query_group, set_traversal
     _, _, VG, FG, Q = c1
@@ -176,7 +176,7 @@ def test_warp_packet_traversal_ragged_and_sorted(c1, n):
         set_traversal(0)
 
 
-@pytest.mark.parametrize("variant", [0, 2, 3, 9])
+@pytest.mark.parametrize("variant", [0, 2, 3, 9, 13])
 def test_warm_start_hint_gives_identical_answers(c1, variant):
     """mesh_closest_point_hinted: exact previous answers, random faces, -1 and
     out-of-range ids as hints, and the hint aliasing the face output, all give
@@ -230,6 +230,7 @@ def test_warm_start_over_a_skinned_sequence_full_size():
 
 
 @pytest.mark.parametrize("variant,leaf,block", [(0, 1, 128), (2, 1, 128), (5, 1, 128), (12, 1, 128),
+                                                (13, 1, 128), (13, 1, 32), (13, 4, 64),
                                                 (12, 8, 128), (2, 4, 32), (3, 1, 64)])
 def test_contact_step_equals_plain_queries(variant, leaf, block):
     """mesh_contact (previous faces as hints, queries ordered by the previous step's
@@ -300,3 +301,66 @@ def test_contact_writes_pinned_host_outputs():
     assert (h_out["face"] >= 0).any()
     ptr = C.c_void_p()
     assert lib().mesh_mapped_pointer(None, C.byref(ptr)) == 1
+
+
+def wide_records_from_nodes(bvh):
+    """The 4-wide records restated on the host from the binary node records (layout
+    off_nodes / off_wide): per internal node and side, the child's own node record when
+    the child is internal, else the node's slot for that leaf link and an empty slot
+    (link INT32_MIN, box +inf..-inf, count 0); slots as in the node records."""
+    L = bvh.layout()
+    nint = L["n_faces"] - 1
+    raw = bvh.storage[L["off_nodes"]:L["off_nodes"] + 64 * nint].cpu().numpy()
+    nd = raw.view(np.float32).reshape(nint, 4, 4)
+    ni = raw.view(np.int32).reshape(nint, 4, 4)
+    W = np.zeros((nint, 8, 4), np.float32)
+    Wi = W.view(np.int32)
+    empty_lo = np.array([np.inf, np.inf, np.inf, 0], np.float32)
+    empty_hi = np.array([-np.inf, -np.inf, -np.inf, 0], np.float32)
+    empty_lo.view(np.int32)[3] = -2 ** 31
+    for n in range(nint):
+        for s in (0, 1):
+            link = ni[n, 2 * s, 3]
+            if link < 0:
+                W[n, 4 * s], W[n, 4 * s + 1] = nd[n, 2 * s], nd[n, 2 * s + 1]
+                W[n, 4 * s + 2], W[n, 4 * s + 3] = empty_lo, empty_hi
+            else:
+                W[n, 4 * s:4 * s + 4] = nd[link]
+    return W, L
+
+
+@pytest.mark.parametrize("leaf", [1, 4])
+def test_wide_records_follow_the_tree(c1, leaf):
+    """Traversal variant 13 reads 4-wide records written from the node records by its
+    first query after a build or refit: they equal the host restatement bit for bit
+    (also after a refit to new vertices and with leaf collapse), its answers equal the
+    binary traversal's (bounded and unbounded) and the oracle's, and its counting form
+    visits fewer records than the binary form visits nodes."""
+    _, _, VG, FG, Q = c1
+    bvh = MeshBVH.from_mesh(dev(VG), dev(FG), method="ploc")
+    bvh.set_leaf_size(leaf)
+    rng = np.random.default_rng(5)
+    V = VG
+    for step in range(2):
+        if step:
+            V = (VG + 0.01 * rng.standard_normal(VG.shape)).astype(np.float32)
+            bvh.refit(dev(V))
+        ref, bin_stats = {}, None
+        bvh.set_query_config(1, 0)
+        for cut in (0.05, np.inf):
+            ref[cut] = bvh.closest_point(dev(Q), max_dist=cut)
+        bin_stats = bvh.closest_point_stats(dev(Q), 0.05)
+        bvh.set_query_config(1, 13)
+        got = {cut: bvh.closest_point(dev(Q), max_dist=cut) for cut in (0.05, np.inf)}
+        torch.cuda.synchronize()
+        W, L = wide_records_from_nodes(bvh)
+        raw = bvh.storage[L["off_wide"]:L["off_wide"] + W.nbytes].cpu().numpy()
+        assert np.array_equal(raw.view(np.uint32).reshape(W.shape), W.view(np.uint32))
+        for cut in (0.05, np.inf):
+            assert_identical(got[cut], ref[cut])
+        wide_stats = bvh.closest_point_stats(dev(Q), 0.05)
+        assert wide_stats["hits"] == bin_stats["hits"]
+        assert wide_stats["visits"] < 0.7 * bin_stats["visits"]
+    check_closest(V, FG, Q, got[0.05], max_dist=0.05)
+    bvh.set_query_config(-1, -1)
+    assert bvh.status()[0] == 0

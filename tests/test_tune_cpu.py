@@ -27,7 +27,8 @@ def test_candidates_cover_leaf_sizes_blocks_and_lanes():
     assert {x["block"] for x in cands if x["lanes"] == 1} == {32, 64, 128}
     assert {x["lanes"] for x in cands} == {1, 2, 4, 8, 16, 32}
     # blocks other than 128 only for the variants compiled in them
-    assert {x["variant"] for x in cands if x["block"] != 128} == {0, 2, 3}
+    assert {x["variant"] for x in cands if x["block"] != 128} == {0, 2, 3, 13}
+    assert {x["variant"] for x in cands if x["lanes"] == 1} == set(range(14))
     # every configuration is tried once per leaf size
     per_leaf = [x for x in cands if x["leaf"] == 1]
-    assert len(per_leaf) == len({(x["lanes"], x["variant"], x["block"]) for x in per_leaf}) == 24
+    assert len(per_leaf) == len({(x["lanes"], x["variant"], x["block"]) for x in per_leaf}) == 27

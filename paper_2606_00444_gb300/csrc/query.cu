@@ -953,6 +953,44 @@ __device__ __forceinline__ void set_scale(Traversal &T, const Header *hdr) {
     set_scale(T, hdr->root_lo, hdr->root_hi);
 }
 
+// The weights and closest point of a hit on leaf `leaf` (squared distance d2),
+// recomputed from the packed triangle.
+__device__ __forceinline__ void write_weights(const Traversal &T, int leaf, float d2, float3 q, int64_t i,
+                                              float *bary, float *point) {
+    const float4 *t = T.tris + 3 * (size_t)leaf;
+    float4 a = ldg4(t), b = ldg4(t + 1), c = ldg4(t + 2);
+    float u, v, w;
+    tri_closest(q, xyz(a), xyz(b), xyz(c), b.w != 0.0f, u, v, w);
+    if (weights_need_f64(xyz(a), xyz(b), xyz(c), d2))
+        tri_weights_f64(q, xyz(a), xyz(b), xyz(c), b.w != 0.0f, u, v, w);
+    if (bary) { bary[3 * i] = u; bary[3 * i + 1] = v; bary[3 * i + 2] = w; }
+    if (point) {
+        point[3 * i] = u * a.x + v * b.x + w * c.x;
+        point[3 * i + 1] = u * a.y + v * b.y + w * c.y;
+        point[3 * i + 2] = u * a.z + v * b.z + w * c.z;
+    }
+}
+
+// The weights of the contact step, after its search (which writes face and
+// distance only): one thread per query, so the recomputation of a hit's weights
+// no longer holds a search warp until its last lane is done.  Same values as
+// write_hit.
+__global__ void __launch_bounds__(256)
+k_hit_weights(Traversal T, const float *__restrict__ Q, int64_t nQ, const int *__restrict__ face,
+              const float *__restrict__ dist2, const int *__restrict__ iperm, float *bary, float *point) {
+    pdl_wait();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nQ) return;
+    const int f = face[i];
+    if (f < 0) {
+        if (bary) { bary[3 * i] = 0.0f; bary[3 * i + 1] = 0.0f; bary[3 * i + 2] = 0.0f; }
+        if (point) { point[3 * i] = 0.0f; point[3 * i + 1] = 0.0f; point[3 * i + 2] = 0.0f; }
+        return;
+    }
+    const float3 q = make_float3(Q[3 * i], Q[3 * i + 1], Q[3 * i + 2]);
+    write_weights(T, __ldg(iperm + f), dist2[i], q, i, bary, point);
+}
+
 // Writes the outputs of one query (recomputing the weights of the winning face).
 __device__ __forceinline__ void write_hit(const Traversal &T, const Hit &h, float3 q, int64_t i,
                                           int *face, float *bary, float *point, float *dist2) {
@@ -965,20 +1003,7 @@ __device__ __forceinline__ void write_hit(const Traversal &T, const Hit &h, floa
     }
     if (face) face[i] = h.face;
     if (dist2) dist2[i] = h.d2;
-    if (bary || point) {
-        const float4 *t = T.tris + 3 * (size_t)h.leaf;
-        float4 a = ldg4(t), b = ldg4(t + 1), c = ldg4(t + 2);
-        float u, v, w;
-        tri_closest(q, xyz(a), xyz(b), xyz(c), b.w != 0.0f, u, v, w);
-        if (weights_need_f64(xyz(a), xyz(b), xyz(c), h.d2))
-            tri_weights_f64(q, xyz(a), xyz(b), xyz(c), b.w != 0.0f, u, v, w);
-        if (bary) { bary[3 * i] = u; bary[3 * i + 1] = v; bary[3 * i + 2] = w; }
-        if (point) {
-            point[3 * i] = u * a.x + v * b.x + w * c.x;
-            point[3 * i + 1] = u * a.y + v * b.y + w * c.y;
-            point[3 * i + 2] = u * a.z + v * b.z + w * c.z;
-        }
-    }
+    if (bary || point) write_weights(T, h.leaf, h.d2, q, i, bary, point);
 }
 
 // kMode: 0 depth-first, 1 while-while, 2 depth-first with one leaf-test site,
@@ -2090,6 +2115,7 @@ struct ContactWs {
     unsigned int *cls;
     int *order;
     int4 *counts;
+    float *d2;             // the distances, when the caller does not take them
     size_t bytes;
 };
 
@@ -2097,10 +2123,14 @@ static ContactWs contact_ws(void *ws, int64_t n) {
     size_t off = 0;
     auto take = [&](size_t b) { size_t o = off; off = align_up(off + b, 256); return o; };
     int64_t m = n > 0 ? n : 1;
-    size_t oC = take(4 * m), oO = take(4 * m), oT = take(16 * ((m + kClassTile - 1) / kClassTile));
+    size_t oC = take(4 * m), oO = take(4 * m), oT = take(16 * ((m + kClassTile - 1) / kClassTile)),
+           oD = take(4 * m);
     char *b = (char *)ws;
-    return ContactWs{(unsigned int *)(b + oC), (int *)(b + oO), (int4 *)(b + oT), off};
+    return ContactWs{(unsigned int *)(b + oC), (int *)(b + oO), (int4 *)(b + oT), (float *)(b + oD), off};
 }
+
+// The contact step's weights in their own launch after the search (k_hit_weights).
+constexpr bool kContactSplitWeights = true;
 
 mesh_status mesh_knn_project(const mesh_bvh *bvh, const float *d_Q, int64_t nQ, int k,
                              const float *d_anchor, float anchor_weight, float *d_point,
@@ -2151,13 +2181,22 @@ mesh_status mesh_contact(const mesh_bvh *bvh, const float *d_Q, int64_t nQ, floa
     Traversal T = traversal_of(bvh, isinf(max_dist));
     Header *h = bvh->hdr();
     const int *iperm = bvh->iperm();
+    // the search writes face and distance; the weights follow in one thread per query
+    const bool split = kContactSplitWeights && variant != 12 && (d_bary || d_point);
+    float *sb = split ? nullptr : d_bary, *sp = split ? nullptr : d_point;
+    float *sd = split && !d_dist2 ? w.d2 : d_dist2;
     if (bvh->leaf_size > 1)
-        launch_contact<true>(T, h, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2, iperm, w.order, w.cls,
-                             variant, bvh->cfg_block, s);
+        launch_contact<true>(T, h, d_Q, nQ, maxd2, d_face, sb, sp, sd, iperm, w.order, w.cls, variant,
+                             bvh->cfg_block, s);
     else
-        launch_contact<false>(T, h, d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2, iperm, w.order, w.cls,
-                              variant, bvh->cfg_block, s);
+        launch_contact<false>(T, h, d_Q, nQ, maxd2, d_face, sb, sp, sd, iperm, w.order, w.cls, variant,
+                              bvh->cfg_block, s);
     count_launch();
+    if (split) {
+        pdl_launch(k_hit_weights, grid_for(nQ, 256), 256, 0, s, T, d_Q, nQ, (const int *)d_face, (const float *)sd,
+                   iperm, d_bary, d_point);
+        count_launch();
+    }
     return check_launch();
 }
 

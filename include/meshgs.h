@@ -366,7 +366,10 @@ size_t mesh_contact_workspace_bytes(int64_t nQ);
  * carries state from one step to the next: pass the same workspace every
  * step for the same particles; its contents steer only the order (a fresh
  * or unrelated workspace gives a worse order, never a wrong answer).
- * Answers equal mesh_closest_point's bit for bit.
+ * Answers equal mesh_closest_point's bit for bit.  The one-thread searches
+ * write face and distance; the weights and closest points (when asked for)
+ * follow in a second launch with one thread per query (the distances are kept
+ * in d_ws when d_dist2 is NULL).
  * Traversal variants 1, 10, 11 and cooperative groups run unordered without
  * classes (the warp packets of variant 12 take the classes, counting for each
  * query the nodes whose children it needed).  d_ws:
@@ -377,7 +380,8 @@ mesh_status mesh_contact(const mesh_bvh *bvh, const float *d_Q, int64_t nQ, floa
 
 /* Work counters of the one-thread depth-first traversal for these queries:
  * d_counts[0] = node visits (each reads one 64-byte record holding two child
- * boxes), d_counts[1] = triangle tests, d_counts[2] = queries with a face
+ * boxes; with traversal variant 13, 4-wide records of 128 bytes), d_counts[1] =
+ * triangle tests, d_counts[2] = queries with a face
  * within max_dist; uint64, summed over all queries.  Runs a separate counting
  * kernel; writes no query results.  For roofline accounting and diagnosis. */
 mesh_status mesh_closest_point_stats(const mesh_bvh *bvh, const float *d_Q, int64_t nQ,

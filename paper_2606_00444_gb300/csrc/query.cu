@@ -1759,6 +1759,9 @@ static size_t chamfer_blocks(int64_t n, int G = 1) {
 // the GPU (two resident blocks of threads per SM), otherwise the smallest power
 // of two G <= 32 that does.  (An explicit override can come from
 // mesh_set_query_group.)
+// The one-thread searches' weights in their own launch after the search (k_hit_weights).
+constexpr bool kContactSplitWeights = true;
+
 static int g_group_override = 0;
 static int g_traversal = 0;          // one-thread traversal variant, see mesh_set_traversal
 
@@ -2013,13 +2016,25 @@ mesh_status mesh_closest_point_hinted(const mesh_bvh *bvh, const float *d_Q, int
     if (variant >= 10 && variant <= 12 && nQ >= ((int64_t)1 << 31)) variant = 0;   // 32-bit work counter
     if (G == 1 && variant == 13) ensure_wide(bvh, s);
     Traversal T = traversal_of(bvh, isinf(max_dist));
+    // the one-thread depth-first searches write face and distance; the weights and
+    // closest points follow in one thread per query (as in the contact step)
+    const int rv = (bvh->leaf_size > 1 && !(variant == 0 || variant == 2 || variant == 3 || variant == 13))
+                       ? 0 : variant;
+    const bool split = kContactSplitWeights && G == 1 && d_face && d_dist2 && (d_bary || d_point) &&
+                       !(rv == 1 || (rv >= 10 && rv <= 12));
+    float *sb = split ? nullptr : d_bary, *sp = split ? nullptr : d_point;
     if (bvh->leaf_size > 1)
-        launch_closest_point<true>(T, bvh->hdr(), d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2, d_hint,
+        launch_closest_point<true>(T, bvh->hdr(), d_Q, nQ, maxd2, d_face, sb, sp, d_dist2, d_hint,
                                    iperm, G, variant, bvh->cfg_block, s);
     else
-        launch_closest_point<false>(T, bvh->hdr(), d_Q, nQ, maxd2, d_face, d_bary, d_point, d_dist2, d_hint,
+        launch_closest_point<false>(T, bvh->hdr(), d_Q, nQ, maxd2, d_face, sb, sp, d_dist2, d_hint,
                                     iperm, G, variant, bvh->cfg_block, s);
     count_launch();
+    if (split) {
+        pdl_launch(k_hit_weights, grid_for(nQ, 256), 256, 0, s, T, d_Q, nQ, (const int *)d_face,
+                   (const float *)d_dist2, iperm, d_bary, d_point);
+        count_launch();
+    }
     return check_launch();
 }
 
@@ -2129,8 +2144,6 @@ static ContactWs contact_ws(void *ws, int64_t n) {
     return ContactWs{(unsigned int *)(b + oC), (int *)(b + oO), (int4 *)(b + oT), (float *)(b + oD), off};
 }
 
-// The contact step's weights in their own launch after the search (k_hit_weights).
-constexpr bool kContactSplitWeights = true;
 
 mesh_status mesh_knn_project(const mesh_bvh *bvh, const float *d_Q, int64_t nQ, int k,
                              const float *d_anchor, float anchor_weight, float *d_point,

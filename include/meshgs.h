@@ -234,7 +234,9 @@ mesh_status mesh_refit_bind(mesh_bvh *bvh, const float *d_V, int64_t nV, const i
  * (faces whose exact distances are within ~1e-7 x the coordinate magnitude of
  * each other or of the window's edge).  A query with no face within max_dist
  * (INFINITY = no cutoff) gets face -1, dist2 = +inf, bary = point = 0.  Any
- * output pointer may be NULL (not written). */
+ * output pointer may be NULL (not written).  With the one-thread depth-first
+ * variants, a call that takes faces and distances and weights or points runs
+ * as two launches: the search, then the weights and points of the hits. */
 mesh_status mesh_closest_point(const mesh_bvh *bvh, const float *d_Q, int64_t nQ,
                                float max_dist, int32_t *d_face, float *d_bary, float *d_point,
                                float *d_dist2, void *stream);
@@ -245,8 +247,8 @@ mesh_status mesh_closest_point(const mesh_bvh *bvh, const float *d_Q, int64_t nQ
  * the final tie window is still reached, so the answer is the one without the
  * hint, bit for bit; the hint changes only the work.  d_hint may be the same
  * array as d_face (each query reads its hint before writing its face).  Used by
- * the depth-first one-thread variants (0, 2-9), the warp packets (12) and the
- * cooperative groups (lanes > 1); variants 1, 10 and 11 ignore it. */
+ * the depth-first one-thread variants (0, 2-9, 13), the warp packets (12) and
+ * the cooperative groups (lanes > 1); variants 1, 10 and 11 ignore it. */
 mesh_status mesh_closest_point_hinted(const mesh_bvh *bvh, const float *d_Q, int64_t nQ,
                                       float max_dist, const int32_t *d_hint, int32_t *d_face,
                                       float *d_bary, float *d_point, float *d_dist2, void *stream);

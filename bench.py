@@ -585,6 +585,12 @@ def gpu_arm(args, rank, world, local_rank):
     return out, W
 
 
+def node_bytes(cfg: dict) -> int:
+    """Bytes one counted visit reads: a 64-byte node record, or a 128-byte 4-wide record
+    with the one-thread traversal variant 13."""
+    return WIDE_BYTES if (cfg.get("variant") == 13 and cfg.get("lanes", 1) == 1) else NODE_BYTES
+
+
 def traversal_label(cfg: dict) -> str:
     """Key of a contact-kernel configuration: leaf size, variant, threads per block."""
     return f"L{cfg.get('leaf', 1)}/v{cfg['variant']}/b{cfg.get('block', 128)}"
@@ -823,8 +829,7 @@ def bench_contact(args):
             tc.append(e[1].elapsed_time(e[2]))
     l2 = l2_read_bandwidth()
     vis, tst = stats["visits"] / N_PART, stats["tests"] / N_PART
-    node_bytes = WIDE_BYTES if (tuned["variant"] == 13 and tuned["lanes"] == 1) else NODE_BYTES
-    bpq = CONTACT_BYTES + node_bytes * vis + TRI_BYTES * tst
+    bpq = CONTACT_BYTES + node_bytes(tuned) * vis + TRI_BYTES * tst
     line = {"metric": "contact kernel and refit alone", "workload": "contact", "steps": args.steps,
             "warmup": args.warmup, "tuned": tuned,
             "contact_ms": {"median": float(np.median(tc)), "mean": float(np.mean(tc)),
@@ -1269,8 +1274,8 @@ def main():
     vis = res["stats"]["visits"] / N_PART
     tst = res["stats"]["tests"] / N_PART
     # (with the 4-wide traversal the counting form counts its 128-byte records)
-    node_bytes = WIDE_BYTES if (res["tuned"]["variant"] == 13 and res["tuned"]["lanes"] == 1) else NODE_BYTES
-    per_query = CONTACT_BYTES + node_bytes * vis + TRI_BYTES * tst
+    nb = node_bytes(res["tuned"])
+    per_query = CONTACT_BYTES + nb * vis + TRI_BYTES * tst
     achieved = per_query * N_PART / t_contact / 1e9
     rec = contact_traffic(res["tuned"]) if res["tuned"]["lanes"] == 1 else None
     rec = rec or {}
@@ -1284,7 +1289,7 @@ def main():
             "traffic": dram,
             "bytes_per_query": per_query,
             "per_query": {"io": CONTACT_BYTES, "node_visits": vis, "triangle_tests": tst,
-                          "node_bytes": node_bytes, "triangle_bytes": TRI_BYTES},
+                          "node_bytes": nb, "triangle_bytes": TRI_BYTES},
             "algorithmic_over_hbm_peak": achieved / hbm,
             "hbm": {"bytes_per_launch": dram, "achieved": dram / t_contact / 1e9 if dram else None,
                     "peak": hbm, "peak_source": src,

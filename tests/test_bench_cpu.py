@@ -47,3 +47,7 @@ def test_traffic_record_is_used_only_for_the_captured_sources():
         assert got == (rec if current else None)
     assert bench.contact_traffic("L9/v99/b7") is None
     assert bench.traversal_label({"leaf": 2, "lanes": 1, "variant": 3, "block": 64}) == "L2/v3/b64"
+    # a counted visit reads a 64-byte node record, or a 128-byte 4-wide record (variant 13)
+    assert bench.node_bytes({"lanes": 1, "variant": 13}) == 128
+    assert bench.node_bytes({"lanes": 1, "variant": 2}) == 64
+    assert bench.node_bytes({"lanes": 4, "variant": 13}) == 64

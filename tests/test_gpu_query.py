@@ -364,3 +364,27 @@ def test_wide_records_follow_the_tree(c1, leaf):
     check_closest(V, FG, Q, got[0.05], max_dist=0.05)
     bvh.set_query_config(-1, -1)
     assert bvh.status()[0] == 0
+
+
+def test_wide_traversal_on_tiny_deep_and_degenerate_meshes():
+    """Variant 13 on meshes of 1, 2, 3 and 5 faces (a single record, records with empty
+    slots), on 40 copies of one triangle (a 39-level chain of ties) and on faces with
+    coincident vertices: the oracle's answers, bounded and unbounded."""
+    V = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [1, 1, 0], [2, 0.5, 0.3]], np.float32)
+    meshes = [(V, np.array(F, np.int32)) for F in
+              ([[0, 1, 2]], [[0, 1, 2], [1, 3, 2]], [[0, 1, 2], [1, 3, 2], [1, 4, 3]],
+               [[0, 1, 2], [1, 3, 2], [1, 4, 3], [0, 4, 2], [3, 4, 0]])]
+    meshes.append((V, np.tile(np.array([[0, 1, 2]], np.int32), (40, 1))))
+    Vd, Fd = icosphere(2)
+    Fd = Fd.copy()
+    Fd[::7, 1] = Fd[::7, 0]
+    meshes.append((Vd.astype(np.float32), Fd))
+    for Vm, Fm in meshes:
+        lo, hi = Vm.min(0) - 0.5, Vm.max(0) + 0.5
+        Q = uniform_box(300, lo, hi, seed=int(Fm.shape[0]))
+        for method in ("lbvh", "ploc"):
+            bvh = MeshBVH.from_mesh(dev(Vm), dev(Fm), method=method)
+            bvh.set_query_config(1, 13)
+            check_closest(Vm, Fm, Q, bvh.closest_point(dev(Q)))
+            check_closest(Vm, Fm, Q, bvh.closest_point(dev(Q), max_dist=0.3), max_dist=0.3)
+            assert bvh.status()[0] == 0

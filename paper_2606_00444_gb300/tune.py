@@ -4,7 +4,7 @@ The best traversal depends on the workload: how many queries there are
 (whether one thread per query fills the GPU), whether a cutoff bounds the
 search, and the mesh.  `tune_closest_point` times every candidate -- the leaf
 size of the tree (1, 2, 4, 8 faces per collapsed leaf), lanes per query (1, 2,
-4, ..., 32) and, for one lane, the thirteen traversal variants of
+4, ..., 32) and, for one lane, the fourteen traversal variants of
 mesh_set_traversal, the main ones also in blocks of 32 and 64 threads -- on
 the caller's own BVH and queries with CUDA events, keeps the fastest, and
 applies it (a new leaf size takes a refit of the tree from its current

@@ -415,8 +415,11 @@ mesh_status mesh_set_query_group(int lanes);
  *  13 depth-first over 4-wide records (each visit tests up to four boxes:
  *     the node's children, an internal child replaced by its two; about half
  *     the visits of the binary tree), 8 shared entries; the records are
- *     written from the binary tree by the first such query after a build or
- *     refit (layout off_wide)
+ *     written from the binary tree by every build or refit of a handle whose
+ *     traversal is 13, else by the first such query after one (layout
+ *     off_wide; a host-side flag per handle: a captured graph that queries
+ *     with 13 relies on the handle's refits writing them, so keep the handle
+ *     at 13 while such a graph is replayed)
  * (the shared part of the stack spills to local memory; local-only leaves the
  * SM's L1 to the node cache).  Process-wide; the same answers, bit for bit,
  * for every variant. */

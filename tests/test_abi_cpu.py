@@ -60,8 +60,15 @@ def test_create_validates_storage_on_the_host():
     assert L.mesh_bvh_get_layout(h, C.byref(lay)) == 0
     assert lay.max_faces == 16 and lay.storage_bytes == need
     offs = [lay.off_header, lay.off_verts, lay.off_faces, lay.off_keys, lay.off_perm,
-            lay.off_nodes, lay.off_parent, lay.off_tris, lay.off_rend, lay.off_iperm, lay.off_adj, lay.off_fnorm, lay.off_xlist]
+            lay.off_nodes, lay.off_parent, lay.off_tris, lay.off_rend, lay.off_iperm, lay.off_adj, lay.off_fnorm, lay.off_xlist,
+            lay.off_wide]
     assert offs == sorted(offs) and all(o % 256 == 0 for o in offs)
+    # the 4-wide records: 128 bytes per internal node, the last array of the block
+    assert lay.off_wide + 128 * (16 - 1) <= lay.storage_bytes
+    # traversal variants 0-13, -1 = the process-wide setting; anything else is refused
+    assert L.mesh_bvh_set_query_config(h, 1, 13) == 0 and L.mesh_bvh_set_query_config(h, 1, 14) == 1
+    assert L.mesh_bvh_set_query_config(h, -1, -1) == 0
+    assert L.mesh_set_traversal(14) == 1 and L.mesh_set_traversal(-1) == 1
     # argument errors are caught before anything is launched
     n0 = L.mesh_launch_count()
     assert L.mesh_build_lbvh(h, None, 10, None, 16, None, 0, None) == 1
